@@ -1,0 +1,24 @@
+"""FP64 CPU oracle for finite-temperature CCSD (White & Chan, arXiv:2004.01729).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this
+package: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` use it.  It shares no code with the CUDA library in
+``paper_2004_01729_gb300/`` (no kernels, helpers, tables or constants); the
+only common module is the seeded input generator
+``paper_2004_01729_gb300/workloads.py``, which holds no FT-CC arithmetic.
+
+Contents
+  systems.py  model Hamiltonians (1D Hubbard in k space, plane-wave UEG,
+              generic), built from their textbook definitions.
+  ftccsd.py   reference quantities, thermal integrals (App. A), the Simpson
+              quadrature tensors (Sec. II.C, Eqs. g/G), the E, S1, S2
+              kernels term by term (Eqs. E, ccS1, ccS2), the integral-form
+              fixed point (Eq. smu / Alg. 2), the lambda equations (Eqs.
+              Lagrangian, lmu, ltilde) and response outputs (App. B).
+  exact.py    exact grand potentials (Fock-space diagonalisation and
+              non-interacting closed forms) used only to pin the oracle.
+
+Every function is plain and slow by design; torch is used on the CPU in
+float64 so that reverse-mode differentiation is available for the lambda
+equations and the property derivatives.
+"""
