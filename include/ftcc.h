@@ -206,8 +206,18 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
                                  ftcc_quadrature quad, const ftcc_options* opt);
 
 /* Response of the converged solve (Eqs. Lagrangian, lmu, ltilde; App. B).
- * Not implemented in this build: returns FTCC_ERR_UNSUPPORTED after a
- * converged solve, FTCC_ERR_STATE before one. */
+ * Solves the lambda equations in FP64 (the stationarity of the discrete
+ * Lagrangian: the transposed propagation of Eq. ltilde and the transpose of
+ * the S kernel, Eq. lmu, iterated from lambda = 0), then differentiates the
+ * Lagrangian at fixed (s, lambda): through the Fermi factors and the thermal
+ * Fock matrix of every integral block, the propagator (Delta and the grid,
+ * both exact for the discrete scheme), and Omega0 + Omega1.  Fills `out`
+ * (dOmega/dmu, dOmega/dbeta, N, E, S, trace of the 1-RDM) and, if rdm1 is not
+ * NULL, the partially relaxed density p^cc (N*N host doubles, rdm1[q*N + p]
+ * pairs with a perturbation X[p][q]; diagonal entries include the orbital
+ * energy and occupation response).  A low-precision solve is first refined
+ * in FP64.  FTCC_ERR_STATE without a converged solve; FTCC_ERR_NOT_CONVERGED
+ * when the lambda iteration does not converge. */
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* ctx, ftcc_adjoint_result* out, double* rdm1);
 
 /* Copy the current amplitudes (FP64, layouts above) to host buffers of
@@ -227,6 +237,22 @@ ftcc_status ftcc_eval_s(ftcc_ctx* ctx, int nx, int precision, const double* t1_d
  * with Delta from the slot classes `slots` ("ia" or "ijab": hole letters
  * i..n, particle letters a..h).  S_dev, s_dev: FP64 device [ngrid][size]. */
 ftcc_status ftcc_propagate(ftcc_ctx* ctx, const char* slots, const double* S_dev, double* s_dev);
+
+/* Vector-Jacobian product of the S kernel (the transpose that the lambda
+ * equations, Eqs. lmu/ltilde, apply): t1bar = (dS1/ds1)^T w1 + (dS2/ds1)^T w2,
+ * t2bar likewise, at the caller's amplitudes t1_dev/t2_dev for nx tau slices
+ * of the prepared single-instance problem, in FP64.  Shapes as ftcc_eval_s;
+ * all pointers FP64 device memory (w1/w2 are not modified). */
+ftcc_status ftcc_eval_s_vjp(ftcc_ctx* ctx, int nx, const double* t1_dev, const double* t2_dev, const double* w1_dev,
+                            const double* w2_dev, double* t1bar_dev, double* t2bar_dev);
+
+/* Transpose of ftcc_propagate: u[x][mu] = sum_y G[y,x] exp(Delta_mu (tau_x - tau_y)) m[y][mu]
+ * (the propagation of lambda-tilde in Eq. ltilde, App. A, up to the weights g). */
+ftcc_status ftcc_propagate_adjoint(ftcc_ctx* ctx, const char* slots, const double* m_dev, double* u_dev);
+
+/* Copy the converged weighted multipliers m_y = g_y lambda_y / beta of the
+ * context's instance (layouts of s1 / s2) after ft_ccsd_adjoint. */
+ftcc_status ftcc_get_lambda(ftcc_ctx* ctx, double* m1, double* m2);
 
 /* Dense GEMM on the tensor-core engine, exposed for testing:
  * C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (A, B, C FP32 for

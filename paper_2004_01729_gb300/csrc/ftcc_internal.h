@@ -152,4 +152,25 @@ cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, 
                           const int* live, double* state, cudaStream_t st);
 double simpson_weight_host(int y, int ng);
 
+// ---- adjoint ----
+// u[z][x][mu] = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m[z][y][mu] (transpose of the propagation)
+cudaError_t launch_propagate_t(const double* m, double* u, const PropArgs& a, cudaStream_t st);
+// m_new = -c[z][x] * base' - tbar with base' = cbase * base[z][mu] (cbase != 0, tau-independent base)
+// or base[z][x][mu] (cbase == 0); partials [nblocks][2] = max|m_new - m_old|, max|m_new|
+cudaError_t launch_lambda_combine(const double* base, const double* tbar, double* mnew, const double* mold,
+                                  long long size, int ng, int nz, const double* cz, double cbase, double* partials,
+                                  int nblocks, cudaStream_t st);
+
+// ---- response (App. B) ----
+// Do[z][q] / Dv[z][q] += sum A*I over elements with a hole-like / particle-like
+// slot at position q; cls bit k set = slot k particle-like.  dims[nslot].
+cudaError_t launch_slot_sums(const double* I, const double* A, int nslot, const int* dims, int cls, int no, int nv,
+                             int nz, double* Do, double* Dv, cudaStream_t st);
+cudaError_t launch_fbar_scatter(const double* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
+                                const int* i1, const double* f1, long long f1z, int N, int nz, double* Fb,
+                                cudaStream_t st);
+cudaError_t launch_fock_n(const double* Fb, const double* eri, int N, double* Gn, cudaStream_t st);
+cudaError_t launch_prop_response(const double* S, const double* m, const double* epsz, const PropArgs& a, double* Ee,
+                                 double* Eb, cudaStream_t st);
+
 }  // namespace ftcc

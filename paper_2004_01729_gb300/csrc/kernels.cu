@@ -476,6 +476,284 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
   }
 }
 
+// Transposed propagation: u_x = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m_y,
+// the adjoint of the Simpson recurrences above, run from the last tau point
+// down with the even-chain adjoint E'_y = m_y + r^2 E'_{y+2} + r^3 m_{y+3}.
+template <int NS>
+__global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const double* __restrict__ m, double* __restrict__ u,
+                                                                   PropArgs a) {
+  const int ng = a.ng;
+  const int z = blockIdx.y;
+  const long long size = a.size;
+  m += static_cast<long long>(z) * ng * size;
+  u += static_cast<long long>(z) * ng * size;
+  const double* em = a.em + static_cast<long long>(z) * a.N;
+  const double* ep = a.ep + static_cast<long long>(z) * a.N;
+  const double h = a.hz[z];
+  for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
+       mu += static_cast<long long>(gridDim.x) * blockDim.x) {
+    int i, j = 0, aa, b = 0;
+    {
+      uint32_t r = static_cast<uint32_t>(mu);
+      uint32_t q = fdiv(a.fv, r);
+      if (NS == 4) {
+        b = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fo, r);
+        j = r - q * a.no;
+        i = q;
+      } else {
+        aa = r - q * a.nv;
+        i = q;
+      }
+    }
+    const int pi = a.idxO[i], pa = a.idxV[aa];
+    double rr = em[pa] * ep[pi];
+    double ri = ep[pa] * em[pi];
+    if (NS == 4) {
+      const int pj = a.idxO[j], pb = a.idxV[b];
+      rr *= em[pb] * ep[pj];
+      ri *= ep[pb] * em[pj];
+    }
+    const double r2 = rr * rr, r3 = r2 * rr;
+    const double m1 = m[size + mu];
+    double mp1 = 0.0, mp2 = 0.0, mp3 = 0.0;   // m_{x+1}, m_{x+2}, m_{x+3}
+    double Ep1 = 0.0, Ep2 = 0.0;              // E'_{x+1}, E'_{x+2}
+    for (int x = ng - 1; x >= 0; --x) {
+      const double mx = m[static_cast<long long>(x) * size + mu];
+      double Ex = 0.0;
+      if ((x & 1) == 0 && x >= 2) Ex = mx + r2 * Ep2 + r3 * mp3;
+      double ux = 0.0;
+      if ((x & 1) == 0 && x >= 2) ux += h / 3.0 * Ex;
+      if (((x + 1) & 1) == 0 && x + 1 >= 2 && x + 1 < ng) ux += 4.0 * h / 3.0 * rr * Ep1;
+      if (((x + 2) & 1) == 0 && x + 2 < ng) ux += h / 3.0 * r2 * Ep2;
+      if ((x & 1) == 1 && x >= 3) ux += 3.0 * h / 8.0 * mx;
+      if (((x + 1) & 1) == 1 && x + 1 >= 3 && x + 1 < ng) ux += 9.0 * h / 8.0 * rr * mp1;
+      if (((x + 2) & 1) == 1 && x + 2 >= 3 && x + 2 < ng) ux += 9.0 * h / 8.0 * r2 * mp2;
+      if (((x + 3) & 1) == 1 && x + 3 >= 3 && x + 3 < ng) ux += 3.0 * h / 8.0 * r3 * mp3;
+      if (x == 0) ux += 5.0 * h / 12.0 * rr * m1;
+      if (x == 1) ux += 8.0 * h / 12.0 * m1;
+      if (x == 2) ux -= h / 12.0 * ri * m1;
+      u[static_cast<long long>(x) * size + mu] = ux;
+      mp3 = mp2;
+      mp2 = mp1;
+      mp1 = mx;
+      Ep2 = Ep1;
+      Ep1 = Ex;
+    }
+  }
+}
+
+// m_new = -c_x (f_ov + <ij||ab> s_j^b) - tbar (singles) or -c_x/4 <ij||ab> - tbar
+// (doubles), c_x = g_x / beta, and per-block max|m_new - m_old|, max|m_new|.
+// E'(s) is the derivative of E (Eq. E) with respect to the amplitudes.
+__global__ void lambda_combine_kernel(const double* __restrict__ base, const double* __restrict__ tbar,
+                                      double* __restrict__ mnew, const double* __restrict__ mold, long long size, int ng,
+                                      int nz, const double* __restrict__ cz, double cbase, double* partials) {
+  __shared__ double dm[256], sm[256];
+  double dmax = 0.0, smax = 0.0;
+  const long long total = static_cast<long long>(nz) * ng * size;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long zx = e / size;
+    const long long mu = e - zx * size;
+    const long long z = zx / ng;
+    const int x = static_cast<int>(zx - z * ng);
+    const double c = cz[z * ng + x];
+    const double bval = base[z * size * (cbase != 0.0 ? 1 : ng) + (cbase != 0.0 ? mu : x * size + mu)];
+    const double v = -c * (cbase != 0.0 ? cbase * bval : bval) - tbar[e];
+    dmax = fmax(dmax, fabs(v - mold[e]));
+    smax = fmax(smax, fabs(v));
+    mnew[e] = v;
+  }
+  dm[threadIdx.x] = dmax;
+  sm[threadIdx.x] = smax;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      dm[threadIdx.x] = fmax(dm[threadIdx.x], dm[threadIdx.x + s]);
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = dm[0];
+    partials[2 * blockIdx.x + 1] = sm[0];
+  }
+}
+
+// Response sums of one thermal block (App. B): with I the block and A its
+// Lagrangian adjoint, Do[z][q] += sum of A*I over the elements whose hole-like
+// slot holds orbital position q, Dv likewise for particle-like slots.  These
+// are the derivatives of the Lagrangian with respect to log sqrt(n_q) and
+// log sqrt(1 - n_q).
+__global__ void slot_sums_kernel(const double* __restrict__ I, const double* __restrict__ A, int nslot, int d0, int d1,
+                                 int d2, int d3, int cls, int no, int nv, double* Do, double* Dv) {
+  const int z = blockIdx.y;
+  const long long per = static_cast<long long>(d0) * d1 * d2 * d3;
+  I += z * per;
+  A += z * per;
+  Do += static_cast<long long>(z) * no;
+  Dv += static_cast<long long>(z) * nv;
+  const int dims[4] = {d0, d1, d2, d3};
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < per;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const double p = I[e] * A[e];
+    if (p == 0.0) continue;
+    long long r = e;
+    int c[4];
+    for (int k = nslot - 1; k >= 0; --k) {
+      c[k] = static_cast<int>(r % dims[k]);
+      r /= dims[k];
+    }
+    for (int k = 0; k < nslot; ++k) {
+      if ((cls >> k) & 1) atomicAdd(&Dv[c[k]], p);
+      else atomicAdd(&Do[c[k]], p);
+    }
+  }
+}
+
+// dL/dFbar[p][q] += A[a][b] fac0[a] fac1[b] for a thermal Fock block.
+__global__ void fbar_scatter_kernel(const double* __restrict__ A, int n0, int n1, const int* i0, const double* f0,
+                                    long long f0z, const int* i1, const double* f1, long long f1z, int N, double* Fb) {
+  const int z = blockIdx.y;
+  A += static_cast<long long>(z) * n0 * n1;
+  f0 += z * f0z;
+  f1 += z * f1z;
+  Fb += static_cast<long long>(z) * N * N;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n0 * n1) return;
+  const int a = e / n1, b = e % n1;
+  atomicAdd(&Fb[static_cast<long long>(i0[a]) * N + i1[b]], A[e] * f0[a] * f1[b]);
+}
+
+// Gn[z][r] = sum_pq Fb[z][p][q] <pr||qr>: the occupation dependence of the
+// thermal Fock matrix f = h + sum_r n_r <pr||qr>.
+__global__ void fock_n_kernel(const double* __restrict__ Fb, const double* __restrict__ eri, int N, double* Gn) {
+  const int r = blockIdx.x;
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long pq = threadIdx.x; pq < static_cast<long long>(N) * N; pq += blockDim.x) {
+    const long long p = pq / N, q = pq % N;
+    acc += Fb[pq] * eri[((p * N + r) * N + q) * N + r];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Gn[r] = red[0];
+}
+
+// Propagator dependence of the Lagrangian: per element, with I_y the Simpson
+// integral of S (so s = -I) and J_y = sum_x G[y,x] (tau_y - tau_x) e^{-Delta(tau_y - tau_x)} S_x
+// (from the r-derivative of the recurrences, J = h r dI/dr):
+//   dL/dDelta_mu = -sum_y m_y J_y,   beta dL/dbeta|prop = sum_y m_y (I_y - Delta J_y).
+// Accumulated per orbital (dL/deps_q = sum_mu dL/dDelta_mu dDelta_mu/deps_q)
+// and per instance (beta part).
+template <int NS>
+__global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const double* __restrict__ S,
+                                                                     const double* __restrict__ m, const double* __restrict__ epsz,
+                                                                     PropArgs a, double* Ee, double* Eb) {
+  const int ng = a.ng;
+  const int z = blockIdx.y;
+  const long long size = a.size;
+  S += static_cast<long long>(z) * ng * size;
+  m += static_cast<long long>(z) * ng * size;
+  const double* em = a.em + static_cast<long long>(z) * a.N;
+  const double* ep = a.ep + static_cast<long long>(z) * a.N;
+  const double* eps = epsz + static_cast<long long>(z) * a.N;
+  const double h = a.hz[z];
+  __shared__ double bred[kPropThreads];
+  double bsum = 0.0;
+  for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
+       mu += static_cast<long long>(gridDim.x) * blockDim.x) {
+    int i, j = 0, aa, b = 0;
+    {
+      uint32_t r = static_cast<uint32_t>(mu);
+      uint32_t q = fdiv(a.fv, r);
+      if (NS == 4) {
+        b = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fo, r);
+        j = r - q * a.no;
+        i = q;
+      } else {
+        aa = r - q * a.nv;
+        i = q;
+      }
+    }
+    const int pi = a.idxO[i], pa = a.idxV[aa];
+    double rr = em[pa] * ep[pi];
+    double ri = ep[pa] * em[pi];
+    double delta = eps[pa] - eps[pi];
+    int pj = 0, pb = 0;
+    if (NS == 4) {
+      pj = a.idxO[j];
+      pb = a.idxV[b];
+      rr *= em[pb] * ep[pj];
+      ri *= ep[pb] * em[pj];
+      delta += eps[pb] - eps[pj];
+    }
+    const double r2 = rr * rr, r3 = r2 * rr;
+    const double s0 = S[mu], s1 = S[size + mu], s2 = S[2 * size + mu];
+    double sm1 = 0.0, sm2 = 0.0, sm3 = 0.0;
+    double Il = 0.0, Ip = 0.0, dIl = 0.0, dIp = 0.0;   // last / second-last even I and dI/dr
+    double P1 = 0.0, K = 0.0;
+    for (int y = 0; y < ng; ++y) {
+      const double sy = y == 0 ? s0 : (y == 1 ? s1 : (y == 2 ? s2 : S[static_cast<long long>(y) * size + mu]));
+      double I, dI;
+      if (y == 0) {
+        I = 0.0;
+        dI = 0.0;
+      } else if (y == 1) {
+        I = h / 12.0 * (5.0 * rr * s0 + 8.0 * s1 - ri * s2);
+        dI = h / 12.0 * (5.0 * s0 + ri * ri * s2);
+      } else if ((y & 1) == 0) {
+        I = r2 * Il + h / 3.0 * (r2 * sm2 + 4.0 * rr * sm1 + sy);
+        dI = 2.0 * rr * Il + r2 * dIl + h / 3.0 * (2.0 * rr * sm2 + 4.0 * sm1);
+        Ip = Il;
+        dIp = dIl;
+        Il = I;
+        dIl = dI;
+      } else {
+        I = r3 * Ip + 3.0 * h / 8.0 * (r3 * sm3 + 3.0 * r2 * sm2 + 3.0 * rr * sm1 + sy);
+        dI = 3.0 * r2 * Ip + r3 * dIp + 3.0 * h / 8.0 * (3.0 * r2 * sm3 + 6.0 * rr * sm2 + 3.0 * sm1);
+      }
+      sm3 = sm2;
+      sm2 = sm1;
+      sm1 = sy;
+      const double my = m[static_cast<long long>(y) * size + mu];
+      P1 += my * I;
+      K += my * h * rr * dI;
+    }
+    // dL/dDelta = -K; dDelta/deps: +1 for particle slots, -1 for hole slots
+    if (K != 0.0) {
+      atomicAdd(&Ee[static_cast<long long>(z) * a.N + pa], -K);
+      atomicAdd(&Ee[static_cast<long long>(z) * a.N + pi], K);
+      if (NS == 4) {
+        atomicAdd(&Ee[static_cast<long long>(z) * a.N + pb], -K);
+        atomicAdd(&Ee[static_cast<long long>(z) * a.N + pj], K);
+      }
+    }
+    bsum += P1 - delta * K;
+  }
+  bred[threadIdx.x] = bsum;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) bred[threadIdx.x] += bred[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&Eb[z], bred[0]);
+}
+
 __device__ double simpson_weight(int y, int ng) {
   // g = G^{ng-1} in units of h (reading R1 of the quadrature tensors)
   const int last = ng - 1;
@@ -769,6 +1047,58 @@ double simpson_weight_host(int y, int ng) {
     w += (k == 0 || k == 3) ? 3.0 / 8.0 : 9.0 / 8.0;
   }
   return w;
+}
+
+cudaError_t launch_propagate_t(const double* m, double* u, const PropArgs& a_in, cudaStream_t st) {
+  if (a_in.ng < 3 || a_in.size >= (1LL << 31) || a_in.nz < 1) return cudaErrorInvalidValue;
+  PropArgs a = a_in;
+  a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
+  a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
+  dim3 grid(a.nblocks, a.nz);
+  if (a.nslot == 4) propagate_t_kernel<4><<<grid, kPropThreads, 0, st>>>(m, u, a);
+  else propagate_t_kernel<2><<<grid, kPropThreads, 0, st>>>(m, u, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_combine(const double* base, const double* tbar, double* mnew, const double* mold,
+                                  long long size, int ng, int nz, const double* cz, double cbase, double* partials,
+                                  int nblocks, cudaStream_t st) {
+  lambda_combine_kernel<<<nblocks, 256, 0, st>>>(base, tbar, mnew, mold, size, ng, nz, cz, cbase, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_sums(const double* I, const double* A, int nslot, const int* dims, int cls, int no, int nv,
+                             int nz, double* Do, double* Dv, cudaStream_t st) {
+  long long per = 1;
+  for (int k = 0; k < nslot; ++k) per *= dims[k];
+  dim3 grid(grid_for(per, 256, 1024), nz);
+  slot_sums_kernel<<<grid, 256, 0, st>>>(I, A, nslot, dims[0], dims[1], nslot > 2 ? dims[2] : 1,
+                                          nslot > 3 ? dims[3] : 1, cls, no, nv, Do, Dv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fbar_scatter(const double* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
+                                const int* i1, const double* f1, long long f1z, int N, int nz, double* Fb,
+                                cudaStream_t st) {
+  dim3 grid((n0 * n1 + 255) / 256, nz);
+  fbar_scatter_kernel<<<grid, 256, 0, st>>>(A, n0, n1, i0, f0, f0z, i1, f1, f1z, N, Fb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fock_n(const double* Fb, const double* eri, int N, double* Gn, cudaStream_t st) {
+  fock_n_kernel<<<N, 256, 0, st>>>(Fb, eri, N, Gn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prop_response(const double* S, const double* m, const double* epsz, const PropArgs& a_in, double* Ee,
+                                 double* Eb, cudaStream_t st) {
+  PropArgs a = a_in;
+  a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
+  a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
+  dim3 grid(a.nblocks, a.nz);
+  if (a.nslot == 4) prop_response_kernel<4><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
+  else prop_response_kernel<2><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
+  return cudaGetLastError();
 }
 
 }  // namespace ftcc

@@ -146,6 +146,12 @@ struct Batch {
   std::unique_ptr<Solver<float>> s32;
   std::unique_ptr<Solver<double>> s64;
   int active = 0;                // 0 = FP64 solver, 1 = FP32 solver
+  // adjoint state (FP64): weighted multipliers m = g lambda / beta, their
+  // back-propagated cotangents u, and the S-kernel VJP
+  Buf m1, m2, mn1, mn2, u1, u2, tb1, tb2, dE1, cz, lpart;
+  Buf facOz, facVz, epsz;        // stacked [nz][no], [nz][nv], [nz][N] for the response
+  bool lambda_done = false;
+  int lambda_iterations = 0;
   int iterations = 0, refine_iterations = 0;
   double ms_total = 0;
   int ms_count = 0;
@@ -175,6 +181,27 @@ struct Solver {
   long long gemm_flops = 0;   // algorithmic GEMM flops counted while `counting`
   bool counting = false;
 
+  // Tape of one S-kernel pass, replayed backwards for the vector-Jacobian
+  // product (the lambda equations are the transpose of the S kernel).
+  struct Op {
+    int kind;                  // 0 contract, 1 scatter, 2 tau build, 3 X build
+    T* C;
+    std::string Lc;
+    const T* A;
+    std::string La;
+    const T* B;
+    std::string Lb;
+    T* C2;
+    double alpha, beta;
+    std::string anti;
+  };
+  std::vector<Op> tape;
+  bool recording = false;
+  std::map<const void*, T*> bar;            // forward buffer -> its adjoint
+  std::map<const void*, Buf> fixed_bar;     // integral / Fock block -> adjoint (when wanted)
+  bool want_fixed_bar = false;
+  Buf btt, bta, bX, bWmnij, bWabef, bWmbej, bY, bFae, bFmi, bFme, bFt, bFt2, bD, bP, bQ, ones, sx1, sx2;
+
   Solver(Batch* batch, int kind) : b(batch), h_(batch->home), gk(kind) {}
   ~Solver() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -185,8 +212,10 @@ struct Solver {
       h_->put(kv.second.second);
     }
     Buf* bs[] = {&t1, &t2, &S1, &S2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
-                 &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2};
+                 &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2, &btt, &bta, &bX, &bWmnij, &bWabef, &bWmbej,
+                 &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
+    for (auto& kv : fixed_bar) h_->put(kv.second);
   }
   cudaStream_t st() const { return h_->st; }
 
@@ -227,6 +256,7 @@ struct Solver {
   // dst missing from src are broadcast.  anti names letter pairs of dst to
   // antisymmetrise: "", "ij", "ab" or "ijab".
   void scatter(T* dst, const char* Ld, const T* src, const char* Ls, double alpha, double beta, const char* anti) {
+    if (recording) tape.push_back(Op{1, dst, Ld, src, Ls, nullptr, "", nullptr, alpha, beta, anti});
     ScatDesc d{};
     d.nd = static_cast<int>(strlen(Ld));
     auto ss = strides_of(Ls);
@@ -319,6 +349,7 @@ struct Solver {
 
   // C(Lc) = beta_acc * C + alpha * P(sum over shared letters A(La) B(Lb))
   void contract(Tn<T> C, double alpha, Tn<const T> A, Tn<const T> B, const char* anti = "", double beta_acc = 1.0) {
+    if (recording) tape.push_back(Op{0, C.p, C.L, A.p, A.L, B.p, B.L, nullptr, alpha, beta_acc, anti});
     std::string Lc = C.L, La = A.L, Lb = B.L, bat, Ml, Nl, Kl;
     for (char ch : Lc) {
       const bool ia = La.find(ch) != std::string::npos, ib = Lb.find(ch) != std::string::npos;
@@ -375,7 +406,12 @@ struct Solver {
     if (kind == GEMM_F64) CU(gemm_f64(g, st()));
     else if (kind == -1) CU(gemm_f32(g, st()));
     else CU(gemm_tc(kind, g, h_->dev_err, st()));
-    if (!direct) scatter(C.p, C.L, static_cast<const T*>(Ct.p), Lt.c_str(), alpha, beta_acc, anti);
+    if (!direct) {
+      const bool rec = recording;   // part of this contraction, not an op of its own
+      recording = false;
+      scatter(C.p, C.L, static_cast<const T*>(Ct.p), Lt.c_str(), alpha, beta_acc, anti);
+      recording = rec;
+    }
   }
 
   void alloc_chunk() {
@@ -406,6 +442,7 @@ struct Solver {
     using CT = Tn<const T>;
     auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
     auto CF = [this](const char* L) { return Tn<const T>{F(L), L, true}; };
+    if (recording) tape.push_back(Op{2, ptt, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
     CU(launch_tau<T>(t1c, t2c, ptt, pta, 0.5, 1.0, nz * nx, no, nv, st()));
     // F_me = f_me + sum_nf s_n^f <mn||ef>
     scatter(pFme, "zxme", F("zme"), "zme", 1.0, 0.0, "");
@@ -431,6 +468,7 @@ struct Solver {
     scatter(pWmbej, "zxmbej", V("zmbej"), "zmbej", 1.0, 0.0, "");
     contract({pWmbej, "zxmbej"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
     contract({pWmbej, "zxmbej"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
+    if (recording) tape.push_back(Op{3, pX, "", t1c, "", t2c, "", nullptr, 0.5, 1.0, ""});
     CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st()));
     contract({pWmbej, "zxmbej"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
     // S1 (Eq. ccS1)
@@ -457,6 +495,144 @@ struct Solver {
     contract({S2c, "zxijab"}, 1.0, CT{t1c, "zxie"}, CV("zabej"), "ij");
     contract({S2c, "zxijab"}, -1.0, CT{t1c, "zxma"}, CV("zmbij"), "ab");
   }
+
+  bool is_fixed(const void* p) const {
+    for (auto& kv : Vb)
+      if (p >= kv.second.p && p < static_cast<const char*>(kv.second.p) + kv.second.bytes) return true;
+    for (auto& kv : Fb)
+      if (p >= kv.second.p && p < static_cast<const char*>(kv.second.p) + kv.second.bytes) return true;
+    return false;
+  }
+  T* fixed_adjoint(const void* p) {
+    for (auto* mp : {&Vb, &Fb})
+      for (auto& kv : *mp)
+        if (kv.second.p == p) {
+          Buf& b = fixed_bar[p];
+          if (!b.p) {
+            ensure(h_, b, kv.second.bytes);
+            CU(cudaMemsetAsync(b.p, 0, kv.second.bytes, st()));
+          }
+          return static_cast<T*>(b.p);
+        }
+    throw Fail{FTCC_ERR_STATE, "adjoint of an unknown fixed operand"};
+  }
+  void zero(T* p, const char* L) {
+    long long n = 1;
+    for (const char* q = L; *q; ++q) n *= dimof(*q);
+    CU(cudaMemsetAsync(p, 0, n * sizeof(T), st()));
+  }
+  T* adj(const void* p) {
+    auto it = bar.find(p);
+    if (it == bar.end()) throw Fail{FTCC_ERR_STATE, "tape operand without adjoint"};
+    return it->second;
+  }
+
+  // Vector-Jacobian product of the S kernel for nx tau slices of every
+  // instance: given cotangents w1 (S1 shape) and w2 (S2 shape), overwrites
+  // t1bar, t2bar with (dS/ds)^T w.  w1 and w2 are used as scratch.  With
+  // want_fixed_bar the adjoints of the integral and Fock blocks accumulate in
+  // fixed_bar (not cleared here).
+  void vjp(const T* t1c, const T* t2c, T* w1, T* w2, T* t1bar, T* t2bar, int nxcur) {
+    const long long o = no, v = nv, x = static_cast<long long>(nxcur) * nz;
+    // adjoint buffers sized like the chunk intermediates
+    Buf* pairs[][2] = {{&btt, &tt}, {&bta, &ta}, {&bX, &X}, {&bWmnij, &Wmnij}, {&bWabef, &Wabef}, {&bWmbej, &Wmbej},
+                       {&bY, &Y}, {&bFae, &Fae}, {&bFmi, &Fmi}, {&bFme, &Fme}, {&bFt, &Ft}, {&bFt2, &Ft2}};
+    for (auto& pr : pairs) {
+      ensure(h_, *pr[0], pr[1]->bytes);
+      CU(cudaMemsetAsync(pr[0]->p, 0, pr[1]->bytes, st()));
+    }
+    const size_t big = std::max(std::max(o * o * v * v, v * v * v * v), o * o * o * o) * static_cast<size_t>(x) * sizeof(T);
+    ensure(h_, bD, big);
+    ensure(h_, bP, x * o * o * v * v * sizeof(T));
+    ensure(h_, bQ, x * o * o * v * v * sizeof(T));
+    ensure(h_, sx1, x * o * v * sizeof(T));
+    ensure(h_, sx2, x * o * o * v * v * sizeof(T));
+    ensure(h_, ones, static_cast<size_t>(nz) * nxc * sizeof(T));
+    {
+      std::vector<T> h1(static_cast<size_t>(nz) * nxc, T(1));
+      CU(cudaMemcpyAsync(ones.p, h1.data(), h1.size() * sizeof(T), cudaMemcpyHostToDevice, st()));
+      CU(cudaStreamSynchronize(st()));
+    }
+    // forward pass on the tape
+    tape.clear();
+    recording = true;
+    try {
+      s_kernel(t1c, t2c, static_cast<T*>(sx1.p), static_cast<T*>(sx2.p), nxcur);
+    } catch (...) {
+      recording = false;
+      throw;
+    }
+    recording = false;
+    bar.clear();
+    for (auto& pr : pairs) bar[pr[1]->p] = static_cast<T*>(pr[0]->p);
+    bar[sx1.p] = w1;
+    bar[sx2.p] = w2;
+    bar[t1c] = t1bar;
+    bar[t2c] = t2bar;
+    CU(cudaMemsetAsync(t1bar, 0, x * o * v * sizeof(T), st()));
+    CU(cudaMemsetAsync(t2bar, 0, x * o * o * v * v * sizeof(T), st()));
+    using CT = Tn<const T>;
+    T* dbuf = static_cast<T*>(bD.p);
+    for (auto it = tape.rbegin(); it != tape.rend(); ++it) {
+      const Op& op = *it;
+      if (op.kind == 0) {
+        T* cb = adj(op.C);
+        const T* D = cb;
+        if (op.alpha != 1.0 || !op.anti.empty()) {
+          scatter(dbuf, op.Lc.c_str(), cb, op.Lc.c_str(), op.alpha, 0.0, op.anti.c_str());
+          D = dbuf;
+        }
+        for (int side = 0; side < 2; ++side) {
+          const T* X = side == 0 ? op.A : op.B;
+          const std::string& LX = side == 0 ? op.La : op.Lb;
+          const T* Y = side == 0 ? op.B : op.A;
+          const std::string& LY = side == 0 ? op.Lb : op.La;
+          T* xb = nullptr;
+          if (!is_fixed(X)) xb = adj(X);
+          else if (want_fixed_bar) xb = fixed_adjoint(X);
+          if (xb) contract({xb, LX.c_str()}, 1.0, CT{D, op.Lc.c_str()}, CT{Y, LY.c_str()}, "", 1.0);
+        }
+        if (op.beta == 0.0) zero(cb, op.Lc.c_str());
+      } else if (op.kind == 1) {
+        T* db = adj(op.C);
+        if (!is_fixed(op.A)) {
+          scatter(adj(op.A), op.La.c_str(), db, op.Lc.c_str(), op.alpha, 1.0, op.anti.c_str());
+        } else if (want_fixed_bar) {
+          // broadcast copy of a block over tau: its adjoint sums over tau
+          const T* src = db;
+          if (!op.anti.empty()) {
+            scatter(dbuf, op.Lc.c_str(), db, op.Lc.c_str(), 1.0, 0.0, op.anti.c_str());
+            src = dbuf;
+          }
+          contract({fixed_adjoint(op.A), op.La.c_str()}, op.alpha, CT{src, op.Lc.c_str()}, CT{static_cast<const T*>(ones.p), "zx"}, "",
+                   1.0);
+        }
+        if (op.beta == 0.0) zero(db, op.Lc.c_str());
+      } else if (op.kind == 2) {
+        // tt = t2 + 1/2 p, ta = t2 + p, p_ijab = t_ia t_jb - t_ib t_ja
+        T* ttb = adj(op.C);
+        T* tab = adj(op.C2);
+        T* t2b = adj(op.B);
+        T* t1b = adj(op.A);
+        T* P = static_cast<T*>(bP.p);
+        T* Q = static_cast<T*>(bQ.p);
+        scatter(t2b, "zxijab", ttb, "zxijab", 1.0, 1.0, "");
+        scatter(t2b, "zxijab", tab, "zxijab", 1.0, 1.0, "");
+        scatter(P, "zxijab", tab, "zxijab", 1.0, 0.0, "");
+        scatter(P, "zxijab", ttb, "zxijab", 0.5, 1.0, "");
+        scatter(Q, "zxijab", P, "zxijab", 1.0, 0.0, "ijab");
+        contract({t1b, "zxkc"}, 1.0, CT{Q, "zxkjcb"}, CT{op.A, "zxjb"}, "", 1.0);
+      } else {
+        // X[j,n,f,b] = 1/2 t2[j,n,f,b] + t1[j,f] t1[n,b]
+        T* xb = adj(op.C);
+        T* t2b = adj(op.B);
+        T* t1b = adj(op.A);
+        scatter(t2b, "zxjnfb", xb, "zxjnfb", 0.5, 1.0, "");
+        contract({t1b, "zxjf"}, 1.0, CT{xb, "zxjnfb"}, CT{op.A, "zxnb"}, "", 1.0);
+        contract({t1b, "zxnb"}, 1.0, CT{xb, "zxjnfb"}, CT{op.A, "zxjf"}, "", 1.0);
+      }
+    }
+  }
 };
 
 Batch::~Batch() {
@@ -466,7 +642,8 @@ Batch::~Batch() {
     Buf* bs[] = {&I.n, &I.nbar, &I.f, &I.fbar, &I.facO, &I.facV};
     for (Buf* q : bs) home->put(*q);
   }
-  Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live};
+  Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
+               &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -883,6 +1060,17 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
                                    static_cast<double*>(B->F64.p) + z * no * nv, home->st));
     hb[z] = I.hstep;
     hb[n + z] = I.beta;
+    if (z == 0) {
+      ensure(home, B->facOz, static_cast<size_t>(n) * no * sizeof(double));
+      ensure(home, B->facVz, static_cast<size_t>(n) * nv * sizeof(double));
+      ensure(home, B->epsz, static_cast<size_t>(n) * N * sizeof(double));
+    }
+    CU(cudaMemcpyAsync(static_cast<double*>(B->facOz.p) + z * no, fo.data(), no * sizeof(double), cudaMemcpyHostToDevice,
+                       home->st));
+    CU(cudaMemcpyAsync(static_cast<double*>(B->facVz.p) + z * nv, fv.data(), nv * sizeof(double), cudaMemcpyHostToDevice,
+                       home->st));
+    CU(cudaMemcpyAsync(static_cast<double*>(B->epsz.p) + z * N, cs[z]->eps.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                       home->st));
     sync(home);   // the host vectors fo / fv must outlive their copies
   }
   CU(cudaMemcpyAsync(B->hz.p, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
@@ -1002,6 +1190,245 @@ ftcc_status solve_batch(Batch& B) {
   if (dead) return fail(h, FTCC_ERR_DIVERGED, "%d of %d instances diverged (frozen)", dead, B.nz);
   if (!conv) return fail(h, FTCC_ERR_NOT_CONVERGED, "not converged after %d iterations", B.iterations);
   return FTCC_OK;
+}
+
+// Make the FP64 solver current with converged amplitudes (refining a
+// low-precision solution in FP64 when needed).
+void ensure_fp64_solution(Batch& B) {
+  if (B.active == 0) return;
+  promote_to_fp64(B);
+  ftcc_ctx* h = B.home;
+  for (int r = 0; r < std::max(50, B.opt.refine_max_iter); ++r) {
+    timed_iterations(B, 1);
+    B.refine_iterations++;
+    std::vector<double> st = read_states(B);
+    bool ok = true;
+    for (int z = 0; z < B.nz; ++z) {
+      const double* q = st.data() + static_cast<size_t>(z) * kStateStride;
+      if (B.live_host[z]) ok = ok && q[1] < B.opt.tol_omega && q[2] < B.opt.tol_amp;
+    }
+    if (ok) return;
+  }
+  (void)h;
+  throw Fail{FTCC_ERR_NOT_CONVERGED, "FP64 refinement before the adjoint did not converge"};
+}
+
+// Stationarity of the discrete Lagrangian (Eqs. Lagrangian, lmu, ltilde):
+// m = -dEcc/ds - (dS/ds)^T u,  u_x = sum_y G[y,x] exp(-Delta(tau_y - tau_x)) m_y,
+// with m_y = g_y lambda_y / beta; fixed-point iteration from m = 0.
+int lambda_solve(Batch& B, double tol, int max_iter) {
+  ftcc_ctx* h = B.home;
+  Solver<double>& s = *B.s64;
+  const long long o = B.no, v = B.nv, ng = B.ng, nz = B.nz;
+  const long long n1 = nz * ng * o * v, n2 = nz * ng * o * o * v * v;
+  ensure(h, B.m1, n1 * 8);
+  ensure(h, B.m2, n2 * 8);
+  ensure(h, B.mn1, n1 * 8);
+  ensure(h, B.mn2, n2 * 8);
+  ensure(h, B.u1, n1 * 8);
+  ensure(h, B.u2, n2 * 8);
+  ensure(h, B.tb1, n1 * 8);
+  ensure(h, B.tb2, n2 * 8);
+  ensure(h, B.dE1, n1 * 8);
+  ensure(h, B.cz, nz * ng * 8);
+  const int nblk = 152 * 4;
+  ensure(h, B.lpart, 2 * nblk * 8);
+  std::vector<double> c(nz * ng);
+  for (long long z = 0; z < nz; ++z)
+    for (long long x = 0; x < ng; ++x) c[z * ng + x] = simpson_weight_host(static_cast<int>(x), static_cast<int>(ng)) / (ng - 1);
+  CU(cudaMemcpyAsync(B.cz.p, c.data(), c.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CU(cudaMemsetAsync(B.m1.p, 0, n1 * 8, h->st));
+  CU(cudaMemsetAsync(B.m2.p, 0, n2 * 8, h->st));
+  // dE/ds1 without the weight: f_kc + sum_jb <kj||cb> s_j^b   (Eq. E)
+  s.nx = s.ng;
+  double* dE1 = static_cast<double*>(B.dE1.p);
+  s.scatter(dE1, "zxkc", s.F("zkc"), "zkc", 1.0, 0.0, "");
+  s.contract({dE1, "zxkc"}, 1.0, Tn<const double>{s.V("zkjcb"), "zkjcb", true},
+             Tn<const double>{static_cast<const double*>(s.t1.p), "zxjb"});
+  CU(cudaStreamSynchronize(h->st));
+  PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
+  a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
+  a2.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a2.size + 127) / 128)));
+  std::vector<double> parts(2 * nblk);
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    CU(launch_propagate_t(static_cast<const double*>(B.m1.p), static_cast<double*>(B.u1.p), a1, h->st));
+    CU(launch_propagate_t(static_cast<const double*>(B.m2.p), static_cast<double*>(B.u2.p), a2, h->st));
+    for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
+      const int nx = std::min(s.nxc, s.ng - x0);
+      const long long f1 = x0 * o * v, f2 = x0 * o * o * v * v;
+      s.vjp(static_cast<const double*>(s.t1.p) + f1, static_cast<const double*>(s.t2.p) + f2,
+            static_cast<double*>(B.u1.p) + f1, static_cast<double*>(B.u2.p) + f2, static_cast<double*>(B.tb1.p) + f1,
+            static_cast<double*>(B.tb2.p) + f2, nx);
+    }
+    double dmax = 0, smax = 0;
+    for (int k = 0; k < 2; ++k) {
+      const bool one = k == 0;
+      CU(launch_lambda_combine(one ? dE1 : static_cast<const double*>(B.V64.p),
+                               static_cast<const double*>(one ? B.tb1.p : B.tb2.p),
+                               static_cast<double*>(one ? B.mn1.p : B.mn2.p),
+                               static_cast<const double*>(one ? B.m1.p : B.m2.p), one ? o * v : o * o * v * v,
+                               static_cast<int>(ng), static_cast<int>(nz), static_cast<const double*>(B.cz.p),
+                               one ? 0.0 : 0.25, static_cast<double*>(B.lpart.p), nblk, h->st));
+      CU(cudaMemcpyAsync(parts.data(), B.lpart.p, 2 * nblk * 8, cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      for (int b = 0; b < nblk; ++b) {
+        dmax = std::max(dmax, parts[2 * b]);
+        smax = std::max(smax, parts[2 * b + 1]);
+      }
+    }
+    std::swap(B.m1, B.mn1);
+    std::swap(B.m2, B.mn2);
+    if (!std::isfinite(dmax)) throw Fail{FTCC_ERR_DIVERGED, "lambda iteration diverged"};
+    if (dmax / std::max(1.0, smax) < tol) break;
+  }
+  check_device_error(h);
+  B.lambda_iterations = it;
+  B.lambda_done = it <= max_iter;
+  return it;
+}
+
+// Response of the converged solve from the multipliers m (App. B): partial
+// derivatives of the Lagrangian at fixed (s, m) through the thermal integral
+// blocks (Fermi factors and the Fock matrix), the propagator (Delta, beta)
+// and the reference (Omega0, Omega1).  Fills out[z] and rdm[z] (N x N,
+// rdm[q][p] pairs with X[p][q]).
+void response(Batch& B, std::vector<ftcc_adjoint_result>& out, std::vector<std::vector<double>>& rdm) {
+  ftcc_ctx* h = B.home;
+  Solver<double>& s = *B.s64;
+  const int nz = B.nz, no = B.no, nv = B.nv, N = B.N, ng = B.ng;
+  const long long n1 = static_cast<long long>(nz) * ng * no * nv;
+  PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
+  a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
+  a2.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a2.size + 127) / 128)));
+  // cotangent of S at the converged multipliers
+  CU(launch_propagate_t(static_cast<const double*>(B.m1.p), static_cast<double*>(B.u1.p), a1, h->st));
+  CU(launch_propagate_t(static_cast<const double*>(B.m2.p), static_cast<double*>(B.u2.p), a2, h->st));
+  for (auto& kv : s.fixed_bar) h->put(kv.second);
+  s.fixed_bar.clear();
+  s.want_fixed_bar = true;
+  for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
+    const int nx = std::min(s.nxc, s.ng - x0);
+    const long long f1 = static_cast<long long>(x0) * no * nv, f2 = f1 * no * nv;
+    s.vjp(static_cast<const double*>(s.t1.p) + f1, static_cast<const double*>(s.t2.p) + f2,
+          static_cast<double*>(B.u1.p) + f1, static_cast<double*>(B.u2.p) + f2, static_cast<double*>(B.tb1.p) + f1,
+          static_cast<double*>(B.tb2.p) + f2, nx);
+  }
+  s.want_fixed_bar = false;
+  // direct dependence of Omega_CC = sum_y (g_y / beta) E_y on f_ia and <ij||ab> (Eq. E)
+  s.nx = s.ng;
+  using CT = Tn<const double>;
+  const double* cz = static_cast<const double*>(B.cz.p);
+  const double* t1 = static_cast<const double*>(s.t1.p);
+  const double* t2 = static_cast<const double*>(s.t2.p);
+  double* Aov = s.fixed_adjoint(s.F("zia"));
+  double* Aoovv = s.fixed_adjoint(s.V("zijab"));
+  double* cs1 = static_cast<double*>(B.tb1.p);
+  s.contract({Aov, "zia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"});
+  s.contract({Aoovv, "zijab"}, 0.25, CT{cz, "zx"}, CT{t2, "zxijab"});
+  s.contract({cs1, "zxia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"}, "", 0.0);
+  s.contract({Aoovv, "zijab"}, 0.5, CT{cs1, "zxia"}, CT{t1, "zxjb"});
+  (void)n1;
+  // per-orbital sums through the Fermi factors
+  Buf Do = h->get(static_cast<size_t>(nz) * no * 8), Dv = h->get(static_cast<size_t>(nz) * nv * 8);
+  Buf Fbar = h->get(static_cast<size_t>(nz) * N * N * 8), Gn = h->get(static_cast<size_t>(nz) * N * 8);
+  Buf Ee = h->get(static_cast<size_t>(nz) * N * 8), Eb = h->get(static_cast<size_t>(nz) * 8);
+  if (!Do.p || !Dv.p || !Fbar.p || !Gn.p || !Ee.p || !Eb.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+  CU(cudaMemsetAsync(Do.p, 0, Do.bytes, h->st));
+  CU(cudaMemsetAsync(Dv.p, 0, Dv.bytes, h->st));
+  CU(cudaMemsetAsync(Fbar.p, 0, Fbar.bytes, h->st));
+  CU(cudaMemsetAsync(Ee.p, 0, Ee.bytes, h->st));
+  CU(cudaMemsetAsync(Eb.p, 0, Eb.bytes, h->st));
+  for (auto* mp : {&s.Vb, &s.Fb}) {
+    for (auto& kv : *mp) {
+      auto it = s.fixed_bar.find(kv.second.p);
+      if (it == s.fixed_bar.end()) continue;
+      const std::string& pat = kv.first;
+      int dims[4], cls = 0;
+      for (size_t k = 0; k < pat.size(); ++k) {
+        dims[k] = pat[k] == 'o' ? no : nv;
+        if (pat[k] == 'v') cls |= 1 << k;
+      }
+      CU(launch_slot_sums(static_cast<const double*>(kv.second.p), static_cast<const double*>(it->second.p),
+                          static_cast<int>(pat.size()), dims, cls, no, nv, nz, static_cast<double*>(Do.p),
+                          static_cast<double*>(Dv.p), h->st));
+      if (pat.size() == 2) {
+        const bool h0 = pat[0] == 'o', h1 = pat[1] == 'o';
+        CU(launch_fbar_scatter(static_cast<const double*>(it->second.p), h0 ? no : nv, h1 ? no : nv,
+                               static_cast<const int*>(h0 ? B.idxO.p : B.idxV.p),
+                               static_cast<const double*>(h0 ? B.facOz.p : B.facVz.p), h0 ? no : nv,
+                               static_cast<const int*>(h1 ? B.idxO.p : B.idxV.p),
+                               static_cast<const double*>(h1 ? B.facOz.p : B.facVz.p), h1 ? no : nv, N, nz,
+                               static_cast<double*>(Fbar.p), h->st));
+      }
+    }
+  }
+  for (int z = 0; z < nz; ++z)
+    CU(launch_fock_n(static_cast<const double*>(Fbar.p) + static_cast<long long>(z) * N * N,
+                     static_cast<const double*>(B.inst[z].ctx->eri.p), N, static_cast<double*>(Gn.p) + z * N, h->st));
+  CU(launch_prop_response(static_cast<const double*>(s.S1.p), static_cast<const double*>(B.m1.p),
+                          static_cast<const double*>(B.epsz.p), a1, static_cast<double*>(Ee.p),
+                          static_cast<double*>(Eb.p), h->st));
+  CU(launch_prop_response(static_cast<const double*>(s.S2.p), static_cast<const double*>(B.m2.p),
+                          static_cast<const double*>(B.epsz.p), a2, static_cast<double*>(Ee.p),
+                          static_cast<double*>(Eb.p), h->st));
+  std::vector<double> hDo(nz * no), hDv(nz * nv), hF(static_cast<size_t>(nz) * N * N), hGn(nz * N), hEe(nz * N), hEb(nz);
+  CU(cudaMemcpyAsync(hDo.data(), Do.p, Do.bytes, cudaMemcpyDeviceToHost, h->st));
+  CU(cudaMemcpyAsync(hDv.data(), Dv.p, Dv.bytes, cudaMemcpyDeviceToHost, h->st));
+  CU(cudaMemcpyAsync(hF.data(), Fbar.p, Fbar.bytes, cudaMemcpyDeviceToHost, h->st));
+  CU(cudaMemcpyAsync(hGn.data(), Gn.p, Gn.bytes, cudaMemcpyDeviceToHost, h->st));
+  CU(cudaMemcpyAsync(hEe.data(), Ee.p, Ee.bytes, cudaMemcpyDeviceToHost, h->st));
+  CU(cudaMemcpyAsync(hEb.data(), Eb.p, Eb.bytes, cudaMemcpyDeviceToHost, h->st));
+  const std::vector<double> st = read_states(B);
+  std::vector<double> eps(N), fdiag(N * N), hdiag(N * N);
+  out.assign(nz, ftcc_adjoint_result{});
+  rdm.assign(nz, std::vector<double>(static_cast<size_t>(N) * N, 0.0));
+  for (int z = 0; z < nz; ++z) {
+    const Inst& I = B.inst[z];
+    CU(cudaMemcpyAsync(eps.data(), I.ctx->eps.p, N * 8, cudaMemcpyDeviceToHost, h->st));
+    CU(cudaMemcpyAsync(fdiag.data(), I.f.p, static_cast<size_t>(N) * N * 8, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    std::vector<int> posO(N, -1), posV(N, -1);
+    for (int k = 0; k < no; ++k) posO[B.O[k]] = k;
+    for (int k = 0; k < nv; ++k) posV[B.V[k]] = k;
+    const double beta = I.beta, mu = I.mu;
+    double dmu = 0, dbeta = 0, sum_n = 0, sum_ne = 0;
+    std::vector<double> Tq(N);
+    for (int q = 0; q < N; ++q) {
+      const double nq = I.n_host[q], nb = I.nbar_host[q];
+      const double Do_q = posO[q] >= 0 ? hDo[z * no + posO[q]] : 0.0;
+      const double Dv_q = posV[q] >= 0 ? hDv[z * nv + posV[q]] : 0.0;
+      const double Ln = (fdiag[static_cast<size_t>(q) * N + q] - eps[q]) + hGn[z * N + q];
+      Tq[q] = Ln * nq * nb + 0.5 * Do_q * nb - 0.5 * Dv_q * nq;   // dL/dz'_q, z'_q = -beta (eps_q - mu)
+      sum_n += nq;
+      sum_ne += nq * (eps[q] - mu);
+      dmu += beta * Tq[q];
+      dbeta += -(eps[q] - mu) * Tq[q];
+    }
+    const double omega0 = I.omega0;
+    dmu += -sum_n;
+    dbeta += -omega0 / beta + sum_ne / beta + hEb[z] / beta;
+    const double* F = hF.data() + static_cast<size_t>(z) * N * N;
+    std::vector<double>& R = rdm[z];
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q) R[static_cast<size_t>(q) * N + p] = F[static_cast<size_t>(p) * N + q];
+    double tr = 0;
+    for (int q = 0; q < N; ++q) {
+      R[static_cast<size_t>(q) * N + q] = I.n_host[q] - beta * Tq[q] + hEe[z * N + q];
+      tr += R[static_cast<size_t>(q) * N + q];
+    }
+    const double omega = I.omega0 + I.omega1 + st[static_cast<size_t>(z) * kStateStride];
+    ftcc_adjoint_result& r = out[z];
+    r.dOmega_dmu = dmu;
+    r.dOmega_dbeta = dbeta;
+    r.N = -dmu;
+    r.E = omega + beta * dbeta + mu * r.N;
+    r.S = beta * beta * dbeta;
+    r.trace_rdm1 = tr;
+    r.iterations = B.lambda_iterations;
+  }
+  Buf* bs[] = {&Do, &Dv, &Fbar, &Gn, &Ee, &Eb};
+  for (Buf* q : bs) h->put(*q);
 }
 
 ftcc_status check_solve_args(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_quadrature quad) {
@@ -1293,11 +1720,22 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
 }
 
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1) {
-  (void)out;
-  (void)rdm1;
   if (!c) return FTCC_ERR_INVALID_ARG;
   if (!c->batch || !c->batch->solved) return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
-  return fail(c, FTCC_ERR_UNSUPPORTED, "the lambda sweep is not built yet");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    CU(cudaSetDevice(B.home->device));
+    ensure_fp64_solution(B);
+    if (!B.lambda_done) lambda_solve(B, 1e-11, 400);
+    if (!B.lambda_done) return fail(c, FTCC_ERR_NOT_CONVERGED, "lambda equations not converged");
+    std::vector<ftcc_adjoint_result> res;
+    std::vector<std::vector<double>> rdms;
+    response(B, res, rdms);
+    if (out) *out = res[c->member];
+    if (rdm1) memcpy(rdm1, rdms[c->member].data(), rdms[c->member].size() * sizeof(double));
+    check_device_error(B.home);
+    return FTCC_OK;
+  });
 }
 
 ftcc_status ftcc_get_amplitudes(ftcc_ctx* c, double* s1, double* s2) {
@@ -1385,6 +1823,60 @@ ftcc_status ftcc_propagate(ftcc_ctx* c, const char* slots, const double* S_dev, 
     CU(launch_propagate<double>(S_dev, s_dev, a, c->st));
     sync(c);
     c->put(part);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_eval_s_vjp(ftcc_ctx* c, int nx, const double* t1_dev, const double* t2_dev, const double* w1_dev,
+                            const double* w2_dev, double* t1bar_dev, double* t2bar_dev) {
+  if (!c || !t1_dev || !t2_dev || !w1_dev || !w2_dev || !t1bar_dev || !t2bar_dev) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
+  if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "works on a single prepared instance");
+  if (nx < 1 || nx > c->batch->ng) return fail(c, FTCC_ERR_INVALID_ARG, "bad nx");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    Solver<double>& s = make_solver<double>(B, GEMM_F64);
+    if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+    const long long n1 = nx * static_cast<long long>(B.no) * B.nv, n2 = n1 * B.no * B.nv;
+    Buf a = c->get(n1 * 8), b = c->get(n2 * 8);
+    if (!a.p || !b.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+    CU(cudaMemcpyAsync(a.p, w1_dev, n1 * 8, cudaMemcpyDeviceToDevice, c->st));
+    CU(cudaMemcpyAsync(b.p, w2_dev, n2 * 8, cudaMemcpyDeviceToDevice, c->st));
+    s.vjp(t1_dev, t2_dev, static_cast<double*>(a.p), static_cast<double*>(b.p), t1bar_dev, t2bar_dev, nx);
+    sync(c);
+    c->put(a);
+    c->put(b);
+    check_device_error(c);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_propagate_adjoint(ftcc_ctx* c, const char* slots, const double* m_dev, double* u_dev) {
+  if (!c || !slots || !m_dev || !u_dev) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
+  if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "works on a single prepared instance");
+  const int ns = static_cast<int>(strlen(slots));
+  if (ns != 2 && ns != 4) return fail(c, FTCC_ERR_INVALID_ARG, "slots must be 'ia' or 'ijab'");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    PropArgs a = prop_args(B, ns);
+    a.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a.size + 127) / 128)));
+    CU(launch_propagate_t(m_dev, u_dev, a, c->st));
+    sync(c);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_get_lambda(ftcc_ctx* c, double* m1, double* m2) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch || !c->batch->lambda_done) return fail(c, FTCC_ERR_STATE, "run ft_ccsd_adjoint first");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    const long long n1 = static_cast<long long>(B.ng) * B.no * B.nv, n2 = n1 * B.no * B.nv;
+    const long long z = c->member;
+    if (m1) CU(cudaMemcpyAsync(m1, static_cast<const double*>(B.m1.p) + z * n1, n1 * 8, cudaMemcpyDeviceToHost, B.home->st));
+    if (m2) CU(cudaMemcpyAsync(m2, static_cast<const double*>(B.m2.p) + z * n2, n2 * 8, cudaMemcpyDeviceToHost, B.home->st));
+    sync(B.home);
     return FTCC_OK;
   });
 }

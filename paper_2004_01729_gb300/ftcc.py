@@ -86,6 +86,10 @@ _SIGS = [
     ("ftcc_gemm", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                             C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p, C.c_longlong, C.c_longlong,
                             C.c_void_p, C.c_longlong, C.c_longlong]),
+    ("ftcc_eval_s_vjp", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    ("ftcc_propagate_adjoint", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p]),
+    ("ftcc_get_lambda", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ftcc_device_error", C.c_int, [C.c_void_p]),
 ]
 
@@ -251,13 +255,16 @@ class Context:
         d["status"] = s
         return d
 
-    def adjoint(self, with_rdm1=True):
+    def adjoint(self, with_rdm1=True, allow_unsupported=False):
+        """ft_ccsd_adjoint: dOmega/dmu, dOmega/dbeta, N, E, S and the 1-RDM p^cc."""
         out = AdjointResult()
         N = self.num_orbitals()
         rdm = np.empty((N, N)) if with_rdm1 else None
-        self._check(self.lib.ft_ccsd_adjoint(self.h, C.byref(out), rdm.ctypes.data if with_rdm1 else None),
-                    "ft_ccsd_adjoint")
-        return {k: getattr(out, k) for k, _ in out._fields_}, rdm
+        s = self.lib.ft_ccsd_adjoint(self.h, C.byref(out), rdm.ctypes.data if with_rdm1 else None)
+        self._check(s, "ft_ccsd_adjoint", allow=(ERR_UNSUPPORTED,) if allow_unsupported else ())
+        d = {k: getattr(out, k) for k, _ in out._fields_}
+        d["status"] = s
+        return d, rdm
 
     def amplitudes(self, ngrid, no, nv):
         s1 = np.empty((ngrid, no, nv))
@@ -277,6 +284,34 @@ class Context:
                                          t2.data_ptr(), s1.data_ptr(), s2.data_ptr()), "ftcc_eval_s")
         self._out(cur)
         return s1, s2
+
+    def eval_s_vjp(self, t1, t2, w1, w2):
+        torch = self._torch
+        dev = f"cuda:{self.device}"
+        t1, t2, w1, w2 = [a.to(device=dev, dtype=torch.float64).contiguous() for a in (t1, t2, w1, w2)]
+        b1 = torch.empty_like(t1)
+        b2 = torch.empty_like(t2)
+        cur = self._in()
+        self._check(self.lib.ftcc_eval_s_vjp(self.h, t1.shape[0], t1.data_ptr(), t2.data_ptr(), w1.data_ptr(),
+                                             w2.data_ptr(), b1.data_ptr(), b2.data_ptr()), "ftcc_eval_s_vjp")
+        self._out(cur)
+        return b1, b2
+
+    def propagate_adjoint(self, slots, m):
+        torch = self._torch
+        m = m.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()
+        out = torch.empty_like(m)
+        cur = self._in()
+        self._check(self.lib.ftcc_propagate_adjoint(self.h, slots.encode(), m.data_ptr(), out.data_ptr()),
+                    "ftcc_propagate_adjoint")
+        self._out(cur)
+        return out
+
+    def get_lambda(self, ngrid, no, nv):
+        m1 = np.empty((ngrid, no, nv))
+        m2 = np.empty((ngrid, no, no, nv, nv))
+        self._check(self.lib.ftcc_get_lambda(self.h, m1.ctypes.data, m2.ctypes.data), "ftcc_get_lambda")
+        return m1, m2
 
     def propagate(self, slots, S):
         torch = self._torch
