@@ -265,6 +265,30 @@ ftcc_status ftcc_gemm(ftcc_ctx* ctx, int precision, int batch, int M, int N, int
                       const void* B_dev, long long ldb, long long sb,
                       void* C_dev, long long ldc, long long sc);
 
+/* FP64 GEMM that allocates nothing (no paper counterpart: an engineering
+ * entry point).  Same operation and layouts as ftcc_gemm with precision
+ * FP64: C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k], all device
+ * pointers, issued on `stream` (a cudaStream_t; NULL = legacy stream), no
+ * context needed.  The K dimension is split across blocks when the output
+ * is small, and the partial sums live in a 16 MiB static device array held
+ * by every GPU that loads the library until the process exits; no
+ * cudaMalloc, cudaFree or allocating library routine is called.  For callers
+ * that cannot allocate device memory where they call it: inside a stream
+ * capture in global mode, inside a device-memory allocator's callback, or
+ * under a fixed device-memory budget.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (different
+ *     streams, or different host threads) race and give wrong results.
+ *   - batch * M * N must not exceed 2^20 (half the array, so that at least
+ *     two K splits fit): larger outputs return FTCC_ERR_INVALID_ARG.
+ * Returns FTCC_ERR_INVALID_ARG for bad sizes or NULL pointers,
+ * FTCC_ERR_NO_DEVICE without a GPU, FTCC_ERR_CUDA if a launch fails. */
+ftcc_status ftcc_gemm_f64_static(void* stream, int batch, int M, int N, int K, double alpha, const double* A_dev,
+                                 long long lda, long long sa, const double* B_dev, long long ldb, long long sb,
+                                 double* C_dev, long long ldc, long long sc);
+
 /* Device error flag set by bounded in-kernel waits (0 = none); reading it
  * synchronises the stream and clears it. */
 int ftcc_device_error(ftcc_ctx* ctx);

@@ -90,6 +90,9 @@ _SIGS = [
                                   C.c_void_p, C.c_void_p]),
     ("ftcc_propagate_adjoint", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p]),
     ("ftcc_get_lambda", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ftcc_gemm_f64_static", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                       C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p, C.c_longlong,
+                                       C.c_longlong, C.c_void_p, C.c_longlong, C.c_longlong]),
     ("ftcc_device_error", C.c_int, [C.c_void_p]),
 ]
 
