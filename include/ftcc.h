@@ -254,12 +254,30 @@ ftcc_status ftcc_propagate_adjoint(ftcc_ctx* ctx, const char* slots, const doubl
  * context's instance (layouts of s1 / s2) after ft_ccsd_adjoint. */
 ftcc_status ftcc_get_lambda(ftcc_ctx* ctx, double* m1, double* m2);
 
+/* Per-kernel timing of the iterations of a context's batch.  With enable = 1
+ * every launch of an iteration is bracketed by CUDA events (recorded into
+ * the per-iteration graph, which is captured again) and ft_ccsd_iterate /
+ * ft_ccsd_solve accumulate, per kernel class, the device time, the number of
+ * launches and the algorithmic bytes (elements read and written once each)
+ * and flops of those launches.  Enabling or disabling resets the sums.
+ * ftcc_profile_read fills up to max entries and returns how many. */
+typedef struct {
+  char name[32];
+  long long launches;
+  double ms, bytes, flops;
+} ftcc_kernel_stats;
+ftcc_status ftcc_profile(ftcc_ctx* ctx, int enable);
+int ftcc_profile_read(ftcc_ctx* ctx, ftcc_kernel_stats* out, int max);
+
 /* Dense GEMM on the tensor-core engine, exposed for testing:
  * C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (A, B, C FP32 for
  * TF32 / BF16X3, FP64 for FP64; row-major with leading dimensions lda,
  * ldb, ldc; batch strides sa, sb (0 = shared), sc).  lda and ldb must be
  * multiples of 4 elements and the base pointers 16-byte aligned for the
- * tensor-core kinds.  FTCC_ERR_INVALID_ARG otherwise. */
+ * tensor-core kinds.  FTCC_ERR_INVALID_ARG otherwise.  When the output tiles
+ * cannot fill the SMs the K loop is split over CTAs, with the partial sums
+ * in scratch from the context's allocator (at most 64 MiB, released before
+ * return) and reduced in a fixed order. */
 ftcc_status ftcc_gemm(ftcc_ctx* ctx, int precision, int batch, int M, int N, int K, double alpha,
                       const void* A_dev, long long lda, long long sa,
                       const void* B_dev, long long ldb, long long sb,

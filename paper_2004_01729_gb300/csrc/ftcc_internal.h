@@ -73,11 +73,11 @@ inline FastDiv make_fastdiv(uint32_t d) {
   return f;
 }
 
-// Gather a strided source into a row-major [rows][cpad] operand (zero in the
-// padding columns).  Row index = mixed radix over rdim (last fastest), column
-// index over cdim; source offset = sum coord * stride.  rows < 2^32 and
-// cpad < 2^31; the launcher splits the rows so that one launch covers fewer
-// than 2^31 elements.
+// Gather a strided source into a row-major [rows][cpad] operand.  The
+// padding columns creal..cpad are left unwritten: every GEMM reads only the
+// first creal columns (the tensor maps have K = creal and fill the rest of
+// a box with zeros).  Row index = mixed radix over rdim (last fastest), column
+// index over cdim; source offset = sum coord * stride.
 struct PackDesc {
   int nr, nc;
   long long rdim[kMaxL], rst[kMaxL], cdim[kMaxL], cst[kMaxL];
@@ -85,8 +85,9 @@ struct PackDesc {
 };
 // dst[e] = beta * dst[e] + alpha * sum_p sign_p * src[off_p(e)] where the
 // terms p run over the antisymmetriser: identity, swap(s0a, s0b),
-// swap(s1a, s1b), both swaps (signs +, -, -, +); nswap = 0, 1, 2.  Every
-// dst letter but the first spans fewer than 2^31 elements.
+// swap(s1a, s1b), both swaps (signs +, -, -, +); nswap = 0, 1, 2.  A source
+// stride of 0 broadcasts along that letter.  Both launchers run the tiled
+// permute kernel (shared-memory tiles, coalesced reads and writes).
 struct ScatDesc {
   int nd;
   long long dim[kMaxL], sst[kMaxL];

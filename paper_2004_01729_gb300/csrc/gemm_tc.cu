@@ -4,11 +4,14 @@
 //   C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (+ beta * C)
 //
 // Both operands are K-major ("TN"), which is the layout every contraction of
-// the FT-CCSD S kernel is packed into.  One CTA owns a 128 x 128 output tile:
+// the FT-CCSD S kernel is packed into.  Persistent CTAs (one per SM) walk
+// 128 x BN output tiles (BN = 256, or 128 for narrow outputs):
 //   warp 0 / lane 0   TMA producer (multi-stage ring of shared-memory stages)
-//   warp 1 / lane 0   MMA issuer (tcgen05.mma, kind::tf32 or kind::f16)
-//   warp 2            TMEM allocation and release (128 columns)
-//   warps 0-3         epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store
+//   warp 1            TMEM allocation (2 x BN columns), MMA issuer (one thread,
+//                     tcgen05.mma kind::tf32 or kind::f16)
+//   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store,
+//                     overlapping the next tile's main loop (double-buffered
+//                     accumulator)
 // BF16X3 keeps a two-way bf16 split of each operand (x = hi + lo) and issues
 // hi*hi + hi*lo + lo*hi into the same FP32 accumulator.
 //
@@ -18,6 +21,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "ftcc_internal.h"
 
@@ -142,48 +147,60 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int KIND>
-struct TcCfg;
-template <>
-struct TcCfg<GEMM_TF32> {
-  static constexpr int kStages = 4;
-  static constexpr int kOps = 2;          // A, B
-  static constexpr int kKElems = 32;      // fp32 elements per 128-byte row
-};
-template <>
-struct TcCfg<GEMM_BF16X3> {
-  static constexpr int kStages = 3;
-  static constexpr int kOps = 4;          // A_hi, B_hi, A_lo, B_lo
-  static constexpr int kKElems = 64;      // bf16 elements per 128-byte row
-};
-
-template <int KIND>
-constexpr int tc_smem_bytes() {
-  return TcCfg<KIND>::kStages * TcCfg<KIND>::kOps * kTileBytes + 1024 /*align*/ + 256 /*bars*/;
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+// Instruction descriptor for an M = 128 x N = bn tile.
+__host__ __device__ constexpr uint32_t instr_desc_n(uint32_t fmt, uint32_t bn) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((bn >> 3) << 17) | ((uint32_t(kBM) >> 4) << 24);
+}
+
+template <int KIND, int BN>
+struct TcCfg {
+  static constexpr int kOps = KIND == GEMM_TF32 ? 1 : 2;                       // hi (and lo) halves
+  static constexpr int kABytes = 128 * 128;                                     // 128 rows x 128 B
+  static constexpr int kBBytes = BN * 128;                                      // BN rows x 128 B
+  static constexpr int kStageBytes = kOps * (kABytes + kBBytes);
+  static constexpr int kStages = (192 * 1024) / kStageBytes > 6 ? 6 : (192 * 1024) / kStageBytes;
+  static constexpr int kKElems = KIND == GEMM_TF32 ? 32 : 64;                  // elements per 128-byte row
+  static constexpr uint32_t kTmemCols = 2 * BN;                                // double-buffered accumulator
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+};
+
+constexpr int kGroupM = 8;   // tile raster: groups of 8 row tiles swept across all column tiles
+
+// Persistent warp-specialised GEMM.  CTA = 6 warps:
+//   warp 0        TMA producer over a ring of kStages shared-memory stages
+//   warp 1        TMEM owner and MMA issuer (one thread), two accumulators
+//   warps 2..5    epilogue; warp w drains TMEM lanes 32 (w % 4) .. + 31
+// Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; the accumulator of tile
+// i is buffer i % 2, so tile i's epilogue overlaps tile i+1's main loop.
+template <int KIND, int BN>
+__global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2,
-                   float* __restrict__ C, int M, int N, int K, long long ldc, long long sc,
-                   int a_batched, int b_batched, float alpha, float beta, int* err) {
-  using Cfg = TcCfg<KIND>;
+                   float* __restrict__ C, int M, int N, int K, long long ldc, long long sc, int a_batched,
+                   int b_batched, float alpha, float beta, int batch, int splits, int kc, float* __restrict__ W,
+                   int* err) {
+  using Cfg = TcCfg<KIND, BN>;
   constexpr int S = Cfg::kStages;
-  constexpr int kStageBytes = Cfg::kOps * kTileBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::kStageBytes);
   uint64_t* empty = full + S;
-  uint64_t* accum = empty + S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int tile_n = blockIdx.x;
-  const int tile_m = blockIdx.y;
-  const int bz = blockIdx.z;
+  const int mt = (M + kBM - 1) / kBM;
+  const int nt = (N + BN - 1) / BN;
+  const long long per_batch = static_cast<long long>(mt) * nt;
+  const long long per_split = per_batch * batch;
+  const long long tiles = per_split * splits;   // split-K: each split sums kc K steps into W
   const int nk = (K + Cfg::kKElems - 1) / Cfg::kKElems;
 
   if (threadIdx.x == 0) {
@@ -191,13 +208,15 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -206,94 +225,161 @@ __global__ void __launch_bounds__(128, 1)
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    const int ca = a_batched ? bz : 0;
-    const int cb = b_batched ? bz : 0;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % S;
-      const uint32_t ph = (kt / S) & 1;
-      if (kt >= S && !mbar_wait(&empty[s], ph ^ 1u, err, DEVERR_TMA_TIMEOUT)) break;
-      mbar_expect_tx(&full[s], kStageBytes);
-      uint8_t* st = smem + s * kStageBytes;
-      const int kc = kt * Cfg::kKElems;
-      tma_load_3d(st, &mA, &full[s], kc, tile_m * kBM, ca);
-      tma_load_3d(st + kTileBytes, &mB, &full[s], kc, tile_n * kBN, cb);
-      if (KIND == GEMM_BF16X3) {
-        tma_load_3d(st + 2 * kTileBytes, &mA2, &full[s], kc, tile_m * kBM, ca);
-        tma_load_3d(st + 3 * kTileBytes, &mB2, &full[s], kc, tile_n * kBN, cb);
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = instr_desc(KIND == GEMM_TF32 ? 2u : 1u);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % S;
-      const uint32_t ph = (kt / S) & 1;
-      if (!mbar_wait(&full[s], ph, err, DEVERR_MMA_TIMEOUT)) break;
-      fence_after_sync();
-      const uint32_t a0 = smem_u32(smem + s * kStageBytes);
-      const uint32_t b0 = a0 + kTileBytes;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {       // four 32-byte K slices per 128-byte row
-        const uint64_t da = smem_desc(a0 + kk * 32);
-        const uint64_t db = smem_desc(b0 + kk * 32);
-        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-        if (KIND == GEMM_TF32) {
-          mma_tf32(tmem, da, db, idesc, acc);
-        } else {
-          const uint64_t da2 = smem_desc(a0 + 2 * kTileBytes + kk * 32);
-          const uint64_t db2 = smem_desc(a0 + 3 * kTileBytes + kk * 32);
-          mma_f16(tmem, da, db, idesc, acc);     // hi * hi
-          mma_f16(tmem, da, db2, idesc, 1u);     // hi * lo
-          mma_f16(tmem, da2, db, idesc, 1u);     // lo * hi
-        }
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(accum);
-  }
+  // tile t -> (split, batch, row tile, column tile) with grouped rasterisation
+  auto decode = [&](long long t, int& sp, int& b, int& m0, int& n0) {
+    sp = static_cast<int>(t / per_split);
+    t -= static_cast<long long>(sp) * per_split;
+    b = static_cast<int>(t / per_batch);
+    const long long r = t - static_cast<long long>(b) * per_batch;
+    const long long group = r / (static_cast<long long>(kGroupM) * nt);
+    const int first = static_cast<int>(group * kGroupM);
+    const int gsize = min(kGroupM, mt - first);
+    const long long in = r - group * kGroupM * nt;
+    m0 = (first + static_cast<int>(in % gsize)) * kBM;
+    n0 = static_cast<int>(in / gsize) * BN;
+  };
 
-  // ---- epilogue (all four warps; warp w reads TMEM lanes 32w..32w+31)
-  __syncwarp();
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(accum, 0, err, DEVERR_EPI_TIMEOUT));
-  fence_after_sync();
-  if (ok) {
-    const int row = tile_m * kBM + warp * 32 + lane;
-    float* crow = C + static_cast<long long>(bz) * sc + static_cast<long long>(row) * ldc;
-    const int col0 = tile_n * kBN;
-#pragma unroll 1
-    for (int c = 0; c < kBN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c), r);
-      if (row < M) {
-        const int cb = col0 + c;
-        if (cb + 32 <= N && (ldc & 3) == 0 && beta == 0.0f) {
-          float4* dst = reinterpret_cast<float4*>(crow + cb);
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            dst[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
-                                 alpha * __uint_as_float(r[4 * j + 2]),
-                                 alpha * __uint_as_float(r[4 * j + 3]));
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = cb + j;
-            if (col < N) {
-              const float v = alpha * __uint_as_float(r[j]);
-              crow[col] = (beta == 0.0f) ? v : v + beta * crow[col];
-            }
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      uint32_t it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        int sp, b, m0, n0;
+        decode(t, sp, b, m0, n0);
+        const int ca = a_batched ? b : 0, cb = b_batched ? b : 0;
+        const int kt0 = sp * kc, kt1 = min(nk, kt0 + kc);
+        for (int kt = kt0; kt < kt1; ++kt, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          if (it >= static_cast<uint32_t>(S) && !mbar_wait(&empty[s], ph ^ 1u, err, DEVERR_TMA_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], Cfg::kStageBytes);
+          uint8_t* st = smem + s * Cfg::kStageBytes;
+          const int kc = kt * Cfg::kKElems;
+          tma_load_3d(st, &mA, &full[s], kc, m0, ca);
+          tma_load_3d(st + Cfg::kABytes, &mB, &full[s], kc, n0, cb);
+          if (KIND == GEMM_BF16X3) {
+            tma_load_3d(st + Cfg::kABytes + Cfg::kBBytes, &mA2, &full[s], kc, m0, ca);
+            tma_load_3d(st + 2 * Cfg::kABytes + Cfg::kBBytes, &mB2, &full[s], kc, n0, cb);
           }
         }
       }
     }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = instr_desc_n(KIND == GEMM_TF32 ? 2u : 1u, BN);
+      uint32_t it = 0, local = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
+        const uint32_t acc = local & 1u, use = local >> 1;
+        if (local >= 2 && !mbar_wait(&tempty[acc], (use - 1) & 1u, err, DEVERR_MMA_TIMEOUT)) break;
+        fence_after_sync();
+        const uint32_t d = tmem + acc * BN;
+        int sp, b, m0, n0;
+        decode(t, sp, b, m0, n0);
+        const int kt0 = sp * kc, kt1 = min(nk, kt0 + kc);
+        for (int kt = kt0; kt < kt1; ++kt, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          if (!mbar_wait(&full[s], ph, err, DEVERR_MMA_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t a0 = smem_u32(smem + s * Cfg::kStageBytes);
+          const uint32_t b0 = a0 + Cfg::kABytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {   // four 32-byte K slices per 128-byte row
+            const uint64_t da = smem_desc(a0 + kk * 32);
+            const uint64_t db = smem_desc(b0 + kk * 32);
+            const uint32_t accum = (kt > kt0 || kk > 0) ? 1u : 0u;
+            if (KIND == GEMM_TF32) {
+              mma_tf32(d, da, db, idesc, accum);
+            } else {
+              const uint64_t da2 = smem_desc(b0 + Cfg::kBBytes + kk * 32);
+              const uint64_t db2 = smem_desc(b0 + Cfg::kBBytes + Cfg::kABytes + kk * 32);
+              mma_f16(d, da, db, idesc, accum);   // hi * hi
+              mma_f16(d, da, db2, idesc, 1u);     // hi * lo
+              mma_f16(d, da2, db, idesc, 1u);     // lo * hi
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[acc]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    uint32_t local = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+      const uint32_t acc = local & 1u, use = local >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], use & 1u, err, DEVERR_EPI_TIMEOUT));
+      if (!ok) break;
+      fence_after_sync();
+      int sp, b, m0, n0;
+      decode(t, sp, b, m0, n0);
+      const int row = m0 + q * 32 + lane;
+      const bool part = splits > 1;   // split-K partial: dense [split][batch][M][N] in W, no beta
+      float* crow = part ? W + ((static_cast<long long>(sp) * batch + b) * M + row) * static_cast<long long>(N)
+                         : C + static_cast<long long>(b) * sc + static_cast<long long>(row) * ldc;
+      const float bta = part ? 0.0f : beta;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + static_cast<uint32_t>(c), r);
+        if (row < M) {
+          const int cb = n0 + c;
+          if (cb + 32 <= N && (reinterpret_cast<uintptr_t>(crow + cb) & 15) == 0 && bta == 0.0f) {
+            float4* dst = reinterpret_cast<float4*>(crow + cb);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              dst[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
+                                   alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = cb + j;
+              if (col < N) {
+                const float v = alpha * __uint_as_float(r[j]);
+                crow[col] = (bta == 0.0f) ? v : v + bta * crow[col];
+              }
+            }
+          }
+        }
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
-                 : "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kTmemCols) : "memory");
+  }
+}
+
+// C[b][m][n] = sum_s W[s][b][m][n] (+ beta C): the split-K reduction, fixed order.
+__global__ void tc_splitk_reduce(const float* __restrict__ W, float* __restrict__ C, long long ldc, long long sc, int M,
+                                 int N, int batch, int splits, float beta) {
+  const long long mn = static_cast<long long>(M) * N;
+  const long long total = mn * batch;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = e / mn;
+    const long long r = e - b * mn;
+    const long long m = r / N, n = r - m * N;
+    float acc = 0.0f;
+    for (int s = 0; s < splits; ++s) acc += W[static_cast<long long>(s) * total + e];
+    float* c = C + b * sc + m * ldc + n;
+    *c = (beta == 0.0f) ? acc : acc + beta * *c;
   }
 }
 
@@ -314,13 +400,13 @@ bool get_encode() {
 // 3D tiled map over [batch][rows][K] (K innermost), 128-byte swizzle, box of
 // 128 bytes x 128 rows x 1.  Out-of-range elements load as zero.
 bool make_map(CUtensorMap* m, const void* base, bool bf16, long long K, long long rows, long long ld,
-              long long bstride, int batch) {
+              long long bstride, int batch, int box_rows) {
   const int es = bf16 ? 2 : 4;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
                         static_cast<cuuint64_t>(bstride > 0 ? batch : 1)};
   const long long bs = bstride > 0 ? bstride : rows * ld;
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld * es), static_cast<cuuint64_t>(bs * es)};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / es), 128u, 1u};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / es), static_cast<cuuint32_t>(box_rows), 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                         const_cast<void*>(base), dims, strides, box, estr,
@@ -329,31 +415,55 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, long long K, long lon
   return r == CUDA_SUCCESS;
 }
 
-template <int KIND>
+template <int KIND, int BN>
 cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
   const bool bf = (KIND == GEMM_BF16X3);
   CUtensorMap mA, mB, mA2, mB2;
-  if (!make_map(&mA, g.A, bf, g.K, g.M, g.lda, g.sa, g.batch)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, g.B, bf, g.K, g.N, g.ldb, g.sb, g.batch)) return cudaErrorInvalidValue;
+  if (!make_map(&mA, g.A, bf, g.K, g.M, g.lda, g.sa, g.batch, kBM)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, g.B, bf, g.K, g.N, g.ldb, g.sb, g.batch, BN)) return cudaErrorInvalidValue;
   if (bf) {
-    if (!make_map(&mA2, g.A2, bf, g.K, g.M, g.lda, g.sa, g.batch)) return cudaErrorInvalidValue;
-    if (!make_map(&mB2, g.B2, bf, g.K, g.N, g.ldb, g.sb, g.batch)) return cudaErrorInvalidValue;
+    if (!make_map(&mA2, g.A2, bf, g.K, g.M, g.lda, g.sa, g.batch, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&mB2, g.B2, bf, g.K, g.N, g.ldb, g.sb, g.batch, BN)) return cudaErrorInvalidValue;
   } else {
     mA2 = mA;
     mB2 = mB;
   }
-  constexpr int smem = tc_smem_bytes<KIND>();
+  constexpr int smem = TcCfg<KIND, BN>::kSmem;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((g.N + kBN - 1) / kBN, (g.M + kBM - 1) / kBM, g.batch);
-  gemm_tc_kernel<KIND><<<grid, 128, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K,
-                                                g.ldc, g.sc, g.sa > 0 ? 1 : 0, g.sb > 0 ? 1 : 0,
-                                                static_cast<float>(g.alpha), static_cast<float>(g.beta),
-                                                dev_err);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  const long long tiles = static_cast<long long>((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * g.batch;
+  const int nk = (g.K + TcCfg<KIND, BN>::kKElems - 1) / TcCfg<KIND, BN>::kKElems;
+  // split K when the output tiles cannot fill half the SMs and the K loop is long
+  int splits = 1;
+  const long long outer = static_cast<long long>(g.M) * g.N * g.batch;
+  if (g.work && tiles * 2 < sms && nk >= 8) {
+    splits = static_cast<int>(std::min<long long>((sms + tiles - 1) / tiles, nk / 4));
+    splits = std::min(splits, 32);
+    while (splits > 1 && static_cast<size_t>(splits) * outer * sizeof(float) > g.work_bytes) --splits;
+  }
+  const int kc = (nk + splits - 1) / splits;
+  splits = (nk + kc - 1) / kc;
+  const int grid = static_cast<int>(std::min<long long>(tiles * splits, sms));
+  gemm_tc_kernel<KIND, BN><<<grid, 192, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K, g.ldc,
+                                                    g.sc, g.sa > 0 ? 1 : 0, g.sb > 0 ? 1 : 0,
+                                                    static_cast<float>(g.alpha), static_cast<float>(g.beta), g.batch,
+                                                    splits, kc, static_cast<float*>(g.work), dev_err);
+  if (splits > 1) {
+    const int blocks = static_cast<int>(std::min<long long>((outer + 255) / 256, 152LL * 8));
+    tc_splitk_reduce<<<blocks, 256, 0, st>>>(static_cast<const float*>(g.work), static_cast<float*>(g.C), g.ldc, g.sc,
+                                             g.M, g.N, g.batch, splits, static_cast<float>(g.beta));
+  }
   return cudaGetLastError();
 }
 
@@ -365,9 +475,26 @@ cudaError_t gemm_tc(int kind, const GemmArgs& g, int* dev_err, cudaStream_t st) 
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.K <= 0) return cudaErrorInvalidValue;
   if (!get_encode()) return cudaErrorNotSupported;
-  if (g.batch > 65535 || (g.M + kBM - 1) / kBM > 65535) return cudaErrorInvalidValue;
-  if (kind == GEMM_TF32) return launch_tc<GEMM_TF32>(g, dev_err, st);
-  if (kind == GEMM_BF16X3) return launch_tc<GEMM_BF16X3>(g, dev_err, st);
+  if (g.batch > 65535) return cudaErrorInvalidValue;
+  // tile width: the narrowest of 32 / 64 / 128 / 256 columns that covers N (tcgen05 with
+  // M = 128 takes N in steps of 16 up to 256)
+  const int bn = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256));
+  if (kind == GEMM_TF32) {
+    switch (bn) {
+      case 32: return launch_tc<GEMM_TF32, 32>(g, dev_err, st);
+      case 64: return launch_tc<GEMM_TF32, 64>(g, dev_err, st);
+      case 128: return launch_tc<GEMM_TF32, 128>(g, dev_err, st);
+      default: return launch_tc<GEMM_TF32, 256>(g, dev_err, st);
+    }
+  }
+  if (kind == GEMM_BF16X3) {
+    switch (bn) {
+      case 32: return launch_tc<GEMM_BF16X3, 32>(g, dev_err, st);
+      case 64: return launch_tc<GEMM_BF16X3, 64>(g, dev_err, st);
+      case 128: return launch_tc<GEMM_BF16X3, 128>(g, dev_err, st);
+      default: return launch_tc<GEMM_BF16X3, 256>(g, dev_err, st);
+    }
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -5,6 +5,7 @@
 #include <math_constants.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "ftcc_internal.h"
 
@@ -24,99 +25,163 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
   return static_cast<uint32_t>((static_cast<uint64_t>(__umulhi(n, f.m)) + n) >> f.s);
 }
 
-struct DevPack {
-  int nr, nc;
-  FastDiv rd[kMaxL];
-  long long rst[kMaxL];
-  FastDiv cd[kMaxL];
-  long long cst[kMaxL];
-  FastDiv cpad;
-  uint32_t creal, row0, nrows;
-};
+// ----------------------------------------------------------------- tiled permute
+// dst[k-coords] = beta dst + alpha sum_p sign_p src[sum_k c_k sst_p[k]] over
+// the terms p of an antisymmetriser (identity, one swap, two swaps).  One
+// block owns one tile: a box over a few "tile letters" (the destination's
+// innermost letter and, for every term, the letter at unit source stride),
+// every other letter fixed.  Each term is read in its own letter order
+// (unit source stride fastest) into shared memory and the tile is written
+// in destination order, so both global streams are coalesced whatever the
+// permutation.  Used for the GEMM operand packs (one term, beta 0) and the
+// antisymmetrising scatters of GEMM outputs.
+constexpr int kPermThreads = 256;
+constexpr int kPermTile = 4096;   // elements of one tile in shared memory
+constexpr int kPermRows = 512;    // rows per pass of the shared row table
 
-__device__ __forceinline__ long long pack_offset(const DevPack& d, uint32_t r, uint32_t c) {
-  long long off = 0;
-  for (int k = d.nr - 1; k >= 0; --k) {
-    const uint32_t q = fdiv(d.rd[k], r);
-    off += static_cast<long long>(r - q * d.rd[k].d) * d.rst[k];
-    r = q;
-  }
-  for (int k = d.nc - 1; k >= 0; --k) {
-    const uint32_t q = fdiv(d.cd[k], c);
-    off += static_cast<long long>(c - q * d.cd[k].d) * d.cst[k];
-    c = q;
-  }
-  return off;
-}
-
-// ----------------------------------------------------------------- packing
-template <class T>
-__global__ void pack_kernel(const T* __restrict__ src, T* __restrict__ dst, DevPack d) {
-  const uint32_t total = d.nrows * d.cpad.d;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const uint32_t rl = fdiv(d.cpad, e);
-    const uint32_t c = e - rl * d.cpad.d;
-    const uint32_t r = d.row0 + rl;
-    const T v = (c < d.creal) ? src[pack_offset(d, r, c)] : T(0);
-    dst[static_cast<long long>(r) * d.cpad.d + c] = v;
-  }
-}
-
-__global__ void pack_bf16x2_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
-                                   __nv_bfloat16* __restrict__ lo, DevPack d) {
-  const uint32_t total = d.nrows * d.cpad.d;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const uint32_t rl = fdiv(d.cpad, e);
-    const uint32_t c = e - rl * d.cpad.d;
-    const uint32_t r = d.row0 + rl;
-    const float v = (c < d.creal) ? src[pack_offset(d, r, c)] : 0.0f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const long long o = static_cast<long long>(r) * d.cpad.d + c;
-    hi[o] = h;
-    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
-// ----------------------------------------------------------------- scatter
-struct DevScat {
-  int nd, nswap;
-  FastDiv dim[kMaxL];          // dim[0] = first-letter values in this launch
-  long long sst[kMaxL];
-  int sw[2][2];
-  uint32_t c0, total;          // first-letter offset of this launch, elements in it
-  long long inner;             // elements per first-letter value
+struct DevPerm {
+  int nd, nterm, nt;
+  FastDiv bcnt[kMaxL];             // blocks along dst letter k
+  int bstep[kMaxL];                // coordinate step per block along k (1, or the tile extent)
+  int tslot[kMaxL];                // tile-letter slot of dst letter k, -1 if not a tile letter
+  long long sst[4][kMaxL];         // term p: source stride of dst letter k (swaps applied)
+  long long dstr[kMaxL];           // destination stride of dst letter k
+  // per order o (terms 0..3, write = 4), position l (fastest first):
+  FastDiv fd_full[5][kMaxL], fd_tail[5][kMaxL];   // extent of that tile letter in an inner / last block
+  int slot[5][kMaxL];              // tile-letter slot at that position
+  long long gstr[5][kMaxL];        // global stride at that position (source for terms, dst for write)
+  int tstr[5][kMaxL];              // shared-memory stride at that position
+  int tail_blk[kMaxL];             // per tile slot: block coordinate of the last (tail) block
+  int ext_full[kMaxL], ext_tail[kMaxL];
+  float sign[4];
+  uint32_t block0;
 };
 
 template <class T>
-__global__ void scatter_kernel(const T* __restrict__ src, T* __restrict__ dst, DevScat d, T alpha, T beta) {
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < d.total; e += gridDim.x * blockDim.x) {
-    uint32_t c[kMaxL];
-    uint32_t rem = e;
-    for (int k = d.nd - 1; k >= 1; --k) {
-      const uint32_t q = fdiv(d.dim[k], rem);
-      c[k] = rem - q * d.dim[k].d;
-      rem = q;
+struct PermOut {
+  T* dst;
+  __nv_bfloat16* hi;   // bf16 hi / lo split output (dst unused) when non-null
+  __nv_bfloat16* lo;
+};
+
+// Rows of one order: every tile element is (row, f) with f the coordinate of
+// the order's fastest letter.  A row table (global offset, tile index) is
+// built in shared memory, then a warp covers 32 / ext_f rows per pass with
+// lane = (row within the pass, f): one table lookup and two multiply-adds per
+// element.
+template <int O, class F>
+__device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, int n, long long* rowG, int* rowT,
+                                          F&& body) {
+  const int sl0 = d.slot[O][0];
+  const int ef = ((tailmask >> sl0) & 1u) ? d.ext_tail[sl0] : d.ext_full[sl0];
+  const long long gf = d.gstr[O][0];
+  const int tf = d.tstr[O][0];
+  const int nrows = n / ef;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarps = kPermThreads / 32;
+  const int per = ef <= 32 ? 32 / ef : 1;
+  const int sub = ef <= 32 ? lane / ef : 0;
+  const int co0 = ef <= 32 ? lane - sub * ef : lane;
+  for (int r0 = 0; r0 < nrows; r0 += kPermRows) {
+    const int nr = min(kPermRows, nrows - r0);
+    for (int r = threadIdx.x; r < nr; r += kPermThreads) {
+      uint32_t rr = static_cast<uint32_t>(r0 + r);
+      long long g = 0;
+      int t = 0;
+#pragma unroll
+      for (int l = 1; l < kMaxL; ++l) {
+        if (l < d.nt) {
+          const FastDiv f = ((tailmask >> d.slot[O][l]) & 1u) ? d.fd_tail[O][l] : d.fd_full[O][l];
+          const uint32_t q = fdiv(f, rr);
+          const uint32_t co = rr - q * f.d;
+          rr = q;
+          g += static_cast<long long>(co) * d.gstr[O][l];
+          t += static_cast<int>(co) * d.tstr[O][l];
+        }
+      }
+      rowG[r] = g;
+      rowT[r] = t;
     }
-    c[0] = rem + d.c0;
-    long long off = 0;
-    for (int k = 0; k < d.nd; ++k) off += static_cast<long long>(c[k]) * d.sst[k];
-    T v = src[off];
-    if (d.nswap >= 1) {
-      const int a = d.sw[0][0], b = d.sw[0][1];
-      const long long ca = c[a], cb = c[b];
-      const long long o1 = off + (cb - ca) * d.sst[a] + (ca - cb) * d.sst[b];
-      v -= src[o1];
-      if (d.nswap == 2) {
-        const int p = d.sw[1][0], q = d.sw[1][1];
-        const long long cp = c[p], cq = c[q];
-        const long long dq = (cq - cp) * d.sst[p] + (cp - cq) * d.sst[q];
-        v -= src[off + dq];
-        v += src[o1 + dq];
+    __syncthreads();
+    if (sub < per) {
+      for (int r = warp * per + sub; r < nr; r += kWarps * per)
+        for (int co = co0; co < ef; co += 32) body(rowG[r] + co * gf, rowT[r] + co * tf);
+    }
+    __syncthreads();
+  }
+}
+
+// Term P of the antisymmetriser into the tile (term 0 stores, the others add
+// with their sign).
+template <int P, class T>
+__device__ __forceinline__ void perm_term(const DevPerm& d, const long long* c, uint32_t tailmask, int n,
+                                          long long* rowG, int* rowT, const T* __restrict__ src, T* tile) {
+  long long base = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxL; ++k)
+    if (k < d.nd) base += c[k] * d.sst[P][k];
+  const T* sp = src + base;
+  if (P == 0) {
+    perm_rows<0>(d, tailmask, n, rowG, rowT, [&](long long g, int t) { tile[t] = sp[g]; });
+  } else {
+    const T sg = static_cast<T>(d.sign[P]);
+    perm_rows<P>(d, tailmask, n, rowG, rowT, [&](long long g, int t) { tile[t] += sg * sp[g]; });
+  }
+}
+
+template <class T, bool SPLIT>
+__global__ void __launch_bounds__(kPermThreads) permute_kernel(const T* __restrict__ src, PermOut<T> out, DevPerm d,
+                                                               T alpha, T beta) {
+  extern __shared__ __align__(16) unsigned char perm_smem[];
+  T* tile = reinterpret_cast<T*>(perm_smem);
+  __shared__ long long rowG[kPermRows];
+  __shared__ int rowT[kPermRows];
+  // block -> coordinates of every dst letter (tile letters: the box start)
+  uint32_t r = d.block0 + blockIdx.x;
+  long long c[kMaxL];
+  uint32_t tailmask = 0;
+  int n = 1;
+#pragma unroll
+  for (int k = kMaxL - 1; k >= 0; --k) {
+    c[k] = 0;
+    if (k < d.nd) {
+      const uint32_t q = fdiv(d.bcnt[k], r);
+      const uint32_t bk = r - q * d.bcnt[k].d;
+      r = q;
+      c[k] = static_cast<long long>(bk) * d.bstep[k];
+      const int sl = d.tslot[k];
+      if (sl >= 0) {
+        const bool tail = bk == static_cast<uint32_t>(d.tail_blk[sl]);
+        tailmask |= (tail ? 1u : 0u) << sl;
+        n *= tail ? d.ext_tail[sl] : d.ext_full[sl];
       }
     }
-    const long long o = static_cast<long long>(d.c0) * d.inner + e;
-    const T out = alpha * v;
-    dst[o] = (beta == T(0)) ? out : beta * dst[o] + out;
+  }
+  // terms: gather into the tile, each in its own letter order
+  perm_term<0>(d, c, tailmask, n, rowG, rowT, src, tile);
+  if (d.nterm > 1) perm_term<1>(d, c, tailmask, n, rowG, rowT, src, tile);
+  if (d.nterm > 2) perm_term<2>(d, c, tailmask, n, rowG, rowT, src, tile);
+  if (d.nterm > 3) perm_term<3>(d, c, tailmask, n, rowG, rowT, src, tile);
+  // write in destination order
+  long long dbase = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxL; ++k)
+    if (k < d.nd) dbase += c[k] * d.dstr[k];
+  if constexpr (SPLIT) {
+    __nv_bfloat16* hi = out.hi + dbase;
+    __nv_bfloat16* lo = out.lo + dbase;
+    perm_rows<4>(d, tailmask, n, rowG, rowT, [&](long long g, int t) {
+      const float v = static_cast<float>(tile[t]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[g] = h;
+      lo[g] = __float2bfloat16_rn(v - __bfloat162float(h));
+    });
+  } else {
+    T* dp = out.dst + dbase;
+    perm_rows<4>(d, tailmask, n, rowG, rowT, [&](long long g, int t) {
+      const T v = alpha * tile[t];
+      dp[g] = (beta == T(0)) ? v : beta * dp[g] + v;
+    });
   }
 }
 
@@ -365,10 +430,12 @@ constexpr int kPropThreads = 128;
 
 template <class T, int NS>
 __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __restrict__ S, T* __restrict__ t, PropArgs a) {
-  extern __shared__ double eacc[];                    // [ng][blockDim]
+  constexpr int kWarps = kPropThreads / 32;
+  extern __shared__ double eacc[];                    // [ng][kWarps] energy partial per warp
   const int ng = a.ng;
   const int z = blockIdx.y;                           // instance
   if (a.live && !a.live[z]) return;                   // frozen: amplitudes and partials untouched
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long size = a.size;
   S += static_cast<long long>(z) * ng * size;
   t += static_cast<long long>(z) * ng * size;
@@ -377,12 +444,22 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
   const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * a.no * a.nv : nullptr;
   double* partials = a.partials + static_cast<long long>(z) * a.nblocks * (ng + 2);
-  for (int y = 0; y < ng; ++y) eacc[y * blockDim.x + threadIdx.x] = 0.0;
-  double dmax = 0.0, smax = 0.0;
-  for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
-       mu += static_cast<long long>(gridDim.x) * blockDim.x) {
-    int i, j = 0, aa, b = 0;
-    {
+  for (int i = threadIdx.x; i < ng * kWarps; i += blockDim.x) eacc[i] = 0.0;
+  __syncthreads();
+  T dmax = T(0), smax = T(0);
+  const T h = static_cast<T>(a.hz[z]);
+  const T c12 = h / T(12), c3 = h / T(3), c38 = T(3) * h / T(8);
+  const T damp = static_cast<T>(a.damping);
+  const T cE = static_cast<T>(a.cE);
+  // warp-uniform loop: every lane runs every tau step so the per-tau energy
+  // can be reduced across the warp; lanes past the end contribute zero
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x + warp * 32; base < size; base += stride) {
+    const long long mu = base + lane;
+    const bool valid = mu < size;
+    int i = 0, j = 0, aa = 0, b = 0;
+    T r1 = T(0), rinv = T(0), w = T(0);
+    if (valid) {
       uint32_t r = static_cast<uint32_t>(mu);
       uint32_t q = fdiv(a.fv, r);
       if (NS == 4) {
@@ -398,79 +475,94 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
         aa = r - q * a.nv;
         i = q;
       }
+      const int pi = a.idxO[i], pa = a.idxV[aa];
+      double rr = em[pa] * ep[pi];
+      double ri = ep[pa] * em[pi];
+      if (NS == 4) {
+        const int pj = a.idxO[j], pb = a.idxV[b];
+        rr *= em[pb] * ep[pj];
+        ri *= ep[pb] * em[pj];
+      }
+      // The recurrence runs in the storage precision: FP32 storage carries
+      // ~1e-7 relative error anyway, and FP64 issue rate is a small fraction
+      // of FP32 on this part.  FP64 storage keeps everything in FP64.
+      r1 = static_cast<T>(rr);
+      rinv = static_cast<T>(ri);
+      w = wE ? static_cast<T>(wE[mu]) : T(0);
     }
-    const int pi = a.idxO[i], pa = a.idxV[aa];
-    double rr = em[pa] * ep[pi];
-    double ri = ep[pa] * em[pi];
-    if (NS == 4) {
-      const int pj = a.idxO[j], pb = a.idxV[b];
-      rr *= em[pb] * ep[pj];
-      ri *= ep[pb] * em[pj];
-    }
-    const double r2 = rr * rr, r3 = r2 * rr;
-    const double w = wE ? wE[mu] : 0.0;
-    const double h = a.hz[z];
-    double s0 = static_cast<double>(S[mu]);
-    double s1 = static_cast<double>(S[size + mu]);
-    double s2 = static_cast<double>(S[2 * size + mu]);
-    double sm1 = 0.0, sm2 = 0.0, sm3 = 0.0;   // S_{y-1}, S_{y-2}, S_{y-3}
-    double Ilast = 0.0, Iprev = 0.0;          // I at the last and second-last even y
+    const T r2 = r1 * r1, r3 = r2 * r1;
+    const T s0 = valid ? S[mu] : T(0);
+    const T s1 = valid ? S[size + mu] : T(0);
+    const T s2 = valid ? S[2 * size + mu] : T(0);
+    T sm1 = T(0), sm2 = T(0), sm3 = T(0);   // S_{y-1}, S_{y-2}, S_{y-3}
+    T Ilast = T(0), Iprev = T(0);           // I at the last and second-last even y
+    T s_next = s0, t_next = valid ? t[mu] : T(0);
     for (int y = 0; y < ng; ++y) {
-      double sy;
-      if (y == 0) sy = s0;
-      else if (y == 1) sy = s1;
-      else if (y == 2) sy = s2;
-      else sy = static_cast<double>(S[y * size + mu]);
-      double I;
+      const T sy = s_next;
+      const T old = t_next;
+      if (y + 1 < ng && valid) {            // loads of the next step, one step ahead
+        const long long nx = (y + 1) * size + mu;
+        s_next = (y + 1 == 1) ? s1 : ((y + 1 == 2) ? s2 : S[nx]);
+        t_next = t[nx];
+      }
+      T I;
       if (y == 0) {
-        I = 0.0;
+        I = T(0);
       } else if (y == 1) {
-        I = h / 12.0 * (5.0 * rr * s0 + 8.0 * s1 - ri * s2);
+        I = c12 * (T(5) * r1 * s0 + T(8) * s1 - rinv * s2);
       } else if ((y & 1) == 0) {
-        I = r2 * Ilast + h / 3.0 * (r2 * sm2 + 4.0 * rr * sm1 + sy);
+        I = r2 * Ilast + c3 * (r2 * sm2 + T(4) * r1 * sm1 + sy);
         Iprev = Ilast;
         Ilast = I;
       } else {
-        I = r3 * Iprev + 3.0 * h / 8.0 * (r3 * sm3 + 3.0 * r2 * sm2 + 3.0 * rr * sm1 + sy);
+        I = r3 * Iprev + c38 * (r3 * sm3 + T(3) * r2 * sm2 + T(3) * r1 * sm1 + sy);
       }
       sm3 = sm2;
       sm2 = sm1;
       sm1 = sy;
-      const long long off = y * size + mu;
-      const double old = static_cast<double>(t[off]);
-      double nw = -I;
-      if (a.damping != 1.0) nw = (1.0 - a.damping) * old + a.damping * nw;
-      const T stored = static_cast<T>(nw);
-      t[off] = stored;
-      const double sv = static_cast<double>(stored);
-      dmax = fmax(dmax, fabs(sv - old));
-      smax = fmax(smax, fabs(sv));
+      T stored = -I;
+      if (a.damping != 1.0) stored = (T(1) - damp) * old + damp * stored;
+      if (valid) {
+        t[y * size + mu] = stored;
+        dmax = fmax(dmax, fabs(stored - old));
+        smax = fmax(smax, fabs(stored));
+      }
       if (wE) {
-        double e = a.cE * sv;
-        if (NS == 4 && t1E) {
-          const T* s1y = t1E + static_cast<long long>(y) * a.no * a.nv;
-          e += 0.5 * static_cast<double>(s1y[i * a.nv + aa]) * static_cast<double>(s1y[j * a.nv + b]);
+        T e = T(0);
+        if (valid) {
+          e = cE * stored;
+          if (NS == 4 && t1E) {
+            const T* s1y = t1E + static_cast<long long>(y) * a.no * a.nv;
+            e += T(0.5) * s1y[i * a.nv + aa] * s1y[j * a.nv + b];
+          }
+          e *= w;
         }
-        eacc[y * blockDim.x + threadIdx.x] += w * e;
+        // fixed-order warp sum, then one FP64 add per warp and tau
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if (lane == 0) eacc[y * kWarps + warp] += static_cast<double>(e);
       }
     }
   }
   __shared__ double dm[kPropThreads], sm[kPropThreads];
-  dm[threadIdx.x] = dmax;
-  sm[threadIdx.x] = smax;
+  dm[threadIdx.x] = static_cast<double>(dmax);
+  sm[threadIdx.x] = static_cast<double>(smax);
   __syncthreads();
   // deterministic tree reductions
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       dm[threadIdx.x] = fmax(dm[threadIdx.x], dm[threadIdx.x + s]);
       sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
-      for (int y = 0; y < ng; ++y) eacc[y * blockDim.x + threadIdx.x] += eacc[y * blockDim.x + threadIdx.x + s];
     }
     __syncthreads();
   }
+  double* p = partials + static_cast<long long>(blockIdx.x) * (ng + 2);
+  for (int y = threadIdx.x; y < ng; y += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < kWarps; ++k) acc += eacc[y * kWarps + k];
+    p[y] = acc;
+  }
   if (threadIdx.x == 0) {
-    double* p = partials + static_cast<long long>(blockIdx.x) * (ng + 2);
-    for (int y = 0; y < ng; ++y) p[y] = eacc[y * blockDim.x];
     p[ng] = dm[0];
     p[ng + 1] = sm[0];
   }
@@ -827,80 +919,205 @@ __global__ void reduce_kernel(const double* __restrict__ p1, int nb1, const doub
 
 // ----------------------------------------------------------------- launchers
 namespace {
-constexpr uint32_t kChunk = 0x7FFFFFFFu;
+// Host side of the tiled permute: choose the tile letters and their extents,
+// the per-term read orders and the block decomposition.
+struct PermPlan {
+  int nd = 0, nterm = 1;
+  long long dim[kMaxL] = {}, sst[4][kMaxL] = {}, dstr[kMaxL] = {};
+};
 
-DevPack dev_pack(const PackDesc& d) {
-  DevPack p{};
-  p.nr = d.nr;
-  p.nc = d.nc;
-  for (int k = 0; k < d.nr; ++k) {
-    p.rd[k] = make_fastdiv(static_cast<uint32_t>(d.rdim[k]));
-    p.rst[k] = d.rst[k];
+template <class T, bool SPLIT>
+cudaError_t run_permute(const PermPlan& P, const T* src, PermOut<T> out, double alpha, double beta, cudaStream_t st) {
+  const int nd = P.nd;
+  if (nd < 1 || nd > kMaxL) return cudaErrorInvalidValue;
+  long long total = 1;
+  for (int k = 0; k < nd; ++k) total *= P.dim[k];
+  if (total == 0) return cudaSuccess;
+  // tile letters: dst innermost, then each term's unit-stride letter
+  auto argmin = [&](const long long* st_) {
+    int best = -1;
+    for (int k = 0; k < nd; ++k)
+      if (P.dim[k] > 1 && st_[k] > 0 && (best < 0 || st_[k] < st_[best])) best = k;
+    return best;
+  };
+  int tl[kMaxL], nt = 0;
+  auto add = [&](int k) {
+    if (k < 0) return;
+    for (int l = 0; l < nt; ++l)
+      if (tl[l] == k) return;
+    tl[nt++] = k;
+  };
+  add(argmin(P.dstr));
+  for (int p = 0; p < P.nterm; ++p) add(argmin(P.sst[p]));
+  if (nt == 0) add(nd - 1);
+  long long ext[kMaxL];
+  for (int l = 0; l < nt; ++l) ext[l] = P.dim[tl[l]];
+  auto prod = [&]() {
+    long long v = 1;
+    for (int l = 0; l < nt; ++l) v *= ext[l];
+    return v;
+  };
+  while (prod() > kPermTile) {   // shrink the widest extent
+    int w = 0;
+    for (int l = 1; l < nt; ++l)
+      if (ext[l] > ext[w]) w = l;
+    ext[w] = (ext[w] + 1) / 2;
   }
-  for (int k = 0; k < d.nc; ++k) {
-    p.cd[k] = make_fastdiv(static_cast<uint32_t>(d.cdim[k]));
-    p.cst[k] = d.cst[k];
+  // grow with whole destination letters, innermost first
+  {
+    int order[kMaxL];
+    for (int k = 0; k < nd; ++k) order[k] = k;
+    std::sort(order, order + nd, [&](int a, int b) { return P.dstr[a] < P.dstr[b]; });
+    for (int i = 0; i < nd; ++i) {
+      const int k = order[i];
+      bool in = false;
+      for (int l = 0; l < nt; ++l) in |= tl[l] == k;
+      if (in || P.dim[k] <= 1) continue;
+      if (prod() * P.dim[k] > kPermTile) continue;
+      tl[nt] = k;
+      ext[nt] = P.dim[k];
+      ++nt;
+    }
   }
-  p.cpad = make_fastdiv(static_cast<uint32_t>(d.cpad));
-  p.creal = static_cast<uint32_t>(d.creal);
-  return p;
-}
-
-template <class F>
-cudaError_t pack_chunks(const PackDesc& d, F&& launch) {
-  if (d.rows <= 0 || d.cpad <= 0) return cudaSuccess;
-  if (d.rows >= (1LL << 32) || d.cpad >= (1LL << 31)) return cudaErrorInvalidValue;
-  DevPack p = dev_pack(d);
-  const long long per = std::max<long long>(1, kChunk / d.cpad);
-  for (long long r0 = 0; r0 < d.rows; r0 += per) {
-    p.row0 = static_cast<uint32_t>(r0);
-    p.nrows = static_cast<uint32_t>(std::min(per, d.rows - r0));
-    launch(p, static_cast<long long>(p.nrows) * d.cpad);
+  DevPerm d{};
+  d.nd = nd;
+  d.nterm = P.nterm;
+  d.nt = nt;
+  const float signs[4] = {1.0f, -1.0f, -1.0f, 1.0f};
+  for (int p = 0; p < 4; ++p) d.sign[p] = signs[p];
+  for (int k = 0; k < nd; ++k) {
+    d.tslot[k] = -1;
+    d.dstr[k] = P.dstr[k];
+    for (int p = 0; p < P.nterm; ++p) d.sst[p][k] = P.sst[p][k];
+  }
+  unsigned long long nblocks = 1;
+  for (int k = 0; k < nd; ++k) {
+    long long cnt = P.dim[k], step = 1;
+    for (int l = 0; l < nt; ++l)
+      if (tl[l] == k) {
+        d.tslot[k] = l;
+        cnt = (P.dim[k] + ext[l] - 1) / ext[l];
+        step = ext[l];
+        d.tail_blk[l] = static_cast<int>(cnt - 1);
+        d.ext_full[l] = static_cast<int>(ext[l]);
+        d.ext_tail[l] = static_cast<int>(P.dim[k] - (cnt - 1) * ext[l]);
+      }
+    if (cnt >= (1LL << 32)) return cudaErrorInvalidValue;
+    d.bcnt[k] = make_fastdiv(static_cast<uint32_t>(cnt));
+    d.bstep[k] = static_cast<int>(step);
+    nblocks *= static_cast<unsigned long long>(cnt);
+  }
+  if (nblocks >= (1ULL << 32)) return cudaErrorInvalidValue;
+  // orders: terms by source stride, the write by destination stride; the
+  // shared-memory tile is dense in write order
+  int word[kMaxL];
+  for (int l = 0; l < nt; ++l) word[l] = l;
+  std::sort(word, word + nt, [&](int a, int b) { return P.dstr[tl[a]] < P.dstr[tl[b]]; });
+  int tstr[kMaxL];
+  long long tile_elems = 1;
+  {
+    // dense in write order, except that the stride after the fastest letter
+    // is made odd so that a transposed pass hits 32 different banks
+    long long dense = 1;
+    for (int l = 0; l < nt; ++l) dense *= ext[l];
+    const bool pad = nt > 1 && (ext[word[0]] & 1) == 0 &&
+                     static_cast<size_t>(dense / ext[word[0]] * (ext[word[0]] + 1)) * sizeof(T) <= 40 * 1024;
+    long long acc = 1;
+    for (int i = 0; i < nt; ++i) {
+      tstr[word[i]] = static_cast<int>(acc);
+      acc *= ext[word[i]];
+      if (i == 0 && pad) acc += 1;
+    }
+    tile_elems = acc;
+  }
+  auto fill = [&](int o, const int* ord, const long long* gst) {
+    for (int i = 0; i < nt; ++i) {
+      const int l = ord[i];
+      d.slot[o][i] = l;
+      d.fd_full[o][i] = make_fastdiv(static_cast<uint32_t>(d.ext_full[l]));
+      d.fd_tail[o][i] = make_fastdiv(static_cast<uint32_t>(d.ext_tail[l]));
+      d.gstr[o][i] = gst[tl[l]];
+      d.tstr[o][i] = tstr[l];
+    }
+  };
+  for (int p = 0; p < P.nterm; ++p) {
+    int ord[kMaxL];
+    for (int l = 0; l < nt; ++l) ord[l] = l;
+    std::stable_sort(ord, ord + nt, [&](int a, int b) {
+      const long long sa = P.sst[p][tl[a]], sb = P.sst[p][tl[b]];
+      return (sa == 0 ? LLONG_MAX : sa) < (sb == 0 ? LLONG_MAX : sb);
+    });
+    fill(p, ord, P.sst[p]);
+  }
+  fill(4, word, P.dstr);
+  const size_t smem = static_cast<size_t>(tile_elems) * sizeof(T);
+  for (unsigned long long b0 = 0; b0 < nblocks; b0 += 0x7FFFFFFFull) {
+    d.block0 = static_cast<uint32_t>(b0);
+    const unsigned int g = static_cast<unsigned int>(std::min<unsigned long long>(nblocks - b0, 0x7FFFFFFFull));
+    permute_kernel<T, SPLIT><<<g, kPermThreads, smem, st>>>(src, out, d, static_cast<T>(alpha), static_cast<T>(beta));
   }
   return cudaGetLastError();
+}
+
+PermPlan pack_plan(const PackDesc& d) {
+  PermPlan P;
+  P.nd = d.nr + d.nc;
+  P.nterm = 1;
+  long long s = 1;
+  for (int k = d.nc - 1; k >= 0; --k) {
+    P.dim[d.nr + k] = d.cdim[k];
+    P.sst[0][d.nr + k] = d.cst[k];
+    P.dstr[d.nr + k] = s;
+    s *= d.cdim[k];
+  }
+  s = d.cpad;
+  for (int k = d.nr - 1; k >= 0; --k) {
+    P.dim[k] = d.rdim[k];
+    P.sst[0][k] = d.rst[k];
+    P.dstr[k] = s;
+    s *= d.rdim[k];
+  }
+  return P;
 }
 }  // namespace
 
 template <class T>
 cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st) {
-  return pack_chunks(d, [&](const DevPack& p, long long n) {
-    pack_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(src, dst, p);
-  });
+  if (d.rows <= 0 || d.creal <= 0) return cudaSuccess;
+  return run_permute<T, false>(pack_plan(d), src, PermOut<T>{dst, nullptr, nullptr}, 1.0, 0.0, st);
 }
 template cudaError_t launch_pack<float>(const float*, float*, const PackDesc&, cudaStream_t);
 template cudaError_t launch_pack<double>(const double*, double*, const PackDesc&, cudaStream_t);
 
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st) {
-  return pack_chunks(d, [&](const DevPack& p, long long n) {
-    pack_bf16x2_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, static_cast<__nv_bfloat16*>(hi),
-                                                        static_cast<__nv_bfloat16*>(lo), p);
-  });
+  if (d.rows <= 0 || d.creal <= 0) return cudaSuccess;
+  return run_permute<float, true>(pack_plan(d), src,
+                                  PermOut<float>{nullptr, static_cast<__nv_bfloat16*>(hi),
+                                                 static_cast<__nv_bfloat16*>(lo)},
+                                  1.0, 0.0, st);
 }
 
 template <class T>
 cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha, double beta, cudaStream_t st) {
   if (d.total <= 0) return cudaSuccess;
-  DevScat s{};
-  s.nd = d.nd;
-  s.nswap = d.nswap;
-  long long inner = 1;
-  for (int k = 1; k < d.nd; ++k) inner *= d.dim[k];
-  if (inner >= (1LL << 31) || d.dim[0] >= (1LL << 32)) return cudaErrorInvalidValue;
-  for (int k = 0; k < d.nd; ++k) {
-    s.dim[k] = make_fastdiv(static_cast<uint32_t>(d.dim[k]));
-    s.sst[k] = d.sst[k];
+  if (d.nswap < 0 || d.nswap > 2) return cudaErrorInvalidValue;
+  PermPlan P;
+  P.nd = d.nd;
+  P.nterm = 1 << d.nswap;
+  long long s = 1;
+  for (int k = d.nd - 1; k >= 0; --k) {
+    P.dim[k] = d.dim[k];
+    P.dstr[k] = s;
+    s *= d.dim[k];
   }
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) s.sw[a][b] = d.sw[a][b];
-  s.inner = inner;
-  const long long per = std::max<long long>(1, kChunk / inner);
-  for (long long c0 = 0; c0 < d.dim[0]; c0 += per) {
-    const long long cnt = std::min(per, d.dim[0] - c0);
-    s.c0 = static_cast<uint32_t>(c0);
-    s.total = static_cast<uint32_t>(cnt * inner);
-    scatter_kernel<T><<<grid_for(s.total, 256), 256, 0, st>>>(src, dst, s, static_cast<T>(alpha), static_cast<T>(beta));
+  for (int p = 0; p < P.nterm; ++p) {
+    int pm[kMaxL];
+    for (int k = 0; k < d.nd; ++k) pm[k] = k;
+    for (int w = 0; w < 2; ++w)
+      if (p & (1 << w)) std::swap(pm[d.sw[w][0]], pm[d.sw[w][1]]);
+    for (int k = 0; k < d.nd; ++k) P.sst[p][k] = d.sst[pm[k]];
   }
-  return cudaGetLastError();
+  return run_permute<T, false>(P, src, PermOut<T>{dst, nullptr, nullptr}, alpha, beta, st);
 }
 template cudaError_t launch_scatter<float>(const float*, float*, const ScatDesc&, double, double, cudaStream_t);
 template cudaError_t launch_scatter<double>(const double*, double*, const ScatDesc&, double, double, cudaStream_t);
@@ -1004,7 +1221,7 @@ cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
-  const size_t smem = static_cast<size_t>(a.ng) * kPropThreads * sizeof(double);
+  const size_t smem = static_cast<size_t>(a.ng) * (kPropThreads / 32) * sizeof(double);
   int blocks = a.nblocks;
   if (a.nz < 1 || a.nz > 65535) return cudaErrorInvalidValue;
   dim3 grid(blocks, a.nz);

@@ -152,6 +152,8 @@ struct Batch {
   Buf facOz, facVz, epsz;        // stacked [nz][no], [nz][nv], [nz][N] for the response
   bool lambda_done = false;
   int lambda_iterations = 0;
+  double prof_ms[8] = {0}, prof_bytes[8] = {0}, prof_flops[8] = {0};
+  long long prof_launches[8] = {0};
   int iterations = 0, refine_iterations = 0;
   double ms_total = 0;
   int ms_count = 0;
@@ -160,6 +162,11 @@ struct Batch {
 };
 
 constexpr int kStateStride = 8 + 256;
+
+// kernel classes of the per-iteration timing
+enum { kClsScatter = 0, kClsPack, kClsGemmTc, kClsGemmSimt, kClsPropagate, kClsOther, kNumCls };
+const char* const kClsName[kNumCls] = {"permute_kernel:scatter", "permute_kernel:pack", "gemm_tc_kernel",
+                                       "gemm_simt_kernel", "propagate_kernel", "other"};
 
 template <class T>
 struct Solver {
@@ -197,6 +204,42 @@ struct Solver {
   };
   std::vector<Op> tape;
   bool recording = false;
+
+  // Kernel timing: CUDA events around every launch of the iteration (inside
+  // the captured graph as event nodes), summed per kernel class with the
+  // algorithmic bytes and flops of each launch.
+  struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double bytes, flops;
+  };
+  bool profiling = false;
+  std::vector<ProfRec> prof;
+  size_t prof_next = 0;
+  template <class F>
+  void timed_launch(int cls, double bytes, double flops, F&& launch) {
+    if (!profiling) {
+      launch();
+      return;
+    }
+    if (prof_next == prof.size()) {
+      ProfRec r{};
+      CU(cudaEventCreate(&r.e0));
+      CU(cudaEventCreate(&r.e1));
+      prof.push_back(r);
+    }
+    ProfRec& r = prof[prof_next++];
+    r.cls = cls;
+    r.bytes = bytes;
+    r.flops = flops;
+    // inside a stream capture the records must become graph nodes of their own
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(st(), &cs));
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CU(cudaEventRecordWithFlags(r.e0, st(), flags));
+    launch();
+    CU(cudaEventRecordWithFlags(r.e1, st(), flags));
+  }
   std::map<const void*, T*> bar;            // forward buffer -> its adjoint
   std::map<const void*, Buf> fixed_bar;     // integral / Fock block -> adjoint (when wanted)
   bool want_fixed_bar = false;
@@ -216,6 +259,10 @@ struct Solver {
                  &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
     for (auto& kv : fixed_bar) h_->put(kv.second);
+    for (auto& r : prof) {
+      cudaEventDestroy(r.e0);
+      cudaEventDestroy(r.e1);
+    }
   }
   cudaStream_t st() const { return h_->st; }
 
@@ -276,7 +323,9 @@ struct Solver {
       d.sw[d.nswap][1] = static_cast<int>(pb - Ld);
       d.nswap++;
     }
-    CU(launch_scatter<T>(src, dst, d, alpha, beta, st()));
+    const double reads = (d.nswap == 0 ? 1 : (d.nswap == 1 ? 2 : 4)) + (beta != 0.0 ? 1 : 0);
+    timed_launch(kClsScatter, static_cast<double>(d.total) * (reads + 1) * sizeof(T), 0.0,
+                 [&] { CU(launch_scatter<T>(src, dst, d, alpha, beta, st())); });
   }
 
   void pack(const T* src, const char* Ls, const std::string& rows, const std::string& cols, long long cpad, T* dst,
@@ -298,11 +347,14 @@ struct Solver {
       d.creal *= d.cdim[k];
     }
     d.cpad = cpad;
-    if (hi) {
-      CU(launch_pack_bf16x2(reinterpret_cast<const float*>(src), hi, lo, d, st()));
-    } else {
-      CU(launch_pack<T>(src, dst, d, st()));
-    }
+    const double pbytes = static_cast<double>(d.rows) * (d.creal * sizeof(T) + d.cpad * (hi ? 4 : sizeof(T)));
+    timed_launch(kClsPack, pbytes, 0.0, [&] {
+      if (hi) {
+        CU(launch_pack_bf16x2(reinterpret_cast<const float*>(src), hi, lo, d, st()));
+      } else {
+        CU(launch_pack<T>(src, dst, d, st()));
+      }
+    });
   }
 
   // One GEMM operand: [rows][ld] row-major with K = cols contiguous.  Uses
@@ -348,24 +400,72 @@ struct Solver {
   }
 
   // C(Lc) = beta_acc * C + alpha * P(sum over shared letters A(La) B(Lb))
+  //
+  // Among the 16 ways to feed this contraction to the GEMM (which operand is
+  // "A", and the order of the row letters of each operand and of the summed
+  // letters) the engine takes the one that moves the fewest bytes: an operand
+  // already stored as [rows][K] is used in place, a fixed operand's pack is
+  // cached, and a GEMM output already in C's layout (no antisymmetriser) is
+  // written straight into C.
   void contract(Tn<T> C, double alpha, Tn<const T> A, Tn<const T> B, const char* anti = "", double beta_acc = 1.0) {
     if (recording) tape.push_back(Op{0, C.p, C.L, A.p, A.L, B.p, B.L, nullptr, alpha, beta_acc, anti});
-    std::string Lc = C.L, La = A.L, Lb = B.L, bat, Ml, Nl, Kl;
-    for (char ch : Lc) {
-      const bool ia = La.find(ch) != std::string::npos, ib = Lb.find(ch) != std::string::npos;
-      if (ia && ib) bat += ch;
-      else if (ia) Ml += ch;
-      else if (ib) Nl += ch;
-      else throw Fail{FTCC_ERR_STATE, "letter of C in neither operand"};
-    }
-    for (char ch : La)
-      if (Lc.find(ch) == std::string::npos) {
-        if (Lb.find(ch) == std::string::npos) throw Fail{FTCC_ERR_STATE, "free letter in A"};
-        Kl += ch;
+    const std::string Lc = C.L;
+    for (char ch : Lc)
+      if (!strchr(A.L, ch) && !strchr(B.L, ch)) throw Fail{FTCC_ERR_STATE, "letter of C in neither operand"};
+    for (const char* q = A.L; *q; ++q)
+      if (!strchr(C.L, *q) && !strchr(B.L, *q)) throw Fail{FTCC_ERR_STATE, "free letter in A"};
+    for (const char* q = B.L; *q; ++q)
+      if (!strchr(C.L, *q) && !strchr(A.L, *q)) throw Fail{FTCC_ERR_STATE, "free letter in B"};
+    auto size_of_letters = [&](const std::string& L) {
+      long long s = 1;
+      for (char ch : L) s *= dimof(ch);
+      return s;
+    };
+    auto ordered = [](const std::string& from, const std::string& keep) {
+      std::string out;
+      for (char ch : from)
+        if (keep.find(ch) != std::string::npos) out += ch;
+      return out;
+    };
+    struct Plan {
+      bool swap;
+      std::string bat, Ml, Nl, Kl;
+      bool direct;
+      long long cost;
+    };
+    Plan best{};
+    best.cost = -1;
+    const bool anti_none = anti[0] == 0;
+    const long long csize = size_of_letters(Lc);
+    for (int mask = 0; mask < 16; ++mask) {
+      const bool swap = mask & 1;
+      const Tn<const T>& X = swap ? B : A;
+      const Tn<const T>& Y = swap ? A : B;
+      const std::string LX = X.L, LY = Y.L;
+      std::string bat, Mset, Nset, Kset;
+      for (char ch : Lc) {
+        const bool ix = LX.find(ch) != std::string::npos, iy = LY.find(ch) != std::string::npos;
+        if (ix && iy) bat += ch;
+        else if (ix) Mset += ch;
+        else Nset += ch;
       }
-    for (char ch : Lb)
-      if (Lc.find(ch) == std::string::npos && La.find(ch) == std::string::npos)
-        throw Fail{FTCC_ERR_STATE, "free letter in B"};
+      for (char ch : LX)
+        if (Lc.find(ch) == std::string::npos) Kset += ch;
+      const std::string Ml = (mask & 2) ? ordered(LX, Mset) : Mset;
+      const std::string Nl = (mask & 4) ? ordered(LY, Nset) : Nset;
+      const std::string Kl = (mask & 8) ? ordered(LY, Kset) : Kset;
+      const bool direct = anti_none && bat + Ml + Nl == Lc;
+      long long cost = direct ? 0 : 2 * csize;
+      if (!X.fixed && LX != bat + Ml + Kl) cost += 2 * size_of_letters(LX);
+      if (!Y.fixed && LY != bat + Nl + Kl) cost += 2 * size_of_letters(LY);
+      // the tensor-core tile is 128 rows high: a plan that puts fewer than 64
+      // rows on M while N has more would run on the SIMT kernel instead
+      if (gk != GEMM_F64 && size_of_letters(Mset) < 64 && size_of_letters(Nset) >= 64) cost += 4 * csize;
+      if (best.cost < 0 || cost < best.cost) best = Plan{swap, bat, Ml, Nl, Kl, direct, cost};
+    }
+    const Tn<const T>& GA = best.swap ? B : A;
+    const Tn<const T>& GB = best.swap ? A : B;
+    const std::string bat = best.bat, Ml = best.Ml, Nl = best.Nl, Kl = best.Kl;
     long long nb = 1, m = 1, n = 1, k = 1;
     for (char ch : bat) nb *= dimof(ch);
     for (char ch : Ml) m *= dimof(ch);
@@ -373,12 +473,12 @@ struct Solver {
     for (char ch : Kl) k *= dimof(ch);
     if (nb * m * n == 0) return;
     if (counting) gemm_flops += 2 * nb * m * n * k;
-    const bool tc = (gk != GEMM_F64) && m >= 128 && n >= 64 && k >= 16;
+    const bool tc = (gk != GEMM_F64) && m >= 64 && k >= 8;   // narrow N uses a narrow tile
     const int kind = tc ? gk : (gk == GEMM_F64 ? GEMM_F64 : -1);   // -1: FP32 SIMT
-    const Operand oa = operand(A, bat + Ml, Kl, k, kind, pA, pA2);
-    const Operand ob = operand(B, bat + Nl, Kl, k, kind, pB, pB2);
+    const Operand oa = operand(GA, bat + Ml, Kl, k, kind, pA, pA2);
+    const Operand ob = operand(GB, bat + Nl, Kl, k, kind, pB, pB2);
     const std::string Lt = bat + Ml + Nl;
-    const bool direct = (Lt == Lc) && anti[0] == 0;   // GEMM output is already C's layout
+    const bool direct = best.direct;   // GEMM output is already C's layout
     if (!direct) ensure(h_, Ct, nb * m * n * sizeof(T));
     GemmArgs g{};
     g.batch = static_cast<int>(nb);
@@ -398,14 +498,17 @@ struct Solver {
     g.sc = m * n;
     g.alpha = direct ? alpha : 1.0;
     g.beta = direct ? beta_acc : 0.0;
-    if (kind != GEMM_TF32 && kind != GEMM_BF16X3) {
-      ensure(h_, skw, 64u << 20);
-      g.work = skw.p;
-      g.work_bytes = skw.bytes;
-    }
-    if (kind == GEMM_F64) CU(gemm_f64(g, st()));
-    else if (kind == -1) CU(gemm_f32(g, st()));
-    else CU(gemm_tc(kind, g, h_->dev_err, st()));
+    ensure(h_, skw, 64u << 20);   // split-K partials (SIMT and tensor-core kernels)
+    g.work = skw.p;
+    g.work_bytes = skw.bytes;
+    const double es = kind == GEMM_BF16X3 ? 4.0 : static_cast<double>(sizeof(T));   // hi + lo halves
+    const double gbytes = static_cast<double>(nb) * ((m + n) * k * es + m * n * sizeof(T) * (g.beta != 0.0 ? 2 : 1));
+    const double gflops = 2.0 * nb * m * n * k;
+    timed_launch(kind == GEMM_TF32 || kind == GEMM_BF16X3 ? kClsGemmTc : kClsGemmSimt, gbytes, gflops, [&] {
+      if (kind == GEMM_F64) CU(gemm_f64(g, st()));
+      else if (kind == -1) CU(gemm_f32(g, st()));
+      else CU(gemm_tc(kind, g, h_->dev_err, st()));
+    });
     if (!direct) {
       const bool rec = recording;   // part of this contraction, not an op of its own
       recording = false;
@@ -443,7 +546,8 @@ struct Solver {
     auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
     auto CF = [this](const char* L) { return Tn<const T>{F(L), L, true}; };
     if (recording) tape.push_back(Op{2, ptt, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
-    CU(launch_tau<T>(t1c, t2c, ptt, pta, 0.5, 1.0, nz * nx, no, nv, st()));
+    timed_launch(kClsOther, 4.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
+                 [&] { CU(launch_tau<T>(t1c, t2c, ptt, pta, 0.5, 1.0, nz * nx, no, nv, st())); });
     // F_me = f_me + sum_nf s_n^f <mn||ef>
     scatter(pFme, "zxme", F("zme"), "zme", 1.0, 0.0, "");
     contract({pFme, "zxme"}, 1.0, CT{t1c, "zxnf"}, CV("zmnef"));
@@ -469,7 +573,8 @@ struct Solver {
     contract({pWmbej, "zxmbej"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
     contract({pWmbej, "zxmbej"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
     if (recording) tape.push_back(Op{3, pX, "", t1c, "", t2c, "", nullptr, 0.5, 1.0, ""});
-    CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st()));
+    timed_launch(kClsOther, 2.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
+                 [&] { CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st())); });
     contract({pWmbej, "zxmbej"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
     // S1 (Eq. ccS1)
     scatter(S1c, "zxia", F("zai"), "zai", 1.0, 0.0, "");
@@ -783,6 +888,7 @@ PropArgs prop_args(Batch& B, int nslot) {
 // One application of the fixed-point map to every tau point of every instance.
 template <class T>
 void iterate_once(Batch& B, Solver<T>& s) {
+  s.prof_next = 0;
   const long long o = s.no, v = s.nv;
   const long long n1 = o * v, n2 = o * o * v * v;
   for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {   // tau chunks only when nz == 1
@@ -796,14 +902,18 @@ void iterate_once(Batch& B, Solver<T>& s) {
   a.t1E = nullptr;
   a.partials = static_cast<double*>(s.part1.p);
   a.nblocks = s.nb1;
-  CU(launch_propagate<T>(static_cast<const T*>(s.S1.p), static_cast<T*>(s.t1.p), a, B.home->st));
+  const double b1 = static_cast<double>(B.nz) * s.ng * n1 * 3 * sizeof(T) + static_cast<double>(B.nz) * n1 * 8;
+  s.timed_launch(kClsPropagate, b1, 0.0,
+                 [&] { CU(launch_propagate<T>(static_cast<const T*>(s.S1.p), static_cast<T*>(s.t1.p), a, B.home->st)); });
   a = prop_args(B, 4);
   a.wE = static_cast<const double*>(B.V64.p);
   a.cE = 0.25;
   a.t1E = s.t1.p;
   a.partials = static_cast<double*>(s.part2.p);
   a.nblocks = s.nb2;
-  CU(launch_propagate<T>(static_cast<const T*>(s.S2.p), static_cast<T*>(s.t2.p), a, B.home->st));
+  const double b2 = static_cast<double>(B.nz) * s.ng * n2 * 3 * sizeof(T) + static_cast<double>(B.nz) * n2 * 8;
+  s.timed_launch(kClsPropagate, b2, 0.0,
+                 [&] { CU(launch_propagate<T>(static_cast<const T*>(s.S2.p), static_cast<T*>(s.t2.p), a, B.home->st)); });
   CU(launch_reduce(static_cast<const double*>(s.part1.p), s.nb1, static_cast<const double*>(s.part2.p), s.nb2, s.ng,
                    B.nz, static_cast<const double*>(B.hz.p), static_cast<const int*>(B.live.p),
                    static_cast<double*>(B.state.p), B.home->st));
@@ -839,9 +949,34 @@ void run_iterations(Batch& B, Solver<T>& s, int n) {
   }
 }
 
+template <class T>
+void collect_profile(Batch& B, Solver<T>& s) {
+  if (!s.profiling || s.prof_next == 0) return;
+  CU(cudaStreamSynchronize(B.home->st));
+  for (size_t i = 0; i < s.prof_next; ++i) {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, s.prof[i].e0, s.prof[i].e1));
+    const int c = s.prof[i].cls;
+    B.prof_ms[c] += ms;
+    B.prof_bytes[c] += s.prof[i].bytes;
+    B.prof_flops[c] += s.prof[i].flops;
+    B.prof_launches[c] += 1;
+  }
+}
+
 void run_batch(Batch& B, int n) {
-  if (B.active == 1) run_iterations<float>(B, *B.s32, n);
-  else run_iterations<double>(B, *B.s64, n);
+  // with kernel timing on, each iteration is replayed and read back on its own
+  const bool prof = B.active == 1 ? (B.s32 && B.s32->profiling) : (B.s64 && B.s64->profiling);
+  const int reps = prof ? n : 1, per = prof ? 1 : n;
+  for (int r = 0; r < reps; ++r) {
+    if (B.active == 1) {
+      run_iterations<float>(B, *B.s32, per);
+      collect_profile<float>(B, *B.s32);
+    } else {
+      run_iterations<double>(B, *B.s64, per);
+      collect_profile<double>(B, *B.s64);
+    }
+  }
   B.iterations += n;
 }
 
@@ -1881,6 +2016,47 @@ ftcc_status ftcc_get_lambda(ftcc_ctx* c, double* m1, double* m2) {
   });
 }
 
+ftcc_status ftcc_profile(ftcc_ctx* c, int enable) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (!c->batch) return fail(c, FTCC_ERR_STATE, "prepare or solve first");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    auto toggle = [&](auto* s) {
+      if (!s) return;
+      if (s->profiling != (enable != 0)) {
+        if (s->gexec) cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+        s->warm = false;   // the next iteration runs uncaptured, then a new graph with / without event nodes
+      }
+      s->profiling = enable != 0;
+    };
+    toggle(B.s32.get());
+    toggle(B.s64.get());
+    for (int k = 0; k < 8; ++k) {
+      B.prof_ms[k] = B.prof_bytes[k] = B.prof_flops[k] = 0;
+      B.prof_launches[k] = 0;
+    }
+    return FTCC_OK;
+  });
+}
+
+int ftcc_profile_read(ftcc_ctx* c, ftcc_kernel_stats* out, int max) {
+  if (!c || !c->batch || !out || max < 1) return 0;
+  Batch& B = *c->batch;
+  int n = 0;
+  for (int k = 0; k < kNumCls && n < max; ++k) {
+    if (B.prof_launches[k] == 0) continue;
+    ftcc_kernel_stats& r = out[n++];
+    memset(&r, 0, sizeof(r));
+    strncpy(r.name, kClsName[k], sizeof(r.name) - 1);
+    r.launches = B.prof_launches[k];
+    r.ms = B.prof_ms[k];
+    r.bytes = B.prof_bytes[k];
+    r.flops = B.prof_flops[k];
+  }
+  return n;
+}
+
 ftcc_status ftcc_gemm(ftcc_ctx* c, int precision, int batch, int M, int N, int K, double alpha, const void* A,
                       long long lda, long long sa, const void* B, long long ldb, long long sb, void* C, long long ldc,
                       long long sc) {
@@ -1908,6 +2084,19 @@ ftcc_status ftcc_gemm(ftcc_ctx* c, int precision, int batch, int M, int N, int K
     g.sc = sc;
     g.alpha = alpha;
     g.beta = 0.0;
+    // split-K partials when the output alone cannot fill the SMs
+    const size_t wbytes = std::min<size_t>(64u << 20, static_cast<size_t>(batch) * M * N * 8 * 32);
+    Buf w = c->get(wbytes);
+    g.work = w.p;
+    g.work_bytes = w.bytes;
+    struct Release {
+      ftcc_ctx* c;
+      Buf& b;
+      ~Release() {
+        cudaStreamSynchronize(c->st);
+        c->put(b);
+      }
+    } release{c, w};
     if (precision == FTCC_PREC_FP64) {
       CU(gemm_f64(g, c->st));
     } else if (precision == FTCC_PREC_TF32) {
@@ -1943,8 +2132,7 @@ ftcc_status ftcc_gemm(ftcc_ctx* c, int precision, int batch, int M, int N, int K
       g.A2 = al.p;
       g.B = bh.p;
       g.B2 = bl.p;
-      g.K = static_cast<int>(kp);
-      g.lda = kp;
+      g.lda = kp;   // K stays the true length: columns K..kp are never read
       g.ldb = kp;
       g.sa = sa > 0 ? M * kp : 0;
       g.sb = sb > 0 ? N * kp : 0;

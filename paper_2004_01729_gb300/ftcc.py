@@ -49,6 +49,11 @@ class AdjointResult(C.Structure):
                 ("S", C.c_double), ("trace_rdm1", C.c_double), ("iterations", C.c_int)]
 
 
+class KernelStats(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -93,6 +98,8 @@ _SIGS = [
     ("ftcc_gemm_f64_static", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                        C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p, C.c_longlong,
                                        C.c_longlong, C.c_void_p, C.c_longlong, C.c_longlong]),
+    ("ftcc_profile", C.c_int, [C.c_void_p, C.c_int]),
+    ("ftcc_profile_read", C.c_int, [C.c_void_p, C.POINTER(KernelStats), C.c_int]),
     ("ftcc_device_error", C.c_int, [C.c_void_p]),
 ]
 
@@ -342,6 +349,15 @@ class Context:
                                        Cm.data_ptr(), N, M * N), "ftcc_gemm")
         self._out(cur)
         return Cm
+
+    def profile(self, enable=True):
+        self._check(self.lib.ftcc_profile(self.h, 1 if enable else 0), "ftcc_profile")
+
+    def profile_read(self):
+        out = (KernelStats * 8)()
+        n = self.lib.ftcc_profile_read(self.h, out, 8)
+        return [{"name": out[i].name.decode(), "launches": out[i].launches, "ms": out[i].ms,
+                 "bytes": out[i].bytes, "flops": out[i].flops} for i in range(n)]
 
     def device_error(self):
         return self.lib.ftcc_device_error(self.h)

@@ -38,7 +38,10 @@ GEMM_TOL = {"fp64": 1e-13, "tf32": 4e-3, "bf16x3": 1e-4}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
-@pytest.mark.parametrize("shape", [(1, 128, 128, 32), (1, 200, 130, 68), (3, 257, 129, 36), (2, 640, 384, 520)])
+@pytest.mark.parametrize("shape", [(1, 128, 128, 32), (1, 200, 130, 68), (3, 257, 129, 36), (2, 640, 384, 520),
+                                   # narrow tiles (N <= 32 / 64) and split K (few output tiles, long K)
+                                   (1, 400, 20, 8000), (4, 160, 40, 1200), (2, 300, 64, 64), (1, 130, 100, 4100),
+                                   (1, 64, 17, 12)])
 def test_gemm_matches_torch(ctx, prec, shape):
     b, M, N, K = shape
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
@@ -193,3 +196,23 @@ def test_solve_hubbard10(ctx, k, prec):
     assert r["converged"]
     tol = 1e-8 if prec == "fp64" else 1e-6
     assert abs(r["omega"] - gold["omega"]) < tol, (r, gold["omega"])
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_kernel_profile_leaves_results_unchanged(ctx, graph):
+    """Per-kernel timing brackets launches with events (inside the graph when
+    one is used) and changes no number the iteration computes."""
+    c = wl.HUBBARD_6
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    ctx.prepare(c["beta"], c["mu"], c["ngrid"], precision="tf32", use_graph=graph)
+    plain = [ctx.iterate(1)["omega"] for _ in range(3)]
+    ctx.prepare(c["beta"], c["mu"], c["ngrid"], precision="tf32", use_graph=graph)
+    ctx.profile(True)
+    timed = [ctx.iterate(1)["omega"] for _ in range(3)]
+    stats = ctx.profile_read()
+    ctx.profile(False)
+    assert timed == plain
+    names = {s["name"] for s in stats}
+    assert {"gemm_tc_kernel", "propagate_kernel", "permute_kernel:scatter"} <= names, names
+    for s in stats:
+        assert s["launches"] > 0 and s["ms"] > 0.0
