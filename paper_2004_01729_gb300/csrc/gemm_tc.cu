@@ -165,7 +165,8 @@ struct TcCfg {
   static constexpr int kStages = (192 * 1024) / kStageBytes > 6 ? 6 : (192 * 1024) / kStageBytes;
   static constexpr int kKElems = KIND == GEMM_TF32 ? 32 : 64;                  // elements per 128-byte row
   static constexpr uint32_t kTmemCols = 2 * BN;                                // double-buffered accumulator
-  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr int kEpiBytes = 4 * 32 * 33 * 4;                           // epilogue staging
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + kEpiBytes;
 };
 
 constexpr int kGroupM = 8;   // tile raster: groups of 8 row tiles swept across all column tiles
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  float* epi = reinterpret_cast<float*>(smem + S * Cfg::kStageBytes + 256);   // 4 x 32 x 33 staging
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -325,38 +327,48 @@ __global__ void __launch_bounds__(192, 1)
       fence_after_sync();
       int sp, b, m0, n0;
       decode(t, sp, b, m0, n0);
-      const int row = m0 + q * 32 + lane;
       const bool part = splits > 1;   // split-K partial: dense [split][batch][M][N] in W, no beta
-      float* crow = part ? W + ((static_cast<long long>(sp) * batch + b) * M + row) * static_cast<long long>(N)
-                         : C + static_cast<long long>(b) * sc + static_cast<long long>(row) * ldc;
+      float* cbase = part ? W + (static_cast<long long>(sp) * batch + b) * M * static_cast<long long>(N)
+                          : C + static_cast<long long>(b) * sc;
+      const long long ldo = part ? N : ldc;
       const float bta = part ? 0.0f : beta;
+      float* stg = epi + q * (32 * 33);   // this warp's 32 x 32 staging block, row stride 33
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + static_cast<uint32_t>(c), r);
-        if (row < M) {
-          const int cb = n0 + c;
-          if (cb + 32 <= N && (reinterpret_cast<uintptr_t>(crow + cb) & 15) == 0 && bta == 0.0f) {
-            float4* dst = reinterpret_cast<float4*>(crow + cb);
+        if (c + 32 >= BN) {   // accumulator drained: the MMA warp may reuse it
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+        if (n0 + c >= N) continue;
+        // transpose through shared memory: thread = row while staging,
+        // lane = column while storing, so every store (and the beta load) is
+        // one contiguous 128-byte row segment
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              dst[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
-                                   alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int col = n0 + c + lane;
+        const int nrow = min(32, M - (m0 + q * 32));
+        float* p0 = cbase + static_cast<long long>(m0 + q * 32) * ldo + col;
+        if (col < N) {
+          if (bta == 0.0f) {
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr)
+              if (rr < nrow) p0[rr * ldo] = alpha * stg[rr * 33 + lane];
           } else {
+            // all 32 loads of the old values in flight before the first store
+            float old[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = cb + j;
-              if (col < N) {
-                const float v = alpha * __uint_as_float(r[j]);
-                crow[col] = (bta == 0.0f) ? v : v + bta * crow[col];
-              }
-            }
+            for (int rr = 0; rr < 32; ++rr) old[rr] = rr < nrow ? p0[rr * ldo] : 0.0f;
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+              if (rr < nrow) p0[rr * ldo] = alpha * stg[rr * 33 + lane] + bta * old[rr];
           }
         }
+        __syncwarp();
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
     }
   }
   fence_before_sync();

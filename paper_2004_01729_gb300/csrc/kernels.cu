@@ -66,22 +66,22 @@ struct PermOut {
 
 // Rows of one order: every tile element is (row, f) with f the coordinate of
 // the order's fastest letter.  A row table (global offset, tile index) is
-// built in shared memory, then a warp covers 32 / ext_f rows per pass with
-// lane = (row within the pass, f): one table lookup and two multiply-adds per
-// element.
-template <int O, class F>
+// built in shared memory; the elements e = row * ext_f + f of up to
+// kPermRows rows are then spread over the block's threads (consecutive
+// threads on consecutive f), kPermUnroll of them per thread with all loads
+// issued before any is used: load(g, t) -> value, then apply(g, t, value).
+constexpr int kPermUnroll = 4;
+
+template <int O, class V, class L, class A>
 __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, int n, long long* rowG, int* rowT,
-                                          F&& body) {
+                                          L&& load, A&& apply) {
   const int sl0 = d.slot[O][0];
-  const int ef = ((tailmask >> sl0) & 1u) ? d.ext_tail[sl0] : d.ext_full[sl0];
+  const bool tail0 = (tailmask >> sl0) & 1u;
+  const FastDiv fe = tail0 ? d.fd_tail[O][0] : d.fd_full[O][0];
+  const int ef = static_cast<int>(fe.d);
   const long long gf = d.gstr[O][0];
   const int tf = d.tstr[O][0];
   const int nrows = n / ef;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kWarps = kPermThreads / 32;
-  const int per = ef <= 32 ? 32 / ef : 1;
-  const int sub = ef <= 32 ? lane / ef : 0;
-  const int co0 = ef <= 32 ? lane - sub * ef : lane;
   for (int r0 = 0; r0 < nrows; r0 += kPermRows) {
     const int nr = min(kPermRows, nrows - r0);
     for (int r = threadIdx.x; r < nr; r += kPermThreads) {
@@ -103,9 +103,25 @@ __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, i
       rowT[r] = t;
     }
     __syncthreads();
-    if (sub < per) {
-      for (int r = warp * per + sub; r < nr; r += kWarps * per)
-        for (int co = co0; co < ef; co += 32) body(rowG[r] + co * gf, rowT[r] + co * tf);
+    const int ne = nr * ef;
+    for (int e0 = threadIdx.x; e0 < ne; e0 += kPermThreads * kPermUnroll) {
+      V v[kPermUnroll];
+      long long gg[kPermUnroll];
+      int tt[kPermUnroll];
+#pragma unroll
+      for (int u = 0; u < kPermUnroll; ++u) {
+        const int e = e0 + u * kPermThreads;
+        if (e < ne) {
+          const uint32_t q = fdiv(fe, static_cast<uint32_t>(e));
+          const int co = e - static_cast<int>(q) * ef;
+          gg[u] = rowG[q] + co * gf;
+          tt[u] = rowT[q] + co * tf;
+          v[u] = load(gg[u], tt[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPermUnroll; ++u)
+        if (e0 + u * kPermThreads < ne) apply(gg[u], tt[u], v[u]);
     }
     __syncthreads();
   }
@@ -121,16 +137,17 @@ __device__ __forceinline__ void perm_term(const DevPerm& d, const long long* c, 
   for (int k = 0; k < kMaxL; ++k)
     if (k < d.nd) base += c[k] * d.sst[P][k];
   const T* sp = src + base;
+  auto load = [&](long long g, int) { return sp[g]; };
   if (P == 0) {
-    perm_rows<0>(d, tailmask, n, rowG, rowT, [&](long long g, int t) { tile[t] = sp[g]; });
+    perm_rows<0, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] = v; });
   } else {
     const T sg = static_cast<T>(d.sign[P]);
-    perm_rows<P>(d, tailmask, n, rowG, rowT, [&](long long g, int t) { tile[t] += sg * sp[g]; });
+    perm_rows<P, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] += sg * v; });
   }
 }
 
 template <class T, bool SPLIT>
-__global__ void __launch_bounds__(kPermThreads) permute_kernel(const T* __restrict__ src, PermOut<T> out, DevPerm d,
+__global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(const T* __restrict__ src, PermOut<T> out, DevPerm d,
                                                                T alpha, T beta) {
   extern __shared__ __align__(16) unsigned char perm_smem[];
   T* tile = reinterpret_cast<T*>(perm_smem);
@@ -170,18 +187,23 @@ __global__ void __launch_bounds__(kPermThreads) permute_kernel(const T* __restri
   if constexpr (SPLIT) {
     __nv_bfloat16* hi = out.hi + dbase;
     __nv_bfloat16* lo = out.lo + dbase;
-    perm_rows<4>(d, tailmask, n, rowG, rowT, [&](long long g, int t) {
-      const float v = static_cast<float>(tile[t]);
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      hi[g] = h;
-      lo[g] = __float2bfloat16_rn(v - __bfloat162float(h));
-    });
+    perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
+                    [&](long long g, int, T tv) {
+                      const float v = static_cast<float>(tv);
+                      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                      hi[g] = h;
+                      lo[g] = __float2bfloat16_rn(v - __bfloat162float(h));
+                    });
   } else {
     T* dp = out.dst + dbase;
-    perm_rows<4>(d, tailmask, n, rowG, rowT, [&](long long g, int t) {
-      const T v = alpha * tile[t];
-      dp[g] = (beta == T(0)) ? v : beta * dp[g] + v;
-    });
+    if (beta == T(0)) {
+      perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
+                      [&](long long g, int, T v) { dp[g] = alpha * v; });
+    } else {
+      // the destination values are the loads; the tile is read at the store
+      perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long g, int) { return dp[g]; },
+                      [&](long long g, int t, T old) { dp[g] = beta * old + alpha * tile[t]; });
+    }
   }
 }
 
@@ -927,12 +949,46 @@ struct PermPlan {
 };
 
 template <class T, bool SPLIT>
-cudaError_t run_permute(const PermPlan& P, const T* src, PermOut<T> out, double alpha, double beta, cudaStream_t st) {
-  const int nd = P.nd;
-  if (nd < 1 || nd > kMaxL) return cudaErrorInvalidValue;
+cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double alpha, double beta, cudaStream_t st) {
+  if (P0.nd < 1 || P0.nd > kMaxL) return cudaErrorInvalidValue;
   long long total = 1;
-  for (int k = 0; k < nd; ++k) total *= P.dim[k];
+  for (int k = 0; k < P0.nd; ++k) total *= P0.dim[k];
   if (total == 0) return cudaSuccess;
+  // Drop letters of extent 1 and merge neighbouring destination letters that
+  // are neighbours in the same order in every term's source: fewer, longer
+  // letters mean longer contiguous runs and less index arithmetic.
+  PermPlan P;
+  P.nterm = P0.nterm;
+  for (int k = P0.nd - 1; k >= 0; --k) {   // innermost first; P is built reversed
+    if (P0.dim[k] == 1) continue;
+    bool merge = P.nd > 0;
+    if (merge) {
+      const int g = P.nd - 1;
+      merge = P0.dstr[k] == P.dstr[g] * P.dim[g];
+      for (int p = 0; p < P0.nterm && merge; ++p) merge = P0.sst[p][k] == P.sst[p][g] * P.dim[g];
+      if (merge && P.dim[g] * P0.dim[k] >= (1LL << 31)) merge = false;
+      if (merge) {
+        P.dim[g] *= P0.dim[k];
+        continue;
+      }
+    }
+    P.dim[P.nd] = P0.dim[k];
+    P.dstr[P.nd] = P0.dstr[k];
+    for (int p = 0; p < P0.nterm; ++p) P.sst[p][P.nd] = P0.sst[p][k];
+    ++P.nd;
+  }
+  if (P.nd == 0) {   // a single element
+    P.nd = 1;
+    P.dim[0] = 1;
+    P.dstr[0] = 1;
+    for (int p = 0; p < P0.nterm; ++p) P.sst[p][0] = 0;
+  }
+  for (int a = 0, b = P.nd - 1; a < b; ++a, --b) {   // back to outermost first
+    std::swap(P.dim[a], P.dim[b]);
+    std::swap(P.dstr[a], P.dstr[b]);
+    for (int p = 0; p < P.nterm; ++p) std::swap(P.sst[p][a], P.sst[p][b]);
+  }
+  const int nd = P.nd;
   // tile letters: dst innermost, then each term's unit-stride letter
   auto argmin = [&](const long long* st_) {
     int best = -1;
@@ -963,7 +1019,9 @@ cudaError_t run_permute(const PermPlan& P, const T* src, PermOut<T> out, double 
       if (ext[l] > ext[w]) w = l;
     ext[w] = (ext[w] + 1) / 2;
   }
-  // grow with whole destination letters, innermost first
+  // grow with destination letters, innermost first: whole letters while they
+  // fit, then a part of the next one (long contiguous destination runs and
+  // enough work per block to hide the phase latencies)
   {
     int order[kMaxL];
     for (int k = 0; k < nd; ++k) order[k] = k;
@@ -973,10 +1031,12 @@ cudaError_t run_permute(const PermPlan& P, const T* src, PermOut<T> out, double 
       bool in = false;
       for (int l = 0; l < nt; ++l) in |= tl[l] == k;
       if (in || P.dim[k] <= 1) continue;
-      if (prod() * P.dim[k] > kPermTile) continue;
+      const long long room = kPermTile / prod();
+      if (room < 2) break;
       tl[nt] = k;
-      ext[nt] = P.dim[k];
+      ext[nt] = std::min<long long>(P.dim[k], room);
       ++nt;
+      if (ext[nt - 1] < P.dim[k]) break;
     }
   }
   DevPerm d{};
