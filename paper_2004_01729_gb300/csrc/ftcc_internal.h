@@ -42,6 +42,7 @@ struct GemmArgs {
   const void* A2; const void* B2;     // low halves for BF16X3 (bf16 arrays)
   void* C; long long ldc, sc;
   double alpha, beta;
+  int trans;                          // 1: C stored transposed, element (m, n) at C[b*sc + n*ldc + m]
 };
 // Tensor-core GEMM (tcgen05 + TMA).  kind TF32: A, B, C float.  kind BF16X3:
 // A, A2, B, B2 __nv_bfloat16 (hi, lo), C float.  Returns cudaSuccess or an error.
@@ -96,6 +97,16 @@ struct ScatDesc {
   long long total;
 };
 
+// dst (dense, nd letters of extents dim) = beta * dst + sum_p coef_p * src_p[sum_k c_k sst_p[k]]:
+// up to nine source terms (each a tensor read in its own letter order, a
+// stride of 0 broadcasting), one pass, shared-memory tiles.
+struct CombTerm {
+  const void* src;
+  long long sst[kMaxL];
+  double coef;
+};
+template <class T> cudaError_t launch_combine(T* dst, int nd, const long long* dim, const CombTerm* terms, int nterm,
+                                              double beta, cudaStream_t st);
 template <class T> cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st);
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st);
 template <class T> cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha,

@@ -1,6 +1,7 @@
 // SIMT GEMM for the FP64 path (GB300 has no FP64 tensor-core MMA in tcgen05)
 // and for FP32 contractions too thin for a 128 x 128 tensor-core tile.
 //   C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] + beta * C[b][m][n]
+// (with trans, C[b][n][m]: the output stored transposed)
 // 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K
 // staged 16 at a time through shared memory (stored k-major so that the
 // inner loop reads broadcast rows).
@@ -21,7 +22,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const T* __restrict__ A,
                                                         const T* __restrict__ B, long long ldb, long long sb,
                                                         T* __restrict__ C, long long ldc, long long sc, int M,
                                                         int N, int K, T alpha, T beta, int splits, int kchunk,
-                                                        T* __restrict__ W, int batch) {
+                                                        T* __restrict__ W, int batch, int trans) {
   __shared__ T As[kK][kT + 1];
   __shared__ T Bs[kK][kT + 1];
   const int bz = blockIdx.z / splits;
@@ -30,12 +31,17 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const T* __restrict__ A,
   const int kend = min(K, kbeg + kchunk);
   A += static_cast<long long>(bz) * sa;
   B += static_cast<long long>(bz) * sb;
+  long long csm = ldc, csn = 1;   // element strides of C along m and n
   if (splits > 1) {
     C = W + (static_cast<long long>(sp) * batch + bz) * M * static_cast<long long>(N);
-    ldc = N;
+    csm = N;
     beta = T(0);
   } else {
     C += static_cast<long long>(bz) * sc;
+    if (trans) {
+      csm = 1;
+      csn = ldc;
+    }
   }
   const int m0 = blockIdx.y * kT;
   const int n0 = blockIdx.x * kT;
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const T* __restrict__ A,
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx * 4 + j;
       if (gn >= N) continue;
-      T* c = C + static_cast<long long>(gm) * ldc + gn;
+      T* c = C + static_cast<long long>(gm) * csm + static_cast<long long>(gn) * csn;
       const T v = alpha * acc[i][j];
       *c = (beta == T(0)) ? v : v + beta * *c;
     }
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const T* __restrict__ A,
 
 template <class T>
 __global__ void splitk_reduce_kernel(const T* __restrict__ W, T* __restrict__ C, long long ldc, long long sc, int M,
-                                     int N, int batch, int splits, T beta) {
+                                     int N, int batch, int splits, T beta, int trans) {
   const long long mn = static_cast<long long>(M) * N;
   const long long total = mn * batch;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -99,7 +105,7 @@ __global__ void splitk_reduce_kernel(const T* __restrict__ W, T* __restrict__ C,
     const long long m = r / N, n = r - m * N;
     T acc = T(0);
     for (int s = 0; s < splits; ++s) acc += W[static_cast<long long>(s) * total + e];
-    T* c = C + b * sc + m * ldc + n;
+    T* c = C + b * sc + (trans ? n * ldc + m : m * ldc + n);
     *c = (beta == T(0)) ? acc : acc + beta * *c;
   }
 }
@@ -125,12 +131,12 @@ cudaError_t launch(const GemmArgs& g, cudaStream_t st) {
   gemm_simt_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(g.A), g.lda, g.sa, static_cast<const T*>(g.B),
                                             g.ldb, g.sb, static_cast<T*>(g.C), g.ldc, g.sc, g.M, g.N, g.K,
                                             static_cast<T>(g.alpha), static_cast<T>(g.beta), splits, kchunk,
-                                            static_cast<T*>(g.work), g.batch);
+                                            static_cast<T*>(g.work), g.batch, g.trans);
   if (splits > 1) {
     const long long total = outer;
     int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152 * 8));
     splitk_reduce_kernel<T><<<blocks, 256, 0, st>>>(static_cast<const T*>(g.work), static_cast<T*>(g.C), g.ldc, g.sc,
-                                                    g.M, g.N, g.batch, splits, static_cast<T>(g.beta));
+                                                    g.M, g.N, g.batch, splits, static_cast<T>(g.beta), g.trans);
   }
   return cudaGetLastError();
 }

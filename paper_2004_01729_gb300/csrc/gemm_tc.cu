@@ -2,16 +2,17 @@
 // staged by TMA (cp.async.bulk.tensor) into 128-byte-swizzled shared memory.
 //
 //   C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k] (+ beta * C)
+//   (or stored transposed, C[b][n][m], when the caller asks for it)
 //
 // Both operands are K-major ("TN"), which is the layout every contraction of
 // the FT-CCSD S kernel is packed into.  Persistent CTAs (one per SM) walk
-// 128 x BN output tiles (BN = 256, or 128 for narrow outputs):
+// 128 x BN output tiles (BN = 32, 64, 128 or 256, the narrowest covering N):
 //   warp 0 / lane 0   TMA producer (multi-stage ring of shared-memory stages)
 //   warp 1            TMEM allocation (2 x BN columns), MMA issuer (one thread,
 //                     tcgen05.mma kind::tf32 or kind::f16)
-//   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store,
-//                     overlapping the next tile's main loop (double-buffered
-//                     accumulator)
+//   warps 2-9         epilogue: tcgen05.ld 32 lanes x 32 columns, scale, store
+//                     through a shared-memory transpose, overlapping the next
+//                     tile's main loop (double-buffered accumulator)
 // BF16X3 keeps a two-way bf16 split of each operand (x = hi + lo) and issues
 // hi*hi + hi*lo + lo*hi into the same FP32 accumulator.
 //
@@ -156,6 +157,9 @@ __host__ __device__ constexpr uint32_t instr_desc_n(uint32_t fmt, uint32_t bn) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((bn >> 3) << 17) | ((uint32_t(kBM) >> 4) << 24);
 }
 
+constexpr int kEpiWarps = 8;   // two epilogue warps per TMEM lane quadrant, one per column half
+constexpr int kGemmThreads = 32 * (2 + kEpiWarps);
+
 template <int KIND, int BN>
 struct TcCfg {
   static constexpr int kOps = KIND == GEMM_TF32 ? 1 : 2;                       // hi (and lo) halves
@@ -165,25 +169,26 @@ struct TcCfg {
   static constexpr int kStages = (192 * 1024) / kStageBytes > 6 ? 6 : (192 * 1024) / kStageBytes;
   static constexpr int kKElems = KIND == GEMM_TF32 ? 32 : 64;                  // elements per 128-byte row
   static constexpr uint32_t kTmemCols = 2 * BN;                                // double-buffered accumulator
-  static constexpr int kEpiBytes = 4 * 32 * 33 * 4;                           // epilogue staging
+  static constexpr int kEpiBytes = kEpiWarps * 32 * 33 * 4;                   // epilogue staging
   static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + kEpiBytes;
 };
 
 constexpr int kGroupM = 8;   // tile raster: groups of 8 row tiles swept across all column tiles
 
-// Persistent warp-specialised GEMM.  CTA = 6 warps:
+// Persistent warp-specialised GEMM.  CTA = 10 warps:
 //   warp 0        TMA producer over a ring of kStages shared-memory stages
 //   warp 1        TMEM owner and MMA issuer (one thread), two accumulators
-//   warps 2..5    epilogue; warp w drains TMEM lanes 32 (w % 4) .. + 31
+//   warps 2..9    epilogue; warp w drains TMEM lanes 32 (w % 4) .. + 31 of
+//                 column half (w - 2) / 4 of the tile (all columns when BN = 32)
 // Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; the accumulator of tile
 // i is buffer i % 2, so tile i's epilogue overlaps tile i+1's main loop.
 template <int KIND, int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2,
                    float* __restrict__ C, int M, int N, int K, long long ldc, long long sc, int a_batched,
                    int b_batched, float alpha, float beta, int batch, int splits, int kc, float* __restrict__ W,
-                   int* err) {
+                   int trans, int* err) {
   using Cfg = TcCfg<KIND, BN>;
   constexpr int S = Cfg::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&tempty[a], kEpiWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -318,7 +323,11 @@ __global__ void __launch_bounds__(192, 1)
     __syncwarp();
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
-    const int q = warp & 3;
+    const int q = warp & 3;                                  // TMEM lane quadrant of this warp
+    const int half = (warp - 2) >> 2;                        // column half of the tile
+    constexpr int kHalf = BN >= 64 ? BN / 2 : BN;            // columns per epilogue warp
+    const int c_lo = BN >= 64 ? half * kHalf : 0;
+    const bool idle = BN < 64 && half == 1;                  // narrow tiles: one warp per quadrant
     uint32_t local = 0;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
       const uint32_t acc = local & 1u, use = local >> 1;
@@ -332,17 +341,44 @@ __global__ void __launch_bounds__(192, 1)
                           : C + static_cast<long long>(b) * sc;
       const long long ldo = part ? N : ldc;
       const float bta = part ? 0.0f : beta;
-      float* stg = epi + q * (32 * 33);   // this warp's 32 x 32 staging block, row stride 33
+      float* stg = epi + (warp - 2) * (32 * 33);   // this warp's 32 x 32 staging block, row stride 33
+      if (idle) {
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        continue;
+      }
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = c_lo; c < c_lo + kHalf; c += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + static_cast<uint32_t>(c), r);
-        if (c + 32 >= BN) {   // accumulator drained: the MMA warp may reuse it
+        if (c + 32 >= c_lo + kHalf) {   // this warp's part drained: the MMA warp may reuse it
           fence_before_sync();
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[acc]);
         }
         if (n0 + c >= N) continue;
+        if (trans && !part) {
+          // C stored transposed: lanes are rows m, contiguous in memory
+          const int row = m0 + q * 32 + lane;
+          float* pc = cbase + row;
+          const int ncol = min(32, N - (n0 + c));
+          if (row < M) {
+            if (bta == 0.0f) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < ncol) pc[static_cast<long long>(n0 + c + j) * ldc] = alpha * __uint_as_float(r[j]);
+            } else {
+              float old[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) old[j] = j < ncol ? pc[static_cast<long long>(n0 + c + j) * ldc] : 0.0f;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < ncol) pc[static_cast<long long>(n0 + c + j) * ldc] = alpha * __uint_as_float(r[j]) + bta * old[j];
+            }
+          }
+          continue;
+        }
         // transpose through shared memory: thread = row while staging,
         // lane = column while storing, so every store (and the beta load) is
         // one contiguous 128-byte row segment
@@ -380,7 +416,7 @@ __global__ void __launch_bounds__(192, 1)
 
 // C[b][m][n] = sum_s W[s][b][m][n] (+ beta C): the split-K reduction, fixed order.
 __global__ void tc_splitk_reduce(const float* __restrict__ W, float* __restrict__ C, long long ldc, long long sc, int M,
-                                 int N, int batch, int splits, float beta) {
+                                 int N, int batch, int splits, float beta, int trans) {
   const long long mn = static_cast<long long>(M) * N;
   const long long total = mn * batch;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -390,7 +426,7 @@ __global__ void tc_splitk_reduce(const float* __restrict__ W, float* __restrict_
     const long long m = r / N, n = r - m * N;
     float acc = 0.0f;
     for (int s = 0; s < splits; ++s) acc += W[static_cast<long long>(s) * total + e];
-    float* c = C + b * sc + m * ldc + n;
+    float* c = C + b * sc + (trans ? n * ldc + m : m * ldc + n);
     *c = (beta == 0.0f) ? acc : acc + beta * *c;
   }
 }
@@ -467,14 +503,14 @@ cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
   const int kc = (nk + splits - 1) / splits;
   splits = (nk + kc - 1) / kc;
   const int grid = static_cast<int>(std::min<long long>(tiles * splits, sms));
-  gemm_tc_kernel<KIND, BN><<<grid, 192, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K, g.ldc,
+  gemm_tc_kernel<KIND, BN><<<grid, kGemmThreads, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K, g.ldc,
                                                     g.sc, g.sa > 0 ? 1 : 0, g.sb > 0 ? 1 : 0,
                                                     static_cast<float>(g.alpha), static_cast<float>(g.beta), g.batch,
-                                                    splits, kc, static_cast<float*>(g.work), dev_err);
+                                                    splits, kc, static_cast<float*>(g.work), g.trans, dev_err);
   if (splits > 1) {
     const int blocks = static_cast<int>(std::min<long long>((outer + 255) / 256, 152LL * 8));
     tc_splitk_reduce<<<blocks, 256, 0, st>>>(static_cast<const float*>(g.work), static_cast<float*>(g.C), g.ldc, g.sc,
-                                             g.M, g.N, g.batch, splits, static_cast<float>(g.beta));
+                                             g.M, g.N, g.batch, splits, static_cast<float>(g.beta), g.trans);
   }
   return cudaGetLastError();
 }

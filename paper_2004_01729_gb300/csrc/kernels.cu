@@ -39,21 +39,24 @@ constexpr int kPermThreads = 256;
 constexpr int kPermTile = 4096;   // elements of one tile in shared memory
 constexpr int kPermRows = 512;    // rows per pass of the shared row table
 
+constexpr int kPermTerms = 9;     // source terms of one launch (the write is order kPermTerms)
+
 struct DevPerm {
   int nd, nterm, nt;
   FastDiv bcnt[kMaxL];             // blocks along dst letter k
   int bstep[kMaxL];                // coordinate step per block along k (1, or the tile extent)
   int tslot[kMaxL];                // tile-letter slot of dst letter k, -1 if not a tile letter
-  long long sst[4][kMaxL];         // term p: source stride of dst letter k (swaps applied)
+  const void* src[kPermTerms];     // term p: source tensor
+  double coef[kPermTerms];         // term p: coefficient (sign of the antisymmetriser included)
+  long long sst[kPermTerms][kMaxL];   // term p: source stride of dst letter k (swaps applied)
   long long dstr[kMaxL];           // destination stride of dst letter k
-  // per order o (terms 0..3, write = 4), position l (fastest first):
-  FastDiv fd_full[5][kMaxL], fd_tail[5][kMaxL];   // extent of that tile letter in an inner / last block
-  int slot[5][kMaxL];              // tile-letter slot at that position
-  long long gstr[5][kMaxL];        // global stride at that position (source for terms, dst for write)
-  int tstr[5][kMaxL];              // shared-memory stride at that position
+  // per order o (terms 0..kPermTerms-1, the write = kPermTerms), position l (fastest first):
+  FastDiv fd_full[kPermTerms + 1][kMaxL], fd_tail[kPermTerms + 1][kMaxL];   // extent in an inner / last block
+  int slot[kPermTerms + 1][kMaxL];        // tile-letter slot at that position
+  long long gstr[kPermTerms + 1][kMaxL];  // global stride at that position (source for terms, dst for write)
+  int tstr[kPermTerms + 1][kMaxL];        // shared-memory stride at that position
   int tail_blk[kMaxL];             // per tile slot: block coordinate of the last (tail) block
   int ext_full[kMaxL], ext_tail[kMaxL];
-  float sign[4];
   uint32_t block0;
 };
 
@@ -129,25 +132,27 @@ __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, i
 
 // Term P of the antisymmetriser into the tile (term 0 stores, the others add
 // with their sign).
+// Term P into the tile: term 0 stores, the others add, each scaled by its
+// coefficient.
 template <int P, class T>
 __device__ __forceinline__ void perm_term(const DevPerm& d, const long long* c, uint32_t tailmask, int n,
-                                          long long* rowG, int* rowT, const T* __restrict__ src, T* tile) {
+                                          long long* rowG, int* rowT, T* tile) {
   long long base = 0;
 #pragma unroll
   for (int k = 0; k < kMaxL; ++k)
     if (k < d.nd) base += c[k] * d.sst[P][k];
-  const T* sp = src + base;
+  const T* sp = static_cast<const T*>(d.src[P]) + base;
+  const T cf = static_cast<T>(d.coef[P]);
   auto load = [&](long long g, int) { return sp[g]; };
   if (P == 0) {
-    perm_rows<0, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] = v; });
+    perm_rows<0, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] = cf * v; });
   } else {
-    const T sg = static_cast<T>(d.sign[P]);
-    perm_rows<P, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] += sg * v; });
+    perm_rows<P, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] += cf * v; });
   }
 }
 
 template <class T, bool SPLIT>
-__global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(const T* __restrict__ src, PermOut<T> out, DevPerm d,
+__global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out, const __grid_constant__ DevPerm d,
                                                                T alpha, T beta) {
   extern __shared__ __align__(16) unsigned char perm_smem[];
   T* tile = reinterpret_cast<T*>(perm_smem);
@@ -175,10 +180,15 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(const T* __res
     }
   }
   // terms: gather into the tile, each in its own letter order
-  perm_term<0>(d, c, tailmask, n, rowG, rowT, src, tile);
-  if (d.nterm > 1) perm_term<1>(d, c, tailmask, n, rowG, rowT, src, tile);
-  if (d.nterm > 2) perm_term<2>(d, c, tailmask, n, rowG, rowT, src, tile);
-  if (d.nterm > 3) perm_term<3>(d, c, tailmask, n, rowG, rowT, src, tile);
+  perm_term<0>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 1) perm_term<1>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 2) perm_term<2>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 3) perm_term<3>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 4) perm_term<4>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 5) perm_term<5>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 6) perm_term<6>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 7) perm_term<7>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 8) perm_term<8>(d, c, tailmask, n, rowG, rowT, tile);
   // write in destination order
   long long dbase = 0;
 #pragma unroll
@@ -187,7 +197,7 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(const T* __res
   if constexpr (SPLIT) {
     __nv_bfloat16* hi = out.hi + dbase;
     __nv_bfloat16* lo = out.lo + dbase;
-    perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
+    perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
                     [&](long long g, int, T tv) {
                       const float v = static_cast<float>(tv);
                       const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -197,11 +207,11 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(const T* __res
   } else {
     T* dp = out.dst + dbase;
     if (beta == T(0)) {
-      perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
+      perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
                       [&](long long g, int, T v) { dp[g] = alpha * v; });
     } else {
       // the destination values are the loads; the tile is read at the store
-      perm_rows<4, T>(d, tailmask, n, rowG, rowT, [&](long long g, int) { return dp[g]; },
+      perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long g, int) { return dp[g]; },
                       [&](long long g, int t, T old) { dp[g] = beta * old + alpha * tile[t]; });
     }
   }
@@ -945,12 +955,14 @@ namespace {
 // the per-term read orders and the block decomposition.
 struct PermPlan {
   int nd = 0, nterm = 1;
-  long long dim[kMaxL] = {}, sst[4][kMaxL] = {}, dstr[kMaxL] = {};
+  long long dim[kMaxL] = {}, sst[kPermTerms][kMaxL] = {}, dstr[kMaxL] = {};
+  const void* src[kPermTerms] = {};
+  double coef[kPermTerms] = {};
 };
 
 template <class T, bool SPLIT>
-cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double alpha, double beta, cudaStream_t st) {
-  if (P0.nd < 1 || P0.nd > kMaxL) return cudaErrorInvalidValue;
+cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double beta, cudaStream_t st) {
+  if (P0.nd < 1 || P0.nd > kMaxL || P0.nterm < 1 || P0.nterm > kPermTerms) return cudaErrorInvalidValue;
   long long total = 1;
   for (int k = 0; k < P0.nd; ++k) total *= P0.dim[k];
   if (total == 0) return cudaSuccess;
@@ -959,6 +971,10 @@ cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double
   // letters mean longer contiguous runs and less index arithmetic.
   PermPlan P;
   P.nterm = P0.nterm;
+  for (int p = 0; p < P0.nterm; ++p) {
+    P.src[p] = P0.src[p];
+    P.coef[p] = P0.coef[p];
+  }
   for (int k = P0.nd - 1; k >= 0; --k) {   // innermost first; P is built reversed
     if (P0.dim[k] == 1) continue;
     bool merge = P.nd > 0;
@@ -1004,7 +1020,11 @@ cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double
     tl[nt++] = k;
   };
   add(argmin(P.dstr));
-  for (int p = 0; p < P.nterm; ++p) add(argmin(P.sst[p]));
+  for (int p = 0; p < P.nterm; ++p) {
+    bool bcast = false;   // a broadcast source is small and read from cache
+    for (int k = 0; k < nd; ++k) bcast |= P.dim[k] > 1 && P.sst[p][k] == 0;
+    if (!bcast) add(argmin(P.sst[p]));
+  }
   if (nt == 0) add(nd - 1);
   long long ext[kMaxL];
   for (int l = 0; l < nt; ++l) ext[l] = P.dim[tl[l]];
@@ -1043,8 +1063,10 @@ cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double
   d.nd = nd;
   d.nterm = P.nterm;
   d.nt = nt;
-  const float signs[4] = {1.0f, -1.0f, -1.0f, 1.0f};
-  for (int p = 0; p < 4; ++p) d.sign[p] = signs[p];
+  for (int p = 0; p < P.nterm; ++p) {
+    d.src[p] = P.src[p];
+    d.coef[p] = P.coef[p];
+  }
   for (int k = 0; k < nd; ++k) {
     d.tslot[k] = -1;
     d.dstr[k] = P.dstr[k];
@@ -1109,20 +1131,22 @@ cudaError_t run_permute(const PermPlan& P0, const T* src, PermOut<T> out, double
     });
     fill(p, ord, P.sst[p]);
   }
-  fill(4, word, P.dstr);
+  fill(kPermTerms, word, P.dstr);
   const size_t smem = static_cast<size_t>(tile_elems) * sizeof(T);
   for (unsigned long long b0 = 0; b0 < nblocks; b0 += 0x7FFFFFFFull) {
     d.block0 = static_cast<uint32_t>(b0);
     const unsigned int g = static_cast<unsigned int>(std::min<unsigned long long>(nblocks - b0, 0x7FFFFFFFull));
-    permute_kernel<T, SPLIT><<<g, kPermThreads, smem, st>>>(src, out, d, static_cast<T>(alpha), static_cast<T>(beta));
+    permute_kernel<T, SPLIT><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
   }
   return cudaGetLastError();
 }
 
-PermPlan pack_plan(const PackDesc& d) {
+PermPlan pack_plan(const void* src, const PackDesc& d) {
   PermPlan P;
   P.nd = d.nr + d.nc;
   P.nterm = 1;
+  P.src[0] = src;
+  P.coef[0] = 1.0;
   long long s = 1;
   for (int k = d.nc - 1; k >= 0; --k) {
     P.dim[d.nr + k] = d.cdim[k];
@@ -1144,14 +1168,14 @@ PermPlan pack_plan(const PackDesc& d) {
 template <class T>
 cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st) {
   if (d.rows <= 0 || d.creal <= 0) return cudaSuccess;
-  return run_permute<T, false>(pack_plan(d), src, PermOut<T>{dst, nullptr, nullptr}, 1.0, 0.0, st);
+  return run_permute<T, false>(pack_plan(src, d), PermOut<T>{dst, nullptr, nullptr}, 1.0, 0.0, st);
 }
 template cudaError_t launch_pack<float>(const float*, float*, const PackDesc&, cudaStream_t);
 template cudaError_t launch_pack<double>(const double*, double*, const PackDesc&, cudaStream_t);
 
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st) {
   if (d.rows <= 0 || d.creal <= 0) return cudaSuccess;
-  return run_permute<float, true>(pack_plan(d), src,
+  return run_permute<float, true>(pack_plan(src, d),
                                   PermOut<float>{nullptr, static_cast<__nv_bfloat16*>(hi),
                                                  static_cast<__nv_bfloat16*>(lo)},
                                   1.0, 0.0, st);
@@ -1176,11 +1200,37 @@ cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha
     for (int w = 0; w < 2; ++w)
       if (p & (1 << w)) std::swap(pm[d.sw[w][0]], pm[d.sw[w][1]]);
     for (int k = 0; k < d.nd; ++k) P.sst[p][k] = d.sst[pm[k]];
+    P.src[p] = src;
+    P.coef[p] = (p == 1 || p == 2) ? -1.0 : 1.0;
   }
-  return run_permute<T, false>(P, src, PermOut<T>{dst, nullptr, nullptr}, alpha, beta, st);
+  return run_permute<T, false>(P, PermOut<T>{dst, nullptr, nullptr}, alpha, beta, st);
 }
 template cudaError_t launch_scatter<float>(const float*, float*, const ScatDesc&, double, double, cudaStream_t);
 template cudaError_t launch_scatter<double>(const double*, double*, const ScatDesc&, double, double, cudaStream_t);
+
+template <class T>
+cudaError_t launch_combine(T* dst, int nd, const long long* dim, const CombTerm* terms, int nterm, double beta,
+                           cudaStream_t st) {
+  if (nd < 1 || nd > kMaxL || nterm < 1 || nterm > kPermTerms) return cudaErrorInvalidValue;
+  PermPlan P;
+  P.nd = nd;
+  P.nterm = nterm;
+  long long s = 1;
+  for (int k = nd - 1; k >= 0; --k) {
+    P.dim[k] = dim[k];
+    P.dstr[k] = s;
+    s *= dim[k];
+  }
+  for (int p = 0; p < nterm; ++p) {
+    P.src[p] = terms[p].src;
+    P.coef[p] = terms[p].coef;
+    for (int k = 0; k < nd; ++k) P.sst[p][k] = terms[p].sst[k];
+  }
+  return run_permute<T, false>(P, PermOut<T>{dst, nullptr, nullptr}, 1.0, beta, st);
+}
+template cudaError_t launch_combine<float>(float*, int, const long long*, const CombTerm*, int, double, cudaStream_t);
+template cudaError_t launch_combine<double>(double*, int, const long long*, const CombTerm*, int, double,
+                                            cudaStream_t);
 
 template <class T>
 cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double ctt, double cta, int nx, int no, int nv,

@@ -177,7 +177,7 @@ struct Solver {
   int nx = 0;              // tau points of the current pass
   std::map<std::string, Buf> Vb, Fb;
   Buf t1, t2, S1, S2;
-  Buf tt, ta, X, Wmnij, Wabef, Wmbej, Fae, Fmi, Fme, Ft, Ft2, Y;
+  Buf tt, ta, X, Wmnij, Wabef, Wmbej, Fae, Fmi, Fme, Ft, Ft2, Y, R, R2;
   Buf pA, pB, pA2, pB2, Ct, skw;
   std::map<PackKey, std::pair<Buf, Buf>> packed;   // cached packs of fixed operands
   Buf part1, part2;
@@ -243,7 +243,7 @@ struct Solver {
   std::map<const void*, T*> bar;            // forward buffer -> its adjoint
   std::map<const void*, Buf> fixed_bar;     // integral / Fock block -> adjoint (when wanted)
   bool want_fixed_bar = false;
-  Buf btt, bta, bX, bWmnij, bWabef, bWmbej, bY, bFae, bFmi, bFme, bFt, bFt2, bD, bP, bQ, ones, sx1, sx2;
+  Buf btt, bta, bX, bWmnij, bWabef, bWmbej, bY, bFae, bFmi, bFme, bFt, bFt2, bR, bR2, bD, bP, bQ, ones, sx1, sx2;
 
   Solver(Batch* batch, int kind) : b(batch), h_(batch->home), gk(kind) {}
   ~Solver() {
@@ -254,10 +254,14 @@ struct Solver {
       h_->put(kv.second.first);
       h_->put(kv.second.second);
     }
-    Buf* bs[] = {&t1, &t2, &S1, &S2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
+    Buf* bs[] = {&t1, &t2, &S1, &S2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y, &R, &R2, &bR, &bR2,
                  &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2, &btt, &bta, &bX, &bWmnij, &bWabef, &bWmbej,
                  &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
+    for (auto& e : amp_cache) {
+      h_->put(e.a);
+      h_->put(e.b);
+    }
     for (auto& kv : fixed_bar) h_->put(kv.second);
     for (auto& r : prof) {
       cudaEventDestroy(r.e0);
@@ -328,6 +332,68 @@ struct Solver {
                  [&] { CU(launch_scatter<T>(src, dst, d, alpha, beta, st())); });
   }
 
+  // dst (letters Ld) = beta * dst + sum over the sources of coef * P_anti(src)
+  // in one launch of the multi-source permute.  On the tape it is the
+  // equivalent sequence of scatters, whose adjoints are the transposes.
+  struct Src {
+    const T* p;
+    const char* L;
+    double coef;
+    const char* anti;
+  };
+  void combine(T* dst, const char* Ld, std::initializer_list<Src> srcs, double beta) {
+    if (recording) {
+      bool first = true;
+      for (const Src& q : srcs) {
+        tape.push_back(Op{1, dst, Ld, q.p, q.L, nullptr, "", nullptr, q.coef, first ? beta : 1.0, q.anti});
+        first = false;
+      }
+    }
+    const int nd = static_cast<int>(strlen(Ld));
+    long long dim[kMaxL];
+    long long total = 1;
+    for (int k = 0; k < nd; ++k) {
+      dim[k] = dimof(Ld[k]);
+      total *= dim[k];
+    }
+    std::vector<CombTerm> terms;
+    double reads = beta != 0.0 ? 1.0 : 0.0;
+    for (const Src& q : srcs) {
+      auto ss = strides_of(q.L);
+      long long base[kMaxL];
+      bool bcast = false;
+      for (int k = 0; k < nd; ++k) {
+        const char* at = strchr(q.L, Ld[k]);
+        base[k] = at ? ss[at - q.L] : 0;
+        bcast |= !at;
+      }
+      int sw[2][2], nsw = 0;
+      for (const char* a = q.anti; *a; a += 2) {
+        const char* pa = strchr(Ld, a[0]);
+        const char* pb = strchr(Ld, a[1]);
+        if (!pa || !pb || nsw == 2) throw Fail{FTCC_ERR_STATE, "bad antisymmetriser"};
+        sw[nsw][0] = static_cast<int>(pa - Ld);
+        sw[nsw][1] = static_cast<int>(pb - Ld);
+        ++nsw;
+      }
+      for (int p = 0; p < (1 << nsw); ++p) {
+        int pm[kMaxL];
+        for (int k = 0; k < nd; ++k) pm[k] = k;
+        for (int w = 0; w < nsw; ++w)
+          if (p & (1 << w)) std::swap(pm[sw[w][0]], pm[sw[w][1]]);
+        CombTerm t{};
+        t.src = q.p;
+        for (int k = 0; k < nd; ++k) t.sst[k] = base[pm[k]];
+        t.coef = ((p == 1 || p == 2) ? -1.0 : 1.0) * q.coef;
+        terms.push_back(t);
+      }
+      reads += bcast ? 0.0 : static_cast<double>(1 << nsw);
+    }
+    timed_launch(kClsScatter, static_cast<double>(total) * (reads + 1) * sizeof(T), 0.0, [&] {
+      CU(launch_combine<T>(dst, nd, dim, terms.data(), static_cast<int>(terms.size()), beta, st()));
+    });
+  }
+
   void pack(const T* src, const char* Ls, const std::string& rows, const std::string& cols, long long cpad, T* dst,
             void* hi, void* lo) {
     PackDesc d{};
@@ -365,6 +431,25 @@ struct Solver {
     const void* p2;
     long long ld;
   };
+  // Packs of the S-kernel inputs (t1, t2 of the current pass), kept for the
+  // rest of the pass: t2 enters two contractions in the same packed order.
+  struct AmpPack {
+    const void* src;
+    std::string L, rows, cols;
+    long long ld;
+    int kind;
+    Buf a, b;
+    bool valid;
+  };
+  std::vector<AmpPack> amp_cache;
+  const void* amp_in[2] = {nullptr, nullptr};
+  void amp_begin(const void* t1c, const void* t2c) {
+    amp_in[0] = t1c;
+    amp_in[1] = t2c;
+    for (auto& e : amp_cache) e.valid = false;
+  }
+  void amp_end() { amp_in[0] = amp_in[1] = nullptr; }
+
   Operand operand(Tn<const T> X, const std::string& rows, const std::string& cols, long long k, int kind, Buf& buf,
                   Buf& buf2) {
     const long long q = kind == GEMM_TF32 ? 4 : (kind == GEMM_BF16X3 ? 8 : 1);
@@ -376,6 +461,30 @@ struct Solver {
     for (char ch : rows) nrow *= dimof(ch);
     const size_t es = kind == GEMM_BF16X3 ? 2 : sizeof(T);
     const size_t bytes = static_cast<size_t>(nrow) * ld * es;
+    if (!X.fixed && X.p && (X.p == amp_in[0] || X.p == amp_in[1])) {
+      AmpPack* slot = nullptr;
+      for (auto& e : amp_cache) {
+        if (e.rows == rows && e.cols == cols && e.ld == ld && e.kind == kind) {
+          if (e.valid && e.src == X.p && e.L == X.L) return {e.a.p, e.b.p, ld};
+          if (!e.valid && !slot) slot = &e;
+        }
+      }
+      if (!slot) {
+        amp_cache.push_back(AmpPack{nullptr, "", rows, cols, ld, kind, Buf{}, Buf{}, false});
+        slot = &amp_cache.back();
+      }
+      ensure(h_, slot->a, bytes);
+      if (kind == GEMM_BF16X3) {
+        ensure(h_, slot->b, bytes);
+        pack(X.p, X.L, rows, cols, ld, nullptr, slot->a.p, slot->b.p);
+      } else {
+        pack(X.p, X.L, rows, cols, ld, static_cast<T*>(slot->a.p), nullptr, nullptr);
+      }
+      slot->src = X.p;
+      slot->L = X.L;
+      slot->valid = true;
+      return {slot->a.p, slot->b.p, ld};
+    }
     if (X.fixed) {
       PackKey key{X.p, rows, cols, ld, kind};
       auto it = packed.find(key);
@@ -430,7 +539,7 @@ struct Solver {
     struct Plan {
       bool swap;
       std::string bat, Ml, Nl, Kl;
-      bool direct;
+      bool direct, trans;
       long long cost;
     };
     Plan best{};
@@ -454,14 +563,18 @@ struct Solver {
       const std::string Ml = (mask & 2) ? ordered(LX, Mset) : Mset;
       const std::string Nl = (mask & 4) ? ordered(LY, Nset) : Nset;
       const std::string Kl = (mask & 8) ? ordered(LY, Kset) : Kset;
-      const bool direct = anti_none && bat + Ml + Nl == Lc;
+      // the GEMM writes C in place when C's layout is [bat][M][N], or [bat][N][M]
+      // with the output stored transposed
+      const bool dn = anti_none && bat + Ml + Nl == Lc;
+      const bool dt = anti_none && !dn && bat + Nl + Ml == Lc;
+      const bool direct = dn || dt;
       long long cost = direct ? 0 : 2 * csize;
       if (!X.fixed && LX != bat + Ml + Kl) cost += 2 * size_of_letters(LX);
       if (!Y.fixed && LY != bat + Nl + Kl) cost += 2 * size_of_letters(LY);
       // the tensor-core tile is 128 rows high: a plan that puts fewer than 64
       // rows on M while N has more would run on the SIMT kernel instead
       if (gk != GEMM_F64 && size_of_letters(Mset) < 64 && size_of_letters(Nset) >= 64) cost += 4 * csize;
-      if (best.cost < 0 || cost < best.cost) best = Plan{swap, bat, Ml, Nl, Kl, direct, cost};
+      if (best.cost < 0 || cost < best.cost) best = Plan{swap, bat, Ml, Nl, Kl, direct, dt, cost};
     }
     const Tn<const T>& GA = best.swap ? B : A;
     const Tn<const T>& GB = best.swap ? A : B;
@@ -494,7 +607,8 @@ struct Solver {
     g.A2 = oa.p2;
     g.B2 = ob.p2;
     g.C = direct ? static_cast<void*>(C.p) : Ct.p;
-    g.ldc = n;
+    g.trans = best.trans ? 1 : 0;
+    g.ldc = best.trans ? m : n;
     g.sc = m * n;
     g.alpha = direct ? alpha : 1.0;
     g.beta = direct ? beta_acc : 0.0;
@@ -531,6 +645,8 @@ struct Solver {
     ensure(h_, Fme, x * o * v * sizeof(T));
     ensure(h_, Ft, x * v * v * sizeof(T));
     ensure(h_, Ft2, x * o * o * sizeof(T));
+    ensure(h_, R, x * o * o * v * v * sizeof(T));
+    ensure(h_, R2, x * o * o * v * v * sizeof(T));
   }
 
   // S kernel for nx tau slices of every instance (Eqs. ccS1 and ccS2
@@ -539,9 +655,10 @@ struct Solver {
   // W_mnij with weight 1/2).  Inputs [z][x][...] with nx slices per instance.
   void s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
     nx = nxcur;
+    amp_begin(t1c, t2c);
     T *ptt = (T*)tt.p, *pta = (T*)ta.p, *pX = (T*)X.p, *pWmnij = (T*)Wmnij.p, *pWabef = (T*)Wabef.p,
       *pWmbej = (T*)Wmbej.p, *pY = (T*)Y.p, *pFae = (T*)Fae.p, *pFmi = (T*)Fmi.p, *pFme = (T*)Fme.p,
-      *pFt = (T*)Ft.p, *pFt2 = (T*)Ft2.p;
+      *pFt = (T*)Ft.p, *pFt2 = (T*)Ft2.p, *pR = (T*)R.p, *pR2 = (T*)R2.p;
     using CT = Tn<const T>;
     auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
     auto CF = [this](const char* L) { return Tn<const T>{F(L), L, true}; };
@@ -561,21 +678,31 @@ struct Solver {
     contract({pFmi, "zxmi"}, 0.5, CT{t1c, "zxie"}, CF("zme"));
     contract({pFmi, "zxmi"}, 1.0, CT{t1c, "zxne"}, CV("zmnie"));
     contract({pFmi, "zxmi"}, 0.5, CT{ptt, "zxinef"}, CV("zmnef"));
-    // W_mnij = <mn||ij> + P(ij) s_j^e <mn||ie> + 1/2 ta_ij^ef <mn||ef>   [hole-ladder, o^4 v^2]
-    scatter(pWmnij, "zxmnij", V("zmnij"), "zmnij", 1.0, 0.0, "");
-    contract({pWmnij, "zxmnij"}, 1.0, CT{t1c, "zxje"}, CV("zmnie"), "ij");
-    contract({pWmnij, "zxmnij"}, 0.5, CT{pta, "zxijef"}, CV("zmnef"));
-    // W_abef = <ab||ef> - P(ab) s_m^b <am||ef>
+    // S2 is assembled as P(ij)P(ab) R + <ab||ij> with R = R1 + R2 (below).
+    // A contribution X that is already antisymmetric in ij enters R as X/2
+    // when the paper applies P(ab) to it (P(ij)P(ab) X = 2 P(ab) X), likewise
+    // for ab, and a fully antisymmetric one as X/4.  A contribution may also
+    // be relabelled, X -> -X(i<->j) or -X(a<->b), which P(ij)P(ab) maps to
+    // the same result; the labels are chosen so that each GEMM writes its
+    // accumulator in place.  The same argument lets an intermediate used only
+    // inside such a term carry 2Z in place of P(ij)Z (W_mnij, W_abef).
+    //
+    // W'_mnij = <mn||ij> - 2 s_i^e <mn||je> + 1/2 ta_ij^ef <mn||ef>, stored [ij][mn]   [o^4 v^2]
+    scatter(pWmnij, "zxijmn", V("zmnij"), "zmnij", 1.0, 0.0, "");
+    contract({pWmnij, "zxijmn"}, -2.0, CT{t1c, "zxie"}, CV("zmnje"));
+    contract({pWmnij, "zxijmn"}, 0.5, CT{pta, "zxijef"}, CV("zmnef"));
+    // W'_abef = <ab||ef> - 2 s_m^a <mb||ef>
     scatter(pWabef, "zxabef", V("zabef"), "zabef", 1.0, 0.0, "");
-    contract({pWabef, "zxabef"}, -1.0, CT{t1c, "zxmb"}, CV("zamef"), "ab");
-    // W_mbej = <mb||ej> + s_j^f <mb||ef> - s_n^b <mn||ej> - (1/2 s_jn^fb + s_j^f s_n^b) <mn||ef>   [o^3 v^3]
-    scatter(pWmbej, "zxmbej", V("zmbej"), "zmbej", 1.0, 0.0, "");
-    contract({pWmbej, "zxmbej"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
-    contract({pWmbej, "zxmbej"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
+    contract({pWabef, "zxabef"}, -2.0, CT{t1c, "zxma"}, CV("zmbef"));
+    // W_mbej = <mb||ej> + s_j^f <mb||ef> - s_n^b <mn||ej> - (1/2 s_jn^fb + s_j^f s_n^b) <mn||ef>,
+    // stored [jb][me] for the ring   [o^3 v^3]
+    scatter(pWmbej, "zxjbme", V("zmbej"), "zmbej", 1.0, 0.0, "");
+    contract({pWmbej, "zxjbme"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
+    contract({pWmbej, "zxjbme"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
     if (recording) tape.push_back(Op{3, pX, "", t1c, "", t2c, "", nullptr, 0.5, 1.0, ""});
     timed_launch(kClsOther, 2.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
                  [&] { CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st())); });
-    contract({pWmbej, "zxmbej"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
+    contract({pWmbej, "zxjbme"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
     // S1 (Eq. ccS1)
     scatter(S1c, "zxia", F("zai"), "zai", 1.0, 0.0, "");
     contract({S1c, "zxia"}, 1.0, CT{t1c, "zxie"}, CT{pFae, "zxae"});
@@ -589,16 +716,20 @@ struct Solver {
     contract({pFt, "zxbe"}, -0.5, CT{t1c, "zxmb"}, CT{pFme, "zxme"});
     scatter(pFt2, "zxmj", pFmi, "zxmj", 1.0, 0.0, "");
     contract({pFt2, "zxmj"}, 0.5, CT{t1c, "zxje"}, CT{pFme, "zxme"});
-    scatter(S2c, "zxijab", V("zabij"), "zabij", 1.0, 0.0, "");
-    contract({S2c, "zxijab"}, 1.0, CT{t2c, "zxijae"}, CT{pFt, "zxbe"}, "ab");
-    contract({S2c, "zxijab"}, -1.0, CT{t2c, "zximab"}, CT{pFt2, "zxmj"}, "ij");
-    contract({S2c, "zxijab"}, 0.5, CT{pta, "zxmnab"}, CT{pWmnij, "zxmnij"});            // hole ladder
-    contract({S2c, "zxijab"}, 0.5, CT{pta, "zxijef"}, CT{pWabef, "zxabef"});            // particle ladder
-    contract({S2c, "zxijab"}, 1.0, CT{t2c, "zximae"}, CT{pWmbej, "zxmbej"}, "ijab");    // ring
-    contract({pY, "zximbj"}, 1.0, CT{t1c, "zxie"}, CV("zmbej"), "", 0.0);
-    contract({S2c, "zxijab"}, -1.0, CT{t1c, "zxma"}, CT{pY, "zximbj"}, "ijab");
-    contract({S2c, "zxijab"}, 1.0, CT{t1c, "zxie"}, CV("zabej"), "ij");
-    contract({S2c, "zxijab"}, -1.0, CT{t1c, "zxma"}, CV("zmbij"), "ab");
+    // R1 [ij][ab]
+    contract({pR, "zxijab"}, 0.5, CT{t2c, "zxijae"}, CT{pFt, "zxbe"}, "", 0.0);        // P(ab) s_ij^ae Ft_be
+    contract({pR, "zxijab"}, 0.5, CT{pFt2, "zxmi"}, CT{t2c, "zxjmab"});                // -P(ij) s_im^ab Ft2_mj, i<->j
+    contract({pR, "zxijab"}, 0.125, CT{pWmnij, "zxijmn"}, CT{pta, "zxmnab"});           // hole ladder
+    contract({pR, "zxijab"}, 0.125, CT{pta, "zxijef"}, CT{pWabef, "zxabef"});           // particle ladder
+    contract({pR, "zxijab"}, 0.5, CT{t1c, "zxie"}, CV("zabej"));                        // P(ij) s_i^e <ab||ej>
+    contract({pR, "zxijab"}, -0.5, CT{t1c, "zxma"}, CV("zmbij"));                       // -P(ab) s_m^a <mb||ij>
+    // R2 [ia][jb]
+    contract({pR2, "zxiajb"}, 1.0, CT{t2c, "zximae"}, CT{pWmbej, "zxjbme"}, "", 0.0);  // ring
+    contract({pY, "zxibjm"}, 1.0, CT{t1c, "zxie"}, CV("zmbej"), "", 0.0);              // Y_imbj = s_i^e <mb||ej>
+    contract({pR2, "zxiajb"}, 1.0, CT{pY, "zxiajm"}, CT{t1c, "zxmb"});                 // -P(ij)P(ab) s_m^a Y_imbj, a<->b
+    combine(S2c, "zxijab",
+            {Src{pR, "zxijab", 1.0, "ijab"}, Src{pR2, "zxiajb", 1.0, "ijab"}, Src{V("zabij"), "zabij", 1.0, ""}}, 0.0);
+    amp_end();
   }
 
   bool is_fixed(const void* p) const {
@@ -641,7 +772,8 @@ struct Solver {
     const long long o = no, v = nv, x = static_cast<long long>(nxcur) * nz;
     // adjoint buffers sized like the chunk intermediates
     Buf* pairs[][2] = {{&btt, &tt}, {&bta, &ta}, {&bX, &X}, {&bWmnij, &Wmnij}, {&bWabef, &Wabef}, {&bWmbej, &Wmbej},
-                       {&bY, &Y}, {&bFae, &Fae}, {&bFmi, &Fmi}, {&bFme, &Fme}, {&bFt, &Ft}, {&bFt2, &Ft2}};
+                       {&bY, &Y}, {&bFae, &Fae}, {&bFmi, &Fmi}, {&bFme, &Fme}, {&bFt, &Ft}, {&bFt2, &Ft2},
+                       {&bR, &R}, {&bR2, &R2}};
     for (auto& pr : pairs) {
       ensure(h_, *pr[0], pr[1]->bytes);
       CU(cudaMemsetAsync(pr[0]->p, 0, pr[1]->bytes, st()));
