@@ -329,6 +329,71 @@ def run_gpu(args, rank, world):
                          "algorithmic_flops_per_iteration": fl_u}
         ctx_u.close()
 
+    # the 162-orbital gas (UEG, 81 plane waves, 40 tau points), streamed over
+    # tau (S kept for one window, Simpson chain carried): one TF32 iteration
+    ueg81 = None
+    if not args.no_ueg and not args.quick and world == 1:
+        c = wl.UEG_81
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats()
+        ctx_u = ftcc.Context(dev)
+        ctx_u.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+        mu_u = ctx_u.reference_mu(c["beta"], float(c["n_elec"]))
+        ctx_u.prepare(c["beta"], mu_u, c["ngrid"], precision="tf32", trunc_thr=c["thr"], stream_tau=1, tau_chunk=1)
+        st = ctx_u.stream
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        r81 = ctx_u.iterate(1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t_it = e0.elapsed_time(e1) / 1e3
+        fl_u = flops_per_iteration(r81["n_occ"], r81["n_vir"], c["ngrid"])
+        ueg81 = {"tf32_streamed": {"s_per_iteration": t_it, "tensor_tflops": fl_u / t_it / 1e12,
+                                   "algorithmic_flops_per_iteration": fl_u,
+                                   "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
+                                   "note": "first iteration from s = 0; S kept for one tau window"}}
+        ctx_u.close()
+
+    # the adjoint (lambda) sweep and response of the beta = 1 instance after an
+    # FP64 solve: seconds per lambda iteration (ft_ccsd_adjoint, host timed)
+    adj = None
+    bat64 = None
+    if not args.quick and world == 1:
+        c = cfgs[1]
+        ctx_a = ftcc.Context(dev)
+        ctx_a.build_hubbard(c["L"], c["t"], c["U"])
+        ctx_a.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ar, _ = ctx_a.adjoint(with_rdm1=True)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        adj = {"workload": "hubbard_1d L=10 U=4 beta=1, ngrid=32, FP64 lambda sweep + response",
+               "s_total": t_adj, "lambda_iterations": ar["iterations"],
+               "s_per_lambda_iteration": t_adj / max(1, ar["iterations"]),
+               "dOmega_dmu": ar["dOmega_dmu"], "N": ar["N"], "E": ar["E"], "S": ar["S"]}
+        ctx_a.close()
+        # the 64-instance batch (6-14 sites, U in [1,8], T in [0.25,4], ngrid=24):
+        # one batched mixed solve with FP64 refinement, per size class
+        cb = wl.hubbard_batch()
+        ctx_b = []
+        for q in cb:
+            x = ftcc.Context(dev)
+            x.build_hubbard(q["L"], q["t"], q["U"])
+            ctx_b.append(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = ftcc.solve_batched(ctx_b, [q["beta"] for q in cb], [q["mu"] for q in cb], cb[0]["ngrid"],
+                                precision=args.precision, refine_max_iter=30, max_iter=400, allow_unconverged=True)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        bat64 = {"workload": "64 hubbard_1d instances, L in {6..14}, ngrid=24, batched per size class",
+                 "s_total": t_b, "instances": len(cb), "converged": int(sum(r["converged"] for r in rb)),
+                 "iterations_max": int(max(r["iterations"] for r in rb))}
+        for x in ctx_b:
+            x.close()
+
     # roofline of the dominant kernel class of the timed step (events inside the graph)
     hbm, bf16, bf16s, src = peaks()
     tf32_peak = bf16 * TF32_PER_BF16
@@ -379,6 +444,8 @@ def run_gpu(args, rank, world):
                 "accuracy": acc,
                 "roofline": roof, "kernels": kernels, "profiled_step_ms": t_prof / args.steps * 1e3,
                 "ueg57_114_spin_orbitals": ueg or None,
+                "ueg81_162_spin_orbitals": ueg81,
+                "adjoint_lambda_sweep": adj, "batched_64_instances": bat64,
                 "e2e": e2e, "gpu_launches": k_mixed * args.steps,
                 "clocks": clk.summary()}
         if cpu:

@@ -96,12 +96,24 @@ typedef struct {
  *   refine_max_iter [8] FP64 iterations after a TF32/BF16X3 phase (0 = none)
  *   tol_mixed  [1e-7]   |dOmega_CC| at which the low-precision phase hands over
  *   tau_chunk  [0]      tau points per S-kernel pass (0 = all that fit)
- *   use_graph  [1]      replay one iteration as a CUDA graph */
+ *   use_graph  [1]      replay one iteration as a CUDA graph
+ *   stream_tau [0]      1: run the S kernel tau_chunk points at a time (0 picks
+ *                       1), keep S only for the current propagation window
+ *                       (max(3, tau_chunk) points) and advance the Simpson
+ *                       propagation window by window, carrying five values per
+ *                       amplitude element (the last two even-point integrals
+ *                       and the last three S).  Same result as the unstreamed
+ *                       iteration; amplitude-sized memory ~ ngrid + 5 +
+ *                       max(3, tau_chunk) slices plus the S-kernel intermediates
+ *                       of tau_chunk points, instead of 2 ngrid + intermediates.
+ *                       Single instance only; ft_ccsd_adjoint then returns
+ *                       FTCC_ERR_UNSUPPORTED. */
 typedef struct {
   double tol_omega, tol_amp, damping, trunc_thr;
   int max_iter, precision, refine_max_iter;
   double tol_mixed;
   int tau_chunk, use_graph;
+  int stream_tau;
 } ftcc_options;
 
 typedef struct {

@@ -51,6 +51,10 @@ cudaError_t gemm_tc(int kind, const GemmArgs& g, int* dev_err, cudaStream_t st);
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
 // FP32 SIMT GEMM (used where a tensor-core tile would be mostly padding).
 cudaError_t gemm_f32(const GemmArgs& g, cudaStream_t st);
+// Row-per-thread kernels for N <= 32 and K <= 32 (full FP32 / FP64 arithmetic).
+bool gemm_skinny_fits(const GemmArgs& g);
+cudaError_t gemm_skinny_f32(const GemmArgs& g, cudaStream_t st);
+cudaError_t gemm_skinny_f64(const GemmArgs& g, cudaStream_t st);
 bool tma_available();
 
 }  // namespace ftcc
@@ -154,6 +158,11 @@ struct PropArgs {
   const void* t1E;               // [nz][ng][o][v] new singles, same type as t, or null
   double* partials;              // [nz][nblocks][ng + 2]
   int nblocks;                   // blocks per instance
+  // tau points [y0, y1) of this launch; S holds s_ng points per instance
+  // starting at y0.  chain ([nz][5][size], same type as t) carries the
+  // recurrence between launches; it may be null only for y0 = 0, y1 = ng.
+  int y0, y1, s_ng;
+  void* chain;
 };
 template <class T> cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a, cudaStream_t st);
 int prop_blocks();

@@ -141,9 +141,63 @@ cudaError_t launch(const GemmArgs& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Skinny products (N <= 32 and K <= 32: the t1- and F-sized operands of the
+// S kernel).  One thread per row of C: it keeps its row of A in registers,
+// B sits in shared memory, and it writes N outputs.  A warp reads 32
+// consecutive rows and writes 32 consecutive rows (or, stored transposed,
+// 32 consecutive entries of each of N columns), so both streams coalesce
+// and the kernel runs at memory speed where a 128-row tensor-core tile
+// would be mostly idle.
+constexpr int kSkinny = 32;
+
+template <class T>
+__global__ void __launch_bounds__(256) gemm_skinny_kernel(const T* __restrict__ A, long long lda, long long sa,
+                                                          const T* __restrict__ B, long long ldb, long long sb,
+                                                          T* __restrict__ C, long long ldc, long long sc, int M,
+                                                          int N, int K, T alpha, T beta, int trans) {
+  __shared__ T Bs[kSkinny][kSkinny + 1];
+  const int bz = blockIdx.y;
+  A += static_cast<long long>(bz) * sa;
+  B += static_cast<long long>(bz) * sb;
+  C += static_cast<long long>(bz) * sc;
+  for (int e = threadIdx.x; e < kSkinny * kSkinny; e += blockDim.x) {   // zero beyond N x K
+    const int n = e / kSkinny, k = e - n * kSkinny;
+    Bs[n][k] = (n < N && k < K) ? B[static_cast<long long>(n) * ldb + k] : T(0);
+  }
+  __syncthreads();
+  const long long m = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  T a[kSkinny];
+#pragma unroll
+  for (int k = 0; k < kSkinny; ++k) a[k] = k < K ? A[m * lda + k] : T(0);
+  const long long csm = trans ? 1 : ldc, csn = trans ? ldc : 1;
+  for (int n = 0; n < N; ++n) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < kSkinny; ++k) acc = fma(a[k], Bs[n][k], acc);
+    T* c = C + m * csm + n * csn;
+    const T v = alpha * acc;
+    *c = (beta == T(0)) ? v : v + beta * *c;
+  }
+}
+
+template <class T>
+cudaError_t launch_skinny(const GemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.N > kSkinny || g.K > kSkinny || g.batch > 65535) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned>((g.M + 255) / 256), static_cast<unsigned>(g.batch));
+  gemm_skinny_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(g.A), g.lda, g.sa, static_cast<const T*>(g.B),
+                                              g.ldb, g.sb, static_cast<T*>(g.C), g.ldc, g.sc, g.M, g.N, g.K,
+                                              static_cast<T>(g.alpha), static_cast<T>(g.beta), g.trans);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st) { return launch<double>(g, st); }
 cudaError_t gemm_f32(const GemmArgs& g, cudaStream_t st) { return launch<float>(g, st); }
+bool gemm_skinny_fits(const GemmArgs& g) { return g.N <= kSkinny && g.K <= kSkinny && g.batch <= 65535; }
+cudaError_t gemm_skinny_f64(const GemmArgs& g, cudaStream_t st) { return launch_skinny<double>(g, st); }
+cudaError_t gemm_skinny_f32(const GemmArgs& g, cudaStream_t st) { return launch_skinny<float>(g, st); }
 
 }  // namespace ftcc

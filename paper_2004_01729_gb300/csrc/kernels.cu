@@ -469,8 +469,10 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
   if (a.live && !a.live[z]) return;                   // frozen: amplitudes and partials untouched
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long size = a.size;
-  S += static_cast<long long>(z) * ng * size;
+  const int y0 = a.y0, y1 = a.y1;                     // tau points of this launch
+  S += static_cast<long long>(z) * a.s_ng * size;     // S[(y - y0) * size + mu]
   t += static_cast<long long>(z) * ng * size;
+  T* chain = a.chain ? static_cast<T*>(a.chain) + static_cast<long long>(z) * 5 * size : nullptr;
   const double* em = a.em + static_cast<long long>(z) * a.N;
   const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
@@ -523,19 +525,28 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
       w = wE ? static_cast<T>(wE[mu]) : T(0);
     }
     const T r2 = r1 * r1, r3 = r2 * r1;
-    const T s0 = valid ? S[mu] : T(0);
-    const T s1 = valid ? S[size + mu] : T(0);
-    const T s2 = valid ? S[2 * size + mu] : T(0);
+    // S_0..S_2 are needed together at y = 1; a launch that starts at 0
+    // covers at least three points
+    const bool head = y0 == 0;
+    const T s0 = (valid && head) ? S[mu] : T(0);
+    const T s1 = (valid && head) ? S[size + mu] : T(0);
+    const T s2 = (valid && head) ? S[2 * size + mu] : T(0);
     T sm1 = T(0), sm2 = T(0), sm3 = T(0);   // S_{y-1}, S_{y-2}, S_{y-3}
     T Ilast = T(0), Iprev = T(0);           // I at the last and second-last even y
-    T s_next = s0, t_next = valid ? t[mu] : T(0);
-    for (int y = 0; y < ng; ++y) {
+    if (!head && valid) {                   // the chain state left by the previous launch
+      Ilast = chain[mu];
+      Iprev = chain[size + mu];
+      sm1 = chain[2 * size + mu];
+      sm2 = chain[3 * size + mu];
+      sm3 = chain[4 * size + mu];
+    }
+    T s_next = valid ? S[mu] : T(0), t_next = valid ? t[y0 * size + mu] : T(0);
+    for (int y = y0; y < y1; ++y) {
       const T sy = s_next;
       const T old = t_next;
-      if (y + 1 < ng && valid) {            // loads of the next step, one step ahead
-        const long long nx = (y + 1) * size + mu;
-        s_next = (y + 1 == 1) ? s1 : ((y + 1 == 2) ? s2 : S[nx]);
-        t_next = t[nx];
+      if (y + 1 < y1 && valid) {            // loads of the next step, one step ahead
+        s_next = (y + 1 == 1) ? s1 : ((y + 1 == 2) ? s2 : S[(y + 1 - y0) * size + mu]);
+        t_next = t[(y + 1) * size + mu];
       }
       T I;
       if (y == 0) {
@@ -575,6 +586,13 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
         if (lane == 0) eacc[y * kWarps + warp] += static_cast<double>(e);
       }
     }
+    if (chain && valid) {
+      chain[mu] = Ilast;
+      chain[size + mu] = Iprev;
+      chain[2 * size + mu] = sm1;
+      chain[3 * size + mu] = sm2;
+      chain[4 * size + mu] = sm3;
+    }
   }
   __shared__ double dm[kPropThreads], sm[kPropThreads];
   dm[threadIdx.x] = static_cast<double>(dmax);
@@ -589,14 +607,14 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
     __syncthreads();
   }
   double* p = partials + static_cast<long long>(blockIdx.x) * (ng + 2);
-  for (int y = threadIdx.x; y < ng; y += blockDim.x) {
+  for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
     double acc = 0.0;
     for (int k = 0; k < kWarps; ++k) acc += eacc[y * kWarps + k];
     p[y] = acc;
   }
-  if (threadIdx.x == 0) {
-    p[ng] = dm[0];
-    p[ng + 1] = sm[0];
+  if (threadIdx.x == 0) {   // maxima over the launches of one iteration
+    p[ng] = y0 == 0 ? dm[0] : fmax(p[ng], dm[0]);
+    p[ng + 1] = y0 == 0 ? sm[0] : fmax(p[ng + 1], sm[0]);
   }
 }
 
@@ -1323,11 +1341,16 @@ template cudaError_t launch_thermal_fock<float>(const double*, int, const int*, 
 template cudaError_t launch_thermal_fock<double>(const double*, int, const int*, const double*, int, const int*,
                                                  const double*, int, double*, cudaStream_t);
 
-int prop_blocks() { return 152 * 4; }
+// Blocks of the propagators over all instances: 16 per SM, so that enough
+// loads are in flight to cover the memory latency.
+int prop_blocks() { return 152 * 16; }
 
 template <class T>
 cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_t st) {
   if (a_in.ng < 3 || a_in.size >= (1LL << 31)) return cudaErrorInvalidValue;
+  if (a_in.y0 < 0 || a_in.y1 > a_in.ng || a_in.y1 <= a_in.y0 || a_in.s_ng < a_in.y1 - a_in.y0) return cudaErrorInvalidValue;
+  if (a_in.y0 == 0 && a_in.y1 < 3) return cudaErrorInvalidValue;                 // S_2 is needed at y = 1
+  if (!a_in.chain && (a_in.y0 != 0 || a_in.y1 != a_in.ng)) return cudaErrorInvalidValue;
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));

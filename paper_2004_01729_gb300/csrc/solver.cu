@@ -174,6 +174,8 @@ struct Solver {
   ftcc_ctx* h_;
   int gk;                  // GEMM_F64 for double; GEMM_TF32 / GEMM_BF16X3 for float
   int nz = 1, no = 0, nv = 0, ng = 0, nxc = 0;   // nxc = tau points per S pass
+  bool stream = false;                            // S kept per tau chunk, propagation chained
+  Buf ch1, ch2;                                   // chain state [5][size] of the singles / doubles
   int nx = 0;              // tau points of the current pass
   std::map<std::string, Buf> Vb, Fb;
   Buf t1, t2, S1, S2;
@@ -254,7 +256,8 @@ struct Solver {
       h_->put(kv.second.first);
       h_->put(kv.second.second);
     }
-    Buf* bs[] = {&t1, &t2, &S1, &S2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y, &R, &R2, &bR, &bR2,
+    Buf* bs[] = {&t1, &t2, &S1, &S2, &ch1, &ch2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
+                 &R, &R2, &bR, &bR2,
                  &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2, &btt, &bta, &bX, &bWmnij, &bWabef, &bWmbej,
                  &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
@@ -586,7 +589,10 @@ struct Solver {
     for (char ch : Kl) k *= dimof(ch);
     if (nb * m * n == 0) return;
     if (counting) gemm_flops += 2 * nb * m * n * k;
-    const bool tc = (gk != GEMM_F64) && m >= 64 && k >= 8;   // narrow N uses a narrow tile
+    // N and K of at most 32 (t1- and F-sized operands): one thread per output row;
+    // otherwise tensor cores when M fills half a tile
+    const bool skinny = n <= 32 && k <= 32 && nb <= 65535;
+    const bool tc = !skinny && (gk != GEMM_F64) && m >= 64 && k >= 8;   // narrow N uses a narrow tile
     const int kind = tc ? gk : (gk == GEMM_F64 ? GEMM_F64 : -1);   // -1: FP32 SIMT
     const Operand oa = operand(GA, bat + Ml, Kl, k, kind, pA, pA2);
     const Operand ob = operand(GB, bat + Nl, Kl, k, kind, pB, pB2);
@@ -619,7 +625,8 @@ struct Solver {
     const double gbytes = static_cast<double>(nb) * ((m + n) * k * es + m * n * sizeof(T) * (g.beta != 0.0 ? 2 : 1));
     const double gflops = 2.0 * nb * m * n * k;
     timed_launch(kind == GEMM_TF32 || kind == GEMM_BF16X3 ? kClsGemmTc : kClsGemmSimt, gbytes, gflops, [&] {
-      if (kind == GEMM_F64) CU(gemm_f64(g, st()));
+      if (skinny) CU(kind == GEMM_F64 ? gemm_skinny_f64(g, st()) : gemm_skinny_f32(g, st()));
+      else if (kind == GEMM_F64) CU(gemm_f64(g, st()));
       else if (kind == -1) CU(gemm_f32(g, st()));
       else CU(gemm_tc(kind, g, h_->dev_err, st()));
     });
@@ -906,6 +913,7 @@ ftcc_options default_options() {
   o.tol_mixed = 1e-7;
   o.tau_chunk = 0;
   o.use_graph = 1;
+  o.stream_tau = 0;
   return o;
 }
 
@@ -980,13 +988,22 @@ Solver<T>& make_solver(Batch& B, int kind) {
     s.no = B.no;
     s.nv = B.nv;
     s.ng = B.ng;
-    s.nxc = (B.nz == 1 && B.opt.tau_chunk > 0) ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
+    s.stream = B.nz == 1 && B.opt.stream_tau != 0;
+    if (s.stream) s.nxc = std::min(B.ng, B.opt.tau_chunk > 0 ? B.opt.tau_chunk : 1);
+    else s.nxc = (B.nz == 1 && B.opt.tau_chunk > 0) ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
     build_blocks<T>(B, s);
     const long long o = s.no, v = s.nv, g = static_cast<long long>(s.ng) * s.nz;
+    // tau slices of S kept: all of them, or (streamed) one propagation window
+    // of max(3, tau_chunk) points
+    const long long gS = s.stream ? std::min(s.ng, std::max(3, s.nxc)) : g;
     ensure(h, s.t1, g * o * v * sizeof(T));
     ensure(h, s.t2, g * o * o * v * v * sizeof(T));
-    ensure(h, s.S1, g * o * v * sizeof(T));
-    ensure(h, s.S2, g * o * o * v * v * sizeof(T));
+    ensure(h, s.S1, gS * o * v * sizeof(T));
+    ensure(h, s.S2, gS * o * o * v * v * sizeof(T));
+    if (s.stream) {
+      ensure(h, s.ch1, 5 * o * v * sizeof(T));
+      ensure(h, s.ch2, 5 * o * o * v * v * sizeof(T));
+    }
     CU(cudaMemsetAsync(s.t1.p, 0, g * o * v * sizeof(T), h->st));
     CU(cudaMemsetAsync(s.t2.p, 0, g * o * o * v * v * sizeof(T), h->st));
     s.alloc_chunk();
@@ -1014,6 +1031,10 @@ PropArgs prop_args(Batch& B, int nslot) {
   a.damping = B.opt.damping;
   a.nslot = nslot;
   a.size = nslot == 2 ? static_cast<long long>(B.no) * B.nv : static_cast<long long>(B.no) * B.no * B.nv * B.nv;
+  a.y0 = 0;
+  a.y1 = B.ng;
+  a.s_ng = B.ng;
+  a.chain = nullptr;
   return a;
 }
 
@@ -1023,6 +1044,45 @@ void iterate_once(Batch& B, Solver<T>& s) {
   s.prof_next = 0;
   const long long o = s.no, v = s.nv;
   const long long n1 = o * v, n2 = o * o * v * v;
+  if (s.stream) {
+    // S for one chunk of tau points at a time, then the propagation of those
+    // points from the carried chain state (the S kernel at tau_x reads only
+    // the amplitudes at tau_x, which the propagation of earlier chunks left
+    // untouched; the first chunk has at least three points)
+    for (int x0 = 0; x0 < s.ng;) {
+      // propagation window: the first one spans at least three points (S_2
+      // enters the y = 1 step); the S kernel runs tau_chunk points at a time
+      const int nx = std::min(x0 == 0 ? std::max(3, s.nxc) : s.nxc, s.ng - x0);
+      for (int xs = 0; xs < nx; xs += s.nxc) {
+        const int nk = std::min(s.nxc, nx - xs);
+        s.s_kernel(static_cast<T*>(s.t1.p) + (x0 + xs) * n1, static_cast<T*>(s.t2.p) + (x0 + xs) * n2,
+                   static_cast<T*>(s.S1.p) + xs * n1, static_cast<T*>(s.S2.p) + xs * n2, nk);
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        PropArgs a = prop_args(B, pass == 0 ? 2 : 4);
+        a.wE = static_cast<const double*>(pass == 0 ? B.F64.p : B.V64.p);
+        a.cE = pass == 0 ? 1.0 : 0.25;
+        a.t1E = pass == 0 ? nullptr : s.t1.p;
+        a.partials = static_cast<double*>(pass == 0 ? s.part1.p : s.part2.p);
+        a.nblocks = pass == 0 ? s.nb1 : s.nb2;
+        a.y0 = x0;
+        a.y1 = x0 + nx;
+        a.s_ng = nx;
+        a.chain = pass == 0 ? s.ch1.p : s.ch2.p;
+        const long long n = pass == 0 ? n1 : n2;
+        const double bytes = static_cast<double>(nx) * n * 3 * sizeof(T) + static_cast<double>(n) * (8 + 10 * sizeof(T));
+        s.timed_launch(kClsPropagate, bytes, 0.0, [&] {
+          CU(launch_propagate<T>(static_cast<const T*>(pass == 0 ? s.S1.p : s.S2.p),
+                                 static_cast<T*>(pass == 0 ? s.t1.p : s.t2.p), a, B.home->st));
+        });
+      }
+      x0 += nx;
+    }
+    CU(launch_reduce(static_cast<const double*>(s.part1.p), s.nb1, static_cast<const double*>(s.part2.p), s.nb2,
+                     s.ng, B.nz, static_cast<const double*>(B.hz.p), static_cast<const int*>(B.live.p),
+                     static_cast<double*>(B.state.p), B.home->st));
+    return;
+  }
   for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {   // tau chunks only when nz == 1
     const int nx = std::min(s.nxc, s.ng - x0);
     s.s_kernel(static_cast<T*>(s.t1.p) + x0 * n1, static_cast<T*>(s.t2.p) + x0 * n2, static_cast<T*>(s.S1.p) + x0 * n1,
@@ -1227,7 +1287,8 @@ bool shell_grid(int n_pw, std::vector<int>& out) {
 
 ftcc_status check_options(ftcc_ctx* c, const ftcc_options& o) {
   if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.trunc_thr < 0 ||
-      o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || !(o.tol_omega >= 0) ||
+      o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || o.stream_tau < 0 ||
+      o.stream_tau > 1 || !(o.tol_omega >= 0) ||
       !(o.tol_amp >= 0) || !(o.tol_mixed >= 0))
     return fail(c, FTCC_ERR_INVALID_ARG, "options out of range");
   return FTCC_OK;
@@ -1989,6 +2050,8 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1) {
   if (!c) return FTCC_ERR_INVALID_ARG;
   if (!c->batch || !c->batch->solved) return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
+  if (c->batch->opt.stream_tau)
+    return fail(c, FTCC_ERR_UNSUPPORTED, "the adjoint needs S at every tau point (solve without stream_tau)");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));

@@ -216,3 +216,26 @@ def test_kernel_profile_leaves_results_unchanged(ctx, graph):
     assert {"gemm_tc_kernel", "propagate_kernel", "permute_kernel:scatter"} <= names, names
     for s in stats:
         assert s["launches"] > 0 and s["ms"] > 0.0
+
+
+@pytest.mark.parametrize("prec,chunk", [("fp64", 1), ("fp64", 5), ("tf32", 1)])
+def test_streamed_tau_matches_full_sweep(ctx, prec, chunk):
+    """stream_tau keeps S for one tau chunk and carries the Simpson chain
+    state between chunks; every iterate equals the unstreamed one.  (In TF32
+    the reference runs the S kernel on the same chunks, since other GEMM
+    shapes round differently.)"""
+    c = wl.HUBBARD_6
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    ref = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=0, max_iter=6,
+                    allow_unconverged=True, tau_chunk=chunk if prec != "fp64" else 0)
+    got = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=0, max_iter=6,
+                    allow_unconverged=True, stream_tau=1, tau_chunk=chunk)
+    assert got["iterations"] == ref["iterations"]
+    assert abs(got["omega"] - ref["omega"]) < (1e-13 if prec == "fp64" else 1e-9)
+    if prec == "fp64":
+        full = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10,
+                         stream_tau=1, tau_chunk=chunk)
+        gold = json.load(open(os.path.join(GOLD, "oracle_hubbard6.json")))
+        assert full["converged"] and abs(full["omega"] - gold["omega"]) < 1e-8
+        d, _ = ctx.adjoint(with_rdm1=False, allow_unsupported=True)
+        assert d["status"] == 7   # FTCC_ERR_UNSUPPORTED: the adjoint needs S at every tau point
