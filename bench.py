@@ -266,7 +266,8 @@ def run_gpu(args, rank, world):
     ctx_mixed[0].profile(False)
     if args.quick:
         print(json.dumps({"quick": True, "s_per_iteration": t_mixed / args.steps,
-                          "kernels_per_iter": ctx_mixed[0].iterate(0)["kernels_per_iter"]}), flush=True)
+                          "kernels_per_iter": ctx_mixed[0].iterate(0)["kernels_per_iter"],
+                          "ms_per_step_by_class": {r["name"]: r["ms"] / args.steps for r in kstats}}), flush=True)
         for ctx in ctx_mixed:
             ctx.close()
         return

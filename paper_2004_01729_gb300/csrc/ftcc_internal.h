@@ -92,7 +92,8 @@ struct PackDesc {
 // terms p run over the antisymmetriser: identity, swap(s0a, s0b),
 // swap(s1a, s1b), both swaps (signs +, -, -, +); nswap = 0, 1, 2.  A source
 // stride of 0 broadcasts along that letter.  Both launchers run the tiled
-// permute kernel (shared-memory tiles, coalesced reads and writes).
+// permute kernel (shared-memory tiles, coalesced reads and writes; each term
+// read in its own letter order).
 struct ScatDesc {
   int nd;
   long long dim[kMaxL], sst[kMaxL];
@@ -101,16 +102,24 @@ struct ScatDesc {
   long long total;
 };
 
-// dst (dense, nd letters of extents dim) = beta * dst + sum_p coef_p * src_p[sum_k c_k sst_p[k]]:
-// up to nine source terms (each a tensor read in its own letter order, a
-// stride of 0 broadcasting), one pass, shared-memory tiles.
-struct CombTerm {
-  const void* src;
-  long long sst[kMaxL];
+// dst[zx][i][j][a][b] (dense) = sum_s coef_s P(ij)P(ab) X_s + V(ab,ij): element
+// (zx,i,j,a,b) of source s at p + zx*sx + i*si + j*sj + a*sa + b*sb; V at
+// vp + z*vz + a*va + b*vb + i*vi + j*vj with z = zx / nx (vp may be null).
+// Each unordered pair {i,j} and pair of 32-wide a/b tiles is evaluated once;
+// the result is exactly antisymmetric.  One or two sources.
+struct AntiSrc {
+  const void* p;
+  long long sx, si, sj, sa, sb;
   double coef;
 };
-template <class T> cudaError_t launch_combine(T* dst, int nd, const long long* dim, const CombTerm* terms, int nterm,
-                                              double beta, cudaStream_t st);
+struct Anti4Desc {
+  int nzx, nx, no, nv, nsrc;
+  int ta;                      // tile edge (set by the launcher)
+  AntiSrc src[2];
+  const void* vp;
+  long long vz, va, vb, vi, vj;
+};
+template <class T> cudaError_t launch_antisym4(T* dst, const Anti4Desc& d, cudaStream_t st);
 template <class T> cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st);
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st);
 template <class T> cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha,
@@ -156,7 +165,7 @@ struct PropArgs {
   const double* wE;              // [nz][size] energy weights (f_ia or <ij||ab>) or null
   double cE;                     // coefficient of wE * s
   const void* t1E;               // [nz][ng][o][v] new singles, same type as t, or null
-  double* partials;              // [nz][nblocks][ng + 2]
+  double* partials;              // [nz][ng + 2][nblocks]
   int nblocks;                   // blocks per instance
   // tau points [y0, y1) of this launch; S holds s_ng points per instance
   // starting at y0.  chain ([nz][5][size], same type as t) carries the

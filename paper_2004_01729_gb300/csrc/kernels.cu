@@ -39,7 +39,7 @@ constexpr int kPermThreads = 256;
 constexpr int kPermTile = 4096;   // elements of one tile in shared memory
 constexpr int kPermRows = 512;    // rows per pass of the shared row table
 
-constexpr int kPermTerms = 9;     // source terms of one launch (the write is order kPermTerms)
+constexpr int kPermTerms = 4;     // source terms of one launch (the write is order kPermTerms)
 
 struct DevPerm {
   int nd, nterm, nt;
@@ -184,11 +184,6 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out
   if (d.nterm > 1) perm_term<1>(d, c, tailmask, n, rowG, rowT, tile);
   if (d.nterm > 2) perm_term<2>(d, c, tailmask, n, rowG, rowT, tile);
   if (d.nterm > 3) perm_term<3>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 4) perm_term<4>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 5) perm_term<5>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 6) perm_term<6>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 7) perm_term<7>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 8) perm_term<8>(d, c, tailmask, n, rowG, rowT, tile);
   // write in destination order
   long long dbase = 0;
 #pragma unroll
@@ -213,6 +208,120 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out
       // the destination values are the loads; the tile is read at the store
       perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long g, int) { return dp[g]; },
                       [&](long long g, int t, T old) { dp[g] = beta * old + alpha * tile[t]; });
+    }
+  }
+}
+
+// ----------------------------------------------------------------- doubles antisymmetriser
+// dst[zx][i][j][a][b] = sum_s c_s ((X_s(ij,ab) - X_s(ji,ab)) - (X_s(ij,ba) - X_s(ji,ba))) + V(ab,ij)
+// evaluated once per unordered pair {i,j} and pair of 32-wide tiles {A,B};
+// the other three orientations are written as its exact negatives, so dst
+// is exactly antisymmetric and every source element is read once.
+constexpr int kAT = 32;   // largest tile edge along a and b
+
+__device__ __forceinline__ void upper_pair(int n, int p, int& i, int& j) {
+  // p-th pair (i <= j) of the upper triangle of an n x n grid, rows in order
+  int r = static_cast<int>((2.0 * n + 1.0 - sqrt((2.0 * n + 1.0) * (2.0 * n + 1.0) - 8.0 * p)) * 0.5);
+  if (r < 0) r = 0;
+  if (r > n - 1) r = n - 1;
+  auto start = [n](int q) { return q * n - q * (q - 1) / 2; };
+  while (r > 0 && start(r) > p) --r;
+  while (r + 1 < n && start(r + 1) <= p) ++r;
+  i = r;
+  j = r + (p - start(r));
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) antisym4_kernel(T* __restrict__ dst, Anti4Desc d) {
+  extern __shared__ __align__(16) unsigned char as_smem[];
+  T* tiles = reinterpret_cast<T*>(as_smem);   // [nsrc][4][TA][TA + 1], then the result [TA][TA + 1]
+  const int TA = d.ta, ld = TA + 1, t2 = TA * TA;
+  const int nA = (d.nv + TA - 1) / TA;
+  const int ntp = nA * (nA + 1) / 2;
+  const int npair = d.no * (d.no + 1) / 2;
+  long long r = blockIdx.x;
+  const int tp = static_cast<int>(r % ntp);
+  r /= ntp;
+  const int pr = static_cast<int>(r % npair);
+  const long long zx = r / npair;
+  int i, j, tA, tB;
+  upper_pair(d.no, pr, i, j);
+  upper_pair(nA, tp, tA, tB);
+  const int A0 = tA * TA, B0 = tB * TA;
+  // thread (row group, lane): lane = column cc of a tile, rows rr = warp,
+  // warp + 8, ...; no index division anywhere
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kRows = 8;   // warps per block
+  // the four orientations of every source: (ij,AB), (ji,AB), (ij,BA), (ji,BA)
+  if (lane < TA) {
+    const int cc = lane;
+    for (int s = 0; s < d.nsrc; ++s) {
+      const AntiSrc& q = d.src[s];
+      const T* base = static_cast<const T*>(q.p) + zx * q.sx;
+      const T* bij = base + i * q.si + j * q.sj;
+      const T* bji = base + j * q.si + i * q.sj;
+      T* ts = tiles + s * 4 * TA * ld;
+      for (int rr = warp; rr < TA; rr += kRows) {
+        const int a1 = A0 + rr, b1 = B0 + cc;   // (AB) orientations
+        const int a2 = B0 + rr, b2 = A0 + cc;   // (BA) orientations
+        const bool in1 = a1 < d.nv && b1 < d.nv, in2 = a2 < d.nv && b2 < d.nv;
+        const long long o1 = a1 * q.sa + b1 * q.sb, o2 = a2 * q.sa + b2 * q.sb;
+        const T v0 = in1 ? bij[o1] : T(0);
+        const T v1 = in1 ? bji[o1] : T(0);
+        const T v2 = in2 ? bij[o2] : T(0);
+        const T v3 = in2 ? bji[o2] : T(0);
+        ts[rr * ld + cc] = v0;
+        ts[(TA + rr) * ld + cc] = v1;
+        ts[(2 * TA + rr) * ld + cc] = v2;
+        ts[(3 * TA + rr) * ld + cc] = v3;
+      }
+    }
+  }
+  __syncthreads();
+  T* res = tiles + d.nsrc * 4 * TA * ld;
+  const long long z = zx / d.nx;
+  const T* vb = static_cast<const T*>(d.vp) + z * d.vz + i * d.vi + j * d.vj;
+  if (lane < TA) {
+    const int cc = lane;
+    for (int rr = warp; rr < TA; rr += kRows) {
+      const int a = A0 + rr, b = B0 + cc;
+      T v = T(0);
+      if (a < d.nv && b < d.nv) {
+        for (int s = 0; s < d.nsrc; ++s) {
+          const T* t0 = tiles + s * 4 * TA * ld;
+          const T x = (t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
+                      (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]);
+          v += static_cast<T>(d.src[s].coef) * x;
+        }
+        if (d.vp) v += vb[a * d.va + b * d.vb];
+      }
+      res[rr * ld + cc] = v;
+    }
+  }
+  __syncthreads();
+  const long long so = static_cast<long long>(d.nv) * d.nv, sj = so, si = static_cast<long long>(d.no) * so;
+  T* out = dst + zx * d.no * si;
+  T* oij = out + i * si + j * sj;
+  T* oji = out + j * si + i * sj;
+  if (lane < TA) {
+    const int cc = lane;
+    for (int rr = warp; rr < TA; rr += kRows) {
+      {
+        const int a = A0 + rr, b = B0 + cc;   // (A, B) orientation: rows along b
+        if (a < d.nv && b < d.nv) {
+          const T v = res[rr * ld + cc];
+          oij[a * d.nv + b] = v;
+          if (i != j) oji[a * d.nv + b] = -v;
+        }
+      }
+      if (tA != tB) {
+        const int a = B0 + rr, b = A0 + cc;   // (B, A) orientation: the transposed tile
+        if (a < d.nv && b < d.nv) {
+          const T v = res[cc * ld + rr];
+          oij[a * d.nv + b] = -v;
+          if (i != j) oji[a * d.nv + b] = v;
+        }
+      }
     }
   }
 }
@@ -459,11 +568,15 @@ __global__ void thermal_fock_kernel(const double* __restrict__ fbar, int N, cons
 // which equals sum_x G[y,x] exp(Delta (tau_x - tau_y)) S_x for the Simpson
 // tensors (composite 1/3 for even y, 1/3 then 3/8 for odd y).  s_y = -I_y.
 constexpr int kPropThreads = 128;
+constexpr int kPropAhead = 2;   // tau steps of loads in flight per element
 
 template <class T, int NS>
-__global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __restrict__ S, T* __restrict__ t, PropArgs a) {
-  constexpr int kWarps = kPropThreads / 32;
-  extern __shared__ double eacc[];                    // [ng][kWarps] energy partial per warp
+__global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagate_kernel(const T* __restrict__ S, T* __restrict__ t,
+                                                                                     PropArgs a) {
+  // per-thread energy slots eacc[y][thread] (storage precision; each thread
+  // sums over its own one or two elements), reduced over the block in FP64
+  extern __shared__ __align__(16) unsigned char pe_smem[];
+  T* eacc = reinterpret_cast<T*>(pe_smem);
   const int ng = a.ng;
   const int z = blockIdx.y;                           // instance
   if (a.live && !a.live[z]) return;                   // frozen: amplitudes and partials untouched
@@ -476,24 +589,20 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
   const double* em = a.em + static_cast<long long>(z) * a.N;
   const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
-  const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * a.no * a.nv : nullptr;
+  const long long n1 = static_cast<long long>(a.no) * a.nv;
+  const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * n1 : nullptr;
   double* partials = a.partials + static_cast<long long>(z) * a.nblocks * (ng + 2);
-  for (int i = threadIdx.x; i < ng * kWarps; i += blockDim.x) eacc[i] = 0.0;
-  __syncthreads();
+  for (int y = y0; y < y1; ++y) eacc[y * kPropThreads + threadIdx.x] = T(0);
   T dmax = T(0), smax = T(0);
   const T h = static_cast<T>(a.hz[z]);
   const T c12 = h / T(12), c3 = h / T(3), c38 = T(3) * h / T(8);
   const T damp = static_cast<T>(a.damping);
+  const bool damped = a.damping != 1.0;
   const T cE = static_cast<T>(a.cE);
-  // warp-uniform loop: every lane runs every tau step so the per-tau energy
-  // can be reduced across the warp; lanes past the end contribute zero
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x + warp * 32; base < size; base += stride) {
-    const long long mu = base + lane;
-    const bool valid = mu < size;
-    int i = 0, j = 0, aa = 0, b = 0;
-    T r1 = T(0), rinv = T(0), w = T(0);
-    if (valid) {
+  for (long long mu = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; mu < size; mu += stride) {
+    int i, j = 0, aa, b = 0;
+    {
       uint32_t r = static_cast<uint32_t>(mu);
       uint32_t q = fdiv(a.fv, r);
       if (NS == 4) {
@@ -509,44 +618,62 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
         aa = r - q * a.nv;
         i = q;
       }
-      const int pi = a.idxO[i], pa = a.idxV[aa];
-      double rr = em[pa] * ep[pi];
-      double ri = ep[pa] * em[pi];
-      if (NS == 4) {
-        const int pj = a.idxO[j], pb = a.idxV[b];
-        rr *= em[pb] * ep[pj];
-        ri *= ep[pb] * em[pj];
-      }
-      // The recurrence runs in the storage precision: FP32 storage carries
-      // ~1e-7 relative error anyway, and FP64 issue rate is a small fraction
-      // of FP32 on this part.  FP64 storage keeps everything in FP64.
-      r1 = static_cast<T>(rr);
-      rinv = static_cast<T>(ri);
-      w = wE ? static_cast<T>(wE[mu]) : T(0);
     }
+    const int pi = a.idxO[i], pa = a.idxV[aa];
+    double rr = em[pa] * ep[pi];
+    double ri = ep[pa] * em[pi];
+    if (NS == 4) {
+      const int pj = a.idxO[j], pb = a.idxV[b];
+      rr *= em[pb] * ep[pj];
+      ri *= ep[pb] * em[pj];
+    }
+    // The recurrence runs in the storage precision: FP32 storage carries
+    // ~1e-7 relative error anyway, and FP64 issue rate is a small fraction
+    // of FP32 on this part.  FP64 storage keeps everything in FP64.
+    const T r1 = static_cast<T>(rr), rinv = static_cast<T>(ri);
+    const T w = wE ? static_cast<T>(wE[mu]) : T(0);
     const T r2 = r1 * r1, r3 = r2 * r1;
     // S_0..S_2 are needed together at y = 1; a launch that starts at 0
     // covers at least three points
     const bool head = y0 == 0;
-    const T s0 = (valid && head) ? S[mu] : T(0);
-    const T s1 = (valid && head) ? S[size + mu] : T(0);
-    const T s2 = (valid && head) ? S[2 * size + mu] : T(0);
+    const T s0 = head ? S[mu] : T(0);
+    const T s1 = head ? S[size + mu] : T(0);
+    const T s2 = head ? S[2 * size + mu] : T(0);
     T sm1 = T(0), sm2 = T(0), sm3 = T(0);   // S_{y-1}, S_{y-2}, S_{y-3}
     T Ilast = T(0), Iprev = T(0);           // I at the last and second-last even y
-    if (!head && valid) {                   // the chain state left by the previous launch
+    if (!head) {                            // the chain state left by the previous launch
       Ilast = chain[mu];
       Iprev = chain[size + mu];
       sm1 = chain[2 * size + mu];
       sm2 = chain[3 * size + mu];
       sm3 = chain[4 * size + mu];
     }
-    T s_next = valid ? S[mu] : T(0), t_next = valid ? t[y0 * size + mu] : T(0);
+    // S_y and the old s_y are loaded kPropAhead steps ahead (a register
+    // window), so that several loads per thread are in flight
+    const T* sq = S + mu;
+    T* tq = t + y0 * size + mu;
+    T sp[kPropAhead], tp[kPropAhead];
+#pragma unroll
+    for (int k = 0; k < kPropAhead; ++k) {
+      const bool in = y0 + k < y1;
+      sp[k] = in ? sq[k * size] : T(0);
+      tp[k] = in ? tq[k * size] : T(0);
+    }
+    const T* s1y = t1E ? t1E + y0 * n1 : nullptr;   // singles of this tau point
+    const int oi = i * a.nv + aa, oj = j * a.nv + b;
+    T* ea = eacc + y0 * kPropThreads + threadIdx.x;
     for (int y = y0; y < y1; ++y) {
-      const T sy = s_next;
-      const T old = t_next;
-      if (y + 1 < y1 && valid) {            // loads of the next step, one step ahead
-        s_next = (y + 1 == 1) ? s1 : ((y + 1 == 2) ? s2 : S[(y + 1 - y0) * size + mu]);
-        t_next = t[(y + 1) * size + mu];
+      const T sy = sp[0];
+      const T old = tp[0];
+#pragma unroll
+      for (int k = 0; k + 1 < kPropAhead; ++k) {
+        sp[k] = sp[k + 1];
+        tp[k] = tp[k + 1];
+      }
+      {
+        const bool in = y + kPropAhead < y1;
+        sp[kPropAhead - 1] = in ? sq[kPropAhead * size] : T(0);
+        tp[kPropAhead - 1] = in ? tq[kPropAhead * size] : T(0);
       }
       T I;
       if (y == 0) {
@@ -564,29 +691,23 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
       sm2 = sm1;
       sm1 = sy;
       T stored = -I;
-      if (a.damping != 1.0) stored = (T(1) - damp) * old + damp * stored;
-      if (valid) {
-        t[y * size + mu] = stored;
-        dmax = fmax(dmax, fabs(stored - old));
-        smax = fmax(smax, fabs(stored));
-      }
+      if (damped) stored = (T(1) - damp) * old + damp * stored;
+      *tq = stored;
+      dmax = fmax(dmax, fabs(stored - old));
+      smax = fmax(smax, fabs(stored));
       if (wE) {
-        T e = T(0);
-        if (valid) {
-          e = cE * stored;
-          if (NS == 4 && t1E) {
-            const T* s1y = t1E + static_cast<long long>(y) * a.no * a.nv;
-            e += T(0.5) * s1y[i * a.nv + aa] * s1y[j * a.nv + b];
-          }
-          e *= w;
+        T e = cE * stored;
+        if (NS == 4 && s1y) {
+          e += T(0.5) * s1y[oi] * s1y[oj];
+          s1y += n1;
         }
-        // fixed-order warp sum, then one FP64 add per warp and tau
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        if (lane == 0) eacc[y * kWarps + warp] += static_cast<double>(e);
+        *ea += w * e;
       }
+      sq += size;
+      tq += size;
+      ea += kPropThreads;
     }
-    if (chain && valid) {
+    if (chain) {
       chain[mu] = Ilast;
       chain[size + mu] = Iprev;
       chain[2 * size + mu] = sm1;
@@ -606,15 +727,20 @@ __global__ void __launch_bounds__(kPropThreads) propagate_kernel(const T* __rest
     }
     __syncthreads();
   }
-  double* p = partials + static_cast<long long>(blockIdx.x) * (ng + 2);
-  for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
+  // partials[q][block] (q = tau point, then the two maxima), so that the
+  // reduction over blocks reads contiguous rows; one warp per tau point sums
+  // the thread slots in a fixed order
+  const long long nbk = a.nblocks;
+  double* p = partials + blockIdx.x;
+  for (int y = y0 + warp; y < y1; y += kPropThreads / 32) {
     double acc = 0.0;
-    for (int k = 0; k < kWarps; ++k) acc += eacc[y * kWarps + k];
-    p[y] = acc;
+    for (int k = lane; k < kPropThreads; k += 32) acc += static_cast<double>(eacc[y * kPropThreads + k]);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) p[y * nbk] = acc;
   }
   if (threadIdx.x == 0) {   // maxima over the launches of one iteration
-    p[ng] = y0 == 0 ? dm[0] : fmax(p[ng], dm[0]);
-    p[ng + 1] = y0 == 0 ? sm[0] : fmax(p[ng + 1], sm[0]);
+    p[ng * nbk] = y0 == 0 ? dm[0] : fmax(p[ng * nbk], dm[0]);
+    p[(ng + 1) * nbk] = y0 == 0 ? sm[0] : fmax(p[(ng + 1) * nbk], sm[0]);
   }
 }
 
@@ -934,12 +1060,12 @@ __global__ void reduce_kernel(const double* __restrict__ p1, int nb1, const doub
   for (int q = warp; q < w; q += nwarp) {
     const bool is_max = q >= ng;
     double acc = 0.0;
-    for (int b = lane; b < nb1; b += 32) {
-      const double v = p1[static_cast<long long>(b) * w + q];
+    for (int b = lane; b < nb1; b += 32) {   // partials are [q][block]
+      const double v = p1[static_cast<long long>(q) * nb1 + b];
       acc = is_max ? fmax(acc, v) : acc + v;
     }
     for (int b = lane; b < nb2; b += 32) {
-      const double v = p2[static_cast<long long>(b) * w + q];
+      const double v = p2[static_cast<long long>(q) * nb2 + b];
       acc = is_max ? fmax(acc, v) : acc + v;
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -1227,28 +1353,28 @@ template cudaError_t launch_scatter<float>(const float*, float*, const ScatDesc&
 template cudaError_t launch_scatter<double>(const double*, double*, const ScatDesc&, double, double, cudaStream_t);
 
 template <class T>
-cudaError_t launch_combine(T* dst, int nd, const long long* dim, const CombTerm* terms, int nterm, double beta,
-                           cudaStream_t st) {
-  if (nd < 1 || nd > kMaxL || nterm < 1 || nterm > kPermTerms) return cudaErrorInvalidValue;
-  PermPlan P;
-  P.nd = nd;
-  P.nterm = nterm;
-  long long s = 1;
-  for (int k = nd - 1; k >= 0; --k) {
-    P.dim[k] = dim[k];
-    P.dstr[k] = s;
-    s *= dim[k];
+cudaError_t launch_antisym4(T* dst, const Anti4Desc& d, cudaStream_t st) {
+  if (d.nzx <= 0 || d.no <= 0 || d.nv <= 0) return cudaSuccess;
+  if (d.nsrc < 1 || d.nsrc > 2 || d.nx < 1) return cudaErrorInvalidValue;
+  Anti4Desc dd = d;
+  dd.ta = std::min(kAT, d.nv);   // a tile spans the whole a/b range when it is short
+  const long long nA = (d.nv + dd.ta - 1) / dd.ta;
+  const long long blocks = static_cast<long long>(d.nzx) * (static_cast<long long>(d.no) * (d.no + 1) / 2) *
+                           (nA * (nA + 1) / 2);
+  if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
+  const size_t smem = static_cast<size_t>(d.nsrc * 4 + 1) * dd.ta * (dd.ta + 1) * sizeof(T);
+  static bool attr[2] = {false, false};
+  if (smem > 48 * 1024 && !attr[sizeof(T) == 8]) {   // the largest tile set of this type
+    cudaError_t e = cudaFuncSetAttribute(antisym4_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(9 * kAT * (kAT + 1) * sizeof(T)));
+    if (e != cudaSuccess) return e;
+    attr[sizeof(T) == 8] = true;
   }
-  for (int p = 0; p < nterm; ++p) {
-    P.src[p] = terms[p].src;
-    P.coef[p] = terms[p].coef;
-    for (int k = 0; k < nd; ++k) P.sst[p][k] = terms[p].sst[k];
-  }
-  return run_permute<T, false>(P, PermOut<T>{dst, nullptr, nullptr}, 1.0, beta, st);
+  antisym4_kernel<T><<<static_cast<unsigned>(blocks), 256, smem, st>>>(dst, dd);
+  return cudaGetLastError();
 }
-template cudaError_t launch_combine<float>(float*, int, const long long*, const CombTerm*, int, double, cudaStream_t);
-template cudaError_t launch_combine<double>(double*, int, const long long*, const CombTerm*, int, double,
-                                            cudaStream_t);
+template cudaError_t launch_antisym4<float>(float*, const Anti4Desc&, cudaStream_t);
+template cudaError_t launch_antisym4<double>(double*, const Anti4Desc&, cudaStream_t);
 
 template <class T>
 cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double ctt, double cta, int nx, int no, int nv,
@@ -1354,7 +1480,8 @@ cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
-  const size_t smem = static_cast<size_t>(a.ng) * (kPropThreads / 32) * sizeof(double);
+  const size_t smem = static_cast<size_t>(a.ng) * kPropThreads * sizeof(T);   // per-thread energy slots
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
   int blocks = a.nblocks;
   if (a.nz < 1 || a.nz > 65535) return cudaErrorInvalidValue;
   dim3 grid(blocks, a.nz);
@@ -1375,7 +1502,7 @@ template cudaError_t launch_propagate<double>(const double*, double*, const Prop
 cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, int ng, int nz, const double* hz,
                           const int* live, double* state, cudaStream_t st) {
   if (ng > 256 || nz < 1) return cudaErrorInvalidValue;
-  reduce_kernel<<<nz, 256, 0, st>>>(p1, nb1, p2, nb2, ng, nz, hz, live, state);
+  reduce_kernel<<<nz, 1024, 0, st>>>(p1, nb1, p2, nb2, ng, nz, hz, live, state);
   return cudaGetLastError();
 }
 

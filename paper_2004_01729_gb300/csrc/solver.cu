@@ -335,68 +335,6 @@ struct Solver {
                  [&] { CU(launch_scatter<T>(src, dst, d, alpha, beta, st())); });
   }
 
-  // dst (letters Ld) = beta * dst + sum over the sources of coef * P_anti(src)
-  // in one launch of the multi-source permute.  On the tape it is the
-  // equivalent sequence of scatters, whose adjoints are the transposes.
-  struct Src {
-    const T* p;
-    const char* L;
-    double coef;
-    const char* anti;
-  };
-  void combine(T* dst, const char* Ld, std::initializer_list<Src> srcs, double beta) {
-    if (recording) {
-      bool first = true;
-      for (const Src& q : srcs) {
-        tape.push_back(Op{1, dst, Ld, q.p, q.L, nullptr, "", nullptr, q.coef, first ? beta : 1.0, q.anti});
-        first = false;
-      }
-    }
-    const int nd = static_cast<int>(strlen(Ld));
-    long long dim[kMaxL];
-    long long total = 1;
-    for (int k = 0; k < nd; ++k) {
-      dim[k] = dimof(Ld[k]);
-      total *= dim[k];
-    }
-    std::vector<CombTerm> terms;
-    double reads = beta != 0.0 ? 1.0 : 0.0;
-    for (const Src& q : srcs) {
-      auto ss = strides_of(q.L);
-      long long base[kMaxL];
-      bool bcast = false;
-      for (int k = 0; k < nd; ++k) {
-        const char* at = strchr(q.L, Ld[k]);
-        base[k] = at ? ss[at - q.L] : 0;
-        bcast |= !at;
-      }
-      int sw[2][2], nsw = 0;
-      for (const char* a = q.anti; *a; a += 2) {
-        const char* pa = strchr(Ld, a[0]);
-        const char* pb = strchr(Ld, a[1]);
-        if (!pa || !pb || nsw == 2) throw Fail{FTCC_ERR_STATE, "bad antisymmetriser"};
-        sw[nsw][0] = static_cast<int>(pa - Ld);
-        sw[nsw][1] = static_cast<int>(pb - Ld);
-        ++nsw;
-      }
-      for (int p = 0; p < (1 << nsw); ++p) {
-        int pm[kMaxL];
-        for (int k = 0; k < nd; ++k) pm[k] = k;
-        for (int w = 0; w < nsw; ++w)
-          if (p & (1 << w)) std::swap(pm[sw[w][0]], pm[sw[w][1]]);
-        CombTerm t{};
-        t.src = q.p;
-        for (int k = 0; k < nd; ++k) t.sst[k] = base[pm[k]];
-        t.coef = ((p == 1 || p == 2) ? -1.0 : 1.0) * q.coef;
-        terms.push_back(t);
-      }
-      reads += bcast ? 0.0 : static_cast<double>(1 << nsw);
-    }
-    timed_launch(kClsScatter, static_cast<double>(total) * (reads + 1) * sizeof(T), 0.0, [&] {
-      CU(launch_combine<T>(dst, nd, dim, terms.data(), static_cast<int>(terms.size()), beta, st()));
-    });
-  }
-
   void pack(const T* src, const char* Ls, const std::string& rows, const std::string& cols, long long cpad, T* dst,
             void* hi, void* lo) {
     PackDesc d{};
@@ -734,8 +672,31 @@ struct Solver {
     contract({pR2, "zxiajb"}, 1.0, CT{t2c, "zximae"}, CT{pWmbej, "zxjbme"}, "", 0.0);  // ring
     contract({pY, "zxibjm"}, 1.0, CT{t1c, "zxie"}, CV("zmbej"), "", 0.0);              // Y_imbj = s_i^e <mb||ej>
     contract({pR2, "zxiajb"}, 1.0, CT{pY, "zxiajm"}, CT{t1c, "zxmb"});                 // -P(ij)P(ab) s_m^a Y_imbj, a<->b
-    combine(S2c, "zxijab",
-            {Src{pR, "zxijab", 1.0, "ijab"}, Src{pR2, "zxiajb", 1.0, "ijab"}, Src{V("zabij"), "zabij", 1.0, ""}}, 0.0);
+    // S2 = P(ij)P(ab) (R + R2) + <ab||ij>: one pass over unordered index pairs
+    if (recording) {
+      tape.push_back(Op{1, S2c, "zxijab", pR, "zxijab", nullptr, "", nullptr, 1.0, 0.0, "ijab"});
+      tape.push_back(Op{1, S2c, "zxijab", pR2, "zxiajb", nullptr, "", nullptr, 1.0, 1.0, "ijab"});
+      tape.push_back(Op{1, S2c, "zxijab", V("zabij"), "zabij", nullptr, "", nullptr, 1.0, 1.0, ""});
+    }
+    {
+      const long long o = no, v = nv;
+      Anti4Desc d{};
+      d.nzx = nz * nx;
+      d.nx = nx;
+      d.no = no;
+      d.nv = nv;
+      d.nsrc = 2;
+      d.src[0] = AntiSrc{pR, o * o * v * v, o * v * v, v * v, v, 1, 1.0};     // [ij][ab]
+      d.src[1] = AntiSrc{pR2, o * o * v * v, v * o * v, v, o * v, 1, 1.0};    // [ia][jb]
+      d.vp = V("zabij");
+      d.vz = v * v * o * o;
+      d.va = v * o * o;
+      d.vb = o * o;
+      d.vi = o;
+      d.vj = 1;
+      timed_launch(kClsScatter, static_cast<double>(d.nzx) * o * o * v * v * 3 * sizeof(T), 0.0,
+                   [&] { CU(launch_antisym4<T>(S2c, d, st())); });
+    }
     amp_end();
   }
 
