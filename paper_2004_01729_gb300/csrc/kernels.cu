@@ -221,7 +221,9 @@ constexpr int kAT = 32;   // largest tile edge along a and b
 
 __device__ __forceinline__ void upper_pair(int n, int p, int& i, int& j) {
   // p-th pair (i <= j) of the upper triangle of an n x n grid, rows in order
-  int r = static_cast<int>((2.0 * n + 1.0 - sqrt((2.0 * n + 1.0) * (2.0 * n + 1.0) - 8.0 * p)) * 0.5);
+  // (an FP32 estimate of the row, then exact integer correction)
+  const float m = 2.0f * n + 1.0f;
+  int r = static_cast<int>((m - sqrtf(fmaxf(m * m - 8.0f * p, 0.0f))) * 0.5f);
   if (r < 0) r = 0;
   if (r > n - 1) r = n - 1;
   auto start = [n](int q) { return q * n - q * (q - 1) / 2; };
@@ -232,27 +234,37 @@ __device__ __forceinline__ void upper_pair(int n, int p, int& i, int& j) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) antisym4_kernel(T* __restrict__ dst, Anti4Desc d) {
+__global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, Anti4Desc d) {
   extern __shared__ __align__(16) unsigned char as_smem[];
   T* tiles = reinterpret_cast<T*>(as_smem);   // [nsrc][4][TA][TA + 1], then the result [TA][TA + 1]
   const int TA = d.ta, ld = TA + 1, t2 = TA * TA;
   const int nA = (d.nv + TA - 1) / TA;
   const int ntp = nA * (nA + 1) / 2;
   const int npair = d.no * (d.no + 1) / 2;
-  long long r = blockIdx.x;
-  const int tp = static_cast<int>(r % ntp);
-  r /= ntp;
-  const int pr = static_cast<int>(r % npair);
-  const long long zx = r / npair;
-  int i, j, tA, tB;
-  upper_pair(d.no, pr, i, j);
-  upper_pair(nA, tp, tA, tB);
+  // block -> (zx, pair {i,j}, tile pair {A,B}), decoded once by thread 0
+  __shared__ int blk[6];
+  if (threadIdx.x == 0) {
+    unsigned r = blockIdx.x;
+    const int tp = static_cast<int>(r % ntp);
+    r /= ntp;
+    const int pr = static_cast<int>(r % npair);
+    blk[0] = static_cast<int>(r / npair);
+    upper_pair(d.no, pr, blk[1], blk[2]);
+    upper_pair(nA, tp, blk[3], blk[4]);
+    blk[5] = blk[0] / d.nx;
+  }
+  __syncthreads();
+  const long long zx = blk[0];
+  const int i = blk[1], j = blk[2], tA = blk[3], tB = blk[4];
   const int A0 = tA * TA, B0 = tB * TA;
   // thread (row group, lane): lane = column cc of a tile, rows rr = warp,
   // warp + 8, ...; no index division anywhere
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kRows = 8;   // warps per block
-  // the four orientations of every source: (ij,AB), (ji,AB), (ij,BA), (ji,BA)
+  constexpr int kRows = 8;   // warps per block (256 threads)
+  // the four orientations of every source: (ij,AB), (ji,AB), (ij,BA), (ji,BA);
+  // each thread issues all of its loads (up to 4 rows x 4 orientations of a
+  // source) before it stores any of them
+  constexpr int kRpw = kAT / kRows;   // rows per warp at most
   if (lane < TA) {
     const int cc = lane;
     for (int s = 0; s < d.nsrc; ++s) {
@@ -261,25 +273,34 @@ __global__ void __launch_bounds__(256) antisym4_kernel(T* __restrict__ dst, Anti
       const T* bij = base + i * q.si + j * q.sj;
       const T* bji = base + j * q.si + i * q.sj;
       T* ts = tiles + s * 4 * TA * ld;
-      for (int rr = warp; rr < TA; rr += kRows) {
+      T v[kRpw][4];
+#pragma unroll
+      for (int k = 0; k < kRpw; ++k) {
+        const int rr = warp + k * kRows;
         const int a1 = A0 + rr, b1 = B0 + cc;   // (AB) orientations
         const int a2 = B0 + rr, b2 = A0 + cc;   // (BA) orientations
-        const bool in1 = a1 < d.nv && b1 < d.nv, in2 = a2 < d.nv && b2 < d.nv;
+        const bool in1 = rr < TA && a1 < d.nv && b1 < d.nv, in2 = rr < TA && a2 < d.nv && b2 < d.nv;
         const long long o1 = a1 * q.sa + b1 * q.sb, o2 = a2 * q.sa + b2 * q.sb;
-        const T v0 = in1 ? bij[o1] : T(0);
-        const T v1 = in1 ? bji[o1] : T(0);
-        const T v2 = in2 ? bij[o2] : T(0);
-        const T v3 = in2 ? bji[o2] : T(0);
-        ts[rr * ld + cc] = v0;
-        ts[(TA + rr) * ld + cc] = v1;
-        ts[(2 * TA + rr) * ld + cc] = v2;
-        ts[(3 * TA + rr) * ld + cc] = v3;
+        v[k][0] = in1 ? bij[o1] : T(0);
+        v[k][1] = in1 ? bji[o1] : T(0);
+        v[k][2] = in2 ? bij[o2] : T(0);
+        v[k][3] = in2 ? bji[o2] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kRpw; ++k) {
+        const int rr = warp + k * kRows;
+        if (rr < TA) {
+          ts[rr * ld + cc] = v[k][0];
+          ts[(TA + rr) * ld + cc] = v[k][1];
+          ts[(2 * TA + rr) * ld + cc] = v[k][2];
+          ts[(3 * TA + rr) * ld + cc] = v[k][3];
+        }
       }
     }
   }
   __syncthreads();
   T* res = tiles + d.nsrc * 4 * TA * ld;
-  const long long z = zx / d.nx;
+  const long long z = blk[5];
   const T* vb = static_cast<const T*>(d.vp) + z * d.vz + i * d.vi + j * d.vj;
   if (lane < TA) {
     const int cc = lane;

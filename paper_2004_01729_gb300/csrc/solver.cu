@@ -578,7 +578,6 @@ struct Solver {
 
   void alloc_chunk() {
     const long long o = no, v = nv, x = static_cast<long long>(nxc) * nz;
-    ensure(h_, tt, x * o * o * v * v * sizeof(T));
     ensure(h_, ta, x * o * o * v * v * sizeof(T));
     ensure(h_, X, x * o * o * v * v * sizeof(T));
     ensure(h_, Wmnij, x * o * o * o * o * sizeof(T));
@@ -601,28 +600,30 @@ struct Solver {
   void s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
     nx = nxcur;
     amp_begin(t1c, t2c);
-    T *ptt = (T*)tt.p, *pta = (T*)ta.p, *pX = (T*)X.p, *pWmnij = (T*)Wmnij.p, *pWabef = (T*)Wabef.p,
+    T *pta = (T*)ta.p, *pX = (T*)X.p, *pWmnij = (T*)Wmnij.p, *pWabef = (T*)Wabef.p,
       *pWmbej = (T*)Wmbej.p, *pY = (T*)Y.p, *pFae = (T*)Fae.p, *pFmi = (T*)Fmi.p, *pFme = (T*)Fme.p,
       *pFt = (T*)Ft.p, *pFt2 = (T*)Ft2.p, *pR = (T*)R.p, *pR2 = (T*)R2.p;
     using CT = Tn<const T>;
     auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
-    auto CF = [this](const char* L) { return Tn<const T>{F(L), L, true}; };
-    if (recording) tape.push_back(Op{2, ptt, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
-    timed_launch(kClsOther, 4.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
-                 [&] { CU(launch_tau<T>(t1c, t2c, ptt, pta, 0.5, 1.0, nz * nx, no, nv, st())); });
+    if (recording) tape.push_back(Op{2, nullptr, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
+    timed_launch(kClsOther, 3.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
+                 [&] { CU(launch_tau<T>(t1c, t2c, nullptr, pta, 0.5, 1.0, nz * nx, no, nv, st())); });
     // F_me = f_me + sum_nf s_n^f <mn||ef>
     scatter(pFme, "zxme", F("zme"), "zme", 1.0, 0.0, "");
     contract({pFme, "zxme"}, 1.0, CT{t1c, "zxnf"}, CV("zmnef"));
-    // F_ae = f_ae - 1/2 f_me s_m^a + s_m^f <ma||fe> - 1/2 tt_mn^af <mn||ef>
+    // The s1 s1 part of tau~ in F_ae and F_mi is -1/2 s_m^a (F_me - f_me) and
+    // +1/2 s_i^e (F_me - f_me); with the f_me terms they combine to F_me, and
+    // only s2 enters the quartic contractions (whose s2 pack the S1 term shares).
+    // F_ae = f_ae - 1/2 s_m^a F_me + s_m^f <ma||fe> - 1/2 s_mn^af <mn||ef>
     scatter(pFae, "zxae", F("zae"), "zae", 1.0, 0.0, "");
-    contract({pFae, "zxae"}, -0.5, CF("zme"), CT{t1c, "zxma"});
+    contract({pFae, "zxae"}, -0.5, CT{pFme, "zxme"}, CT{t1c, "zxma"});
     contract({pFae, "zxae"}, 1.0, CT{t1c, "zxmf"}, CV("zmafe"));
-    contract({pFae, "zxae"}, -0.5, CT{ptt, "zxmnaf"}, CV("zmnef"));
-    // F_mi = f_mi + 1/2 s_i^e f_me + s_n^e <mn||ie> + 1/2 tt_in^ef <mn||ef>
+    contract({pFae, "zxaf"}, -0.5, CT{t2c, "zxmnae"}, CV("zmnfe"));
+    // F_mi = f_mi + 1/2 s_i^e F_me + s_n^e <mn||ie> + 1/2 s_in^ef <mn||ef>
     scatter(pFmi, "zxmi", F("zmi"), "zmi", 1.0, 0.0, "");
-    contract({pFmi, "zxmi"}, 0.5, CT{t1c, "zxie"}, CF("zme"));
+    contract({pFmi, "zxmi"}, 0.5, CT{t1c, "zxie"}, CT{pFme, "zxme"});
     contract({pFmi, "zxmi"}, 1.0, CT{t1c, "zxne"}, CV("zmnie"));
-    contract({pFmi, "zxmi"}, 0.5, CT{ptt, "zxinef"}, CV("zmnef"));
+    contract({pFmi, "zxmi"}, 0.5, CT{t2c, "zxinef"}, CV("zmnef"));
     // S2 is assembled as P(ij)P(ab) R + <ab||ij> with R = R1 + R2 (below).
     // A contribution X that is already antisymmetric in ij enters R as X/2
     // when the paper applies P(ab) to it (P(ij)P(ab) X = 2 P(ab) X), likewise
@@ -739,7 +740,7 @@ struct Solver {
   void vjp(const T* t1c, const T* t2c, T* w1, T* w2, T* t1bar, T* t2bar, int nxcur) {
     const long long o = no, v = nv, x = static_cast<long long>(nxcur) * nz;
     // adjoint buffers sized like the chunk intermediates
-    Buf* pairs[][2] = {{&btt, &tt}, {&bta, &ta}, {&bX, &X}, {&bWmnij, &Wmnij}, {&bWabef, &Wabef}, {&bWmbej, &Wmbej},
+    Buf* pairs[][2] = {{&bta, &ta}, {&bX, &X}, {&bWmnij, &Wmnij}, {&bWabef, &Wabef}, {&bWmbej, &Wmbej},
                        {&bY, &Y}, {&bFae, &Fae}, {&bFmi, &Fmi}, {&bFme, &Fme}, {&bFt, &Ft}, {&bFt2, &Ft2},
                        {&bR, &R}, {&bR2, &R2}};
     for (auto& pr : pairs) {
@@ -814,17 +815,17 @@ struct Solver {
         }
         if (op.beta == 0.0) zero(db, op.Lc.c_str());
       } else if (op.kind == 2) {
-        // tt = t2 + 1/2 p, ta = t2 + p, p_ijab = t_ia t_jb - t_ib t_ja
-        T* ttb = adj(op.C);
+        // tt = t2 + 1/2 p (when built), ta = t2 + p, p_ijab = t_ia t_jb - t_ib t_ja
+        T* ttb = op.C ? adj(op.C) : nullptr;
         T* tab = adj(op.C2);
         T* t2b = adj(op.B);
         T* t1b = adj(op.A);
         T* P = static_cast<T*>(bP.p);
         T* Q = static_cast<T*>(bQ.p);
-        scatter(t2b, "zxijab", ttb, "zxijab", 1.0, 1.0, "");
+        if (ttb) scatter(t2b, "zxijab", ttb, "zxijab", 1.0, 1.0, "");
         scatter(t2b, "zxijab", tab, "zxijab", 1.0, 1.0, "");
         scatter(P, "zxijab", tab, "zxijab", 1.0, 0.0, "");
-        scatter(P, "zxijab", ttb, "zxijab", 0.5, 1.0, "");
+        if (ttb) scatter(P, "zxijab", ttb, "zxijab", 0.5, 1.0, "");
         scatter(Q, "zxijab", P, "zxijab", 1.0, 0.0, "ijab");
         contract({t1b, "zxkc"}, 1.0, CT{Q, "zxkjcb"}, CT{op.A, "zxjb"}, "", 1.0);
       } else {
