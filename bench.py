@@ -328,6 +328,20 @@ def run_gpu(args, rank, world):
             fl_u = flops_per_iteration(114, 114, c["ngrid"])
             ueg[prec] = {"s_per_iteration": t_it, "tensor_tflops": fl_u / t_it / 1e12,
                          "algorithmic_flops_per_iteration": fl_u}
+            # the contractions alone: one more iteration with per-launch events
+            ctx_u.profile(True)
+            ctx_u.iterate(1)
+            ks = ctx_u.profile_read()
+            ctx_u.profile(False)
+            g = [r for r in ks if r["name"] == "gemm_tc_kernel"]
+            if g and g[0]["ms"] > 0:
+                tf = g[0]["flops"] / (g[0]["ms"] * 1e-3) / 1e12
+                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
+                ueg[prec]["tensor_core_gemm"] = {
+                    "ms_per_iteration": g[0]["ms"], "tflops": tf, "peak_tflops": pk, "frac_of_peak": tf / pk,
+                    "peak_source": "measured bf16 burst x nominal tf32/bf16" if prec == "tf32"
+                    else "measured bf16 burst / 3 (three bf16 products per FP32-accurate one)",
+                    "share_of_iteration": g[0]["ms"] / sum(r["ms"] for r in ks)}
         ctx_u.close()
 
     # the 162-orbital gas (UEG, 81 plane waves, 40 tau points), streamed over
