@@ -43,6 +43,13 @@ def peaks():
 # nominal dense ratios of the recipe: tf32 1.1 PF vs bf16 2.25 PF
 TF32_PER_BF16 = 1.1 / 2.25
 
+# DRAM bytes (read + write) per launch of a kernel class in this step, from
+# one ncu capture of the current kernels (profiles/ gives the command); a
+# class missing here reports traffic null
+MEASURED_TRAFFIC = {
+    "gemm_tc_kernel": (67.3e6, "profiles/gemm_tc_kernel_hubbard10_tf32.md: mean over 231 launches"),
+}
+
 
 class Clocks:
     """Sample nvidia-smi during the timed region."""
@@ -429,7 +436,9 @@ def run_gpu(args, rank, world):
     else:
         roof = {"bound": None}
     if dom:
-        roof.update({"traffic": None, "kernel": dom["name"],
+        tr = MEASURED_TRAFFIC.get(dom["name"])
+        roof.update({"traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
+                     "kernel": dom["name"],
                      "launches_per_step": dom["launches"] / args.steps,
                      "avg_launch_us": dom["ms"] * 1e3 / dom["launches"],
                      "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
