@@ -107,13 +107,17 @@ typedef struct {
  *                       max(3, tau_chunk) slices plus the S-kernel intermediates
  *                       of tau_chunk points, instead of 2 ngrid + intermediates.
  *                       Single instance only; ft_ccsd_adjoint then returns
- *                       FTCC_ERR_UNSUPPORTED. */
+ *                       FTCC_ERR_UNSUPPORTED.
+ *   autotune   [1]      time the tensor-core tile width (32/64/128/256) and K split
+ *                       of each contraction shape once, on the first (uncaptured)
+ *                       iteration, and keep the fastest (0 = built-in choice) */
 typedef struct {
   double tol_omega, tol_amp, damping, trunc_thr;
   int max_iter, precision, refine_max_iter;
   double tol_mixed;
   int tau_chunk, use_graph;
   int stream_tau;
+  int autotune;
 } ftcc_options;
 
 typedef struct {

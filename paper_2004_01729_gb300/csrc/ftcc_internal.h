@@ -43,6 +43,7 @@ struct GemmArgs {
   void* C; long long ldc, sc;
   double alpha, beta;
   int trans;                          // 1: C stored transposed, element (m, n) at C[b*sc + n*ldc + m]
+  int bn, split;                      // tensor-core tile width and K splits (0: the built-in choice)
 };
 // Tensor-core GEMM (tcgen05 + TMA).  kind TF32: A, B, C float.  kind BF16X3:
 // A, A2, B, B2 __nv_bfloat16 (hi, lo), C float.  Returns cudaSuccess or an error.
@@ -124,12 +125,10 @@ template <class T> cudaError_t launch_pack(const T* src, T* dst, const PackDesc&
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st);
 template <class T> cudaError_t launch_scatter(const T* src, T* dst, const ScatDesc& d, double alpha,
                                               double beta, cudaStream_t st);
-// tt = t2 + c_tt * (t1 t1 antisymmetrised), ta likewise with c_ta (either output may be null)
-template <class T> cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double c_tt, double c_ta,
+// tt = t2 + c_tt * (t1 t1 antisymmetrised), ta likewise with c_ta, and
+// X_ijab = 1/2 t2_ijab + t1_ia t1_jb (any output may be null), one read of t2
+template <class T> cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, T* X, double c_tt, double c_ta,
                                           int nx, int no, int nv, cudaStream_t st);
-// X[x,j,n,f,b] = 0.5 t2[x,j,n,f,b] + t1[x,j,f] t1[x,n,b]
-template <class T> cudaError_t launch_xbuild(const T* t1, const T* t2, T* X, int nx, int no, int nv,
-                                             cudaStream_t st);
 template <class Ts, class Td> cudaError_t launch_convert(const Ts* s, Td* d, long long n, cudaStream_t st);
 
 // ---- physics (App. A) ----
@@ -159,6 +158,7 @@ struct PropArgs {
   FastDiv fo, fv;                // filled by the launcher
   const int* idxO; const int* idxV;
   const double* em; const double* ep;   // [nz][N]
+  const void* emT; const void* epT;     // the same tables in the amplitude type (forward sweep)
   const double* hz;              // [nz] grid steps
   const int* live;               // [nz] 0 = instance frozen (diverged), or null
   double damping;

@@ -495,11 +495,14 @@ cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
   // split K when the output tiles cannot fill half the SMs and the K loop is long
   int splits = 1;
   const long long outer = static_cast<long long>(g.M) * g.N * g.batch;
-  if (g.work && tiles * 2 < sms && nk >= 8) {
+  if (g.split > 0) {
+    splits = std::min(g.split, std::max(1, nk));   // a tuned choice
+  } else if (g.work && tiles * 2 < sms && nk >= 8) {
     splits = static_cast<int>(std::min<long long>((sms + tiles - 1) / tiles, nk / 4));
     splits = std::min(splits, 32);
-    while (splits > 1 && static_cast<size_t>(splits) * outer * sizeof(float) > g.work_bytes) --splits;
   }
+  if (!g.work) splits = 1;
+  while (splits > 1 && static_cast<size_t>(splits) * outer * sizeof(float) > g.work_bytes) --splits;
   const int kc = (nk + splits - 1) / splits;
   splits = (nk + kc - 1) / kc;
   const int grid = static_cast<int>(std::min<long long>(tiles * splits, sms));
@@ -526,7 +529,8 @@ cudaError_t gemm_tc(int kind, const GemmArgs& g, int* dev_err, cudaStream_t st) 
   if (g.batch > 65535) return cudaErrorInvalidValue;
   // tile width: the narrowest of 32 / 64 / 128 / 256 columns that covers N (tcgen05 with
   // M = 128 takes N in steps of 16 up to 256)
-  const int bn = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256));
+  const int bn = g.bn ? g.bn : (g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256)));
+  if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return cudaErrorInvalidValue;
   if (kind == GEMM_TF32) {
     switch (bn) {
       case 32: return launch_tc<GEMM_TF32, 32>(g, dev_err, st);

@@ -265,22 +265,25 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
   // each thread issues all of its loads (up to 4 rows x 4 orientations of a
   // source) before it stores any of them
   constexpr int kRpw = kAT / kRows;   // rows per warp at most
+  const int nv = d.nv;
   if (lane < TA) {
     const int cc = lane;
     for (int s = 0; s < d.nsrc; ++s) {
       const AntiSrc& q = d.src[s];
+      // offsets inside one zx slice fit in 32 bits (checked by the launcher)
+      const int sa = static_cast<int>(q.sa), sb = static_cast<int>(q.sb);
       const T* base = static_cast<const T*>(q.p) + zx * q.sx;
-      const T* bij = base + i * q.si + j * q.sj;
-      const T* bji = base + j * q.si + i * q.sj;
+      const T* bij = base + (i * static_cast<int>(q.si) + j * static_cast<int>(q.sj));
+      const T* bji = base + (j * static_cast<int>(q.si) + i * static_cast<int>(q.sj));
       T* ts = tiles + s * 4 * TA * ld;
       T v[kRpw][4];
+      const int b1 = B0 + cc, b2 = A0 + cc;   // columns of the (AB) and (BA) orientations
 #pragma unroll
       for (int k = 0; k < kRpw; ++k) {
         const int rr = warp + k * kRows;
-        const int a1 = A0 + rr, b1 = B0 + cc;   // (AB) orientations
-        const int a2 = B0 + rr, b2 = A0 + cc;   // (BA) orientations
-        const bool in1 = rr < TA && a1 < d.nv && b1 < d.nv, in2 = rr < TA && a2 < d.nv && b2 < d.nv;
-        const long long o1 = a1 * q.sa + b1 * q.sb, o2 = a2 * q.sa + b2 * q.sb;
+        const int a1 = A0 + rr, a2 = B0 + rr;
+        const bool in1 = rr < TA && a1 < nv && b1 < nv, in2 = rr < TA && a2 < nv && b2 < nv;
+        const int o1 = a1 * sa + b1 * sb, o2 = a2 * sa + b2 * sb;
         v[k][0] = in1 ? bij[o1] : T(0);
         v[k][1] = in1 ? bji[o1] : T(0);
         v[k][2] = in2 ? bij[o2] : T(0);
@@ -302,45 +305,49 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
   T* res = tiles + d.nsrc * 4 * TA * ld;
   const long long z = blk[5];
   const T* vb = static_cast<const T*>(d.vp) + z * d.vz + i * d.vi + j * d.vj;
+  const T c0 = static_cast<T>(d.src[0].coef), c1 = static_cast<T>(d.src[1].coef);
+  const int va = static_cast<int>(d.va), vbs = static_cast<int>(d.vb);
   if (lane < TA) {
     const int cc = lane;
     for (int rr = warp; rr < TA; rr += kRows) {
       const int a = A0 + rr, b = B0 + cc;
       T v = T(0);
-      if (a < d.nv && b < d.nv) {
-        for (int s = 0; s < d.nsrc; ++s) {
-          const T* t0 = tiles + s * 4 * TA * ld;
-          const T x = (t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
-                      (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]);
-          v += static_cast<T>(d.src[s].coef) * x;
+      if (a < nv && b < nv) {
+        const T* t0 = tiles;
+        v = c0 * ((t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
+                  (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]));
+        if (d.nsrc > 1) {
+          t0 += 4 * TA * ld;
+          v += c1 * ((t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
+                     (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]));
         }
-        if (d.vp) v += vb[a * d.va + b * d.vb];
+        if (d.vp) v += vb[a * va + b * vbs];
       }
       res[rr * ld + cc] = v;
     }
   }
   __syncthreads();
-  const long long so = static_cast<long long>(d.nv) * d.nv, sj = so, si = static_cast<long long>(d.no) * so;
+  const long long so = static_cast<long long>(nv) * nv, sj = so, si = static_cast<long long>(d.no) * so;
   T* out = dst + zx * d.no * si;
-  T* oij = out + i * si + j * sj;
-  T* oji = out + j * si + i * sj;
+  T* oij = out + (i * si + j * sj);
+  T* oji = out + (j * si + i * sj);
   if (lane < TA) {
     const int cc = lane;
     for (int rr = warp; rr < TA; rr += kRows) {
       {
         const int a = A0 + rr, b = B0 + cc;   // (A, B) orientation: rows along b
-        if (a < d.nv && b < d.nv) {
+        if (a < nv && b < nv) {
           const T v = res[rr * ld + cc];
-          oij[a * d.nv + b] = v;
-          if (i != j) oji[a * d.nv + b] = -v;
+          oij[a * nv + b] = v;
+          if (i != j) oji[a * nv + b] = -v;
         }
       }
       if (tA != tB) {
         const int a = B0 + rr, b = A0 + cc;   // (B, A) orientation: the transposed tile
-        if (a < d.nv && b < d.nv) {
+        if (a < nv && b < nv) {
           const T v = res[cc * ld + rr];
-          oij[a * d.nv + b] = -v;
-          if (i != j) oji[a * d.nv + b] = v;
+          oij[a * nv + b] = -v;
+          if (i != j) oji[a * nv + b] = v;
         }
       }
     }
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
 // One tau slice per blockIdx.y; element e = ((i o + j) v + a) v + b.
 template <class T>
 __global__ void tau_kernel(const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ tt,
-                           T* __restrict__ ta, T ctt, T cta, FastDiv fo, FastDiv fv) {
+                           T* __restrict__ ta, T* __restrict__ X, T ctt, T cta, FastDiv fo, FastDiv fv) {
   const uint32_t no = fo.d, nv = fv.d;
   const uint32_t slice = no * no * nv * nv;
   const long long x = blockIdx.y;
@@ -372,30 +379,7 @@ __global__ void tau_kernel(const T* __restrict__ t1, const T* __restrict__ t2, T
     const T v = t2[o];
     if (tt) tt[o] = v + ctt * p;
     if (ta) ta[o] = v + cta * p;
-  }
-}
-
-// X[x,j,n,f,b] = 1/2 t2[x,j,n,f,b] + t1[x,j,f] t1[x,n,b]
-template <class T>
-__global__ void xbuild_kernel(const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ X, FastDiv fo,
-                              FastDiv fv) {
-  const uint32_t no = fo.d, nv = fv.d;
-  const uint32_t slice = no * no * nv * nv;
-  const long long x = blockIdx.y;
-  const T* s = t1 + x * no * nv;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < slice; e += gridDim.x * blockDim.x) {
-    uint32_t r = e;
-    uint32_t q = fdiv(fv, r);
-    const uint32_t b = r - q * nv;
-    r = q;
-    q = fdiv(fv, r);
-    const uint32_t f = r - q * nv;
-    r = q;
-    q = fdiv(fo, r);
-    const uint32_t n = r - q * no;
-    const uint32_t j = q;
-    const long long o = x * slice + e;
-    X[o] = T(0.5) * t2[o] + s[j * nv + f] * s[n * nv + b];
+    if (X) X[o] = T(0.5) * v + s[i * nv + a] * s[j * nv + b];   // X_ijab = 1/2 t2 + t1_ia t1_jb
   }
 }
 
@@ -607,8 +591,11 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
   S += static_cast<long long>(z) * a.s_ng * size;     // S[(y - y0) * size + mu]
   t += static_cast<long long>(z) * ng * size;
   T* chain = a.chain ? static_cast<T*>(a.chain) + static_cast<long long>(z) * 5 * size : nullptr;
-  const double* em = a.em + static_cast<long long>(z) * a.N;
-  const double* ep = a.ep + static_cast<long long>(z) * a.N;
+  // per-orbital factors e^{-eps h}, e^{+eps h} in the amplitude type: the
+  // element ratios are products of four of them (no FP64 work per element
+  // in the FP32 sweep)
+  const T* em = static_cast<const T*>(a.emT) + static_cast<long long>(z) * a.N;
+  const T* ep = static_cast<const T*>(a.epT) + static_cast<long long>(z) * a.N;
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
   const long long n1 = static_cast<long long>(a.no) * a.nv;
   const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * n1 : nullptr;
@@ -641,17 +628,16 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
       }
     }
     const int pi = a.idxO[i], pa = a.idxV[aa];
-    double rr = em[pa] * ep[pi];
-    double ri = ep[pa] * em[pi];
+    T r1 = em[pa] * ep[pi];
+    T rinv = ep[pa] * em[pi];
     if (NS == 4) {
       const int pj = a.idxO[j], pb = a.idxV[b];
-      rr *= em[pb] * ep[pj];
-      ri *= ep[pb] * em[pj];
+      r1 *= em[pb] * ep[pj];
+      rinv *= ep[pb] * em[pj];
     }
     // The recurrence runs in the storage precision: FP32 storage carries
     // ~1e-7 relative error anyway, and FP64 issue rate is a small fraction
     // of FP32 on this part.  FP64 storage keeps everything in FP64.
-    const T r1 = static_cast<T>(rr), rinv = static_cast<T>(ri);
     const T w = wE ? static_cast<T>(wE[mu]) : T(0);
     const T r2 = r1 * r1, r3 = r2 * r1;
     // S_0..S_2 are needed together at y = 1; a launch that starts at 0
@@ -1377,6 +1363,8 @@ template <class T>
 cudaError_t launch_antisym4(T* dst, const Anti4Desc& d, cudaStream_t st) {
   if (d.nzx <= 0 || d.no <= 0 || d.nv <= 0) return cudaSuccess;
   if (d.nsrc < 1 || d.nsrc > 2 || d.nx < 1) return cudaErrorInvalidValue;
+  // element offsets inside one zx slice (and inside one V block) are 32-bit in the kernel
+  if (static_cast<long long>(d.no) * d.no * d.nv * d.nv >= (1LL << 31)) return cudaErrorInvalidValue;
   Anti4Desc dd = d;
   dd.ta = std::min(kAT, d.nv);   // a tile spans the whole a/b range when it is short
   const long long nA = (d.nv + dd.ta - 1) / dd.ta;
@@ -1398,30 +1386,21 @@ template cudaError_t launch_antisym4<float>(float*, const Anti4Desc&, cudaStream
 template cudaError_t launch_antisym4<double>(double*, const Anti4Desc&, cudaStream_t);
 
 template <class T>
-cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, double ctt, double cta, int nx, int no, int nv,
+cudaError_t launch_tau(const T* t1, const T* t2, T* tt, T* ta, T* X, double ctt, double cta, int nx, int no, int nv,
                        cudaStream_t st) {
   const long long slice = static_cast<long long>(no) * no * nv * nv;
   if (slice >= (1LL << 31) || nx > 65535) return cudaErrorInvalidValue;
   dim3 grid(grid_for(slice, 256, 2048), nx);
-  tau_kernel<T><<<grid, 256, 0, st>>>(t1, t2, tt, ta, static_cast<T>(ctt), static_cast<T>(cta), make_fastdiv(no),
+  tau_kernel<T><<<grid, 256, 0, st>>>(t1, t2, tt, ta, X, static_cast<T>(ctt), static_cast<T>(cta), make_fastdiv(no),
                                       make_fastdiv(nv));
   return cudaGetLastError();
 }
-template cudaError_t launch_tau<float>(const float*, const float*, float*, float*, double, double, int, int, int,
+template cudaError_t launch_tau<float>(const float*, const float*, float*, float*, float*, double, double, int, int, int,
                                        cudaStream_t);
-template cudaError_t launch_tau<double>(const double*, const double*, double*, double*, double, double, int, int, int,
+template cudaError_t launch_tau<double>(const double*, const double*, double*, double*, double*, double, double, int,
+                                        int, int,
                                         cudaStream_t);
 
-template <class T>
-cudaError_t launch_xbuild(const T* t1, const T* t2, T* X, int nx, int no, int nv, cudaStream_t st) {
-  const long long slice = static_cast<long long>(no) * no * nv * nv;
-  if (slice >= (1LL << 31) || nx > 65535) return cudaErrorInvalidValue;
-  dim3 grid(grid_for(slice, 256, 2048), nx);
-  xbuild_kernel<T><<<grid, 256, 0, st>>>(t1, t2, X, make_fastdiv(no), make_fastdiv(nv));
-  return cudaGetLastError();
-}
-template cudaError_t launch_xbuild<float>(const float*, const float*, float*, int, int, int, cudaStream_t);
-template cudaError_t launch_xbuild<double>(const double*, const double*, double*, int, int, int, cudaStream_t);
 
 template <class Ts, class Td>
 cudaError_t launch_convert(const Ts* s, Td* d, long long n, cudaStream_t st) {

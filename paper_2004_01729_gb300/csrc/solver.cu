@@ -7,6 +7,7 @@
 // an instance index z in front, so one launch of each contraction serves the
 // whole batch and one CUDA graph replays an iteration of all instances.
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -141,7 +142,7 @@ struct Batch {
   int nz = 0, N = 0, no = 0, nv = 0, ng = 0, prec = 0;
   ftcc_options opt{};
   std::vector<int> O, V;
-  Buf idxO, idxV, em, ep, hz, V64, F64, state, live;
+  Buf idxO, idxV, em, ep, emf, epf, hz, V64, F64, state, live;
   std::vector<int> live_host;     // 0 once an instance diverged (frozen, reported DIVERGED)
   std::unique_ptr<Solver<float>> s32;
   std::unique_ptr<Solver<double>> s64;
@@ -257,7 +258,7 @@ struct Solver {
       h_->put(kv.second.second);
     }
     Buf* bs[] = {&t1, &t2, &S1, &S2, &ch1, &ch2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
-                 &R, &R2, &bR, &bR2,
+                 &R, &R2, &bR, &bR2, &tuneC,
                  &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2, &btt, &bta, &bX, &bWmnij, &bWabef, &bWmbej,
                  &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
@@ -559,6 +560,7 @@ struct Solver {
     ensure(h_, skw, 64u << 20);   // split-K partials (SIMT and tensor-core kernels)
     g.work = skw.p;
     g.work_bytes = skw.bytes;
+    if (kind == GEMM_TF32 || kind == GEMM_BF16X3) tune_tc(kind, g, nb * m * n * sizeof(T));
     const double es = kind == GEMM_BF16X3 ? 4.0 : static_cast<double>(sizeof(T));   // hi + lo halves
     const double gbytes = static_cast<double>(nb) * ((m + n) * k * es + m * n * sizeof(T) * (g.beta != 0.0 ? 2 : 1));
     const double gflops = 2.0 * nb * m * n * k;
@@ -574,6 +576,72 @@ struct Solver {
       scatter(C.p, C.L, static_cast<const T*>(Ct.p), Lt.c_str(), alpha, beta_acc, anti);
       recording = rec;
     }
+  }
+
+  // Tile-width / split-K autotuner for the tensor-core GEMM.  The first time
+  // a shape (kind, batch, M, N, K, output order, accumulate or not) is met
+  // outside a stream capture, every candidate (tile width 32 / 64 / 128 / 256
+  // columns x built-in or no K split) runs twice on a scratch output and
+  // the fastest second run is kept for that shape; later calls (and the
+  // captured graph) use it.  Shapes whose output exceeds 512 MB or whose work
+  // exceeds 2 TFLOP keep the built-in choice, where the tile shape matters
+  // least and a trial run costs the most.
+  struct TuneKey {
+    int kind, nb, m, n, k, trans, acc;
+    bool operator<(const TuneKey& o) const {
+      return std::tie(kind, nb, m, n, k, trans, acc) < std::tie(o.kind, o.nb, o.m, o.n, o.k, o.trans, o.acc);
+    }
+  };
+  std::map<TuneKey, std::pair<int, int>> tuned;
+  Buf tuneC;
+  int tuned_shapes = 0;
+  void tune_tc(int kind, GemmArgs& g, size_t out_bytes) {
+    if (!b->opt.autotune) return;
+    const TuneKey key{kind, g.batch, g.M, g.N, g.K, g.trans, g.beta != 0.0 ? 1 : 0};
+    auto it = tuned.find(key);
+    if (it != tuned.end()) {
+      g.bn = it->second.first;
+      g.split = it->second.second;
+      return;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(st(), &cs));
+    const double flops = 2.0 * g.batch * static_cast<double>(g.M) * g.N * g.K;
+    if (cs != cudaStreamCaptureStatusNone || out_bytes > (512u << 20) || flops > 2e12) return;
+    ensure(h_, tuneC, out_bytes);
+    CU(cudaMemsetAsync(tuneC.p, 0, out_bytes, st()));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    GemmArgs t = g;
+    t.C = tuneC.p;
+    float best = -1.0f;
+    std::pair<int, int> pick{0, 0};
+    for (int bn : {32, 64, 128, 256}) {
+      if (bn > 32 && g.N <= bn / 2) continue;   // mostly empty tiles
+      for (int split : {0, 1}) {
+        t.bn = bn;
+        t.split = split;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+          CU(cudaEventRecord(e0, st()));
+          CU(gemm_tc(kind, t, h_->dev_err, st()));
+          CU(cudaEventRecord(e1, st()));
+          CU(cudaEventSynchronize(e1));
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (best < 0.0f || ms < best) {
+          best = ms;
+          pick = {bn, split};
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tuned[key] = pick;
+    ++tuned_shapes;
+    g.bn = pick.first;
+    g.split = pick.second;
   }
 
   void alloc_chunk() {
@@ -605,9 +673,13 @@ struct Solver {
       *pFt = (T*)Ft.p, *pFt2 = (T*)Ft2.p, *pR = (T*)R.p, *pR2 = (T*)R2.p;
     using CT = Tn<const T>;
     auto CV = [this](const char* L) { return Tn<const T>{V(L), L, true}; };
-    if (recording) tape.push_back(Op{2, nullptr, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
+    // tau = s2 + P(ij) s1 s1 and X = 1/2 s2 + s1 s1 in one pass over s2
+    if (recording) {
+      tape.push_back(Op{2, nullptr, "", t1c, "", t2c, "", pta, 0.5, 1.0, ""});
+      tape.push_back(Op{3, pX, "", t1c, "", t2c, "", nullptr, 0.5, 1.0, ""});
+    }
     timed_launch(kClsOther, 3.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
-                 [&] { CU(launch_tau<T>(t1c, t2c, nullptr, pta, 0.5, 1.0, nz * nx, no, nv, st())); });
+                 [&] { CU(launch_tau<T>(t1c, t2c, nullptr, pta, pX, 0.5, 1.0, nz * nx, no, nv, st())); });
     // F_me = f_me + sum_nf s_n^f <mn||ef>
     scatter(pFme, "zxme", F("zme"), "zme", 1.0, 0.0, "");
     contract({pFme, "zxme"}, 1.0, CT{t1c, "zxnf"}, CV("zmnef"));
@@ -645,9 +717,6 @@ struct Solver {
     scatter(pWmbej, "zxjbme", V("zmbej"), "zmbej", 1.0, 0.0, "");
     contract({pWmbej, "zxjbme"}, 1.0, CT{t1c, "zxjf"}, CV("zmbef"));
     contract({pWmbej, "zxjbme"}, -1.0, CT{t1c, "zxnb"}, CV("zmnej"));
-    if (recording) tape.push_back(Op{3, pX, "", t1c, "", t2c, "", nullptr, 0.5, 1.0, ""});
-    timed_launch(kClsOther, 2.0 * nz * nx * no * no * nv * nv * sizeof(T), 0.0,
-                 [&] { CU(launch_xbuild<T>(t1c, t2c, pX, nz * nx, no, nv, st())); });
     contract({pWmbej, "zxjbme"}, -1.0, CT{pX, "zxjnfb"}, CV("zmnef"));
     // S1 (Eq. ccS1)
     scatter(S1c, "zxia", F("zai"), "zai", 1.0, 0.0, "");
@@ -848,7 +917,7 @@ Batch::~Batch() {
     Buf* bs[] = {&I.n, &I.nbar, &I.f, &I.fbar, &I.facO, &I.facV};
     for (Buf* q : bs) home->put(*q);
   }
-  Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
+  Buf* bs[] = {&idxO, &idxV, &em, &ep, &emf, &epf, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz};
   for (Buf* q : bs) home->put(*q);
 }
@@ -876,6 +945,7 @@ ftcc_options default_options() {
   o.tau_chunk = 0;
   o.use_graph = 1;
   o.stream_tau = 0;
+  o.autotune = 1;
   return o;
 }
 
@@ -988,6 +1058,8 @@ PropArgs prop_args(Batch& B, int nslot) {
   a.idxV = static_cast<const int*>(B.idxV.p);
   a.em = static_cast<const double*>(B.em.p);
   a.ep = static_cast<const double*>(B.ep.p);
+  a.emT = B.em.p;   // FP64 sweep and adjoint kernels; the FP32 sweep swaps in emf / epf
+  a.epT = B.ep.p;
   a.hz = static_cast<const double*>(B.hz.p);
   a.live = static_cast<const int*>(B.live.p);
   a.damping = B.opt.damping;
@@ -998,6 +1070,15 @@ PropArgs prop_args(Batch& B, int nslot) {
   a.s_ng = B.ng;
   a.chain = nullptr;
   return a;
+}
+
+// The propagator factors in the amplitude type of the sweep.
+template <class T>
+void set_tables(Batch& B, PropArgs& a) {
+  if (sizeof(T) == 4) {
+    a.emT = B.emf.p;
+    a.epT = B.epf.p;
+  }
 }
 
 // One application of the fixed-point map to every tau point of every instance.
@@ -1022,6 +1103,7 @@ void iterate_once(Batch& B, Solver<T>& s) {
       }
       for (int pass = 0; pass < 2; ++pass) {
         PropArgs a = prop_args(B, pass == 0 ? 2 : 4);
+        set_tables<T>(B, a);
         a.wE = static_cast<const double*>(pass == 0 ? B.F64.p : B.V64.p);
         a.cE = pass == 0 ? 1.0 : 0.25;
         a.t1E = pass == 0 ? nullptr : s.t1.p;
@@ -1051,6 +1133,7 @@ void iterate_once(Batch& B, Solver<T>& s) {
                static_cast<T*>(s.S2.p) + x0 * n2, nx);
   }
   PropArgs a = prop_args(B, 2);
+  set_tables<T>(B, a);
   a.wE = static_cast<const double*>(B.F64.p);
   a.cE = 1.0;
   a.t1E = nullptr;
@@ -1060,6 +1143,7 @@ void iterate_once(Batch& B, Solver<T>& s) {
   s.timed_launch(kClsPropagate, b1, 0.0,
                  [&] { CU(launch_propagate<T>(static_cast<const T*>(s.S1.p), static_cast<T*>(s.t1.p), a, B.home->st)); });
   a = prop_args(B, 4);
+  set_tables<T>(B, a);
   a.wE = static_cast<const double*>(B.V64.p);
   a.cE = 0.25;
   a.t1E = s.t1.p;
@@ -1250,7 +1334,7 @@ bool shell_grid(int n_pw, std::vector<int>& out) {
 ftcc_status check_options(ftcc_ctx* c, const ftcc_options& o) {
   if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.trunc_thr < 0 ||
       o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || o.stream_tau < 0 ||
-      o.stream_tau > 1 || !(o.tol_omega >= 0) ||
+      o.stream_tau > 1 || o.autotune < 0 || o.autotune > 1 || !(o.tol_omega >= 0) ||
       !(o.tol_amp >= 0) || !(o.tol_mixed >= 0))
     return fail(c, FTCC_ERR_INVALID_ARG, "options out of range");
   return FTCC_OK;
@@ -1363,6 +1447,13 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
                        home->st));
     sync(home);   // the host vectors fo / fv must outlive their copies
   }
+  // FP32 copies of the propagator factors for the FP32 sweep
+  ensure(home, B->emf, static_cast<size_t>(n) * N * sizeof(float));
+  ensure(home, B->epf, static_cast<size_t>(n) * N * sizeof(float));
+  CU(launch_convert<double, float>(static_cast<const double*>(B->em.p), static_cast<float*>(B->emf.p),
+                                   static_cast<long long>(n) * N, home->st));
+  CU(launch_convert<double, float>(static_cast<const double*>(B->ep.p), static_cast<float*>(B->epf.p),
+                                   static_cast<long long>(n) * N, home->st));
   CU(cudaMemcpyAsync(B->hz.p, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
   B->live_host.assign(n, 1);
   ensure(home, B->live, static_cast<size_t>(n) * sizeof(int));

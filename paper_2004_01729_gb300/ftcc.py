@@ -31,7 +31,8 @@ class Options(C.Structure):
     _fields_ = [("tol_omega", C.c_double), ("tol_amp", C.c_double), ("damping", C.c_double),
                 ("trunc_thr", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
                 ("refine_max_iter", C.c_int), ("tol_mixed", C.c_double), ("tau_chunk", C.c_int),
-                ("use_graph", C.c_int), ("stream_tau", C.c_int)]
+                ("use_graph", C.c_int), ("stream_tau", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class Result(C.Structure):
@@ -132,7 +133,8 @@ def _dptr(a):
 
 def default_options(**kw):
     o = Options(tol_omega=1e-10, tol_amp=1e-8, damping=1.0, trunc_thr=0.0, max_iter=200,
-                precision=PREC_FP64, refine_max_iter=8, tol_mixed=1e-7, tau_chunk=0, use_graph=1, stream_tau=0)
+                precision=PREC_FP64, refine_max_iter=8, tol_mixed=1e-7, tau_chunk=0, use_graph=1, stream_tau=0,
+                autotune=1)
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
