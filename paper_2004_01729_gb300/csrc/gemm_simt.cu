@@ -15,6 +15,10 @@ namespace {
 constexpr int kT = 64;
 constexpr int kK = 16;
 
+// fused multiply-add in the type of its arguments (fmaf for float)
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // blockIdx.z = batch * splits + split; with splits > 1 each block sums one
 // K range and writes alpha * partial to W[split][batch][M][N] (reduced later).
 template <class T>
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const T* __restrict__ A,
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma_t(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(const T* __restrict__ 
   for (int n = 0; n < N; ++n) {
     T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < kSkinny; ++k) acc = fma(a[k], Bs[n][k], acc);
+    for (int k = 0; k < kSkinny; ++k) acc = fma_t(a[k], Bs[n][k], acc);
     T* c = C + m * csm + n * csn;
     const T v = alpha * acc;
     *c = (beta == T(0)) ? v : v + beta * *c;

@@ -572,6 +572,10 @@ __global__ void thermal_fock_kernel(const double* __restrict__ fbar, int N, cons
 //   I_y = r^3 I_{y-3} + 3h/8 (r^3 S_{y-3} + 3 r^2 S_{y-2} + 3 r S_{y-1} + S_y)  (y odd >= 3)
 // which equals sum_x G[y,x] exp(Delta (tau_x - tau_y)) S_x for the Simpson
 // tensors (composite 1/3 for even y, 1/3 then 3/8 for odd y).  s_y = -I_y.
+// max(m, |x|) in the type of its arguments (fmaxf / fabsf for float)
+__device__ __forceinline__ float max_abs(float m, float x) { return fmaxf(m, fabsf(x)); }
+__device__ __forceinline__ double max_abs(double m, double x) { return fmax(m, fabs(x)); }
+
 constexpr int kPropThreads = 128;
 constexpr int kPropAhead = 2;   // tau steps of loads in flight per element
 
@@ -700,8 +704,8 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
       T stored = -I;
       if (damped) stored = (T(1) - damp) * old + damp * stored;
       *tq = stored;
-      dmax = fmax(dmax, fabs(stored - old));
-      smax = fmax(smax, fabs(stored));
+      dmax = max_abs(dmax, stored - old);   // in the storage type (no FP64 for FP32)
+      smax = max_abs(smax, stored);
       if (wE) {
         T e = cE * stored;
         if (NS == 4 && s1y) {
