@@ -413,6 +413,24 @@ def run_gpu(args, rank, world):
         bat64 = {"workload": "64 hubbard_1d instances, L in {6..14}, ngrid=24, batched per size class",
                  "s_total": t_b, "instances": len(cb), "converged": int(sum(r["converged"] for r in rb)),
                  "iterations_max": int(max(r["iterations"] for r in rb))}
+        # energies and entropies from the adjoint (one FP64 lambda sweep per
+        # size-class batch; a batch with a diverged member has none), for the
+        # 6- and 8-site classes, which keep the default run within minutes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_adj = 0
+        for x, q in zip(ctx_b, cb):
+            if q["L"] > 8:
+                continue
+            try:
+                x.adjoint(with_rdm1=False)
+                n_adj += 1
+            except ftcc.FTCCError:
+                pass
+        torch.cuda.synchronize()
+        bat64["adjoint_s_total"] = time.perf_counter() - t0
+        bat64["adjoint_instances"] = n_adj
+        bat64["adjoint_scope"] = "instances with L <= 8 (12 and 16 spin orbitals)"
         for x in ctx_b:
             x.close()
 

@@ -400,3 +400,52 @@ def prepare_batched(ctxs, betas, mus, ngrid, quad=QUAD_SIMPSON, **opts):
     if s != OK:
         raise FTCCError(s, "ftcc_prepare_batched: " + lib.ftcc_status_string(s).decode() + ": "
                         + lib.ftcc_last_error(ctxs[0].h).decode())
+
+
+def _omega_function():
+    """torch.autograd.Function for Omega(beta, mu, V) of a context's system
+    (built on first use so that importing this module needs no torch)."""
+    import torch
+
+    class FTCCOmega(torch.autograd.Function):
+        """Omega = Omega0 + Omega1 + Omega_CC of the system held by a Context,
+        as a differentiable function of beta, mu and a one-body perturbation V
+        (N x N, added to h with its diagonal also added to the reference
+        energies).  forward runs ft_ccsd_solve; backward runs the GPU lambda
+        sweep (ft_ccsd_adjoint) and returns dOmega/dbeta, dOmega/dmu (= -N)
+        and dOmega/dV_pq = rdm1[q, p] (App. B).  V = None leaves the system
+        as built; a V solves the perturbed system, rebuilt from the context's
+        first (unperturbed) system."""
+
+        @staticmethod
+        def forward(fctx, beta, mu, V, context, ngrid, opts):
+            if V is not None:
+                if not hasattr(context, "_base_system"):
+                    context._base_system = context.get_system()
+                h, eri, eps = context._base_system
+                v = V.detach().cpu().double().numpy()
+                context.build_generic(h + v, eri, eps + np.diag(v))
+            r = context.solve(float(beta), float(mu), int(ngrid), **(opts or {}))
+            fctx.context = context
+            fctx.has_v = V is not None
+            return torch.tensor(r["omega"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, g):
+            d, rdm = fctx.context.adjoint(with_rdm1=True)
+            gb = g * d["dOmega_dbeta"]
+            gm = g * d["dOmega_dmu"]
+            gv = g * torch.from_numpy(rdm.T.copy()) if fctx.has_v else None
+            return gb, gm, gv, None, None, None
+
+    return FTCCOmega
+
+
+def omega(context, beta, mu, ngrid, V=None, **opts):
+    """Differentiable Omega(beta, mu[, V]) (see _omega_function); beta and mu
+    may be torch scalars with requires_grad."""
+    import torch
+    f = _omega_function()
+    b = beta if torch.is_tensor(beta) else torch.tensor(float(beta), dtype=torch.float64)
+    m = mu if torch.is_tensor(mu) else torch.tensor(float(mu), dtype=torch.float64)
+    return f.apply(b, m, V, context, ngrid, opts)

@@ -145,3 +145,59 @@ def test_response_after_mixed_solve(ctx):
     ref = fc.response(sysd, beta, mu, ng, thr, solve_kw=dict(tol=1e-13, tol_amp=1e-11))
     assert abs(d["dOmega_dbeta"] - ref["dOmega_dbeta"]) < 1e-7
     assert abs(d["N"] - ref["N"]) < 1e-7
+
+
+def test_batched_adjoint_equals_single_instances():
+    """ft_ccsd_adjoint on the members of a batched solve: the lambda sweep
+    runs over the whole batch at once and every member gets the response of
+    its own single-instance solve (dOmega/dmu, dOmega/dbeta, E, S, 1-RDM)."""
+    from paper_2004_01729_gb300 import ftcc
+    L, U, ng = 6, 2.0, 12
+    betas, mus = [0.7, 1.0, 1.6], [1.0, 0.8, 1.2]
+    ctxs = []
+    for _ in betas:
+        c = ftcc.Context(0)
+        c.build_hubbard(L, 1.0, U)
+        ctxs.append(c)
+    res = ftcc.solve_batched(ctxs, betas, mus, ng, precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    assert all(r["converged"] for r in res)
+    got = [c.adjoint(with_rdm1=True) for c in ctxs]
+    one = ftcc.Context(0)
+    one.build_hubbard(L, 1.0, U)
+    for (d, rdm), b, m in zip(got, betas, mus):
+        one.solve(b, m, ng, precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+        e, erdm = one.adjoint(with_rdm1=True)
+        for k in ("dOmega_dmu", "dOmega_dbeta", "N", "E", "S"):
+            assert abs(d[k] - e[k]) < 1e-9, (k, d[k], e[k])
+        assert np.max(np.abs(rdm - erdm)) < 1e-9
+    for c in ctxs + [one]:
+        c.close()
+
+
+def test_autograd_omega_matches_adjoint_and_differences():
+    """ftcc.omega: Omega as a torch function whose backward is the GPU lambda
+    sweep; its beta, mu and one-body gradients agree with ft_ccsd_adjoint and
+    with central differences of GPU solves."""
+    from paper_2004_01729_gb300 import ftcc
+    c = ftcc.Context(0)
+    c.build_hubbard(6, 1.0, 2.0)
+    N = c.num_orbitals()
+    kw = dict(precision="fp64", tol_omega=1e-13, tol_amp=1e-11)
+    beta = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor(0.9, dtype=torch.float64, requires_grad=True)
+    V = torch.zeros((N, N), dtype=torch.float64, requires_grad=True)
+    om = ftcc.omega(c, beta, mu, 12, V=V, **kw)
+    om.backward()
+    d, rdm = c.adjoint(with_rdm1=True)
+    assert abs(beta.grad.item() - d["dOmega_dbeta"]) < 1e-12
+    assert abs(mu.grad.item() + d["N"]) < 1e-12
+    assert np.max(np.abs(V.grad.numpy() - rdm.T)) < 1e-12
+    step = 1e-4
+    fd_b = (ftcc.omega(c, 1.0 + step, 0.9, 12, V=V.detach(), **kw).item()
+            - ftcc.omega(c, 1.0 - step, 0.9, 12, V=V.detach(), **kw).item()) / (2 * step)
+    assert abs(fd_b - beta.grad.item()) < 1e-6
+    dv = torch.zeros((N, N), dtype=torch.float64)
+    dv[0, 1] = dv[1, 0] = step          # a symmetric off-diagonal one-body change
+    fd_v = (ftcc.omega(c, 1.0, 0.9, 12, V=dv, **kw).item() - ftcc.omega(c, 1.0, 0.9, 12, V=-dv, **kw).item()) / (2 * step)
+    assert abs(fd_v - (V.grad[0, 1] + V.grad[1, 0]).item()) < 1e-6
+    c.close()
