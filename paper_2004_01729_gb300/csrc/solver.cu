@@ -159,6 +159,7 @@ struct Batch {
   double ms_total = 0;
   int ms_count = 0;
   bool solved = false;
+  bool solved_live = false;   // every live member converged (diverged members are frozen)
   ~Batch();
 };
 
@@ -1568,6 +1569,7 @@ ftcc_status solve_batch(Batch& B) {
   int dead = 0;
   for (int z = 0; z < B.nz; ++z) dead += !B.live_host[z];
   B.solved = conv && dead == 0;
+  B.solved_live = conv && dead < B.nz;
   if (dead) return fail(h, FTCC_ERR_DIVERGED, "%d of %d instances diverged (frozen)", dead, B.nz);
   if (!conv) return fail(h, FTCC_ERR_NOT_CONVERGED, "not converged after %d iterations", B.iterations);
   return FTCC_OK;
@@ -1620,6 +1622,13 @@ int lambda_solve(Batch& B, double tol, int max_iter) {
   CU(cudaMemcpyAsync(B.cz.p, c.data(), c.size() * 8, cudaMemcpyHostToDevice, h->st));
   CU(cudaMemsetAsync(B.m1.p, 0, n1 * 8, h->st));
   CU(cudaMemsetAsync(B.m2.p, 0, n2 * 8, h->st));
+  // a member frozen after diverging takes no part: its amplitudes are set to
+  // zero so that its (unused) multipliers stay finite
+  for (long long z = 0; z < nz; ++z)
+    if (!B.live_host[z]) {
+      CU(cudaMemsetAsync(static_cast<double*>(s.t1.p) + z * ng * o * v, 0, ng * o * v * 8, h->st));
+      CU(cudaMemsetAsync(static_cast<double*>(s.t2.p) + z * ng * o * o * v * v, 0, ng * o * o * v * v * 8, h->st));
+    }
   // dE/ds1 without the weight: f_kc + sum_jb <kj||cb> s_j^b   (Eq. E)
   s.nx = s.ng;
   double* dE1 = static_cast<double*>(B.dE1.p);
@@ -2102,7 +2111,8 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
 
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1) {
   if (!c) return FTCC_ERR_INVALID_ARG;
-  if (!c->batch || !c->batch->solved) return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
+  if (!c->batch || !(c->batch->solved || (c->batch->solved_live && c->batch->live_host[c->member])))
+    return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
   if (c->batch->opt.stream_tau)
     return fail(c, FTCC_ERR_UNSUPPORTED, "the adjoint needs S at every tau point (solve without stream_tau)");
   return run_guarded(c, [&]() -> ftcc_status {

@@ -201,3 +201,35 @@ def test_autograd_omega_matches_adjoint_and_differences():
     fd_v = (ftcc.omega(c, 1.0, 0.9, 12, V=dv, **kw).item() - ftcc.omega(c, 1.0, 0.9, 12, V=-dv, **kw).item()) / (2 * step)
     assert abs(fd_v - (V.grad[0, 1] + V.grad[1, 0]).item()) < 1e-6
     c.close()
+
+
+def test_adjoint_of_live_members_beside_a_diverged_one():
+    """In a batch where one member diverges from s = 0 (and is frozen), the
+    other members still get their adjoint, equal to their single-instance
+    response; the diverged member's call is refused."""
+    from paper_2004_01729_gb300 import ftcc
+    cb = wl.hubbard_batch()
+    bad = cb[43]                          # 6 sites, U = 7.7, beta = 2.8: diverges from s = 0
+    good = next(q for q in cb if q["L"] == bad["L"] and q is not bad)
+    pair = [bad, good]
+    ctxs = []
+    for q in pair:
+        c = ftcc.Context(0)
+        c.build_hubbard(q["L"], q["t"], q["U"])
+        ctxs.append(c)
+    kw = dict(precision="tf32", refine_max_iter=30, max_iter=400)
+    res = ftcc.solve_batched(ctxs, [q["beta"] for q in pair], [q["mu"] for q in pair], bad["ngrid"],
+                             allow_unconverged=True, **kw)
+    assert not res[0]["converged"] and res[1]["converged"]
+    d, rdm = ctxs[1].adjoint(with_rdm1=True)
+    with pytest.raises(ftcc.FTCCError):
+        ctxs[0].adjoint(with_rdm1=False)
+    one = ftcc.Context(0)
+    one.build_hubbard(good["L"], good["t"], good["U"])
+    one.solve(good["beta"], good["mu"], good["ngrid"], **kw)
+    e, erdm = one.adjoint(with_rdm1=True)
+    for k in ("dOmega_dmu", "dOmega_dbeta", "E", "S"):
+        assert abs(d[k] - e[k]) < 1e-8, (k, d[k], e[k])
+    assert np.max(np.abs(rdm - erdm)) < 1e-8
+    for c in ctxs + [one]:
+        c.close()
