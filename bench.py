@@ -443,7 +443,12 @@ def run_gpu(args, rank, world):
                 "GB_per_s": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None,
                 "TFLOP_per_s": r["flops"] / (r["ms"] * 1e-3) / 1e12 if r["ms"] > 0 and r["flops"] else None}
                for r in sorted(kstats, key=lambda r: -r["ms"])]
-    if dom and dom["name"] == "gemm_tc_kernel":
+    # a contraction is tensor-bound only when its algorithmic intensity
+    # (flops per algorithmic byte) is above the ridge point peak_flops / peak_bw;
+    # below it the roofline ceiling is intensity x HBM bandwidth
+    ridge = tf32_peak * 1e12 / (hbm * 1e9)
+    intensity = dom["flops"] / dom["bytes"] if dom and dom["flops"] and dom["bytes"] else None
+    if dom and dom["name"] == "gemm_tc_kernel" and intensity is not None and intensity >= ridge:
         ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
                 "peak_source": f"bf16 burst {bf16} ({src}) x nominal tf32/bf16 {TF32_PER_BF16:.3f}"}
@@ -461,6 +466,10 @@ def run_gpu(args, rank, world):
                      "avg_launch_us": dom["ms"] * 1e3 / dom["launches"],
                      "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                      "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
+                     "intensity_flop_per_byte": intensity,
+                     "ridge_flop_per_byte": ridge,
+                     "tensor_frac": (dom["flops"] / (dom["ms"] * 1e-3) / 1e12 / tf32_peak
+                                     if dom["flops"] else None),
                      "timed_with": "CUDA events around every launch inside the per-iteration graph, "
                                    "a second pass of the same steps"})
     for ctx in ctx_mixed + ctx_fp64:

@@ -148,6 +148,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Output block of the epilogue: 32 rows x 32 FP32 columns from shared memory
+// (128-byte swizzle) to C[c2][c1][c0..c0+31] through the TMA unit; rows and
+// columns beyond the tensor's extent are not written.  `add` makes it a
+// reduce-add into C (C += block) performed in L2.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2,
+                                             bool add) {
+  if (add)
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// the TMA unit has finished reading this thread's earlier bulk-store sources
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and finished writing them
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the TMA unit
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -188,7 +215,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2,
                    float* __restrict__ C, int M, int N, int K, long long ldc, long long sc, int a_batched,
                    int b_batched, float alpha, float beta, int batch, int splits, int kc, float* __restrict__ W,
-                   int trans, int* err) {
+                   int trans, const __grid_constant__ CUtensorMap mC, int cmode, int* err) {
   using Cfg = TcCfg<KIND, BN>;
   constexpr int S = Cfg::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -199,7 +226,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-  float* epi = reinterpret_cast<float*>(smem + S * Cfg::kStageBytes + 256);   // 4 x 32 x 33 staging
+  float* epi = reinterpret_cast<float*>(smem + S * Cfg::kStageBytes + 256);   // 8 x 32 x 33 staging
+  // bulk-store staging (same region, 1024-byte aligned): 8 blocks of 32 x 128 bytes
+  float4* bulk = reinterpret_cast<float4*>(smem + S * Cfg::kStageBytes + 1024);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -358,6 +387,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           if (lane == 0) mbar_arrive(&tempty[acc]);
         }
         if (n0 + c >= N) continue;
+        if (cmode != 0) {
+          // cmode 1: C = alpha AB; cmode 2: C += alpha AB.  Thread = row: its
+          // 32 columns go to one 128-byte row of the block, 16-byte chunk j
+          // at position j ^ (row % 8) (the TMA 128-byte swizzle), so the
+          // eight threads of each quarter-warp store hit distinct banks.
+          const int row0 = m0 + q * 32;
+          if (row0 >= M) continue;
+          float4* blk = bulk + (warp - 2) * (32 * 8);
+          if (lane == 0) bulk_wait_read();   // the previous block has left this buffer
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            blk[lane * 8 + (j ^ (lane & 7))] =
+                make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
+                            alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) tma_store_3d(&mC, blk, n0 + c, row0, b, cmode == 2);
+          continue;
+        }
         if (trans && !part) {
           // C stored transposed: lanes are rows m, contiguous in memory
           const int row = m0 + q * 32 + lane;
@@ -406,6 +455,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         __syncwarp();
       }
     }
+    if (cmode != 0 && lane == 0) bulk_wait_all();   // every bulk store of this warp has landed
+    __syncwarp();
   }
   fence_before_sync();
   __syncthreads();
@@ -463,6 +514,23 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, long long K, long lon
   return r == CUDA_SUCCESS;
 }
 
+// 3D tiled map over C [batch][M][N] (N innermost, row stride ldc, batch stride
+// sc), box of 32 columns x 32 rows x 1, 128-byte swizzle: the epilogue's bulk
+// stores.  False when the layout breaks a TMA rule (16-byte aligned base and
+// strides); the epilogue then stores element by element.
+bool make_cmap(CUtensorMap* m, void* C, int M, int N, long long ldc, long long sc, int batch) {
+  if (reinterpret_cast<uintptr_t>(C) % 16 != 0 || ldc % 4 != 0 || ldc < N) return false;
+  if (batch > 1 && (sc % 4 != 0 || sc < static_cast<long long>(M) * ldc)) return false;
+  const long long bs = batch > 1 ? sc : static_cast<long long>(M) * ldc;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(M), static_cast<cuuint64_t>(batch)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldc * 4), static_cast<cuuint64_t>(((bs * 4 + 15) / 16) * 16)};
+  cuuint32_t box[3] = {32u, 32u, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int KIND, int BN>
 cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
   const bool bf = (KIND == GEMM_BF16X3);
@@ -506,10 +574,17 @@ cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
   const int kc = (nk + splits - 1) / splits;
   splits = (nk + kc - 1) / kc;
   const int grid = static_cast<int>(std::min<long long>(tiles * splits, sms));
+  // bulk (TMA) output stores for row-major outputs written in one pass with
+  // beta 0 (store) or 1 (reduce-add)
+  CUtensorMap mC = mA;
+  int cmode = 0;
+  if (splits == 1 && !g.trans && (g.beta == 0.0 || g.beta == 1.0) &&
+      make_cmap(&mC, g.C, g.M, g.N, g.ldc, g.sc, g.batch))
+    cmode = g.beta == 0.0 ? 1 : 2;
   gemm_tc_kernel<KIND, BN><<<grid, kGemmThreads, smem, st>>>(mA, mB, mA2, mB2, static_cast<float*>(g.C), g.M, g.N, g.K, g.ldc,
                                                     g.sc, g.sa > 0 ? 1 : 0, g.sb > 0 ? 1 : 0,
                                                     static_cast<float>(g.alpha), static_cast<float>(g.beta), g.batch,
-                                                    splits, kc, static_cast<float*>(g.work), g.trans, dev_err);
+                                                    splits, kc, static_cast<float*>(g.work), g.trans, mC, cmode, dev_err);
   if (splits > 1) {
     const int blocks = static_cast<int>(std::min<long long>((outer + 255) / 256, 152LL * 8));
     tc_splitk_reduce<<<blocks, 256, 0, st>>>(static_cast<const float*>(g.work), static_cast<float*>(g.C), g.ldc, g.sc,

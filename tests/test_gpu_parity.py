@@ -41,7 +41,10 @@ GEMM_TOL = {"fp64": 1e-13, "tf32": 4e-3, "bf16x3": 1e-4}
 @pytest.mark.parametrize("shape", [(1, 128, 128, 32), (1, 200, 130, 68), (3, 257, 129, 36), (2, 640, 384, 520),
                                    # narrow tiles (N <= 32 / 64) and split K (few output tiles, long K)
                                    (1, 400, 20, 8000), (4, 160, 40, 1200), (2, 300, 64, 64), (1, 130, 100, 4100),
-                                   (1, 64, 17, 12)])
+                                   (1, 64, 17, 12),
+                                   # outputs written by TMA bulk stores (row stride a multiple of 16 bytes),
+                                   # ragged in M and N, and a tile only partly inside M
+                                   (3, 333, 100, 72), (1, 96, 36, 40)])
 def test_gemm_matches_torch(ctx, prec, shape):
     b, M, N, K = shape
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
