@@ -233,8 +233,8 @@ __device__ __forceinline__ void upper_pair(int n, int p, int& i, int& j) {
   j = r + (p - start(r));
 }
 
-template <class T>
-__global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, Anti4Desc d) {
+template <class T, int KP>
+__global__ void __launch_bounds__(256, 4) antisym4_kernel(T* __restrict__ dst, Anti4Desc d) {
   extern __shared__ __align__(16) unsigned char as_smem[];
   T* tiles = reinterpret_cast<T*>(as_smem);   // [nsrc][4][TA][TA + 1], then the result [TA][TA + 1]
   const int TA = d.ta, ld = TA + 1, t2 = TA * TA;
@@ -257,46 +257,56 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
   const long long zx = blk[0];
   const int i = blk[1], j = blk[2], tA = blk[3], tB = blk[4];
   const int A0 = tA * TA, B0 = tB * TA;
-  // thread (row group, lane): lane = column cc of a tile, rows rr = warp,
-  // warp + 8, ...; no index division anywhere
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kRows = 8;   // warps per block (256 threads)
-  // the four orientations of every source: (ij,AB), (ji,AB), (ij,BA), (ji,BA);
-  // each thread issues all of its loads (up to 4 rows x 4 orientations of a
-  // source) before it stores any of them
-  constexpr int kRpw = kAT / kRows;   // rows per warp at most
+  // On a diagonal tile (A = B) the (BA) orientations are the (AB) tiles
+  // transposed: they are neither loaded nor stored twice.
+  const bool diag = tA == tB;
+  // thread -> up to KP tile elements e = threadIdx.x + 256 k (KP = the
+  // launcher's ceil(TA^2 / 256), so no thread carries idle element slots),
+  // row rr = e / TA and column cc = e % TA (the float quotient is exact for
+  // e < 1024, TA <= 32); all lanes work when TA < 32, and consecutive
+  // threads take consecutive columns, so every global access coalesces
+  constexpr int kPer = KP;
+  const float inv = 1.0f / static_cast<float>(TA);
+  int rr[kPer], cc[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    rr[k] = e < t2 ? static_cast<int>((static_cast<float>(e) + 0.5f) * inv) : TA;   // TA: no element
+    cc[k] = e - rr[k] * TA;
+  }
   const int nv = d.nv;
-  if (lane < TA) {
-    const int cc = lane;
-    for (int s = 0; s < d.nsrc; ++s) {
-      const AntiSrc& q = d.src[s];
-      // offsets inside one zx slice fit in 32 bits (checked by the launcher)
-      const int sa = static_cast<int>(q.sa), sb = static_cast<int>(q.sb);
-      const T* base = static_cast<const T*>(q.p) + zx * q.sx;
-      const T* bij = base + (i * static_cast<int>(q.si) + j * static_cast<int>(q.sj));
-      const T* bji = base + (j * static_cast<int>(q.si) + i * static_cast<int>(q.sj));
-      T* ts = tiles + s * 4 * TA * ld;
-      T v[kRpw][4];
-      const int b1 = B0 + cc, b2 = A0 + cc;   // columns of the (AB) and (BA) orientations
+  // the four orientations of every source: (ij,AB), (ji,AB), (ij,BA), (ji,BA);
+  // each thread issues all of its loads (up to 4 elements x 4 orientations of
+  // a source) before it stores any of them
+  for (int s = 0; s < d.nsrc; ++s) {
+    const AntiSrc& q = d.src[s];
+    // offsets inside one zx slice fit in 32 bits (checked by the launcher)
+    const int sa = static_cast<int>(q.sa), sb = static_cast<int>(q.sb);
+    const T* base = static_cast<const T*>(q.p) + zx * q.sx;
+    const T* bij = base + (i * static_cast<int>(q.si) + j * static_cast<int>(q.sj));
+    const T* bji = base + (j * static_cast<int>(q.si) + i * static_cast<int>(q.sj));
+    T* ts = tiles + s * 4 * TA * ld;
+    T v[kPer][4];
 #pragma unroll
-      for (int k = 0; k < kRpw; ++k) {
-        const int rr = warp + k * kRows;
-        const int a1 = A0 + rr, a2 = B0 + rr;
-        const bool in1 = rr < TA && a1 < nv && b1 < nv, in2 = rr < TA && a2 < nv && b2 < nv;
-        const int o1 = a1 * sa + b1 * sb, o2 = a2 * sa + b2 * sb;
-        v[k][0] = in1 ? bij[o1] : T(0);
-        v[k][1] = in1 ? bji[o1] : T(0);
-        v[k][2] = in2 ? bij[o2] : T(0);
-        v[k][3] = in2 ? bji[o2] : T(0);
-      }
+    for (int k = 0; k < kPer; ++k) {
+      const int a1 = A0 + rr[k], b1 = B0 + cc[k], a2 = B0 + rr[k], b2 = A0 + cc[k];
+      const bool in1 = rr[k] < TA && a1 < nv && b1 < nv;
+      const bool in2 = !diag && rr[k] < TA && a2 < nv && b2 < nv;
+      const int o1 = a1 * sa + b1 * sb, o2 = a2 * sa + b2 * sb;
+      v[k][0] = in1 ? bij[o1] : T(0);
+      v[k][1] = in1 ? bji[o1] : T(0);
+      v[k][2] = in2 ? bij[o2] : T(0);
+      v[k][3] = in2 ? bji[o2] : T(0);
+    }
 #pragma unroll
-      for (int k = 0; k < kRpw; ++k) {
-        const int rr = warp + k * kRows;
-        if (rr < TA) {
-          ts[rr * ld + cc] = v[k][0];
-          ts[(TA + rr) * ld + cc] = v[k][1];
-          ts[(2 * TA + rr) * ld + cc] = v[k][2];
-          ts[(3 * TA + rr) * ld + cc] = v[k][3];
+    for (int k = 0; k < kPer; ++k) {
+      if (rr[k] < TA) {
+        const int o = rr[k] * ld + cc[k];
+        ts[o] = v[k][0];
+        ts[TA * ld + o] = v[k][1];
+        if (!diag) {
+          ts[2 * TA * ld + o] = v[k][2];
+          ts[3 * TA * ld + o] = v[k][3];
         }
       }
     }
@@ -307,23 +317,23 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
   const T* vb = static_cast<const T*>(d.vp) + z * d.vz + i * d.vi + j * d.vj;
   const T c0 = static_cast<T>(d.src[0].coef), c1 = static_cast<T>(d.src[1].coef);
   const int va = static_cast<int>(d.va), vbs = static_cast<int>(d.vb);
-  if (lane < TA) {
-    const int cc = lane;
-    for (int rr = warp; rr < TA; rr += kRows) {
-      const int a = A0 + rr, b = B0 + cc;
+  const int off2 = diag ? 0 : 2 * TA, off3 = diag ? TA : 3 * TA;   // where the (BA) tiles live
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int r = rr[k], c = cc[k];
+    if (r < TA) {
+      const int a = A0 + r, b = B0 + c;
       T v = T(0);
       if (a < nv && b < nv) {
         const T* t0 = tiles;
-        v = c0 * ((t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
-                  (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]));
+        v = c0 * ((t0[r * ld + c] - t0[(TA + r) * ld + c]) - (t0[(off2 + c) * ld + r] - t0[(off3 + c) * ld + r]));
         if (d.nsrc > 1) {
           t0 += 4 * TA * ld;
-          v += c1 * ((t0[rr * ld + cc] - t0[(TA + rr) * ld + cc]) -
-                     (t0[(2 * TA + cc) * ld + rr] - t0[(3 * TA + cc) * ld + rr]));
+          v += c1 * ((t0[r * ld + c] - t0[(TA + r) * ld + c]) - (t0[(off2 + c) * ld + r] - t0[(off3 + c) * ld + r]));
         }
         if (d.vp) v += vb[a * va + b * vbs];
       }
-      res[rr * ld + cc] = v;
+      res[r * ld + c] = v;
     }
   }
   __syncthreads();
@@ -331,21 +341,22 @@ __global__ void __launch_bounds__(256, 5) antisym4_kernel(T* __restrict__ dst, A
   T* out = dst + zx * d.no * si;
   T* oij = out + (i * si + j * sj);
   T* oji = out + (j * si + i * sj);
-  if (lane < TA) {
-    const int cc = lane;
-    for (int rr = warp; rr < TA; rr += kRows) {
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int r = rr[k], c = cc[k];
+    if (r < TA) {
       {
-        const int a = A0 + rr, b = B0 + cc;   // (A, B) orientation: rows along b
+        const int a = A0 + r, b = B0 + c;   // (A, B) orientation
         if (a < nv && b < nv) {
-          const T v = res[rr * ld + cc];
+          const T v = res[r * ld + c];
           oij[a * nv + b] = v;
           if (i != j) oji[a * nv + b] = -v;
         }
       }
-      if (tA != tB) {
-        const int a = B0 + rr, b = A0 + cc;   // (B, A) orientation: the transposed tile
+      if (!diag) {
+        const int a = B0 + r, b = A0 + c;   // (B, A) orientation: the transposed tile
         if (a < nv && b < nv) {
-          const T v = res[cc * ld + rr];
+          const T v = res[c * ld + r];
           oij[a * nv + b] = -v;
           if (i != j) oji[a * nv + b] = v;
         }
@@ -726,15 +737,20 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
       chain[4 * size + mu] = sm3;
     }
   }
-  __shared__ double dm[kPropThreads], sm[kPropThreads];
-  dm[threadIdx.x] = static_cast<double>(dmax);
-  sm[threadIdx.x] = static_cast<double>(smax);
+  // The block's own reductions run in the storage type: maxima are exact in
+  // any type, and FP64 arithmetic issues at a small fraction of the FP32 rate
+  // on this part, so an FP64 tree over 32 tau points x 128 slots per block
+  // would cost as much as the propagation itself.  Only the per-block
+  // results are widened; the sum over blocks is FP64.
+  __shared__ T dm[kPropThreads], sm[kPropThreads];
+  dm[threadIdx.x] = dmax;
+  sm[threadIdx.x] = smax;
   __syncthreads();
   // deterministic tree reductions
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      dm[threadIdx.x] = fmax(dm[threadIdx.x], dm[threadIdx.x + s]);
-      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+      dm[threadIdx.x] = max_abs(dm[threadIdx.x], dm[threadIdx.x + s]);
+      sm[threadIdx.x] = max_abs(sm[threadIdx.x], sm[threadIdx.x + s]);
     }
     __syncthreads();
   }
@@ -744,14 +760,15 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
   const long long nbk = a.nblocks;
   double* p = partials + blockIdx.x;
   for (int y = y0 + warp; y < y1; y += kPropThreads / 32) {
-    double acc = 0.0;
-    for (int k = lane; k < kPropThreads; k += 32) acc += static_cast<double>(eacc[y * kPropThreads + k]);
+    T acc = T(0);
+    for (int k = lane; k < kPropThreads; k += 32) acc += eacc[y * kPropThreads + k];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (lane == 0) p[y * nbk] = acc;
+    if (lane == 0) p[y * nbk] = static_cast<double>(acc);
   }
   if (threadIdx.x == 0) {   // maxima over the launches of one iteration
-    p[ng * nbk] = y0 == 0 ? dm[0] : fmax(p[ng * nbk], dm[0]);
-    p[(ng + 1) * nbk] = y0 == 0 ? sm[0] : fmax(p[(ng + 1) * nbk], sm[0]);
+    const double d0 = static_cast<double>(dm[0]), s0 = static_cast<double>(sm[0]);
+    p[ng * nbk] = y0 == 0 ? d0 : fmax(p[ng * nbk], d0);
+    p[(ng + 1) * nbk] = y0 == 0 ? s0 : fmax(p[(ng + 1) * nbk], s0);
   }
 }
 
@@ -1034,7 +1051,8 @@ __global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const doubl
 }
 
 __device__ double simpson_weight(int y, int ng) {
-  // g = G^{ng-1} in units of h (reading R1 of the quadrature tensors)
+  // g = G^{ng-1} in units of h: composite Simpson 1/3, with Simpson 3/8 on the
+  // last three intervals when the interval count is odd
   const int last = ng - 1;
   if ((last & 1) == 0) {
     if (y == 0 || y == last) return 1.0 / 3.0;
@@ -1054,52 +1072,60 @@ __device__ double simpson_weight(int y, int ng) {
   return w;
 }
 
-__global__ void reduce_kernel(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2, int ng,
-                              int nz, const double* __restrict__ hz, const int* __restrict__ live, double* state) {
-  const int z = blockIdx.x;
+// Block (q, z) reduces quantity q of instance z (E_y for y < ng, then
+// max|ds|, max|s|) over the partial rows of both propagation passes: thread
+// t takes rows t, t + 256, ... in order, then a fixed shuffle tree and the
+// eight warp results in order, so the result is bitwise reproducible.  The
+// rows are spread over (ng + 2) x nz blocks because FP64 adds issue at a few
+// per clock per SM on this part.  The last block of an instance to finish
+// (counter in state[6]) forms Omega_CC from the E_y in a fixed order and
+// resets the counter.
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __restrict__ p1, int nb1,
+                                                                const double* __restrict__ p2, int nb2, int ng, int nz,
+                                                                const double* __restrict__ hz,
+                                                                const int* __restrict__ live, double* state) {
+  const int q = blockIdx.x, z = blockIdx.y;
   if (live && !live[z]) return;
-  p1 += static_cast<long long>(z) * nb1 * (ng + 2);
-  p2 += static_cast<long long>(z) * nb2 * (ng + 2);
+  p1 += static_cast<long long>(z) * nb1 * (ng + 2) + static_cast<long long>(q) * nb1;   // partials are [q][block]
+  p2 += static_cast<long long>(z) * nb2 * (ng + 2) + static_cast<long long>(q) * nb2;
   state += static_cast<long long>(z) * (8 + 256);
-  const double beta = hz[nz + z];
-  // Every quantity q (E_y for y < ng, then max|ds|, max|s|) is reduced over
-  // the partial rows of both passes by one warp: lane l takes rows l, l+32,
-  // ... in order, then a fixed shuffle tree; the result is bitwise reproducible.
-  __shared__ double vals[256 + 2];
-  const int w = ng + 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int q = warp; q < w; q += nwarp) {
-    const bool is_max = q >= ng;
-    double acc = 0.0;
-    for (int b = lane; b < nb1; b += 32) {   // partials are [q][block]
-      const double v = p1[static_cast<long long>(q) * nb1 + b];
-      acc = is_max ? fmax(acc, v) : acc + v;
-    }
-    for (int b = lane; b < nb2; b += 32) {
-      const double v = p2[static_cast<long long>(q) * nb2 + b];
-      acc = is_max ? fmax(acc, v) : acc + v;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const double o = __shfl_down_sync(0xffffffffu, acc, off);
-      acc = is_max ? fmax(acc, o) : acc + o;
-    }
-    if (lane == 0) vals[q] = acc;
+  const bool is_max = q >= ng;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb1; b += kReduceThreads) acc = is_max ? fmax(acc, p1[b]) : acc + p1[b];
+  for (int b = threadIdx.x; b < nb2; b += kReduceThreads) acc = is_max ? fmax(acc, p2[b]) : acc + p2[b];
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, acc, off);
+    acc = is_max ? fmax(acc, o) : acc + o;
   }
+  __shared__ double wsum[kReduceThreads / 32];
+  __shared__ bool last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) wsum[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double h = beta / (ng - 1);
-    double om = 0.0;
-    for (int y = 0; y < ng; ++y) {
-      om += simpson_weight(y, ng) * h * vals[y];
-      state[8 + y] = vals[y];
-    }
-    om /= beta;
-    const double prev = state[0];
-    state[3] = prev;
-    state[0] = om;
-    state[1] = fabs(om - prev);
-    state[2] = vals[ng] / fmax(1.0, vals[ng + 1]);
+    double v = wsum[0];
+    for (int w = 1; w < kReduceThreads / 32; ++w) v = is_max ? fmax(v, wsum[w]) : v + wsum[w];
+    state[q < ng ? 8 + q : 4 + (q - ng)] = v;   // E_y, or state[4] max|ds|, state[5] max|s|
+    __threadfence();
+    unsigned long long* count = reinterpret_cast<unsigned long long*>(state + 6);
+    last = atomicAdd(count, 1ull) == static_cast<unsigned long long>(ng + 1);
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const volatile double* vs = state;
+  const double beta = hz[nz + z];
+  const double h = beta / (ng - 1);
+  double om = 0.0;
+  for (int y = 0; y < ng; ++y) om += simpson_weight(y, ng) * h * vs[8 + y];
+  om /= beta;
+  const double prev = state[0];
+  state[3] = prev;
+  state[0] = om;
+  state[1] = fabs(om - prev);
+  state[2] = vs[4] / fmax(1.0, vs[5]);
+  *reinterpret_cast<unsigned long long*>(state + 6) = 0ull;
 }
 
 }  // namespace
@@ -1376,15 +1402,24 @@ cudaError_t launch_antisym4(T* dst, const Anti4Desc& d, cudaStream_t st) {
                            (nA * (nA + 1) / 2);
   if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
   const size_t smem = static_cast<size_t>(d.nsrc * 4 + 1) * dd.ta * (dd.ta + 1) * sizeof(T);
-  static bool attr[2] = {false, false};
-  if (smem > 48 * 1024 && !attr[sizeof(T) == 8]) {   // the largest tile set of this type
-    cudaError_t e = cudaFuncSetAttribute(antisym4_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(9 * kAT * (kAT + 1) * sizeof(T)));
-    if (e != cudaSuccess) return e;
-    attr[sizeof(T) == 8] = true;
+  const int kp = (dd.ta * dd.ta + 255) / 256;   // element slots per thread, 1..4
+  static bool attr[5] = {false, false, false, false, false};   // per instantiation (this T)
+  auto launch = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024 && !attr[kp]) {   // the largest tile set of this instantiation
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(9 * kAT * (kAT + 1) * sizeof(T)));
+      if (e != cudaSuccess) return e;
+      attr[kp] = true;
+    }
+    kern<<<static_cast<unsigned>(blocks), 256, smem, st>>>(dst, dd);
+    return cudaGetLastError();
+  };
+  switch (kp) {
+    case 1: return launch(antisym4_kernel<T, 1>);
+    case 2: return launch(antisym4_kernel<T, 2>);
+    case 3: return launch(antisym4_kernel<T, 3>);
+    default: return launch(antisym4_kernel<T, 4>);
   }
-  antisym4_kernel<T><<<static_cast<unsigned>(blocks), 256, smem, st>>>(dst, dd);
-  return cudaGetLastError();
 }
 template cudaError_t launch_antisym4<float>(float*, const Anti4Desc&, cudaStream_t);
 template cudaError_t launch_antisym4<double>(double*, const Anti4Desc&, cudaStream_t);
@@ -1506,7 +1541,8 @@ template cudaError_t launch_propagate<double>(const double*, double*, const Prop
 cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, int ng, int nz, const double* hz,
                           const int* live, double* state, cudaStream_t st) {
   if (ng > 256 || nz < 1) return cudaErrorInvalidValue;
-  reduce_kernel<<<nz, 1024, 0, st>>>(p1, nb1, p2, nb2, ng, nz, hz, live, state);
+  if (nz > 65535) return cudaErrorInvalidValue;
+  reduce_kernel<<<dim3(ng + 2, nz), kReduceThreads, 0, st>>>(p1, nb1, p2, nb2, ng, nz, hz, live, state);
   return cudaGetLastError();
 }
 
