@@ -75,7 +75,11 @@ struct PermOut {
 // issued before any is used: load(g, t) -> value, then apply(g, t, value).
 constexpr int kPermUnroll = 4;
 
-template <int O, class V, class L, class A>
+// With VW > 1 each index names VW consecutive elements along the fastest
+// letter (unit global stride, extent a multiple of VW, every row offset a
+// multiple of VW: checked by the launcher), moved by one vector access on
+// the global side and VW accesses tile stride tf apart on the tile side.
+template <int O, class V, int VW = 1, class L, class A>
 __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, int n, long long* rowG, int* rowT,
                                           L&& load, A&& apply) {
   const int sl0 = d.slot[O][0];
@@ -106,15 +110,15 @@ __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, i
       rowT[r] = t;
     }
     __syncthreads();
-    const int ne = nr * ef;
+    const int ne = nr * ef / VW;
     for (int e0 = threadIdx.x; e0 < ne; e0 += kPermThreads * kPermUnroll) {
       V v[kPermUnroll];
       long long gg[kPermUnroll];
       int tt[kPermUnroll];
 #pragma unroll
       for (int u = 0; u < kPermUnroll; ++u) {
-        const int e = e0 + u * kPermThreads;
-        if (e < ne) {
+        const int e = (e0 + u * kPermThreads) * VW;   // first element of this index
+        if (e < ne * VW) {
           const uint32_t q = fdiv(fe, static_cast<uint32_t>(e));
           const int co = e - static_cast<int>(q) * ef;
           gg[u] = rowG[q] + co * gf;
@@ -130,11 +134,39 @@ __device__ __forceinline__ void perm_rows(const DevPerm& d, uint32_t tailmask, i
   }
 }
 
-// Term P of the antisymmetriser into the tile (term 0 stores, the others add
-// with their sign).
+// VW elements of T moved as one 16-byte access
+template <class T, int VW>
+struct PermVec {
+  T x[VW];
+};
+template <class T, int VW>
+__device__ __forceinline__ PermVec<T, VW> vload(const T* p) {
+  PermVec<T, VW> r;
+  if constexpr (VW == 1) {
+    r.x[0] = *p;
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r.x[0] = v.x, r.x[1] = v.y, r.x[2] = v.z, r.x[3] = v.w;
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r.x[0] = v.x, r.x[1] = v.y;
+  }
+  return r;
+}
+template <class T, int VW>
+__device__ __forceinline__ void vstore(T* p, const PermVec<T, VW>& r) {
+  if constexpr (VW == 1) {
+    *p = r.x[0];
+  } else if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(r.x[0], r.x[1], r.x[2], r.x[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(r.x[0], r.x[1]);
+  }
+}
+
 // Term P into the tile: term 0 stores, the others add, each scaled by its
-// coefficient.
-template <int P, class T>
+// coefficient (the sign of the antisymmetriser included).
+template <int P, class T, int VW>
 __device__ __forceinline__ void perm_term(const DevPerm& d, const long long* c, uint32_t tailmask, int n,
                                           long long* rowG, int* rowT, T* tile) {
   long long base = 0;
@@ -143,16 +175,24 @@ __device__ __forceinline__ void perm_term(const DevPerm& d, const long long* c, 
     if (k < d.nd) base += c[k] * d.sst[P][k];
   const T* sp = static_cast<const T*>(d.src[P]) + base;
   const T cf = static_cast<T>(d.coef[P]);
-  auto load = [&](long long g, int) { return sp[g]; };
+  const int tf = d.tstr[P][0];
+  using V = PermVec<T, VW>;
+  auto load = [&](long long g, int) { return vload<T, VW>(sp + g); };
   if (P == 0) {
-    perm_rows<0, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] = cf * v; });
+    perm_rows<P, V, VW>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, const V& v) {
+#pragma unroll
+      for (int w = 0; w < VW; ++w) tile[t + w * tf] = cf * v.x[w];
+    });
   } else {
-    perm_rows<P, T>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, T v) { tile[t] += cf * v; });
+    perm_rows<P, V, VW>(d, tailmask, n, rowG, rowT, load, [&](long long, int t, const V& v) {
+#pragma unroll
+      for (int w = 0; w < VW; ++w) tile[t + w * tf] += cf * v.x[w];
+    });
   }
 }
 
-template <class T, bool SPLIT>
-__global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out, const __grid_constant__ DevPerm d,
+template <class T, bool SPLIT, int VW>
+__global__ void __launch_bounds__(kPermThreads, VW == 1 ? 5 : 4) permute_kernel(PermOut<T> out, const __grid_constant__ DevPerm d,
                                                                T alpha, T beta) {
   extern __shared__ __align__(16) unsigned char perm_smem[];
   T* tile = reinterpret_cast<T*>(perm_smem);
@@ -180,10 +220,10 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out
     }
   }
   // terms: gather into the tile, each in its own letter order
-  perm_term<0>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 1) perm_term<1>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 2) perm_term<2>(d, c, tailmask, n, rowG, rowT, tile);
-  if (d.nterm > 3) perm_term<3>(d, c, tailmask, n, rowG, rowT, tile);
+  perm_term<0, T, VW>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 1) perm_term<1, T, VW>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 2) perm_term<2, T, VW>(d, c, tailmask, n, rowG, rowT, tile);
+  if (d.nterm > 3) perm_term<3, T, VW>(d, c, tailmask, n, rowG, rowT, tile);
   // write in destination order
   long long dbase = 0;
 #pragma unroll
@@ -201,13 +241,33 @@ __global__ void __launch_bounds__(kPermThreads, 5) permute_kernel(PermOut<T> out
                     });
   } else {
     T* dp = out.dst + dbase;
+    using V = PermVec<T, VW>;
+    const int tf = d.tstr[kPermTerms][0];
     if (beta == T(0)) {
-      perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
-                      [&](long long g, int, T v) { dp[g] = alpha * v; });
+      perm_rows<kPermTerms, V, VW>(
+          d, tailmask, n, rowG, rowT,
+          [&](long long, int t) {
+            V v;
+#pragma unroll
+            for (int w = 0; w < VW; ++w) v.x[w] = tile[t + w * tf];
+            return v;
+          },
+          [&](long long g, int, const V& v) {
+            V o;
+#pragma unroll
+            for (int w = 0; w < VW; ++w) o.x[w] = alpha * v.x[w];
+            vstore<T, VW>(dp + g, o);
+          });
     } else {
       // the destination values are the loads; the tile is read at the store
-      perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long g, int) { return dp[g]; },
-                      [&](long long g, int t, T old) { dp[g] = beta * old + alpha * tile[t]; });
+      perm_rows<kPermTerms, V, VW>(
+          d, tailmask, n, rowG, rowT, [&](long long g, int) { return vload<T, VW>(dp + g); },
+          [&](long long g, int t, const V& old) {
+            V o;
+#pragma unroll
+            for (int w = 0; w < VW; ++w) o.x[w] = beta * old.x[w] + alpha * tile[t + w * tf];
+            vstore<T, VW>(dp + g, o);
+          });
     }
   }
 }
@@ -1214,7 +1274,10 @@ cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double
     for (int l = 0; l < nt; ++l) v *= ext[l];
     return v;
   };
-  while (prod() > kPermTile) {   // shrink the widest extent
+  // a small tensor gets smaller tiles, so that its blocks cover about two per
+  // SM instead of a few SMs running long blocks
+  const long long tile_cap = std::max<long long>(256, std::min<long long>(kPermTile, total / (2 * 152)));
+  while (prod() > tile_cap) {   // shrink the widest extent
     int w = 0;
     for (int l = 1; l < nt; ++l)
       if (ext[l] > ext[w]) w = l;
@@ -1232,7 +1295,7 @@ cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double
       bool in = false;
       for (int l = 0; l < nt; ++l) in |= tl[l] == k;
       if (in || P.dim[k] <= 1) continue;
-      const long long room = kPermTile / prod();
+      const long long room = tile_cap / prod();
       if (room < 2) break;
       tl[nt] = k;
       ext[nt] = std::min<long long>(P.dim[k], room);
@@ -1313,11 +1376,29 @@ cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double
     fill(p, ord, P.sst[p]);
   }
   fill(kPermTerms, word, P.dstr);
+  // 16-byte global accesses when every order's fastest tile letter has unit
+  // stride and an extent (full and tail) that is a multiple of the vector
+  // width, every other stride and every block's base offset is a multiple
+  // of it, and the tensors start on 16-byte boundaries
+  constexpr int kVW = 16 / sizeof(T);
+  bool vec = !SPLIT && reinterpret_cast<uintptr_t>(out.dst) % 16 == 0;
+  for (int o = 0; o <= P.nterm && vec; ++o) {
+    const int oo = o == P.nterm ? kPermTerms : o;
+    const int l0 = d.slot[oo][0];
+    vec = d.gstr[oo][0] == 1 && d.ext_full[l0] % kVW == 0 && d.ext_tail[l0] % kVW == 0;
+    for (int i = 1; i < nt && vec; ++i) vec = d.gstr[oo][i] % kVW == 0;
+    if (o < P.nterm) vec = vec && reinterpret_cast<uintptr_t>(P.src[o]) % 16 == 0;
+    for (int k = 0; k < nd && vec; ++k)
+      vec = (static_cast<long long>(d.bstep[k]) * (o < P.nterm ? P.sst[o][k] : P.dstr[k])) % kVW == 0;
+  }
   const size_t smem = static_cast<size_t>(tile_elems) * sizeof(T);
   for (unsigned long long b0 = 0; b0 < nblocks; b0 += 0x7FFFFFFFull) {
     d.block0 = static_cast<uint32_t>(b0);
     const unsigned int g = static_cast<unsigned int>(std::min<unsigned long long>(nblocks - b0, 0x7FFFFFFFull));
-    permute_kernel<T, SPLIT><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
+    if (vec)
+      permute_kernel<T, false, kVW><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
+    else
+      permute_kernel<T, SPLIT, 1><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
   }
   return cudaGetLastError();
 }

@@ -7,6 +7,7 @@
 // an instance index z in front, so one launch of each contraction serves the
 // whole batch and one CUDA graph replays an iteration of all instances.
 #include <algorithm>
+#include <array>
 #include <tuple>
 #include <cmath>
 #include <cstdarg>
@@ -61,6 +62,11 @@ struct ftcc_ctx {
   // prepared problem: the batch this context belongs to and its index in it
   std::shared_ptr<ftcc::Batch> batch;
   int member = 0;
+  // tensor-core GEMM autotuner: (kind, batch, M, N, K, transposed output,
+  // accumulate) -> (tile width, K split), kept for the context's lifetime so
+  // that repeated solves in one context take the same launches (and round
+  // the same way)
+  std::map<std::array<int, 7>, std::pair<int, int>> tuned;
 
   ftcc::Buf get(size_t bytes) {
     ftcc::Buf b;
@@ -582,23 +588,17 @@ struct Solver {
   // Tile-width / split-K autotuner for the tensor-core GEMM.  The first time
   // a shape (kind, batch, M, N, K, output order, accumulate or not) is met
   // outside a stream capture, every candidate (tile width 32 / 64 / 128 / 256
-  // columns x built-in or no K split) runs twice on a scratch output and
-  // the fastest second run is kept for that shape; later calls (and the
-  // captured graph) use it.  Shapes whose output exceeds 512 MB or whose work
+  // columns x built-in or no K split) runs on a scratch output, timed as a
+  // graph replay of three launches, and the fastest is kept for that shape;
+  // later calls (and the captured graph) use it.  Shapes whose output exceeds 512 MB or whose work
   // exceeds 2 TFLOP keep the built-in choice, where the tile shape matters
-  // least and a trial run costs the most.
-  struct TuneKey {
-    int kind, nb, m, n, k, trans, acc;
-    bool operator<(const TuneKey& o) const {
-      return std::tie(kind, nb, m, n, k, trans, acc) < std::tie(o.kind, o.nb, o.m, o.n, o.k, o.trans, o.acc);
-    }
-  };
-  std::map<TuneKey, std::pair<int, int>> tuned;
+  // least and a trial run costs the most.  The table lives in the home
+  // context (ftcc_ctx::tuned), so later solves there reuse the choices.
   Buf tuneC;
-  int tuned_shapes = 0;
   void tune_tc(int kind, GemmArgs& g, size_t out_bytes) {
     if (!b->opt.autotune) return;
-    const TuneKey key{kind, g.batch, g.M, g.N, g.K, g.trans, g.beta != 0.0 ? 1 : 0};
+    const std::array<int, 7> key{kind, g.batch, g.M, g.N, g.K, g.trans, g.beta != 0.0 ? 1 : 0};
+    auto& tuned = h_->tuned;
     auto it = tuned.find(key);
     if (it != tuned.end()) {
       g.bn = it->second.first;
@@ -623,14 +623,33 @@ struct Solver {
       for (int split : {0, 1}) {
         t.bn = bn;
         t.split = split;
+        // device time alone: after one plain launch (attributes, module
+        // load), three launches are captured once into a graph and a replay
+        // of it is timed, so host work per launch (tensor-map encoding, the
+        // split-K reduction's launch) is not counted
+        constexpr int kReps = 3;
+        CU(gemm_tc(kind, t, h_->dev_err, st()));
+        cudaGraph_t gr = nullptr;
+        CU(cudaStreamBeginCapture(st(), cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (int rep = 0; rep < kReps && ce == cudaSuccess; ++rep) ce = gemm_tc(kind, t, h_->dev_err, st());
+        const cudaError_t ee = cudaStreamEndCapture(st(), &gr);
+        CU(ce);
+        CU(ee);
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
+        cudaGraphDestroy(gr);
+        CU(ie);
         float ms = 0.0f;
-        for (int rep = 0; rep < 2; ++rep) {
-          CU(cudaEventRecord(e0, st()));
-          CU(gemm_tc(kind, t, h_->dev_err, st()));
-          CU(cudaEventRecord(e1, st()));
-          CU(cudaEventSynchronize(e1));
-          CU(cudaEventElapsedTime(&ms, e0, e1));
-        }
+        cudaError_t re = cudaGraphLaunch(ge, st());   // upload and warm
+        if (re == cudaSuccess) re = cudaEventRecord(e0, st());
+        if (re == cudaSuccess) re = cudaGraphLaunch(ge, st());
+        if (re == cudaSuccess) re = cudaEventRecord(e1, st());
+        if (re == cudaSuccess) re = cudaEventSynchronize(e1);
+        if (re == cudaSuccess) re = cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(ge);
+        CU(re);
+        ms /= kReps;
         if (best < 0.0f || ms < best) {
           best = ms;
           pick = {bn, split};
@@ -640,7 +659,6 @@ struct Solver {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     tuned[key] = pick;
-    ++tuned_shapes;
     g.bn = pick.first;
     g.split = pick.second;
   }
