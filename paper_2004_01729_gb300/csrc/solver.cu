@@ -589,8 +589,9 @@ struct Solver {
   // a shape (kind, batch, M, N, K, output order, accumulate or not) is met
   // outside a stream capture, every candidate (tile width 32 / 64 / 128 / 256
   // columns x built-in or no K split) runs on a scratch output, timed as a
-  // graph replay of three launches, and the fastest is kept for that shape;
-  // later calls (and the captured graph) use it.  Shapes whose output exceeds 512 MB or whose work
+  // plain launch (long products) or a graph replay of three launches (short
+  // ones), and the fastest is kept for that shape; later calls (and the
+  // captured graph) use it.  Shapes whose output exceeds 512 MB or whose work
   // exceeds 2 TFLOP keep the built-in choice, where the tile shape matters
   // least and a trial run costs the most.  The table lives in the home
   // context (ftcc_ctx::tuned), so later solves there reuse the choices.
@@ -623,12 +624,31 @@ struct Solver {
       for (int split : {0, 1}) {
         t.bn = bn;
         t.split = split;
-        // device time alone: after one plain launch (attributes, module
-        // load), three launches are captured once into a graph and a replay
-        // of it is timed, so host work per launch (tensor-map encoding, the
-        // split-K reduction's launch) is not counted
+        // device time alone.  A plain launch first (attributes, module load);
+        // when it already runs for more than half a millisecond, host work
+        // per launch is negligible and a second plain launch is the timing.
+        // Shorter products are timed as a graph replay of three launches
+        // captured once, so that host work per launch (tensor-map encoding,
+        // the split-K reduction's launch) is not counted.
         constexpr int kReps = 3;
+        float ms = 0.0f;
+        CU(cudaEventRecord(e0, st()));
         CU(gemm_tc(kind, t, h_->dev_err, st()));
+        CU(cudaEventRecord(e1, st()));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms > 0.5f) {
+          CU(cudaEventRecord(e0, st()));
+          CU(gemm_tc(kind, t, h_->dev_err, st()));
+          CU(cudaEventRecord(e1, st()));
+          CU(cudaEventSynchronize(e1));
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+          if (best < 0.0f || ms < best) {
+            best = ms;
+            pick = {bn, split};
+          }
+          continue;
+        }
         cudaGraph_t gr = nullptr;
         CU(cudaStreamBeginCapture(st(), cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
@@ -640,7 +660,6 @@ struct Solver {
         const cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
         cudaGraphDestroy(gr);
         CU(ie);
-        float ms = 0.0f;
         cudaError_t re = cudaGraphLaunch(ge, st());   // upload and warm
         if (re == cudaSuccess) re = cudaEventRecord(e0, st());
         if (re == cudaSuccess) re = cudaGraphLaunch(ge, st());
