@@ -31,9 +31,6 @@ namespace ftcc {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kBN = 128;
-constexpr int kTileBytes = 128 * 128;   // 128 rows x 128 bytes
-constexpr uint32_t kTmemCols = 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -95,12 +92,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          (static_cast<uint64_t>(2) << 61);
 }
 
-// Instruction descriptor: D = F32, A/B format `fmt` (1 = BF16, 2 = TF32),
-// both K-major, N = 128, M = 128.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t(kBN) >> 3) << 17) |
-         ((uint32_t(kBM) >> 4) << 24);
-}
 
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {

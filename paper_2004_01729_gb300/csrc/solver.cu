@@ -1617,7 +1617,6 @@ ftcc_status solve_batch(Batch& B) {
 void ensure_fp64_solution(Batch& B) {
   if (B.active == 0) return;
   promote_to_fp64(B);
-  ftcc_ctx* h = B.home;
   for (int r = 0; r < std::max(50, B.opt.refine_max_iter); ++r) {
     timed_iterations(B, 1);
     B.refine_iterations++;
@@ -1629,7 +1628,6 @@ void ensure_fp64_solution(Batch& B) {
     }
     if (ok) return;
   }
-  (void)h;
   throw Fail{FTCC_ERR_NOT_CONVERGED, "FP64 refinement before the adjoint did not converge"};
 }
 
