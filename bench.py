@@ -64,12 +64,18 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                          "-lms", "50", "-i", os.environ.get("LOCAL_RANK", "0")],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+        # nvidia-smi takes longer to start than the timed loop lasts: wait
+        # (at most 3 s) for its first sample so that the loop is covered
+        t0 = time.time()
+        while self.proc is not None and not self.samples and self.proc.poll() is None and time.time() - t0 < 3.0:
+            time.sleep(0.01)
+        self.first = len(self.samples)   # samples before the timed region
         return self
 
     def _read(self):
@@ -95,7 +101,8 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(self.samples), "interval_ms": 50,
+                "samples_before_timed_region": getattr(self, "first", 0)}
 
 
 def dist_init(args):
