@@ -15,6 +15,9 @@ Contents
               kernels term by term (Eqs. E, ccS1, ccS2), the integral-form
               fixed point (Eq. smu / Alg. 2), the lambda equations (Eqs.
               Lagrangian, lmu, ltilde) and response outputs (App. B).
+  differential.py  the differential form of the amplitude equations (Eq.
+              smud) marched over the grid by explicit RK1 / RK2 / RK4 steps
+              (Alg. 1), with Omega_CC from the same quadrature weights.
   exact.py    exact grand potentials (Fock-space diagonalisation and
               non-interacting closed forms) used only to pin the oracle.
 
