@@ -53,8 +53,16 @@ typedef enum {
 } ftcc_status;
 
 /* Quadrature / propagation scheme (Sec. II.C).  SIMPSON is the implicit
- * integral method with the Simpson tensors g, G; the explicit Runge-Kutta
- * drivers are not implemented and return FTCC_ERR_UNSUPPORTED. */
+ * integral method with the Simpson tensors g, G (Eq. smu, solved as one
+ * fixed point over the grid).  RK1 / RK2 / RK4 march the differential form
+ * ds/dtau = -(Delta s + S[s]) (Eq. smud) from s = 0 with one explicit step
+ * per grid interval (Alg. 1; read as forward Euler, Heun's method and the
+ * classical four-stage method, since the paper does not print the tableaux);
+ * Omega_CC keeps the quadrature weights g.  The RK drivers run through
+ * ft_ccsd_solve / ft_ccsd_solve_batched in FP64 without stream_tau
+ * (otherwise FTCC_ERR_UNSUPPORTED); ft_ccsd_iterate and ft_ccsd_adjoint on
+ * an RK solve return FTCC_ERR_UNSUPPORTED.  ftcc_result.iterations is then
+ * the number of steps (ngrid - 1). */
 typedef enum { FTCC_QUAD_SIMPSON = 0, FTCC_QUAD_RK1 = 1, FTCC_QUAD_RK2 = 2, FTCC_QUAD_RK4 = 3 } ftcc_quadrature;
 
 /* Arithmetic of the contractions.  FP64: every tensor and GEMM in FP64.

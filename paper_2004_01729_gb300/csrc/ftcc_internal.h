@@ -178,6 +178,26 @@ int prop_blocks();
 // Per instance z, sum the partials of the singles and doubles passes; row
 // state[z][.]: 0 <- Omega_CC, 1 <- |dOmega_CC|, 2 <- max|ds|/max(1, max|s|),
 // 3 <- previous Omega_CC, 8 + y <- E(tau_y).  hz holds [nz] steps then [nz] betas.
+// ---- differential form (Eq. smud) marched by explicit RK steps (rk.cu) ----
+// up to four stage derivatives K_j with their coefficients
+template <class T>
+struct RkTerms {
+  int n;
+  T c[4];
+  const T* K[4];
+};
+// out[z][mu] = base[z][mu] + hz[z] sum_j c_j K_j[z][mu] (K_j dense [nz][n])
+template <class T>
+cudaError_t launch_rk_combine(T* out, long long out_zstride, const T* base, long long base_zstride,
+                              const RkTerms<T>& k, const double* hz, long long n, int nz, cudaStream_t st);
+// K = -(Delta Y + S) for the singles (nslot 2) or doubles (nslot 4) of nz instances
+template <class T>
+cudaError_t launch_rk_deriv(T* K, const T* Y, const T* S, const double* eps, const int* idxO, const int* idxV, int N,
+                            int no, int nv, int nslot, int nz, cudaStream_t st);
+// per-block energy partials of every tau point (Eq. E) in the layout launch_reduce folds
+template <class T>
+cudaError_t launch_rk_energy(const T* t1, const T* t2, const double* F64, const double* V64, int ng, int no, int nv,
+                             int nz, int nb1, int nb2, double* part1, double* part2, cudaStream_t st);
 cudaError_t launch_reduce(const double* p1, int nb1, const double* p2, int nb2, int ng, int nz, const double* hz,
                           const int* live, double* state, cudaStream_t st);
 double simpson_weight_host(int y, int ng);

@@ -166,6 +166,7 @@ struct Batch {
   int ms_count = 0;
   bool solved = false;
   bool solved_live = false;   // every live member converged (diverged members are frozen)
+  int quad = FTCC_QUAD_SIMPSON;   // integral form (Simpson fixed point) or an RK march of Eq. smud
   ~Batch();
 };
 
@@ -1515,7 +1516,108 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
 }
 
 // Fixed-point loop of a prepared batch (see ft_ccsd_solve).
+// Alg. 1: the differential form ds/dtau = -(Delta s + S[s]) (Eq. smud)
+// marched from s(0) = 0 by one explicit Runge-Kutta step per grid interval,
+// every instance of the batch at once, in FP64.  The paper names RK1 / RK2 /
+// RK4 without printing their tableaux; they are read as forward Euler, Heun's
+// method and the classical four-stage method.  Each stage evaluates the S
+// kernel on one tau slice per instance through the engine; Omega_CC is then
+// integrated from the energies at every grid point with the quadrature
+// weights g (Eq. Ecc), as in the integral form.
+ftcc_status rk_solve(Batch& B) {
+  static const double kA1[1][3] = {{0, 0, 0}}, kB1[1] = {1.0};
+  static const double kA2[2][3] = {{0, 0, 0}, {1.0, 0, 0}}, kB2[2] = {0.5, 0.5};
+  static const double kA4[4][3] = {{0, 0, 0}, {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 1.0}},
+                      kB4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  int ns;
+  const double(*A)[3];
+  const double* bw;
+  switch (B.quad) {
+    case FTCC_QUAD_RK1: ns = 1, A = kA1, bw = kB1; break;
+    case FTCC_QUAD_RK2: ns = 2, A = kA2, bw = kB2; break;
+    case FTCC_QUAD_RK4: ns = 4, A = kA4, bw = kB4; break;
+    default: throw Fail{FTCC_ERR_STATE, "not an RK quadrature"};
+  }
+  ftcc_ctx* h = B.home;
+  cudaStream_t st = h->st;
+  Solver<double>& s = make_solver<double>(B, GEMM_F64);
+  B.active = 0;
+  const int nz = B.nz, ng = B.ng, no = B.no, nv = B.nv;
+  const long long n1 = static_cast<long long>(no) * nv, n2 = n1 * no * nv;
+  // stage inputs and stage derivatives, [nz][n] each; released on every exit
+  struct Held {
+    ftcc_ctx* h;
+    Buf b[10];
+    ~Held() {
+      for (Buf& x : b) h->put(x);
+    }
+  } held{h, {}};
+  Buf &Y1 = held.b[0], &Y2 = held.b[1];
+  ensure(h, Y1, nz * n1 * sizeof(double));
+  ensure(h, Y2, nz * n2 * sizeof(double));
+  double *K1[4], *K2[4];
+  for (int j = 0; j < ns; ++j) {
+    ensure(h, held.b[2 + j], nz * n1 * sizeof(double));
+    ensure(h, held.b[6 + j], nz * n2 * sizeof(double));
+    K1[j] = static_cast<double*>(held.b[2 + j].p);
+    K2[j] = static_cast<double*>(held.b[6 + j].p);
+  }
+  double* t1 = static_cast<double*>(s.t1.p);
+  double* t2 = static_cast<double*>(s.t2.p);
+  double* S1 = static_cast<double*>(s.S1.p);
+  double* S2 = static_cast<double*>(s.S2.p);
+  double* y1 = static_cast<double*>(Y1.p);
+  double* y2 = static_cast<double*>(Y2.p);
+  const double* hz = static_cast<const double*>(B.hz.p);   // [nz] steps, then [nz] betas
+  const double* eps = static_cast<const double*>(B.epsz.p);
+  const int* iO = static_cast<const int*>(B.idxO.p);
+  const int* iV = static_cast<const int*>(B.idxV.p);
+  CU(cudaMemsetAsync(t1, 0, static_cast<size_t>(nz) * ng * n1 * sizeof(double), st));   // s(tau_0) = 0
+  CU(cudaMemsetAsync(t2, 0, static_cast<size_t>(nz) * ng * n2 * sizeof(double), st));
+  for (int k = 0; k + 1 < ng; ++k) {
+    const double* b1 = t1 + k * n1;   // s(tau_k), instance stride ng n
+    const double* b2 = t2 + k * n2;
+    for (int q = 0; q < ns; ++q) {
+      RkTerms<double> r1{}, r2{};
+      for (int j = 0; j < q; ++j)
+        if (A[q][j] != 0.0) {
+          r1.c[r1.n] = A[q][j], r1.K[r1.n++] = K1[j];
+          r2.c[r2.n] = A[q][j], r2.K[r2.n++] = K2[j];
+        }
+      CU(launch_rk_combine<double>(y1, n1, b1, ng * n1, r1, hz, n1, nz, st));
+      CU(launch_rk_combine<double>(y2, n2, b2, ng * n2, r2, hz, n2, nz, st));
+      s.s_kernel(y1, y2, S1, S2, 1);
+      CU(launch_rk_deriv<double>(K1[q], y1, S1, eps, iO, iV, B.N, no, nv, 2, nz, st));
+      CU(launch_rk_deriv<double>(K2[q], y2, S2, eps, iO, iV, B.N, no, nv, 4, nz, st));
+    }
+    RkTerms<double> r1{}, r2{};
+    for (int q = 0; q < ns; ++q) {
+      r1.c[r1.n] = bw[q], r1.K[r1.n++] = K1[q];
+      r2.c[r2.n] = bw[q], r2.K[r2.n++] = K2[q];
+    }
+    CU(launch_rk_combine<double>(t1 + (k + 1) * n1, ng * n1, b1, ng * n1, r1, hz, n1, nz, st));
+    CU(launch_rk_combine<double>(t2 + (k + 1) * n2, ng * n2, b2, ng * n2, r2, hz, n2, nz, st));
+  }
+  CU(launch_rk_energy<double>(t1, t2, static_cast<const double*>(B.F64.p), static_cast<const double*>(B.V64.p), ng, no,
+                              nv, nz, s.nb1, s.nb2, static_cast<double*>(s.part1.p), static_cast<double*>(s.part2.p),
+                              st));
+  CU(launch_reduce(static_cast<const double*>(s.part1.p), s.nb1, static_cast<const double*>(s.part2.p), s.nb2, ng, nz,
+                   hz, static_cast<const int*>(B.live.p), static_cast<double*>(B.state.p), st));
+  check_device_error(h);
+  std::vector<double> sv = read_states(B);
+  B.iterations = ng - 1;   // steps marched
+  bool finite = true;
+  for (int z = 0; z < nz; ++z) {
+    const double om = sv[static_cast<size_t>(z) * kStateStride];
+    if (std::isfinite(om)) B.inst[z].conv_iter = ng - 1;
+    else finite = false;
+  }
+  if (!finite) return fail(h, FTCC_ERR_DIVERGED, "the RK march became non-finite (a step too long for the stiffness)");
+  return FTCC_OK;
+}
+
 ftcc_status solve_batch(Batch& B) {
+  if (B.quad != FTCC_QUAD_SIMPSON) return rk_solve(B);
   const ftcc_options& o = B.opt;
   ftcc_ctx* h = B.home;
   std::vector<double> s;
@@ -1860,7 +1962,17 @@ ftcc_status check_solve_args(ftcc_ctx* c, double beta, double mu, int ngrid, ftc
   if (c->N == 0) return fail(c, FTCC_ERR_STATE, "build_integrals first");
   if (!(beta > 0) || !std::isfinite(beta) || !std::isfinite(mu) || ngrid < 3 || ngrid > 256)
     return fail(c, FTCC_ERR_INVALID_ARG, "need beta > 0 finite, mu finite, 3 <= ngrid <= 256");
-  if (quad != FTCC_QUAD_SIMPSON) return fail(c, FTCC_ERR_UNSUPPORTED, "only the Simpson integral method is built");
+  if (quad != FTCC_QUAD_SIMPSON && quad != FTCC_QUAD_RK1 && quad != FTCC_QUAD_RK2 && quad != FTCC_QUAD_RK4)
+    return fail(c, FTCC_ERR_INVALID_ARG, "unknown quadrature");
+  return FTCC_OK;
+}
+
+// The RK drivers march the FP64 amplitudes over the whole grid at once.
+ftcc_status check_quad_options(ftcc_ctx* c, ftcc_quadrature quad, const ftcc_options& o) {
+  if (quad == FTCC_QUAD_SIMPSON) return FTCC_OK;
+  if (o.precision != FTCC_PREC_FP64)
+    return fail(c, FTCC_ERR_UNSUPPORTED, "the RK drivers run in FP64 (precision = FTCC_PREC_FP64)");
+  if (o.stream_tau) return fail(c, FTCC_ERR_UNSUPPORTED, "the RK drivers keep every tau point (stream_tau = 0)");
   return FTCC_OK;
 }
 
@@ -2051,10 +2163,12 @@ ftcc_status ftcc_prepare(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_qu
   if (s != FTCC_OK) return s;
   const ftcc_options o = opt ? *opt : default_options();
   if ((s = check_options(c, o)) != FTCC_OK) return s;
+  if ((s = check_quad_options(c, quad, o)) != FTCC_OK) return s;
   return run_guarded(c, [&]() -> ftcc_status {
     drop_batch(c);
     ftcc_ctx* cs[1] = {c};
     std::shared_ptr<Batch> B = prepare_batch(cs, 1, &beta, &mu, ngrid, o);
+    B->quad = quad;
     fill_result(*B, 0, read_states(*B), out);
     return FTCC_OK;
   });
@@ -2063,6 +2177,8 @@ ftcc_status ftcc_prepare(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_qu
 ftcc_status ft_ccsd_iterate(ftcc_ctx* c, int n_iter, ftcc_result* out) {
   if (!c || n_iter < 0) return FTCC_ERR_INVALID_ARG;
   if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare or ft_ccsd_solve first");
+  if (c->batch->quad != FTCC_QUAD_SIMPSON)
+    return fail(c, FTCC_ERR_UNSUPPORTED, "the RK drivers march the grid once (ft_ccsd_solve), they do not iterate");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
@@ -2101,6 +2217,7 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
   const ftcc_options o = opt ? *opt : default_options();
   ftcc_status s = check_options(c0, o);
   if (s != FTCC_OK) return s;
+  if ((s = check_quad_options(c0, quad, o)) != FTCC_OK) return s;
   return run_guarded(c0, [&]() -> ftcc_status {
     for (int i = 0; i < n; ++i) drop_batch(ctx[i]);
     // one batch per orbital count, in order of first appearance
@@ -2120,6 +2237,7 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
           done[j] = 1;
         }
       std::shared_ptr<Batch> B = prepare_batch(cs.data(), static_cast<int>(cs.size()), bs.data(), ms.data(), ngrid, o);
+      B->quad = quad;
       if (!iterate) continue;
       ftcc_status r = solve_batch(*B);
       if (r != FTCC_OK) {
@@ -2145,6 +2263,8 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
 }
 
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1) {
+  if (c && c->batch && c->batch->quad != FTCC_QUAD_SIMPSON)
+    return fail(c, FTCC_ERR_UNSUPPORTED, "the adjoint is built for the integral (Simpson) form only");
   if (!c) return FTCC_ERR_INVALID_ARG;
   if (!c->batch || !(c->batch->solved || (c->batch->solved_live && c->batch->live_host[c->member])))
     return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
