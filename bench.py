@@ -242,6 +242,33 @@ def run_gpu(args, rank, world):
         for c in ctxs:
             c.close()
 
+    # the differential form (Eq. smud, Alg. 1): an RK4 / RK2 march of the same
+    # batch in FP64, host-timed whole solves beside the FP64 Simpson fixed
+    # point (the paper's Table II compares these costs); a failure here is
+    # reported in the line, not raised
+    rk = None
+    if not args.quick and world == 1:
+        rk = {"workload": WORKLOAD + ", FP64, one batched solve each (host-timed, synchronised)"}
+        try:
+            for name, quad, kw in (("simpson_fp64", ftcc.QUAD_SIMPSON, {"max_iter": 300}),
+                                   ("rk4_fp64", ftcc.QUAD_RK4, {}), ("rk2_fp64", ftcc.QUAD_RK2, {})):
+                ctxs = built()
+                try:
+                    ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)  # warm
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
+                    torch.cuda.synchronize()
+                    rk[name] = {"s_total": time.perf_counter() - t0, "iterations_or_steps": res[0]["iterations"],
+                                "omega": [r["omega"] for r in res]}
+                finally:
+                    for c in ctxs:
+                        c.close()
+            rk["rk4_minus_simpson_omega"] = [a - b for a, b in zip(rk["rk4_fp64"]["omega"],
+                                                                   rk["simpson_fp64"]["omega"])]
+        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
+            rk["error"] = f"{type(e).__name__}: {e}"[:300]
+
     def make_ctxs(prec):
         out = built()
         ftcc.prepare_batched(out, betas, mus, cfgs[0]["ngrid"], precision=prec)
@@ -503,7 +530,7 @@ def run_gpu(args, rank, world):
                 "roofline": roof, "kernels": kernels, "profiled_step_ms": t_prof / args.steps * 1e3,
                 "ueg57_114_spin_orbitals": ueg or None,
                 "ueg81_162_spin_orbitals": ueg81,
-                "adjoint_lambda_sweep": adj, "batched_64_instances": bat64,
+                "adjoint_lambda_sweep": adj, "batched_64_instances": bat64, "differential_form": rk,
                 "e2e": e2e, "gpu_launches": k_mixed * args.steps,
                 "clocks": clk.summary()}
         if cpu:
