@@ -18,6 +18,9 @@ Contents
   differential.py  the differential form of the amplitude equations (Eq.
               smud) marched over the grid by explicit RK1 / RK2 / RK4 steps
               (Alg. 1), with Omega_CC from the same quadrature weights.
+  chemical_potential.py  the chemical potential for a fixed mean particle
+              number: the reference mu_0 (Fermi sum) and mu_CC from the
+              FT-CCSD N(mu) = -dOmega/dmu (App. B, App. D).
   exact.py    exact grand potentials (Fock-space diagonalisation and
               non-interacting closed forms) used only to pin the oracle.
 
