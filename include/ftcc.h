@@ -190,7 +190,8 @@ ftcc_status ftcc_reference_mu(ftcc_ctx* ctx, double beta, double n_elec, double*
  * App. A-B), truncation sets, the Fermi-scaled integral blocks, the
  * quadrature tensors, and s = 0 at every tau point.
  * FTCC_ERR_INVALID_ARG: beta <= 0 or not finite, mu not finite, ngrid < 3,
- * options out of range.  FTCC_ERR_UNSUPPORTED: quadrature other than SIMPSON. */
+ * options out of range or an unknown quadrature.  FTCC_ERR_UNSUPPORTED: an RK
+ * quadrature with a precision other than FP64 or with stream_tau. */
 ftcc_status ftcc_prepare(ftcc_ctx* ctx, double beta, double mu, int ngrid,
                          ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out);
 
@@ -199,14 +200,16 @@ ftcc_status ftcc_prepare(ftcc_ctx* ctx, double beta, double mu, int ngrid,
  * kernel (Eqs. ccS1, ccS2), propagation with exp(-Delta (tau_y - tau_x))
  * Simpson weights, E kernel (Eq. E) and Omega_CC (Eq. Ecc).  Requires
  * ftcc_prepare or a solve.  Precision is the prepared one.  `out` (may be
- * NULL) receives the state after the last iteration. */
+ * NULL) receives the state after the last iteration.  FTCC_ERR_UNSUPPORTED
+ * when the prepared quadrature is an RK march (it is not iterated). */
 ftcc_status ft_ccsd_iterate(ftcc_ctx* ctx, int n_iter, ftcc_result* out);
 
 /* Full solve: ftcc_prepare, then fixed-point iterations from s = 0 until
  * converged (Alg. 2 run to self-consistency over the whole tau grid),
- * followed by FP64 refinement when the precision is TF32 / BF16X3.
- * Returns FTCC_ERR_NOT_CONVERGED (with `out` filled) at the iteration cap
- * and FTCC_ERR_DIVERGED on NaN/Inf. */
+ * followed by FP64 refinement when the precision is TF32 / BF16X3; with an
+ * RK quadrature, the explicit march of Eq. smud instead (ngrid - 1 steps,
+ * FP64).  Returns FTCC_ERR_NOT_CONVERGED (with `out` filled) at the
+ * iteration cap and FTCC_ERR_DIVERGED on NaN/Inf. */
 ftcc_status ft_ccsd_solve(ftcc_ctx* ctx, double beta, double mu, int ngrid,
                           ftcc_quadrature quad, const ftcc_options* opt, ftcc_result* out);
 
