@@ -8,8 +8,10 @@ only common module is the seeded input generator
 ``paper_2004_01729_gb300/workloads.py``, which holds no FT-CC arithmetic.
 
 Contents
-  systems.py  model Hamiltonians (1D Hubbard in k space, plane-wave UEG,
-              generic), built from their textbook definitions.
+  systems.py  model Hamiltonians (1D Hubbard in k space, in the site basis
+              with the Neel-state reference, plane-wave UEG, generic), built
+              from their textbook definitions; the staggered magnetisation
+              of a site-basis 1-RDM.
   ftccsd.py   reference quantities, thermal integrals (App. A), the Simpson
               quadrature tensors (Sec. II.C, Eqs. g/G), the E, S1, S2
               kernels term by term (Eqs. E, ccS1, ccS2), the integral-form

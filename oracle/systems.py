@@ -8,9 +8,10 @@ all float64 torch tensors on the CPU.  Spin orbital p = sigma * M + g with
 sigma = 0 (up), 1 (down) and g the spatial index.
 
 Sources: 1D Hubbard Hamiltonian (Sec. IV.A), the plane-wave UEG used in
-Sec. IV.B / App. D, and the k-space restricted reference of the Hubbard
-model at half filling (Sec. II.B: orbitals and orbital energies define the
-reference).
+Sec. IV.B / App. D, the k-space restricted reference of the Hubbard model at
+half filling (Sec. II.B: orbitals and orbital energies define the
+reference), and the Neel-state reference with the staggered magnetisation
+of Sec. IV.A (Fig. 5).
 """
 import math
 
@@ -83,6 +84,31 @@ def hubbard_1d_sites(L, t, U, pbc=True):
     h[M:, M:] = torch.tensor(hs)
     eri = _two_body_from_spatial(torch.tensor(v, dtype=DT))
     return {"h": h, "eri": eri, "eps": torch.diagonal(h).clone() + U / 2.0}
+
+
+def hubbard_1d_neel(L, t, U, pbc=True):
+    """Site-basis 1D Hubbard model with the Neel-state reference (Sec. IV.A):
+    the reference non-interacting system is the diagonal of the
+    zero-temperature Fock matrix of the Neel determinant (spin up on even
+    sites, spin down on odd sites), eps_{i sigma} = h_ii + U n^Neel_{i, -sigma}."""
+    s = hubbard_1d_sites(L, t, U, pbc)
+    M = L
+    eps = torch.diagonal(s["h"]).clone()
+    for i in range(M):
+        n_up = 1.0 if i % 2 == 0 else 0.0
+        eps[i] += U * (1.0 - n_up)     # spin up on site i meets the Neel down electron
+        eps[M + i] += U * n_up         # spin down meets the up electron
+    s["eps"] = eps
+    s.update(kind="hubbard_neel", L=L, t=t, U=U)
+    return s
+
+
+def staggered_magnetisation(rdm1, L):
+    """m_s = L^-1 sum_i (-1)^i (<n_i,up> - <n_i,down>) from the diagonal of a
+    1-RDM in the site basis (spin orbital sigma * L + i)."""
+    d = torch.diagonal(torch.as_tensor(rdm1, dtype=DT))
+    sign = torch.tensor([(-1.0) ** i for i in range(L)], dtype=DT)
+    return float(torch.sum(sign * (d[:L] - d[L:])) / L)
 
 
 def plane_wave_grid(n_pw):
