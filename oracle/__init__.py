@@ -9,7 +9,7 @@ only common module is the seeded input generator
 
 Contents
   systems.py  model Hamiltonians (1D Hubbard in k space, in the site basis
-              with the Neel-state reference, plane-wave UEG, generic), built
+              with the Neel-state or UHF reference, plane-wave UEG, generic), built
               from their textbook definitions; the staggered magnetisation
               of a site-basis 1-RDM.
   ftccsd.py   reference quantities, thermal integrals (App. A), the Simpson

@@ -10,8 +10,8 @@ sigma = 0 (up), 1 (down) and g the spatial index.
 Sources: 1D Hubbard Hamiltonian (Sec. IV.A), the plane-wave UEG used in
 Sec. IV.B / App. D, the k-space restricted reference of the Hubbard model at
 half filling (Sec. II.B: orbitals and orbital energies define the
-reference), and the Neel-state reference with the staggered magnetisation
-of Sec. IV.A (Fig. 5).
+reference), and the Neel-state and zero-temperature UHF references with the
+staggered magnetisation of Sec. IV.A (Figs. 4 and 5).
 """
 import math
 
@@ -101,6 +101,60 @@ def hubbard_1d_neel(L, t, U, pbc=True):
     s["eps"] = eps
     s.update(kind="hubbard_neel", L=L, t=t, U=U)
     return s
+
+
+def uhf_site_hubbard(L, t, U, n_up=None, n_dn=None, pbc=True, max_iter=2000, tol=1e-12, mix=0.5):
+    """Zero-temperature unrestricted Hartree-Fock of the site-basis 1D Hubbard
+    model, started from the Neel density (Sec. IV.A).
+
+    F_sigma = h + U diag(n_{-sigma}); each spin fills its n_sigma lowest
+    orbitals; the densities are mixed linearly until they change by less
+    than tol.  Returns the per-spin orbital coefficients C [2, L, L] (columns
+    are orbitals in ascending energy), orbital energies e [2, L], densities
+    n [2, L] and the UHF energy.
+    """
+    n_up = L // 2 if n_up is None else n_up
+    n_dn = L - n_up if n_dn is None else n_dn
+    hs = hubbard_1d_sites(L, t, U, pbc)["h"][:L, :L].numpy()
+    dens = np.zeros((2, L))
+    for i in range(L):
+        dens[0, i] = 1.0 if i % 2 == 0 else 0.0
+        dens[1, i] = 1.0 - dens[0, i]
+    occ = (n_up, n_dn)
+    for _ in range(max_iter):
+        C, e, new = [], [], np.zeros((2, L))
+        for sg in range(2):
+            F = hs + U * np.diag(dens[1 - sg])
+            w, v = np.linalg.eigh(F)
+            C.append(v)
+            e.append(w)
+            new[sg] = np.sum(v[:, :occ[sg]] ** 2, axis=1)
+        diff = np.max(np.abs(new - dens))
+        dens = (1.0 - mix) * dens + mix * new
+        if diff < tol:
+            dens = new
+            break
+    C, e = np.array(C), np.array(e)
+    P = [C[sg][:, :occ[sg]] @ C[sg][:, :occ[sg]].T for sg in range(2)]
+    energy = float(sum(np.sum(hs * P[sg]) for sg in range(2)) + U * np.sum(dens[0] * dens[1]))
+    return {"C": C, "e": e, "n": dens, "P": np.array(P), "energy": energy, "h_site": hs}
+
+
+def hubbard_1d_uhf(L, t, U, pbc=True, **scf):
+    """Site-basis 1D Hubbard model in the UHF orbital basis with the UHF
+    reference (Sec. IV.A: the reference is the diagonal of the
+    zero-temperature Fock matrix, here the UHF orbital energies).  Spin
+    orbital sigma * L + k is UHF orbital k of spin sigma."""
+    uhf = uhf_site_hubbard(L, t, U, pbc=pbc, **scf)
+    s = hubbard_1d_sites(L, t, U, pbc)
+    N = 2 * L
+    Cso = torch.zeros((N, N), dtype=DT)   # site spin orbital -> UHF spin orbital
+    Cso[:L, :L] = torch.tensor(uhf["C"][0])
+    Cso[L:, L:] = torch.tensor(uhf["C"][1])
+    h = Cso.T @ s["h"] @ Cso
+    eri = torch.einsum("pqrs,pa,qb,rc,sd->abcd", s["eri"], Cso, Cso, Cso, Cso)
+    eps = torch.tensor(np.concatenate([uhf["e"][0], uhf["e"][1]]), dtype=DT)
+    return {"h": h, "eri": eri, "eps": eps, "kind": "hubbard_uhf", "L": L, "t": t, "U": U, "uhf": uhf}
 
 
 def staggered_magnetisation(rdm1, L):
