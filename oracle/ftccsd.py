@@ -32,6 +32,9 @@ design notes of the repository):
   R7  truncation keeps an orbital as hole-like if n >= thr, particle-like if
       1 - n >= thr.
   R8  the last term of Eq. ccS1 sums over j, k, b, c.
+  R14 the unrelaxed 2-RDM Gamma_N is the Lagrangian's derivative with
+      respect to the integrals of the CC equations and energy at a fixed
+      reference (the printed blocks of App. B are garbled in places).
 """
 import numpy as np
 import torch
@@ -461,6 +464,42 @@ def response(system, beta, mu, ngrid, thr=0.0, solve_kw=None):
     return {"omega": om, "lagrangian": lag.item(), "dOmega_dmu": gm.item(),
             "dOmega_dbeta": dodb, "N": nel, "E": energy_tot,
             "S": float(beta) ** 2 * dodb, "rdm1": rdm1, "solve": sol, "lambda": lam}
+
+
+def rdm2_normal(system, beta, mu, ngrid, thr=0.0, solve_kw=None):
+    """Unrelaxed normal-ordered 2-RDM Gamma_N (reading R14).
+
+    The derivative of the CC Lagrangian (Eqs. Lagrangian, E, ccS1, ccS2) with
+    respect to the antisymmetrised integrals <pq||rs> that enter the CC
+    equations and energy through the thermal blocks, at fixed reference
+    (occupations, Fock matrix, orbital energies), projected onto the
+    antisymmetric tensors: for any perturbation dV with the symmetries of
+    <pq||rs>, dOmega_CC = sum_pqrs Gamma[p, q, r, s] dV[p, q, r, s].
+    """
+    solve_kw = solve_kw or {}
+    prob0 = Problem(system, beta, mu, ngrid, thr)
+    sol = solve(prob0, **solve_kw)
+    lam = lambda_solve(prob0, sol["t1"], sol["t2"])
+    eri = system["eri"].detach().clone().requires_grad_(True)
+    prob = Problem(system, beta, mu, ngrid, thr)   # reference from the unperturbed integrals
+    prob.eri = eri
+    prob.clear_cache()
+    t1, t2 = sol["t1"].detach(), sol["t2"].detach()
+    p1, p2 = fixed_point_map(prob, t1, t2)
+    lag = omega_cc(prob, t1, t2) + torch.sum(lam["m1"] * (t1 - p1)) + torch.sum(lam["m2"] * (t2 - p2))
+    (g,) = torch.autograd.grad(lag, eri)
+    g = 0.5 * (g - g.permute(1, 0, 2, 3))
+    return 0.5 * (g - g.permute(0, 1, 3, 2))
+
+
+def omega_cc_frozen_reference(system, beta, mu, ngrid, eri_cc, thr=0.0, **kw):
+    """Converged Omega_CC with the CC equations and energy built from eri_cc
+    and the reference (n, f, eps) from system["eri"] (for finite-difference
+    checks of rdm2_normal)."""
+    prob = Problem(system, beta, mu, ngrid, thr)
+    prob.eri = eri_cc
+    prob.clear_cache()
+    return solve(prob, **kw)["omega_cc"]
 
 
 def omega_at(system, beta, mu, ngrid, thr=0.0, **kw):
