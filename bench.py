@@ -384,6 +384,34 @@ def run_gpu(args, rank, world):
                     else "measured bf16 burst / 3 (three bf16 products per FP32-accurate one)",
                     "share_of_iteration": g[0]["ms"] / sum(r["ms"] for r in ks)}
         ctx_u.close()
+        # the dense O(N^6) contraction of that sweep on its own: the particle
+        # ladder of one 8-point tau chunk, [8*12996 x 12996] . [12996 x 12996]^T,
+        # through ftcc_gemm (host-timed between synchronisations; the call's
+        # host work is negligible beside its ~40 ms); the class figure above
+        # also holds the short-K, memory-bound products
+        try:
+            nn = 114 * 114
+            ctx_g = ftcc.Context(dev)
+            ga = torch.randn((1, 8 * nn, nn), device="cuda", dtype=torch.float32)
+            gb = torch.randn((1, nn, nn), device="cuda", dtype=torch.float32)
+            fl_g = 2.0 * 8 * nn * nn * nn
+            for prec in ("tf32", "bf16x3"):
+                ctx_g.gemm(ga, gb, precision=prec)   # warm
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    del_c = ctx_g.gemm(ga, gb, precision=prec)
+                    del del_c
+                torch.cuda.synchronize()
+                t_g = (time.perf_counter() - t0) / 3
+                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
+                ueg.setdefault(prec, {})["dense_ladder_gemm"] = {
+                    "shape_bmnk": [1, 8 * nn, nn, nn], "ms": t_g * 1e3, "tflops": fl_g / t_g / 1e12,
+                    "frac_of_peak": fl_g / t_g / 1e12 / pk}
+            del ga, gb
+            ctx_g.close()
+        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
+            ueg["dense_ladder_gemm_error"] = f"{type(e).__name__}: {e}"[:300]
 
     # the 162-orbital gas (UEG, 81 plane waves, 40 tau points), streamed over
     # tau (S kept for one window, Simpson chain carried): one TF32 iteration
