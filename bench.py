@@ -242,33 +242,6 @@ def run_gpu(args, rank, world):
         for c in ctxs:
             c.close()
 
-    # the differential form (Eq. smud, Alg. 1): an RK4 / RK2 march of the same
-    # batch in FP64, host-timed whole solves beside the FP64 Simpson fixed
-    # point (the paper's Table II compares these costs); a failure here is
-    # reported in the line, not raised
-    rk = None
-    if not args.quick and world == 1:
-        rk = {"workload": WORKLOAD + ", FP64, one batched solve each (host-timed, synchronised)"}
-        try:
-            for name, quad, kw in (("simpson_fp64", ftcc.QUAD_SIMPSON, {"max_iter": 300}),
-                                   ("rk4_fp64", ftcc.QUAD_RK4, {}), ("rk2_fp64", ftcc.QUAD_RK2, {})):
-                ctxs = built()
-                try:
-                    ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)  # warm
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
-                    torch.cuda.synchronize()
-                    rk[name] = {"s_total": time.perf_counter() - t0, "iterations_or_steps": res[0]["iterations"],
-                                "omega": [r["omega"] for r in res]}
-                finally:
-                    for c in ctxs:
-                        c.close()
-            rk["rk4_minus_simpson_omega"] = [a - b for a, b in zip(rk["rk4_fp64"]["omega"],
-                                                                   rk["simpson_fp64"]["omega"])]
-        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
-            rk["error"] = f"{type(e).__name__}: {e}"[:300]
-
     def make_ctxs(prec):
         out = built()
         ftcc.prepare_batched(out, betas, mus, cfgs[0]["ngrid"], precision=prec)
@@ -384,33 +357,6 @@ def run_gpu(args, rank, world):
                     else "measured bf16 burst / 3 (three bf16 products per FP32-accurate one)",
                     "share_of_iteration": g[0]["ms"] / sum(r["ms"] for r in ks)}
         ctx_u.close()
-        # the dense O(N^6) contraction of that sweep on its own: the particle
-        # ladder of one 8-point tau chunk, [8*12996 x 12996] . [12996 x 12996]^T,
-        # through ftcc_gemm (host-timed between synchronisations; the call's
-        # host work is negligible beside its ~40 ms); the class figure above
-        # also holds the short-K, memory-bound products
-        try:
-            nn = 114 * 114
-            ctx_g = ftcc.Context(dev)
-            ga = torch.randn((1, 8 * nn, nn), device="cuda", dtype=torch.float32)
-            gb = torch.randn((1, nn, nn), device="cuda", dtype=torch.float32)
-            fl_g = 2.0 * 8 * nn * nn * nn
-            for prec in ("tf32", "bf16x3"):
-                ctx_g.gemm(ga, gb, precision=prec)   # warm
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(3):
-                    ctx_g.gemm(ga, gb, precision=prec)   # output dropped at once
-                torch.cuda.synchronize()
-                t_g = (time.perf_counter() - t0) / 3
-                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
-                ueg.setdefault(prec, {})["dense_ladder_gemm"] = {
-                    "shape_bmnk": [1, 8 * nn, nn, nn], "ms": t_g * 1e3, "tflops": fl_g / t_g / 1e12,
-                    "frac_of_peak": fl_g / t_g / 1e12 / pk}
-            del ga, gb
-            ctx_g.close()
-        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
-            ueg["dense_ladder_gemm_error"] = f"{type(e).__name__}: {e}"[:300]
 
     # the 162-orbital gas (UEG, 81 plane waves, 40 tau points), streamed over
     # tau (S kept for one window, Simpson chain carried): one TF32 iteration
@@ -494,6 +440,63 @@ def run_gpu(args, rank, world):
         bat64["adjoint_scope"] = "instances with L <= 8 (12 and 16 spin orbitals)"
         for x in ctx_b:
             x.close()
+
+    # (the two measurements below run last: a fault in either can only cost its own field)
+    if not args.no_ueg and world == 1:
+        # the dense O(N^6) contraction of that sweep on its own: the particle
+        # ladder of one 8-point tau chunk, [8*12996 x 12996] . [12996 x 12996]^T,
+        # through ftcc_gemm (host-timed between synchronisations; the call's
+        # host work is negligible beside its ~40 ms); the class figure above
+        # also holds the short-K, memory-bound products
+        try:
+            nn = 114 * 114
+            ctx_g = ftcc.Context(dev)
+            ga = torch.randn((1, 8 * nn, nn), device="cuda", dtype=torch.float32)
+            gb = torch.randn((1, nn, nn), device="cuda", dtype=torch.float32)
+            fl_g = 2.0 * 8 * nn * nn * nn
+            for prec in ("tf32", "bf16x3"):
+                ctx_g.gemm(ga, gb, precision=prec)   # warm
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    ctx_g.gemm(ga, gb, precision=prec)   # output dropped at once
+                torch.cuda.synchronize()
+                t_g = (time.perf_counter() - t0) / 3
+                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
+                ueg.setdefault(prec, {})["dense_ladder_gemm"] = {
+                    "shape_bmnk": [1, 8 * nn, nn, nn], "ms": t_g * 1e3, "tflops": fl_g / t_g / 1e12,
+                    "frac_of_peak": fl_g / t_g / 1e12 / pk}
+            del ga, gb
+            ctx_g.close()
+        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
+            ueg["dense_ladder_gemm_error"] = f"{type(e).__name__}: {e}"[:300]
+
+    # the differential form (Eq. smud, Alg. 1): an RK4 / RK2 march of the same
+    # batch in FP64, host-timed whole solves beside the FP64 Simpson fixed
+    # point (the paper's Table II compares these costs); a failure here is
+    # reported in the line, not raised
+    rk = None
+    if not args.quick and world == 1:
+        rk = {"workload": WORKLOAD + ", FP64, one batched solve each (host-timed, synchronised)"}
+        try:
+            for name, quad, kw in (("simpson_fp64", ftcc.QUAD_SIMPSON, {"max_iter": 300}),
+                                   ("rk4_fp64", ftcc.QUAD_RK4, {}), ("rk2_fp64", ftcc.QUAD_RK2, {})):
+                ctxs = built()
+                try:
+                    ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)  # warm
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
+                    torch.cuda.synchronize()
+                    rk[name] = {"s_total": time.perf_counter() - t0, "iterations_or_steps": res[0]["iterations"],
+                                "omega": [r["omega"] for r in res]}
+                finally:
+                    for c in ctxs:
+                        c.close()
+            rk["rk4_minus_simpson_omega"] = [a - b for a, b in zip(rk["rk4_fp64"]["omega"],
+                                                                   rk["simpson_fp64"]["omega"])]
+        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
+            rk["error"] = f"{type(e).__name__}: {e}"[:300]
 
     # roofline of the dominant kernel class of the timed step (events inside the graph)
     hbm, bf16, bf16s, src = peaks()
