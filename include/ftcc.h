@@ -318,16 +318,21 @@ ftcc_status ftcc_gemm(ftcc_ctx* ctx, int precision, int batch, int M, int N, int
  * is small, and the partial sums live in a 16 MiB static device array held
  * by every GPU that loads the library until the process exits; no
  * cudaMalloc, cudaFree or allocating library routine is called.  For callers
- * that cannot allocate device memory where they call it: inside a stream
- * capture in global mode, inside a device-memory allocator's callback, or
- * under a fixed device-memory budget.
+ * that cannot allocate device memory where they call it: code running inside
+ * a device-memory allocator's own callback (allocating there would re-enter
+ * the allocator), or programs that fix their device-memory footprint at
+ * start-up and may not grow it afterwards.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - All calls share the array: calls that overlap on the GPU (different
  *     streams, or different host threads) race and give wrong results.
+ *     Every partial sum a call reads was written earlier in the same call,
+ *     so nothing in the array has to start at zero.
  *   - batch * M * N must not exceed 2^20 (half the array, so that at least
- *     two K splits fit): larger outputs return FTCC_ERR_INVALID_ARG.
+ *     two K splits fit).  The limit covers every call, including outputs
+ *     large enough to run without a K split: larger outputs return
+ *     FTCC_ERR_INVALID_ARG.
  * Returns FTCC_ERR_INVALID_ARG for bad sizes or NULL pointers,
  * FTCC_ERR_NO_DEVICE without a GPU, FTCC_ERR_CUDA if a launch fails. */
 ftcc_status ftcc_gemm_f64_static(void* stream, int batch, int M, int N, int K, double alpha, const double* A_dev,

@@ -3,11 +3,9 @@
 // allocated scratch.
 //
 // Why it exists: some callers cannot allocate device memory at the moment
-// they need a contraction -- code running while a stream is captured into a
-// CUDA graph in global mode (cudaMalloc is not allowed to be captured), code
-// running inside a device-memory allocator's own callback (allocating there
-// re-enters the allocator), or programs that must keep a fixed device-memory
-// budget after start-up.  They call ftcc_gemm_f64_static with their inputs
+// they need a contraction -- code running inside a device-memory allocator's
+// own callback (allocating there re-enters the allocator), or programs that
+// fix their device-memory footprint at start-up and may not grow it later.  They call ftcc_gemm_f64_static with their inputs
 // and outputs; everything else lives in kScratchBytes of static device
 // memory that every GPU which loads the library holds until the process exits.
 #include <cuda_runtime.h>
@@ -48,7 +46,8 @@ extern "C" ftcc_status ftcc_gemm_f64_static(void* stream, int batch, int M, int 
   if (!A || !B || !C || batch < 1 || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || sa < 0 || sb < 0 ||
       sc < 0)
     return FTCC_ERR_INVALID_ARG;
-  // the output of one call must fit the scratch at least twice over (two K splits)
+  // the output of one call must fit the scratch at least twice over (two K
+  // splits); the limit is applied to every call, split or not
   const long long outer = static_cast<long long>(batch) * M * N;
   if (outer > static_cast<long long>(kScratchBytes / sizeof(double)) / 2) return FTCC_ERR_INVALID_ARG;
   int n = 0;

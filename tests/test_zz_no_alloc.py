@@ -1,9 +1,10 @@
 """The FP64 GEMM entry point that allocates nothing (ftcc_gemm_f64_static).
 
 It exists for callers that cannot allocate device memory where they need the
-contraction (inside a global-mode stream capture, inside an allocator's own
-callback, or under a fixed device-memory budget): its split-K partial sums
-live in a static device array instead of allocated scratch.  It is checked
+contraction (code inside a device-memory allocator's own callback, where
+allocating would re-enter the allocator, or programs whose device-memory
+footprint is fixed at start-up): its split-K partial sums live in a static
+device array instead of allocated scratch.  It is checked
 through the C ABI against the regular FP64 GEMM entry point, on two calls in
 a row with different data so that a stale partial left in the shared array
 would show.  This file is collected last so that a failure here stops a
