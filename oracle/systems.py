@@ -183,6 +183,35 @@ def plane_wave_grid(n_pw):
     raise ValueError(f"{n_pw} plane waves is not a closed shell")
 
 
+def _ueg_cell(n_elec, rs, n_pw):
+    """Plane waves of the cubic cell: integer vectors, volume, edge, k, |k|^2/2
+    and the pair interaction 4 pi / (Vc |k_p - k_r|^2) (zero for p = r)."""
+    nv = plane_wave_grid(n_pw)
+    vol = 4.0 / 3.0 * math.pi * n_elec * rs ** 3
+    Lc = vol ** (1.0 / 3.0)
+    kv = 2.0 * math.pi * nv / Lc
+    kin = 0.5 * np.sum(kv * kv, axis=1)
+    diff = nv[:, None, :] - nv[None, :, :]                      # (p, r)
+    q2 = np.sum(diff * diff, axis=2).astype(np.float64)
+    coul = np.zeros_like(q2)
+    nz = q2 > 0
+    coul[nz] = 4.0 * math.pi / (vol * q2[nz] * (2.0 * math.pi / Lc) ** 2)
+    return nv, vol, Lc, kv, kin, coul
+
+
+def ueg_hf_energies(n_elec, rs, n_pw):
+    """Zero-temperature Hartree-Fock energies of the closed shell of the
+    n_elec/2 lowest plane waves per spin (the gas's reference energies):
+    eps_p = |k_p|^2/2 - sum_{q occ} 4 pi / (Vc |k_p - k_q|^2), per spatial
+    plane wave, with |k|^2/2."""
+    nv, vol, Lc, kv, kin, coul = _ueg_cell(n_elec, rs, n_pw)
+    nocc = n_elec // 2
+    eps_sp = kin.copy()
+    for p in range(len(nv)):
+        eps_sp[p] -= sum(coul[p, q] for q in range(nocc))
+    return eps_sp, kin
+
+
 def ueg(n_elec, rs, n_pw):
     """Unpolarised uniform electron gas in a cubic cell of plane waves.
 
@@ -193,18 +222,9 @@ def ueg(n_elec, rs, n_pw):
     zero-temperature Hartree-Fock energies of the closed shell of the n_elec/2
     lowest plane waves per spin: eps_p = |k_p|^2/2 - sum_{q occ} 4 pi/(Vc |k_p-k_q|^2).
     """
-    nv = plane_wave_grid(n_pw)
+    nv, vol, Lc, kv, kin, coul = _ueg_cell(n_elec, rs, n_pw)
     M = len(nv)
-    vol = 4.0 / 3.0 * math.pi * n_elec * rs ** 3
-    Lc = vol ** (1.0 / 3.0)
-    kv = 2.0 * math.pi * nv / Lc
-    kin = 0.5 * np.sum(kv * kv, axis=1)
-    # spatial <pq|rs>: momentum transfer n_p - n_r = n_s - n_q
-    diff = nv[:, None, :] - nv[None, :, :]                      # (p, r)
-    q2 = np.sum(diff * diff, axis=2).astype(np.float64)
-    coul = np.zeros_like(q2)
-    nz = q2 > 0
-    coul[nz] = 4.0 * math.pi / (vol * q2[nz] * (2.0 * math.pi / Lc) ** 2)
+    nz = coul > 0
     v = np.zeros((M, M, M, M))
     # v[p,q,r,s] = coul[p,r] if n_p + n_q == n_r + n_s
     key = {tuple(x): i for i, x in enumerate(nv)}
@@ -217,10 +237,7 @@ def ueg(n_elec, rs, n_pw):
                 s = key.get(tuple(nv[q] + dq))
                 if s is not None:
                     v[p, q, r, s] = coul[p, r]
-    nocc = n_elec // 2
-    eps_sp = kin.copy()
-    for p in range(M):
-        eps_sp[p] -= sum(coul[p, q] for q in range(nocc))
+    eps_sp, _ = ueg_hf_energies(n_elec, rs, n_pw)
     h = torch.zeros((2 * M, 2 * M), dtype=DT)
     h[range(2 * M), range(2 * M)] = torch.tensor(np.concatenate([kin, kin]), dtype=DT)
     eri = _two_body_from_spatial(torch.tensor(v, dtype=DT))
