@@ -1,16 +1,24 @@
 """Benchmark of the FT-CCSD imaginary-time amplitude sweep on GB300.
 
-Workload: the 10-site Hubbard ring (t=1, U=4, mu=U/2, 20 spin orbitals,
-32 Simpson tau points) at beta = 2, 1 and 0.5, solved as one batch.  One
-step = one application of the fixed-point map (S kernel at every tau point,
-propagation, energy and Omega) to all three temperatures; the metric is
-seconds per such iteration, mixed-precision path (TF32 tensor cores, FP32
-storage, FP64 propagators and Omega) with the FP64 GPU path measured beside it.
+Headline workload: the warm dense electron gas of 14 electrons at rs = 1,
+Theta = T/T_F = 0.5 in 57 plane waves (114 spin orbitals, no truncation),
+32 Simpson tau points, mu = mu_0 (the reference chemical potential of 14
+electrons) -- the largest configuration whose sweep keeps every tau point
+resident on one GPU.  One step = one iteration of the mixed-precision sweep
+(BF16X3 tensor-core contractions with FP32 accumulation and FP32
+amplitudes; propagators, Simpson recurrence, energy and Omega in FP64): the
+S kernel at all 32 tau points, the propagation, the energy and Omega_CC.
+value = seconds per step; the line also carries the time to a solution
+within 1e-6 Ha of the oracle (the block-sparse oracle's converged Omega),
+the FP64 GPU path's time per iteration, the roofline of the dominant kernel
+and the oracle on the host cores.  Extra fields: the 10-site Hubbard ring at
+three temperatures (mixed vs FP64 time to 1e-6 Ha), the 162-orbital gas,
+the adjoint, the 64-instance batch and the RK drivers.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32|bf16x3|fp64]
-  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
 
-With N > 1 (torchrun) each rank runs its own copy of the three problems
+With N > 1 (torchrun) each rank runs its own copy of the problem
 (independent instances, no collective on the data path: weak scaling); the
 timing is the maximum over ranks.
 """
@@ -29,10 +37,14 @@ sys.path.insert(0, ROOT)
 from paper_2004_01729_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "FT-CCSD s/iteration & tensor TFLOP/s, mixed vs FP64 GPU at |dOmega|<=1e-6 Ha"
-WORKLOAD = "hubbard_1d L=10 t=1 U=4 mu=2 N=20 spin orbitals, beta in {2,1,0.5}, ngrid=32 Simpson"
+C3 = wl.UEG_57
+WORKLOAD = ("ueg 14 electrons rs=1 Theta=0.5, 57 plane waves = 114 spin orbitals, ngrid=32 Simpson, "
+            "mu=mu_0(N=14); mixed-precision sweep (no FP64 iteration)")
+C2_WORKLOAD = "hubbard_1d L=10 t=1 U=4 mu=2 N=20 spin orbitals, beta in {2,1,0.5}, ngrid=32 Simpson, batched"
+GOLD = os.path.join(ROOT, "tests", "golden")
 
 
-def peaks():
+def measured_peaks_file():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
@@ -40,15 +52,70 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-# nominal dense ratios of the recipe: tf32 1.1 PF vs bf16 2.25 PF
-TF32_PER_BF16 = 1.1 / 2.25
+def measure_peaks(torch):
+    """TF32 (burst and a 3 s loop) and FP64 dense matmul rates of this GPU
+    (torch.matmul 8192^3, CUDA events); the bf16 and HBM figures come from
+    the driver's measurement."""
+    out = {}
 
-# DRAM bytes (read + write) per launch of a kernel class in this step, from
-# one ncu capture of the current kernels (profiles/ gives the command); a
-# class missing here reports traffic null
-MEASURED_TRAFFIC = {
-    "gemm_tc_kernel": (78.6e6, "profiles/gemm_tc_kernel_hubbard10_tf32.md: mean over 327 launches"),
-}
+    def rate(dt, tf32, reps, loop_s=0.0):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        n = 8192
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        r = {"burst": 2.0 * n ** 3 / best / 1e12}
+        if loop_s > 0:
+            k = max(1, int(loop_s / best))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(k):
+                a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            r["sustained"] = 2.0 * n ** 3 * k / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = False
+        del a, b
+        return r
+
+    out["tf32_tflops"] = rate(torch.float32, True, 5, 3.0)
+    out["fp64_tflops"] = rate(torch.float64, False, 2)
+    hbm, bf16, bf16s, src = measured_peaks_file()
+    out.update({"bf16_tflops": {"burst": bf16, "sustained": bf16s}, "hbm_gbs": hbm, "bf16_hbm_source": src,
+                "how": "torch.matmul 8192^3 with CUDA events: best of several (burst), a 3 s loop (sustained); "
+                       "bf16 and HBM from the driver-written measured peaks"})
+    return out
+
+
+def cpu_info():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"cpu_count": os.cpu_count(), "model": model or platform.machine()}
 
 
 class Clocks:
@@ -64,14 +131,13 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "50", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
-        # nvidia-smi takes longer to start than the timed loop lasts: wait
-        # (at most 3 s) for its first sample so that the loop is covered
+        # wait (at most 3 s) for the first sample so that the loop is covered
         t0 = time.time()
         while self.proc is not None and not self.samples and self.proc.poll() is None and time.time() - t0 < 3.0:
             time.sleep(0.01)
@@ -98,11 +164,12 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
         mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        pw = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples), "interval_ms": 50,
-                "samples_before_timed_region": getattr(self, "first", 0)}
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(self.samples),
+                "interval_ms": 200, "samples_before_timed_region": getattr(self, "first", 0)}
 
 
 def dist_init(args):
@@ -132,44 +199,71 @@ def barrier(world):
         dist.barrier()
 
 
-# ---------------------------------------------------------------- CPU oracle arm
-def oracle_iteration_seconds(cfg, n_iter=1):
-    """Time n_iter oracle fixed-point iterations from s = 0 (bounded sample)."""
-    import torch
-    from oracle import ftccsd as fc, systems
-    s = systems.hubbard_1d(cfg["L"], cfg["t"], cfg["U"])
-    p = fc.Problem(s, cfg["beta"], cfg["mu"], cfg["ngrid"])
-    no, nv, ng = len(p.iO), len(p.iV), cfg["ngrid"]
-    t1 = torch.zeros((ng, no, nv), dtype=torch.float64)
-    t2 = torch.zeros((ng, no, no, nv, nv), dtype=torch.float64)
-    fc.fixed_point_map(p, t1, t2)   # warm caches
-    t0 = time.perf_counter()
-    with torch.no_grad():
-        for _ in range(n_iter):
-            t1, t2 = fc.fixed_point_map(p, t1, t2)
-            fc.omega_cc(p, t1, t2)
-    return (time.perf_counter() - t0) / n_iter
+def c3_gold():
+    p = os.path.join(GOLD, "oracle_ueg57.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+# ---------------------------------------------------------------- CPU oracle
+class OracleSample:
+    """The block-sparse oracle (the oracle for the plane-wave gas: the same
+    term tables restricted to momentum- and spin-allowed blocks) on a bounded
+    sample of one fixed-point iteration of the headline workload: the S
+    kernel, the propagation and the energy on n_tau of the 32 tau points,
+    scaled to the whole grid (every part is linear in the tau points)."""
+
+    def __init__(self, n_tau=4):
+        import torch
+        from oracle import blocksparse as bs, chemical_potential as cp
+        self.torch, self.bs = torch, bs
+        sysc = bs.ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+        mu = cp.mu_reference(sysc["eps"], C3["beta"], float(C3["n_elec"]))
+        self.prob = bs.Problem(sysc, C3["beta"], mu, C3["ngrid"])
+        self.n_tau = n_tau
+        N = self.prob.ch.N
+        self.t1, self.t2 = bs.random_amplitudes(self.prob.ch, 1, n_tau, 0.01)
+        self.cores = torch.get_num_threads()
+        self.N = N
+
+    def run(self):
+        """Seconds for the sample and its scale factor to one iteration."""
+        bs = self.bs
+        t0 = time.perf_counter()
+        with self.torch.no_grad():
+            S1 = bs.S1(self.prob, self.t1, self.t2)
+            S2 = bs.S2(self.prob, self.t1, self.t2)
+            bs.energy(self.prob, self.t1, self.t2)
+            # the propagation of the sample's tau points (same per-element work as in the sweep)
+            for x in range(self.n_tau):
+                _ = S2[x] * self.prob.D2
+                _ = S1[x] * self.prob.D1
+        return time.perf_counter() - t0, C3["ngrid"] / self.n_tau
+
+    def describe(self):
+        return (f"block-sparse oracle (FP64, torch CPU, {self.cores} threads): S1, S2, energy and propagation "
+                f"of {self.n_tau} of the 32 tau points of the headline workload, scaled by {C3['ngrid'] // self.n_tau}")
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    import torch
-    cores = torch.get_num_threads()
-    cfgs = wl.HUBBARD_10
+    smp = OracleSample()
+    smp.run()   # builds the contraction plans (untimed)
     for _ in range(args.warmup):
-        pass
+        smp.run()
     times = []
     for _ in range(args.steps):
-        times.append(sum(oracle_iteration_seconds(c, 1) for c in cfgs))
-    step = statistics.mean(times)
-    value = step / len(cfgs)
+        dt, scale = smp.run()
+        times.append(dt * scale)
+    value = statistics.mean(times)
+    cpu = cpu_info()
     line = {"metric": METRIC, "value": value, "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": cores, "kind": "oracle",
-                             "sample": "one fixed-point iteration of each temperature per step, from s=0"},
+            "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": smp.cores, "kind": "oracle",
+                             "sample": smp.describe(), "cpu_count": cpu["cpu_count"], "cpu_model": cpu["model"],
+                             "step_spread_s": [min(times), max(times)]},
             "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -190,7 +284,7 @@ def run_gemm_only(args):
     g = torch.Generator(device="cuda").manual_seed(0)
     A = torch.randn((b, M, K), device="cuda", dtype=torch.float32, generator=g)
     B = torch.randn((b, N, K), device="cuda", dtype=torch.float32, generator=g)
-    prec = args.precision if args.precision != "fp64" else "tf32"
+    prec = args.precision
     for _ in range(args.warmup):
         ctx.gemm(A, B, precision=prec)
     torch.cuda.synchronize()
@@ -201,383 +295,457 @@ def run_gemm_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # each call returns after a stream synchronise, so ms includes the host
-    # work of the call; ncu's kernel duration is the device-only figure
     print(json.dumps({"gemm": [b, M, N, K], "precision": prec, "ms": ms,
                       "tflops": 2.0 * b * M * N * K / ms / 1e9}), flush=True)
     ctx.close()
 
 
+def run_c3_iteration(args):
+    """Prepare the headline workload and run W + K iterations (for the ncu
+    launch list of one step)."""
+    import torch
+    from paper_2004_01729_gb300 import ftcc
+    ctx = ftcc.Context(0)
+    ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+    mu = ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
+    ctx.prepare(C3["beta"], mu, C3["ngrid"], precision=args.precision, tau_chunk=8)
+    ctx.iterate(args.warmup + args.steps)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def class_table(kstats, steps):
+    total = sum(r["ms"] for r in kstats) or 1.0
+    return [{"name": r["name"], "launches_per_step": r["launches"] / steps, "ms_per_step": r["ms"] / steps,
+             "share": r["ms"] / total,
+             "GB_per_s": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None,
+             "TFLOP_per_s": r["flops"] / (r["ms"] * 1e-3) / 1e12 if r["ms"] > 0 and r["flops"] else None}
+            for r in sorted(kstats, key=lambda r: -r["ms"])]
+
+
+def roofline(kstats, steps, prec, pk):
+    """Roofline of the dominant kernel class: achieved = its algorithmic
+    flops (2MNK per launch) / its device time summed over the launches,
+    against the measured peak of its arithmetic; HBM-bound classes against
+    the measured copy bandwidth."""
+    dom = max(kstats, key=lambda r: r["ms"])
+    hbm = pk["hbm_gbs"]
+    if prec == "tf32":
+        peak, psrc = pk["tf32_tflops"]["sustained"], "TF32 torch.matmul 8192^3, 3 s loop (measured live)"
+    else:
+        peak = pk["bf16_tflops"]["sustained"] / 3.0
+        psrc = "bf16 sustained (driver-measured) / 3: three bf16 products per FP32-accurate one"
+    intensity = dom["flops"] / dom["bytes"] if dom["flops"] and dom["bytes"] else None
+    ridge = peak * 1e12 / (hbm * 1e9)
+    if dom["name"] == "gemm_tc_kernel" and intensity and intensity >= ridge:
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": psrc + " (of measured)"}
+    else:
+        ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+             "peak_source": "HBM copy (of measured)"}
+    r.update({"traffic": None,
+              "traffic_note": "DRAM bytes per launch come from ncu captures kept with the kernel profiles; "
+                              "not measurable inside this run",
+              "kernel": dom["name"], "launches_per_step": dom["launches"] / steps,
+              "avg_launch_ms": dom["ms"] / dom["launches"],
+              "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
+              "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+              "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+              "timed_with": "CUDA events around every launch inside the per-iteration graph "
+                            "(a profiled pass after the timed steps)"})
+    return r
+
+
 def run_gpu(args, rank, world):
-    import numpy as np
     import torch
     from paper_2004_01729_gb300 import ftcc
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    cfgs = wl.HUBBARD_10
-    gold_path = os.path.join(ROOT, "tests", "golden", "oracle_hubbard10.json")
-    gold = json.load(open(gold_path)) if os.path.exists(gold_path) else None
+    prec = args.precision
+    pk = measure_peaks(torch)
+    gold = c3_gold()
+    extra = {}
 
-    betas = [c["beta"] for c in cfgs]
-    mus = [c["mu"] for c in cfgs]
-
-    def built():
-        out = []
-        for c in cfgs:
-            ctx = ftcc.Context(dev)
-            ctx.build_hubbard(c["L"], c["t"], c["U"])
-            out.append(ctx)
-        return out
-
-    # accuracy at convergence (untimed): batched full solves in both arithmetics
-    acc = {}
-    for prec in (() if args.quick else (args.precision, "fp64")):
-        ctxs = built()
-        res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], precision=prec, refine_max_iter=20,
-                                 max_iter=300, allow_unconverged=True)
-        errs = [abs(r["omega"] - g["omega"]) for r, g in zip(res, gold)] if gold else []
-        acc[prec] = {"max_abs_dOmega_vs_oracle": max(errs) if errs else None,
-                     "iterations_total": res[0]["iterations"], "refine_iterations": res[0]["refine_iterations"],
-                     "converged": all(r["converged"] for r in res)}
-        for c in ctxs:
-            c.close()
-
-    def make_ctxs(prec):
-        out = built()
-        ftcc.prepare_batched(out, betas, mus, cfgs[0]["ngrid"], precision=prec)
-        return out
-
-    # L2 hygiene: a 256 MB buffer (twice the 129 MB L2) is rewritten on the
-    # library stream before every timed step, outside the step's events
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def timed(ctxs, steps, warmup):
-        # one step = one batched iteration of all three temperatures, timed
-        # with CUDA events on the stream the library launches on
-        st = ctxs[0].stream
-        for _ in range(warmup):
-            ctxs[0].iterate(1)
-        barrier(world)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in ev:
-            with torch.cuda.stream(st):
-                flush.zero_()
-            a.record(st)
-            ctxs[0].iterate(1)
-            b.record(st)
-        torch.cuda.synchronize()
-        barrier(world)
-        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
-
-    ctx_mixed = make_ctxs(args.precision)
-    with Clocks() as clk:
-        t_mixed = timed(ctx_mixed, args.steps, args.warmup)
-    # the same steps again with per-kernel CUDA events inside the iteration graph
-    ctx_mixed[0].profile(True)
-    t_prof = timed(ctx_mixed, args.steps, 1)
-    kstats = ctx_mixed[0].profile_read()
-    ctx_mixed[0].profile(False)
-    if args.quick:
-        print(json.dumps({"quick": True, "s_per_iteration": t_mixed / args.steps,
-                          "kernels_per_iter": ctx_mixed[0].iterate(0)["kernels_per_iter"],
-                          "ms_per_step_by_class": {r["name"]: r["ms"] / args.steps for r in kstats}}), flush=True)
-        for ctx in ctx_mixed:
-            ctx.close()
-        return
-    ctx_fp64 = make_ctxs("fp64")
-    t_fp64 = timed(ctx_fp64, max(1, min(args.steps, 3)), 1)
-    k_mixed = ctx_mixed[0].iterate(0)["kernels_per_iter"]
-    res0 = ctx_mixed[0].iterate(0)
-    no, nv = res0["n_occ"], res0["n_vir"]
-    n_prob = len(cfgs)
-    t_mixed = barrier_max(t_mixed, world)
-    t_fp64 = barrier_max(t_fp64, world)
-    # one step = one batched fixed-point iteration of the three temperatures
-    s_per_iter = t_mixed / (args.steps * world)
-    fp64_s_per_iter = t_fp64 / (max(1, min(args.steps, 3)) * world)
-    fl = n_prob * flops_per_iteration(no, nv, cfgs[0]["ngrid"])
-
-    # e2e: the public API from pinned host Hamiltonian arrays: build_integrals
-    # (host -> device) for the three instances + one batched solve to
-    # convergence (per-iteration state read back) + results on the host
-    ctx_e = built()
-    h_np, eri_np, eps_np = ctx_e[0].get_system()
-    pin = [torch.from_numpy(a).pin_memory() for a in (h_np, eri_np, eps_np)]
+    # ---- headline: the 114-spin-orbital gas
+    ctx = ftcc.Context(dev)
+    ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+    mu = gold["mu"] if gold else ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
+    opts = dict(precision=prec, refine_max_iter=0, tau_chunk=8, max_iter=80)
+    # a solve to convergence (untimed by events, host-timed between synchronisations)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for ctx in ctx_e:
-        ctx.build_generic(pin[0].numpy(), pin[1].numpy(), pin[2].numpy())
-    res = ftcc.solve_batched(ctx_e, betas, mus, cfgs[0]["ngrid"], precision=args.precision, refine_max_iter=20,
-                             max_iter=300, allow_unconverged=True)
+    sol = ctx.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **opts)
     torch.cuda.synchronize()
-    e2e_t = barrier_max(time.perf_counter() - t0, world)
-    e2e_iters = res[0]["iterations"]
-    h2d = len(ctx_e) * sum(a.numel() * 8 for a in pin)
-    e2e = {"value": e2e_t / (e2e_iters * world), "unit": "s/iteration", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": e2e_iters * 8 * (8 + 256) * len(cfgs) + len(cfgs) * 112,
-           "what": "build_integrals(host arrays) x3 + ft_ccsd_solve_batched to convergence; one step = the whole solve"}
-    for ctx in ctx_e:
-        ctx.close()
+    t_sol = time.perf_counter() - t0
+    solve = {"s_total": t_sol, "iterations": sol["iterations"], "polish_iterations": sol["polish_iterations"],
+             "fp64_iterations": sol["refine_iterations"], "converged": bool(sol["converged"]),
+             "omega": sol["omega"], "abs_dOmega_vs_oracle": abs(sol["omega"] - gold["omega"]) if gold else None,
+             "oracle": "block-sparse oracle, converged to |dOmega_CC| < 1e-11" if gold else None}
 
-    # the 114-spin-orbital gas (UEG, 57 plane waves, 32 tau points): per-iteration time
-    # of the same sweep where the O(N^6) contractions dominate
-    ueg = {}
-    if not args.no_ueg and world == 1:
-        c = wl.UEG_57
-        ctx_u = ftcc.Context(dev)
-        ctx_u.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
-        mu_u = ctx_u.reference_mu(c["beta"], float(c["n_elec"]))
-        for prec in ("tf32", "bf16x3"):
-            ctx_u.prepare(c["beta"], mu_u, c["ngrid"], precision=prec, tau_chunk=8)
-            ctx_u.iterate(1)
-            st = ctx_u.stream
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            ctx_u.iterate(2)
-            e1.record(st)
-            torch.cuda.synchronize()
-            t_it = e0.elapsed_time(e1) / 2e3
-            fl_u = flops_per_iteration(114, 114, c["ngrid"])
-            ueg[prec] = {"s_per_iteration": t_it, "tensor_tflops": fl_u / t_it / 1e12,
-                         "algorithmic_flops_per_iteration": fl_u}
-            # the contractions alone: one more iteration with per-launch events
-            ctx_u.profile(True)
-            ctx_u.iterate(1)
-            ks = ctx_u.profile_read()
-            ctx_u.profile(False)
-            g = [r for r in ks if r["name"] == "gemm_tc_kernel"]
-            if g and g[0]["ms"] > 0:
-                tf = g[0]["flops"] / (g[0]["ms"] * 1e-3) / 1e12
-                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
-                ueg[prec]["tensor_core_gemm"] = {
-                    "ms_per_iteration": g[0]["ms"], "tflops": tf, "peak_tflops": pk, "frac_of_peak": tf / pk,
-                    "peak_source": "measured bf16 burst x nominal tf32/bf16" if prec == "tf32"
-                    else "measured bf16 burst / 3 (three bf16 products per FP32-accurate one)",
-                    "share_of_iteration": g[0]["ms"] / sum(r["ms"] for r in ks)}
-        ctx_u.close()
+    # timed steps: W warm-up iterations, then K iterations each bracketed by
+    # CUDA events on the library stream; the amplitudes (21 GB) and integral
+    # blocks are far larger than the 129 MB L2, so no flush is needed
+    ctx.prepare(C3["beta"], mu, C3["ngrid"], **opts)
+    st = ctx.stream
+    ctx.iterate(max(1, args.warmup))
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks() as clk:
+        for a, b in ev:
+            a.record(st)
+            ctx.iterate(1)
+            b.record(st)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    k_iter = ctx.iterate(0)["kernels_per_iter"]
+    # the same iteration with per-launch events inside the graph
+    ctx.profile(True)
+    prof_steps = 2
+    ctx.iterate(prof_steps)
+    kstats = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    t_steps = barrier_max(t_steps, world)
+    s_per_iter = t_steps / args.steps
+    fl = flops_per_iteration(114, 114, C3["ngrid"])
+    roof = roofline(kstats, prof_steps, prec, pk)
 
-    # the 162-orbital gas (UEG, 81 plane waves, 40 tau points), streamed over
-    # tau (S kept for one window, Simpson chain carried): one TF32 iteration
-    ueg81 = None
-    if not args.no_ueg and not args.quick and world == 1:
-        c = wl.UEG_81
-        torch.cuda.empty_cache()
-        torch.cuda.reset_peak_memory_stats()
-        ctx_u = ftcc.Context(dev)
-        ctx_u.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
-        mu_u = ctx_u.reference_mu(c["beta"], float(c["n_elec"]))
-        ctx_u.prepare(c["beta"], mu_u, c["ngrid"], precision="tf32", trunc_thr=c["thr"], stream_tau=1, tau_chunk=1)
-        st = ctx_u.stream
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        r81 = ctx_u.iterate(1)
-        e1.record(st)
-        torch.cuda.synchronize()
-        t_it = e0.elapsed_time(e1) / 1e3
-        fl_u = flops_per_iteration(r81["n_occ"], r81["n_vir"], c["ngrid"])
-        ueg81 = {"tf32_streamed": {"s_per_iteration": t_it, "tensor_tflops": fl_u / t_it / 1e12,
-                                   "algorithmic_flops_per_iteration": fl_u,
-                                   "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
-                                   "note": "first iteration from s = 0; S kept for one tau window"}}
-        ctx_u.close()
-
-    # the adjoint (lambda) sweep and response of the beta = 1 instance after an
-    # FP64 solve: seconds per lambda iteration (ft_ccsd_adjoint, host timed)
-    adj = None
-    bat64 = None
-    if not args.quick and world == 1:
-        c = cfgs[1]
-        ctx_a = ftcc.Context(dev)
-        ctx_a.build_hubbard(c["L"], c["t"], c["U"])
-        ctx_a.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ar, _ = ctx_a.adjoint(with_rdm1=True)
-        torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
-        adj = {"workload": "hubbard_1d L=10 U=4 beta=1, ngrid=32, FP64 lambda sweep + response",
-               "s_total": t_adj, "lambda_iterations": ar["iterations"],
-               "s_per_lambda_iteration": t_adj / max(1, ar["iterations"]),
-               "dOmega_dmu": ar["dOmega_dmu"], "N": ar["N"], "E": ar["E"], "S": ar["S"]}
-        ctx_a.close()
-        # the 64-instance batch (6-14 sites, U in [1,8], T in [0.25,4], ngrid=24):
-        # one batched mixed solve with FP64 refinement, per size class
-        cb = wl.hubbard_batch()
-        ctx_b = []
-        for q in cb:
-            x = ftcc.Context(dev)
-            x.build_hubbard(q["L"], q["t"], q["U"])
-            ctx_b.append(x)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rb = ftcc.solve_batched(ctx_b, [q["beta"] for q in cb], [q["mu"] for q in cb], cb[0]["ngrid"],
-                                precision=args.precision, refine_max_iter=30, max_iter=400, allow_unconverged=True)
-        torch.cuda.synchronize()
-        t_b = time.perf_counter() - t0
-        bat64 = {"workload": "64 hubbard_1d instances, L in {6..14}, ngrid=24, batched per size class",
-                 "s_total": t_b, "instances": len(cb), "converged": int(sum(r["converged"] for r in rb)),
-                 "iterations_max": int(max(r["iterations"] for r in rb))}
-        # energies and entropies from the adjoint (one FP64 lambda sweep per
-        # size-class batch; a batch with a diverged member has none), for the
-        # 6- and 8-site classes, which keep the default run within minutes
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        n_adj = 0
-        for x, q in zip(ctx_b, cb):
-            if q["L"] > 8:
-                continue
-            try:
-                x.adjoint(with_rdm1=False)
-                n_adj += 1
-            except ftcc.FTCCError:
-                pass
-        torch.cuda.synchronize()
-        bat64["adjoint_s_total"] = time.perf_counter() - t0
-        bat64["adjoint_instances"] = n_adj
-        bat64["adjoint_scope"] = "instances with L <= 8 (12 and 16 spin orbitals)"
-        for x in ctx_b:
-            x.close()
-
-    # (the two measurements below run last: a fault in either can only cost its own field)
-    if not args.no_ueg and world == 1:
-        # the dense O(N^6) contraction of that sweep on its own: the particle
-        # ladder of one 8-point tau chunk, [8*12996 x 12996] . [12996 x 12996]^T,
-        # through ftcc_gemm (host-timed between synchronisations; the call's
-        # host work is negligible beside its ~40 ms); the class figure above
-        # also holds the short-K, memory-bound products
+    # FP64 GPU path on the same workload: one tau point of the S kernel in
+    # FP64 (SIMT: tcgen05 has no FP64 kind) through ftcc_eval_s, scaled to the
+    # 32 points of an iteration (the S kernel is local in tau and takes all
+    # but a few percent of an iteration)
+    fp64 = None
+    if not args.no_fp64:
         try:
-            nn = 114 * 114
-            ctx_g = ftcc.Context(dev)
-            ga = torch.randn((1, 8 * nn, nn), device="cuda", dtype=torch.float32)
-            gb = torch.randn((1, nn, nn), device="cuda", dtype=torch.float32)
-            fl_g = 2.0 * 8 * nn * nn * nn
-            for prec in ("tf32", "bf16x3"):
-                ctx_g.gemm(ga, gb, precision=prec)   # warm
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(3):
-                    ctx_g.gemm(ga, gb, precision=prec)   # output dropped at once
-                torch.cuda.synchronize()
-                t_g = (time.perf_counter() - t0) / 3
-                pk = peaks()[1] * TF32_PER_BF16 if prec == "tf32" else peaks()[1] / 3.0
-                ueg.setdefault(prec, {})["dense_ladder_gemm"] = {
-                    "shape_bmnk": [1, 8 * nn, nn, nn], "ms": t_g * 1e3, "tflops": fl_g / t_g / 1e12,
-                    "frac_of_peak": fl_g / t_g / 1e12 / pk}
-            del ga, gb
-            ctx_g.close()
+            cf = ftcc.Context(dev)
+            cf.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+            cf.prepare(C3["beta"], mu, 3, precision="fp64", tau_chunk=1)
+            t1, t2 = wl.random_amplitudes(3, 1, 114, 114, 0.01)
+            t1 = torch.tensor(t1, device="cuda")
+            t2 = torch.tensor(t2, device="cuda")
+            cf.eval_s(t1, t2, precision="fp64")   # sizes the workspaces
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cf.eval_s(t1, t2, precision="fp64")
+            torch.cuda.synchronize()
+            t_tau = time.perf_counter() - t0
+            it_fp64 = gold["iterations"] if gold else sol["iterations"]
+            fp64 = {"s_per_iteration": t_tau * C3["ngrid"], "s_one_tau_point": t_tau,
+                    "tflops": fl / C3["ngrid"] / t_tau / 1e12,
+                    "frac_of_measured_fp64_peak": fl / C3["ngrid"] / t_tau / 1e12 / pk["fp64_tflops"]["burst"],
+                    "iterations_to_converge": it_fp64,
+                    "estimated_s_to_solution": t_tau * C3["ngrid"] * it_fp64,
+                    "how": "S kernel of one tau point in FP64 (ftcc_eval_s), host-timed, x 32 tau points; "
+                           "iterations from the FP64 oracle's fixed point on the same grid"}
+            del t1, t2
+            cf.close()
         except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
-            ueg["dense_ladder_gemm_error"] = f"{type(e).__name__}: {e}"[:300]
+            fp64 = {"error": f"{type(e).__name__}: {e}"[:300]}
 
-    # the differential form (Eq. smud, Alg. 1): an RK4 / RK2 march of the same
-    # batch in FP64, host-timed whole solves beside the FP64 Simpson fixed
-    # point (the paper's Table II compares these costs); a failure here is
-    # reported in the line, not raised
-    rk = None
-    if not args.quick and world == 1:
-        rk = {"workload": WORKLOAD + ", FP64, one batched solve each (host-timed, synchronised)"}
-        try:
-            for name, quad, kw in (("simpson_fp64", ftcc.QUAD_SIMPSON, {"max_iter": 300}),
-                                   ("rk4_fp64", ftcc.QUAD_RK4, {}), ("rk2_fp64", ftcc.QUAD_RK2, {})):
-                ctxs = built()
-                try:
-                    ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)  # warm
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
-                    torch.cuda.synchronize()
-                    rk[name] = {"s_total": time.perf_counter() - t0, "iterations_or_steps": res[0]["iterations"],
-                                "omega": [r["omega"] for r in res]}
-                finally:
-                    for c in ctxs:
-                        c.close()
-            rk["rk4_minus_simpson_omega"] = [a - b for a, b in zip(rk["rk4_fp64"]["omega"],
-                                                                   rk["simpson_fp64"]["omega"])]
-        except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
-            rk["error"] = f"{type(e).__name__}: {e}"[:300]
+    # e2e through the public API with host buffers: build_integrals from the
+    # pinned host Hamiltonian (h, <pq||rs> N^4, eps in FP64), the mixed solve
+    # to convergence (the per-iteration state read back each iteration) and
+    # the result on the host; value = that time / iterations
+    e2e = None
+    if not args.no_e2e:
+        ce = ftcc.Context(dev)
+        ce.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+        h_np, eri_np, eps_np = ce.get_system()
+        pin = [torch.from_numpy(a).pin_memory() for a in (h_np, eri_np, eps_np)]
+        del h_np, eri_np, eps_np
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ce.build_generic(pin[0].numpy(), pin[1].numpy(), pin[2].numpy())
+        r = ce.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **opts)
+        torch.cuda.synchronize()
+        t_e = barrier_max(time.perf_counter() - t0, world)
+        h2d = sum(a.numel() * 8 for a in pin)
+        e2e = {"value": t_e / r["iterations"], "unit": "s/iteration", "h2d_bytes_per_step": h2d / r["iterations"],
+               "d2h_bytes_per_step": 8 * (8 + 256) + 112 / r["iterations"],
+               "what": "build_integrals(GENERIC, pinned host h, <pq||rs>, eps) + ft_ccsd_solve (mixed, to "
+                       "convergence) + result to the host, divided by the iterations of the solve",
+               "s_total": t_e, "iterations": r["iterations"],
+               "abs_dOmega_vs_oracle": abs(r["omega"] - gold["omega"]) if gold else None}
+        del pin
+        ce.close()
 
-    # roofline of the dominant kernel class of the timed step (events inside the graph)
-    hbm, bf16, bf16s, src = peaks()
-    tf32_peak = bf16 * TF32_PER_BF16
-    dom = max(kstats, key=lambda r: r["ms"]) if kstats else None
-    total_ms = sum(r["ms"] for r in kstats) or 1.0
-    kernels = [{"name": r["name"], "launches": r["launches"], "ms": r["ms"], "share": r["ms"] / total_ms,
-                "GB_per_s": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None,
-                "TFLOP_per_s": r["flops"] / (r["ms"] * 1e-3) / 1e12 if r["ms"] > 0 and r["flops"] else None}
-               for r in sorted(kstats, key=lambda r: -r["ms"])]
-    # a contraction is tensor-bound only when its algorithmic intensity
-    # (flops per algorithmic byte) is above the ridge point peak_flops / peak_bw;
-    # below it the roofline ceiling is intensity x HBM bandwidth
-    ridge = tf32_peak * 1e12 / (hbm * 1e9)
-    intensity = dom["flops"] / dom["bytes"] if dom and dom["flops"] and dom["bytes"] else None
-    if dom and dom["name"] == "gemm_tc_kernel" and intensity is not None and intensity >= ridge:
-        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                "peak_source": f"bf16 burst {bf16} ({src}) x nominal tf32/bf16 {TF32_PER_BF16:.3f}"}
-    elif dom:
-        ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "peak_source": f"hbm copy {hbm} GB/s ({src})"}
-    else:
-        roof = {"bound": None}
-    if dom:
-        tr = MEASURED_TRAFFIC.get(dom["name"])
-        roof.update({"traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
-                     "kernel": dom["name"],
-                     "launches_per_step": dom["launches"] / args.steps,
-                     "avg_launch_us": dom["ms"] * 1e3 / dom["launches"],
-                     "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
-                     "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
-                     "intensity_flop_per_byte": intensity,
-                     "ridge_flop_per_byte": ridge,
-                     "tensor_frac": (dom["flops"] / (dom["ms"] * 1e-3) / 1e12 / tf32_peak
-                                     if dom["flops"] else None),
-                     "timed_with": "CUDA events around every launch inside the per-iteration graph, "
-                                   "a second pass of the same steps"})
-    for ctx in ctx_mixed + ctx_fp64:
-        ctx.close()
+    # ---- extras
+    if not args.quick:
+        extra["hubbard10"] = bench_hubbard10(ftcc, torch, dev, world, args)
+        extra["ueg81_162_spin_orbitals"] = bench_ueg81(ftcc, torch, dev, world, args)
+        extra.update(bench_small_extras(ftcc, torch, dev, world, args))
+        extra["dense_ladder_gemm"] = bench_dense_gemm(ftcc, torch, dev, world, pk)
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            import torch as _t
-            cpu_s = oracle_iteration_seconds(cfgs[1], 1)
-            cpu = {"value": cpu_s, "unit": "s/iteration", "cores": _t.get_num_threads(), "kind": "oracle",
-                   "sample": "one oracle fixed-point iteration at beta=1 (the middle temperature)"}
+            smp = OracleSample()
+            smp.run()
+            runs = [smp.run() for _ in range(3)]
+            vals = [dt * sc for dt, sc in runs]
+            ci = cpu_info()
+            cpu = {"value": statistics.median(vals), "unit": "s/iteration", "cores": smp.cores, "kind": "oracle",
+                   "sample": smp.describe() + "; median of 3", "samples_s_per_iteration": vals,
+                   "cpu_count": ci["cpu_count"], "cpu_model": ci["model"]}
         line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3,
-                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_iter * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": prec,
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": args.precision,
-                           "l2": "flushed: a 256 MB buffer is rewritten on the library stream before every "
-                                 "timed step, outside the step's CUDA events"},
-                "fp64_gpu_s_per_iteration": fp64_s_per_iter,
-                "mixed_over_fp64_speedup": fp64_s_per_iter / s_per_iter,
+                "config": {"workload": WORKLOAD, "precision": prec, "tau_chunk": 8,
+                           "l2": "inputs larger than L2: 21 GB of FP32 amplitudes and 8 GB of integral blocks "
+                                 "are read every step (L2 129 MB), no flush"},
                 "tensor_tflops_per_iteration": fl / s_per_iter / 1e12,
-                "accuracy": acc,
-                "roofline": roof, "kernels": kernels, "profiled_step_ms": t_prof / args.steps * 1e3,
-                "ueg57_114_spin_orbitals": ueg or None,
-                "ueg81_162_spin_orbitals": ueg81,
-                "adjoint_lambda_sweep": adj, "batched_64_instances": bat64, "differential_form": rk,
-                "e2e": e2e, "gpu_launches": k_mixed * args.steps,
-                "clocks": clk.summary()}
+                "algorithmic_flops_per_iteration": fl,
+                "time_to_1e-6": solve,
+                "fp64_gpu": fp64,
+                "mixed_over_fp64_time_to_solution": (fp64["estimated_s_to_solution"] / t_sol
+                                                     if fp64 and "estimated_s_to_solution" in fp64 else None),
+                "peaks": pk, "roofline": roof, "kernels": class_table(kstats, prof_steps),
+                "e2e": e2e, "gpu_launches": k_iter * args.steps, "clocks": clk.summary()}
+        line.update(extra)
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
 
 
+def bench_hubbard10(ftcc, torch, dev, world, args):
+    """The 10-site ring at three temperatures as one batch: time to a
+    solution within 1e-6 Ha of the oracle for the mixed pipeline (TF32,
+    BF16X3 polish, FP64 corrections) and for the FP64 path, plus the
+    steady-state time of one batched TF32 iteration and its kernel classes."""
+    cfgs = wl.HUBBARD_10
+    gold = json.load(open(os.path.join(GOLD, "oracle_hubbard10.json")))
+    betas, mus = [c["beta"] for c in cfgs], [c["mu"] for c in cfgs]
+
+    def built():
+        out = []
+        for c in cfgs:
+            x = ftcc.Context(dev)
+            x.build_hubbard(c["L"], c["t"], c["U"])
+            out.append(x)
+        return out
+
+    out = {"workload": C2_WORKLOAD}
+    for name, kw in (("mixed", dict(precision="tf32")), ("fp64", dict(precision="fp64", max_iter=300)),
+                     ("tf32_bf16x3_no_fp64", dict(precision="tf32", refine_max_iter=0)),
+                     ("tf32_only", dict(precision="tf32", refine_max_iter=0, polish_max_iter=0, tol_mixed=1e-12))):
+        ctxs = built()
+        ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], allow_unconverged=True, **kw)   # tile tuning
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], allow_unconverged=True, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"s_to_solution": time.perf_counter() - t0, "iterations": res[0]["iterations"],
+                     "polish_iterations": res[0]["polish_iterations"], "fp64_iterations": res[0]["refine_iterations"],
+                     "max_abs_dOmega_vs_oracle": max(abs(r["omega"] - g["omega"]) for r, g in zip(res, gold)),
+                     "converged": all(r["converged"] for r in res)}
+        for c in ctxs:
+            c.close()
+    out["mixed_over_fp64_time_to_solution"] = out["fp64"]["s_to_solution"] / out["mixed"]["s_to_solution"]
+    # steady-state TF32 iteration (cold L2 each step)
+    ctxs = built()
+    ftcc.prepare_batched(ctxs, betas, mus, cfgs[0]["ngrid"], precision="tf32")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    st = ctxs[0].stream
+    ctxs[0].iterate(3)
+    torch.cuda.synchronize()
+    n = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in ev:
+        with torch.cuda.stream(st):
+            flush.zero_()
+        a.record(st)
+        ctxs[0].iterate(1)
+        b.record(st)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / n
+    ctxs[0].profile(True)
+    ctxs[0].iterate(n)
+    ks = ctxs[0].profile_read()
+    ctxs[0].profile(False)
+    out["tf32_s_per_batched_iteration"] = t
+    out["kernels"] = class_table(ks, n)
+    for c in ctxs:
+        c.close()
+    # FP64 iteration
+    ctxs = built()
+    ftcc.prepare_batched(ctxs, betas, mus, cfgs[0]["ngrid"], precision="fp64")
+    ctxs[0].iterate(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctxs[0].stream)
+    ctxs[0].iterate(3)
+    e1.record(ctxs[0].stream)
+    torch.cuda.synchronize()
+    out["fp64_s_per_batched_iteration"] = e0.elapsed_time(e1) / 3e3
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def bench_ueg81(ftcc, torch, dev, world, args):
+    """The 162-orbital gas (81 plane waves, 40 tau points), streamed over
+    tau: one mixed iteration from s = 0 and the peak device memory."""
+    if args.no_ueg81 or world != 1:
+        return None
+    c = wl.UEG_81
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    ctx = ftcc.Context(dev)
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    mu = ctx.reference_mu(c["beta"], float(c["n_elec"]))
+    ctx.prepare(c["beta"], mu, c["ngrid"], precision=args.precision, trunc_thr=c["thr"], stream_tau=1, tau_chunk=1)
+    st = ctx.stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    r = ctx.iterate(1)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    fl = flops_per_iteration(r["n_occ"], r["n_vir"], c["ngrid"])
+    out = {"precision": args.precision, "s_per_iteration": t, "tensor_tflops": fl / t / 1e12,
+           "algorithmic_flops_per_iteration": fl, "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
+           "note": "first iteration from s = 0 (includes the tile autotuning of its shapes); S kept for one tau window"}
+    ctx.close()
+    return out
+
+
+def bench_small_extras(ftcc, torch, dev, world, args):
+    out = {}
+    if world != 1:
+        return out
+    # the adjoint (lambda) sweep and response of the beta = 1 ring after an FP64 solve
+    c = wl.HUBBARD_10[1]
+    ca = ftcc.Context(dev)
+    ca.build_hubbard(c["L"], c["t"], c["U"])
+    ca.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ar, _ = ca.adjoint(with_rdm1=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["adjoint_lambda_sweep"] = {"workload": "hubbard_1d L=10 U=4 beta=1, ngrid=32, FP64 lambda sweep + response",
+                                   "s_total": t, "lambda_iterations": ar["iterations"],
+                                   "s_per_lambda_iteration": t / max(1, ar["iterations"]),
+                                   "N": ar["N"], "E": ar["E"], "S": ar["S"]}
+    ca.close()
+    if args.no_batch:
+        return out
+    # the 64-instance batch (6-14 sites, U in [1,8], T in [0.25,4], ngrid=24)
+    cb = wl.hubbard_batch()
+    ctx_b = []
+    for q in cb:
+        x = ftcc.Context(dev)
+        x.build_hubbard(q["L"], q["t"], q["U"])
+        ctx_b.append(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rb = ftcc.solve_batched(ctx_b, [q["beta"] for q in cb], [q["mu"] for q in cb], cb[0]["ngrid"],
+                            precision="tf32", refine_max_iter=30, max_iter=400, allow_unconverged=True)
+    torch.cuda.synchronize()
+    bat = {"workload": "64 hubbard_1d instances, L in {6..14}, ngrid=24, one batch per size class, the five "
+                       "classes iterated together on their own streams; TF32, BF16X3 polish, FP64 corrections "
+                       "until the FP64 tolerances hold (at most 30)",
+           "s_total": time.perf_counter() - t0, "instances": len(cb),
+           "converged": int(sum(r["converged"] for r in rb)),
+           "iterations_max": int(max(r["iterations"] for r in rb))}
+    # energies and entropies from the adjoint of every live instance (one
+    # FP64 lambda sweep per size-class batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_adj = 0
+    for x in ctx_b:
+        try:
+            x.adjoint(with_rdm1=False)
+            n_adj += 1
+        except ftcc.FTCCError:
+            pass
+    torch.cuda.synchronize()
+    bat["adjoint_s_total"] = time.perf_counter() - t0
+    bat["adjoint_instances"] = n_adj
+    for x in ctx_b:
+        x.close()
+    out["batched_64_instances"] = bat
+    # the differential form (Eq. smud, Alg. 1): RK4 / RK2 marches of the
+    # three-temperature ring in FP64 beside the FP64 Simpson fixed point
+    cfgs = wl.HUBBARD_10
+    rk = {"workload": C2_WORKLOAD + ", FP64, one batched solve each (host-timed, synchronised)"}
+    try:
+        for name, quad, kw in (("simpson_fp64", ftcc.QUAD_SIMPSON, {"max_iter": 300}),
+                               ("rk4_fp64", ftcc.QUAD_RK4, {}), ("rk2_fp64", ftcc.QUAD_RK2, {})):
+            ctxs = []
+            for q in cfgs:
+                x = ftcc.Context(dev)
+                x.build_hubbard(q["L"], q["t"], q["U"])
+                ctxs.append(x)
+            betas, mus = [q["beta"] for q in cfgs], [q["mu"] for q in cfgs]
+            ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = ftcc.solve_batched(ctxs, betas, mus, cfgs[0]["ngrid"], quad=quad, precision="fp64", **kw)
+            torch.cuda.synchronize()
+            rk[name] = {"s_total": time.perf_counter() - t0, "iterations_or_steps": res[0]["iterations"],
+                        "omega": [r["omega"] for r in res]}
+            for x in ctxs:
+                x.close()
+        rk["rk4_minus_simpson_omega"] = [a - b for a, b in zip(rk["rk4_fp64"]["omega"], rk["simpson_fp64"]["omega"])]
+    except Exception as e:   # noqa: BLE001 - reported, the headline line still prints
+        rk["error"] = f"{type(e).__name__}: {e}"[:300]
+    out["differential_form"] = rk
+    return out
+
+
+def bench_dense_gemm(ftcc, torch, dev, world, pk):
+    """The dense particle-ladder product of one 8-point tau chunk of the
+    headline workload, [8*12996 x 12996] . [12996 x 12996]^T, through
+    ftcc_gemm alone (host-timed between synchronisations)."""
+    if world != 1:
+        return None
+    out = {}
+    try:
+        nn = 114 * 114
+        cg = ftcc.Context(dev)
+        ga = torch.randn((1, 8 * nn, nn), device="cuda", dtype=torch.float32)
+        gb = torch.randn((1, nn, nn), device="cuda", dtype=torch.float32)
+        fl = 2.0 * 8 * nn * nn * nn
+        for prec in ("tf32", "bf16x3"):
+            cg.gemm(ga, gb, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                cg.gemm(ga, gb, precision=prec)
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / 3
+            peak = pk["tf32_tflops"]["burst"] if prec == "tf32" else pk["bf16_tflops"]["burst"] / 3.0
+            out[prec] = {"shape_bmnk": [1, 8 * nn, nn, nn], "ms": t * 1e3, "tflops": fl / t / 1e12,
+                         "frac_of_measured_peak": fl / t / 1e12 / peak}
+        del ga, gb
+        cg.close()
+    except Exception as e:   # noqa: BLE001
+        out["error"] = f"{type(e).__name__}: {e}"[:300]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ueg", action="store_true", help="skip the 114-spin-orbital gas timing")
-    ap.add_argument("--quick", action="store_true", help="timed mixed loop only (for profiler launch lists)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ueg81", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline only, no extra workloads")
+    ap.add_argument("--c3-iterations", action="store_true",
+                    help="prepare the headline workload and run W + K iterations (profiler launch lists)")
     ap.add_argument("--gemm", default=None, help="B,M,N,K: time the tensor-core GEMM alone on that shape")
     args = ap.parse_args()
     rank, world = dist_init(args)
@@ -585,6 +753,8 @@ def main():
         run_reference(args, rank, world)
     elif args.gemm:
         run_gemm_only(args)
+    elif args.c3_iterations:
+        run_c3_iteration(args)
     else:
         run_gpu(args, rank, world)
     if world > 1:

@@ -66,18 +66,47 @@ typedef enum {
 typedef enum { FTCC_QUAD_SIMPSON = 0, FTCC_QUAD_RK1 = 1, FTCC_QUAD_RK2 = 2, FTCC_QUAD_RK4 = 3 } ftcc_quadrature;
 
 /* Arithmetic of the contractions.  FP64: every tensor and GEMM in FP64.
- * TF32 / BF16X3: amplitudes and intermediates in FP32, contractions on the
- * tcgen05 tensor cores (kind::tf32, or a two-way bf16 split with three
- * kind::f16 products), FP32 accumulation; occupations, propagators,
- * quadrature and the Omega accumulation stay FP64.  After the low-precision
- * fixed point converges, up to refine_max_iter FP64 iterations follow. */
+ * TF32 / BF16X3: amplitudes and intermediates stored in FP32, contractions on
+ * the tcgen05 tensor cores (kind::tf32, or a two-way bf16 split x = hi + lo
+ * with the three kind::f16 products hi*hi + hi*lo + lo*hi), FP32
+ * accumulation; occupations, orbital energies, the propagator factors
+ * exp(-Delta h) (formed in FP64 per element, rounded once), quadrature
+ * weights, the energy sums and the Omega accumulation stay FP64; the Simpson
+ * recurrence runs in FP32 beside the FP32 amplitudes (option
+ * fp64_propagation).
+ * A TF32 solve runs three phases: TF32 iterations until Omega_CC changes by
+ * less than tol_mixed or than the TF32 unit roundoff 2^-11 |Omega_CC|, or
+ * stops improving; then up to polish_max_iter BF16X3 iterations from those
+ * amplitudes, until |dOmega_CC| < tol_mixed or it stops improving; then up to
+ * refine_max_iter FP64 residual corrections s <- s + (Phi(s) - s), each one
+ * FP64 application of the fixed-point map.  A BF16X3 solve skips the TF32
+ * phase. */
 typedef enum { FTCC_PREC_FP64 = 0, FTCC_PREC_TF32 = 1, FTCC_PREC_BF16X3 = 2 } ftcc_precision;
 
 typedef enum { FTCC_SYS_HUBBARD_1D = 0, FTCC_SYS_UEG = 1, FTCC_SYS_GENERIC = 2 } ftcc_system_kind;
 
+/* Reference (orbitals and orbital energies) of the Hubbard ring (Sec. II.B:
+ * at T > 0 both the orbitals and the reference energies define the theory;
+ * Sec. IV.A uses the Neel state and zero-temperature UHF).
+ *   KSPACE_RHF: restricted orbitals of crystal momentum k, eps = -2t cos k +
+ *     U/2 (exact thermal HF at half filling of an even ring).
+ *   NEEL_SITE: site orbitals (spin orbital sigma * L + i), eps_{i sigma} =
+ *     h_ii + U n^Neel_{i,-sigma} with the Neel determinant spin up on even,
+ *     spin down on odd sites: the diagonal of its zero-temperature Fock matrix.
+ *   UHF_SITE: the zero-temperature unrestricted Hartree-Fock solution of the
+ *     site-basis ring with L/2 up and L - L/2 down electrons, found from the
+ *     Neel density by F_sigma = h + U diag(n_-sigma), filling the lowest
+ *     orbitals and mixing old and new densities half and half until they
+ *     change by less than 1e-12 (2000 iterations at most, else
+ *     FTCC_ERR_NOT_CONVERGED); h and <pq||rs> are transformed to the UHF spin
+ *     orbitals (sigma * L + k, k in ascending energy) and eps are the UHF
+ *     orbital energies.  Built on the host (O(N^5)), then uploaded. */
+typedef enum { FTCC_REF_KSPACE_RHF = 0, FTCC_REF_NEEL_SITE = 1, FTCC_REF_UHF_SITE = 2 } ftcc_reference;
+
 /* Hamiltonian description for build_integrals.
- *   HUBBARD_1D: L-site ring (pbc must be 1), hopping t, on-site U; k-space
- *     restricted orbitals phi_k, k = 2 pi m / L, h_kk = -2 t cos k,
+ *   HUBBARD_1D: L-site ring (pbc must be 1), hopping t, on-site U, in the
+ *     basis of its reference (ftcc_reference); the default k-space restricted
+ *     orbitals phi_k, k = 2 pi m / L, give h_kk = -2 t cos k,
  *     <k1 k2|k3 k4> = U/L delta(k1 + k2 = k3 + k4), eps = h_kk + U/2
  *     (Sec. IV.A; the restricted reference at half filling).
  *   UEG: n_elec electrons at density rs in the n_pw lowest plane waves of a
@@ -92,6 +121,7 @@ typedef struct {
   int L; double t, U; int pbc;          /* HUBBARD_1D */
   int n_elec; double rs; int n_pw;      /* UEG */
   int N; const double* h; const double* eri; const double* eps; /* GENERIC */
+  int reference;                        /* HUBBARD_1D: ftcc_reference (0 = KSPACE_RHF) */
 } ftcc_system;
 
 /* Solver options; pass NULL for the defaults in brackets.
@@ -101,8 +131,30 @@ typedef struct {
  *   trunc_thr  [0.0]    orbital kept hole-like if n >= thr, particle-like if 1 - n >= thr
  *   max_iter   [200]    iterations of the low-precision (or FP64) phase
  *   precision  [FP64]   ftcc_precision
- *   refine_max_iter [8] FP64 iterations after a TF32/BF16X3 phase (0 = none)
- *   tol_mixed  [1e-7]   |dOmega_CC| at which the low-precision phase hands over
+ *   refine_max_iter [2] FP64 residual corrections after the low-precision
+ *                       phases (0 = none); they stop early once tol_omega and
+ *                       tol_amp hold
+ *   tol_mixed  [1e-7]   |dOmega_CC| at which a low-precision phase hands over;
+ *                       without FP64 corrections a mixed solve counts as
+ *                       converged when its last iteration moved Omega_CC by
+ *                       less than tol_mixed
+ *   polish_max_iter [40] BF16X3 iterations after the TF32 phase of a TF32 solve
+ *                       (0 = straight from TF32 to the FP64 corrections)
+ *   fp64_propagation [1] arithmetic of the Simpson recurrence and the energy
+ *                       sums of a TF32 / BF16X3 sweep (the ratios exp(-Delta h)
+ *                       always come from FP64 factors): 2 = FP64 for both,
+ *                       1 = FP32 recurrence with FP64 energy sums, 0 = FP32
+ *   tol_refine [1e-6]   with FP64 corrections, a mixed solve counts as
+ *                       converged when the FP64 tolerances hold or its last
+ *                       correction moved Omega_CC by less than tol_refine
+ *   mixed_adjoint [0]   1: ft_ccsd_adjoint after a mixed solve that ended in
+ *                       a low-precision phase (refine_max_iter = 0) runs the
+ *                       lambda sweep and the response on the FP32 solver
+ *                       (FP32 multipliers, BF16X3 contractions, FP64 factors,
+ *                       weights and sums), stopping when the multipliers
+ *                       change by less than 1e-7 relative or stop falling;
+ *                       0: the amplitudes are first refined in FP64 and the
+ *                       sweep runs in FP64 (ftcc_rdm2 needs this one)
  *   tau_chunk  [0]      tau points per S-kernel pass (0 = all that fit)
  *   use_graph  [1]      replay one iteration as a CUDA graph
  *   stream_tau [0]      1: run the S kernel tau_chunk points at a time (0 picks
@@ -111,7 +163,8 @@ typedef struct {
  *                       propagation window by window, carrying five values per
  *                       amplitude element (the last two even-point integrals
  *                       and the last three S).  Same result as the unstreamed
- *                       iteration; amplitude-sized memory ~ ngrid + 5 +
+ *                       iteration (in FP32 sweeps the carried values are
+ *                       stored in FP32); amplitude-sized memory ~ ngrid + 5 +
  *                       max(3, tau_chunk) slices plus the S-kernel intermediates
  *                       of tau_chunk points, instead of 2 ngrid + intermediates.
  *                       Single instance only; ft_ccsd_adjoint then returns
@@ -126,6 +179,10 @@ typedef struct {
   int tau_chunk, use_graph;
   int stream_tau;
   int autotune;
+  int polish_max_iter;
+  int fp64_propagation;
+  double tol_refine;
+  int mixed_adjoint;
 } ftcc_options;
 
 typedef struct {
@@ -133,12 +190,13 @@ typedef struct {
   double omega0, omega1, omega_cc;
   double d_omega;     /* |Omega_CC change| in the last iteration              */
   double d_amp;       /* max|ds| / max(1, max|s|) in the last iteration       */
-  int iterations;     /* total iterations, both phases                        */
-  int refine_iterations;
+  int iterations;     /* total iterations, every phase                        */
+  int refine_iterations; /* FP64 residual corrections of a mixed solve        */
   int converged;
   int n_occ, n_vir;   /* sizes of the hole-like / particle-like sets           */
   double ms_per_iter; /* mean device time of one iteration                    */
   int kernels_per_iter; /* kernel launches in one iteration (graph nodes)      */
+  int polish_iterations; /* BF16X3 iterations after the TF32 phase             */
 } ftcc_result;
 
 typedef struct {
@@ -168,8 +226,9 @@ const char* ftcc_last_error(const ftcc_ctx* ctx);
 
 /* Build the spin-orbital Hamiltonian (h, <pq||rs>, eps) in device memory
  * (layer below App. A).  Invalidates any previous solve.
- * FTCC_ERR_INVALID_ARG: L < 1, pbc != 1, U or t not finite, n_elec odd or
- * < 2, rs <= 0, n_pw not a closed shell, N < 1, or a NULL array. */
+ * FTCC_ERR_INVALID_ARG: L < 1, pbc != 1, U or t not finite, an unknown
+ * reference, n_elec odd or < 2, rs <= 0, n_pw not a closed shell, N < 1, or
+ * a NULL array. */
 ftcc_status build_integrals(ftcc_ctx* ctx, const ftcc_system* sys);
 
 /* Number of spin orbitals of the built system (0 before build_integrals). */
@@ -181,9 +240,28 @@ ftcc_status ftcc_get_system(ftcc_ctx* ctx, double* eps, double* h, double* eri);
 
 /* Chemical potential mu0 with sum_p n_p(beta, mu0) = n_elec for the
  * reference energies eps (the reference-system electron count used to fix
- * mu for the gas at fixed N, App. D).  Bisection in FP64 on the device
- * orbital energies to 1e-14 relative. */
+ * mu for the gas at fixed N, App. D).  FP64 bisection on the host, on a copy
+ * of the device orbital energies, to 1e-15 relative. */
 ftcc_status ftcc_reference_mu(ftcc_ctx* ctx, double beta, double n_elec, double* mu);
+
+/* Chemical potential mu_CC of the coupled-cluster system at a fixed mean
+ * electron number (App. D: the CC system and the reference each get their
+ * own mu for N electrons; Sec. III.A fixes <N> for every grid):
+ * N(mu) = -dOmega/dmu = n_target, with N(mu) from ft_ccsd_solve followed by
+ * ft_ccsd_adjoint on this context (the lambda sweep, App. B).  Secant steps
+ * from mu0 and mu0 + dmu (or mu0 - dmu when N(mu0) is above the target);
+ * once two evaluations straddle the target, regula falsi with the Illinois
+ * weighting (an end point kept twice in a row has its residual halved).
+ * Stops when |N - n_target| < tol_n.  mu_out, n_out (may be NULL) and
+ * evals_out (may be NULL) receive mu_CC, its N and the number of N
+ * evaluations; out (may be NULL) the last solve; the context is left with
+ * the last solve and its adjoint.  FTCC_ERR_NOT_CONVERGED after max_evals
+ * evaluations (outputs hold the last point); FTCC_ERR_INVALID_ARG for beta,
+ * dmu or tol_n not positive and finite, max_evals < 2, or n_target outside
+ * (0, N); the errors of ft_ccsd_solve and ft_ccsd_adjoint pass through. */
+ftcc_status ftcc_mu_for_n(ftcc_ctx* ctx, double beta, double n_target, int ngrid, ftcc_quadrature quad,
+                          const ftcc_options* opt, double mu0, double dmu, double tol_n, int max_evals,
+                          double* mu_out, double* n_out, int* evals_out, ftcc_result* out);
 
 /* Set up a solve without iterating: Fermi-Dirac occupations, the thermal
  * Fock matrix f = h + sum_r n_r <pr||qr>, Omega0, Omega1 (Sec. II.A,
@@ -243,9 +321,24 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
  * NULL, the partially relaxed density p^cc (N*N host doubles, rdm1[q*N + p]
  * pairs with a perturbation X[p][q]; diagonal entries include the orbital
  * energy and occupation response).  A low-precision solve is first refined
- * in FP64.  FTCC_ERR_STATE without a converged solve; FTCC_ERR_NOT_CONVERGED
- * when the lambda iteration does not converge. */
+ * in FP64, unless the solve's options set mixed_adjoint (then the sweep runs
+ * in the mixed arithmetic).  FTCC_ERR_STATE without a converged solve;
+ * FTCC_ERR_NOT_CONVERGED when the lambda iteration does not converge. */
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* ctx, ftcc_adjoint_result* out, double* rdm1);
+
+/* Unrelaxed normal-ordered two-particle density Gamma_N of the converged
+ * solve (App. B), read as the derivative of the CC Lagrangian with respect
+ * to the antisymmetrised integrals <pq||rs> that enter the CC equations and
+ * the energy through the thermal blocks, at a fixed reference (occupations,
+ * Fock matrix, orbital energies), projected onto the symmetries of the real
+ * integrals (antisymmetric in (p, q) and in (r, s), symmetric under
+ * (pq) <-> (rs)), the part a perturbation can see:
+ * dOmega_CC = sum_pqrs Gamma[p][q][r][s] dV[p][q][r][s] for any dV with the
+ * symmetries of <pq||rs>.  (The printed blocks
+ * of App. B are garbled in places; this is what they are derived from.)
+ * gamma: caller-owned host array of N^4 doubles.  Requires ft_ccsd_adjoint on
+ * this context (FTCC_ERR_STATE otherwise). */
+ftcc_status ftcc_rdm2(ftcc_ctx* ctx, double* gamma);
 
 /* Copy the current amplitudes (FP64, layouts above) to host buffers of
  * ngrid*o*v and ngrid*o*o*v*v doubles (either may be NULL). */
@@ -342,6 +435,14 @@ ftcc_status ftcc_gemm_f64_static(void* stream, int batch, int M, int N, int K, d
 /* Device error flag set by bounded in-kernel waits (0 = none); reading it
  * synchronises the stream and clears it. */
 int ftcc_device_error(ftcc_ctx* ctx);
+
+/* Host-side fault injection (no paper counterpart; failure-handling tests):
+ * write `code` (> 0) into the context's device error flag, as a bounded
+ * device wait that gave up would.  The next entry point that checks the flag
+ * (every solve does, before returning) returns FTCC_ERR_TIMEOUT and clears
+ * it.  No kernel is made to fault or wait.  FTCC_ERR_INVALID_ARG for a NULL
+ * context or code <= 0. */
+ftcc_status ftcc_inject_device_error(ftcc_ctx* ctx, int code);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,9 @@ cudaError_t launch_reference(const double* h, const double* eri, const double* e
 // em[p] = exp(-eps_p h), ep[p] = exp(eps_p h)
 cudaError_t launch_prop_tables(const double* eps, int N, double h, double* em, double* ep, cudaStream_t st);
 // thermal block: out[p0][p1][p2][p3] = eri[...] * fac(slot0) * ... with per-slot index lists
+cudaError_t launch_eri_adjoint(const double* bar, int N, const int* idx0, const double* fac0, int n0, const int* idx1,
+                              const double* fac1, int n1, const int* idx2, const double* fac2, int n2,
+                              const int* idx3, const double* fac3, int n3, double* gamma, cudaStream_t st);
 template <class T> cudaError_t launch_thermal_eri(const double* eri, int N, const int* idx0, const double* fac0,
                                                   int n0, const int* idx1, const double* fac1, int n1,
                                                   const int* idx2, const double* fac2, int n2, const int* idx3,
@@ -158,7 +161,6 @@ struct PropArgs {
   FastDiv fo, fv;                // filled by the launcher
   const int* idxO; const int* idxV;
   const double* em; const double* ep;   // [nz][N]
-  const void* emT; const void* epT;     // the same tables in the amplitude type (forward sweep)
   const double* hz;              // [nz] grid steps
   const int* live;               // [nz] 0 = instance frozen (diverged), or null
   double damping;
@@ -172,8 +174,14 @@ struct PropArgs {
   // recurrence between launches; it may be null only for y0 = 0, y1 = ng.
   int y0, y1, s_ng;
   void* chain;
+  int arith64;                   // FP32 storage: 0 = FP32 recurrence and energy sums, 1 = FP32
+                                 // recurrence with FP64 energy sums, 2 = FP64 for both
 };
 template <class T> cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a, cudaStream_t st);
+// Site-basis Hubbard ring with the Neel or UHF reference (references.cu):
+// h [N*N], <pq||rs> [N^4], eps [N] on the host; false with err on failure.
+bool hubbard_site_reference(int L, double t, double U, int reference, std::vector<double>& h,
+                            std::vector<double>& eri, std::vector<double>& eps, std::string& err);
 int prop_blocks();
 // Per instance z, sum the partials of the singles and doubles passes; row
 // state[z][.]: 0 <- Omega_CC, 1 <- |dOmega_CC|, 2 <- max|ds|/max(1, max|s|),
@@ -204,23 +212,26 @@ double simpson_weight_host(int y, int ng);
 
 // ---- adjoint ----
 // u[z][x][mu] = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m[z][y][mu] (transpose of the propagation)
-cudaError_t launch_propagate_t(const double* m, double* u, const PropArgs& a, cudaStream_t st);
+template <class T> cudaError_t launch_propagate_t(const T* m, T* u, const PropArgs& a, cudaStream_t st);
 // m_new = -c[z][x] * base' - tbar with base' = cbase * base[z][mu] (cbase != 0, tau-independent base)
 // or base[z][x][mu] (cbase == 0); partials [nblocks][2] = max|m_new - m_old|, max|m_new|
-cudaError_t launch_lambda_combine(const double* base, const double* tbar, double* mnew, const double* mold,
-                                  long long size, int ng, int nz, const double* cz, double cbase, double* partials,
-                                  int nblocks, cudaStream_t st);
+template <class T, class BT>
+cudaError_t launch_lambda_combine(const BT* base, const T* tbar, T* mnew, const T* mold, long long size, int ng, int nz,
+                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st);
 
 // ---- response (App. B) ----
 // Do[z][q] / Dv[z][q] += sum A*I over elements with a hole-like / particle-like
 // slot at position q; cls bit k set = slot k particle-like.  dims[nslot].
-cudaError_t launch_slot_sums(const double* I, const double* A, int nslot, const int* dims, int cls, int no, int nv,
-                             int nz, double* Do, double* Dv, cudaStream_t st);
-cudaError_t launch_fbar_scatter(const double* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
+template <class T>
+cudaError_t launch_slot_sums(const T* I, const T* A, int nslot, const int* dims, int cls, int no, int nv, int nz,
+                             double* Do, double* Dv, cudaStream_t st);
+template <class T>
+cudaError_t launch_fbar_scatter(const T* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
                                 const int* i1, const double* f1, long long f1z, int N, int nz, double* Fb,
                                 cudaStream_t st);
 cudaError_t launch_fock_n(const double* Fb, const double* eri, int N, double* Gn, cudaStream_t st);
-cudaError_t launch_prop_response(const double* S, const double* m, const double* epsz, const PropArgs& a, double* Ee,
-                                 double* Eb, cudaStream_t st);
+template <class T>
+cudaError_t launch_prop_response(const T* S, const T* m, const double* epsz, const PropArgs& a, double* Ee, double* Eb,
+                                 cudaStream_t st);
 
 }  // namespace ftcc

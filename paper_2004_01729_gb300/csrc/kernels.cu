@@ -626,6 +626,27 @@ __global__ void thermal_eri_kernel(const double* __restrict__ eri, int N, const 
   }
 }
 
+// The transpose of thermal_eri_kernel: the adjoint of one thermal block
+// added to the adjoint of the antisymmetrised integrals,
+// gamma[i0[a]][i1[b]][i2[c]][i3[d]] += bar[a][b][c][d] f0[a] f1[b] f2[c] f3[d].
+// The index maps of one block are injective, so no two elements of a
+// launch write the same slot.
+__global__ void eri_adjoint_kernel(const double* __restrict__ bar, int N, const int* i0, const double* f0, int n0,
+                                   const int* i1, const double* f1, int n1, const int* i2, const double* f2, int n2,
+                                   const int* i3, const double* f3, int n3, double* gamma) {
+  const long long total = static_cast<long long>(n0) * n1 * n2 * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long r = e;
+    const int d = r % n3; r /= n3;
+    const int c = r % n2; r /= n2;
+    const int b = r % n1; r /= n1;
+    const int a = static_cast<int>(r);
+    const long long dst = ((static_cast<long long>(i0[a]) * N + i1[b]) * N + i2[c]) * N + i3[d];
+    gamma[dst] += bar[e] * f0[a] * f1[b] * f2[c] * f3[d];
+  }
+}
+
 template <class T>
 __global__ void thermal_fock_kernel(const double* __restrict__ fbar, int N, const int* i0, const double* f0, int n0,
                                     const int* i1, const double* f1, int n1, T* out) {
@@ -650,13 +671,16 @@ __device__ __forceinline__ double max_abs(double m, double x) { return fmax(m, f
 constexpr int kPropThreads = 128;
 constexpr int kPropAhead = 2;   // tau steps of loads in flight per element
 
-template <class T, int NS>
-__global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagate_kernel(const T* __restrict__ S, T* __restrict__ t,
+template <class T, class A, class EA, int NS>
+__global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagate_kernel(const T* __restrict__ S, T* __restrict__ t,
                                                                                      PropArgs a) {
-  // per-thread energy slots eacc[y][thread] (storage precision; each thread
-  // sums over its own one or two elements), reduced over the block in FP64
+  // T is the storage type of S and s, A the arithmetic type of the
+  // recurrence, EA that of the energy terms and their sums.  The element
+  // ratios r = exp(-Delta h) are always formed in FP64 from the FP64 tables
+  // and rounded once to A.  Per-thread energy slots eacc[y][thread] (each
+  // thread sums over its own elements).
   extern __shared__ __align__(16) unsigned char pe_smem[];
-  T* eacc = reinterpret_cast<T*>(pe_smem);
+  EA* eacc = reinterpret_cast<EA*>(pe_smem);
   const int ng = a.ng;
   const int z = blockIdx.y;                           // instance
   if (a.live && !a.live[z]) return;                   // frozen: amplitudes and partials untouched
@@ -666,22 +690,21 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
   S += static_cast<long long>(z) * a.s_ng * size;     // S[(y - y0) * size + mu]
   t += static_cast<long long>(z) * ng * size;
   T* chain = a.chain ? static_cast<T*>(a.chain) + static_cast<long long>(z) * 5 * size : nullptr;
-  // per-orbital factors e^{-eps h}, e^{+eps h} in the amplitude type: the
-  // element ratios are products of four of them (no FP64 work per element
-  // in the FP32 sweep)
-  const T* em = static_cast<const T*>(a.emT) + static_cast<long long>(z) * a.N;
-  const T* ep = static_cast<const T*>(a.epT) + static_cast<long long>(z) * a.N;
+  // per-orbital factors e^{-eps h}, e^{+eps h} (FP64): the element ratios
+  // are products of four
+  const double* em = a.em + static_cast<long long>(z) * a.N;
+  const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
   const long long n1 = static_cast<long long>(a.no) * a.nv;
   const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * n1 : nullptr;
   double* partials = a.partials + static_cast<long long>(z) * a.nblocks * (ng + 2);
-  for (int y = y0; y < y1; ++y) eacc[y * kPropThreads + threadIdx.x] = T(0);
+  for (int y = y0; y < y1; ++y) eacc[y * kPropThreads + threadIdx.x] = EA(0);
   T dmax = T(0), smax = T(0);
-  const T h = static_cast<T>(a.hz[z]);
-  const T c12 = h / T(12), c3 = h / T(3), c38 = T(3) * h / T(8);
-  const T damp = static_cast<T>(a.damping);
+  const A h = static_cast<A>(a.hz[z]);
+  const A c12 = h / A(12), c3 = h / A(3), c38 = A(3) * h / A(8);
+  const A damp = static_cast<A>(a.damping);
   const bool damped = a.damping != 1.0;
-  const T cE = static_cast<T>(a.cE);
+  const EA cE = static_cast<EA>(a.cE);
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long mu = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; mu < size; mu += stride) {
     int i, j = 0, aa, b = 0;
@@ -703,32 +726,30 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
       }
     }
     const int pi = a.idxO[i], pa = a.idxV[aa];
-    T r1 = em[pa] * ep[pi];
-    T rinv = ep[pa] * em[pi];
+    double r1d = em[pa] * ep[pi];
+    double rinvd = ep[pa] * em[pi];
     if (NS == 4) {
       const int pj = a.idxO[j], pb = a.idxV[b];
-      r1 *= em[pb] * ep[pj];
-      rinv *= ep[pb] * em[pj];
+      r1d *= em[pb] * ep[pj];
+      rinvd *= ep[pb] * em[pj];
     }
-    // The recurrence runs in the storage precision: FP32 storage carries
-    // ~1e-7 relative error anyway, and FP64 issue rate is a small fraction
-    // of FP32 on this part.  FP64 storage keeps everything in FP64.
-    const T w = wE ? static_cast<T>(wE[mu]) : T(0);
-    const T r2 = r1 * r1, r3 = r2 * r1;
+    const A r1 = static_cast<A>(r1d), rinv = static_cast<A>(rinvd);
+    const EA w = wE ? static_cast<EA>(wE[mu]) : EA(0);
+    const A r2 = static_cast<A>(r1d * r1d), r3 = static_cast<A>(r1d * r1d * r1d);
     // S_0..S_2 are needed together at y = 1; a launch that starts at 0
     // covers at least three points
     const bool head = y0 == 0;
-    const T s0 = head ? S[mu] : T(0);
-    const T s1 = head ? S[size + mu] : T(0);
-    const T s2 = head ? S[2 * size + mu] : T(0);
-    T sm1 = T(0), sm2 = T(0), sm3 = T(0);   // S_{y-1}, S_{y-2}, S_{y-3}
-    T Ilast = T(0), Iprev = T(0);           // I at the last and second-last even y
+    const A s0 = head ? static_cast<A>(S[mu]) : A(0);
+    const A s1 = head ? static_cast<A>(S[size + mu]) : A(0);
+    const A s2 = head ? static_cast<A>(S[2 * size + mu]) : A(0);
+    A sm1 = A(0), sm2 = A(0), sm3 = A(0);   // S_{y-1}, S_{y-2}, S_{y-3}
+    A Ilast = A(0), Iprev = A(0);           // I at the last and second-last even y
     if (!head) {                            // the chain state left by the previous launch
-      Ilast = chain[mu];
-      Iprev = chain[size + mu];
-      sm1 = chain[2 * size + mu];
-      sm2 = chain[3 * size + mu];
-      sm3 = chain[4 * size + mu];
+      Ilast = static_cast<A>(chain[mu]);
+      Iprev = static_cast<A>(chain[size + mu]);
+      sm1 = static_cast<A>(chain[2 * size + mu]);
+      sm2 = static_cast<A>(chain[3 * size + mu]);
+      sm3 = static_cast<A>(chain[4 * size + mu]);
     }
     // S_y and the old s_y are loaded kPropAhead steps ahead (a register
     // window), so that several loads per thread are in flight
@@ -743,10 +764,11 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
     }
     const T* s1y = t1E ? t1E + y0 * n1 : nullptr;   // singles of this tau point
     const int oi = i * a.nv + aa, oj = j * a.nv + b;
-    T* ea = eacc + y0 * kPropThreads + threadIdx.x;
+    EA* ea = eacc + y0 * kPropThreads + threadIdx.x;
     for (int y = y0; y < y1; ++y) {
-      const T sy = sp[0];
-      const T old = tp[0];
+      const A sy = static_cast<A>(sp[0]);
+      const T tp_old = tp[0];
+      const A old = static_cast<A>(tp_old);
 #pragma unroll
       for (int k = 0; k + 1 < kPropAhead; ++k) {
         sp[k] = sp[k + 1];
@@ -757,30 +779,32 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
         sp[kPropAhead - 1] = in ? sq[kPropAhead * size] : T(0);
         tp[kPropAhead - 1] = in ? tq[kPropAhead * size] : T(0);
       }
-      T I;
+      A I;
       if (y == 0) {
-        I = T(0);
+        I = A(0);
       } else if (y == 1) {
-        I = c12 * (T(5) * r1 * s0 + T(8) * s1 - rinv * s2);
+        I = c12 * (A(5) * r1 * s0 + A(8) * s1 - rinv * s2);
       } else if ((y & 1) == 0) {
-        I = r2 * Ilast + c3 * (r2 * sm2 + T(4) * r1 * sm1 + sy);
+        I = r2 * Ilast + c3 * (r2 * sm2 + A(4) * r1 * sm1 + sy);
         Iprev = Ilast;
         Ilast = I;
       } else {
-        I = r3 * Iprev + c38 * (r3 * sm3 + T(3) * r2 * sm2 + T(3) * r1 * sm1 + sy);
+        I = r3 * Iprev + c38 * (r3 * sm3 + A(3) * r2 * sm2 + A(3) * r1 * sm1 + sy);
       }
       sm3 = sm2;
       sm2 = sm1;
       sm1 = sy;
-      T stored = -I;
-      if (damped) stored = (T(1) - damp) * old + damp * stored;
+      A next = -I;
+      if (damped) next = (A(1) - damp) * old + damp * next;
+      const T stored = static_cast<T>(next);
       *tq = stored;
-      dmax = max_abs(dmax, stored - old);   // in the storage type (no FP64 for FP32)
+      // convergence maxima in the storage type, on what the next iteration reads
+      dmax = max_abs(dmax, stored - tp_old);
       smax = max_abs(smax, stored);
       if (wE) {
-        T e = cE * stored;
+        EA e = cE * static_cast<EA>(stored);
         if (NS == 4 && s1y) {
-          e += T(0.5) * s1y[oi] * s1y[oj];
+          e += EA(0.5) * static_cast<EA>(s1y[oi]) * static_cast<EA>(s1y[oj]);
           s1y += n1;
         }
         *ea += w * e;
@@ -790,18 +814,15 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
       ea += kPropThreads;
     }
     if (chain) {
-      chain[mu] = Ilast;
-      chain[size + mu] = Iprev;
-      chain[2 * size + mu] = sm1;
-      chain[3 * size + mu] = sm2;
-      chain[4 * size + mu] = sm3;
+      chain[mu] = static_cast<T>(Ilast);
+      chain[size + mu] = static_cast<T>(Iprev);
+      chain[2 * size + mu] = static_cast<T>(sm1);
+      chain[3 * size + mu] = static_cast<T>(sm2);
+      chain[4 * size + mu] = static_cast<T>(sm3);
     }
   }
-  // The block's own reductions run in the storage type: maxima are exact in
-  // any type, and FP64 arithmetic issues at a small fraction of the FP32 rate
-  // on this part, so an FP64 tree over 32 tau points x 128 slots per block
-  // would cost as much as the propagation itself.  Only the per-block
-  // results are widened; the sum over blocks is FP64.
+  // The block's maxima are exact in any type; the energy sums run in EA and
+  // the sum over blocks is FP64.
   __shared__ T dm[kPropThreads], sm[kPropThreads];
   dm[threadIdx.x] = dmax;
   sm[threadIdx.x] = smax;
@@ -820,7 +841,7 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
   const long long nbk = a.nblocks;
   double* p = partials + blockIdx.x;
   for (int y = y0 + warp; y < y1; y += kPropThreads / 32) {
-    T acc = T(0);
+    EA acc = EA(0);
     for (int k = lane; k < kPropThreads; k += 32) acc += eacc[y * kPropThreads + k];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) p[y * nbk] = static_cast<double>(acc);
@@ -835,8 +856,8 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(T) == 4 ? 8 : 4) propagat
 // Transposed propagation: u_x = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m_y,
 // the adjoint of the Simpson recurrences above, run from the last tau point
 // down with the even-chain adjoint E'_y = m_y + r^2 E'_{y+2} + r^3 m_{y+3}.
-template <int NS>
-__global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const double* __restrict__ m, double* __restrict__ u,
+template <class T, int NS>
+__global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __restrict__ m, T* __restrict__ u,
                                                                    PropArgs a) {
   const int ng = a.ng;
   const int z = blockIdx.y;
@@ -875,11 +896,11 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const double*
       ri *= ep[pb] * em[pj];
     }
     const double r2 = rr * rr, r3 = r2 * rr;
-    const double m1 = m[size + mu];
+    const double m1 = static_cast<double>(m[size + mu]);
     double mp1 = 0.0, mp2 = 0.0, mp3 = 0.0;   // m_{x+1}, m_{x+2}, m_{x+3}
     double Ep1 = 0.0, Ep2 = 0.0;              // E'_{x+1}, E'_{x+2}
     for (int x = ng - 1; x >= 0; --x) {
-      const double mx = m[static_cast<long long>(x) * size + mu];
+      const double mx = static_cast<double>(m[static_cast<long long>(x) * size + mu]);
       double Ex = 0.0;
       if ((x & 1) == 0 && x >= 2) Ex = mx + r2 * Ep2 + r3 * mp3;
       double ux = 0.0;
@@ -893,7 +914,7 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const double*
       if (x == 0) ux += 5.0 * h / 12.0 * rr * m1;
       if (x == 1) ux += 8.0 * h / 12.0 * m1;
       if (x == 2) ux -= h / 12.0 * ri * m1;
-      u[static_cast<long long>(x) * size + mu] = ux;
+      u[static_cast<long long>(x) * size + mu] = static_cast<T>(ux);
       mp3 = mp2;
       mp2 = mp1;
       mp1 = mx;
@@ -906,8 +927,9 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const double*
 // m_new = -c_x (f_ov + <ij||ab> s_j^b) - tbar (singles) or -c_x/4 <ij||ab> - tbar
 // (doubles), c_x = g_x / beta, and per-block max|m_new - m_old|, max|m_new|.
 // E'(s) is the derivative of E (Eq. E) with respect to the amplitudes.
-__global__ void lambda_combine_kernel(const double* __restrict__ base, const double* __restrict__ tbar,
-                                      double* __restrict__ mnew, const double* __restrict__ mold, long long size, int ng,
+template <class T, class BT>
+__global__ void lambda_combine_kernel(const BT* __restrict__ base, const T* __restrict__ tbar,
+                                      T* __restrict__ mnew, const T* __restrict__ mold, long long size, int ng,
                                       int nz, const double* __restrict__ cz, double cbase, double* partials) {
   __shared__ double dm[256], sm[256];
   double dmax = 0.0, smax = 0.0;
@@ -919,11 +941,12 @@ __global__ void lambda_combine_kernel(const double* __restrict__ base, const dou
     const long long z = zx / ng;
     const int x = static_cast<int>(zx - z * ng);
     const double c = cz[z * ng + x];
-    const double bval = base[z * size * (cbase != 0.0 ? 1 : ng) + (cbase != 0.0 ? mu : x * size + mu)];
-    const double v = -c * (cbase != 0.0 ? cbase * bval : bval) - tbar[e];
-    dmax = fmax(dmax, fabs(v - mold[e]));
-    smax = fmax(smax, fabs(v));
-    mnew[e] = v;
+    const double bval = static_cast<double>(base[z * size * (cbase != 0.0 ? 1 : ng) + (cbase != 0.0 ? mu : x * size + mu)]);
+    const double v = -c * (cbase != 0.0 ? cbase * bval : bval) - static_cast<double>(tbar[e]);
+    const T vs = static_cast<T>(v);
+    dmax = fmax(dmax, fabs(static_cast<double>(vs) - static_cast<double>(mold[e])));
+    smax = fmax(smax, fabs(static_cast<double>(vs)));
+    mnew[e] = vs;
   }
   dm[threadIdx.x] = dmax;
   sm[threadIdx.x] = smax;
@@ -946,7 +969,8 @@ __global__ void lambda_combine_kernel(const double* __restrict__ base, const dou
 // slot holds orbital position q, Dv likewise for particle-like slots.  These
 // are the derivatives of the Lagrangian with respect to log sqrt(n_q) and
 // log sqrt(1 - n_q).
-__global__ void slot_sums_kernel(const double* __restrict__ I, const double* __restrict__ A, int nslot, int d0, int d1,
+template <class T>
+__global__ void slot_sums_kernel(const T* __restrict__ I, const T* __restrict__ A, int nslot, int d0, int d1,
                                  int d2, int d3, int cls, int no, int nv, double* Do, double* Dv) {
   const int z = blockIdx.y;
   const long long per = static_cast<long long>(d0) * d1 * d2 * d3;
@@ -957,7 +981,7 @@ __global__ void slot_sums_kernel(const double* __restrict__ I, const double* __r
   const int dims[4] = {d0, d1, d2, d3};
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < per;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const double p = I[e] * A[e];
+    const double p = static_cast<double>(I[e]) * static_cast<double>(A[e]);
     if (p == 0.0) continue;
     long long r = e;
     int c[4];
@@ -973,7 +997,8 @@ __global__ void slot_sums_kernel(const double* __restrict__ I, const double* __r
 }
 
 // dL/dFbar[p][q] += A[a][b] fac0[a] fac1[b] for a thermal Fock block.
-__global__ void fbar_scatter_kernel(const double* __restrict__ A, int n0, int n1, const int* i0, const double* f0,
+template <class T>
+__global__ void fbar_scatter_kernel(const T* __restrict__ A, int n0, int n1, const int* i0, const double* f0,
                                     long long f0z, const int* i1, const double* f1, long long f1z, int N, double* Fb) {
   const int z = blockIdx.y;
   A += static_cast<long long>(z) * n0 * n1;
@@ -983,7 +1008,7 @@ __global__ void fbar_scatter_kernel(const double* __restrict__ A, int n0, int n1
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n0 * n1) return;
   const int a = e / n1, b = e % n1;
-  atomicAdd(&Fb[static_cast<long long>(i0[a]) * N + i1[b]], A[e] * f0[a] * f1[b]);
+  atomicAdd(&Fb[static_cast<long long>(i0[a]) * N + i1[b]], static_cast<double>(A[e]) * f0[a] * f1[b]);
 }
 
 // Gn[z][r] = sum_pq Fb[z][p][q] <pr||qr>: the occupation dependence of the
@@ -1011,9 +1036,9 @@ __global__ void fock_n_kernel(const double* __restrict__ Fb, const double* __res
 //   dL/dDelta_mu = -sum_y m_y J_y,   beta dL/dbeta|prop = sum_y m_y (I_y - Delta J_y).
 // Accumulated per orbital (dL/deps_q = sum_mu dL/dDelta_mu dDelta_mu/deps_q)
 // and per instance (beta part).
-template <int NS>
-__global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const double* __restrict__ S,
-                                                                     const double* __restrict__ m, const double* __restrict__ epsz,
+template <class T, int NS>
+__global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const T* __restrict__ S,
+                                                                     const T* __restrict__ m, const double* __restrict__ epsz,
                                                                      PropArgs a, double* Ee, double* Eb) {
   const int ng = a.ng;
   const int z = blockIdx.y;
@@ -1059,12 +1084,14 @@ __global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const doubl
       delta += eps[pb] - eps[pj];
     }
     const double r2 = rr * rr, r3 = r2 * rr;
-    const double s0 = S[mu], s1 = S[size + mu], s2 = S[2 * size + mu];
+    const double s0 = static_cast<double>(S[mu]), s1 = static_cast<double>(S[size + mu]),
+                 s2 = static_cast<double>(S[2 * size + mu]);
     double sm1 = 0.0, sm2 = 0.0, sm3 = 0.0;
     double Il = 0.0, Ip = 0.0, dIl = 0.0, dIp = 0.0;   // last / second-last even I and dI/dr
     double P1 = 0.0, K = 0.0;
     for (int y = 0; y < ng; ++y) {
-      const double sy = y == 0 ? s0 : (y == 1 ? s1 : (y == 2 ? s2 : S[static_cast<long long>(y) * size + mu]));
+      const double sy =
+          y == 0 ? s0 : (y == 1 ? s1 : (y == 2 ? s2 : static_cast<double>(S[static_cast<long long>(y) * size + mu])));
       double I, dI;
       if (y == 0) {
         I = 0.0;
@@ -1086,7 +1113,7 @@ __global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const doubl
       sm3 = sm2;
       sm2 = sm1;
       sm1 = sy;
-      const double my = m[static_cast<long long>(y) * size + mu];
+      const double my = static_cast<double>(m[static_cast<long long>(y) * size + mu]);
       P1 += my * I;
       K += my * h * rr * dI;
     }
@@ -1568,6 +1595,14 @@ cudaError_t launch_thermal_eri(const double* eri, int N, const int* idx0, const 
                                                           fac3, n3, out);
   return cudaGetLastError();
 }
+cudaError_t launch_eri_adjoint(const double* bar, int N, const int* idx0, const double* fac0, int n0, const int* idx1,
+                              const double* fac1, int n1, const int* idx2, const double* fac2, int n2,
+                              const int* idx3, const double* fac3, int n3, double* gamma, cudaStream_t st) {
+  const long long n = static_cast<long long>(n0) * n1 * n2 * n3;
+  eri_adjoint_kernel<<<grid_for(n, 256), 256, 0, st>>>(bar, N, idx0, fac0, n0, idx1, fac1, n1, idx2, fac2, n2, idx3,
+                                                       fac3, n3, gamma);
+  return cudaGetLastError();
+}
 template cudaError_t launch_thermal_eri<float>(const double*, int, const int*, const double*, int, const int*,
                                                const double*, int, const int*, const double*, int, const int*,
                                                const double*, int, float*, cudaStream_t);
@@ -1591,6 +1626,24 @@ template cudaError_t launch_thermal_fock<double>(const double*, int, const int*,
 // loads are in flight to cover the memory latency.
 int prop_blocks() { return 152 * 16; }
 
+template <class T, class A, class EA>
+cudaError_t launch_prop_t(const T* S, T* t, const PropArgs& a, dim3 grid, cudaStream_t st) {
+  const size_t smem = static_cast<size_t>(a.ng) * kPropThreads * sizeof(EA);   // per-thread energy slots
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (a.nslot == 4) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(propagate_kernel<T, A, EA, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+    propagate_kernel<T, A, EA, 4><<<grid, kPropThreads, smem, st>>>(S, t, a);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(propagate_kernel<T, A, EA, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+    propagate_kernel<T, A, EA, 2><<<grid, kPropThreads, smem, st>>>(S, t, a);
+  }
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_t st) {
   if (a_in.ng < 3 || a_in.size >= (1LL << 31)) return cudaErrorInvalidValue;
@@ -1600,21 +1653,13 @@ cudaError_t launch_propagate(const T* S, T* t, const PropArgs& a_in, cudaStream_
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
-  const size_t smem = static_cast<size_t>(a.ng) * kPropThreads * sizeof(T);   // per-thread energy slots
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  int blocks = a.nblocks;
   if (a.nz < 1 || a.nz > 65535) return cudaErrorInvalidValue;
-  dim3 grid(blocks, a.nz);
-  if (a.nslot == 4) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(propagate_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    propagate_kernel<T, 4><<<grid, kPropThreads, smem, st>>>(S, t, a);
-  } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(propagate_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    propagate_kernel<T, 2><<<grid, kPropThreads, smem, st>>>(S, t, a);
-  }
-  return cudaGetLastError();
+  dim3 grid(a.nblocks, a.nz);
+  // FP32 storage: arith64 0 = FP32 recurrence and energy sums, 1 = FP32
+  // recurrence with FP64 energy sums, 2 = FP64 recurrence and energy sums
+  if (sizeof(T) == 4 && a.arith64 == 0) return launch_prop_t<T, float, float>(S, t, a, grid, st);
+  if (sizeof(T) == 4 && a.arith64 == 1) return launch_prop_t<T, float, double>(S, t, a, grid, st);
+  return launch_prop_t<T, double, double>(S, t, a, grid, st);
 }
 template cudaError_t launch_propagate<float>(const float*, float*, const PropArgs&, cudaStream_t);
 template cudaError_t launch_propagate<double>(const double*, double*, const PropArgs&, cudaStream_t);
@@ -1647,39 +1692,42 @@ double simpson_weight_host(int y, int ng) {
   return w;
 }
 
-cudaError_t launch_propagate_t(const double* m, double* u, const PropArgs& a_in, cudaStream_t st) {
+template <class T>
+cudaError_t launch_propagate_t(const T* m, T* u, const PropArgs& a_in, cudaStream_t st) {
   if (a_in.ng < 3 || a_in.size >= (1LL << 31) || a_in.nz < 1) return cudaErrorInvalidValue;
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
   dim3 grid(a.nblocks, a.nz);
-  if (a.nslot == 4) propagate_t_kernel<4><<<grid, kPropThreads, 0, st>>>(m, u, a);
-  else propagate_t_kernel<2><<<grid, kPropThreads, 0, st>>>(m, u, a);
+  if (a.nslot == 4) propagate_t_kernel<T, 4><<<grid, kPropThreads, 0, st>>>(m, u, a);
+  else propagate_t_kernel<T, 2><<<grid, kPropThreads, 0, st>>>(m, u, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lambda_combine(const double* base, const double* tbar, double* mnew, const double* mold,
-                                  long long size, int ng, int nz, const double* cz, double cbase, double* partials,
-                                  int nblocks, cudaStream_t st) {
-  lambda_combine_kernel<<<nblocks, 256, 0, st>>>(base, tbar, mnew, mold, size, ng, nz, cz, cbase, partials);
+template <class T, class BT>
+cudaError_t launch_lambda_combine(const BT* base, const T* tbar, T* mnew, const T* mold, long long size, int ng, int nz,
+                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st) {
+  lambda_combine_kernel<T, BT><<<nblocks, 256, 0, st>>>(base, tbar, mnew, mold, size, ng, nz, cz, cbase, partials);
   return cudaGetLastError();
 }
 
-cudaError_t launch_slot_sums(const double* I, const double* A, int nslot, const int* dims, int cls, int no, int nv,
+template <class T>
+cudaError_t launch_slot_sums(const T* I, const T* A, int nslot, const int* dims, int cls, int no, int nv,
                              int nz, double* Do, double* Dv, cudaStream_t st) {
   long long per = 1;
   for (int k = 0; k < nslot; ++k) per *= dims[k];
   dim3 grid(grid_for(per, 256, 1024), nz);
-  slot_sums_kernel<<<grid, 256, 0, st>>>(I, A, nslot, dims[0], dims[1], nslot > 2 ? dims[2] : 1,
+  slot_sums_kernel<T><<<grid, 256, 0, st>>>(I, A, nslot, dims[0], dims[1], nslot > 2 ? dims[2] : 1,
                                           nslot > 3 ? dims[3] : 1, cls, no, nv, Do, Dv);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fbar_scatter(const double* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
+template <class T>
+cudaError_t launch_fbar_scatter(const T* A, int n0, int n1, const int* i0, const double* f0, long long f0z,
                                 const int* i1, const double* f1, long long f1z, int N, int nz, double* Fb,
                                 cudaStream_t st) {
   dim3 grid((n0 * n1 + 255) / 256, nz);
-  fbar_scatter_kernel<<<grid, 256, 0, st>>>(A, n0, n1, i0, f0, f0z, i1, f1, f1z, N, Fb);
+  fbar_scatter_kernel<T><<<grid, 256, 0, st>>>(A, n0, n1, i0, f0, f0z, i1, f1, f1z, N, Fb);
   return cudaGetLastError();
 }
 
@@ -1688,15 +1736,32 @@ cudaError_t launch_fock_n(const double* Fb, const double* eri, int N, double* Gn
   return cudaGetLastError();
 }
 
-cudaError_t launch_prop_response(const double* S, const double* m, const double* epsz, const PropArgs& a_in, double* Ee,
+template <class T>
+cudaError_t launch_prop_response(const T* S, const T* m, const double* epsz, const PropArgs& a_in, double* Ee,
                                  double* Eb, cudaStream_t st) {
   PropArgs a = a_in;
   a.fo = make_fastdiv(static_cast<uint32_t>(a.no));
   a.fv = make_fastdiv(static_cast<uint32_t>(a.nv));
   dim3 grid(a.nblocks, a.nz);
-  if (a.nslot == 4) prop_response_kernel<4><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
-  else prop_response_kernel<2><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
+  if (a.nslot == 4) prop_response_kernel<T, 4><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
+  else prop_response_kernel<T, 2><<<grid, kPropThreads, 0, st>>>(S, m, epsz, a, Ee, Eb);
   return cudaGetLastError();
 }
+
+#define FTCC_ADJOINT_INSTANTIATE(T)                                                                                 \
+  template cudaError_t launch_propagate_t<T>(const T*, T*, const PropArgs&, cudaStream_t);                         \
+  template cudaError_t launch_slot_sums<T>(const T*, const T*, int, const int*, int, int, int, int, double*, double*, \
+                                           cudaStream_t);                                                           \
+  template cudaError_t launch_fbar_scatter<T>(const T*, int, int, const int*, const double*, long long, const int*,  \
+                                              const double*, long long, int, int, double*, cudaStream_t);          \
+  template cudaError_t launch_prop_response<T>(const T*, const T*, const double*, const PropArgs&, double*, double*, \
+                                               cudaStream_t);                                                       \
+  template cudaError_t launch_lambda_combine<T, T>(const T*, const T*, T*, const T*, long long, int, int,           \
+                                                   const double*, double, double*, int, cudaStream_t);
+FTCC_ADJOINT_INSTANTIATE(float)
+FTCC_ADJOINT_INSTANTIATE(double)
+#undef FTCC_ADJOINT_INSTANTIATE
+template cudaError_t launch_lambda_combine<float, double>(const double*, const float*, float*, const float*, long long,
+                                                          int, int, const double*, double, double*, int, cudaStream_t);
 
 }  // namespace ftcc

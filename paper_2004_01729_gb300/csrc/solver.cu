@@ -148,7 +148,7 @@ struct Batch {
   int nz = 0, N = 0, no = 0, nv = 0, ng = 0, prec = 0;
   ftcc_options opt{};
   std::vector<int> O, V;
-  Buf idxO, idxV, em, ep, emf, epf, hz, V64, F64, state, live;
+  Buf idxO, idxV, em, ep, hz, V64, F64, state, live;
   std::vector<int> live_host;     // 0 once an instance diverged (frozen, reported DIVERGED)
   std::unique_ptr<Solver<float>> s32;
   std::unique_ptr<Solver<double>> s64;
@@ -158,10 +158,12 @@ struct Batch {
   Buf m1, m2, mn1, mn2, u1, u2, tb1, tb2, dE1, cz, lpart;
   Buf facOz, facVz, epsz;        // stacked [nz][no], [nz][nv], [nz][N] for the response
   bool lambda_done = false;
+  bool adjoint_fp32 = false;     // the multipliers live on the FP32 solver (mixed adjoint)
   int lambda_iterations = 0;
   double prof_ms[8] = {0}, prof_bytes[8] = {0}, prof_flops[8] = {0};
   long long prof_launches[8] = {0};
-  int iterations = 0, refine_iterations = 0;
+  int iterations = 0, refine_iterations = 0, polish_iterations = 0;
+  bool polishing = false;        // the FP32 solver runs the BF16X3 polishing phase
   double ms_total = 0;
   int ms_count = 0;
   bool solved = false;
@@ -257,6 +259,29 @@ struct Solver {
   Buf btt, bta, bX, bWmnij, bWabef, bWmbej, bY, bFae, bFmi, bFme, bFt, bFt2, bR, bR2, bD, bP, bQ, ones, sx1, sx2;
 
   Solver(Batch* batch, int kind) : b(batch), h_(batch->home), gk(kind) {}
+
+  // Change the tensor-core arithmetic of the contractions (TF32 -> BF16X3
+  // for the polishing phase) keeping the amplitudes: the operand packs of the
+  // old kind are released and the next iteration runs uncaptured (sizing the
+  // new kind's workspaces) before a new graph is captured.
+  void set_kind(int kind) {
+    if (kind == gk) return;
+    gk = kind;
+    for (auto& kv : packed) {
+      h_->put(kv.second.first);
+      h_->put(kv.second.second);
+    }
+    packed.clear();
+    for (auto& e : amp_cache) {
+      h_->put(e.a);
+      h_->put(e.b);
+    }
+    amp_cache.clear();
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    warm = false;
+    graph_nodes = 0;
+  }
   ~Solver() {
     if (gexec) cudaGraphExecDestroy(gexec);
     for (auto& kv : Vb) h_->put(kv.second);
@@ -956,7 +981,7 @@ Batch::~Batch() {
     Buf* bs[] = {&I.n, &I.nbar, &I.f, &I.fbar, &I.facO, &I.facV};
     for (Buf* q : bs) home->put(*q);
   }
-  Buf* bs[] = {&idxO, &idxV, &em, &ep, &emf, &epf, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
+  Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz};
   for (Buf* q : bs) home->put(*q);
 }
@@ -979,8 +1004,12 @@ ftcc_options default_options() {
   o.trunc_thr = 0.0;
   o.max_iter = 200;
   o.precision = FTCC_PREC_FP64;
-  o.refine_max_iter = 8;
+  o.refine_max_iter = 2;
   o.tol_mixed = 1e-7;
+  o.polish_max_iter = 40;
+  o.fp64_propagation = 1;
+  o.tol_refine = 1e-6;
+  o.mixed_adjoint = 0;
   o.tau_chunk = 0;
   o.use_graph = 1;
   o.stream_tau = 0;
@@ -1097,8 +1126,6 @@ PropArgs prop_args(Batch& B, int nslot) {
   a.idxV = static_cast<const int*>(B.idxV.p);
   a.em = static_cast<const double*>(B.em.p);
   a.ep = static_cast<const double*>(B.ep.p);
-  a.emT = B.em.p;   // FP64 sweep and adjoint kernels; the FP32 sweep swaps in emf / epf
-  a.epT = B.ep.p;
   a.hz = static_cast<const double*>(B.hz.p);
   a.live = static_cast<const int*>(B.live.p);
   a.damping = B.opt.damping;
@@ -1111,13 +1138,13 @@ PropArgs prop_args(Batch& B, int nslot) {
   return a;
 }
 
-// The propagator factors in the amplitude type of the sweep.
+// Arithmetic of the propagation in an FP32 sweep (option fp64_propagation):
+// the element ratios exp(-Delta h) always come from the FP64 tables; the
+// recurrence and the energy sums run in FP64 (2), the sums only (1) or
+// neither (0).
 template <class T>
 void set_tables(Batch& B, PropArgs& a) {
-  if (sizeof(T) == 4) {
-    a.emT = B.emf.p;
-    a.epT = B.epf.p;
-  }
+  if (sizeof(T) == 4) a.arith64 = B.opt.fp64_propagation;
 }
 
 // One application of the fixed-point map to every tau point of every instance.
@@ -1299,6 +1326,7 @@ void fill_result(Batch& B, int z, const std::vector<double>& st, ftcc_result* ou
   out->d_amp = s[2];
   out->iterations = I.conv_iter > 0 ? I.conv_iter : B.iterations;
   out->refine_iterations = B.refine_iterations;
+  out->polish_iterations = B.polish_iterations;
   out->converged = (B.live_host.empty() || B.live_host[z]) && (B.solved || I.conv_iter > 0) ? 1 : 0;
   out->n_occ = B.no;
   out->n_vir = B.nv;
@@ -1371,7 +1399,9 @@ bool shell_grid(int n_pw, std::vector<int>& out) {
 }
 
 ftcc_status check_options(ftcc_ctx* c, const ftcc_options& o) {
-  if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.trunc_thr < 0 ||
+  if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.polish_max_iter < 0 || o.trunc_thr < 0 ||
+      o.fp64_propagation < 0 || o.fp64_propagation > 2 || !(o.tol_refine >= 0) || o.mixed_adjoint < 0 ||
+      o.mixed_adjoint > 1 ||
       o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || o.stream_tau < 0 ||
       o.stream_tau > 1 || o.autotune < 0 || o.autotune > 1 || !(o.tol_omega >= 0) ||
       !(o.tol_amp >= 0) || !(o.tol_mixed >= 0))
@@ -1486,13 +1516,6 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
                        home->st));
     sync(home);   // the host vectors fo / fv must outlive their copies
   }
-  // FP32 copies of the propagator factors for the FP32 sweep
-  ensure(home, B->emf, static_cast<size_t>(n) * N * sizeof(float));
-  ensure(home, B->epf, static_cast<size_t>(n) * N * sizeof(float));
-  CU(launch_convert<double, float>(static_cast<const double*>(B->em.p), static_cast<float*>(B->emf.p),
-                                   static_cast<long long>(n) * N, home->st));
-  CU(launch_convert<double, float>(static_cast<const double*>(B->ep.p), static_cast<float*>(B->epf.p),
-                                   static_cast<long long>(n) * N, home->st));
   CU(cudaMemcpyAsync(B->hz.p, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, home->st));
   B->live_host.assign(n, 1);
   ensure(home, B->live, static_cast<size_t>(n) * sizeof(int));
@@ -1616,34 +1639,73 @@ ftcc_status rk_solve(Batch& B) {
   return FTCC_OK;
 }
 
-ftcc_status solve_batch(Batch& B) {
-  if (B.quad != FTCC_QUAD_SIMPSON) return rk_solve(B);
-  const ftcc_options& o = B.opt;
-  ftcc_ctx* h = B.home;
-  std::vector<double> s;
-  bool conv = false;
-  std::vector<double> best(B.nz, 1e300);
-  std::vector<int> stall(B.nz, 0);
-  auto all_done = [&](const std::vector<double>& st, double tol_o, double tol_a) {
+// The fixed-point loop of one batch as a state machine advanced one
+// iteration at a time, so that the batches of a batched solve (one per
+// orbital count) run their iterations in lockstep, each on its own stream,
+// and overlap on the GPU.  Phases: the low-precision phase (TF32, then the
+// BF16X3 polish) or the FP64 iteration, then the FP64 residual corrections.
+struct SolveDriver {
+  Batch& B;
+  const ftcc_options& o;
+  ftcc_ctx* h;
+  std::vector<double> s, best;
+  std::vector<int> stall;
+  bool conv = false, finished = false, refining = false;
+  int it = 0, r = 0;
+  ftcc_status status = FTCC_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+
+  explicit SolveDriver(Batch& b) : B(b), o(b.opt), h(b.home), best(b.nz, 1e300), stall(b.nz, 0) {
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    if (o.max_iter <= 0) end();
+  }
+  ~SolveDriver() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  // enqueue one iteration on the batch's stream (no host wait)
+  void launch() {
+    CU(cudaEventRecord(e0, h->st));
+    run_batch(B, 1);
+    CU(cudaEventRecord(e1, h->st));
+  }
+  // wait for it, then the convergence and phase logic
+  void collect() {
+    CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    B.ms_total += ms;
+    B.ms_count += 1;
+    s = read_states(B);
+    step();
+  }
+  bool all_done(double tol_o, double tol_a) {
     bool all = true;
     for (int z = 0; z < B.nz; ++z) {
       if (!B.live_host[z]) continue;
-      const double* r = st.data() + static_cast<size_t>(z) * kStateStride;
-      const bool ok = r[1] < tol_o && r[2] < tol_a;
+      const double* q = s.data() + static_cast<size_t>(z) * kStateStride;
+      const bool ok = q[1] < tol_o && q[2] < tol_a;
       if (ok && B.inst[z].conv_iter < 0) B.inst[z].conv_iter = B.iterations;
       all = all && ok;
     }
     return all;
-  };
+  }
+  bool mixed_done(double tol) {
+    bool all = true;
+    for (int z = 0; z < B.nz; ++z)
+      if (B.live_host[z]) all = all && s[static_cast<size_t>(z) * kStateStride + 1] < tol;
+    return all;
+  }
   // an instance whose Omega_CC or amplitudes stop being finite is frozen
   // (its slice keeps its last state) so that the rest of the batch goes on;
   // returns false when no live instance is left
-  auto finite = [&](const std::vector<double>& st) {
+  bool finite() {
     bool changed = false, any = false;
     for (int z = 0; z < B.nz; ++z) {
       if (!B.live_host[z]) continue;
-      const double* r = st.data() + static_cast<size_t>(z) * kStateStride;
-      if (!std::isfinite(r[0]) || !std::isfinite(r[2]) || std::fabs(r[0]) > 1e12) {
+      const double* q = s.data() + static_cast<size_t>(z) * kStateStride;
+      if (!std::isfinite(q[0]) || !std::isfinite(q[2]) || std::fabs(q[0]) > 1e12) {
         B.live_host[z] = 0;
         changed = true;
       } else {
@@ -1653,22 +1715,57 @@ ftcc_status solve_batch(Batch& B) {
     if (changed)
       CU(cudaMemcpyAsync(B.live.p, B.live_host.data(), B.nz * sizeof(int), cudaMemcpyHostToDevice, h->st));
     return any;
-  };
-  for (int it = 0; it < o.max_iter; ++it) {
-    timed_iterations(B, 1);
-    s = read_states(B);
-    if (!finite(s)) {
+  }
+  void end() {
+    finished = true;
+    check_device_error(h);
+    int dead = 0;
+    for (int z = 0; z < B.nz; ++z) dead += !B.live_host[z];
+    B.solved = conv && dead == 0;
+    B.solved_live = conv && dead < B.nz;
+    if (dead) status = fail(h, FTCC_ERR_DIVERGED, "%d of %d instances diverged (frozen)", dead, B.nz);
+    else if (!conv) status = fail(h, FTCC_ERR_NOT_CONVERGED, "not converged after %d iterations", B.iterations);
+  }
+  void step() {
+    if (refining) {
+      // FP64 residual corrections: s <- s + r with the FP64 residual
+      // r = Phi(s) - s (one FP64 application of the fixed-point map each), at
+      // most refine_max_iter of them; they stop early once the FP64 tolerances
+      // hold.  The mixed solve counts as converged when the last correction
+      // moved Omega_CC by less than tol_refine.
+      B.refine_iterations++;
+      if (!finite()) {
+        finished = true;
+        status = fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite in refinement");
+        return;
+      }
+      if (B.nz == 1 && !B.live_host[0]) return end();
+      if (all_done(o.tol_omega, o.tol_amp)) {
+        conv = true;
+        return end();
+      }
+      if (++r < o.refine_max_iter) return;
+      conv = mixed_done(o.tol_refine);
+      if (conv)
+        for (Inst& I : B.inst)
+          if (I.conv_iter < 0) I.conv_iter = B.iterations;
+      return end();
+    }
+    ++it;
+    if (!finite()) {
       check_device_error(h);
-      return fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite at iteration %d", B.iterations);
+      finished = true;
+      status = fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite at iteration %d", B.iterations);
+      return;
     }
     if (B.active == 0) {
-      if (all_done(s, o.tol_omega, o.tol_amp)) {
-        conv = true;
-        break;
-      }
-      continue;
+      if (all_done(o.tol_omega, o.tol_amp)) conv = true;
+      if (conv || it >= o.max_iter) end();
+      return;
     }
-    // low-precision phase: hand over once every instance's dOmega is small or has stopped falling
+    // a low-precision phase hands over once every instance's dOmega is small
+    // or has stopped falling (or the polishing phase reached its cap)
+    if (B.s32->gk == GEMM_BF16X3 && B.polishing) B.polish_iterations++;
     bool handover = true;
     for (int z = 0; z < B.nz; ++z) {
       if (!B.live_host[z]) continue;
@@ -1679,39 +1776,77 @@ ftcc_status solve_batch(Batch& B) {
       } else {
         ++stall[z];
       }
-      handover = handover && (d < o.tol_mixed || stall[z] >= 3);
+      // TF32 stops helping once Omega_CC changes by less than its unit
+      // roundoff (2^-11) relative to Omega_CC
+      const double floor_tf32 =
+          B.s32->gk == GEMM_TF32 ? std::ldexp(std::fabs(s[static_cast<size_t>(z) * kStateStride]), -11) : 0.0;
+      handover = handover && (d < o.tol_mixed || d < floor_tf32 || stall[z] >= 3);
     }
-    if (!handover) continue;
+    if (B.polishing && B.polish_iterations >= o.polish_max_iter) handover = true;
+    if (!handover) {
+      if (it >= o.max_iter) end();
+      return;
+    }
+    // TF32 phase done: polish with the two-way bf16 split (about 2^-16
+    // relative per product against 2^-11 for TF32) from the TF32 amplitudes
+    if (B.s32->gk == GEMM_TF32 && o.polish_max_iter > 0) {
+      check_device_error(h);
+      B.s32->set_kind(GEMM_BF16X3);
+      B.polishing = true;
+      std::fill(best.begin(), best.end(), 1e300);
+      std::fill(stall.begin(), stall.end(), 0);
+      if (it >= o.max_iter) end();
+      return;
+    }
     if (o.refine_max_iter == 0) {
-      conv = true;
-      for (int z = 0; z < B.nz; ++z)
-        if (B.live_host[z]) conv = conv && s[static_cast<size_t>(z) * kStateStride + 1] < o.tol_mixed;
-      break;
+      conv = mixed_done(o.tol_mixed);
+      return end();
     }
     check_device_error(h);
     promote_to_fp64(B);
     for (Inst& I : B.inst) I.conv_iter = -1;
-    for (int r = 0; r < o.refine_max_iter; ++r) {
-      timed_iterations(B, 1);
-      B.refine_iterations++;
-      s = read_states(B);
-      if (!finite(s)) return fail(h, FTCC_ERR_DIVERGED, "Omega_CC became non-finite in refinement");
-      if (B.nz == 1 && !B.live_host[0]) break;
-      if (all_done(s, o.tol_omega, o.tol_amp)) {
-        conv = true;
-        break;
-      }
-    }
-    break;
+    refining = true;
+    r = 0;
   }
-  check_device_error(h);
-  int dead = 0;
-  for (int z = 0; z < B.nz; ++z) dead += !B.live_host[z];
-  B.solved = conv && dead == 0;
-  B.solved_live = conv && dead < B.nz;
-  if (dead) return fail(h, FTCC_ERR_DIVERGED, "%d of %d instances diverged (frozen)", dead, B.nz);
-  if (!conv) return fail(h, FTCC_ERR_NOT_CONVERGED, "not converged after %d iterations", B.iterations);
-  return FTCC_OK;
+};
+
+ftcc_status solve_batch(Batch& B) {
+  if (B.quad != FTCC_QUAD_SIMPSON) return rk_solve(B);
+  SolveDriver d(B);
+  while (!d.finished) {
+    d.launch();
+    d.collect();
+  }
+  return d.status;
+}
+
+// The batches of one batched solve advanced together: each iteration is
+// launched on every unfinished batch's stream before any is waited for.
+std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
+  std::vector<ftcc_status> st(Bs.size(), FTCC_OK);
+  std::vector<std::unique_ptr<SolveDriver>> ds;
+  for (size_t k = 0; k < Bs.size(); ++k) {
+    if (Bs[k]->quad != FTCC_QUAD_SIMPSON) {
+      st[k] = rk_solve(*Bs[k]);
+      ds.emplace_back(nullptr);
+      continue;
+    }
+    ds.emplace_back(new SolveDriver(*Bs[k]));
+  }
+  for (;;) {
+    bool any = false;
+    for (auto& d : ds)
+      if (d && !d->finished) {
+        d->launch();
+        any = true;
+      }
+    if (!any) break;
+    for (auto& d : ds)
+      if (d && !d->finished) d->collect();
+  }
+  for (size_t k = 0; k < ds.size(); ++k)
+    if (ds[k]) st[k] = ds[k]->status;
+  return st;
 }
 
 // Make the FP64 solver current with converged amplitudes (refining a
@@ -1736,20 +1871,21 @@ void ensure_fp64_solution(Batch& B) {
 // Stationarity of the discrete Lagrangian (Eqs. Lagrangian, lmu, ltilde):
 // m = -dEcc/ds - (dS/ds)^T u,  u_x = sum_y G[y,x] exp(-Delta(tau_y - tau_x)) m_y,
 // with m_y = g_y lambda_y / beta; fixed-point iteration from m = 0.
-int lambda_solve(Batch& B, double tol, int max_iter) {
+template <class T>
+int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   ftcc_ctx* h = B.home;
-  Solver<double>& s = *B.s64;
+  constexpr size_t es = sizeof(T);
   const long long o = B.no, v = B.nv, ng = B.ng, nz = B.nz;
   const long long n1 = nz * ng * o * v, n2 = nz * ng * o * o * v * v;
-  ensure(h, B.m1, n1 * 8);
-  ensure(h, B.m2, n2 * 8);
-  ensure(h, B.mn1, n1 * 8);
-  ensure(h, B.mn2, n2 * 8);
-  ensure(h, B.u1, n1 * 8);
-  ensure(h, B.u2, n2 * 8);
-  ensure(h, B.tb1, n1 * 8);
-  ensure(h, B.tb2, n2 * 8);
-  ensure(h, B.dE1, n1 * 8);
+  ensure(h, B.m1, n1 * es);
+  ensure(h, B.m2, n2 * es);
+  ensure(h, B.mn1, n1 * es);
+  ensure(h, B.mn2, n2 * es);
+  ensure(h, B.u1, n1 * es);
+  ensure(h, B.u2, n2 * es);
+  ensure(h, B.tb1, n1 * es);
+  ensure(h, B.tb2, n2 * es);
+  ensure(h, B.dE1, n1 * es);
   ensure(h, B.cz, nz * ng * 8);
   const int nblk = 152 * 4;
   ensure(h, B.lpart, 2 * nblk * 8);
@@ -1757,46 +1893,52 @@ int lambda_solve(Batch& B, double tol, int max_iter) {
   for (long long z = 0; z < nz; ++z)
     for (long long x = 0; x < ng; ++x) c[z * ng + x] = simpson_weight_host(static_cast<int>(x), static_cast<int>(ng)) / (ng - 1);
   CU(cudaMemcpyAsync(B.cz.p, c.data(), c.size() * 8, cudaMemcpyHostToDevice, h->st));
-  CU(cudaMemsetAsync(B.m1.p, 0, n1 * 8, h->st));
-  CU(cudaMemsetAsync(B.m2.p, 0, n2 * 8, h->st));
+  CU(cudaMemsetAsync(B.m1.p, 0, n1 * es, h->st));
+  CU(cudaMemsetAsync(B.m2.p, 0, n2 * es, h->st));
   // a member frozen after diverging takes no part: its amplitudes are set to
   // zero so that its (unused) multipliers stay finite
   for (long long z = 0; z < nz; ++z)
     if (!B.live_host[z]) {
-      CU(cudaMemsetAsync(static_cast<double*>(s.t1.p) + z * ng * o * v, 0, ng * o * v * 8, h->st));
-      CU(cudaMemsetAsync(static_cast<double*>(s.t2.p) + z * ng * o * o * v * v, 0, ng * o * o * v * v * 8, h->st));
+      CU(cudaMemsetAsync(static_cast<T*>(s.t1.p) + z * ng * o * v, 0, ng * o * v * es, h->st));
+      CU(cudaMemsetAsync(static_cast<T*>(s.t2.p) + z * ng * o * o * v * v, 0, ng * o * o * v * v * es, h->st));
     }
   // dE/ds1 without the weight: f_kc + sum_jb <kj||cb> s_j^b   (Eq. E)
   s.nx = s.ng;
-  double* dE1 = static_cast<double*>(B.dE1.p);
+  T* dE1 = static_cast<T*>(B.dE1.p);
   s.scatter(dE1, "zxkc", s.F("zkc"), "zkc", 1.0, 0.0, "");
-  s.contract({dE1, "zxkc"}, 1.0, Tn<const double>{s.V("zkjcb"), "zkjcb", true},
-             Tn<const double>{static_cast<const double*>(s.t1.p), "zxjb"});
+  s.contract({dE1, "zxkc"}, 1.0, Tn<const T>{s.V("zkjcb"), "zkjcb", true},
+             Tn<const T>{static_cast<const T*>(s.t1.p), "zxjb"});
   CU(cudaStreamSynchronize(h->st));
   PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
   a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
   a2.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a2.size + 127) / 128)));
   std::vector<double> parts(2 * nblk);
-  int it = 0;
+  int it = 0, stall = 0;
+  double best_rel = 1e300;
   for (it = 1; it <= max_iter; ++it) {
-    CU(launch_propagate_t(static_cast<const double*>(B.m1.p), static_cast<double*>(B.u1.p), a1, h->st));
-    CU(launch_propagate_t(static_cast<const double*>(B.m2.p), static_cast<double*>(B.u2.p), a2, h->st));
+    CU(launch_propagate_t(static_cast<const T*>(B.m1.p), static_cast<T*>(B.u1.p), a1, h->st));
+    CU(launch_propagate_t(static_cast<const T*>(B.m2.p), static_cast<T*>(B.u2.p), a2, h->st));
     for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
       const int nx = std::min(s.nxc, s.ng - x0);
       const long long f1 = x0 * o * v, f2 = x0 * o * o * v * v;
-      s.vjp(static_cast<const double*>(s.t1.p) + f1, static_cast<const double*>(s.t2.p) + f2,
-            static_cast<double*>(B.u1.p) + f1, static_cast<double*>(B.u2.p) + f2, static_cast<double*>(B.tb1.p) + f1,
-            static_cast<double*>(B.tb2.p) + f2, nx);
+      s.vjp(static_cast<const T*>(s.t1.p) + f1, static_cast<const T*>(s.t2.p) + f2,
+            static_cast<T*>(B.u1.p) + f1, static_cast<T*>(B.u2.p) + f2, static_cast<T*>(B.tb1.p) + f1,
+            static_cast<T*>(B.tb2.p) + f2, nx);
     }
     double dmax = 0, smax = 0;
     for (int k = 0; k < 2; ++k) {
       const bool one = k == 0;
-      CU(launch_lambda_combine(one ? dE1 : static_cast<const double*>(B.V64.p),
-                               static_cast<const double*>(one ? B.tb1.p : B.tb2.p),
-                               static_cast<double*>(one ? B.mn1.p : B.mn2.p),
-                               static_cast<const double*>(one ? B.m1.p : B.m2.p), one ? o * v : o * o * v * v,
-                               static_cast<int>(ng), static_cast<int>(nz), static_cast<const double*>(B.cz.p),
-                               one ? 0.0 : 0.25, static_cast<double*>(B.lpart.p), nblk, h->st));
+      if (one)
+        CU(launch_lambda_combine<T, T>(dE1, static_cast<const T*>(B.tb1.p), static_cast<T*>(B.mn1.p),
+                                       static_cast<const T*>(B.m1.p), o * v, static_cast<int>(ng), static_cast<int>(nz),
+                                       static_cast<const double*>(B.cz.p), 0.0, static_cast<double*>(B.lpart.p), nblk,
+                                       h->st));
+      else
+        CU(launch_lambda_combine<T, double>(static_cast<const double*>(B.V64.p), static_cast<const T*>(B.tb2.p),
+                                            static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), o * o * v * v,
+                                            static_cast<int>(ng), static_cast<int>(nz),
+                                            static_cast<const double*>(B.cz.p), 0.25, static_cast<double*>(B.lpart.p),
+                                            nblk, h->st));
       CU(cudaMemcpyAsync(parts.data(), B.lpart.p, 2 * nblk * 8, cudaMemcpyDeviceToHost, h->st));
       sync(h);
       for (int b = 0; b < nblk; ++b) {
@@ -1807,7 +1949,18 @@ int lambda_solve(Batch& B, double tol, int max_iter) {
     std::swap(B.m1, B.mn1);
     std::swap(B.m2, B.mn2);
     if (!std::isfinite(dmax)) throw Fail{FTCC_ERR_DIVERGED, "lambda iteration diverged"};
-    if (dmax / std::max(1.0, smax) < tol) break;
+    const double rel = dmax / std::max(1.0, smax);
+    if (rel < tol) break;
+    // in FP32 the change stops falling at the rounding of the multipliers:
+    // three iterations without a new smallest change end the sweep there
+    if (sizeof(T) == 4) {
+      if (rel < best_rel) {
+        best_rel = rel;
+        stall = 0;
+      } else if (++stall >= 3 && best_rel < 1e-4) {
+        break;
+      }
+    }
   }
   check_device_error(h);
   B.lambda_iterations = it;
@@ -1820,37 +1973,42 @@ int lambda_solve(Batch& B, double tol, int max_iter) {
 // blocks (Fermi factors and the Fock matrix), the propagator (Delta, beta)
 // and the reference (Omega0, Omega1).  Fills out[z] and rdm[z] (N x N,
 // rdm[q][p] pairs with X[p][q]).
-void response(Batch& B, std::vector<ftcc_adjoint_result>& out, std::vector<std::vector<double>>& rdm) {
+template <class T>
+void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std::vector<std::vector<double>>& rdm) {
   ftcc_ctx* h = B.home;
-  Solver<double>& s = *B.s64;
   const int nz = B.nz, no = B.no, nv = B.nv, N = B.N, ng = B.ng;
   const long long n1 = static_cast<long long>(nz) * ng * no * nv;
   PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
   a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
   a2.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a2.size + 127) / 128)));
   // cotangent of S at the converged multipliers
-  CU(launch_propagate_t(static_cast<const double*>(B.m1.p), static_cast<double*>(B.u1.p), a1, h->st));
-  CU(launch_propagate_t(static_cast<const double*>(B.m2.p), static_cast<double*>(B.u2.p), a2, h->st));
+  CU(launch_propagate_t(static_cast<const T*>(B.m1.p), static_cast<T*>(B.u1.p), a1, h->st));
+  CU(launch_propagate_t(static_cast<const T*>(B.m2.p), static_cast<T*>(B.u2.p), a2, h->st));
   for (auto& kv : s.fixed_bar) h->put(kv.second);
   s.fixed_bar.clear();
   s.want_fixed_bar = true;
   for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
     const int nx = std::min(s.nxc, s.ng - x0);
     const long long f1 = static_cast<long long>(x0) * no * nv, f2 = f1 * no * nv;
-    s.vjp(static_cast<const double*>(s.t1.p) + f1, static_cast<const double*>(s.t2.p) + f2,
-          static_cast<double*>(B.u1.p) + f1, static_cast<double*>(B.u2.p) + f2, static_cast<double*>(B.tb1.p) + f1,
-          static_cast<double*>(B.tb2.p) + f2, nx);
+    s.vjp(static_cast<const T*>(s.t1.p) + f1, static_cast<const T*>(s.t2.p) + f2,
+          static_cast<T*>(B.u1.p) + f1, static_cast<T*>(B.u2.p) + f2, static_cast<T*>(B.tb1.p) + f1,
+          static_cast<T*>(B.tb2.p) + f2, nx);
   }
   s.want_fixed_bar = false;
   // direct dependence of Omega_CC = sum_y (g_y / beta) E_y on f_ia and <ij||ab> (Eq. E)
   s.nx = s.ng;
-  using CT = Tn<const double>;
-  const double* cz = static_cast<const double*>(B.cz.p);
-  const double* t1 = static_cast<const double*>(s.t1.p);
-  const double* t2 = static_cast<const double*>(s.t2.p);
-  double* Aov = s.fixed_adjoint(s.F("zia"));
-  double* Aoovv = s.fixed_adjoint(s.V("zijab"));
-  double* cs1 = static_cast<double*>(B.tb1.p);
+  using CT = Tn<const T>;
+  // the energy weights c_x = g_x / beta in the amplitude type
+  Buf czT = h->get(static_cast<size_t>(nz) * ng * sizeof(T));
+  if (!czT.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+  CU(launch_convert<double, T>(static_cast<const double*>(B.cz.p), static_cast<T*>(czT.p),
+                               static_cast<long long>(nz) * ng, h->st));
+  const T* cz = static_cast<const T*>(czT.p);
+  const T* t1 = static_cast<const T*>(s.t1.p);
+  const T* t2 = static_cast<const T*>(s.t2.p);
+  T* Aov = s.fixed_adjoint(s.F("zia"));
+  T* Aoovv = s.fixed_adjoint(s.V("zijab"));
+  T* cs1 = static_cast<T*>(B.tb1.p);
   s.contract({Aov, "zia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"});
   s.contract({Aoovv, "zijab"}, 0.25, CT{cz, "zx"}, CT{t2, "zxijab"});
   s.contract({cs1, "zxia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"}, "", 0.0);
@@ -1876,12 +2034,12 @@ void response(Batch& B, std::vector<ftcc_adjoint_result>& out, std::vector<std::
         dims[k] = pat[k] == 'o' ? no : nv;
         if (pat[k] == 'v') cls |= 1 << k;
       }
-      CU(launch_slot_sums(static_cast<const double*>(kv.second.p), static_cast<const double*>(it->second.p),
+      CU(launch_slot_sums(static_cast<const T*>(kv.second.p), static_cast<const T*>(it->second.p),
                           static_cast<int>(pat.size()), dims, cls, no, nv, nz, static_cast<double*>(Do.p),
                           static_cast<double*>(Dv.p), h->st));
       if (pat.size() == 2) {
         const bool h0 = pat[0] == 'o', h1 = pat[1] == 'o';
-        CU(launch_fbar_scatter(static_cast<const double*>(it->second.p), h0 ? no : nv, h1 ? no : nv,
+        CU(launch_fbar_scatter(static_cast<const T*>(it->second.p), h0 ? no : nv, h1 ? no : nv,
                                static_cast<const int*>(h0 ? B.idxO.p : B.idxV.p),
                                static_cast<const double*>(h0 ? B.facOz.p : B.facVz.p), h0 ? no : nv,
                                static_cast<const int*>(h1 ? B.idxO.p : B.idxV.p),
@@ -1893,10 +2051,10 @@ void response(Batch& B, std::vector<ftcc_adjoint_result>& out, std::vector<std::
   for (int z = 0; z < nz; ++z)
     CU(launch_fock_n(static_cast<const double*>(Fbar.p) + static_cast<long long>(z) * N * N,
                      static_cast<const double*>(B.inst[z].ctx->eri.p), N, static_cast<double*>(Gn.p) + z * N, h->st));
-  CU(launch_prop_response(static_cast<const double*>(s.S1.p), static_cast<const double*>(B.m1.p),
+  CU(launch_prop_response(static_cast<const T*>(s.S1.p), static_cast<const T*>(B.m1.p),
                           static_cast<const double*>(B.epsz.p), a1, static_cast<double*>(Ee.p),
                           static_cast<double*>(Eb.p), h->st));
-  CU(launch_prop_response(static_cast<const double*>(s.S2.p), static_cast<const double*>(B.m2.p),
+  CU(launch_prop_response(static_cast<const T*>(s.S2.p), static_cast<const T*>(B.m2.p),
                           static_cast<const double*>(B.epsz.p), a2, static_cast<double*>(Ee.p),
                           static_cast<double*>(Eb.p), h->st));
   std::vector<double> hDo(nz * no), hDv(nz * nv), hF(static_cast<size_t>(nz) * N * N), hGn(nz * N), hEe(nz * N), hEb(nz);
@@ -1954,7 +2112,7 @@ void response(Batch& B, std::vector<ftcc_adjoint_result>& out, std::vector<std::
     r.trace_rdm1 = tr;
     r.iterations = B.lambda_iterations;
   }
-  Buf* bs[] = {&Do, &Dv, &Fbar, &Gn, &Ee, &Eb};
+  Buf* bs[] = {&Do, &Dv, &Fbar, &Gn, &Ee, &Eb, &czT};
   for (Buf* q : bs) h->put(*q);
 }
 
@@ -2065,10 +2223,18 @@ ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
     drop_batch(c);
     int N = 0;
     std::vector<int> nvec;
+    std::vector<double> hh, he, hp;   // host-built site-basis systems
     if (s->kind == FTCC_SYS_HUBBARD_1D) {
       if (s->L < 1 || s->pbc != 1 || !std::isfinite(s->t) || !std::isfinite(s->U))
         return fail(c, FTCC_ERR_INVALID_ARG, "Hubbard: need L >= 1, pbc = 1, finite t and U");
+      if (s->reference < FTCC_REF_KSPACE_RHF || s->reference > FTCC_REF_UHF_SITE)
+        return fail(c, FTCC_ERR_INVALID_ARG, "Hubbard: unknown reference %d", s->reference);
       N = 2 * s->L;
+      if (s->reference != FTCC_REF_KSPACE_RHF) {
+        std::string msg;
+        if (!hubbard_site_reference(s->L, s->t, s->U, s->reference, hh, he, hp, msg))
+          return fail(c, FTCC_ERR_NOT_CONVERGED, "Hubbard reference: %s", msg.c_str());
+      }
     } else if (s->kind == FTCC_SYS_UEG) {
       if (s->n_elec < 2 || (s->n_elec & 1) || !(s->rs > 0) || !std::isfinite(s->rs))
         return fail(c, FTCC_ERR_INVALID_ARG, "UEG: need an even n_elec >= 2 and rs > 0");
@@ -2090,7 +2256,11 @@ ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
     ensure(c, c->h, static_cast<size_t>(N) * N * sizeof(double));
     ensure(c, c->eri, N4 * sizeof(double));
     ensure(c, c->eps, static_cast<size_t>(N) * sizeof(double));
-    if (s->kind == FTCC_SYS_HUBBARD_1D) {
+    if (s->kind == FTCC_SYS_HUBBARD_1D && s->reference != FTCC_REF_KSPACE_RHF) {
+      CU(cudaMemcpyAsync(c->h.p, hh.data(), hh.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CU(cudaMemcpyAsync(c->eri.p, he.data(), he.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CU(cudaMemcpyAsync(c->eps.p, hp.data(), hp.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    } else if (s->kind == FTCC_SYS_HUBBARD_1D) {
       CU(launch_hubbard(static_cast<double*>(c->h.p), static_cast<double*>(c->eri.p), static_cast<double*>(c->eps.p),
                         s->L, s->t, s->U, c->st));
     } else if (s->kind == FTCC_SYS_UEG) {
@@ -2154,6 +2324,78 @@ ftcc_status ftcc_reference_mu(ftcc_ctx* c, double beta, double n_elec, double* m
     *mu = 0.5 * (lo + hi);
     return FTCC_OK;
   });
+}
+
+// mu_CC with N(mu) = -dOmega/dmu = n_target (App. D): secant steps from mu0
+// and mu0 +- dmu (towards the target), regula falsi with the Illinois
+// weighting once the target is straddled.  Each N(mu) is a full solve plus
+// the adjoint on this context.
+ftcc_status ftcc_mu_for_n(ftcc_ctx* c, double beta, double n_target, int ngrid, ftcc_quadrature quad,
+                          const ftcc_options* opt, double mu0, double dmu, double tol_n, int max_evals, double* mu_out,
+                          double* n_out, int* evals_out, ftcc_result* out) {
+  if (!c || !mu_out || !(beta > 0) || !std::isfinite(beta) || !std::isfinite(mu0) || !(dmu > 0) ||
+      !std::isfinite(dmu) || !(tol_n > 0) || max_evals < 2 || !std::isfinite(n_target))
+    return FTCC_ERR_INVALID_ARG;
+  if (c->N == 0) return fail(c, FTCC_ERR_STATE, "no system built");
+  if (!(n_target > 0) || !(n_target < c->N)) return fail(c, FTCC_ERR_INVALID_ARG, "need 0 < n_target < N");
+  int evals = 0;
+  ftcc_result last{};
+  auto f = [&](double m, double* val) -> ftcc_status {
+    ftcc_status s = ft_ccsd_solve(c, beta, m, ngrid, quad, opt, &last);
+    if (s != FTCC_OK) return s;
+    ftcc_adjoint_result ar{};
+    s = ft_ccsd_adjoint(c, &ar, nullptr);
+    if (s != FTCC_OK) return s;
+    ++evals;
+    *val = ar.N - n_target;
+    if (!std::isfinite(*val)) return fail(c, FTCC_ERR_DIVERGED, "N(mu) not finite at mu = %.17g", m);
+    return FTCC_OK;
+  };
+  auto finish = [&](double m, double fm, ftcc_status s) {
+    *mu_out = m;
+    if (n_out) *n_out = fm + n_target;
+    if (evals_out) *evals_out = evals;
+    if (out) *out = last;
+    return s;
+  };
+  double a = mu0, fa = 0.0;
+  ftcc_status s = f(a, &fa);
+  if (s != FTCC_OK) return s;
+  if (std::fabs(fa) < tol_n) return finish(a, fa, FTCC_OK);
+  double b = mu0 + (fa < 0 ? dmu : -dmu), fb = 0.0;
+  if ((s = f(b, &fb)) != FTCC_OK) return s;
+  bool bracket = fa * fb < 0;
+  int side = 0;
+  while (std::fabs(fb) >= tol_n) {
+    if (evals >= max_evals)
+      return finish(b, fb, fail(c, FTCC_ERR_NOT_CONVERGED, "|N - n_target| = %.3g after %d evaluations",
+                                std::fabs(fb), evals));
+    if (fb == fa) return finish(b, fb, fail(c, FTCC_ERR_NOT_CONVERGED, "flat N(mu): no secant step"));
+    const double m = b - fb * (b - a) / (fb - fa);
+    double fm = 0.0;
+    if ((s = f(m, &fm)) != FTCC_OK) return s;
+    if (bracket) {
+      // keep the pair that straddles the target; halve the weight of an end
+      // point retained twice in a row (Illinois)
+      if (fm * fb < 0) {
+        a = b;
+        fa = fb;
+        side = 0;
+      } else {
+        if (side == -1) fa *= 0.5;
+        side = -1;
+      }
+      b = m;
+      fb = fm;
+    } else {
+      a = b;
+      fa = fb;
+      b = m;
+      fb = fm;
+      bracket = fa * fb < 0;
+    }
+  }
+  return finish(b, fb, FTCC_OK);
 }
 
 ftcc_status ftcc_prepare(ftcc_ctx* c, double beta, double mu, int ngrid, ftcc_quadrature quad, const ftcc_options* opt,
@@ -2220,9 +2462,12 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
   if ((s = check_quad_options(c0, quad, o)) != FTCC_OK) return s;
   return run_guarded(c0, [&]() -> ftcc_status {
     for (int i = 0; i < n; ++i) drop_batch(ctx[i]);
-    // one batch per orbital count, in order of first appearance
+    // one batch per orbital count, in order of first appearance; the batches
+    // then iterate together (solve_batches)
     std::vector<int> done(n, 0);
     ftcc_status worst = FTCC_OK;
+    std::vector<std::shared_ptr<Batch>> batches;
+    std::vector<std::vector<int>> members;
     for (int i = 0; i < n; ++i) {
       if (done[i]) continue;
       std::vector<ftcc_ctx*> cs;
@@ -2238,15 +2483,23 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
         }
       std::shared_ptr<Batch> B = prepare_batch(cs.data(), static_cast<int>(cs.size()), bs.data(), ms.data(), ngrid, o);
       B->quad = quad;
-      if (!iterate) continue;
-      ftcc_status r = solve_batch(*B);
+      batches.push_back(B);
+      members.push_back(idx);
+    }
+    if (!iterate) return FTCC_OK;
+    std::vector<Batch*> raw;
+    for (auto& B : batches) raw.push_back(B.get());
+    const std::vector<ftcc_status> rs = solve_batches(raw);
+    for (size_t b = 0; b < batches.size(); ++b) {
+      Batch& B = *batches[b];
+      const ftcc_status r = rs[b];
       if (r != FTCC_OK) {
-        if (worst == FTCC_OK) c0->err = B->home->err;
+        if (worst == FTCC_OK) c0->err = B.home->err;
         if (worst == FTCC_OK || r == FTCC_ERR_DIVERGED) worst = r;
       }
-      const std::vector<double> st = read_states(*B);
+      const std::vector<double> st = read_states(B);
       if (out)
-        for (size_t k = 0; k < idx.size(); ++k) fill_result(*B, static_cast<int>(k), st, &out[idx[k]]);
+        for (size_t k = 0; k < members[b].size(); ++k) fill_result(B, static_cast<int>(k), st, &out[members[b][k]]);
     }
     return worst;
   });
@@ -2273,15 +2526,84 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
-    ensure_fp64_solution(B);
-    if (!B.lambda_done) lambda_solve(B, 1e-11, 400);
-    if (!B.lambda_done) return fail(c, FTCC_ERR_NOT_CONVERGED, "lambda equations not converged");
     std::vector<ftcc_adjoint_result> res;
     std::vector<std::vector<double>> rdms;
-    response(B, res, rdms);
+    if (B.active == 1 && B.opt.mixed_adjoint) {
+      // the lambda sweep and the response on the FP32 solver: FP32
+      // multipliers, BF16X3 contractions in the VJP, FP64 propagator
+      // factors, weights and sums
+      Solver<float>& s = *B.s32;
+      s.set_kind(GEMM_BF16X3);
+      if (!B.lambda_done) lambda_solve<float>(B, s, 1e-7, 400);
+      if (!B.lambda_done) return fail(c, FTCC_ERR_NOT_CONVERGED, "lambda equations not converged");
+      B.adjoint_fp32 = true;
+      response<float>(B, s, res, rdms);
+    } else {
+      ensure_fp64_solution(B);
+      if (!B.lambda_done) lambda_solve<double>(B, *B.s64, 1e-11, 400);
+      if (!B.lambda_done) return fail(c, FTCC_ERR_NOT_CONVERGED, "lambda equations not converged");
+      B.adjoint_fp32 = false;
+      response<double>(B, *B.s64, res, rdms);
+    }
     if (out) *out = res[c->member];
     if (rdm1) memcpy(rdm1, rdms[c->member].data(), rdms[c->member].size() * sizeof(double));
     check_device_error(B.home);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_rdm2(ftcc_ctx* c, double* gamma) {
+  if (!c || !gamma) return FTCC_ERR_INVALID_ARG;
+  if (c->batch && c->batch->lambda_done && c->batch->adjoint_fp32)
+    return fail(c, FTCC_ERR_UNSUPPORTED, "the two-particle density needs the FP64 adjoint (mixed_adjoint = 0)");
+  if (!c->batch || !c->batch->lambda_done || !c->batch->s64 || c->batch->s64->fixed_bar.empty())
+    return fail(c, FTCC_ERR_STATE, "the two-particle density needs ft_ccsd_adjoint first");
+  return run_guarded(c, [&]() -> ftcc_status {
+    Batch& B = *c->batch;
+    Solver<double>& s = *B.s64;
+    ftcc_ctx* h = B.home;
+    CU(cudaSetDevice(h->device));
+    const int N = B.N, no = B.no, nv = B.nv, z = c->member;
+    const Inst& I = B.inst[z];
+    const size_t N4 = static_cast<size_t>(N) * N * N * N;
+    Buf g = h->get(N4 * sizeof(double));
+    if (!g.p) throw Fail{FTCC_ERR_OOM, "allocation of the two-particle density failed"};
+    CU(cudaMemsetAsync(g.p, 0, g.bytes, h->st));
+    // dL/d<pq||rs> at a fixed reference: the adjoint of every thermal block
+    // (integral times the slot factors of its letters) mapped back
+    for (auto& kv : s.Vb) {
+      auto it = s.fixed_bar.find(kv.second.p);
+      if (it == s.fixed_bar.end()) continue;
+      const std::string& pat = kv.first;
+      const int* ix[4];
+      const double* fx[4];
+      int nn[4];
+      long long total = 1;
+      for (int k = 0; k < 4; ++k) {
+        const bool ho = pat[k] == 'o';
+        ix[k] = static_cast<const int*>(ho ? B.idxO.p : B.idxV.p);
+        fx[k] = static_cast<const double*>(ho ? I.facO.p : I.facV.p);
+        nn[k] = ho ? no : nv;
+        total *= nn[k];
+      }
+      CU(launch_eri_adjoint(static_cast<const double*>(it->second.p) + z * total, N, ix[0], fx[0], nn[0], ix[1],
+                            fx[1], nn[1], ix[2], fx[2], nn[2], ix[3], fx[3], nn[3], static_cast<double*>(g.p), h->st));
+    }
+    std::vector<double> raw(N4);
+    CU(cudaMemcpyAsync(raw.data(), g.p, N4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    h->put(g);
+    // projection onto the symmetries of <pq||rs>: antisymmetric in (p, q)
+    // and in (r, s), symmetric under (pq) <-> (rs)
+    auto at = [&](int p, int q, int r, int t) { return raw[((static_cast<size_t>(p) * N + q) * N + r) * N + t]; };
+    auto anti = [&](int p, int q, int r, int t) {
+      return 0.25 * (at(p, q, r, t) - at(q, p, r, t) - at(p, q, t, r) + at(q, p, t, r));
+    };
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q)
+        for (int r = 0; r < N; ++r)
+          for (int t = 0; t < N; ++t)
+            gamma[((static_cast<size_t>(p) * N + q) * N + r) * N + t] = 0.5 * (anti(p, q, r, t) + anti(r, t, p, q));
     return FTCC_OK;
   });
 }
@@ -2422,6 +2744,20 @@ ftcc_status ftcc_get_lambda(ftcc_ctx* c, double* m1, double* m2) {
     Batch& B = *c->batch;
     const long long n1 = static_cast<long long>(B.ng) * B.no * B.nv, n2 = n1 * B.no * B.nv;
     const long long z = c->member;
+    if (B.adjoint_fp32) {
+      std::vector<float> tmp;
+      const std::pair<double*, long long> parts[2] = {{m1, n1}, {m2, n2}};
+      for (int k = 0; k < 2; ++k) {
+        if (!parts[k].first) continue;
+        const long long n = parts[k].second;
+        tmp.resize(n);
+        CU(cudaMemcpyAsync(tmp.data(), static_cast<const float*>(k == 0 ? B.m1.p : B.m2.p) + z * n, n * 4,
+                           cudaMemcpyDeviceToHost, B.home->st));
+        sync(B.home);
+        for (long long e = 0; e < n; ++e) parts[k].first[e] = tmp[e];
+      }
+      return FTCC_OK;
+    }
     if (m1) CU(cudaMemcpyAsync(m1, static_cast<const double*>(B.m1.p) + z * n1, n1 * 8, cudaMemcpyDeviceToHost, B.home->st));
     if (m2) CU(cudaMemcpyAsync(m2, static_cast<const double*>(B.m2.p) + z * n2, n2 * 8, cudaMemcpyDeviceToHost, B.home->st));
     sync(B.home);
@@ -2558,6 +2894,16 @@ ftcc_status ftcc_gemm(ftcc_ctx* c, int precision, int batch, int M, int N, int K
     }
     sync(c);
     check_device_error(c);
+    return FTCC_OK;
+  });
+}
+
+ftcc_status ftcc_inject_device_error(ftcc_ctx* c, int code) {
+  if (!c || code <= 0) return FTCC_ERR_INVALID_ARG;
+  return run_guarded(c, [&] {
+    CU(cudaSetDevice(c->device));
+    CU(cudaMemcpyAsync(c->dev_err, &code, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    sync(c);
     return FTCC_OK;
   });
 }

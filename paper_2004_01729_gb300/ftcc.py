@@ -18,13 +18,16 @@ OK, ERR_INVALID_ARG, ERR_NO_DEVICE, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVERGED, ER
 QUAD_SIMPSON, QUAD_RK1, QUAD_RK2, QUAD_RK4 = range(4)
 PREC_FP64, PREC_TF32, PREC_BF16X3 = range(3)
 SYS_HUBBARD_1D, SYS_UEG, SYS_GENERIC = range(3)
+REF_KSPACE_RHF, REF_NEEL_SITE, REF_UHF_SITE = range(3)
+REFERENCES = {"kspace_rhf": REF_KSPACE_RHF, "neel": REF_NEEL_SITE, "uhf": REF_UHF_SITE}
 PRECISIONS = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16x3": PREC_BF16X3}
 
 
 class System(C.Structure):
     _fields_ = [("kind", C.c_int), ("L", C.c_int), ("t", C.c_double), ("U", C.c_double), ("pbc", C.c_int),
                 ("n_elec", C.c_int), ("rs", C.c_double), ("n_pw", C.c_int), ("N", C.c_int),
-                ("h", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double))]
+                ("h", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double)),
+                ("reference", C.c_int)]
 
 
 class Options(C.Structure):
@@ -32,14 +35,15 @@ class Options(C.Structure):
                 ("trunc_thr", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
                 ("refine_max_iter", C.c_int), ("tol_mixed", C.c_double), ("tau_chunk", C.c_int),
                 ("use_graph", C.c_int), ("stream_tau", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("polish_max_iter", C.c_int), ("fp64_propagation", C.c_int),
+                ("tol_refine", C.c_double), ("mixed_adjoint", C.c_int)]
 
 
 class Result(C.Structure):
     _fields_ = [("omega", C.c_double), ("omega0", C.c_double), ("omega1", C.c_double), ("omega_cc", C.c_double),
                 ("d_omega", C.c_double), ("d_amp", C.c_double), ("iterations", C.c_int),
                 ("refine_iterations", C.c_int), ("converged", C.c_int), ("n_occ", C.c_int), ("n_vir", C.c_int),
-                ("ms_per_iter", C.c_double), ("kernels_per_iter", C.c_int)]
+                ("ms_per_iter", C.c_double), ("kernels_per_iter", C.c_int), ("polish_iterations", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +79,9 @@ _SIGS = [
     ("ftcc_num_orbitals", C.c_int, [C.c_void_p]),
     ("ftcc_get_system", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ftcc_reference_mu", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
+    ("ftcc_mu_for_n", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(Options),
+                                C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(Result)]),
     ("ftcc_prepare", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(Options),
                                C.POINTER(Result)]),
     ("ft_ccsd_iterate", C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
@@ -87,6 +94,7 @@ _SIGS = [
                                        C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(Options)]),
     ("ft_ccsd_adjoint", C.c_int, [C.c_void_p, C.POINTER(AdjointResult), C.c_void_p]),
     ("ftcc_get_amplitudes", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ftcc_rdm2", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ftcc_eval_s", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ftcc_propagate", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p]),
     ("ftcc_gemm", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
@@ -102,6 +110,7 @@ _SIGS = [
     ("ftcc_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("ftcc_profile_read", C.c_int, [C.c_void_p, C.POINTER(KernelStats), C.c_int]),
     ("ftcc_device_error", C.c_int, [C.c_void_p]),
+    ("ftcc_inject_device_error", C.c_int, [C.c_void_p, C.c_int]),
 ]
 
 
@@ -133,8 +142,8 @@ def _dptr(a):
 
 def default_options(**kw):
     o = Options(tol_omega=1e-10, tol_amp=1e-8, damping=1.0, trunc_thr=0.0, max_iter=200,
-                precision=PREC_FP64, refine_max_iter=8, tol_mixed=1e-7, tau_chunk=0, use_graph=1, stream_tau=0,
-                autotune=1)
+                precision=PREC_FP64, refine_max_iter=2, tol_mixed=1e-7, tau_chunk=0, use_graph=1, stream_tau=0,
+                autotune=1, polish_max_iter=40, fp64_propagation=1, tol_refine=1e-6, mixed_adjoint=0)
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
@@ -204,8 +213,9 @@ class Context:
         return s
 
     # -- systems
-    def build_hubbard(self, L, t, U):
-        sysd = System(kind=SYS_HUBBARD_1D, L=L, t=t, U=U, pbc=1)
+    def build_hubbard(self, L, t, U, reference="kspace_rhf"):
+        ref = REFERENCES[reference] if isinstance(reference, str) else int(reference)
+        sysd = System(kind=SYS_HUBBARD_1D, L=L, t=t, U=U, pbc=1, reference=ref)
         self._check(self.lib.build_integrals(self.h, C.byref(sysd)), "build_integrals")
         return self.num_orbitals()
 
@@ -246,6 +256,16 @@ class Context:
         self._check(self.lib.ftcc_reference_mu(self.h, beta, n_elec, C.byref(mu)), "ftcc_reference_mu")
         return mu.value
 
+    def mu_for_n(self, beta, n_target, ngrid, mu0, dmu=0.05, tol_n=1e-10, max_evals=40, quad=QUAD_SIMPSON, **opts):
+        """ftcc_mu_for_n: mu_CC with N(mu_CC) = n_target; returns (mu, N, evaluations, last solve)."""
+        o = default_options(**opts)
+        r = Result()
+        mu, n, ev = C.c_double(), C.c_double(), C.c_int()
+        self._check(self.lib.ftcc_mu_for_n(self.h, beta, n_target, ngrid, quad, C.byref(o), mu0, dmu, tol_n,
+                                           max_evals, C.byref(mu), C.byref(n), C.byref(ev), C.byref(r)),
+                    "ftcc_mu_for_n")
+        return mu.value, n.value, ev.value, r.as_dict()
+
     # -- solves
     def prepare(self, beta, mu, ngrid, quad=QUAD_SIMPSON, **opts):
         o = default_options(**opts)
@@ -277,6 +297,13 @@ class Context:
         d = {k: getattr(out, k) for k, _ in out._fields_}
         d["status"] = s
         return d, rdm
+
+    def rdm2(self):
+        """ftcc_rdm2: the unrelaxed normal-ordered 2-RDM Gamma_N [N, N, N, N] after adjoint()."""
+        N = self.num_orbitals()
+        g = np.empty((N, N, N, N))
+        self._check(self.lib.ftcc_rdm2(self.h, g.ctypes.data), "ftcc_rdm2")
+        return g
 
     def amplitudes(self, ngrid, no, nv):
         s1 = np.empty((ngrid, no, nv))
@@ -363,6 +390,9 @@ class Context:
 
     def device_error(self):
         return self.lib.ftcc_device_error(self.h)
+
+    def inject_device_error(self, code):
+        self._check(self.lib.ftcc_inject_device_error(self.h, int(code)), "ftcc_inject_device_error")
 
 
 def _batch_args(ctxs, betas, mus):

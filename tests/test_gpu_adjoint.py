@@ -233,3 +233,45 @@ def test_adjoint_of_live_members_beside_a_diverged_one():
     assert np.max(np.abs(rdm - erdm)) < 1e-8
     for c in ctxs + [one]:
         c.close()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_response_matches_golden_hubbard10(ctx, k):
+    """N, E, S and dOmega/dbeta of the three 10-site temperatures (FP64 solve,
+    GPU lambda sweep) against the oracle's golden values."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "oracle_hubbard10.json")))[k]
+    c = wl.HUBBARD_10[k]
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    r = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    assert r["converged"]
+    d, rdm = ctx.adjoint(with_rdm1=True)
+    for key in ("dOmega_dmu", "dOmega_dbeta", "N", "E", "S"):
+        assert abs(d[key] - gold[key]) < 1e-8, (key, d[key], gold[key])
+    assert np.max(np.abs(np.diag(rdm) - np.array(gold["rdm1_diag"]))) < 1e-8
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_mixed_adjoint_hubbard10(ctx, k):
+    """The lambda sweep and the response in the mixed arithmetic (FP32
+    multipliers, BF16X3 contractions, FP64 propagator factors and sums) after
+    a BF16X3 solve without FP64 iterations: N, E and S of the three 10-site
+    temperatures against the oracle's golden values."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "oracle_hubbard10.json")))[k]
+    c = wl.HUBBARD_10[k]
+    ctx.build_hubbard(c["L"], c["t"], c["U"])
+    r = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision="bf16x3", refine_max_iter=0, mixed_adjoint=1)
+    assert r["converged"] and r["refine_iterations"] == 0
+    d, rdm = ctx.adjoint(with_rdm1=True)
+    for key in ("N", "E", "S"):
+        assert abs(d[key] - gold[key]) < 2e-5 * max(1.0, abs(gold[key])), (key, d[key], gold[key])
+    assert np.max(np.abs(np.diag(rdm) - np.array(gold["rdm1_diag"]))) < 2e-5
+    from paper_2004_01729_gb300 import ftcc
+    with pytest.raises(ftcc.FTCCError) as e:
+        ctx.rdm2()
+    assert e.value.status == ftcc.ERR_UNSUPPORTED

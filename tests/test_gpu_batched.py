@@ -3,6 +3,7 @@ CUDA graph per iteration) against the oracle and against single solves."""
 import json
 import os
 
+import numpy as np
 import pytest
 import torch
 
@@ -73,26 +74,38 @@ def test_batched_equals_single_solves():
 
 def test_hubbard_batch_64_instances():
     """The 64-instance workload (6-14 sites, U in [1,8], T in [0.25,4]) in
-    one batched solve per size class; the 6-site instances are checked
-    against the oracle, the rest against single-instance GPU solves."""
+    one batched mixed solve per size class.  Exactly one member, instance 43
+    (6 sites, U = 7.74, beta = 2.78), diverges from s = 0, and so does the
+    oracle's iteration on it (undamped and damped down to 0.15): the method's
+    fixed point is not reached from zero amplitudes there, so it is reported
+    diverged and frozen while the other 63 converge.  One converged member of
+    every size class is checked against a single-instance FP64 GPU solve, and
+    the first 6- and 8-site members against the oracle."""
     from paper_2004_01729_gb300 import ftcc
     cfgs = wl.hubbard_batch()
     ng = cfgs[0]["ngrid"]
     ctxs = _ctxs(cfgs)
     res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], ng, precision="tf32",
                              refine_max_iter=30, max_iter=400, allow_unconverged=True)
-    checked = 0
-    for r, c, ctx in zip(res, cfgs, ctxs):
-        if not r["converged"]:
+    failed = [k for k, r in enumerate(res) if not r["converged"]]
+    assert failed == [43], failed
+    c = cfgs[43]
+    bad = fc.solve(fc.Problem(systems.hubbard_1d(c["L"], c["t"], c["U"]), c["beta"], c["mu"], ng), max_iter=40)
+    assert not bad["converged"]
+    assert not np.isfinite(bad["history"][-1]) or abs(bad["history"][-1]) > 1e6, bad["history"][-3:]
+    seen = set()
+    for k, (r, c, ctx) in enumerate(zip(res, cfgs, ctxs)):
+        if not r["converged"] or c["L"] in seen:
             continue
-        if c["L"] == 6 and checked < 4:
+        seen.add(c["L"])
+        single = ctx.solve(c["beta"], c["mu"], ng, precision="fp64", tol_omega=1e-12, tol_amp=1e-10, max_iter=400)
+        assert single["converged"]
+        assert abs(r["omega"] - single["omega"]) < 1e-6, (k, c, r["omega"], single["omega"])
+        if c["L"] <= 8:
             ref = fc.solve(fc.Problem(systems.hubbard_1d(c["L"], c["t"], c["U"]), c["beta"], c["mu"], ng),
                            tol=1e-12, tol_amp=1e-10, max_iter=600)
-            if ref["converged"]:
-                assert abs(r["omega"] - ref["omega"]) < 1e-6
-                checked += 1
-    assert checked >= 1
-    n_conv = sum(r["converged"] for r in res)
-    assert n_conv >= len(res) // 2, n_conv
+            assert ref["converged"]
+            assert abs(single["omega"] - ref["omega"]) < 1e-8
+    assert seen == {6, 8, 10, 12, 14}
     for c in ctxs:
         c.close()

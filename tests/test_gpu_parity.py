@@ -117,6 +117,9 @@ def _build(ctx, spec):
 
 
 S_TOL = {"fp64": 1e-12, "tf32": 5e-3, "bf16x3": 1e-4}
+# element by element, relative to the largest |S|: one wrong element among
+# many would pass a norm bound but not this one
+S_TOL_MAX = {"fp64": 1e-12, "tf32": 1e-2, "bf16x3": 3e-4}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
@@ -136,8 +139,9 @@ def test_s_kernel_matches_oracle_terms(ctx, which, prec):
     r1, r2 = fc.S1(prob, t1, t2), fc.S2(prob, t1, t2)
     assert rel(s1, r1) < S_TOL[prec]
     assert rel(s2, r2) < S_TOL[prec]
-    if prec == "fp64":
-        assert torch.max(torch.abs(s2.cpu() - r2)).item() < 1e-12 * torch.max(torch.abs(r2)).item()
+    for got, ref in ((s1, r1), (s2, r2)):
+        err = torch.max(torch.abs(got.cpu() - ref)).item()
+        assert err < S_TOL_MAX[prec] * torch.max(torch.abs(ref)).item(), (prec, err)
 
 
 @pytest.mark.parametrize("slots", ["ia", "ijab"])
@@ -226,7 +230,9 @@ def test_streamed_tau_matches_full_sweep(ctx, prec, chunk):
     """stream_tau keeps S for one tau chunk and carries the Simpson chain
     state between chunks; every iterate equals the unstreamed one.  (In TF32
     the reference runs the S kernel on the same chunks, since other GEMM
-    shapes round differently.)"""
+    shapes round differently, and the chain values carried between chunks
+    are stored in FP32 while the unstreamed recurrence keeps them in FP64
+    registers: a few 1e-8 Ha after six iterations.)"""
     c = wl.HUBBARD_6
     ctx.build_hubbard(c["L"], c["t"], c["U"])
     ref = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=0, max_iter=6,
@@ -234,7 +240,7 @@ def test_streamed_tau_matches_full_sweep(ctx, prec, chunk):
     got = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision=prec, refine_max_iter=0, max_iter=6,
                     allow_unconverged=True, stream_tau=1, tau_chunk=chunk)
     assert got["iterations"] == ref["iterations"]
-    assert abs(got["omega"] - ref["omega"]) < (1e-13 if prec == "fp64" else 1e-9)
+    assert abs(got["omega"] - ref["omega"]) < (1e-13 if prec == "fp64" else 1e-7)
     if prec == "fp64":
         full = ctx.solve(c["beta"], c["mu"], c["ngrid"], precision="fp64", tol_omega=1e-12, tol_amp=1e-10,
                          stream_tau=1, tau_chunk=chunk)
