@@ -373,16 +373,34 @@ def run_gpu(args, rank, world):
     ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
     mu = gold["mu"] if gold else ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
     opts = dict(precision=prec, refine_max_iter=0, tau_chunk=8, max_iter=80)
-    # a solve to convergence (untimed by events, host-timed between synchronisations)
+    # a solve to convergence (host-timed between synchronisations), in tau
+    # chunks of 2 so that the adjoint that follows fits beside it
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sol = ctx.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **opts)
+    sol = ctx.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, mixed_adjoint=1,
+                    **dict(opts, tau_chunk=2))
     torch.cuda.synchronize()
     t_sol = time.perf_counter() - t0
     solve = {"s_total": t_sol, "iterations": sol["iterations"], "polish_iterations": sol["polish_iterations"],
              "fp64_iterations": sol["refine_iterations"], "converged": bool(sol["converged"]),
              "omega": sol["omega"], "abs_dOmega_vs_oracle": abs(sol["omega"] - gold["omega"]) if gold else None,
              "oracle": "block-sparse oracle, converged to |dOmega_CC| < 1e-11" if gold else None}
+    # the response of that solve: the lambda sweep in the mixed arithmetic
+    # (FP32 multipliers, BF16X3 VJP), N, E, S against the oracle's central
+    # differences of converged solves
+    adjoint = None
+    if not args.no_adjoint and sol["converged"]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ad, _ = ctx.adjoint(with_rdm1=False)
+        torch.cuda.synchronize()
+        adjoint = {"s_total": time.perf_counter() - t0, "lambda_iterations": ad["iterations"],
+                   "N": ad["N"], "E": ad["E"], "S": ad["S"], "dOmega_dbeta": ad["dOmega_dbeta"]}
+        rp = os.path.join(GOLD, "oracle_ueg57_response.json")
+        if os.path.exists(rp):
+            gr = json.load(open(rp))
+            adjoint["abs_diff_vs_oracle"] = {k: abs(ad[k] - gr[k]) for k in ("N", "E", "S")}
+            adjoint["oracle"] = gr["how"]
 
     # timed steps: W warm-up iterations, then K iterations each bracketed by
     # CUDA events on the library stream; the amplitudes (21 GB) and integral
@@ -501,6 +519,7 @@ def run_gpu(args, rank, world):
                 "tensor_tflops_per_iteration": fl / s_per_iter / 1e12,
                 "algorithmic_flops_per_iteration": fl,
                 "time_to_1e-6": solve,
+                "adjoint_mixed": adjoint,
                 "fp64_gpu": fp64,
                 "mixed_over_fp64_time_to_solution": (fp64["estimated_s_to_solution"] / t_sol
                                                      if fp64 and "estimated_s_to_solution" in fp64 else None),
@@ -743,6 +762,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ueg81", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the lambda sweep of the headline workload")
     ap.add_argument("--quick", action="store_true", help="headline only, no extra workloads")
     ap.add_argument("--c3-iterations", action="store_true",
                     help="prepare the headline workload and run W + K iterations (profiler launch lists)")

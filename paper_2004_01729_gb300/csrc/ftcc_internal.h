@@ -95,6 +95,19 @@ struct PackDesc {
 // stride of 0 broadcasts along that letter.  Both launchers run the tiled
 // permute kernel (shared-memory tiles, coalesced reads and writes; each term
 // read in its own letter order).
+// Contiguous-block copy (see launch_block_copy): the destination's leading
+// letters (dim, outermost first) with the source strides of those letters (0
+// where the source lacks one).
+struct BlockCopyDesc {
+  int nouter;
+  long long dim[kMaxL], sst[kMaxL];
+};
+template <class T>
+cudaError_t launch_block_copy(T* dst, const T* src, long long B, const BlockCopyDesc& d, double alpha, double beta,
+                              cudaStream_t st);
+// hi / lo bf16 halves of rows already in GEMM order (row strides sld, ld).
+cudaError_t launch_split_rows(const float* src, long long sld, void* hi, void* lo, long long ld, long long rows,
+                              long long K, cudaStream_t st);
 struct ScatDesc {
   int nd;
   long long dim[kMaxL], sst[kMaxL];

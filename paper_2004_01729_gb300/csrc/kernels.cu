@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kPermThreads, VW == 1 ? 5 : 4) permute_kernel(
 #pragma unroll
   for (int k = 0; k < kMaxL; ++k)
     if (k < d.nd) dbase += c[k] * d.dstr[k];
-  if constexpr (SPLIT) {
+  if constexpr (SPLIT && VW == 1) {
     __nv_bfloat16* hi = out.hi + dbase;
     __nv_bfloat16* lo = out.lo + dbase;
     perm_rows<kPermTerms, T>(d, tailmask, n, rowG, rowT, [&](long long, int t) { return tile[t]; },
@@ -239,6 +239,40 @@ __global__ void __launch_bounds__(kPermThreads, VW == 1 ? 5 : 4) permute_kernel(
                       hi[g] = h;
                       lo[g] = __float2bfloat16_rn(v - __bfloat162float(h));
                     });
+  } else if constexpr (SPLIT) {
+    // VW = 4 floats of the tile become four bf16 hi and four bf16 lo halves,
+    // each stored as one 8-byte access
+    static_assert(VW == 4 && sizeof(T) == 4, "vector split of FP32 tiles");
+    __nv_bfloat16* hi = out.hi + dbase;
+    __nv_bfloat16* lo = out.lo + dbase;
+    using V = PermVec<T, VW>;
+    const int tf = d.tstr[kPermTerms][0];
+    perm_rows<kPermTerms, V, VW>(
+        d, tailmask, n, rowG, rowT,
+        [&](long long, int t) {
+          V v;
+#pragma unroll
+          for (int w = 0; w < VW; ++w) v.x[w] = tile[t + w * tf];
+          return v;
+        },
+        [&](long long g, int, const V& v) {
+          __nv_bfloat162 h2[2], l2[2];
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            const float a = static_cast<float>(v.x[2 * w]), b = static_cast<float>(v.x[2 * w + 1]);
+            const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+            h2[w] = __halves2bfloat162(ha, hb);
+            l2[w] = __halves2bfloat162(__float2bfloat16_rn(a - __bfloat162float(ha)),
+                                       __float2bfloat16_rn(b - __bfloat162float(hb)));
+          }
+          uint2 uh, ul;
+          uh.x = *reinterpret_cast<const uint32_t*>(&h2[0]);
+          uh.y = *reinterpret_cast<const uint32_t*>(&h2[1]);
+          ul.x = *reinterpret_cast<const uint32_t*>(&l2[0]);
+          ul.y = *reinterpret_cast<const uint32_t*>(&l2[1]);
+          *reinterpret_cast<uint2*>(hi + g) = uh;
+          *reinterpret_cast<uint2*>(lo + g) = ul;
+        });
   } else {
     T* dp = out.dst + dbase;
     using V = PermVec<T, VW>;
@@ -1408,7 +1442,10 @@ cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double
   // width, every other stride and every block's base offset is a multiple
   // of it, and the tensors start on 16-byte boundaries
   constexpr int kVW = 16 / sizeof(T);
-  bool vec = !SPLIT && reinterpret_cast<uintptr_t>(out.dst) % 16 == 0;
+  // (a split writes VW bf16 halves: 8-byte aligned hi and lo arrays)
+  bool vec = SPLIT ? (sizeof(T) == 4 && reinterpret_cast<uintptr_t>(out.hi) % 8 == 0 &&
+                      reinterpret_cast<uintptr_t>(out.lo) % 8 == 0)
+                   : reinterpret_cast<uintptr_t>(out.dst) % 16 == 0;
   for (int o = 0; o <= P.nterm && vec; ++o) {
     const int oo = o == P.nterm ? kPermTerms : o;
     const int l0 = d.slot[oo][0];
@@ -1423,7 +1460,8 @@ cudaError_t run_permute(const PermPlan& P0, PermOut<T> out, double alpha, double
     d.block0 = static_cast<uint32_t>(b0);
     const unsigned int g = static_cast<unsigned int>(std::min<unsigned long long>(nblocks - b0, 0x7FFFFFFFull));
     if (vec)
-      permute_kernel<T, false, kVW><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
+      permute_kernel<T, SPLIT && sizeof(T) == 4, kVW><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha),
+                                                                                     static_cast<T>(beta));
     else
       permute_kernel<T, SPLIT, 1><<<g, kPermThreads, smem, st>>>(out, d, static_cast<T>(alpha), static_cast<T>(beta));
   }
@@ -1461,6 +1499,122 @@ cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st
 }
 template cudaError_t launch_pack<float>(const float*, float*, const PackDesc&, cudaStream_t);
 template cudaError_t launch_pack<double>(const double*, double*, const PackDesc&, cudaStream_t);
+
+// ---- fast paths of the layout engine for contiguous rows
+// hi/lo halves of rows already in GEMM order: src[r][k] (row stride sld) ->
+// hi[r][k], lo[r][k] (row stride ld), k < K.  With K, sld and ld multiples of
+// four (and aligned bases) a thread moves four floats in one 16-byte load and
+// four bf16 halves in one 8-byte store each.
+template <bool VEC>
+__global__ void split_rows_kernel(const float* __restrict__ src, long long sld, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, long long ld, long long rows, long long K) {
+  const long long per = VEC ? K / 4 : K;
+  const long long total = rows * per;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = e / per, c = e - r * per;
+    if constexpr (VEC) {
+      const float4 v = *reinterpret_cast<const float4*>(src + r * sld + 4 * c);
+      const float x[4] = {v.x, v.y, v.z, v.w};
+      __nv_bfloat162 h2[2], l2[2];
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const __nv_bfloat16 ha = __float2bfloat16_rn(x[2 * w]), hb = __float2bfloat16_rn(x[2 * w + 1]);
+        h2[w] = __halves2bfloat162(ha, hb);
+        l2[w] = __halves2bfloat162(__float2bfloat16_rn(x[2 * w] - __bfloat162float(ha)),
+                                   __float2bfloat16_rn(x[2 * w + 1] - __bfloat162float(hb)));
+      }
+      uint2 uh, ul;
+      uh.x = *reinterpret_cast<const uint32_t*>(&h2[0]);
+      uh.y = *reinterpret_cast<const uint32_t*>(&h2[1]);
+      ul.x = *reinterpret_cast<const uint32_t*>(&l2[0]);
+      ul.y = *reinterpret_cast<const uint32_t*>(&l2[1]);
+      *reinterpret_cast<uint2*>(hi + r * ld + 4 * c) = uh;
+      *reinterpret_cast<uint2*>(lo + r * ld + 4 * c) = ul;
+    } else {
+      const float v = src[r * sld + c];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[r * ld + c] = h;
+      lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+cudaError_t launch_split_rows(const float* src, long long sld, void* hi, void* lo, long long ld, long long rows,
+                              long long K, cudaStream_t st) {
+  if (rows <= 0 || K <= 0) return cudaSuccess;
+  if (sld < K || ld < K) return cudaErrorInvalidValue;
+  const bool vec = K % 4 == 0 && sld % 4 == 0 && ld % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(hi) % 8 == 0 && reinterpret_cast<uintptr_t>(lo) % 8 == 0;
+  const long long work = vec ? rows * (K / 4) : rows * K;
+  const int blocks = static_cast<int>(std::min<long long>((work + 255) / 256, 152LL * 16));
+  if (vec)
+    split_rows_kernel<true><<<blocks, 256, 0, st>>>(src, sld, static_cast<__nv_bfloat16*>(hi),
+                                                    static_cast<__nv_bfloat16*>(lo), ld, rows, K);
+  else
+    split_rows_kernel<false><<<blocks, 256, 0, st>>>(src, sld, static_cast<__nv_bfloat16*>(hi),
+                                                     static_cast<__nv_bfloat16*>(lo), ld, rows, K);
+  return cudaGetLastError();
+}
+
+// dst[o][q] = beta * dst[o][q] + alpha * src[soff(o) + q] for a destination
+// whose last letters form one contiguous block of B elements that the
+// source holds in the same order: o runs over the destination's leading
+// letters (blockIdx.y), soff(o) = sum_k c_k(o) * sst_k with sst_k = 0 for a
+// letter the source lacks (broadcast).  VW elements per access.
+template <class T, int VW>
+__global__ void block_copy_kernel(T* __restrict__ dst, const T* __restrict__ src, long long B, BlockCopyDesc d,
+                                  T alpha, T beta) {
+  long long o = blockIdx.y, soff = 0;
+#pragma unroll
+  for (int k = kMaxL - 1; k >= 0; --k) {
+    if (k < d.nouter) {
+      const long long c = o % d.dim[k];
+      o /= d.dim[k];
+      soff += c * d.sst[k];
+    }
+  }
+  T* dp = dst + static_cast<long long>(blockIdx.y) * B;
+  const T* sp = src + soff;
+  const long long nv = B / VW;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < nv;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    PermVec<T, VW> v = vload<T, VW>(sp + e * VW);
+    if (beta != T(0)) {
+      const PermVec<T, VW> old = vload<T, VW>(dp + e * VW);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) v.x[w] = alpha * v.x[w] + beta * old.x[w];
+    } else {
+#pragma unroll
+      for (int w = 0; w < VW; ++w) v.x[w] = alpha * v.x[w];
+    }
+    vstore<T, VW>(dp + e * VW, v);
+  }
+}
+
+template <class T>
+cudaError_t launch_block_copy(T* dst, const T* src, long long B, const BlockCopyDesc& d, double alpha, double beta,
+                              cudaStream_t st) {
+  long long nout = 1;
+  for (int k = 0; k < d.nouter; ++k) nout *= d.dim[k];
+  if (nout <= 0 || B <= 0) return cudaSuccess;
+  if (nout > 65535 || d.nouter > kMaxL) return cudaErrorInvalidValue;
+  constexpr int kVW = 16 / sizeof(T);
+  bool vec = B % kVW == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+  for (int k = 0; k < d.nouter && vec; ++k) vec = d.sst[k] % kVW == 0;
+  const long long per = vec ? B / kVW : B;
+  const int bx = static_cast<int>(std::min<long long>((per + 255) / 256, std::max<long long>(1, 152LL * 16 / nout)));
+  dim3 grid(bx, static_cast<unsigned>(nout));
+  if (vec)
+    block_copy_kernel<T, kVW><<<grid, 256, 0, st>>>(dst, src, B, d, static_cast<T>(alpha), static_cast<T>(beta));
+  else
+    block_copy_kernel<T, 1><<<grid, 256, 0, st>>>(dst, src, B, d, static_cast<T>(alpha), static_cast<T>(beta));
+  return cudaGetLastError();
+}
+template cudaError_t launch_block_copy<float>(float*, const float*, long long, const BlockCopyDesc&, double, double,
+                                              cudaStream_t);
+template cudaError_t launch_block_copy<double>(double*, const double*, long long, const BlockCopyDesc&, double, double,
+                                               cudaStream_t);
 
 cudaError_t launch_pack_bf16x2(const float* src, void* hi, void* lo, const PackDesc& d, cudaStream_t st) {
   if (d.rows <= 0 || d.creal <= 0) return cudaSuccess;

@@ -300,6 +300,7 @@ struct Solver {
       h_->put(e.b);
     }
     for (auto& kv : fixed_bar) h_->put(kv.second);
+    for (auto& kv : perm_cache) h_->put(kv.second);
     for (auto& r : prof) {
       cudaEventDestroy(r.e0);
       cudaEventDestroy(r.e1);
@@ -343,8 +344,83 @@ struct Solver {
   // dst (letters Ld) = beta * dst + alpha * P(src with letters Ls); letters of
   // dst missing from src are broadcast.  anti names letter pairs of dst to
   // antisymmetrise: "", "ij", "ab" or "ijab".
+  // Fixed (integral or Fock) blocks stored again in another letter order for
+  // the broadcast copies of the S kernel (at most kPermCacheBytes in all).
+  static constexpr size_t kPermCacheBytes = size_t(4) << 30;
+  std::map<std::pair<const void*, std::string>, Buf> perm_cache;
+  size_t perm_cache_bytes = 0;
+
+  // dst = beta dst + alpha src when dst's trailing letters form one block
+  // that src holds contiguously in the same order (its other letters leading
+  // in dst, the ones src lacks broadcast): one vectorised copy per leading
+  // index.  False when the layouts do not have that form.
+  bool block_copy(T* dst, const char* Ld, const T* src, const char* Ls, double alpha, double beta) {
+    const int nd = static_cast<int>(strlen(Ld)), ns = static_cast<int>(strlen(Ls));
+    int k = 0;
+    while (k < nd && k < ns && Ld[nd - 1 - k] == Ls[ns - 1 - k]) ++k;
+    if (k == 0 || nd - k > kMaxL) return false;
+    long long B = 1;
+    for (int q = nd - k; q < nd; ++q) B *= dimof(Ld[q]);
+    BlockCopyDesc bd{};
+    bd.nouter = nd - k;
+    const auto ss = strides_of(Ls);
+    int found = 0;
+    long long nout = 1;
+    for (int q = 0; q < bd.nouter; ++q) {
+      bd.dim[q] = dimof(Ld[q]);
+      nout *= bd.dim[q];
+      const char* f = strchr(Ls, Ld[q]);
+      if (f) {
+        if (f - Ls >= ns - k) return false;
+        bd.sst[q] = ss[f - Ls];
+        ++found;
+      } else {
+        bd.sst[q] = 0;
+      }
+    }
+    if (found != ns - k || nout > 65535 || B < 1024) return false;
+    const double reads = 1.0 + (beta != 0.0 ? 1.0 : 0.0);
+    timed_launch(kClsScatter, static_cast<double>(nout) * B * (reads + 1) * sizeof(T), 0.0,
+                 [&] { CU(launch_block_copy<T>(dst, src, B, bd, alpha, beta, st())); });
+    return true;
+  }
+
   void scatter(T* dst, const char* Ld, const T* src, const char* Ls, double alpha, double beta, const char* anti) {
     if (recording) tape.push_back(Op{1, dst, Ld, src, Ls, nullptr, "", nullptr, alpha, beta, anti});
+    if (!*anti) {
+      if (block_copy(dst, Ld, src, Ls, alpha, beta)) return;
+      // a fixed block broadcast in another order: copy it once into dst's
+      // order (without the broadcast letters), then block copies
+      if (is_fixed(src)) {
+        std::string Lt;
+        for (const char* q = Ld; *q; ++q)
+          if (strchr(Ls, *q)) Lt += *q;
+        if (Lt.size() == strlen(Ls)) {
+          const auto key = std::make_pair(static_cast<const void*>(src), Lt);
+          auto it = perm_cache.find(key);
+          long long n = 1;
+          for (const char* q = Ls; *q; ++q) n *= dimof(*q);
+          const size_t bytes = static_cast<size_t>(n) * sizeof(T);
+          if (it == perm_cache.end() && perm_cache_bytes + bytes <= kPermCacheBytes) {
+            Buf b;
+            ensure(h_, b, bytes);
+            scatter_permute(static_cast<T*>(b.p), Lt.c_str(), src, Ls, 1.0, 0.0, "");
+            perm_cache_bytes += bytes;
+            it = perm_cache.emplace(key, b).first;
+          }
+          if (it != perm_cache.end() &&
+              block_copy(dst, Ld, static_cast<const T*>(it->second.p), Lt.c_str(), alpha, beta))
+            return;
+        }
+      }
+    }
+    scatter_permute(dst, Ld, src, Ls, alpha, beta, anti);
+  }
+
+  // the general case: the tiled permute kernel (any letter orders, the
+  // antisymmetriser, broadcast letters); not recorded on the tape
+  void scatter_permute(T* dst, const char* Ld, const T* src, const char* Ls, double alpha, double beta,
+                       const char* anti) {
     ScatDesc d{};
     d.nd = static_cast<int>(strlen(Ld));
     auto ss = strides_of(Ls);
@@ -389,6 +465,17 @@ struct Solver {
     }
     d.cpad = cpad;
     const double pbytes = static_cast<double>(d.rows) * (d.creal * sizeof(T) + d.cpad * (hi ? 4 : sizeof(T)));
+    // rows already in GEMM order: a row split (bf16 halves) or a pitched copy
+    if (rows + cols == std::string(Ls)) {
+      timed_launch(kClsPack, pbytes, 0.0, [&] {
+        if (hi)
+          CU(launch_split_rows(reinterpret_cast<const float*>(src), d.creal, hi, lo, d.cpad, d.rows, d.creal, st()));
+        else
+          CU(cudaMemcpy2DAsync(dst, d.cpad * sizeof(T), src, d.creal * sizeof(T), d.creal * sizeof(T), d.rows,
+                               cudaMemcpyDeviceToDevice, st()));
+      });
+      return;
+    }
     timed_launch(kClsPack, pbytes, 0.0, [&] {
       if (hi) {
         CU(launch_pack_bf16x2(reinterpret_cast<const float*>(src), hi, lo, d, st()));
