@@ -380,7 +380,13 @@ ftcc_status ftcc_get_lambda(ftcc_ctx* ctx, double* m1, double* m2);
  * ft_ccsd_solve accumulate, per kernel class, the device time, the number of
  * launches and the algorithmic bytes (elements read and written once each)
  * and flops of those launches.  Enabling or disabling resets the sums.
- * ftcc_profile_read fills up to max entries and returns how many. */
+ * ftcc_profile_read fills up to max entries and returns how many.  Classes:
+ * "gemm_tc_kernel" (tensor-core contractions), "gemm_simt_kernel" (FP64 and
+ * skinny contractions), "layout:pack" (operand packs: permutes, bf16 hi/lo
+ * splits, packs over unordered index pairs), "layout:scatter" (GEMM outputs
+ * into the intermediates' layouts, block copies, the unpacking of pair-packed
+ * results, the P(ij)P(ab) assembly of S2), "propagate_kernel" (Eq. smu and
+ * the energy sums), "other" (tau, the remaining elementwise kernels). */
 typedef struct {
   char name[32];
   long long launches;

@@ -95,6 +95,15 @@ struct PackDesc {
 // stride of 0 broadcasts along that letter.  Both launchers run the tiled
 // permute kernel (shared-memory tiles, coalesced reads and writes; each term
 // read in its own letter order).
+// Unordered pairs (p < q) of antisymmetric tensors: pack [b][P][Q] from a
+// strided four-index tensor (optionally antisymmetrising the first pair), and
+// add the dense antisymmetric tensor of a packed [b][P_ij][P_ab] one.
+template <class T>
+cudaError_t launch_pair_pack(const T* src, T* dst, long long nb, long long sb, const int2* pairs1, long long np1,
+                             const int2* pairs2, long long np2, long long s0, long long s1, long long s2, long long s3,
+                             int anti, double coef, cudaStream_t st);
+template <class T>
+cudaError_t launch_pair_unpack_add(T* R, const T* L, long long nb, int no, int nv, double coef, cudaStream_t st);
 // Contiguous-block copy (see launch_block_copy): the destination's leading
 // letters (dim, outermost first) with the source strides of those letters (0
 // where the source lacks one).

@@ -1500,6 +1500,94 @@ cudaError_t launch_pack(const T* src, T* dst, const PackDesc& d, cudaStream_t st
 template cudaError_t launch_pack<float>(const float*, float*, const PackDesc&, cudaStream_t);
 template cudaError_t launch_pack<double>(const double*, double*, const PackDesc&, cudaStream_t);
 
+// ---- unordered index pairs (p < q) of antisymmetric tensors
+// pair index of (p, q), p < q, among the n(n-1)/2 pairs in row order
+__device__ __forceinline__ long long pair_index(int p, int q, int n) {
+  return static_cast<long long>(p) * n - static_cast<long long>(p) * (p + 1) / 2 + (q - p - 1);
+}
+
+// dst[b][P][Q] = coef * X(l0, l1, l2, l3) over pairs P = (l0 < l1) of n1
+// and Q = (l2 < l3) of n2, X read through the strides s0..s3 (sb per batch
+// entry); with anti the first pair is antisymmetrised on the way,
+// X -> (X(l0, l1, ..) - X(l1, l0, ..)) / 2.  pairs1 / pairs2 hold the
+// (p, q) of every pair index.
+template <class T>
+__global__ void pair_pack_kernel(const T* __restrict__ src, T* __restrict__ dst, long long nb, long long sb,
+                                 const int2* __restrict__ pairs1, long long np1, const int2* __restrict__ pairs2,
+                                 long long np2, long long s0, long long s1, long long s2, long long s3, int anti,
+                                 T coef) {
+  const long long total = nb * np1 * np2;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long q = e % np2;
+    const long long r = e / np2;
+    const long long p = r % np1;
+    const long long b = r / np1;
+    const int2 a = pairs1[p], c = pairs2[q];
+    const T* x = src + b * sb + c.x * s2 + c.y * s3;
+    T v = x[a.x * s0 + a.y * s1];
+    if (anti) v = T(0.5) * (v - x[a.y * s0 + a.x * s1]);
+    dst[e] = coef * v;
+  }
+}
+
+// R[b][i][j][a][c] += coef * sgn * L[b][pair(i, j)][pair(a, c)] with sgn the
+// sign of the two orderings (zero where i = j or a = c): adds the dense
+// antisymmetric tensor of a pair-packed one.
+template <class T>
+__global__ void pair_unpack_add_kernel(T* __restrict__ R, const T* __restrict__ L, long long nb, int no, int nv,
+                                       T coef) {
+  const long long npo = static_cast<long long>(no) * (no - 1) / 2, npv = static_cast<long long>(nv) * (nv - 1) / 2;
+  const long long per = static_cast<long long>(no) * no * nv * nv;
+  const long long total = nb * per;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    long long r = e;
+    const int c = static_cast<int>(r % nv);
+    r /= nv;
+    const int a = static_cast<int>(r % nv);
+    r /= nv;
+    const int j = static_cast<int>(r % no);
+    r /= no;
+    const int i = static_cast<int>(r % no);
+    const long long b = r / no;
+    if (i == j || a == c) continue;
+    const long long P = i < j ? pair_index(i, j, no) : pair_index(j, i, no);
+    const long long Q = a < c ? pair_index(a, c, nv) : pair_index(c, a, nv);
+    const T v = L[(b * npo + P) * npv + Q];
+    R[e] += ((i < j) == (a < c)) ? coef * v : -coef * v;
+  }
+}
+
+template <class T>
+cudaError_t launch_pair_pack(const T* src, T* dst, long long nb, long long sb, const int2* pairs1, long long np1,
+                             const int2* pairs2, long long np2, long long s0, long long s1, long long s2, long long s3,
+                             int anti, double coef, cudaStream_t st) {
+  const long long total = nb * np1 * np2;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 16));
+  pair_pack_kernel<T><<<blocks, 256, 0, st>>>(src, dst, nb, sb, pairs1, np1, pairs2, np2, s0, s1, s2, s3, anti,
+                                              static_cast<T>(coef));
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pair_unpack_add(T* R, const T* L, long long nb, int no, int nv, double coef, cudaStream_t st) {
+  const long long total = nb * static_cast<long long>(no) * no * nv * nv;
+  if (total <= 0 || no < 2 || nv < 2) return cudaSuccess;
+  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 16));
+  pair_unpack_add_kernel<T><<<blocks, 256, 0, st>>>(R, L, nb, no, nv, static_cast<T>(coef));
+  return cudaGetLastError();
+}
+template cudaError_t launch_pair_pack<float>(const float*, float*, long long, long long, const int2*, long long,
+                                             const int2*, long long, long long, long long, long long, long long, int,
+                                             double, cudaStream_t);
+template cudaError_t launch_pair_pack<double>(const double*, double*, long long, long long, const int2*, long long,
+                                              const int2*, long long, long long, long long, long long, long long, int,
+                                              double, cudaStream_t);
+template cudaError_t launch_pair_unpack_add<float>(float*, const float*, long long, int, int, double, cudaStream_t);
+template cudaError_t launch_pair_unpack_add<double>(double*, const double*, long long, int, int, double, cudaStream_t);
+
 // ---- fast paths of the layout engine for contiguous rows
 // hi/lo halves of rows already in GEMM order: src[r][k] (row stride sld) ->
 // hi[r][k], lo[r][k] (row stride ld), k < K.  With K, sld and ld multiples of

@@ -176,7 +176,7 @@ constexpr int kStateStride = 8 + 256;
 
 // kernel classes of the per-iteration timing
 enum { kClsScatter = 0, kClsPack, kClsGemmTc, kClsGemmSimt, kClsPropagate, kClsOther, kNumCls };
-const char* const kClsName[kNumCls] = {"permute_kernel:scatter", "permute_kernel:pack", "gemm_tc_kernel",
+const char* const kClsName[kNumCls] = {"layout:scatter", "layout:pack", "gemm_tc_kernel",
                                        "gemm_simt_kernel", "propagate_kernel", "other"};
 
 template <class T>
@@ -191,6 +191,9 @@ struct Solver {
   std::map<std::string, Buf> Vb, Fb;
   Buf t1, t2, S1, S2;
   Buf tt, ta, X, Wmnij, Wabef, Wmbej, Fae, Fmi, Fme, Ft, Ft2, Y, R, R2;
+  // the ladders over unordered pairs: tau, W_mnij, W_abef and their result
+  // packed [zx][pair][pair], <mn||ef> packed once, and the pair tables
+  Buf tp, WAmn, WAef, Lp, Vp, pairsO, pairsV;
   Buf pA, pB, pA2, pB2, Ct, skw;
   std::map<PackKey, std::pair<Buf, Buf>> packed;   // cached packs of fixed operands
   Buf part1, part2;
@@ -291,7 +294,7 @@ struct Solver {
       h_->put(kv.second.second);
     }
     Buf* bs[] = {&t1, &t2, &S1, &S2, &ch1, &ch2, &tt, &ta, &X, &Wmnij, &Wabef, &Wmbej, &Fae, &Fmi, &Fme, &Ft, &Ft2, &Y,
-                 &R, &R2, &bR, &bR2, &tuneC,
+                 &R, &R2, &bR, &bR2, &tuneC, &tp, &WAmn, &WAef, &Lp, &Vp, &pairsO, &pairsV,
                  &pA, &pB, &pA2, &pB2, &Ct, &skw, &part1, &part2, &btt, &bta, &bX, &bWmnij, &bWabef, &bWmbej,
                  &bY, &bFae, &bFmi, &bFme, &bFt, &bFt2, &bD, &bP, &bQ, &ones, &sx1, &sx2};
     for (Buf* q : bs) h_->put(*q);
@@ -311,6 +314,9 @@ struct Solver {
   long long dimof(char ch) const {
     if (ch == 'z') return nz;
     if (ch == 'x') return nx;
+    // unordered pairs (p < q) of hole-like (I, J) and particle-like (A, E) letters
+    if (ch == 'I' || ch == 'J') return static_cast<long long>(no) * (no - 1) / 2;
+    if (ch == 'A' || ch == 'E') return static_cast<long long>(nv) * (nv - 1) / 2;
     if (is_hole(ch)) return no;
     return nv;
   }
@@ -810,6 +816,39 @@ struct Solver {
     ensure(h_, Ft2, x * o * o * sizeof(T));
     ensure(h_, R, x * o * o * v * v * sizeof(T));
     ensure(h_, R2, x * o * o * v * v * sizeof(T));
+    const long long po = o * (o - 1) / 2, pv = v * (v - 1) / 2;
+    ensure(h_, tp, std::max(1LL, x * po * pv) * sizeof(T));
+    ensure(h_, WAmn, std::max(1LL, x * po * po) * sizeof(T));
+    ensure(h_, WAef, std::max(1LL, x * pv * pv) * sizeof(T));
+    ensure(h_, Lp, std::max(1LL, x * po * pv) * sizeof(T));
+    if (!pairsO.p) {
+      auto table = [&](Buf& b, long long n) {
+        std::vector<int2> t;
+        for (int p = 0; p < n; ++p)
+          for (int q = p + 1; q < n; ++q) t.push_back(make_int2(p, q));
+        ensure(h_, b, std::max<size_t>(1, t.size()) * sizeof(int2));
+        if (!t.empty()) {
+          CU(cudaMemcpyAsync(b.p, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, st()));
+          CU(cudaStreamSynchronize(st()));
+        }
+      };
+      table(pairsO, o);
+      table(pairsV, v);
+    }
+  }
+
+  // dst[zx][P][Q] from a dense [zx][l0][l1][l2][l3] (dims d0 = d1, d2 = d3;
+  // P over pairs of l0 < l1, Q over l2 < l3), the first pair antisymmetrised
+  // on the way when anti
+  void pair_pack(const T* src, T* dst, long long nb, bool first_hole, bool second_hole, bool anti) {
+    const long long n1 = first_hole ? no : nv, n2 = second_hole ? no : nv;
+    const long long np1 = n1 * (n1 - 1) / 2, np2 = n2 * (n2 - 1) / 2;
+    const long long s3 = 1, s2 = n2, s1 = n2 * n2, s0 = n1 * n2 * n2, sb = n1 * n1 * n2 * n2;
+    timed_launch(kClsPack, static_cast<double>(nb) * (sb + np1 * np2) * sizeof(T), 0.0, [&] {
+      CU(launch_pair_pack<T>(src, dst, nb, sb, static_cast<const int2*>((first_hole ? pairsO : pairsV).p), np1,
+                             static_cast<const int2*>((second_hole ? pairsO : pairsV).p), np2, s0, s1, s2, s3,
+                             anti ? 1 : 0, 1.0, st()));
+    });
   }
 
   // S kernel for nx tau slices of every instance (Eqs. ccS1 and ccS2
@@ -859,7 +898,11 @@ struct Solver {
     // W'_mnij = <mn||ij> - 2 s_i^e <mn||je> + 1/2 ta_ij^ef <mn||ef>, stored [ij][mn]   [o^4 v^2]
     scatter(pWmnij, "zxijmn", V("zmnij"), "zmnij", 1.0, 0.0, "");
     contract({pWmnij, "zxijmn"}, -2.0, CT{t1c, "zxie"}, CV("zmnje"));
-    contract({pWmnij, "zxijmn"}, 0.5, CT{pta, "zxijef"}, CV("zmnef"));
+    // Outside the recorded (adjoint) pass the tau <mn||ef> term and both
+    // ladders run over unordered pairs (below); the recorded pass keeps the
+    // dense contractions, whose transposes the tape replays.
+    const bool pairs = !recording && no >= 2 && nv >= 2;
+    if (!pairs) contract({pWmnij, "zxijmn"}, 0.5, CT{pta, "zxijef"}, CV("zmnef"));
     // W'_abef = <ab||ef> - 2 s_m^a <mb||ef>
     scatter(pWabef, "zxabef", V("zabef"), "zabef", 1.0, 0.0, "");
     contract({pWabef, "zxabef"}, -2.0, CT{t1c, "zxma"}, CV("zmbef"));
@@ -885,8 +928,34 @@ struct Solver {
     // R1 [ij][ab]
     contract({pR, "zxijab"}, 0.5, CT{t2c, "zxijae"}, CT{pFt, "zxbe"}, "", 0.0);        // P(ab) s_ij^ae Ft_be
     contract({pR, "zxijab"}, 0.5, CT{pFt2, "zxmi"}, CT{t2c, "zxjmab"});                // -P(ij) s_im^ab Ft2_mj, i<->j
-    contract({pR, "zxijab"}, 0.125, CT{pWmnij, "zxijmn"}, CT{pta, "zxmnab"});           // hole ladder
-    contract({pR, "zxijab"}, 0.125, CT{pta, "zxijef"}, CT{pWabef, "zxabef"});           // particle ladder
+    if (!pairs) {
+      contract({pR, "zxijab"}, 0.125, CT{pWmnij, "zxijmn"}, CT{pta, "zxmnab"});         // hole ladder
+      contract({pR, "zxijab"}, 0.125, CT{pta, "zxijef"}, CT{pWabef, "zxabef"});         // particle ladder
+    } else {
+      // W^A_ijmn = (W'_ijmn - W'_jimn)/2 + sum_{e<f} tau_ij^ef <mn||ef> and
+      // W^A_abef = (W'_abef - W'_baef)/2 are fully antisymmetric and give
+      // P(ij)P(ab) of the two ladders above (the s1 terms of W' become their
+      // P(ij) / P(ab) forms), i.e. the contribution
+      //   L_ij^ab = sum_{m<n} W^A_ijmn tau_mn^ab + sum_{e<f} tau_ij^ef W^A_abef
+      // to S2, computed for i<j, a<b and added to R as L/4 in every orientation
+      // (R enters S2 through P(ij)P(ab)).  Each product is an eighth of the
+      // dense one.
+      T *ptp = (T*)tp.p, *pWAmn = (T*)WAmn.p, *pWAef = (T*)WAef.p, *pLp = (T*)Lp.p;
+      const long long zx = static_cast<long long>(nz) * nx;
+      if (!Vp.p) {
+        const long long po = static_cast<long long>(no) * (no - 1) / 2, pv = static_cast<long long>(nv) * (nv - 1) / 2;
+        ensure(h_, Vp, std::max(1LL, static_cast<long long>(nz) * po * pv) * sizeof(T));
+        pair_pack(V("zmnef"), static_cast<T*>(Vp.p), nz, true, false, false);
+      }
+      pair_pack(pta, ptp, zx, true, false, false);
+      pair_pack(pWmnij, pWAmn, zx, true, true, true);
+      contract({pWAmn, "zxIJ"}, 1.0, CT{ptp, "zxIE"}, CT{static_cast<const T*>(Vp.p), "zJE", true});
+      pair_pack(pWabef, pWAef, zx, false, false, true);
+      contract({pLp, "zxIA"}, 1.0, CT{pWAmn, "zxIJ"}, CT{ptp, "zxJA"}, "", 0.0);
+      contract({pLp, "zxIA"}, 1.0, CT{ptp, "zxIE"}, CT{pWAef, "zxAE"});
+      timed_launch(kClsScatter, static_cast<double>(zx) * no * no * nv * nv * 2 * sizeof(T), 0.0,
+                   [&] { CU(launch_pair_unpack_add<T>(pR, pLp, zx, no, nv, 0.25, st())); });
+    }
     contract({pR, "zxijab"}, 0.5, CT{t1c, "zxie"}, CV("zabej"));                        // P(ij) s_i^e <ab||ej>
     contract({pR, "zxijab"}, -0.5, CT{t1c, "zxma"}, CV("zmbij"));                       // -P(ab) s_m^a <mb||ij>
     // R2 [ia][jb]

@@ -220,7 +220,7 @@ def test_kernel_profile_leaves_results_unchanged(ctx, graph):
     ctx.profile(False)
     assert timed == plain
     names = {s["name"] for s in stats}
-    assert {"gemm_tc_kernel", "propagate_kernel", "permute_kernel:scatter"} <= names, names
+    assert {"gemm_tc_kernel", "propagate_kernel", "layout:scatter"} <= names, names
     for s in stats:
         assert s["launches"] > 0 and s["ms"] > 0.0
 
