@@ -171,7 +171,22 @@ typedef struct {
  *                       FTCC_ERR_UNSUPPORTED.
  *   autotune   [1]      time the tensor-core tile width (32/64/128/256) and K split
  *                       of each contraction shape once, on the first (uncaptured)
- *                       iteration, and keep the fastest (0 = built-in choice) */
+ *                       iteration, and keep the fastest (0 = built-in choice)
+ *   block_sparse [0]    1: exploit the conserved charge of every spin orbital
+ *                       (crystal momentum and S_z) of the UEG and the k-space
+ *                       Hubbard ring, whose orbitals all carry distinct charges:
+ *                       one-index-pair factors become their diagonals, four-index
+ *                       factors N^3 arrays with the fourth index implied, and
+ *                       the contractions run over charge sectors only.  The same
+ *                       equations and fixed point in FP64, with the work and
+ *                       memory of one iteration cut by about the number of
+ *                       k-points.  Needs precision FP64, a single instance of
+ *                       such a system (FTCC_ERR_INVALID_ARG otherwise), no
+ *                       truncation (trunc_thr removes nothing) and the Simpson
+ *                       integral form; stream_tau is ignored.
+ *                       ftcc_get_amplitudes and ftcc_eval_s convert between
+ *                       the dense layouts and the compressed one; the adjoint
+ *                       returns FTCC_ERR_UNSUPPORTED. */
 typedef struct {
   double tol_omega, tol_amp, damping, trunc_thr;
   int max_iter, precision, refine_max_iter;
@@ -183,6 +198,7 @@ typedef struct {
   int fp64_propagation;
   double tol_refine;
   int mixed_adjoint;
+  int block_sparse;
 } ftcc_options;
 
 typedef struct {

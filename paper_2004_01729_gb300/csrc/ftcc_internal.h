@@ -196,6 +196,9 @@ struct PropArgs {
   // recurrence between launches; it may be null only for y0 = 0, y1 = ng.
   int y0, y1, s_ng;
   void* chain;
+  // block-sparse storage (null: dense): doubles are [i][j][a] with b =
+  // imp[i][j][a] (no = nv = N, holes skipped), singles the diagonal [i]
+  const int16_t* imp;
   int arith64;                   // FP32 storage: 0 = FP32 recurrence and energy sums, 1 = FP32
                                  // recurrence with FP64 energy sums, 2 = FP64 for both
 };
@@ -255,5 +258,58 @@ cudaError_t launch_fock_n(const double* Fb, const double* eri, int N, double* Gn
 template <class T>
 cudaError_t launch_prop_response(const T* S, const T* m, const double* epsz, const PropArgs& a, double* Ee, double* Eb,
                                  cudaStream_t st);
+
+// ---- momentum/spin block-sparse S kernel (sparse.cu), FP64 ----
+// Four-index tensors are N^3 arrays [p0][p1][p2] with q_p0 + q_p1 = q_p2 + q_p3
+// and p3 implied; imp[a][b][c] (int16, N^3) = the orbital of charge
+// q_a + q_b - q_c or -1.  Two-index tensors are their diagonals [p].
+struct SpBlocks {   // thermal integral blocks <pq||rs> of each hole / particle class, N^3 each
+  const double *oovv, *ovvv, *ooov, *oooo, *vvvv, *ovvo, *oovo, *ovov, *vvoo, *vvvo, *ovoo;
+};
+struct SpVecArgs {
+  const double *t1, *t2;
+  const double *fov, *foo, *fvv, *fvo;   // diagonals of the thermal Fock blocks
+  const double *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
+  const int16_t* imp;
+  int n;
+  double *Fme, *Fae, *Fmi, *S1, *Ft, *Ft2;   // [nx][n] each
+};
+// Products of the blocks of one pair-charge sector (see sparse.cu).
+struct SecGemmArgs {
+  const double* A;
+  long long ax;          // slice stride of A
+  const double* B;
+  long long bx;          // slice stride of B (0: fixed)
+  double* C;
+  long long cx;
+  double alpha;
+  int n;
+  int swapB;
+  long long s0, s1, s2, s3;   // output position = p_r s0 + q_r s1 + p_c s2 + q_c s3
+  const int2* ent;       // ordered pairs of every sector, sector by sector
+  const int* kl;         // summed-index list of every sector
+  const int4* sec;       // (entry offset, rows, K offset, K count)
+  const int4* work;      // (sector, row tile start, column tile start, 0)
+};
+cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
+                          double* tp, double* tr, double* xp, cudaStream_t st);
+cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st);
+cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
+                            double* wab, double* wr, cudaStream_t st);
+cudaError_t launch_sp_rinit(const double* t1, const double* t2, const double* Ft, const double* Ft2, const SpBlocks& V,
+                            const int16_t* imp, int n, int nx, double* R, cudaStream_t st);
+cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* imp, int n, int nx, double* S2,
+                         cudaStream_t st);
+cudaError_t launch_sector_gemm(const SecGemmArgs& g, int nwork, int nx, cudaStream_t st);
+int sector_tile();
+cudaError_t launch_sp_thermal_eri(const double* eri, const int16_t* imp, int n, const double* f0, const double* f1,
+                                  const double* f2, const double* f3, double* out, cudaStream_t st);
+cudaError_t launch_sp_swap12(const double* in, int n, double* out, cudaStream_t st);   // out[a][b][c] = in[a][c][b]
+cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, double* out,
+                                   cudaStream_t st);
+cudaError_t launch_sp_compress(const double* d1, const double* d2, const int16_t* imp, int n, int nx, double* s1,
+                               double* s2, cudaStream_t st);
+cudaError_t launch_sp_expand(const double* s1, const double* s2, const int16_t* imp, int n, int nx, double* d1,
+                             double* d2, cudaStream_t st);
 
 }  // namespace ftcc

@@ -729,7 +729,8 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
   const double* em = a.em + static_cast<long long>(z) * a.N;
   const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double* wE = a.wE ? a.wE + static_cast<long long>(z) * size : nullptr;
-  const long long n1 = static_cast<long long>(a.no) * a.nv;
+  const bool sparse = a.imp != nullptr;
+  const long long n1 = sparse ? a.N : static_cast<long long>(a.no) * a.nv;   // singles per tau point
   const T* t1E = a.t1E ? static_cast<const T*>(a.t1E) + static_cast<long long>(z) * ng * n1 : nullptr;
   double* partials = a.partials + static_cast<long long>(z) * a.nblocks * (ng + 2);
   for (int y = y0; y < y1; ++y) eacc[y * kPropThreads + threadIdx.x] = EA(0);
@@ -742,7 +743,23 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long mu = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; mu < size; mu += stride) {
     int i, j = 0, aa, b = 0;
-    {
+    if (sparse) {
+      // [i][j][a] with b implied (a hole of the storage is skipped), or the
+      // diagonal singles [i] (a = i)
+      uint32_t r = static_cast<uint32_t>(mu);
+      if (NS == 4) {
+        uint32_t q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        j = r - q * a.nv;
+        i = q;
+        b = a.imp[mu];
+        if (b < 0) continue;
+      } else {
+        i = aa = static_cast<int>(r);
+      }
+    } else {
       uint32_t r = static_cast<uint32_t>(mu);
       uint32_t q = fdiv(a.fv, r);
       if (NS == 4) {
@@ -796,8 +813,10 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
       sp[k] = in ? sq[k * size] : T(0);
       tp[k] = in ? tq[k * size] : T(0);
     }
-    const T* s1y = t1E ? t1E + y0 * n1 : nullptr;   // singles of this tau point
-    const int oi = i * a.nv + aa, oj = j * a.nv + b;
+    // singles of this tau point; with diagonal singles only a = i (then b = j)
+    // carries the s_i^a s_j^b energy term
+    const T* s1y = (t1E && (!sparse || aa == i)) ? t1E + y0 * n1 : nullptr;
+    const int oi = sparse ? i : i * a.nv + aa, oj = sparse ? j : j * a.nv + b;
     EA* ea = eacc + y0 * kPropThreads + threadIdx.x;
     for (int y = y0; y < y1; ++y) {
       const A sy = static_cast<A>(sp[0]);
@@ -901,10 +920,27 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
   const double* em = a.em + static_cast<long long>(z) * a.N;
   const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double h = a.hz[z];
+  const bool sparse = a.imp != nullptr;
   for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
        mu += static_cast<long long>(gridDim.x) * blockDim.x) {
     int i, j = 0, aa, b = 0;
-    {
+    if (sparse) {
+      // [i][j][a] with b implied (a hole of the storage is skipped), or the
+      // diagonal singles [i] (a = i)
+      uint32_t r = static_cast<uint32_t>(mu);
+      if (NS == 4) {
+        uint32_t q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        j = r - q * a.nv;
+        i = q;
+        b = a.imp[mu];
+        if (b < 0) continue;
+      } else {
+        i = aa = static_cast<int>(r);
+      }
+    } else {
       uint32_t r = static_cast<uint32_t>(mu);
       uint32_t q = fdiv(a.fv, r);
       if (NS == 4) {
@@ -1085,10 +1121,27 @@ __global__ void __launch_bounds__(kPropThreads) prop_response_kernel(const T* __
   const double h = a.hz[z];
   __shared__ double bred[kPropThreads];
   double bsum = 0.0;
+  const bool sparse = a.imp != nullptr;
   for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
        mu += static_cast<long long>(gridDim.x) * blockDim.x) {
     int i, j = 0, aa, b = 0;
-    {
+    if (sparse) {
+      // [i][j][a] with b implied (a hole of the storage is skipped), or the
+      // diagonal singles [i] (a = i)
+      uint32_t r = static_cast<uint32_t>(mu);
+      if (NS == 4) {
+        uint32_t q = fdiv(a.fv, r);
+        aa = r - q * a.nv;
+        r = q;
+        q = fdiv(a.fv, r);
+        j = r - q * a.nv;
+        i = q;
+        b = a.imp[mu];
+        if (b < 0) continue;
+      } else {
+        i = aa = static_cast<int>(r);
+      }
+    } else {
       uint32_t r = static_cast<uint32_t>(mu);
       uint32_t q = fdiv(a.fv, r);
       if (NS == 4) {

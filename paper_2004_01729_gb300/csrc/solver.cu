@@ -15,6 +15,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <unordered_map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -67,6 +68,12 @@ struct ftcc_ctx {
   // that repeated solves in one context take the same launches (and round
   // the same way)
   std::map<std::array<int, 7>, std::pair<int, int>> tuned;
+  // conserved charge of every spin orbital (up to four integer components,
+  // component k taken modulo charge_mod[k] when that is > 0), for systems
+  // whose orbitals all carry distinct charges (UEG: momentum and S_z; k-space
+  // Hubbard ring: crystal momentum mod L and S_z); empty otherwise
+  std::vector<std::array<int, 4>> charge;
+  int charge_mod[4] = {0, 0, 0, 0};
 
   ftcc::Buf get(size_t bytes) {
     ftcc::Buf b;
@@ -142,6 +149,15 @@ struct Inst {
   int conv_iter = -1;
 };
 
+// Charge sectors of ordered orbital pairs (p, q), grouped by q_p + q_q
+// (sum) or q_p - q_q (difference), with the summed-index list of each sector
+// and the tiles of its products (see sector_gemm_kernel).
+struct SecTab {
+  Buf ent, kl, sec, work;
+  int nwork = 0;
+  double flops = 0;   // 2 sum_s rows_s^2 K_s per slice
+};
+
 struct Batch {
   ftcc_ctx* home = nullptr;      // allocator, stream and error flag of the batch
   std::vector<Inst> inst;
@@ -169,15 +185,20 @@ struct Batch {
   bool solved = false;
   bool solved_live = false;   // every live member converged (diverged members are frozen)
   int quad = FTCC_QUAD_SIMPSON;   // integral form (Simpson fixed point) or an RK march of Eq. smud
+  // block-sparse storage (option block_sparse): the implied-index table
+  // imp[a][b][c] (int16, N^3) and the pair-charge sectors
+  bool sparse = false;
+  Buf imp;
+  SecTab ssum, sdiff;
   ~Batch();
 };
 
 constexpr int kStateStride = 8 + 256;
 
 // kernel classes of the per-iteration timing
-enum { kClsScatter = 0, kClsPack, kClsGemmTc, kClsGemmSimt, kClsPropagate, kClsOther, kNumCls };
+enum { kClsScatter = 0, kClsPack, kClsGemmTc, kClsGemmSimt, kClsPropagate, kClsOther, kClsSector, kNumCls };
 const char* const kClsName[kNumCls] = {"layout:scatter", "layout:pack", "gemm_tc_kernel",
-                                       "gemm_simt_kernel", "propagate_kernel", "other"};
+                                       "gemm_simt_kernel", "propagate_kernel", "other", "sector_gemm_kernel"};
 
 template <class T>
 struct Solver {
@@ -185,6 +206,9 @@ struct Solver {
   ftcc_ctx* h_;
   int gk;                  // GEMM_F64 for double; GEMM_TF32 / GEMM_BF16X3 for float
   int nz = 1, no = 0, nv = 0, ng = 0, nxc = 0;   // nxc = tau points per S pass
+  bool sp = false;         // block-sparse storage (FP64 only): singles [N], doubles [N^3] per tau point
+  long long n1() const { return sp ? no : static_cast<long long>(no) * nv; }
+  long long n2() const { return sp ? static_cast<long long>(no) * no * no : static_cast<long long>(no) * no * nv * nv; }
   bool stream = false;                            // S kept per tau chunk, propagation chained
   Buf ch1, ch2;                                   // chain state [5][size] of the singles / doubles
   int nx = 0;              // tau points of the current pass
@@ -837,6 +861,115 @@ struct Solver {
     }
   }
 
+  // Workspaces of the block-sparse S kernel for nxc tau points: the
+  // amplitude-derived operands (ta = tau, tt = tau in [a][b][m] order, Y =
+  // s2 in ring order, X = the W_mbej operand), the intermediates W'_mnij,
+  // W'_abef, W_mbej (ring order) and R, the vector intermediates, and the
+  // <mn||ef> block in the W_mbej operand order.
+  void sparse_alloc() {
+    const long long n = no, n3 = n * n * n, x = nxc;
+    for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R}) ensure(h_, *q, x * n3 * sizeof(T));
+    for (Buf* q : {&Fme, &Fae, &Fmi, &Ft, &Ft2}) ensure(h_, *q, x * n * sizeof(T));
+    ensure(h_, Vp, n3 * sizeof(T));
+    if constexpr (sizeof(T) == 8)
+      CU(launch_sp_swap12(V("zmnef"), no, static_cast<double*>(Vp.p), st()));
+  }
+
+  SpBlocks sp_blocks() {
+    if constexpr (sizeof(T) == 8) {
+      return SpBlocks{V("zmnef"), V("zmbef"), V("zmnie"), V("zmnij"), V("zabef"), V("zmbej"),
+                      V("zmnej"), V("zmaie"), V("zabij"), V("zabej"), V("zmbij")};
+    } else {
+      throw Fail{FTCC_ERR_STATE, "block-sparse storage is FP64"};
+    }
+  }
+
+  void sector_product(const SecTab& tab, const T* A, long long ax, const T* Bm, long long bx, T* C, double alpha,
+                      int swapB, long long s0, long long s1, long long s2, long long s3) {
+    if constexpr (sizeof(T) == 8) {
+      const long long n3 = static_cast<long long>(no) * no * no;
+      SecGemmArgs g{};
+      g.A = A;
+      g.ax = ax;
+      g.B = Bm;
+      g.bx = bx;
+      g.C = C;
+      g.cx = n3;
+      g.alpha = alpha;
+      g.n = no;
+      g.swapB = swapB;
+      g.s0 = s0;
+      g.s1 = s1;
+      g.s2 = s2;
+      g.s3 = s3;
+      g.ent = static_cast<const int2*>(tab.ent.p);
+      g.kl = static_cast<const int*>(tab.kl.p);
+      g.sec = static_cast<const int4*>(tab.sec.p);
+      g.work = static_cast<const int4*>(tab.work.p);
+      if (counting) gemm_flops += static_cast<long long>(tab.flops * nx);
+      timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(T), tab.flops * nx,
+                   [&] { CU(launch_sector_gemm(g, tab.nwork, nx, st())); });
+    }
+  }
+
+  // The block-sparse S kernel: the same terms as s_kernel (Eqs. ccS1/ccS2
+  // through the same intermediates) with s1 and every two-index factor
+  // diagonal and the four-index factors in N^3 storage; the five products
+  // of two four-index factors (W_mnij's tau term, W_mbej's X term, the two
+  // ladders and the ring) run over pair-charge sectors.
+  void sparse_s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
+    if constexpr (sizeof(T) == 8) {
+      nx = nxcur;
+      const int n = no;
+      const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
+      const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
+      double *pta = (double*)ta.p, *ptp = (double*)tt.p, *ptr = (double*)Y.p, *pxp = (double*)X.p,
+             *pw1 = (double*)Wmnij.p, *pwab = (double*)Wabef.p, *pwr = (double*)Wmbej.p, *pR = (double*)R.p;
+      const SpBlocks VB = sp_blocks();
+      const double slice = static_cast<double>(nx) * n3 * sizeof(T);
+      timed_launch(kClsOther, 6 * slice, 0.0,
+                   [&] { CU(launch_sp_amp(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, st())); });
+      SpVecArgs v{};
+      v.t1 = t1c;
+      v.t2 = t2c;
+      v.fov = F("zme");
+      v.foo = F("zmi");
+      v.fvv = F("zae");
+      v.fvo = F("zai");
+      v.Voovv = VB.oovv;
+      v.Vovvv = VB.ovvv;
+      v.Vooov = VB.ooov;
+      v.Vovov = VB.ovov;
+      v.Voovo = VB.oovo;
+      v.imp = imp;
+      v.n = n;
+      v.Fme = (double*)Fme.p;
+      v.Fae = (double*)Fae.p;
+      v.Fmi = (double*)Fmi.p;
+      v.S1 = S1c;
+      v.Ft = (double*)Ft.p;
+      v.Ft2 = (double*)Ft2.p;
+      timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors(v, nx, st())); });
+      timed_launch(kClsScatter, 3 * slice + 6.0 * n3 * sizeof(T), 0.0,
+                   [&] { CU(launch_sp_wbase(t1c, VB, imp, n, nx, pw1, pwab, pwr, st())); });
+      // W'_mnij += 1/2 tau_ij^ef <mn||ef>        rows (i,j) | (m,n) by q_i + q_j, sum over e
+      sector_product(b->ssum, pta, n3, VB.oovv, 0, pw1, 0.5, 0, n2, n, 1, 0);
+      // W_mbej -= X_jn^fb <mn||ef>                rows (j,b) | (m,e) by q_j - q_b, sum over n
+      sector_product(b->sdiff, pxp, n3, static_cast<const double*>(Vp.p), 0, pwr, -1.0, 0, n2, n, 1, 0);
+      timed_launch(kClsScatter, 5 * slice, 0.0, [&] {
+        CU(launch_sp_rinit(t1c, t2c, (double*)Ft.p, (double*)Ft2.p, VB, imp, n, nx, pR, st()));
+      });
+      // hole ladder 1/8 W'_ijmn tau_mn^ab          rows (i,j) | (a,b) by q_i + q_j, sum over m
+      sector_product(b->ssum, pw1, n3, ptp, n3, pR, 0.125, 0, n2, n, 1, 0);
+      // particle ladder 1/8 tau_ij^ef W'_abef      rows (i,j) | (a,b), sum over e
+      sector_product(b->ssum, pta, n3, pwab, n3, pR, 0.125, 0, n2, n, 1, 0);
+      // ring s_im^ae W_mbej                        rows (i,a) | (j,b) by q_i - q_a, sum over m
+      sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
+      timed_launch(kClsScatter, 6 * slice, 0.0,
+                   [&] { CU(launch_sp_s2(pR, VB.vvoo, imp, n, nx, S2c, st())); });
+    }
+  }
+
   // dst[zx][P][Q] from a dense [zx][l0][l1][l2][l3] (dims d0 = d1, d2 = d3;
   // P over pairs of l0 < l1, Q over l2 < l3), the first pair antisymmetrised
   // on the way when anti
@@ -856,6 +989,10 @@ struct Solver {
   // the tau*<mn||ef> part of the particle-ladder intermediate is carried by
   // W_mnij with weight 1/2).  Inputs [z][x][...] with nx slices per instance.
   void s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
+    if (sp) {
+      sparse_s_kernel(t1c, t2c, S1c, S2c, nxcur);
+      return;
+    }
     nx = nxcur;
     amp_begin(t1c, t2c);
     T *pta = (T*)ta.p, *pX = (T*)X.p, *pWmnij = (T*)Wmnij.p, *pWabef = (T*)Wabef.p,
@@ -1138,8 +1275,91 @@ Batch::~Batch() {
     for (Buf* q : bs) home->put(*q);
   }
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
-               &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz};
+               &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
+               &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work};
   for (Buf* q : bs) home->put(*q);
+}
+
+// ---- block-sparse tables (host)
+namespace {
+std::array<int, 4> canon_charge(std::array<int, 4> q, const int* mod) {
+  for (int k = 0; k < 4; ++k)
+    if (mod[k] > 0) q[k] = ((q[k] % mod[k]) + mod[k]) % mod[k];
+  return q;
+}
+uint64_t charge_key(const std::array<int, 4>& q) {
+  uint64_t key = 0;
+  for (int k = 0; k < 4; ++k) key = (key << 16) | static_cast<uint16_t>(q[k] + 32768);
+  return key;
+}
+}  // namespace
+
+// imp[a][b][c] = the orbital whose charge is q_a + q_b - q_c, or -1
+void build_implied(Batch& B, const ftcc_ctx* c) {
+  const int n = B.N;
+  std::unordered_map<uint64_t, int> orb;
+  for (int p = 0; p < n; ++p) orb[charge_key(canon_charge(c->charge[p], c->charge_mod))] = p;
+  if (static_cast<int>(orb.size()) != n) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: two orbitals share a charge"};
+  const long long n3 = static_cast<long long>(n) * n * n;
+  std::vector<int16_t> t(n3);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int cc = 0; cc < n; ++cc) {
+        std::array<int, 4> q;
+        for (int k = 0; k < 4; ++k) q[k] = c->charge[a][k] + c->charge[b][k] - c->charge[cc][k];
+        auto it = orb.find(charge_key(canon_charge(q, c->charge_mod)));
+        t[(static_cast<long long>(a) * n + b) * n + cc] = static_cast<int16_t>(it == orb.end() ? -1 : it->second);
+      }
+  ensure(B.home, B.imp, n3 * sizeof(int16_t));
+  CU(cudaMemcpyAsync(B.imp.p, t.data(), n3 * sizeof(int16_t), cudaMemcpyHostToDevice, B.home->st));
+  CU(cudaStreamSynchronize(B.home->st));
+}
+
+// sectors of ordered pairs (p, q) by q_p + q_q (diff = false) or q_p - q_q;
+// the summed index of a sector runs over the first (sum) or second (diff)
+// letters of its pairs
+void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T) {
+  const int n = B.N, tile = sector_tile();
+  std::unordered_map<uint64_t, int> sid;
+  std::vector<std::vector<int2>> rows;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      std::array<int, 4> ch;
+      for (int k = 0; k < 4; ++k) ch[k] = c->charge[p][k] + (diff ? -c->charge[q][k] : c->charge[q][k]);
+      const uint64_t key = charge_key(canon_charge(ch, c->charge_mod));
+      auto it = sid.find(key);
+      if (it == sid.end()) {
+        it = sid.emplace(key, static_cast<int>(rows.size())).first;
+        rows.emplace_back();
+      }
+      rows[it->second].push_back(make_int2(p, q));
+    }
+  std::vector<int2> ent;
+  std::vector<int> kl;
+  std::vector<int4> sec, work;
+  T.flops = 0;
+  for (size_t s = 0; s < rows.size(); ++s) {
+    const int off = static_cast<int>(ent.size()), cnt = static_cast<int>(rows[s].size());
+    for (const int2& e : rows[s]) {
+      ent.push_back(e);
+      kl.push_back(diff ? e.y : e.x);
+    }
+    sec.push_back(make_int4(off, cnt, off, cnt));
+    for (int r0 = 0; r0 < cnt; r0 += tile)
+      for (int c0 = 0; c0 < cnt; c0 += tile) work.push_back(make_int4(static_cast<int>(s), r0, c0, 0));
+    T.flops += 2.0 * cnt * static_cast<double>(cnt) * cnt;
+  }
+  ftcc_ctx* h = B.home;
+  ensure(h, T.ent, ent.size() * sizeof(int2));
+  ensure(h, T.kl, kl.size() * sizeof(int));
+  ensure(h, T.sec, sec.size() * sizeof(int4));
+  ensure(h, T.work, work.size() * sizeof(int4));
+  CU(cudaMemcpyAsync(T.ent.p, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
+  CU(cudaMemcpyAsync(T.kl.p, kl.data(), kl.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CU(cudaMemcpyAsync(T.sec.p, sec.data(), sec.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+  CU(cudaMemcpyAsync(T.work.p, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+  CU(cudaStreamSynchronize(h->st));
+  T.nwork = static_cast<int>(work.size());
 }
 
 }  // namespace ftcc
@@ -1166,6 +1386,7 @@ ftcc_options default_options() {
   o.fp64_propagation = 1;
   o.tol_refine = 1e-6;
   o.mixed_adjoint = 0;
+  o.block_sparse = 0;
   o.tau_chunk = 0;
   o.use_graph = 1;
   o.stream_tau = 0;
@@ -1231,6 +1452,32 @@ void build_blocks(Batch& B, Solver<T>& s) {
   }
 }
 
+// The thermal integral and Fock blocks in block-sparse storage: each ERI
+// class as an N^3 array (fourth index implied), each Fock class as its
+// diagonal.  No truncation, so the hole and particle lists are every orbital.
+void build_blocks_sparse(Batch& B, Solver<double>& s) {
+  ftcc_ctx* h = B.home;
+  const int n = B.N;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const Inst& I = B.inst[0];
+  const int16_t* imp = static_cast<const int16_t*>(B.imp.p);
+  auto fac = [&](char c) { return static_cast<const double*>(c == 'o' ? I.facO.p : I.facV.p); };
+  const char* eri_pat[] = {"oovv", "ovvv", "ooov", "oooo", "vvvv", "vovv", "ovvo", "oovo", "ovov", "vvoo", "vvvo", "ovoo"};
+  for (const char* pat : eri_pat) {
+    Buf& buf = s.Vb[pat];
+    ensure(h, buf, n3 * sizeof(double));
+    CU(launch_sp_thermal_eri(static_cast<const double*>(I.ctx->eri.p), imp, n, fac(pat[0]), fac(pat[1]), fac(pat[2]),
+                             fac(pat[3]), static_cast<double*>(buf.p), h->st));
+  }
+  const char* f_pat[] = {"ov", "vv", "oo", "vo"};
+  for (const char* pat : f_pat) {
+    Buf& buf = s.Fb[pat];
+    ensure(h, buf, n * sizeof(double));
+    CU(launch_sp_thermal_fock(static_cast<const double*>(I.fbar.p), n, fac(pat[0]), fac(pat[1]),
+                              static_cast<double*>(buf.p), h->st));
+  }
+}
+
 template <class T>
 Solver<T>& make_solver(Batch& B, int kind) {
   std::unique_ptr<Solver<T>>* slot;
@@ -1244,6 +1491,26 @@ Solver<T>& make_solver(Batch& B, int kind) {
     s.no = B.no;
     s.nv = B.nv;
     s.ng = B.ng;
+    if constexpr (sizeof(T) == 8) {
+      if (B.sparse) {
+        s.sp = true;
+        s.nxc = B.opt.tau_chunk > 0 ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
+        build_blocks_sparse(B, s);
+        const long long g = s.ng, n1 = s.n1(), n2 = s.n2();
+        ensure(h, s.t1, g * n1 * sizeof(T));
+        ensure(h, s.t2, g * n2 * sizeof(T));
+        ensure(h, s.S1, g * n1 * sizeof(T));
+        ensure(h, s.S2, g * n2 * sizeof(T));
+        CU(cudaMemsetAsync(s.t1.p, 0, g * n1 * sizeof(T), h->st));
+        CU(cudaMemsetAsync(s.t2.p, 0, g * n2 * sizeof(T), h->st));
+        s.sparse_alloc();
+        s.nb1 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((n1 + 127) / 128)));
+        s.nb2 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((n2 + 127) / 128)));
+        ensure(h, s.part1, static_cast<size_t>(s.nb1) * (s.ng + 2) * sizeof(double));
+        ensure(h, s.part2, static_cast<size_t>(s.nb2) * (s.ng + 2) * sizeof(double));
+        return s;
+      }
+    }
     s.stream = B.nz == 1 && B.opt.stream_tau != 0;
     if (s.stream) s.nxc = std::min(B.ng, B.opt.tau_chunk > 0 ? B.opt.tau_chunk : 1);
     else s.nxc = (B.nz == 1 && B.opt.tau_chunk > 0) ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
@@ -1287,6 +1554,10 @@ PropArgs prop_args(Batch& B, int nslot) {
   a.damping = B.opt.damping;
   a.nslot = nslot;
   a.size = nslot == 2 ? static_cast<long long>(B.no) * B.nv : static_cast<long long>(B.no) * B.no * B.nv * B.nv;
+  if (B.sparse) {
+    a.size = nslot == 2 ? B.N : static_cast<long long>(B.N) * B.N * B.N;
+    a.imp = static_cast<const int16_t*>(B.imp.p);
+  }
   a.y0 = 0;
   a.y1 = B.ng;
   a.s_ng = B.ng;
@@ -1307,8 +1578,7 @@ void set_tables(Batch& B, PropArgs& a) {
 template <class T>
 void iterate_once(Batch& B, Solver<T>& s) {
   s.prof_next = 0;
-  const long long o = s.no, v = s.nv;
-  const long long n1 = o * v, n2 = o * o * v * v;
+  const long long n1 = s.n1(), n2 = s.n2();
   if (s.stream) {
     // S for one chunk of tau points at a time, then the propagation of those
     // points from the carried chain state (the S kernel at tau_x reads only
@@ -1557,7 +1827,7 @@ bool shell_grid(int n_pw, std::vector<int>& out) {
 ftcc_status check_options(ftcc_ctx* c, const ftcc_options& o) {
   if (!(o.damping > 0 && o.damping <= 1) || o.max_iter < 0 || o.refine_max_iter < 0 || o.polish_max_iter < 0 || o.trunc_thr < 0 ||
       o.fp64_propagation < 0 || o.fp64_propagation > 2 || !(o.tol_refine >= 0) || o.mixed_adjoint < 0 ||
-      o.mixed_adjoint > 1 ||
+      o.mixed_adjoint > 1 || o.block_sparse < 0 || o.block_sparse > 1 ||
       o.trunc_thr >= 0.5 || o.precision < 0 || o.precision > 2 || o.tau_chunk < 0 || o.stream_tau < 0 ||
       o.stream_tau > 1 || o.autotune < 0 || o.autotune > 1 || !(o.tol_omega >= 0) ||
       !(o.tol_amp >= 0) || !(o.tol_mixed >= 0))
@@ -1626,6 +1896,18 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
   if (B->O.empty() || B->V.empty()) throw Fail{FTCC_ERR_INVALID_ARG, "truncation left an empty space"};
   B->no = static_cast<int>(B->O.size());
   B->nv = static_cast<int>(B->V.size());
+  if (o.block_sparse) {
+    if (n != 1) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: one instance per solve"};
+    if (o.precision != FTCC_PREC_FP64) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: precision must be FP64"};
+    if (static_cast<int>(home->charge.size()) != N)
+      throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: the system has no conserved orbital charges (UEG or k-space Hubbard)"};
+    if (B->no != N || B->nv != N) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: truncation must keep every orbital"};
+    if (N > 32767) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: at most 32767 spin orbitals"};
+    B->sparse = true;
+    build_implied(*B, home);
+    build_sectors(*B, home, false, B->ssum);
+    build_sectors(*B, home, true, B->sdiff);
+  }
   ensure(home, B->idxO, B->O.size() * sizeof(int));
   ensure(home, B->idxV, B->V.size() * sizeof(int));
   CU(cudaMemcpyAsync(B->idxO.p, B->O.data(), B->O.size() * sizeof(int), cudaMemcpyHostToDevice, home->st));
@@ -1634,8 +1916,11 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
   ensure(home, B->ep, static_cast<size_t>(n) * N * sizeof(double));
   ensure(home, B->hz, static_cast<size_t>(n) * 2 * sizeof(double));
   const long long no = B->no, nv = B->nv;
-  ensure(home, B->V64, static_cast<size_t>(n) * no * no * nv * nv * sizeof(double));
-  ensure(home, B->F64, static_cast<size_t>(n) * no * nv * sizeof(double));
+  // energy weights <ij||ab> and f_ia (Eq. E) in the storage of the amplitudes
+  const long long w2 = B->sparse ? static_cast<long long>(N) * N * N : no * no * nv * nv;
+  const long long w1 = B->sparse ? N : no * nv;
+  ensure(home, B->V64, static_cast<size_t>(n) * w2 * sizeof(double));
+  ensure(home, B->F64, static_cast<size_t>(n) * w1 * sizeof(double));
   ensure(home, B->state, static_cast<size_t>(n) * kStateStride * sizeof(double));
   std::vector<double> hb(2 * n);
   for (int z = 0; z < n; ++z) {
@@ -1653,10 +1938,18 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
     const int* iV = static_cast<const int*>(B->idxV.p);
     const double* fO = static_cast<const double*>(I.facO.p);
     const double* fV = static_cast<const double*>(I.facV.p);
-    CU(launch_thermal_eri<double>(static_cast<const double*>(cs[z]->eri.p), N, iO, fO, B->no, iO, fO, B->no, iV, fV,
-                                  B->nv, iV, fV, B->nv, static_cast<double*>(B->V64.p) + z * no * no * nv * nv, home->st));
-    CU(launch_thermal_fock<double>(static_cast<const double*>(I.fbar.p), N, iO, fO, B->no, iV, fV, B->nv,
-                                   static_cast<double*>(B->F64.p) + z * no * nv, home->st));
+    if (B->sparse) {
+      CU(launch_sp_thermal_eri(static_cast<const double*>(cs[z]->eri.p), static_cast<const int16_t*>(B->imp.p), N, fO,
+                               fO, fV, fV, static_cast<double*>(B->V64.p), home->st));
+      CU(launch_sp_thermal_fock(static_cast<const double*>(I.fbar.p), N, fO, fV, static_cast<double*>(B->F64.p),
+                                home->st));
+    } else {
+      CU(launch_thermal_eri<double>(static_cast<const double*>(cs[z]->eri.p), N, iO, fO, B->no, iO, fO, B->no, iV, fV,
+                                    B->nv, iV, fV, B->nv, static_cast<double*>(B->V64.p) + z * no * no * nv * nv,
+                                    home->st));
+      CU(launch_thermal_fock<double>(static_cast<const double*>(I.fbar.p), N, iO, fO, B->no, iV, fV, B->nv,
+                                     static_cast<double*>(B->F64.p) + z * no * nv, home->st));
+    }
     hb[z] = I.hstep;
     hb[n + z] = I.beta;
     if (z == 0) {
@@ -2284,6 +2577,7 @@ ftcc_status check_solve_args(ftcc_ctx* c, double beta, double mu, int ngrid, ftc
 // The RK drivers march the FP64 amplitudes over the whole grid at once.
 ftcc_status check_quad_options(ftcc_ctx* c, ftcc_quadrature quad, const ftcc_options& o) {
   if (quad == FTCC_QUAD_SIMPSON) return FTCC_OK;
+  if (o.block_sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: Simpson integral form only");
   if (o.precision != FTCC_PREC_FP64)
     return fail(c, FTCC_ERR_UNSUPPORTED, "the RK drivers run in FP64 (precision = FTCC_PREC_FP64)");
   if (o.stream_tau) return fail(c, FTCC_ERR_UNSUPPORTED, "the RK drivers keep every tau point (stream_tau = 0)");
@@ -2436,6 +2730,21 @@ ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
       CU(cudaMemcpyAsync(c->eps.p, s->eps, static_cast<size_t>(N) * sizeof(double), cudaMemcpyHostToDevice, c->st));
     }
     sync(c);
+    // conserved orbital charges: p = sigma * L + m with crystal momentum m
+    // (mod L) for the k-space ring, p = sigma * n_pw + g with the plane wave
+    // n_g for the gas; S_z as sigma
+    c->charge.clear();
+    for (int k = 0; k < 4; ++k) c->charge_mod[k] = 0;
+    if (s->kind == FTCC_SYS_HUBBARD_1D && s->reference == FTCC_REF_KSPACE_RHF) {
+      for (int p = 0; p < N; ++p) c->charge.push_back({p % s->L, p / s->L, 0, 0});
+      c->charge_mod[0] = s->L;
+    } else if (s->kind == FTCC_SYS_UEG) {
+      const int M = s->n_pw;
+      for (int p = 0; p < N; ++p) {
+        const int g = p % M;
+        c->charge.push_back({nvec[3 * g], nvec[3 * g + 1], nvec[3 * g + 2], p / M});
+      }
+    }
     c->N = N;
     return FTCC_OK;
   });
@@ -2679,6 +2988,7 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
     return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
   if (c->batch->opt.stream_tau)
     return fail(c, FTCC_ERR_UNSUPPORTED, "the adjoint needs S at every tau point (solve without stream_tau)");
+  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: the adjoint runs on the dense storage");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
@@ -2773,6 +3083,20 @@ ftcc_status ftcc_get_amplitudes(ftcc_ctx* c, double* s1, double* s2) {
     const long long g = B.ng, o = B.no, v = B.nv;
     const long long n1 = g * o * v, n2 = g * o * o * v * v;
     const long long z = c->member;
+    if (B.sparse) {   // expand the compressed storage into the dense layouts
+      Solver<double>& sv = *B.s64;
+      Buf d1 = h->get(n1 * sizeof(double)), d2 = h->get(n2 * sizeof(double));
+      if (!d1.p || !d2.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      CU(launch_sp_expand(static_cast<const double*>(sv.t1.p), static_cast<const double*>(sv.t2.p),
+                          static_cast<const int16_t*>(B.imp.p), B.N, B.ng, static_cast<double*>(d1.p),
+                          static_cast<double*>(d2.p), h->st));
+      if (s1) CU(cudaMemcpyAsync(s1, d1.p, n1 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      if (s2) CU(cudaMemcpyAsync(s2, d2.p, n2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      h->put(d1);
+      h->put(d2);
+      return FTCC_OK;
+    }
     Buf tmp = h->get(std::max(n1, n2) * sizeof(double));
     if (!tmp.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
     auto copy_out = [&](const void* base, long long n, double* dst) {
@@ -2801,7 +3125,24 @@ ftcc_status ftcc_eval_s(ftcc_ctx* c, int nx, int precision, const double* t1_dev
     Batch& B = *c->batch;
     const long long o = B.no, v = B.nv;
     const long long n1 = nx * o * v, n2 = nx * o * o * v * v;
-    if (precision == FTCC_PREC_FP64) {
+    if (B.sparse) {
+      // dense in and out: the inputs are projected onto the charge-conserving
+      // elements (s1 diagonal, s2 with q_i + q_j = q_a + q_b), the outputs
+      // expanded with zeros elsewhere
+      if (precision != FTCC_PREC_FP64) return fail(c, FTCC_ERR_INVALID_ARG, "block_sparse: FP64 only");
+      Solver<double>& s = make_solver<double>(B, GEMM_F64);
+      if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+      const long long N = B.N, n3 = N * N * N;
+      Buf a = c->get(nx * N * 8), b = c->get(nx * n3 * 8), d = c->get(nx * N * 8), e = c->get(nx * n3 * 8);
+      if (!a.p || !b.p || !d.p || !e.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      const int16_t* imp = static_cast<const int16_t*>(B.imp.p);
+      CU(launch_sp_compress(t1_dev, t2_dev, imp, B.N, nx, static_cast<double*>(a.p), static_cast<double*>(b.p), c->st));
+      s.s_kernel(static_cast<double*>(a.p), static_cast<double*>(b.p), static_cast<double*>(d.p),
+                 static_cast<double*>(e.p), nx);
+      CU(launch_sp_expand(static_cast<double*>(d.p), static_cast<double*>(e.p), imp, B.N, nx, s1_dev, s2_dev, c->st));
+      sync(c);
+      for (Buf* q : {&a, &b, &d, &e}) c->put(*q);
+    } else if (precision == FTCC_PREC_FP64) {
       Solver<double>& s = make_solver<double>(B, GEMM_F64);
       if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
       s.s_kernel(t1_dev, t2_dev, s1_dev, s2_dev, nx);
@@ -2832,6 +3173,7 @@ ftcc_status ftcc_propagate(ftcc_ctx* c, const char* slots, const double* S_dev, 
   if (!c || !slots || !S_dev || !s_dev) return FTCC_ERR_INVALID_ARG;
   if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
   if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "ftcc_propagate works on a single prepared instance");
+  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: dense layouts only");
   const int ns = static_cast<int>(strlen(slots));
   if (ns != 2 && ns != 4) return fail(c, FTCC_ERR_INVALID_ARG, "slots must be 'ia' or 'ijab'");
   return run_guarded(c, [&]() -> ftcc_status {
@@ -2859,6 +3201,7 @@ ftcc_status ftcc_eval_s_vjp(ftcc_ctx* c, int nx, const double* t1_dev, const dou
   if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
   if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "works on a single prepared instance");
   if (nx < 1 || nx > c->batch->ng) return fail(c, FTCC_ERR_INVALID_ARG, "bad nx");
+  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: no S-kernel transpose");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     Solver<double>& s = make_solver<double>(B, GEMM_F64);
@@ -2880,6 +3223,7 @@ ftcc_status ftcc_eval_s_vjp(ftcc_ctx* c, int nx, const double* t1_dev, const dou
 ftcc_status ftcc_propagate_adjoint(ftcc_ctx* c, const char* slots, const double* m_dev, double* u_dev) {
   if (!c || !slots || !m_dev || !u_dev) return FTCC_ERR_INVALID_ARG;
   if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
+  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: dense layouts only");
   if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "works on a single prepared instance");
   const int ns = static_cast<int>(strlen(slots));
   if (ns != 2 && ns != 4) return fail(c, FTCC_ERR_INVALID_ARG, "slots must be 'ia' or 'ijab'");

@@ -1,0 +1,502 @@
+// Momentum/spin block-sparse execution of the S kernel (Eqs. ccS1/ccS2),
+// FP64.
+//
+// In the plane-wave electron gas (Sec. IV.B) and the k-space Hubbard ring
+// (Sec. IV.A) every spin orbital p carries its own conserved charge q_p
+// (crystal momentum and S_z): no two orbitals share one.  Every factor of the
+// CCSD equations conserves it, so
+//   * a two-index factor (f, s1, F_ae, F_mi, F_me, S1) is diagonal: a vector
+//     X[p] = X_pp;
+//   * a four-index factor with q_0 + q_1 = q_2 + q_3 (in the order it is
+//     stored here) is fixed by its first three indices: it is stored as an
+//     N^3 array X[p0][p1][p2], the fourth index implied by charge balance.
+//     A triple whose implied charge belongs to no orbital (a "hole" of the
+//     storage) holds zero.
+// The implied index comes from one table imp[a][b][c] = the orbital whose
+// charge is q_a + q_b - q_c, or -1 (int16, N^3 entries).
+//
+// Contractions of two four-index factors over two indices leave one free
+// summed index once the output indices are fixed; they run as products of
+// small dense blocks ("sectors"): the rows of the left operand are ordered
+// index pairs (p, q) grouped by their pair charge (q_p + q_q for the
+// ladders, q_p - q_q for the ring), the summed index runs over the K list of
+// the sector, and every row of a sector meets every row of the matching
+// sector of the right operand (sector_gemm_kernel).  Everything else is
+// element by element over the N^3 positions or a reduction to a vector.
+//
+// Layout of a slice: [x][p0][p1][p2] for four-index tensors, [x][p] for
+// vectors; fixed tensors (integrals, Fock diagonals) have no x.
+#include <cstdint>
+
+#include "ftcc_internal.h"
+
+namespace ftcc {
+namespace {
+
+constexpr int kSpThreads = 256;
+
+inline int sp_grid(long long n, int threads = kSpThreads, int cap = 152 * 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return static_cast<int>(b);
+}
+
+__device__ __forceinline__ int impl(const int16_t* __restrict__ imp, int n, int a, int b, int c) {
+  return imp[(static_cast<long long>(a) * n + b) * n + c];
+}
+
+__device__ __forceinline__ long long pos3(int n, int a, int b, int c) {
+  return (static_cast<long long>(a) * n + b) * n + c;
+}
+
+// ---- amplitude-derived operands of one S evaluation (one pass over the
+// N^3 positions of every slice x):
+//   ta[i][j][a]  = tau_ij^ab = s_ij^ab + P(ij) s_i^a s_j^b      (b implied)
+//   tp[a][b][m]  = tau_mn^ab                                    (n implied)
+//   tr[i][a][m]  = s_im^ae                                      (e implied)
+//   xp[j][b][n]  = X_jn^fb = 1/2 s_jn^fb + s_j^f s_n^b          (f implied)
+// with s1 diagonal (s_i^a = delta_ia s1[i]).
+__global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __restrict__ t2,
+                              const int16_t* __restrict__ imp, int n, double* __restrict__ ta,
+                              double* __restrict__ tp, double* __restrict__ tr, double* __restrict__ xp) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* s1 = t1 + x * n;
+  const double* s2 = t2 + x * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p2 = static_cast<int>(e % n);
+    const int p1 = static_cast<int>((e / n) % n);
+    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const long long o = x * n3 + e;
+    {   // ta: (i, j, a) = (p0, p1, p2), b implied
+      const int b = impl(imp, n, p0, p1, p2);
+      double v = 0.0;
+      if (b >= 0) {
+        v = s2[e];
+        const double pr = s1[p0] * s1[p1];
+        if (p2 == p0) v += pr;
+        if (p2 == p1) v -= pr;
+      }
+      ta[o] = v;
+    }
+    {   // tp: (a, b, m) = (p0, p1, p2), n = q_a + q_b - q_m
+      const int nn = impl(imp, n, p0, p1, p2);
+      double v = 0.0;
+      if (nn >= 0) {
+        v = s2[pos3(n, p2, nn, p0)];   // s_{m nn}^{a b}
+        const double pr = s1[p2] * s1[nn];
+        if (p0 == p2) v += pr;
+        if (p0 == nn) v -= pr;
+      }
+      tp[o] = v;
+    }
+    {   // tr: (i, a, m) = (p0, p1, p2), e = q_i + q_m - q_a
+      const int ee = impl(imp, n, p0, p2, p1);
+      tr[o] = ee >= 0 ? s2[pos3(n, p0, p2, p1)] : 0.0;   // s_{i m}^{a e}
+    }
+    {   // xp: (j, b, n) = (p0, p1, p2), f = q_j + q_n - q_b
+      const int f = impl(imp, n, p0, p2, p1);
+      double v = 0.0;
+      if (f >= 0) {
+        v = 0.5 * s2[pos3(n, p0, p2, f)];   // 1/2 s_{j n}^{f b}
+        if (f == p0) v += s1[p0] * s1[p2];
+      }
+      xp[o] = v;
+    }
+  }
+}
+
+// ---- F_me = f_me + sum_n s1[n] <mn||mn>   (diagonal, e = m, f = n)
+__global__ void sp_fme_kernel(const double* __restrict__ t1, const double* __restrict__ fov,
+                              const double* __restrict__ Voovv, int n, int nx, double* __restrict__ Fme) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n * nx) return;
+  const int x = warp / n, m = warp % n;
+  const double* s1 = t1 + static_cast<long long>(x) * n;
+  double acc = 0.0;
+  for (int q = lane; q < n; q += 32) acc += s1[q] * Voovv[pos3(n, m, q, m)];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) Fme[static_cast<long long>(x) * n + m] = fov[m] + acc;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (blockDim.x >> 5); ++k) s += red[k];
+  return s;   // valid in thread 0
+}
+
+// ---- the vector intermediates and S1 of one (x, p):
+//   F_ae[p] = f_vv[p] - 1/2 s1[p] F_me[p] + sum_m s1[m] <mp||mp> - 1/2 sum_mn s_mn^pe <mn||pe>
+//   F_mi[p] = f_oo[p] + 1/2 s1[p] F_me[p] + sum_n s1[n] <pn||pn> + 1/2 sum_ne s_pn^ef <pn||ef>
+//   S1[p]   = f_vo[p] + s1[p] (F_ae[p] - F_mi[p]) + sum_m s_pm^pm F_me[m] - sum_n s1[n] <np||pn>
+//             - 1/2 sum_me s_pm^ef <mp||ef> - 1/2 sum_mn s_mn^pe <nm||ep>
+//   Ft[p] = F_ae[p] - 1/2 s1[p] F_me[p],  Ft2[p] = F_mi[p] + 1/2 s1[p] F_me[p]
+// (the diagonal forms of Eq. ccS1's terms and of the F intermediates; each
+// integral block in its own thermal scaling).
+struct SpVec {
+  const double *t1, *t2, *Fme;
+  const double *foo, *fvv, *fvo;
+  const double *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
+  const int16_t* imp;
+  int n;
+  double *Fae, *Fmi, *S1, *Ft, *Ft2;
+};
+
+__global__ void sp_vec_kernel(SpVec a) {
+  __shared__ double red[32];
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const int p = blockIdx.x, x = blockIdx.y;
+  const double* s1 = a.t1 + static_cast<long long>(x) * n;
+  const double* s2 = a.t2 + x * n3;
+  const double* Fme = a.Fme + static_cast<long long>(x) * n;
+  double cae = 0.0, cmi = 0.0, cs1 = 0.0;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    cae += s1[m] * a.Vovvv[pos3(n, m, p, m)];
+    cmi += s1[m] * a.Vooov[pos3(n, p, m, p)];
+    cs1 += s2[pos3(n, p, m, p)] * Fme[m] - s1[m] * a.Vovov[pos3(n, m, p, p)];
+  }
+  const long long nn = static_cast<long long>(n) * n;
+  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
+    const int m = static_cast<int>(r / n), q = static_cast<int>(r % n);
+    const long long o1 = pos3(n, m, q, p);   // (m, q, p)
+    const long long o2 = pos3(n, p, m, q);   // (p, m, q)
+    const double t_mqp = s2[o1];
+    cae -= 0.5 * t_mqp * a.Voovv[o1];
+    cmi += 0.5 * s2[o2] * a.Voovv[o2];
+    cs1 -= 0.5 * s2[o2] * a.Vovvv[pos3(n, m, p, q)];
+    if (t_mqp != 0.0) {
+      const int e = impl(a.imp, n, m, q, p);   // q_e = q_m + q_q - q_p
+      if (e >= 0) cs1 -= 0.5 * t_mqp * a.Voovo[pos3(n, q, m, e)];
+    }
+  }
+  cae = block_sum(cae, red);
+  cmi = block_sum(cmi, red);
+  cs1 = block_sum(cs1, red);
+  if (threadIdx.x == 0) {
+    const long long o = static_cast<long long>(x) * n + p;
+    const double s = s1[p], fm = Fme[p];
+    const double fae = a.fvv[p] - 0.5 * s * fm + cae;
+    const double fmi = a.foo[p] + 0.5 * s * fm + cmi;
+    a.Fae[o] = fae;
+    a.Fmi[o] = fmi;
+    a.S1[o] = a.fvo[p] + s * (fae - fmi) + cs1;
+    a.Ft[o] = fae - 0.5 * s * fm;
+    a.Ft2[o] = fmi + 0.5 * s * fm;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// ---- bases of the four-index intermediates (one pass over the positions):
+//   w1[i][j][m] = W'_mnij without its tau term = <mn||ij> - 2 s1[i] <mn||ji>   (n implied)
+//   wab[a][b][e] = W'_abef = <ab||ef> - 2 s1[a] <ab||ef>_ovvv                    (f implied)
+//   wr[j][b][m] = W_mbej without its X term
+//               = <mb||ej> + s1[j] <mb||ej>_ovvv - s1[b] <mb||ej>_oovo          (e implied)
+// (s1 diagonal turns every s1 contraction of these intermediates into a
+// scaling; the integral blocks differ only by their thermal factors).
+struct SpW {
+  const double *t1, *Voooo, *Vooov, *Vvvvv, *Vovvv, *Vovvo, *Voovo;
+  const int16_t* imp;
+  int n;
+  double *w1, *wab, *wr;
+};
+
+__global__ void sp_wbase_kernel(SpW a) {
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* s1 = a.t1 + x * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p2 = static_cast<int>(e % n);
+    const int p1 = static_cast<int>((e / n) % n);
+    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const long long o = x * n3 + e;
+    {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
+      const int q = impl(a.imp, n, p0, p1, p2);
+      a.w1[o] = q >= 0 ? a.Voooo[pos3(n, p2, q, p0)] - 2.0 * s1[p0] * a.Vooov[pos3(n, p2, q, p1)] : 0.0;
+    }
+    // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide
+    a.wab[o] = a.Vvvvv[e] - 2.0 * s1[p0] * a.Vovvv[e];
+    {   // (j, b, m) = (p0, p1, p2), e = q_b + q_m - q_j
+      const int ee = impl(a.imp, n, p1, p2, p0);
+      double v = 0.0;
+      if (ee >= 0) {
+        const long long c = pos3(n, p2, p1, ee);   // (m, b, e), j implied
+        v = a.Vovvo[c] + s1[p0] * a.Vovvv[c] - s1[p1] * a.Voovo[c];
+      }
+      a.wr[o] = v;
+    }
+  }
+}
+
+// ---- R (the accumulator that enters S2 through P(ij)P(ab)), the terms
+// that need no sector product, for (i, j, a) with b implied:
+//   R = 1/2 s_ij^ab Ft[b] + 1/2 Ft2[i] s_ji^ab + 1/2 s1[i] <ab||ij>_vvvo
+//     - 1/2 s1[a] <ab||ij>_ovoo + s1[i] s1[b] <ba||ij>_ovvo
+// (the last is the s_i^e <mb||ej> s_m^b term of Eq. ccS2).
+struct SpR {
+  const double *t1, *t2, *Ft, *Ft2, *Vvvvo, *Vovoo, *Vovvo;
+  const int16_t* imp;
+  int n;
+  double* R;
+};
+
+__global__ void sp_rinit_kernel(SpR a) {
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* s1 = a.t1 + x * n;
+  const double* s2 = a.t2 + x * n3;
+  const double* Ft = a.Ft + x * n;
+  const double* Ft2 = a.Ft2 + x * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int aa = static_cast<int>(e % n);
+    const int j = static_cast<int>((e / n) % n);
+    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const int b = impl(a.imp, n, i, j, aa);
+    double v = 0.0;
+    if (b >= 0) {
+      const long long c = pos3(n, aa, b, i);   // (a, b, i), j implied
+      v = 0.5 * s2[e] * Ft[b] + 0.5 * Ft2[i] * s2[pos3(n, j, i, aa)] + 0.5 * s1[i] * a.Vvvvo[c] -
+          0.5 * s1[aa] * a.Vovoo[c] + s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)];
+    }
+    a.R[x * n3 + e] = v;
+  }
+}
+
+// ---- S2 = P(ij)P(ab) R + <ab||ij>_vvoo
+__global__ void sp_s2_kernel(const double* __restrict__ R, const double* __restrict__ Vvvoo,
+                             const int16_t* __restrict__ imp, int n, double* __restrict__ S2) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* r = R + x * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int aa = static_cast<int>(e % n);
+    const int j = static_cast<int>((e / n) % n);
+    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const int b = impl(imp, n, i, j, aa);
+    double v = 0.0;
+    if (b >= 0)
+      v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
+    S2[x * n3 + e] = v;
+  }
+}
+
+// ---- sector products.  For every work item (sector s, row tile, column
+// tile) and slice x:
+//   C[pos(r, c)] += alpha * sum_{k in K_s} A[rowA(r)][k] * B[rowB(c)][k]
+// over the rows r, c of the sector.  Row entries are ordered index pairs
+// (p, q); rowA = p n + q, rowB = p n + q, or q n + p with swapB; the output
+// position is p_r s0 + q_r s1 + p_c s2 + q_c s3.  A and B are [n^2][n]
+// views of N^3 tensors.
+constexpr int kSecT = 16;   // output tile edge
+constexpr int kSecK = 16;   // K step
+
+__global__ void __launch_bounds__(kSecT * kSecT) sector_gemm_kernel(SecGemmArgs g) {
+  __shared__ double As[kSecK][kSecT + 1], Bs[kSecK][kSecT + 1];
+  const int4 w = g.work[blockIdx.x];
+  const int4 sec = g.sec[w.x];   // row offset, rows, K offset, K count
+  const long long x = blockIdx.y;
+  const double* A = g.A + x * g.ax;
+  const double* B = g.B + x * g.bx;
+  const int n = g.n;
+  const int tr = threadIdx.x / kSecT, tc = threadIdx.x % kSecT;
+  const int r = w.y + tr, c = w.z + tc;
+  const bool rin = r < sec.y, cin = c < sec.y;
+  // loader: thread (rr, kk) loads A[row rr][k kk] and B[row rr][k kk]
+  // (consecutive threads walk one row's K list)
+  const int lk = threadIdx.x % kSecK, lr = threadIdx.x / kSecK;
+  const int ar = w.y + lr, bc = w.z + lr;
+  long long arow = -1, brow = -1;
+  if (ar < sec.y) {
+    const int2 pr = g.ent[sec.x + ar];
+    arow = (static_cast<long long>(pr.x) * n + pr.y) * n;
+  }
+  if (bc < sec.y) {
+    const int2 pr = g.ent[sec.x + bc];
+    brow = (g.swapB ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y) * n;
+  }
+  double acc = 0.0;
+  for (int k0 = 0; k0 < sec.w; k0 += kSecK) {
+    const int kk = k0 + lk;
+    const int kv = kk < sec.w ? g.kl[sec.z + kk] : -1;
+    As[lk][lr] = (arow >= 0 && kv >= 0) ? A[arow + kv] : 0.0;
+    Bs[lk][lr] = (brow >= 0 && kv >= 0) ? B[brow + kv] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSecK; ++k) acc = fma(As[k][tr], Bs[k][tc], acc);
+    __syncthreads();
+  }
+  if (rin && cin) {
+    const int2 pr = g.ent[sec.x + r], pc = g.ent[sec.x + c];
+    const long long o = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
+                        static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
+    g.C[o] += g.alpha * acc;
+  }
+}
+
+// ---- storage conversions
+// Thermal integral block of class (c0 c1 c2 c3) in N^3 storage:
+// out[p][q][r] = <pq||rs> f0[p] f1[q] f2[r] f3[s], s implied (0 where none).
+__global__ void sp_thermal_eri_kernel(const double* __restrict__ eri, const int16_t* __restrict__ imp, int n,
+                                      const double* f0, const double* f1, const double* f2, const double* f3,
+                                      double* __restrict__ out) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e % n);
+    const int q = static_cast<int>((e / n) % n);
+    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const int s = imp[e];
+    out[e] = s >= 0 ? eri[e * n + s] * f0[p] * f1[q] * f2[r] * f3[s] : 0.0;
+  }
+}
+
+// out[p0][p1][p2] = in[p0][p2][p1] (a hole of one is a hole of the other)
+__global__ void sp_swap12_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p2 = static_cast<int>(e % n);
+    const int p1 = static_cast<int>((e / n) % n);
+    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    out[e] = in[pos3(n, p0, p2, p1)];
+  }
+}
+
+// diagonal of a thermal Fock block: out[p] = fbar[p][p] f0[p] f1[p]
+__global__ void sp_thermal_fock_kernel(const double* __restrict__ fbar, int n, const double* f0, const double* f1,
+                                       double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) out[p] = fbar[static_cast<long long>(p) * n + p] * f0[p] * f1[p];
+}
+
+// dense [x][i][j][a][b] / [x][i][a] <-> N^3 [x][i][j][a] / vector [x][i]
+__global__ void sp_compress_kernel(const double* __restrict__ d1, const double* __restrict__ d2,
+                                   const int16_t* __restrict__ imp, int n, double* __restrict__ s1,
+                                   double* __restrict__ s2) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int b = imp[e];
+    s2[x * n3 + e] = b >= 0 ? d2[(x * n3 + e) * n + b] : 0.0;
+    if (e < n) s1[x * n + e] = d1[(x * n + e) * n + e];
+  }
+}
+
+__global__ void sp_expand_kernel(const double* __restrict__ s1, const double* __restrict__ s2,
+                                 const int16_t* __restrict__ imp, int n, double* __restrict__ d1,
+                                 double* __restrict__ d2) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3 * n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long t = e / n;
+    const int b = static_cast<int>(e % n);
+    d2[x * n3 * n + e] = imp[t] == b ? s2[x * n3 + t] : 0.0;
+    if (e < static_cast<long long>(n) * n) {
+      const int i = static_cast<int>(e / n), a = static_cast<int>(e % n);
+      d1[x * n * n + e] = i == a ? s1[x * n + i] : 0.0;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
+                          double* tp, double* tr, double* xp, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_amp_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st) {
+  const int warps = v.n * nx;
+  sp_fme_kernel<<<(warps * 32 + 127) / 128, 128, 0, st>>>(v.t1, v.fov, v.Voovv, v.n, nx, v.Fme);
+  SpVec a{v.t1, v.t2, v.Fme, v.foo, v.fvv, v.fvo, v.Voovv, v.Vovvv, v.Vooov, v.Vovov, v.Voovo, v.imp, v.n,
+          v.Fae, v.Fmi, v.S1, v.Ft, v.Ft2};
+  sp_vec_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
+                            double* wab, double* wr, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  SpW a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, w1, wab, wr};
+  sp_wbase_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_rinit(const double* t1, const double* t2, const double* Ft, const double* Ft2, const SpBlocks& V,
+                            const int16_t* imp, int n, int nx, double* R, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  SpR a{t1, t2, Ft, Ft2, V.vvvo, V.ovoo, V.ovvo, imp, n, R};
+  sp_rinit_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* imp, int n, int nx, double* S2,
+                         cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_s2_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, n, S2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_gemm(const SecGemmArgs& g, int nwork, int nx, cudaStream_t st) {
+  if (nwork <= 0 || nx <= 0) return cudaSuccess;
+  if (nx > 65535) return cudaErrorInvalidValue;
+  sector_gemm_kernel<<<dim3(nwork, nx), kSecT * kSecT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+int sector_tile() { return kSecT; }
+
+cudaError_t launch_sp_thermal_eri(const double* eri, const int16_t* imp, int n, const double* f0, const double* f1,
+                                  const double* f2, const double* f3, double* out, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_thermal_eri_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(eri, imp, n, f0, f1, f2, f3, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_swap12(const double* in, int n, double* out, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_swap12_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, double* out,
+                                   cudaStream_t st) {
+  sp_thermal_fock_kernel<<<(n + 127) / 128, 128, 0, st>>>(fbar, n, f0, f1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_compress(const double* d1, const double* d2, const int16_t* imp, int n, int nx, double* s1,
+                               double* s2, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_compress_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(d1, d2, imp, n, s1, s2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_expand(const double* s1, const double* s2, const int16_t* imp, int n, int nx, double* d1,
+                             double* d2, cudaStream_t st) {
+  const long long n4 = static_cast<long long>(n) * n * n * n;
+  sp_expand_kernel<<<dim3(sp_grid(n4), nx), kSpThreads, 0, st>>>(s1, s2, imp, n, d1, d2);
+  return cudaGetLastError();
+}
+
+}  // namespace ftcc

@@ -36,7 +36,7 @@ class Options(C.Structure):
                 ("refine_max_iter", C.c_int), ("tol_mixed", C.c_double), ("tau_chunk", C.c_int),
                 ("use_graph", C.c_int), ("stream_tau", C.c_int),
                 ("autotune", C.c_int), ("polish_max_iter", C.c_int), ("fp64_propagation", C.c_int),
-                ("tol_refine", C.c_double), ("mixed_adjoint", C.c_int)]
+                ("tol_refine", C.c_double), ("mixed_adjoint", C.c_int), ("block_sparse", C.c_int)]
 
 
 class Result(C.Structure):
@@ -143,7 +143,8 @@ def _dptr(a):
 def default_options(**kw):
     o = Options(tol_omega=1e-10, tol_amp=1e-8, damping=1.0, trunc_thr=0.0, max_iter=200,
                 precision=PREC_FP64, refine_max_iter=2, tol_mixed=1e-7, tau_chunk=0, use_graph=1, stream_tau=0,
-                autotune=1, polish_max_iter=40, fp64_propagation=1, tol_refine=1e-6, mixed_adjoint=0)
+                autotune=1, polish_max_iter=40, fp64_propagation=1, tol_refine=1e-6, mixed_adjoint=0,
+                block_sparse=0)
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]

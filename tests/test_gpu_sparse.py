@@ -1,0 +1,145 @@
+"""The momentum/spin block-sparse execution (option block_sparse) of the
+plane-wave gas and the k-space Hubbard ring on the GPU: its S kernel on
+random charge-conserving amplitudes element by element against the oracle's
+printed terms of Eqs. ccS1/ccS2, converged solves against the dense FP64 GPU
+path and the oracle, the 114- and 162-spin-orbital gases against the
+block-sparse oracle's converged goldens, and the argument checks."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import blocksparse as bs, ftccsd as fc, systems
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2004_01729_gb300 import ftcc
+    c = ftcc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n_elec,n_pw", [(6, 7), (14, 19)])
+def test_sparse_s_kernel_matches_oracle_terms(ctx, n_elec, n_pw):
+    """S1 and S2 of random amplitudes that conserve momentum and spin, from
+    the block-sparse kernel, against the dense oracle's 45 terms, element by
+    element (every element, including the ones that must vanish)."""
+    rs, beta, ng = 1.0, 1.5, 4
+    sysc = bs.ueg(n_elec, rs, n_pw)
+    t1c, t2c = bs.random_amplitudes(sysc["charges"], 11, 2, 0.05)
+    d1, d2 = bs.dense_amplitudes(sysc["charges"], t1c, t2c)
+    ctx.build_ueg(n_elec, rs, n_pw)
+    mu = ctx.reference_mu(beta, float(n_elec))
+    ctx.prepare(beta, mu, ng, precision="fp64", block_sparse=1)
+    s1, s2 = ctx.eval_s(d1, d2)
+    prob = fc.Problem(systems.ueg(n_elec, rs, n_pw), beta, mu, ng, 0.0)
+    r1 = fc.S1(prob, d1, d2)
+    r2 = fc.S2(prob, d1, d2)
+    e1 = torch.max(torch.abs(s1.cpu() - r1)).item()
+    e2 = torch.max(torch.abs(s2.cpu() - r2)).item()
+    assert torch.max(torch.abs(r2)).item() > 1e-3
+    assert e1 < 1e-12 * max(1.0, torch.max(torch.abs(r1)).item()), e1
+    assert e2 < 1e-12 * max(1.0, torch.max(torch.abs(r2)).item()), e2
+
+
+def test_sparse_s_kernel_matches_dense_gpu(ctx):
+    """The same S evaluation through the dense FP64 engine: identical up to
+    rounding order."""
+    n_elec, rs, n_pw, beta, ng = 14, 1.0, 19, 2.0, 4
+    sysc = bs.ueg(n_elec, rs, n_pw)
+    t1c, t2c = bs.random_amplitudes(sysc["charges"], 3, 3, 0.05)
+    d1, d2 = bs.dense_amplitudes(sysc["charges"], t1c, t2c)
+    ctx.build_ueg(n_elec, rs, n_pw)
+    mu = ctx.reference_mu(beta, float(n_elec))
+    ctx.prepare(beta, mu, ng, precision="fp64", block_sparse=1)
+    a1, a2 = ctx.eval_s(d1, d2)
+    ctx.prepare(beta, mu, ng, precision="fp64")
+    b1, b2 = ctx.eval_s(d1, d2)
+    assert torch.max(torch.abs(a1 - b1)).item() < 1e-12 * max(1.0, torch.max(torch.abs(b1)).item())
+    assert torch.max(torch.abs(a2 - b2)).item() < 1e-12 * max(1.0, torch.max(torch.abs(b2)).item())
+
+
+@pytest.mark.parametrize("which", ["ueg7", "ueg19", "hubbard6", "hubbard10"])
+def test_sparse_solve_matches_dense_and_oracle(ctx, which):
+    """Converged Omega, its history and the amplitudes of the block-sparse
+    solve against the dense FP64 GPU solve; Omega against the oracle."""
+    if which.startswith("ueg"):
+        n_pw = int(which[3:])
+        n_elec, rs, beta, ng = (6 if n_pw == 7 else 14), 1.0, 2.0, 8
+        sysd = systems.ueg(n_elec, rs, n_pw)
+        build = lambda: ctx.build_ueg(n_elec, rs, n_pw)
+        build()
+        mu = ctx.reference_mu(beta, float(n_elec))
+    else:
+        L = int(which[7:])
+        U, beta, ng = 2.0, 1.0, 8
+        sysd = systems.hubbard_1d(L, 1.0, U)
+        build = lambda: ctx.build_hubbard(L, 1.0, U)
+        build()
+        mu = U / 2.0
+    rs_ = ctx.solve(beta, mu, ng, precision="fp64", block_sparse=1, tol_omega=1e-12, tol_amp=1e-10)
+    s1s, s2s = ctx.amplitudes(ng, sysd["eps"].shape[0], sysd["eps"].shape[0])
+    rd = ctx.solve(beta, mu, ng, precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    s1d, s2d = ctx.amplitudes(ng, sysd["eps"].shape[0], sysd["eps"].shape[0])
+    assert rs_["converged"] and rd["converged"]
+    assert rs_["iterations"] == rd["iterations"]
+    assert abs(rs_["omega"] - rd["omega"]) < 1e-11, (rs_["omega"], rd["omega"])
+    assert np.max(np.abs(s1s - s1d)) < 1e-11
+    assert np.max(np.abs(s2s - s2d)) < 1e-11
+    if which in ("ueg7", "hubbard6"):
+        prob = fc.Problem(sysd, beta, mu, ng, 0.0)
+        ref = fc.solve(prob, tol=1e-13, tol_amp=1e-11)
+        assert abs(rs_["omega_cc"] - float(ref["omega_cc"])) < 1e-10
+
+
+@pytest.mark.parametrize("name,tau_chunk", [("oracle_ueg57.json", 0), ("oracle_ueg57.json", 8),
+                                            ("oracle_ueg81.json", 0)])
+def test_sparse_converged_gases_match_goldens(ctx, name, tau_chunk):
+    """The 114- and 162-spin-orbital gases solved in FP64 with the
+    block-sparse storage against the block-sparse oracle's converged Omega
+    (the oracle converged to |dOmega_CC| < 1e-11; the two run the same
+    Jacobi fixed point, so the iteration counts agree too)."""
+    gold = json.load(open(os.path.join(GOLD, name)))
+    c = gold["config"]
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    mu = ctx.reference_mu(c["beta"], float(c["n_elec"]))
+    assert abs(mu - gold["mu"]) < 1e-10
+    r = ctx.solve(c["beta"], gold["mu"], c["ngrid"], precision="fp64", block_sparse=1, tau_chunk=tau_chunk,
+                  tol_omega=1e-11, tol_amp=1e-9, max_iter=80)
+    assert r["converged"] and (r["n_occ"], r["n_vir"]) == (gold["n_orbitals"], gold["n_orbitals"])
+    assert abs(r["omega0"] - gold["omega0"]) < 1e-10
+    assert abs(r["omega1"] - gold["omega1"]) < 1e-10
+    assert abs(r["omega"] - gold["omega"]) < 1e-9, (r["omega"], gold["omega"])
+
+
+def test_sparse_argument_checks(ctx):
+    from paper_2004_01729_gb300 import ftcc
+    ctx.build_ueg(6, 1.0, 7)
+    with pytest.raises(ftcc.FTCCError) as e:          # FP64 only
+        ctx.prepare(1.0, 0.5, 4, precision="tf32", block_sparse=1)
+    assert e.value.status == ftcc.ERR_INVALID_ARG
+    with pytest.raises(ftcc.FTCCError) as e:          # Simpson integral form only
+        ctx.solve(1.0, 0.5, 5, quad=ftcc.QUAD_RK4, precision="fp64", block_sparse=1)
+    assert e.value.status == ftcc.ERR_UNSUPPORTED
+    r = ctx.solve(1.0, 0.5, 6, precision="fp64", block_sparse=1)
+    assert r["converged"]
+    d, _ = ctx.adjoint(with_rdm1=False, allow_unsupported=True)
+    assert d["status"] == ftcc.ERR_UNSUPPORTED
+    rng = np.random.default_rng(0)
+    N = 6
+    h = np.diag(rng.standard_normal(N))
+    eri = np.zeros((N, N, N, N))
+    ctx.build_generic(h, eri, np.diag(h).copy())       # no conserved charges
+    with pytest.raises(ftcc.FTCCError) as e:
+        ctx.prepare(1.0, 0.0, 4, precision="fp64", block_sparse=1)
+    assert e.value.status == ftcc.ERR_INVALID_ARG
+    ctx.build_hubbard(4, 1.0, 2.0, reference="neel")   # site basis: no conserved momentum
+    with pytest.raises(ftcc.FTCCError) as e:
+        ctx.prepare(1.0, 1.0, 4, precision="fp64", block_sparse=1)
+    assert e.value.status == ftcc.ERR_INVALID_ARG
