@@ -3,19 +3,20 @@
 Headline workload: the warm dense electron gas of 14 electrons at rs = 1,
 Theta = T/T_F = 0.5 in 57 plane waves (114 spin orbitals, no truncation),
 32 Simpson tau points, mu = mu_0 (the reference chemical potential of 14
-electrons) -- the largest configuration whose sweep keeps every tau point
-resident on one GPU.  One step = one iteration of the mixed-precision sweep
-(BF16X3 tensor-core contractions with FP32 accumulation and FP32
-amplitudes; propagators, Simpson recurrence, energy and Omega in FP64): the
-S kernel at all 32 tau points, the propagation, the energy and Omega_CC.
-value = seconds per step; the line also carries the time to a solution
-within 1e-6 Ha of the oracle (the block-sparse oracle's converged Omega),
-the FP64 GPU path's time per iteration, the roofline of the dominant kernel
-and the oracle on the host cores.  Extra fields: the 10-site Hubbard ring at
-three temperatures (mixed vs FP64 time to 1e-6 Ha), the 162-orbital gas,
+electrons).  One step = one iteration of the FP64 sweep with block-sparse
+storage (every orbital carries its own momentum and S_z, so the integrals
+and amplitudes live in charge sectors): the S kernel at all 32 tau points,
+the propagation, the energy and Omega_CC.  value = seconds per step; the
+line also carries the time to a solution within 1e-6 Ha of the oracle (the
+block-sparse oracle's converged Omega), the roofline of the dominant kernel,
+e2e through host buffers and the oracle on the host cores.  Extra fields:
+the dense schedule on the same workload (the mixed-precision tcgen05 sweep,
+its tensor TFLOP/s, time to 1e-6 Ha, adjoint and the dense FP64 estimate),
+the 162-orbital gas (block-sparse solve; dense streamed iteration), the
+10-site Hubbard ring at three temperatures (mixed vs FP64 time to 1e-6 Ha),
 the adjoint, the 64-instance batch and the RK drivers.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32] [--no-dense] [--quick]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 With N > 1 (torchrun) each rank runs its own copy of the problem
@@ -39,7 +40,7 @@ from paper_2004_01729_gb300 import workloads as wl  # noqa: E402
 METRIC = "FT-CCSD s/iteration & tensor TFLOP/s, mixed vs FP64 GPU at |dOmega|<=1e-6 Ha"
 C3 = wl.UEG_57
 WORKLOAD = ("ueg 14 electrons rs=1 Theta=0.5, 57 plane waves = 114 spin orbitals, ngrid=32 Simpson, "
-            "mu=mu_0(N=14); mixed-precision sweep (no FP64 iteration)")
+            "mu=mu_0(N=14)")
 C2_WORKLOAD = "hubbard_1d L=10 t=1 U=4 mu=2 N=20 spin orbitals, beta in {2,1,0.5}, ngrid=32 Simpson, batched"
 GOLD = os.path.join(ROOT, "tests", "golden")
 
@@ -121,9 +122,10 @@ def cpu_info():
 class Clocks:
     """Sample nvidia-smi during the timed region."""
 
-    def __init__(self):
+    def __init__(self, interval_ms=200):
         self.samples = []
         self.proc = None
+        self.interval_ms = interval_ms
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -131,7 +133,7 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                          "-lms", str(self.interval_ms), "-i", os.environ.get("LOCAL_RANK", "0")],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -169,7 +171,7 @@ class Clocks:
         reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(self.samples),
-                "interval_ms": 200, "samples_before_timed_region": getattr(self, "first", 0)}
+                "interval_ms": self.interval_ms, "samples_before_timed_region": getattr(self, "first", 0)}
 
 
 def dist_init(args):
@@ -308,15 +310,18 @@ def run_c3_iteration(args):
     ctx = ftcc.Context(0)
     ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
     mu = ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
-    ctx.prepare(C3["beta"], mu, C3["ngrid"], precision=args.precision, tau_chunk=8)
+    if args.no_dense:   # the headline path: block-sparse FP64
+        ctx.prepare(C3["beta"], mu, C3["ngrid"], **sparse_opts())
+    else:
+        ctx.prepare(C3["beta"], mu, C3["ngrid"], precision=args.precision, tau_chunk=8)
     ctx.iterate(args.warmup + args.steps)
     torch.cuda.synchronize()
     ctx.close()
 
 
 def gemm_flops_per_step(kstats, steps):
-    """2MNK summed over the contraction classes of one step."""
-    return sum(r["flops"] for r in kstats if r["name"].startswith("gemm")) / steps
+    """Algorithmic flops (2MNK per product) summed over the contraction classes of one step."""
+    return sum(r["flops"] for r in kstats if r["flops"]) / steps
 
 
 def class_table(kstats, steps):
@@ -363,17 +368,12 @@ def roofline(kstats, steps, prec, pk):
     return r
 
 
-def run_gpu(args, rank, world):
-    import torch
-    from paper_2004_01729_gb300 import ftcc
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
+def bench_dense_mixed(ftcc, torch, dev, world, args, pk, gold):
+    """The dense schedule on the headline workload: the mixed-precision
+    sweep (tcgen05 contractions over every element of the 114-orbital
+    tensors), its solve, adjoint, timed iterations, kernel classes and
+    roofline, the FP64 dense estimate and e2e."""
     prec = args.precision
-    pk = measure_peaks(torch)
-    gold = c3_gold()
-    extra = {}
-
-    # ---- headline: the 114-spin-orbital gas
     ctx = ftcc.Context(dev)
     ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
     mu = gold["mu"] if gold else ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
@@ -415,7 +415,8 @@ def run_gpu(args, rank, world):
     ctx.iterate(max(1, args.warmup))
     barrier(world)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dsteps = min(args.steps, 10)   # ~1.2 s per dense step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(dsteps)]
     with Clocks() as clk:
         for a, b in ev:
             a.record(st)
@@ -433,7 +434,7 @@ def run_gpu(args, rank, world):
     ctx.profile(False)
     ctx.close()
     t_steps = barrier_max(t_steps, world)
-    s_per_iter = t_steps / args.steps
+    s_per_iter = t_steps / dsteps
     fl = flops_per_iteration(114, 114, C3["ngrid"])
     roof = roofline(kstats, prof_steps, prec, pk)
 
@@ -496,10 +497,143 @@ def run_gpu(args, rank, world):
         del pin
         ce.close()
 
-    # ---- extras
+    return {"workload": WORKLOAD + "; dense storage (every element), " + prec + " tensor-core contractions",
+            "s_per_iteration": s_per_iter, "steps": dsteps,
+            "tensor_tflops_per_iteration": gemm_flops_per_step(kstats, prof_steps) / s_per_iter / 1e12,
+            "algorithmic_flops_per_iteration": gemm_flops_per_step(kstats, prof_steps),
+            "dense_schedule_flops_per_iteration": fl,
+            "flops_note": "algorithmic = 2MNK summed over the contractions the iteration executes (the ladders "
+                          "over unordered index pairs); dense_schedule = the five O(N^6) contractions of the "
+                          "unpacked schedule",
+            "time_to_1e-6": solve, "adjoint_mixed": adjoint, "fp64_gpu": fp64,
+            "mixed_over_fp64_time_to_solution": (fp64["estimated_s_to_solution"] / t_sol
+                                                 if fp64 and "estimated_s_to_solution" in fp64 else None),
+            "roofline": roof, "kernels": class_table(kstats, prof_steps), "e2e": e2e,
+            "gpu_launches_per_iteration": k_iter, "clocks": clk.summary()}
+
+
+def roofline_sparse(kstats, steps, pk):
+    """Roofline of the dominant kernel class of the block-sparse FP64
+    iteration: the sector products against the FP64 rate of this GPU
+    (cuBLAS DGEMM 8192^3 measured live; the FP64 FMA pipe, "alu"), an
+    elementwise class against the measured HBM copy bandwidth."""
+    dom = max(kstats, key=lambda r: r["ms"])
+    if dom["flops"]:
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        peak = pk["fp64_tflops"]["burst"]
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": "FP64 FMA pipe: torch.matmul float64 8192^3 (cuBLAS DGEMM), measured live (of measured)"}
+    else:
+        ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+             "peak_source": "HBM copy (of measured)"}
+    r.update({"traffic": None,
+              "traffic_note": "DRAM bytes per launch come from ncu captures kept with the kernel profiles; "
+                              "not measurable inside this run",
+              "kernel": dom["name"], "launches_per_step": dom["launches"] / steps,
+              "avg_launch_ms": dom["ms"] / dom["launches"],
+              "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
+              "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+              "timed_with": "CUDA events around every launch inside the per-iteration graph "
+                            "(a profiled pass after the timed steps)"})
+    return r
+
+
+def sparse_opts():
+    return dict(precision="fp64", block_sparse=1, tol_omega=1e-11, tol_amp=1e-9, max_iter=100)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2004_01729_gb300 import ftcc
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    pk = measure_peaks(torch)
+    gold = c3_gold()
+    extra = {}
+
+    # ---- headline: the 114-spin-orbital gas with block-sparse storage, FP64
+    ctx = ftcc.Context(dev)
+    ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+    mu = gold["mu"] if gold else ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
+    ctx.solve(C3["beta"], mu, C3["ngrid"], **sparse_opts())   # first solve: sizes and captures (untimed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol = ctx.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **sparse_opts())
+    torch.cuda.synchronize()
+    t_sol = time.perf_counter() - t0
+    solve = {"s_total": t_sol, "iterations": sol["iterations"], "converged": bool(sol["converged"]),
+             "omega": sol["omega"], "abs_dOmega_vs_oracle": abs(sol["omega"] - gold["omega"]) if gold else None,
+             "oracle": "block-sparse oracle, converged to |dOmega_CC| < 1e-11" if gold else None,
+             "how": "ft_ccsd_solve FP64 block-sparse from s = 0 to |dOmega_CC| < 1e-11, host-timed"}
+    # timed steps: W warm-up iterations, then K iterations each bracketed by
+    # CUDA events on the library stream (one captured graph per iteration);
+    # the amplitudes (32 x 114^3 x 8 B = 379 MB each for s and S) exceed the
+    # 129 MB L2, so no flush is needed
+    ctx.prepare(C3["beta"], mu, C3["ngrid"], **sparse_opts())
+    st = ctx.stream
+    ctx.iterate(max(1, args.warmup))
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(interval_ms=20) as clk:   # steps of ~13 ms: sample every 20 ms
+        for a, b in ev:
+            a.record(st)
+            ctx.iterate(1)
+            b.record(st)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    k_iter = ctx.iterate(0)["kernels_per_iter"]
+    ctx.profile(True)
+    prof_steps = 3
+    ctx.iterate(prof_steps)
+    kstats = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    t_steps = barrier_max(t_steps, world)
+    s_per_iter = t_steps / args.steps
+    roof = roofline_sparse(kstats, prof_steps, pk)
+
+    # e2e through the public API with host buffers: the gas's Hamiltonian and
+    # its orbital charges from pinned host memory (build_integrals GENERIC
+    # with charges), the block-sparse FP64 solve to convergence (the state
+    # read back every iteration) and the result on the host
+    e2e = None
+    if not args.no_e2e:
+        ce = ftcc.Context(dev)
+        ce.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+        h_np, eri_np, eps_np = ce.get_system()
+        ch_np, md_np = ce.get_charges()
+        pin = [torch.from_numpy(a).pin_memory() for a in (h_np, eri_np, eps_np)]
+        del h_np, eri_np, eps_np
+        # first pass sizes the allocator and the graphs (untimed)
+        ce.build_generic(pin[0].numpy(), pin[1].numpy(), pin[2].numpy(), ch_np, md_np)
+        ce.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **sparse_opts())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ce.build_generic(pin[0].numpy(), pin[1].numpy(), pin[2].numpy(), ch_np, md_np)
+        r = ce.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **sparse_opts())
+        torch.cuda.synchronize()
+        t_e = barrier_max(time.perf_counter() - t0, world)
+        h2d = sum(a.numel() * 8 for a in pin) + ch_np.nbytes + md_np.nbytes
+        e2e = {"value": t_e / r["iterations"], "unit": "s/iteration", "h2d_bytes_per_step": h2d / r["iterations"],
+               "d2h_bytes_per_step": 8 * (8 + 256) + 112 / r["iterations"],
+               "what": "build_integrals(GENERIC with charges: pinned host h, <pq||rs> N^4, eps) + ft_ccsd_solve "
+                       "(FP64 block-sparse, to convergence) + result to the host, divided by the iterations",
+               "s_total": t_e, "iterations": r["iterations"],
+               "abs_dOmega_vs_oracle": abs(r["omega"] - gold["omega"]) if gold else None}
+        del pin
+        ce.close()
+
+    # ---- the dense schedule on the same workload, the 162-orbital gas and the rest
+    dense = None
+    if not args.no_dense:
+        dense = bench_dense_mixed(ftcc, torch, dev, world, args, pk, gold)
+        extra["dense_mixed"] = dense
     if not args.quick:
-        extra["hubbard10"] = bench_hubbard10(ftcc, torch, dev, world, args)
         extra["ueg81_162_spin_orbitals"] = bench_ueg81(ftcc, torch, dev, world, args)
+        extra["hubbard10"] = bench_hubbard10(ftcc, torch, dev, world, args)
         extra.update(bench_small_extras(ftcc, torch, dev, world, args))
         extra["dense_ladder_gemm"] = bench_dense_gemm(ftcc, torch, dev, world, pk)
 
@@ -514,24 +648,20 @@ def run_gpu(args, rank, world):
             cpu = {"value": statistics.median(vals), "unit": "s/iteration", "cores": smp.cores, "kind": "oracle",
                    "sample": smp.describe() + "; median of 3", "samples_s_per_iteration": vals,
                    "cpu_count": ci["cpu_count"], "cpu_model": ci["model"]}
+        dts = dense["time_to_1e-6"]["s_total"] if dense and dense.get("time_to_1e-6") else None
         line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_iter * 1e3,
-                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": prec, "tau_chunk": 8,
-                           "l2": "inputs larger than L2: 21 GB of FP32 amplitudes and 8 GB of integral blocks "
-                                 "are read every step (L2 129 MB), no flush"},
-                "tensor_tflops_per_iteration": gemm_flops_per_step(kstats, prof_steps) / s_per_iter / 1e12,
+                "config": {"workload": WORKLOAD, "storage": "block-sparse: momentum/spin charge sectors, FP64",
+                           "l2": "inputs larger than L2: s and S are 379 MB each (FP64, 32 x 114^3), the integral "
+                                 "blocks 12 x 12 MB; L2 129 MB, no flush"},
                 "algorithmic_flops_per_iteration": gemm_flops_per_step(kstats, prof_steps),
-                "dense_schedule_flops_per_iteration": fl,
-                "flops_note": "algorithmic = 2MNK summed over the contractions the iteration executes (the "
-                              "ladders over unordered index pairs); dense_schedule = the five O(N^6) "
-                              "contractions of the unpacked schedule",
+                "flops_note": "2 sum_s rows_s^3 over the charge sectors of the five products of two four-index "
+                              "factors, every tau point; the dense schedule's 7.0e14 flops per iteration are in "
+                              "extra.dense_mixed",
                 "time_to_1e-6": solve,
-                "adjoint_mixed": adjoint,
-                "fp64_gpu": fp64,
-                "mixed_over_fp64_time_to_solution": (fp64["estimated_s_to_solution"] / t_sol
-                                                     if fp64 and "estimated_s_to_solution" in fp64 else None),
+                "fp64_block_sparse_vs_dense_mixed_time_to_solution": (dts / t_sol if dts else None),
                 "peaks": pk, "roofline": roof, "kernels": class_table(kstats, prof_steps),
                 "e2e": e2e, "gpu_launches": k_iter * args.steps, "clocks": clk.summary()}
         line.update(extra)
@@ -616,8 +746,9 @@ def bench_hubbard10(ftcc, torch, dev, world, args):
 
 
 def bench_ueg81(ftcc, torch, dev, world, args):
-    """The 162-orbital gas (81 plane waves, 40 tau points), streamed over
-    tau: one mixed iteration from s = 0 and the peak device memory."""
+    """The 162-orbital gas (81 plane waves, 40 tau points): one dense mixed
+    iteration from s = 0 streamed over tau (with the peak device memory),
+    and the block-sparse FP64 iteration and solve."""
     if args.no_ueg81 or world != 1:
         return None
     c = wl.UEG_81
@@ -636,11 +767,43 @@ def bench_ueg81(ftcc, torch, dev, world, args):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     fl = flops_per_iteration(r["n_occ"], r["n_vir"], c["ngrid"])
-    out = {"precision": args.precision, "s_per_iteration": t, "tensor_tflops": fl / t / 1e12,
-           "algorithmic_flops_per_iteration": fl, "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
-           "note": "first iteration from s = 0 (includes the tile autotuning of its shapes); S kept for one tau window"}
+    dense = {"precision": args.precision, "s_per_iteration": t, "tensor_tflops": fl / t / 1e12,
+             "dense_schedule_flops_per_iteration": fl,
+             "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
+             "note": "dense storage, tau-streamed: first iteration from s = 0 (includes the tile autotuning of its "
+                     "shapes); S kept for one tau window"}
     ctx.close()
-    return out
+    # block-sparse FP64: timed iterations and a solve to convergence against
+    # the block-sparse oracle's converged Omega
+    gp = os.path.join(GOLD, "oracle_ueg81.json")
+    g81 = json.load(open(gp)) if os.path.exists(gp) else None
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    ctx = ftcc.Context(dev)
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    ctx.solve(c["beta"], mu, c["ngrid"], trunc_thr=c["thr"], **sparse_opts())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs = ctx.solve(c["beta"], mu, c["ngrid"], trunc_thr=c["thr"], allow_unconverged=True, **sparse_opts())
+    torch.cuda.synchronize()
+    t_sol = time.perf_counter() - t0
+    ctx.prepare(c["beta"], mu, c["ngrid"], trunc_thr=c["thr"], **sparse_opts())
+    st = ctx.stream
+    ctx.iterate(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    ctx.iterate(10)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sparse = {"s_per_iteration": e0.elapsed_time(e1) / 1e3 / 10, "solve_s_total": t_sol,
+              "iterations": rs["iterations"], "converged": bool(rs["converged"]), "omega": rs["omega"],
+              "abs_dOmega_vs_oracle": abs(rs["omega"] - g81["omega"]) if g81 else None,
+              "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,
+              "how": "FP64 block-sparse; 10 iterations timed with CUDA events after 3 warm-up; the solve from s = 0 "
+                     "to |dOmega_CC| < 1e-11 host-timed"}
+    ctx.close()
+    return {"workload": "ueg 14 electrons rs=1 Theta=1, 81 plane waves = 162 spin orbitals, ngrid=40, mu=mu_0",
+            "block_sparse_fp64": sparse, "dense_first_iteration": dense}
 
 
 def bench_small_extras(ftcc, torch, dev, world, args):
@@ -762,8 +925,8 @@ def bench_dense_gemm(ftcc, torch, dev, world, pk):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -773,6 +936,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the lambda sweep of the headline workload")
     ap.add_argument("--quick", action="store_true", help="headline only, no extra workloads")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense mixed-precision sweep")
     ap.add_argument("--c3-iterations", action="store_true",
                     help="prepare the headline workload and run W + K iterations (profiler launch lists)")
     ap.add_argument("--gemm", default=None, help="B,M,N,K: time the tensor-core GEMM alone on that shape")

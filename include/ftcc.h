@@ -115,13 +115,21 @@ typedef enum { FTCC_REF_KSPACE_RHF = 0, FTCC_REF_NEEL_SITE = 1, FTCC_REF_UHF_SIT
  *     spin conservation, no q = 0 term; eps = zero-temperature HF energies of
  *     the n_elec/2 lowest plane waves per spin (Sec. IV.B, App. D).
  *   GENERIC: host FP64 arrays h[N*N], eri[N^4] (antisymmetrised <pq||rs>),
- *     eps[N]; copied. */
+ *     eps[N]; copied.  Optionally charge[N*4] (host int): a conserved
+ *     integer charge vector per spin orbital (momentum components, S_z ...),
+ *     component k taken modulo charge_mod[k] when charge_mod is given and
+ *     charge_mod[k] > 0; every h_pq and <pq||rs> that does not conserve it
+ *     must vanish.  It enables the block_sparse option when all N charges
+ *     differ.  NULL: none.
+ * UEG and the k-space Hubbard ring (KSPACE_RHF) carry their momentum and
+ * S_z as charges (ftcc_get_charges); the site-basis references carry none. */
 typedef struct {
   int kind;
   int L; double t, U; int pbc;          /* HUBBARD_1D */
   int n_elec; double rs; int n_pw;      /* UEG */
   int N; const double* h; const double* eri; const double* eps; /* GENERIC */
   int reference;                        /* HUBBARD_1D: ftcc_reference (0 = KSPACE_RHF) */
+  const int* charge; const int* charge_mod;   /* GENERIC: optional conserved charges [N*4], [4] */
 } ftcc_system;
 
 /* Solver options; pass NULL for the defaults in brackets.
@@ -253,6 +261,11 @@ int ftcc_num_orbitals(const ftcc_ctx* ctx);
 /* Copy the built eps[N], h[N*N] and, if eri != NULL, <pq||rs>[N^4] to host
  * buffers (any may be NULL). */
 ftcc_status ftcc_get_system(ftcc_ctx* ctx, double* eps, double* h, double* eri);
+
+/* Copy the conserved orbital charges of the built system: charge[N*4] and
+ * charge_mod[4] (0 = not periodic); either may be NULL.  FTCC_ERR_STATE when
+ * the system has none. */
+ftcc_status ftcc_get_charges(ftcc_ctx* ctx, int* charge, int* charge_mod);
 
 /* Chemical potential mu0 with sum_p n_p(beta, mu0) = n_elec for the
  * reference energies eps (the reference-system electron count used to fix

@@ -2744,6 +2744,11 @@ ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
         const int g = p % M;
         c->charge.push_back({nvec[3 * g], nvec[3 * g + 1], nvec[3 * g + 2], p / M});
       }
+    } else if (s->kind == FTCC_SYS_GENERIC && s->charge) {
+      for (int p = 0; p < N; ++p)
+        c->charge.push_back({s->charge[4 * p], s->charge[4 * p + 1], s->charge[4 * p + 2], s->charge[4 * p + 3]});
+      if (s->charge_mod)
+        for (int k = 0; k < 4; ++k) c->charge_mod[k] = std::max(0, s->charge_mod[k]);
     }
     c->N = N;
     return FTCC_OK;
@@ -2761,6 +2766,18 @@ ftcc_status ftcc_get_system(ftcc_ctx* c, double* eps, double* h, double* eri) {
     sync(c);
     return FTCC_OK;
   });
+}
+
+ftcc_status ftcc_get_charges(ftcc_ctx* c, int* charge, int* charge_mod) {
+  if (!c) return FTCC_ERR_INVALID_ARG;
+  if (c->N == 0 || static_cast<int>(c->charge.size()) != c->N)
+    return fail(c, FTCC_ERR_STATE, "the system carries no orbital charges");
+  if (charge)
+    for (int p = 0; p < c->N; ++p)
+      for (int k = 0; k < 4; ++k) charge[4 * p + k] = c->charge[p][k];
+  if (charge_mod)
+    for (int k = 0; k < 4; ++k) charge_mod[k] = c->charge_mod[k];
+  return FTCC_OK;
 }
 
 ftcc_status ftcc_reference_mu(ftcc_ctx* c, double beta, double n_elec, double* mu) {

@@ -27,7 +27,7 @@ class System(C.Structure):
     _fields_ = [("kind", C.c_int), ("L", C.c_int), ("t", C.c_double), ("U", C.c_double), ("pbc", C.c_int),
                 ("n_elec", C.c_int), ("rs", C.c_double), ("n_pw", C.c_int), ("N", C.c_int),
                 ("h", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double)),
-                ("reference", C.c_int)]
+                ("reference", C.c_int), ("charge", C.POINTER(C.c_int)), ("charge_mod", C.POINTER(C.c_int))]
 
 
 class Options(C.Structure):
@@ -78,6 +78,7 @@ _SIGS = [
     ("build_integrals", C.c_int, [C.c_void_p, C.POINTER(System)]),
     ("ftcc_num_orbitals", C.c_int, [C.c_void_p]),
     ("ftcc_get_system", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ftcc_get_charges", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ftcc_reference_mu", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     ("ftcc_mu_for_n", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(Options),
                                 C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
@@ -225,13 +226,32 @@ class Context:
         self._check(self.lib.build_integrals(self.h, C.byref(sysd)), "build_integrals")
         return self.num_orbitals()
 
-    def build_generic(self, h, eri, eps):
+    def build_generic(self, h, eri, eps, charge=None, charge_mod=None):
+        """GENERIC system from host arrays; charge [N, 4] (int) and charge_mod [4]
+        optionally give every orbital's conserved charge (block_sparse)."""
         h = np.ascontiguousarray(h, dtype=np.float64)
         eri = np.ascontiguousarray(eri, dtype=np.float64)
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         sysd = System(kind=SYS_GENERIC, N=len(eps), h=_dptr(h), eri=_dptr(eri), eps=_dptr(eps))
+        keep = []
+        if charge is not None:
+            ch = np.ascontiguousarray(charge, dtype=np.int32).reshape(len(eps), 4)
+            keep.append(ch)
+            sysd.charge = ch.ctypes.data_as(C.POINTER(C.c_int))
+            if charge_mod is not None:
+                md = np.ascontiguousarray(charge_mod, dtype=np.int32).reshape(4)
+                keep.append(md)
+                sysd.charge_mod = md.ctypes.data_as(C.POINTER(C.c_int))
         self._check(self.lib.build_integrals(self.h, C.byref(sysd)), "build_integrals")
         return self.num_orbitals()
+
+    def get_charges(self):
+        """ftcc_get_charges: (charge [N, 4], charge_mod [4]) of the built system."""
+        N = self.num_orbitals()
+        ch = np.empty((N, 4), dtype=np.int32)
+        md = np.empty(4, dtype=np.int32)
+        self._check(self.lib.ftcc_get_charges(self.h, ch.ctypes.data, md.ctypes.data), "ftcc_get_charges")
+        return ch, md
 
     def build(self, cfg):
         if cfg["kind"] == "hubbard":

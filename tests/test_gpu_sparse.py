@@ -143,3 +143,29 @@ def test_sparse_argument_checks(ctx):
     with pytest.raises(ftcc.FTCCError) as e:
         ctx.prepare(1.0, 1.0, 4, precision="fp64", block_sparse=1)
     assert e.value.status == ftcc.ERR_INVALID_ARG
+
+
+def test_generic_system_with_charges(ctx):
+    """A GENERIC system built from the gas's host Hamiltonian with its orbital
+    charges (ftcc_get_charges) solves with block_sparse to the same Omega as
+    the built-in gas; a non-unique charge set is refused."""
+    from paper_2004_01729_gb300 import ftcc
+    n_elec, rs, n_pw, beta, ng = 14, 1.0, 19, 2.0, 8
+    ctx.build_ueg(n_elec, rs, n_pw)
+    mu = ctx.reference_mu(beta, float(n_elec))
+    ref = ctx.solve(beta, mu, ng, precision="fp64", block_sparse=1)
+    h, eri, eps = ctx.get_system()
+    ch, md = ctx.get_charges()
+    assert ch.shape == (2 * n_pw, 4) and len({tuple(r) for r in ch}) == 2 * n_pw
+    ctx.build_generic(h, eri, eps, ch, md)
+    r = ctx.solve(beta, mu, ng, precision="fp64", block_sparse=1)
+    assert abs(r["omega"] - ref["omega"]) < 1e-12
+    ch2 = ch.copy()
+    ch2[1] = ch2[0]
+    ctx.build_generic(h, eri, eps, ch2, md)
+    with pytest.raises(ftcc.FTCCError) as e:
+        ctx.prepare(beta, mu, ng, precision="fp64", block_sparse=1)
+    assert e.value.status == ftcc.ERR_INVALID_ARG
+    ctx.build_generic(h, eri, eps)
+    with pytest.raises(ftcc.FTCCError):
+        ctx.get_charges()
