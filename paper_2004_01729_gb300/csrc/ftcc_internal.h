@@ -291,6 +291,56 @@ struct SecGemmArgs {
   const int4* sec;       // (entry offset, rows, K offset, K count)
   const int4* work;      // (sector, row tile start, column tile start, 0)
 };
+// Transposed sector products (see sparse.cu): D[orow(e_o)][k] += alpha
+// sum_{e_s} G[gpos(e_o, e_s)] A[srow(e_s)][k]; dx = 0: D fixed, the kernel
+// sums the nx slices of G and A.
+struct SecTnArgs {
+  double* D;
+  long long dx;
+  const double* G;
+  long long gx;
+  const double* A;
+  long long ax;
+  double alpha;
+  int n, nx;
+  int swapD, swapA;
+  long long g0, g1, g2, g3;   // gpos = p_o g0 + q_o g1 + p_s g2 + q_s g3
+  const int2* ent;
+  const int* kl;
+  const int4* sec;
+  const int4* work;
+};
+// Forward values and cotangents of the block-sparse S-kernel transpose ([nx][N^3] / [nx][N]).
+struct SpVjpArgs {
+  const double *t1, *t2;
+  const double *Ft, *Ft2, *Fme, *Fae, *Fmi;          // forward vectors
+  const double *S1b;                                 // cotangent of S1
+  const double *Rb, *w1b, *wabb, *wrb, *tab, *tpb, *trb, *xpb;
+  SpBlocks V;
+  const int16_t* imp;
+  int n;
+  double *Ftb, *Ft2b, *Faeb, *Fmib, *Fmeb;           // vector cotangents (written)
+  double *t1b, *t2b;                                 // outputs
+};
+cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, int n, int nx, double* Rb, cudaStream_t st);
+cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st);
+cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st);
+cudaError_t launch_sp_t2bar(const SpVjpArgs& v, int nx, cudaStream_t st);
+// Vbar[11] in SpBlocks order (null entries skipped), fbar[4] = ov, vv, oo, vo (null skipped); cz may be null
+cudaError_t launch_sp_fixed_bar(const SpVjpArgs& v, const double* S2b, const double* cz, double* const* Vbar,
+                                double* const* fbar, int nx, cudaStream_t st);
+cudaError_t launch_sp_swap12_add(const double* in, int n, double* out, cudaStream_t st);   // out[a][b][c] += in[a][c][b]
+cudaError_t launch_sp_eri_adjoint(const double* bar, const int16_t* imp, int n, const double* f0, const double* f1,
+                                  const double* f2, const double* f3, double* gamma, cudaStream_t st);
+cudaError_t launch_sp_energy_bar(const double* t1, const double* t2, const double* cz, const int16_t* imp, int n,
+                                 int ng, double* Voovvb, double* fovb, cudaStream_t st);
+// Do[q] / Dv[q] += sum of I * Ib over the elements with orbital q in a hole-like / particle-like
+// slot (bit k of cls set = slot k particle-like; slot 3 is the implied one)
+cudaError_t launch_sp_slot_sums(const double* I, const double* Ib, const int16_t* imp, int n, int cls, double* Do,
+                                double* Dv, cudaStream_t st);
+// out[x][m] = fov[m] + sum_n s1[x][n] <mn||mn>  (F_me, and dE/ds1 of Eq. E)
+cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voovv, int n, int nx, double* out,
+                          cudaStream_t st);
 cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
                           double* tp, double* tr, double* xp, cudaStream_t st);
 cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st);

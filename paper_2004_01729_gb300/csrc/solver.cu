@@ -871,6 +871,10 @@ struct Solver {
     for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R}) ensure(h_, *q, x * n3 * sizeof(T));
     for (Buf* q : {&Fme, &Fae, &Fmi, &Ft, &Ft2}) ensure(h_, *q, x * n * sizeof(T));
     ensure(h_, Vp, n3 * sizeof(T));
+    // cotangents of the transpose (sparse_vjp)
+    for (Buf* q : {&bR, &bta, &btt, &bY, &bX, &bWmnij, &bWabef, &bWmbej}) ensure(h_, *q, x * n3 * sizeof(T));
+    for (Buf* q : {&bFme, &bFae, &bFmi, &bFt, &bFt2}) ensure(h_, *q, x * n * sizeof(T));
+    ensure(h_, bP, n3 * sizeof(T));
     if constexpr (sizeof(T) == 8)
       CU(launch_sp_swap12(V("zmnef"), no, static_cast<double*>(Vp.p), st()));
   }
@@ -967,6 +971,114 @@ struct Solver {
       sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
       timed_launch(kClsScatter, 6 * slice, 0.0,
                    [&] { CU(launch_sp_s2(pR, VB.vvoo, imp, n, nx, S2c, st())); });
+    }
+  }
+
+  // One transposed sector product (see SecTnArgs): with fixed D (dx = 0)
+  // the slices are summed inside the kernel.
+  void sector_tn(const SecTab& tab, double* D, long long dx, const double* G, const double* A, long long ax,
+                 double alpha, int swapD, int swapA, long long g0, long long g1, long long g2, long long g3) {
+    const long long n3 = static_cast<long long>(no) * no * no;
+    SecTnArgs g{};
+    g.D = D;
+    g.dx = dx;
+    g.G = G;
+    g.gx = n3;
+    g.A = A;
+    g.ax = ax;
+    g.alpha = alpha;
+    g.n = no;
+    g.nx = nx;
+    g.swapD = swapD;
+    g.swapA = swapA;
+    g.g0 = g0;
+    g.g1 = g1;
+    g.g2 = g2;
+    g.g3 = g3;
+    g.ent = static_cast<const int2*>(tab.ent.p);
+    g.kl = static_cast<const int*>(tab.kl.p);
+    g.sec = static_cast<const int4*>(tab.sec.p);
+    g.work = static_cast<const int4*>(tab.work.p);
+    timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(double), tab.flops * nx,
+                 [&] { CU(launch_sector_tn(g, tab.nwork, st())); });
+  }
+
+  // Transpose of sparse_s_kernel: (u1, u2) = cotangents of (S1, S2) ->
+  // (t1bar, t2bar) = cotangents of (s1, s2); with want_fixed_bar the
+  // cotangents of the integral and Fock blocks accumulate in fixed_bar.
+  // The forward intermediates are recomputed first (S lands in t1bar /
+  // t2bar and is overwritten).  Each product C += alpha A B of the forward
+  // pass gives Abar += alpha Cbar B and Bbar += alpha Cbar^T A.
+  void sparse_vjp(const T* t1c, const T* t2c, const T* u1, const T* u2, T* t1bar, T* t2bar, int nxcur) {
+    if constexpr (sizeof(T) == 8) {
+      sparse_s_kernel(t1c, t2c, t1bar, t2bar, nxcur);
+      const int n = no;
+      const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
+      const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
+      const SpBlocks VB = sp_blocks();
+      double *Rb = (double*)bR.p, *tab_ = (double*)bta.p, *tpb = (double*)btt.p, *trb = (double*)bY.p,
+             *xpb = (double*)bX.p, *w1b = (double*)bWmnij.p, *wabb = (double*)bWabef.p, *wrb = (double*)bWmbej.p;
+      for (double* q : {tab_, tpb, trb, xpb, w1b, wabb, wrb})
+        CU(cudaMemsetAsync(q, 0, nx * n3 * sizeof(double), st()));
+      const double *ta_ = (double*)ta.p, *tp_ = (double*)tt.p, *tr_ = (double*)Y.p, *xp_ = (double*)X.p,
+                   *w1_ = (double*)Wmnij.p, *wab_ = (double*)Wabef.p, *wr_ = (double*)Wmbej.p;
+      timed_launch(kClsScatter, 2.0 * nx * n3 * 8, 0.0, [&] { CU(launch_sp_s2_t(u2, imp, n, nx, Rb, st())); });
+      // ring: R += tr wr (rows (i,a) | (j,b) swapped, output (n2, 1, 0, n))
+      sector_tn(b->sdiff, trb, n3, Rb, wr_, n3, 1.0, 0, 1, n2, 1, 0, n);
+      sector_tn(b->sdiff, wrb, n3, Rb, tr_, n3, 1.0, 1, 0, 0, n, n2, 1);
+      // particle ladder: R += 1/8 ta wab
+      sector_tn(b->ssum, tab_, n3, Rb, wab_, n3, 0.125, 0, 0, n2, n, 1, 0);
+      sector_tn(b->ssum, wabb, n3, Rb, ta_, n3, 0.125, 0, 0, 1, 0, n2, n);
+      // hole ladder: R += 1/8 w1 tp
+      sector_tn(b->ssum, w1b, n3, Rb, tp_, n3, 0.125, 0, 0, n2, n, 1, 0);
+      sector_tn(b->ssum, tpb, n3, Rb, w1_, n3, 0.125, 0, 0, 1, 0, n2, n);
+      // W_mbej: wr -= xp Vp;  W_mnij: w1 += 1/2 ta <mn||ef>
+      sector_tn(b->sdiff, xpb, n3, wrb, static_cast<const double*>(Vp.p), 0, -1.0, 0, 0, n2, n, 1, 0);
+      sector_tn(b->ssum, tab_, n3, w1b, VB.oovv, 0, 0.5, 0, 0, n2, n, 1, 0);
+      double* Vbar[11] = {nullptr};
+      double* fbar[4] = {nullptr};
+      if (want_fixed_bar) {
+        const char* eri_L[11] = {"zmnef", "zmbef", "zmnie", "zmnij", "zabef", "zmbej",
+                                 "zmnej", "zmaie", "zabij", "zabej", "zmbij"};
+        for (int k = 0; k < 11; ++k) Vbar[k] = fixed_adjoint(V(eri_L[k]));
+        const char* f_L[4] = {"zme", "zae", "zmi", "zai"};
+        for (int k = 0; k < 4; ++k) fbar[k] = fixed_adjoint(F(f_L[k]));
+        double* Vpb = (double*)bP.p;
+        CU(cudaMemsetAsync(Vpb, 0, n3 * sizeof(double), st()));
+        sector_tn(b->sdiff, Vpb, 0, wrb, xp_, n3, -1.0, 0, 0, 1, 0, n2, n);
+        CU(launch_sp_swap12_add(Vpb, n, Vbar[0], st()));
+        sector_tn(b->ssum, Vbar[0], 0, w1b, ta_, n3, 0.5, 0, 0, 1, 0, n2, n);
+      }
+      SpVjpArgs va{};
+      va.t1 = t1c;
+      va.t2 = t2c;
+      va.Ft = (double*)Ft.p;
+      va.Ft2 = (double*)Ft2.p;
+      va.Fme = (double*)Fme.p;
+      va.Fae = (double*)Fae.p;
+      va.Fmi = (double*)Fmi.p;
+      va.S1b = u1;
+      va.Rb = Rb;
+      va.w1b = w1b;
+      va.wabb = wabb;
+      va.wrb = wrb;
+      va.tab = tab_;
+      va.tpb = tpb;
+      va.trb = trb;
+      va.xpb = xpb;
+      va.V = VB;
+      va.imp = imp;
+      va.n = n;
+      va.Ftb = (double*)bFt.p;
+      va.Ft2b = (double*)bFt2.p;
+      va.Faeb = (double*)bFae.p;
+      va.Fmib = (double*)bFmi.p;
+      va.Fmeb = (double*)bFme.p;
+      va.t1b = t1bar;
+      va.t2b = t2bar;
+      timed_launch(kClsOther, 12.0 * nx * n3 * 8, 0.0, [&] { CU(launch_sp_vjp_vectors(va, nx, st())); });
+      timed_launch(kClsScatter, 12.0 * nx * n3 * 8, 0.0, [&] { CU(launch_sp_t2bar(va, nx, st())); });
+      if (want_fixed_bar) CU(launch_sp_fixed_bar(va, u2, nullptr, Vbar, fbar, nx, st()));
     }
   }
 
@@ -1164,6 +1276,10 @@ struct Solver {
   // want_fixed_bar the adjoints of the integral and Fock blocks accumulate in
   // fixed_bar (not cleared here).
   void vjp(const T* t1c, const T* t2c, T* w1, T* w2, T* t1bar, T* t2bar, int nxcur) {
+    if (sp) {
+      sparse_vjp(t1c, t2c, w1, w2, t1bar, t2bar, nxcur);
+      return;
+    }
     const long long o = no, v = nv, x = static_cast<long long>(nxcur) * nz;
     // adjoint buffers sized like the chunk intermediates
     Buf* pairs[][2] = {{&bta, &ta}, {&bX, &X}, {&bWmnij, &Wmnij}, {&bWabef, &Wabef}, {&bWmbej, &Wmbej},
@@ -2324,8 +2440,9 @@ template <class T>
 int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   ftcc_ctx* h = B.home;
   constexpr size_t es = sizeof(T);
-  const long long o = B.no, v = B.nv, ng = B.ng, nz = B.nz;
-  const long long n1 = nz * ng * o * v, n2 = nz * ng * o * o * v * v;
+  const long long ng = B.ng, nz = B.nz;
+  const long long e1 = s.n1(), e2 = s.n2();   // elements per tau point (dense or block-sparse storage)
+  const long long n1 = nz * ng * e1, n2 = nz * ng * e2;
   ensure(h, B.m1, n1 * es);
   ensure(h, B.m2, n2 * es);
   ensure(h, B.mn1, n1 * es);
@@ -2348,15 +2465,21 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   // zero so that its (unused) multipliers stay finite
   for (long long z = 0; z < nz; ++z)
     if (!B.live_host[z]) {
-      CU(cudaMemsetAsync(static_cast<T*>(s.t1.p) + z * ng * o * v, 0, ng * o * v * es, h->st));
-      CU(cudaMemsetAsync(static_cast<T*>(s.t2.p) + z * ng * o * o * v * v, 0, ng * o * o * v * v * es, h->st));
+      CU(cudaMemsetAsync(static_cast<T*>(s.t1.p) + z * ng * e1, 0, ng * e1 * es, h->st));
+      CU(cudaMemsetAsync(static_cast<T*>(s.t2.p) + z * ng * e2, 0, ng * e2 * es, h->st));
     }
   // dE/ds1 without the weight: f_kc + sum_jb <kj||cb> s_j^b   (Eq. E)
   s.nx = s.ng;
   T* dE1 = static_cast<T*>(B.dE1.p);
-  s.scatter(dE1, "zxkc", s.F("zkc"), "zkc", 1.0, 0.0, "");
-  s.contract({dE1, "zxkc"}, 1.0, Tn<const T>{s.V("zkjcb"), "zkjcb", true},
-             Tn<const T>{static_cast<const T*>(s.t1.p), "zxjb"});
+  if constexpr (sizeof(T) == 8) {
+    if (s.sp)
+      CU(launch_sp_fme(static_cast<const double*>(s.t1.p), s.F("zkc"), s.V("zkjcb"), s.no, s.ng, dE1, h->st));
+  }
+  if (!s.sp) {
+    s.scatter(dE1, "zxkc", s.F("zkc"), "zkc", 1.0, 0.0, "");
+    s.contract({dE1, "zxkc"}, 1.0, Tn<const T>{s.V("zkjcb"), "zkjcb", true},
+               Tn<const T>{static_cast<const T*>(s.t1.p), "zxjb"});
+  }
   CU(cudaStreamSynchronize(h->st));
   PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
   a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
@@ -2369,7 +2492,7 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
     CU(launch_propagate_t(static_cast<const T*>(B.m2.p), static_cast<T*>(B.u2.p), a2, h->st));
     for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
       const int nx = std::min(s.nxc, s.ng - x0);
-      const long long f1 = x0 * o * v, f2 = x0 * o * o * v * v;
+      const long long f1 = x0 * e1, f2 = x0 * e2;
       s.vjp(static_cast<const T*>(s.t1.p) + f1, static_cast<const T*>(s.t2.p) + f2,
             static_cast<T*>(B.u1.p) + f1, static_cast<T*>(B.u2.p) + f2, static_cast<T*>(B.tb1.p) + f1,
             static_cast<T*>(B.tb2.p) + f2, nx);
@@ -2379,12 +2502,12 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
       const bool one = k == 0;
       if (one)
         CU(launch_lambda_combine<T, T>(dE1, static_cast<const T*>(B.tb1.p), static_cast<T*>(B.mn1.p),
-                                       static_cast<const T*>(B.m1.p), o * v, static_cast<int>(ng), static_cast<int>(nz),
+                                       static_cast<const T*>(B.m1.p), e1, static_cast<int>(ng), static_cast<int>(nz),
                                        static_cast<const double*>(B.cz.p), 0.0, static_cast<double*>(B.lpart.p), nblk,
                                        h->st));
       else
         CU(launch_lambda_combine<T, double>(static_cast<const double*>(B.V64.p), static_cast<const T*>(B.tb2.p),
-                                            static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), o * o * v * v,
+                                            static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), e2,
                                             static_cast<int>(ng), static_cast<int>(nz),
                                             static_cast<const double*>(B.cz.p), 0.25, static_cast<double*>(B.lpart.p),
                                             nblk, h->st));
@@ -2438,7 +2561,7 @@ void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std
   s.want_fixed_bar = true;
   for (int x0 = 0; x0 < s.ng; x0 += s.nxc) {
     const int nx = std::min(s.nxc, s.ng - x0);
-    const long long f1 = static_cast<long long>(x0) * no * nv, f2 = f1 * no * nv;
+    const long long f1 = static_cast<long long>(x0) * s.n1(), f2 = static_cast<long long>(x0) * s.n2();
     s.vjp(static_cast<const T*>(s.t1.p) + f1, static_cast<const T*>(s.t2.p) + f2,
           static_cast<T*>(B.u1.p) + f1, static_cast<T*>(B.u2.p) + f2, static_cast<T*>(B.tb1.p) + f1,
           static_cast<T*>(B.tb2.p) + f2, nx);
@@ -2457,11 +2580,17 @@ void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std
   const T* t2 = static_cast<const T*>(s.t2.p);
   T* Aov = s.fixed_adjoint(s.F("zia"));
   T* Aoovv = s.fixed_adjoint(s.V("zijab"));
-  T* cs1 = static_cast<T*>(B.tb1.p);
-  s.contract({Aov, "zia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"});
-  s.contract({Aoovv, "zijab"}, 0.25, CT{cz, "zx"}, CT{t2, "zxijab"});
-  s.contract({cs1, "zxia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"}, "", 0.0);
-  s.contract({Aoovv, "zijab"}, 0.5, CT{cs1, "zxia"}, CT{t1, "zxjb"});
+  if (s.sp) {
+    if constexpr (sizeof(T) == 8)
+      CU(launch_sp_energy_bar(t1, t2, static_cast<const double*>(B.cz.p), static_cast<const int16_t*>(B.imp.p), N, ng,
+                              Aoovv, Aov, h->st));
+  } else {
+    T* cs1 = static_cast<T*>(B.tb1.p);
+    s.contract({Aov, "zia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"});
+    s.contract({Aoovv, "zijab"}, 0.25, CT{cz, "zx"}, CT{t2, "zxijab"});
+    s.contract({cs1, "zxia"}, 1.0, CT{cz, "zx"}, CT{t1, "zxia"}, "", 0.0);
+    s.contract({Aoovv, "zijab"}, 0.5, CT{cs1, "zxia"}, CT{t1, "zxjb"});
+  }
   (void)n1;
   // per-orbital sums through the Fermi factors
   Buf Do = h->get(static_cast<size_t>(nz) * no * 8), Dv = h->get(static_cast<size_t>(nz) * nv * 8);
@@ -2473,7 +2602,44 @@ void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std
   CU(cudaMemsetAsync(Fbar.p, 0, Fbar.bytes, h->st));
   CU(cudaMemsetAsync(Ee.p, 0, Ee.bytes, h->st));
   CU(cudaMemsetAsync(Eb.p, 0, Eb.bytes, h->st));
+  // block-sparse storage: the Fock blocks are diagonals; their I * Ibar (two
+  // slots, both orbital p) and their scatter to Fbar (the diagonal) are done
+  // on the host
+  std::vector<double> spDo(s.sp ? N : 0, 0.0), spDv(s.sp ? N : 0, 0.0);
+  if (s.sp) {
+    if constexpr (sizeof(T) == 8) {
+      for (auto& kv : s.Vb) {
+        auto it = s.fixed_bar.find(kv.second.p);
+        if (it == s.fixed_bar.end()) continue;
+        int cls = 0;
+        for (int k = 0; k < 4; ++k)
+          if (kv.first[k] == 'v') cls |= 1 << k;
+        CU(launch_sp_slot_sums(static_cast<const double*>(kv.second.p), static_cast<const double*>(it->second.p),
+                               static_cast<const int16_t*>(B.imp.p), N, cls, static_cast<double*>(Do.p),
+                               static_cast<double*>(Dv.p), h->st));
+      }
+      std::vector<double> fb(N), fv(N), Fh(static_cast<size_t>(N) * N, 0.0);
+      const Inst& I0 = B.inst[0];
+      for (auto& kv : s.Fb) {
+        auto it = s.fixed_bar.find(kv.second.p);
+        if (it == s.fixed_bar.end()) continue;
+        CU(cudaMemcpyAsync(fb.data(), it->second.p, N * 8, cudaMemcpyDeviceToHost, h->st));
+        CU(cudaMemcpyAsync(fv.data(), kv.second.p, N * 8, cudaMemcpyDeviceToHost, h->st));
+        sync(h);
+        for (int p = 0; p < N; ++p) {
+          const double prod = fb[p] * fv[p];
+          for (int k = 0; k < 2; ++k) (kv.first[k] == 'o' ? spDo : spDv)[p] += prod;
+          double f = 1.0;
+          for (int k = 0; k < 2; ++k) f *= std::sqrt(kv.first[k] == 'o' ? I0.n_host[p] : I0.nbar_host[p]);
+          Fh[static_cast<size_t>(p) * N + p] += fb[p] * f;
+        }
+      }
+      CU(cudaMemcpyAsync(Fbar.p, Fh.data(), Fh.size() * 8, cudaMemcpyHostToDevice, h->st));
+      sync(h);
+    }
+  }
   for (auto* mp : {&s.Vb, &s.Fb}) {
+    if (s.sp) break;
     for (auto& kv : *mp) {
       auto it = s.fixed_bar.find(kv.second.p);
       if (it == s.fixed_bar.end()) continue;
@@ -2513,6 +2679,11 @@ void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std
   CU(cudaMemcpyAsync(hGn.data(), Gn.p, Gn.bytes, cudaMemcpyDeviceToHost, h->st));
   CU(cudaMemcpyAsync(hEe.data(), Ee.p, Ee.bytes, cudaMemcpyDeviceToHost, h->st));
   CU(cudaMemcpyAsync(hEb.data(), Eb.p, Eb.bytes, cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+  for (size_t p = 0; p < spDo.size(); ++p) {
+    hDo[p] += spDo[p];
+    hDv[p] += spDv[p];
+  }
   const std::vector<double> st = read_states(B);
   std::vector<double> eps(N), fdiag(N * N), hdiag(N * N);
   out.assign(nz, ftcc_adjoint_result{});
@@ -3005,7 +3176,6 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
     return fail(c, FTCC_ERR_STATE, "the adjoint needs a converged ft_ccsd_solve");
   if (c->batch->opt.stream_tau)
     return fail(c, FTCC_ERR_UNSUPPORTED, "the adjoint needs S at every tau point (solve without stream_tau)");
-  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: the adjoint runs on the dense storage");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
@@ -3069,8 +3239,13 @@ ftcc_status ftcc_rdm2(ftcc_ctx* c, double* gamma) {
         nn[k] = ho ? no : nv;
         total *= nn[k];
       }
-      CU(launch_eri_adjoint(static_cast<const double*>(it->second.p) + z * total, N, ix[0], fx[0], nn[0], ix[1],
-                            fx[1], nn[1], ix[2], fx[2], nn[2], ix[3], fx[3], nn[3], static_cast<double*>(g.p), h->st));
+      if (B.sparse)
+        CU(launch_sp_eri_adjoint(static_cast<const double*>(it->second.p), static_cast<const int16_t*>(B.imp.p), N,
+                                 fx[0], fx[1], fx[2], fx[3], static_cast<double*>(g.p), h->st));
+      else
+        CU(launch_eri_adjoint(static_cast<const double*>(it->second.p) + z * total, N, ix[0], fx[0], nn[0], ix[1],
+                              fx[1], nn[1], ix[2], fx[2], nn[2], ix[3], fx[3], nn[3], static_cast<double*>(g.p),
+                              h->st));
     }
     std::vector<double> raw(N4);
     CU(cudaMemcpyAsync(raw.data(), g.p, N4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -3218,11 +3393,32 @@ ftcc_status ftcc_eval_s_vjp(ftcc_ctx* c, int nx, const double* t1_dev, const dou
   if (!c->batch) return fail(c, FTCC_ERR_STATE, "ftcc_prepare first");
   if (c->batch->nz != 1) return fail(c, FTCC_ERR_STATE, "works on a single prepared instance");
   if (nx < 1 || nx > c->batch->ng) return fail(c, FTCC_ERR_INVALID_ARG, "bad nx");
-  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: no S-kernel transpose");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     Solver<double>& s = make_solver<double>(B, GEMM_F64);
     if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+    if (B.sparse) {
+      // dense in and out: inputs and cotangents projected onto the
+      // charge-conserving elements, outputs expanded with zeros elsewhere
+      const long long N = B.N, n3 = N * N * N;
+      const int16_t* imp = static_cast<const int16_t*>(B.imp.p);
+      Buf q[6];
+      const long long sz[6] = {nx * N, nx * n3, nx * N, nx * n3, nx * N, nx * n3};
+      for (int k = 0; k < 6; ++k) {
+        q[k] = c->get(sz[k] * 8);
+        if (!q[k].p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+      }
+      double* d[6];
+      for (int k = 0; k < 6; ++k) d[k] = static_cast<double*>(q[k].p);
+      CU(launch_sp_compress(t1_dev, t2_dev, imp, B.N, nx, d[0], d[1], c->st));
+      CU(launch_sp_compress(w1_dev, w2_dev, imp, B.N, nx, d[2], d[3], c->st));
+      s.vjp(d[0], d[1], d[2], d[3], d[4], d[5], nx);
+      CU(launch_sp_expand(d[4], d[5], imp, B.N, nx, t1bar_dev, t2bar_dev, c->st));
+      sync(c);
+      for (Buf& b : q) c->put(b);
+      check_device_error(c);
+      return FTCC_OK;
+    }
     const long long n1 = nx * static_cast<long long>(B.no) * B.nv, n2 = n1 * B.no * B.nv;
     Buf a = c->get(n1 * 8), b = c->get(n2 * 8);
     if (!a.p || !b.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};

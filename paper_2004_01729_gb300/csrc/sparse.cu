@@ -418,6 +418,472 @@ __global__ void sp_expand_kernel(const double* __restrict__ s1, const double* __
 
 }  // namespace
 
+// ============================================================ transpose (VJP)
+// The lambda equations need the transpose of the S kernel: given the
+// cotangents S1b, S2b of S1, S2 (per slice), the cotangents of s1, s2 and
+// (for the response) of the integral and Fock blocks.  The forward
+// intermediates are recomputed first; each forward step is then transposed
+// in reverse order.  Vector quantities (the two-index factors) are
+// reductions per orbital, element-wise contributions are written in gather
+// form (each output element sums what reaches it), so nothing is written by
+// two threads and the sums have a fixed order.
+namespace {
+
+// Rb = P(ij)P(ab) S2b (the antisymmetriser is its own transpose)
+__global__ void sp_s2_t_kernel(const double* __restrict__ S2b, const int16_t* __restrict__ imp, int n,
+                               double* __restrict__ Rb) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* g = S2b + x * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int aa = static_cast<int>(e % n);
+    const int j = static_cast<int>((e / n) % n);
+    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const int b = impl(imp, n, i, j, aa);
+    Rb[x * n3 + e] = b >= 0 ? g[e] - g[pos3(n, j, i, aa)] - g[pos3(n, i, j, b)] + g[pos3(n, j, i, b)] : 0.0;
+  }
+}
+
+// Element-wise transposes, gathered at the s2 position (i, j, a), b implied:
+//   from R's terms:   1/2 Rb(ija) Ft[b] + 1/2 Ft2[j] Rb(jia)
+//   from S1 and F:    [a = i] S1b[i] Fme[j] - 1/2 S1b[i] <ji||ab>_ovvv(j,i,a) + 1/2 Fmib[i] <ij||ab>_oovv
+//                     - 1/2 S1b[a] <ji||bi'>_oovo(j,i,b) - 1/2 Faeb[a] <ij||ab>_oovv
+//   from the operands: tab(ija) + tpb(a b i) + trb(i a j) + 1/2 xpb(i b j)
+struct SpT2 {
+  const double *t1, *Rb, *Ft, *Ft2, *S1b, *Fme, *Fmib, *Faeb, *tab, *tpb, *trb, *xpb;
+  const double *Vovvv, *Voovv, *Voovo;
+  const int16_t* imp;
+  int n;
+  double* t2b;
+};
+
+__global__ void sp_t2bar_kernel(SpT2 a) {
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const double* Rb = a.Rb + x * n3;
+  const double* Ft = a.Ft + x * n;
+  const double* Ft2 = a.Ft2 + x * n;
+  const double* S1b = a.S1b + x * n;
+  const double* Fme = a.Fme + x * n;
+  const double* Fmib = a.Fmib + x * n;
+  const double* Faeb = a.Faeb + x * n;
+  const double* tab = a.tab + x * n3;
+  const double* tpb = a.tpb + x * n3;
+  const double* trb = a.trb + x * n3;
+  const double* xpb = a.xpb + x * n3;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int aa = static_cast<int>(e % n);
+    const int j = static_cast<int>((e / n) % n);
+    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    const int b = impl(a.imp, n, i, j, aa);
+    double v = 0.0;
+    if (b >= 0) {
+      v = 0.5 * Rb[e] * Ft[b] + 0.5 * Ft2[j] * Rb[pos3(n, j, i, aa)];
+      if (aa == i) v += S1b[i] * Fme[j];
+      v += -0.5 * S1b[i] * a.Vovvv[pos3(n, j, i, aa)] + 0.5 * Fmib[i] * a.Voovv[e] -
+           0.5 * S1b[aa] * a.Voovo[pos3(n, j, i, b)] - 0.5 * Faeb[aa] * a.Voovv[e];
+      v += tab[e] + tpb[pos3(n, aa, b, i)] + trb[pos3(n, i, aa, j)] + 0.5 * xpb[pos3(n, i, b, j)];
+    }
+    a.t2b[x * n3 + e] = v;
+  }
+}
+
+// Vector cotangents of one (x, p), in two passes.
+// Pass 1: Ftb[p], Ft2b[p] (from R's terms), Faeb[p], Fmib[p], Fmeb[p].
+//   Ftb[b]  = 1/2 sum_ij Rb(i,j,a) s2(i,j,a),  a = imp(i,j,b)
+//   Ft2b[i] = 1/2 sum_ja Rb(i,j,a) s2(j,i,a)
+//   Faeb = Ftb + S1b s1,  Fmib = Ft2b - S1b s1
+//   Fmeb[m] = s1[m] (-Ftb + Ft2b - Faeb + Fmib)[m] / 2 + sum_p S1b[p] s2(p,m,p)
+struct SpVecT {
+  const double *t1, *t2, *Rb, *S1b, *Fme, *Fae, *Fmi;
+  const double *Vvvvo, *Vovvo, *Vovoo, *Vooov, *Vovvv, *Voovo, *Vovov, *Voovv;
+  const double *w1b, *wabb, *wrb, *tab, *tpb, *xpb;
+  const int16_t* imp;
+  int n;
+  double *Ftb, *Ft2b, *Faeb, *Fmib, *Fmeb, *t1b;
+};
+
+__global__ void sp_vec_t1_kernel(SpVecT a) {
+  __shared__ double red[32];
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const int p = blockIdx.x, x = blockIdx.y;
+  const double* s2 = a.t2 + x * n3;
+  const double* Rb = a.Rb + x * n3;
+  const double* S1b = a.S1b + static_cast<long long>(x) * n;
+  double ftb = 0.0, ft2b = 0.0, fme = 0.0;
+  const long long nn = static_cast<long long>(n) * n;
+  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
+    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+    const int aa = impl(a.imp, n, u, w, p);                    // (i, j, a) = (u, w, aa), b = p
+    if (aa >= 0) ftb += Rb[pos3(n, u, w, aa)] * s2[pos3(n, u, w, aa)];
+    ft2b += Rb[pos3(n, p, u, w)] * s2[pos3(n, u, p, w)];     // (i, j, a) = (p, u, w)
+  }
+  for (int q = threadIdx.x; q < n; q += blockDim.x) fme += S1b[q] * s2[pos3(n, q, p, q)];
+  ftb = block_sum(ftb, red);
+  ft2b = block_sum(ft2b, red);
+  fme = block_sum(fme, red);
+  if (threadIdx.x == 0) {
+    const long long o = static_cast<long long>(x) * n + p;
+    const double s = a.t1[o];
+    const double Ftb = 0.5 * ftb, Ft2b = 0.5 * ft2b;
+    const double Faeb = Ftb + S1b[p] * s, Fmib = Ft2b - S1b[p] * s;
+    a.Ftb[o] = Ftb;
+    a.Ft2b[o] = Ft2b;
+    a.Faeb[o] = Faeb;
+    a.Fmib[o] = Fmib;
+    a.Fmeb[o] = 0.5 * s * (-Ftb + Ft2b - Faeb + Fmib) + fme;
+  }
+}
+
+// Pass 2: the cotangent of s1[p], every contribution:
+//   R's terms (p as i, a, b), the W bases (p as i of W_mnij, a of W_abef,
+//   j and b of W_mbej), the vector intermediates and S1, and the s1 s1
+//   parts of tau, X and the ladder operand.
+__global__ void sp_vec_t2_kernel(SpVecT a) {
+  __shared__ double red[32];
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const int p = blockIdx.x, x = blockIdx.y;
+  const double* s1 = a.t1 + static_cast<long long>(x) * n;
+  const double* Rb = a.Rb + x * n3;
+  const double* w1b = a.w1b + x * n3;
+  const double* wabb = a.wabb + x * n3;
+  const double* wrb = a.wrb + x * n3;
+  const double* tab = a.tab + x * n3;
+  const double* tpb = a.tpb + x * n3;
+  const double* xpb = a.xpb + x * n3;
+  const double* S1b = a.S1b + static_cast<long long>(x) * n;
+  const double* Faeb = a.Faeb + static_cast<long long>(x) * n;
+  const double* Fmib = a.Fmib + static_cast<long long>(x) * n;
+  const double* Fmeb = a.Fmeb + static_cast<long long>(x) * n;
+  double acc = 0.0;
+  const long long nn = static_cast<long long>(n) * n;
+  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
+    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+    {   // R: p as i, (j, a) = (u, w), b = imp(p, u, w)
+      const int b = impl(a.imp, n, p, u, w);
+      if (b >= 0) {
+        const double g = Rb[pos3(n, p, u, w)];
+        acc += g * (0.5 * a.Vvvvo[pos3(n, w, b, p)] + s1[b] * a.Vovvo[pos3(n, b, w, p)]);
+      }
+    }
+    {   // R: p as a, (i, j) = (u, w), b = imp(u, w, p)
+      const int b = impl(a.imp, n, u, w, p);
+      if (b >= 0) acc -= 0.5 * Rb[pos3(n, u, w, p)] * a.Vovoo[pos3(n, p, b, u)];
+    }
+    {   // R: p as b, (i, j) = (u, w), a = imp(u, w, p)
+      const int aa = impl(a.imp, n, u, w, p);
+      if (aa >= 0) acc += Rb[pos3(n, u, w, aa)] * s1[u] * a.Vovvo[pos3(n, p, aa, u)];
+    }
+    {   // W'_mnij base: p as i, (j, m) = (u, w), n = imp(p, u, w)
+      const int q = impl(a.imp, n, p, u, w);
+      if (q >= 0) acc -= 2.0 * w1b[pos3(n, p, u, w)] * a.Vooov[pos3(n, w, q, u)];
+    }
+    // W'_abef base: p as a, (b, e) = (u, w)
+    acc -= 2.0 * wabb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, p, u, w)];
+    {   // W_mbej base, p as j: (b, m) = (u, w), e = imp(u, w, p)
+      const int ee = impl(a.imp, n, u, w, p);
+      if (ee >= 0) acc += wrb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, w, u, ee)];
+    }
+    {   // W_mbej base, p as b: (j, m) = (u, w), e = imp(p, w, u)
+      const int ee = impl(a.imp, n, p, w, u);
+      if (ee >= 0) acc -= wrb[pos3(n, u, p, w)] * a.Voovo[pos3(n, w, p, ee)];
+    }
+  }
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    // S1 and the F intermediates
+    acc += -S1b[q] * a.Vovov[pos3(n, p, q, q)] + Faeb[q] * a.Vovvv[pos3(n, p, q, p)] +
+           Fmib[q] * a.Vooov[pos3(n, q, p, q)] + Fmeb[q] * a.Voovv[pos3(n, q, p, q)];
+    // s1 s1 parts of tau (ta), of the ladder operand (tp) and of X (xp)
+    acc += s1[q] * (tab[pos3(n, p, q, p)] - tab[pos3(n, p, q, q)] + tab[pos3(n, q, p, q)] - tab[pos3(n, q, p, p)] +
+                    tpb[pos3(n, p, q, p)] - tpb[pos3(n, p, q, q)] + tpb[pos3(n, q, p, q)] - tpb[pos3(n, q, p, p)] +
+                    xpb[pos3(n, p, q, q)] + xpb[pos3(n, q, p, p)]);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    const long long o = static_cast<long long>(x) * n + p;
+    const double fm = a.Fme[o], Ftb = a.Ftb[o], Ft2b = a.Ft2b[o];
+    acc += 0.5 * fm * (-Ftb + Ft2b - Faeb[p] + Fmib[p]) + S1b[p] * (a.Fae[o] - a.Fmi[o]);
+    a.t1b[o] = acc;
+  }
+}
+
+// Transposed sector products:
+//   D[orow(e_o)][k] += alpha sum_{e_s in sector} G[gpos(e_o, e_s)] A[srow(e_s)][k]
+// for the pairs e_o of the sector (rows) and k of its K list; orow / srow
+// are p n + q or (swapped) q n + p; gpos = p_o g0 + q_o g1 + p_s g2 + q_s g3.
+// With dx = 0 the output is fixed (an integral block) and the kernel sums
+// the nx slices of G and A itself.
+__global__ void __launch_bounds__(kSecT * kSecT) sector_tn_kernel(SecTnArgs g) {
+  __shared__ double Gs[kSecK][kSecT + 1], As[kSecK][kSecT + 1];
+  const int4 w = g.work[blockIdx.x];
+  const int4 sec = g.sec[w.x];
+  const int n = g.n;
+  const int to = threadIdx.x / kSecT, tk = threadIdx.x % kSecT;   // output row, k column
+  const int lo = threadIdx.x / kSecK, ls = threadIdx.x % kSecK;   // loader: output / k row, summed row
+  const int xr0 = g.dx ? blockIdx.y : 0, xr1 = g.dx ? blockIdx.y + 1 : g.nx;
+  // loader entries
+  const int eo = w.y + lo;                 // output row this thread loads G for
+  const int ek = w.z + lo;                 // k column this thread loads A for
+  int2 po = make_int2(0, 0);
+  const bool oin = eo < sec.y;
+  if (oin) po = g.ent[sec.x + eo];
+  const int kv = ek < sec.w ? g.kl[sec.z + ek] : -1;
+  double acc = 0.0;
+  for (int x = xr0; x < xr1; ++x) {
+    const double* G = g.G + x * g.gx;
+    const double* A = g.A + x * g.ax;
+    for (int s0 = 0; s0 < sec.y; s0 += kSecK) {
+      const int es = s0 + ls;
+      double gv = 0.0, av = 0.0;
+      if (es < sec.y) {
+        const int2 ps = g.ent[sec.x + es];
+        if (oin)
+          gv = G[static_cast<long long>(po.x) * g.g0 + static_cast<long long>(po.y) * g.g1 +
+                 static_cast<long long>(ps.x) * g.g2 + static_cast<long long>(ps.y) * g.g3];
+        if (kv >= 0) {
+          const long long srow = g.swapA ? static_cast<long long>(ps.y) * n + ps.x
+                                         : static_cast<long long>(ps.x) * n + ps.y;
+          av = A[srow * n + kv];
+        }
+      }
+      Gs[ls][lo] = gv;
+      As[ls][lo] = av;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kSecK; ++k) acc = fma(Gs[k][to], As[k][tk], acc);
+      __syncthreads();
+    }
+  }
+  const int ro = w.y + to, rk = w.z + tk;
+  if (ro < sec.y && rk < sec.w) {
+    const int2 pr = g.ent[sec.x + ro];
+    const long long orow = g.swapD ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
+    const long long o = (g.dx ? static_cast<long long>(blockIdx.y) * g.dx : 0) + orow * n + g.kl[sec.z + rk];
+    g.D[o] += g.alpha * acc;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Cotangents of the integral blocks from the element-wise uses (summed over
+// the nx slices; blockIdx.y = block: 0 oovv, 1 ovvv, 2 ooov, 3 oooo,
+// 4 vvvv, 5 ovvo, 6 oovo, 7 ovov, 8 vvoo, 9 vvvo, 10 ovoo), at the block
+// position (p, q, r), s = imp[p][q][r].  With cz (the energy weights g_x /
+// beta) the direct use of <ij||ab> in Eq. E is added to oovv.  The products
+// of two four-index factors add theirs through sector_tn_kernel.
+struct SpFixT {
+  const double *t1, *t2, *S2b, *Rb, *w1b, *wabb, *wrb, *S1b, *Faeb, *Fmib, *Fmeb, *cz;
+  const int16_t* imp;
+  int n, nx;
+  double* Vb[11];
+};
+
+__global__ void sp_fixed_bar_kernel(SpFixT a) {
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const int blk = blockIdx.y;
+  double* out = a.Vb[blk];
+  if (!out) return;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int sl = a.imp[e];
+    if (sl < 0) continue;
+    const int r = static_cast<int>(e % n);
+    const int q = static_cast<int>((e / n) % n);
+    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    double v = 0.0;
+    for (int x = 0; x < a.nx; ++x) {
+      const double* s1 = a.t1 + static_cast<long long>(x) * n;
+      const double* s2 = a.t2 + x * n3;
+      const double* S2b = a.S2b + x * n3;
+      const double* Rb = a.Rb + x * n3;
+      const double* w1b = a.w1b + x * n3;
+      const double* wabb = a.wabb + x * n3;
+      const double* wrb = a.wrb + x * n3;
+      const double* S1b = a.S1b + static_cast<long long>(x) * n;
+      const double* Faeb = a.Faeb + static_cast<long long>(x) * n;
+      const double* Fmib = a.Fmib + static_cast<long long>(x) * n;
+      const double* Fmeb = a.Fmeb + static_cast<long long>(x) * n;
+      switch (blk) {
+        case 0:   // oovv (m, q, e) [f]
+          v += -0.5 * Faeb[r] * s2[e] + 0.5 * Fmib[p] * s2[e];
+          if (r == p) v += Fmeb[p] * s1[q];
+          if (a.cz) {
+            v += a.cz[x] * 0.25 * s2[e];
+            if (r == p) v += a.cz[x] * 0.5 * s1[p] * s1[q];
+          }
+          break;
+        case 1:   // ovvv (m, b, e) [f]
+          v += -2.0 * s1[p] * wabb[e] + s1[sl] * wrb[pos3(n, sl, q, p)] - 0.5 * S1b[q] * s2[pos3(n, q, p, r)];
+          if (r == p) v += Faeb[q] * s1[p];
+          break;
+        case 2:   // ooov (m, n, j) [i]
+          v += -2.0 * s1[sl] * w1b[pos3(n, sl, r, p)];
+          if (r == p) v += Fmib[p] * s1[q];
+          break;
+        case 3:   // oooo (m, n, i) [j]
+          v += w1b[pos3(n, r, sl, p)];
+          break;
+        case 4:   // vvvv
+          v += wabb[e];
+          break;
+        case 5:   // ovvo (b, a, i) [j] from R; (m, b, e) [j] from W_mbej
+          v += s1[r] * s1[p] * Rb[pos3(n, r, sl, q)] + wrb[pos3(n, sl, q, p)];
+          break;
+        case 6:   // oovo (m, b, e) [j] from W_mbej; (q', m', e') [p'] from S1
+          v += -s1[q] * wrb[pos3(n, sl, q, p)] - 0.5 * S1b[sl] * s2[pos3(n, q, p, sl)];
+          break;
+        case 7:   // ovov (m, p', p') [m]
+          if (q == r) v += -S1b[q] * s1[p];
+          break;
+        case 8:   // vvoo (a, b, i) [j]
+          v += S2b[pos3(n, r, sl, p)];
+          break;
+        case 9:   // vvvo (a, b, i) [j]
+          v += 0.5 * s1[r] * Rb[pos3(n, r, sl, p)];
+          break;
+        default:  // ovoo (a, b, i) [j]
+          v += -0.5 * s1[p] * Rb[pos3(n, r, sl, p)];
+          break;
+      }
+    }
+    out[e] += v;
+  }
+}
+
+// Fock-diagonal cotangents summed over the slices: fov += Fmeb (+ the
+// energy's sum_x cz[x] s1), fvv += Faeb, foo += Fmib, fvo += S1b
+__global__ void sp_fock_bar_kernel(const double* __restrict__ t1, const double* __restrict__ Fmeb,
+                                   const double* __restrict__ Faeb, const double* __restrict__ Fmib,
+                                   const double* __restrict__ S1b, const double* __restrict__ cz, int n, int nx,
+                                   double* fov, double* fvv, double* foo, double* fvo) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (int x = 0; x < nx; ++x) {
+    const long long o = static_cast<long long>(x) * n + p;
+    a0 += Fmeb[o] + (cz ? cz[x] * t1[o] : 0.0);
+    a1 += Faeb[o];
+    a2 += Fmib[o];
+    a3 += S1b[o];
+  }
+  if (fov) fov[p] += a0;
+  if (fvv) fvv[p] += a1;
+  if (foo) foo[p] += a2;
+  if (fvo) fvo[p] += a3;
+}
+
+// out[p0][p1][p2] += in[p0][p2][p1]
+__global__ void sp_swap12_add_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p2 = static_cast<int>(e % n);
+    const int p1 = static_cast<int>((e / n) % n);
+    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    out[e] += in[pos3(n, p0, p2, p1)];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Direct dependence of Omega_CC = sum_x cz[x] E_x on the energy weights
+// (Eq. E): <ij||ab>bar += sum_x cz[x] (1/4 s2 + 1/2 [a = i] s1[i] s1[j]),
+// f_ia bar (diagonal) += sum_x cz[x] s1
+__global__ void sp_energy_bar_kernel(const double* __restrict__ t1, const double* __restrict__ t2,
+                                     const double* __restrict__ cz, const int16_t* __restrict__ imp, int n, int ng,
+                                     double* __restrict__ Voovvb, double* __restrict__ fovb) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (e < n) {   // the diagonal f_ia (before the hole test: e indexes an orbital here)
+      double f = 0.0;
+      for (int x = 0; x < ng; ++x) f += cz[x] * t1[static_cast<long long>(x) * n + e];
+      fovb[e] += f;
+    }
+    if (imp[e] < 0) continue;
+    const int aa = static_cast<int>(e % n);
+    const int j = static_cast<int>((e / n) % n);
+    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    double v = 0.0;
+    for (int x = 0; x < ng; ++x) {
+      v += cz[x] * 0.25 * t2[x * n3 + e];
+      if (aa == i) v += cz[x] * 0.5 * t1[static_cast<long long>(x) * n + i] * t1[static_cast<long long>(x) * n + j];
+    }
+    Voovvb[e] += v;
+  }
+}
+
+// Per-orbital sums of I * Ibar over the elements of an N^3 block whose slot
+// k (the implied fourth slot included) is orbital q, added to Do[q] for a
+// hole-like slot (bit k of cls clear) or Dv[q] (set).  One block per q.
+__global__ void sp_slot_sums_kernel(const double* __restrict__ I, const double* __restrict__ Ib,
+                                    const int16_t* __restrict__ imp, int n, int cls, double* __restrict__ Do,
+                                    double* __restrict__ Dv) {
+  __shared__ double red[32];
+  const int q = blockIdx.x;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long nn = static_cast<long long>(n) * n;
+  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
+    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+    long long e = pos3(n, q, u, w);
+    acc[0] += I[e] * Ib[e];
+    e = pos3(n, u, q, w);
+    acc[1] += I[e] * Ib[e];
+    e = pos3(n, u, w, q);
+    acc[2] += I[e] * Ib[e];
+    const int rr = impl(imp, n, u, w, q);   // (u, w, rr) has q implied
+    if (rr >= 0) {
+      e = pos3(n, u, w, rr);
+      acc[3] += I[e] * Ib[e];
+    }
+  }
+  double so = 0.0, sv = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const double t = block_sum(acc[k], red);
+    if (threadIdx.x == 0) {
+      if (cls & (1 << k)) sv += t;
+      else so += t;
+    }
+  }
+  if (threadIdx.x == 0) {
+    Do[q] += so;
+    Dv[q] += sv;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// gamma[p][q][r][s] += bar[p][q][r] f0[p] f1[q] f2[r] f3[s], s implied: the
+// cotangent of one thermal block mapped back to <pq||rs> (N^4, dense)
+__global__ void sp_eri_adjoint_kernel(const double* __restrict__ bar, const int16_t* __restrict__ imp, int n,
+                                      const double* f0, const double* f1, const double* f2, const double* f3,
+                                      double* __restrict__ gamma) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int s = imp[e];
+    if (s < 0) continue;
+    const int r = static_cast<int>(e % n);
+    const int q = static_cast<int>((e / n) % n);
+    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    gamma[e * n + s] += bar[e] * f0[p] * f1[q] * f2[r] * f3[s];
+  }
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
                           double* tp, double* tr, double* xp, cudaStream_t st) {
@@ -496,6 +962,95 @@ cudaError_t launch_sp_expand(const double* s1, const double* s2, const int16_t* 
                              double* d2, cudaStream_t st) {
   const long long n4 = static_cast<long long>(n) * n * n * n;
   sp_expand_kernel<<<dim3(sp_grid(n4), nx), kSpThreads, 0, st>>>(s1, s2, imp, n, d1, d2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, int n, int nx, double* Rb, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_s2_t_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(S2b, imp, n, Rb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st) {
+  if (nwork <= 0 || g.nx <= 0) return cudaSuccess;
+  if (g.nx > 65535) return cudaErrorInvalidValue;
+  sector_tn_kernel<<<dim3(nwork, g.dx ? g.nx : 1), kSecT * kSecT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st) {
+  SpVecT a{v.t1, v.t2, v.Rb, v.S1b, v.Fme, v.Fae, v.Fmi, v.V.vvvo, v.V.ovvo, v.V.ovoo, v.V.ooov, v.V.ovvv,
+           v.V.oovo, v.V.ovov, v.V.oovv, v.w1b, v.wabb, v.wrb, v.tab, v.tpb, v.xpb, v.imp, v.n,
+           v.Ftb, v.Ft2b, v.Faeb, v.Fmib, v.Fmeb, v.t1b};
+  sp_vec_t1_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
+  sp_vec_t2_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_t2bar(const SpVjpArgs& v, int nx, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(v.n) * v.n * v.n;
+  SpT2 a{v.t1, v.Rb, v.Ft, v.Ft2, v.S1b, v.Fme, v.Fmib, v.Faeb, v.tab, v.tpb, v.trb, v.xpb, v.V.ovvv, v.V.oovv,
+         v.V.oovo, v.imp, v.n, v.t2b};
+  sp_t2bar_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_fixed_bar(const SpVjpArgs& v, const double* S2b, const double* cz, double* const* Vbar,
+                                double* const* fbar, int nx, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(v.n) * v.n * v.n;
+  SpFixT a{};
+  a.t1 = v.t1;
+  a.t2 = v.t2;
+  a.S2b = S2b;
+  a.Rb = v.Rb;
+  a.w1b = v.w1b;
+  a.wabb = v.wabb;
+  a.wrb = v.wrb;
+  a.S1b = v.S1b;
+  a.Faeb = v.Faeb;
+  a.Fmib = v.Fmib;
+  a.Fmeb = v.Fmeb;
+  a.cz = cz;
+  a.imp = v.imp;
+  a.n = v.n;
+  a.nx = nx;
+  for (int k = 0; k < 11; ++k) a.Vb[k] = Vbar[k];
+  sp_fixed_bar_kernel<<<dim3(sp_grid(n3), 11), kSpThreads, 0, st>>>(a);
+  sp_fock_bar_kernel<<<(v.n + 127) / 128, 128, 0, st>>>(v.t1, v.Fmeb, v.Faeb, v.Fmib, v.S1b, cz, v.n, nx, fbar[0],
+                                                          fbar[1], fbar[2], fbar[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_energy_bar(const double* t1, const double* t2, const double* cz, const int16_t* imp, int n,
+                                 int ng, double* Voovvb, double* fovb, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_energy_bar_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(t1, t2, cz, imp, n, ng, Voovvb, fovb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_slot_sums(const double* I, const double* Ib, const int16_t* imp, int n, int cls, double* Do,
+                                double* Dv, cudaStream_t st) {
+  sp_slot_sums_kernel<<<n, 256, 0, st>>>(I, Ib, imp, n, cls, Do, Dv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voovv, int n, int nx, double* out,
+                          cudaStream_t st) {
+  const int warps = n * nx;
+  sp_fme_kernel<<<(warps * 32 + 127) / 128, 128, 0, st>>>(t1, fov, Voovv, n, nx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_eri_adjoint(const double* bar, const int16_t* imp, int n, const double* f0, const double* f1,
+                                  const double* f2, const double* f3, double* gamma, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_eri_adjoint_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(bar, imp, n, f0, f1, f2, f3, gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sp_swap12_add(const double* in, int n, double* out, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(n) * n * n;
+  sp_swap12_add_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(in, n, out);
   return cudaGetLastError();
 }
 

@@ -129,8 +129,9 @@ def test_sparse_argument_checks(ctx):
     assert e.value.status == ftcc.ERR_UNSUPPORTED
     r = ctx.solve(1.0, 0.5, 6, precision="fp64", block_sparse=1)
     assert r["converged"]
-    d, _ = ctx.adjoint(with_rdm1=False, allow_unsupported=True)
-    assert d["status"] == ftcc.ERR_UNSUPPORTED
+    with pytest.raises(ftcc.FTCCError) as e:          # dense layouts only
+        ctx.propagate_adjoint("ia", torch.zeros((6, 14, 14), dtype=torch.float64))
+    assert e.value.status == ftcc.ERR_UNSUPPORTED
     rng = np.random.default_rng(0)
     N = 6
     h = np.diag(rng.standard_normal(N))
@@ -169,3 +170,118 @@ def test_generic_system_with_charges(ctx):
     ctx.build_generic(h, eri, eps)
     with pytest.raises(ftcc.FTCCError):
         ctx.get_charges()
+
+
+def _conserving_antisym(ch, t1, t2):
+    """Orthogonal projection of dense s1 [x,i,a] / s2 [x,i,j,a,b] onto the
+    charge-conserving (s1 diagonal, q_i + q_j = q_a + q_b), antisymmetric
+    elements."""
+    q = np.asarray(ch.q)
+    N = q.shape[0]
+    keep1 = torch.eye(N, dtype=torch.float64)
+    tot = q[:, None, :] + q[None, :, :]
+    keep2 = torch.from_numpy(np.all(tot[:, :, None, None, :] == tot[None, None, :, :, :], axis=-1).astype(np.float64))
+    a2 = 0.25 * (t2 - t2.transpose(1, 2) - t2.transpose(3, 4) + t2.transpose(1, 2).transpose(3, 4))
+    return t1 * keep1, a2 * keep2
+
+
+def test_sparse_vjp_matches_dense_gpu(ctx):
+    """The transpose of the block-sparse S kernel against the dense engine's
+    tape-replayed transpose on the conserving antisymmetric subspace
+    (19-plane-wave gas, random amplitudes and cotangents), element by
+    element."""
+    n_elec, rs, n_pw, beta, ng = 14, 1.0, 19, 2.0, 4
+    sysc = bs.ueg(n_elec, rs, n_pw)
+    ch = sysc["charges"]
+    t1c, t2c = bs.random_amplitudes(ch, 5, 2, 0.05)
+    d1, d2 = bs.dense_amplitudes(ch, t1c, t2c)
+    rng = np.random.default_rng(9)
+    w1 = torch.tensor(rng.standard_normal(tuple(d1.shape)))
+    w2 = torch.tensor(rng.standard_normal(tuple(d2.shape)))
+    w1, w2 = _conserving_antisym(ch, w1, w2)
+    ctx.build_ueg(n_elec, rs, n_pw)
+    mu = ctx.reference_mu(beta, float(n_elec))
+    ctx.prepare(beta, mu, ng, precision="fp64", block_sparse=1)
+    a1, a2 = ctx.eval_s_vjp(d1, d2, w1, w2)
+    ctx.prepare(beta, mu, ng, precision="fp64")
+    b1, b2 = ctx.eval_s_vjp(d1, d2, w1, w2)
+    a1, a2 = _conserving_antisym(ch, a1.cpu(), a2.cpu())
+    b1, b2 = _conserving_antisym(ch, b1.cpu(), b2.cpu())
+    s1 = torch.max(torch.abs(b1)).item()
+    s2 = torch.max(torch.abs(b2)).item()
+    assert s2 > 1e-3
+    assert torch.max(torch.abs(a1 - b1)).item() < 1e-11 * max(1.0, s1)
+    assert torch.max(torch.abs(a2 - b2)).item() < 1e-11 * max(1.0, s2)
+
+
+@pytest.mark.parametrize("which", ["ueg19", "hubbard6"])
+def test_sparse_adjoint_matches_dense(ctx, which):
+    """N, E, S, the 1-RDM and Gamma_N from the block-sparse lambda sweep
+    against the dense FP64 adjoint of the same converged solve."""
+    if which == "ueg19":
+        beta, ng = 2.0, 8
+        ctx.build_ueg(14, 1.0, 19)
+        mu = ctx.reference_mu(beta, 14.0)
+    else:
+        beta, ng, mu = 1.0, 8, 1.0
+        ctx.build_hubbard(6, 1.0, 2.0)
+    kw = dict(precision="fp64", tol_omega=1e-12, tol_amp=1e-10)
+    ctx.solve(beta, mu, ng, block_sparse=1, **kw)
+    ds, rs_ = ctx.adjoint(with_rdm1=True)
+    gs = ctx.rdm2()
+    ctx.solve(beta, mu, ng, **kw)
+    dd, rd = ctx.adjoint(with_rdm1=True)
+    gd = ctx.rdm2()
+    for k in ("dOmega_dmu", "dOmega_dbeta", "N", "E", "S"):
+        assert abs(ds[k] - dd[k]) < 1e-9 * max(1.0, abs(dd[k])), (k, ds[k], dd[k])
+    assert np.max(np.abs(rs_ - rd)) < 1e-9
+    assert np.max(np.abs(gs - gd)) < 1e-9 * max(1.0, np.max(np.abs(gd)))
+
+
+def test_sparse_adjoint_ueg57_matches_oracle_differences(ctx):
+    """N, E and S of the 114-spin-orbital gas from the block-sparse FP64
+    lambda sweep against central differences (one Richardson step) of
+    converged block-sparse oracle solves."""
+    gold = json.load(open(os.path.join(GOLD, "oracle_ueg57.json")))
+    gr = json.load(open(os.path.join(GOLD, "oracle_ueg57_response.json")))
+    c = gold["config"]
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    r = ctx.solve(c["beta"], gold["mu"], c["ngrid"], precision="fp64", block_sparse=1, tol_omega=1e-12,
+                  tol_amp=1e-10)
+    assert r["converged"]
+    d, rdm = ctx.adjoint(with_rdm1=True)
+    assert abs(d["N"] - gr["N"]) < 2e-7, (d["N"], gr["N"])
+    assert abs(d["E"] - gr["E"]) < 2e-6, (d["E"], gr["E"])
+    assert abs(d["S"] - gr["S"]) < 2e-6, (d["S"], gr["S"])
+    assert abs(np.trace(rdm) - d["N"]) < 1e-8
+    assert np.max(np.abs(rdm - np.diag(np.diag(rdm)))) == 0.0   # momentum conservation: diagonal
+
+
+def test_sparse_adjoint_ueg81_matches_central_differences(ctx):
+    """The 162-spin-orbital gas: dOmega/dmu and dOmega/dbeta from the
+    block-sparse lambda sweep against central differences (one Richardson
+    step, h = 1e-3) of converged block-sparse solves of the same gas."""
+    gold = json.load(open(os.path.join(GOLD, "oracle_ueg81.json")))
+    c = gold["config"]
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    mu, beta, ng = gold["mu"], c["beta"], c["ngrid"]
+    kw = dict(precision="fp64", block_sparse=1, trunc_thr=c["thr"], tol_omega=1e-13, tol_amp=1e-11, max_iter=100)
+    r = ctx.solve(beta, mu, ng, **kw)
+    assert r["converged"] and abs(r["omega"] - gold["omega"]) < 1e-9
+    d, _ = ctx.adjoint(with_rdm1=False)
+
+    def om(b, m):
+        x = ctx.solve(b, m, ng, **kw)
+        assert x["converged"]
+        return x["omega"]
+
+    def rich(f, h):
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(2 * h) - f(-2 * h)) / (4 * h)
+        return (4 * d1 - d2) / 3
+
+    h = 1e-3
+    dmu = rich(lambda e: om(beta, mu + e), h)
+    dbeta = rich(lambda e: om(beta + e, mu), h)
+    assert abs(d["dOmega_dmu"] - dmu) < 1e-7 * max(1.0, abs(dmu)), (d["dOmega_dmu"], dmu)
+    assert abs(d["dOmega_dbeta"] - dbeta) < 1e-7 * max(1.0, abs(dbeta)), (d["dOmega_dbeta"], dbeta)
