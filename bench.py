@@ -566,6 +566,23 @@ def run_gpu(args, rank, world):
              "omega": sol["omega"], "abs_dOmega_vs_oracle": abs(sol["omega"] - gold["omega"]) if gold else None,
              "oracle": "block-sparse oracle, converged to |dOmega_CC| < 1e-11" if gold else None,
              "how": "ft_ccsd_solve FP64 block-sparse from s = 0 to |dOmega_CC| < 1e-11, host-timed"}
+    # the FP64 lambda sweep and response of that solve: N, E, S and the
+    # 1-RDM against the oracle's central differences of converged solves
+    adjoint = None
+    if not args.no_adjoint and sol["converged"]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ad, rdm1 = ctx.adjoint(with_rdm1=True)
+        torch.cuda.synchronize()
+        adjoint = {"s_total": time.perf_counter() - t0, "lambda_iterations": ad["iterations"],
+                   "N": ad["N"], "E": ad["E"], "S": ad["S"], "trace_rdm1": float(rdm1.trace()),
+                   "how": "ft_ccsd_adjoint after the block-sparse solve: FP64 lambda sweep through the transpose "
+                          "of the block-sparse S kernel, response (App. B), host-timed"}
+        rp = os.path.join(GOLD, "oracle_ueg57_response.json")
+        if os.path.exists(rp):
+            gr = json.load(open(rp))
+            adjoint["abs_diff_vs_oracle"] = {k: abs(ad[k] - gr[k]) for k in ("N", "E", "S")}
+            adjoint["oracle"] = gr["how"]
     # timed steps: W warm-up iterations, then K iterations each bracketed by
     # CUDA events on the library stream (one captured graph per iteration);
     # the amplitudes (32 x 114^3 x 8 B = 379 MB each for s and S) exceed the
@@ -660,7 +677,7 @@ def run_gpu(args, rank, world):
                 "flops_note": "2 sum_s rows_s^3 over the charge sectors of the five products of two four-index "
                               "factors, every tau point; the dense schedule's 7.0e14 flops per iteration are in "
                               "extra.dense_mixed",
-                "time_to_1e-6": solve,
+                "time_to_1e-6": solve, "adjoint": adjoint,
                 "fp64_block_sparse_vs_dense_mixed_time_to_solution": (dts / t_sol if dts else None),
                 "peaks": pk, "roofline": roof, "kernels": class_table(kstats, prof_steps),
                 "e2e": e2e, "gpu_launches": k_iter * args.steps, "clocks": clk.summary()}
@@ -795,7 +812,21 @@ def bench_ueg81(ftcc, torch, dev, world, args):
     ctx.iterate(10)
     e1.record(st)
     torch.cuda.synchronize()
-    sparse = {"s_per_iteration": e0.elapsed_time(e1) / 1e3 / 10, "solve_s_total": t_sol,
+    # the lambda sweep and response of the converged solve (dOmega/dmu,
+    # dOmega/dbeta, N, E, S)
+    adj = None
+    if not args.no_adjoint and rs["converged"]:
+        ctx.solve(c["beta"], mu, c["ngrid"], trunc_thr=c["thr"], **sparse_opts())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ad, _ = ctx.adjoint(with_rdm1=True)
+        torch.cuda.synchronize()
+        adj = {"s_total": time.perf_counter() - t0, "lambda_iterations": ad["iterations"],
+               "dOmega_dmu": ad["dOmega_dmu"], "dOmega_dbeta": ad["dOmega_dbeta"], "N": ad["N"], "E": ad["E"],
+               "S": ad["S"],
+               "check": "tests/test_gpu_sparse.py compares dOmega/dmu and dOmega/dbeta with central differences "
+                        "(one Richardson step) of converged block-sparse solves to 1e-7"}
+    sparse = {"s_per_iteration": e0.elapsed_time(e1) / 1e3 / 10, "solve_s_total": t_sol, "adjoint": adj,
               "iterations": rs["iterations"], "converged": bool(rs["converged"]), "omega": rs["omega"],
               "abs_dOmega_vs_oracle": abs(rs["omega"] - g81["omega"]) if g81 else None,
               "peak_device_memory_gb": torch.cuda.max_memory_allocated() / 1e9,

@@ -192,9 +192,14 @@ typedef struct {
  *                       such a system (FTCC_ERR_INVALID_ARG otherwise), no
  *                       truncation (trunc_thr removes nothing) and the Simpson
  *                       integral form; stream_tau is ignored.
- *                       ftcc_get_amplitudes and ftcc_eval_s convert between
- *                       the dense layouts and the compressed one; the adjoint
- *                       returns FTCC_ERR_UNSUPPORTED. */
+ *                       ft_ccsd_adjoint (the lambda sweep through the transpose
+ *                       of the block-sparse S kernel), ftcc_rdm2 and
+ *                       ftcc_mu_for_n work on it; ftcc_get_amplitudes,
+ *                       ftcc_eval_s and ftcc_eval_s_vjp convert between the
+ *                       dense layouts and the compressed one (inputs projected
+ *                       onto the charge-conserving elements); ftcc_propagate,
+ *                       ftcc_propagate_adjoint and ftcc_get_lambda take dense
+ *                       layouts only (FTCC_ERR_UNSUPPORTED). */
 typedef struct {
   double tol_omega, tol_amp, damping, trunc_thr;
   int max_iter, precision, refine_max_iter;

@@ -3453,6 +3453,7 @@ ftcc_status ftcc_propagate_adjoint(ftcc_ctx* c, const char* slots, const double*
 ftcc_status ftcc_get_lambda(ftcc_ctx* c, double* m1, double* m2) {
   if (!c) return FTCC_ERR_INVALID_ARG;
   if (!c->batch || !c->batch->lambda_done) return fail(c, FTCC_ERR_STATE, "run ft_ccsd_adjoint first");
+  if (c->batch->sparse) return fail(c, FTCC_ERR_UNSUPPORTED, "block_sparse: dense layouts only");
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     const long long n1 = static_cast<long long>(B.ng) * B.no * B.nv, n2 = n1 * B.no * B.nv;
