@@ -174,6 +174,10 @@ struct Batch {
   Buf m1, m2, mn1, mn2, u1, u2, tb1, tb2, dE1, cz, lpart;
   Buf facOz, facVz, epsz;        // stacked [nz][no], [nz][nv], [nz][N] for the response
   bool lambda_done = false;
+  // the response of every member, computed once per converged multipliers
+  bool resp_done = false;
+  std::vector<ftcc_adjoint_result> resp;
+  std::vector<std::vector<double>> resp_rdm;
   bool adjoint_fp32 = false;     // the multipliers live on the FP32 solver (mixed adjoint)
   int lambda_iterations = 0;
   double prof_ms[8] = {0}, prof_bytes[8] = {0}, prof_flops[8] = {0};
@@ -3077,6 +3081,7 @@ ftcc_status ft_ccsd_iterate(ftcc_ctx* c, int n_iter, ftcc_result* out) {
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
+    if (n_iter > 0) B.lambda_done = B.resp_done = false;   // the amplitudes move: multipliers are stale
     run_batch(B, n_iter);
     check_device_error(B.home);
     if (out) fill_result(B, c->member, read_states(B), out);
@@ -3179,9 +3184,11 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
   return run_guarded(c, [&]() -> ftcc_status {
     Batch& B = *c->batch;
     CU(cudaSetDevice(B.home->device));
-    std::vector<ftcc_adjoint_result> res;
-    std::vector<std::vector<double>> rdms;
-    if (B.active == 1 && B.opt.mixed_adjoint) {
+    std::vector<ftcc_adjoint_result>& res = B.resp;
+    std::vector<std::vector<double>>& rdms = B.resp_rdm;
+    if (B.resp_done) {
+      // another member of a batch whose response is already known
+    } else if (B.active == 1 && B.opt.mixed_adjoint) {
       // the lambda sweep and the response on the FP32 solver: FP32
       // multipliers, BF16X3 contractions in the VJP, FP64 propagator
       // factors, weights and sums
@@ -3198,6 +3205,7 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
       B.adjoint_fp32 = false;
       response<double>(B, *B.s64, res, rdms);
     }
+    B.resp_done = true;
     if (out) *out = res[c->member];
     if (rdm1) memcpy(rdm1, rdms[c->member].data(), rdms[c->member].size() * sizeof(double));
     check_device_error(B.home);

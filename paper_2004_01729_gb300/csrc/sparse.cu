@@ -303,49 +303,66 @@ __global__ void sp_s2_kernel(const double* __restrict__ R, const double* __restr
 // (p, q); rowA = p n + q, rowB = p n + q, or q n + p with swapB; the output
 // position is p_r s0 + q_r s1 + p_c s2 + q_c s3.  A and B are [n^2][n]
 // views of N^3 tensors.
-constexpr int kSecT = 16;   // output tile edge
-constexpr int kSecK = 16;   // K step
+// The FP64 pipe bounds these products (a 16-wide padded tile kept it 98 %
+// busy with about half of its FMAs on padding), so a CTA takes a tile of
+// at most kSecT x kSecT outputs of one sector and assigns only the valid
+// ones (flattened, kSecO per thread), and every K chunk runs its exact
+// length: no FMA touches padding.
+constexpr int kSecT = 48;                      // output tile edge
+constexpr int kSecKc = 32;                     // K chunk staged in shared memory
+constexpr int kSecThreads = 256;
+constexpr int kSecO = (kSecT * kSecT + kSecThreads - 1) / kSecThreads;   // outputs per thread
 
-__global__ void __launch_bounds__(kSecT * kSecT) sector_gemm_kernel(SecGemmArgs g) {
-  __shared__ double As[kSecK][kSecT + 1], Bs[kSecK][kSecT + 1];
+__global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g) {
+  __shared__ double As[kSecKc][kSecT + 1], Bs[kSecKc][kSecT + 1];
   const int4 w = g.work[blockIdx.x];
-  const int4 sec = g.sec[w.x];   // row offset, rows, K offset, K count
+  const int4 sec = g.sec[w.x];   // entry offset, rows, K offset, K count
   const long long x = blockIdx.y;
   const double* A = g.A + x * g.ax;
   const double* B = g.B + x * g.bx;
   const int n = g.n;
-  const int tr = threadIdx.x / kSecT, tc = threadIdx.x % kSecT;
-  const int r = w.y + tr, c = w.z + tc;
-  const bool rin = r < sec.y, cin = c < sec.y;
-  // loader: thread (rr, kk) loads A[row rr][k kk] and B[row rr][k kk]
-  // (consecutive threads walk one row's K list)
-  const int lk = threadIdx.x % kSecK, lr = threadIdx.x / kSecK;
-  const int ar = w.y + lr, bc = w.z + lr;
-  long long arow = -1, brow = -1;
-  if (ar < sec.y) {
-    const int2 pr = g.ent[sec.x + ar];
-    arow = (static_cast<long long>(pr.x) * n + pr.y) * n;
-  }
-  if (bc < sec.y) {
-    const int2 pr = g.ent[sec.x + bc];
-    brow = (g.swapB ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y) * n;
-  }
-  double acc = 0.0;
-  for (int k0 = 0; k0 < sec.w; k0 += kSecK) {
-    const int kk = k0 + lk;
-    const int kv = kk < sec.w ? g.kl[sec.z + kk] : -1;
-    As[lk][lr] = (arow >= 0 && kv >= 0) ? A[arow + kv] : 0.0;
-    Bs[lk][lr] = (brow >= 0 && kv >= 0) ? B[brow + kv] : 0.0;
+  const int nr = min(kSecT, sec.y - w.y), nc = min(kSecT, sec.y - w.z);
+  const int nout = nr * nc;
+  double acc[kSecO];
+#pragma unroll
+  for (int j = 0; j < kSecO; ++j) acc[j] = 0.0;
+  for (int k0 = 0; k0 < sec.w; k0 += kSecKc) {
+    const int kc = min(kSecKc, sec.w - k0);
+    // stage A rows [nr][kc] and B rows [nc][kc] (consecutive threads walk a row's K list)
+    for (int idx = threadIdx.x; idx < nr * kc; idx += kSecThreads) {
+      const int r = idx / kc, k = idx - r * kc;
+      const int2 pr = g.ent[sec.x + w.y + r];
+      As[k][r] = A[(static_cast<long long>(pr.x) * n + pr.y) * n + g.kl[sec.z + k0 + k]];
+    }
+    for (int idx = threadIdx.x; idx < nc * kc; idx += kSecThreads) {
+      const int c = idx / kc, k = idx - c * kc;
+      const int2 pr = g.ent[sec.x + w.z + c];
+      const long long row = g.swapB ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
+      Bs[k][c] = B[row * n + g.kl[sec.z + k0 + k]];
+    }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kSecK; ++k) acc = fma(As[k][tr], Bs[k][tc], acc);
+    for (int j = 0; j < kSecO; ++j) {
+      const int o = threadIdx.x + j * kSecThreads;
+      if (o < nout) {
+        const int r = o / nc, c = o - r * nc;
+        double a = acc[j];
+        for (int k = 0; k < kc; ++k) a = fma(As[k][r], Bs[k][c], a);
+        acc[j] = a;
+      }
+    }
     __syncthreads();
   }
-  if (rin && cin) {
-    const int2 pr = g.ent[sec.x + r], pc = g.ent[sec.x + c];
-    const long long o = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
-                        static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
-    g.C[o] += g.alpha * acc;
+#pragma unroll
+  for (int j = 0; j < kSecO; ++j) {
+    const int o = threadIdx.x + j * kSecThreads;
+    if (o < nout) {
+      const int r = o / nc, c = o - r * nc;
+      const int2 pr = g.ent[sec.x + w.y + r], pc = g.ent[sec.x + w.z + c];
+      const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
+                          static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
+      g.C[q] += g.alpha * acc[j];
+    }
   }
 }
 
@@ -618,53 +635,59 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
 // are p n + q or (swapped) q n + p; gpos = p_o g0 + q_o g1 + p_s g2 + q_s g3.
 // With dx = 0 the output is fixed (an integral block) and the kernel sums
 // the nx slices of G and A itself.
-__global__ void __launch_bounds__(kSecT * kSecT) sector_tn_kernel(SecTnArgs g) {
-  __shared__ double Gs[kSecK][kSecT + 1], As[kSecK][kSecT + 1];
+__global__ void __launch_bounds__(kSecThreads) sector_tn_kernel(SecTnArgs g) {
+  __shared__ double Gs[kSecKc][kSecT + 1], As[kSecKc][kSecT + 1];
   const int4 w = g.work[blockIdx.x];
   const int4 sec = g.sec[w.x];
   const int n = g.n;
-  const int to = threadIdx.x / kSecT, tk = threadIdx.x % kSecT;   // output row, k column
-  const int lo = threadIdx.x / kSecK, ls = threadIdx.x % kSecK;   // loader: output / k row, summed row
+  const int no_ = min(kSecT, sec.y - w.y), nk = min(kSecT, sec.w - w.z);   // output rows, k columns
+  const int nout = no_ * nk;
   const int xr0 = g.dx ? blockIdx.y : 0, xr1 = g.dx ? blockIdx.y + 1 : g.nx;
-  // loader entries
-  const int eo = w.y + lo;                 // output row this thread loads G for
-  const int ek = w.z + lo;                 // k column this thread loads A for
-  int2 po = make_int2(0, 0);
-  const bool oin = eo < sec.y;
-  if (oin) po = g.ent[sec.x + eo];
-  const int kv = ek < sec.w ? g.kl[sec.z + ek] : -1;
-  double acc = 0.0;
+  double acc[kSecO];
+#pragma unroll
+  for (int j = 0; j < kSecO; ++j) acc[j] = 0.0;
   for (int x = xr0; x < xr1; ++x) {
     const double* G = g.G + x * g.gx;
     const double* A = g.A + x * g.ax;
-    for (int s0 = 0; s0 < sec.y; s0 += kSecK) {
-      const int es = s0 + ls;
-      double gv = 0.0, av = 0.0;
-      if (es < sec.y) {
-        const int2 ps = g.ent[sec.x + es];
-        if (oin)
-          gv = G[static_cast<long long>(po.x) * g.g0 + static_cast<long long>(po.y) * g.g1 +
-                 static_cast<long long>(ps.x) * g.g2 + static_cast<long long>(ps.y) * g.g3];
-        if (kv >= 0) {
-          const long long srow = g.swapA ? static_cast<long long>(ps.y) * n + ps.x
-                                         : static_cast<long long>(ps.x) * n + ps.y;
-          av = A[srow * n + kv];
-        }
+    for (int s0 = 0; s0 < sec.y; s0 += kSecKc) {
+      const int sc = min(kSecKc, sec.y - s0);
+      // Gs[s][o] = G(output row o, summed row s), As[s][k] = A(summed row s, column k)
+      for (int idx = threadIdx.x; idx < no_ * sc; idx += kSecThreads) {
+        const int o = idx / sc, ss = idx - o * sc;
+        const int2 po = g.ent[sec.x + w.y + o], ps = g.ent[sec.x + s0 + ss];
+        Gs[ss][o] = G[static_cast<long long>(po.x) * g.g0 + static_cast<long long>(po.y) * g.g1 +
+                      static_cast<long long>(ps.x) * g.g2 + static_cast<long long>(ps.y) * g.g3];
       }
-      Gs[ls][lo] = gv;
-      As[ls][lo] = av;
+      for (int idx = threadIdx.x; idx < nk * sc; idx += kSecThreads) {
+        const int ss = idx / nk, k = idx - ss * nk;
+        const int2 ps = g.ent[sec.x + s0 + ss];
+        const long long srow = g.swapA ? static_cast<long long>(ps.y) * n + ps.x : static_cast<long long>(ps.x) * n + ps.y;
+        As[ss][k] = A[srow * n + g.kl[sec.z + w.z + k]];
+      }
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < kSecK; ++k) acc = fma(Gs[k][to], As[k][tk], acc);
+      for (int j = 0; j < kSecO; ++j) {
+        const int o = threadIdx.x + j * kSecThreads;
+        if (o < nout) {
+          const int r = o / nk, k = o - r * nk;
+          double a = acc[j];
+          for (int ss = 0; ss < sc; ++ss) a = fma(Gs[ss][r], As[ss][k], a);
+          acc[j] = a;
+        }
+      }
       __syncthreads();
     }
   }
-  const int ro = w.y + to, rk = w.z + tk;
-  if (ro < sec.y && rk < sec.w) {
-    const int2 pr = g.ent[sec.x + ro];
-    const long long orow = g.swapD ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
-    const long long o = (g.dx ? static_cast<long long>(blockIdx.y) * g.dx : 0) + orow * n + g.kl[sec.z + rk];
-    g.D[o] += g.alpha * acc;
+#pragma unroll
+  for (int j = 0; j < kSecO; ++j) {
+    const int o = threadIdx.x + j * kSecThreads;
+    if (o < nout) {
+      const int r = o / nk, k = o - r * nk;
+      const int2 pr = g.ent[sec.x + w.y + r];
+      const long long orow = g.swapD ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
+      const long long q = (g.dx ? static_cast<long long>(blockIdx.y) * g.dx : 0) + orow * n + g.kl[sec.z + w.z + k];
+      g.D[q] += g.alpha * acc[j];
+    }
   }
 }
 
@@ -927,7 +950,7 @@ cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* im
 cudaError_t launch_sector_gemm(const SecGemmArgs& g, int nwork, int nx, cudaStream_t st) {
   if (nwork <= 0 || nx <= 0) return cudaSuccess;
   if (nx > 65535) return cudaErrorInvalidValue;
-  sector_gemm_kernel<<<dim3(nwork, nx), kSecT * kSecT, 0, st>>>(g);
+  sector_gemm_kernel<<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 int sector_tile() { return kSecT; }
@@ -974,7 +997,7 @@ cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, int n, int nx,
 cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st) {
   if (nwork <= 0 || g.nx <= 0) return cudaSuccess;
   if (g.nx > 65535) return cudaErrorInvalidValue;
-  sector_tn_kernel<<<dim3(nwork, g.dx ? g.nx : 1), kSecT * kSecT, 0, st>>>(g);
+  sector_tn_kernel<<<dim3(nwork, g.dx ? g.nx : 1), kSecThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
