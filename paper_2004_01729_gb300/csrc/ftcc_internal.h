@@ -290,6 +290,13 @@ struct SecGemmArgs {
   const int* kl;         // summed-index list of every sector
   const int4* sec;       // (entry offset, rows, K offset, K count)
   const int4* work;      // (sector, row tile start, column tile start, 0)
+  // optional second product over the same rows and K list: C += alpha (A B^T + A2 B2^T)
+  const double* A2;
+  const double* B2;
+  // anti4: rows (i, j), columns (a, b); the value is added to C[i][j][a],
+  // C[j][i][a] (-), C[i][j][b] (-), C[j][i][b] (N^3 storage, the fourth index
+  // implied), i.e. to all four orientations of an antisymmetric result
+  int anti4;
 };
 // Transposed sector products (see sparse.cu): D[orow(e_o)][k] += alpha
 // sum_{e_s} G[gpos(e_o, e_s)] A[srow(e_s)][k]; dx = 0: D fixed, the kernel
@@ -344,8 +351,10 @@ cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voo
 cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
                           double* tp, double* tr, double* xp, cudaStream_t st);
 cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st);
+// anti != 0: W'_mnij and W'_abef antisymmetrised in (i, j) / (a, b) (the
+// unordered-pair ladders)
 cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
-                            double* wab, double* wr, cudaStream_t st);
+                            double* wab, double* wr, int anti, cudaStream_t st);
 cudaError_t launch_sp_rinit(const double* t1, const double* t2, const double* Ft, const double* Ft2, const SpBlocks& V,
                             const int16_t* imp, int n, int nx, double* R, cudaStream_t st);
 cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* imp, int n, int nx, double* S2,

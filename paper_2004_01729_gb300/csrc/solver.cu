@@ -193,7 +193,7 @@ struct Batch {
   // imp[a][b][c] (int16, N^3) and the pair-charge sectors
   bool sparse = false;
   Buf imp;
-  SecTab ssum, sdiff;
+  SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
   ~Batch();
 };
 
@@ -893,7 +893,8 @@ struct Solver {
   }
 
   void sector_product(const SecTab& tab, const T* A, long long ax, const T* Bm, long long bx, T* C, double alpha,
-                      int swapB, long long s0, long long s1, long long s2, long long s3) {
+                      int swapB, long long s0, long long s1, long long s2, long long s3, const T* A2 = nullptr,
+                      const T* B2 = nullptr, int anti4 = 0) {
     if constexpr (sizeof(T) == 8) {
       const long long n3 = static_cast<long long>(no) * no * no;
       SecGemmArgs g{};
@@ -914,8 +915,12 @@ struct Solver {
       g.kl = static_cast<const int*>(tab.kl.p);
       g.sec = static_cast<const int4*>(tab.sec.p);
       g.work = static_cast<const int4*>(tab.work.p);
-      if (counting) gemm_flops += static_cast<long long>(tab.flops * nx);
-      timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(T), tab.flops * nx,
+      g.A2 = A2;
+      g.B2 = B2;
+      g.anti4 = anti4;
+      const double fl = tab.flops * nx * (A2 ? 2 : 1);
+      if (counting) gemm_flops += static_cast<long long>(fl);
+      timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl,
                    [&] { CU(launch_sector_gemm(g, tab.nwork, nx, st())); });
     }
   }
@@ -925,7 +930,16 @@ struct Solver {
   // diagonal and the four-index factors in N^3 storage; the five products
   // of two four-index factors (W_mnij's tau term, W_mbej's X term, the two
   // ladders and the ring) run over pair-charge sectors.
-  void sparse_s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur) {
+  //
+  // Outside the transpose's recomputation (pairs = true) W_mnij's tau term
+  // and both ladders run over unordered pairs (i < j, m < n, e < f, a < b):
+  // with W'_mnij and W'_abef antisymmetrised (their s1 terms become the
+  // P(ij) / P(ab) forms), W^A_ijmn = W'^A_ijmn + sum_{e<f} tau_ij^ef <mn||ef>
+  // and L_ij^ab = sum_{m<n} W^A_ijmn tau_mn^ab + sum_{e<f} tau_ij^ef W'^A_abef
+  // give P(ij)P(ab) of the two ladders, added to R as L/4 in its four
+  // orientations (R enters S2 through P(ij)P(ab)); each product is an eighth
+  // of its ordered form.  The transpose recomputes the ordered form.
+  void sparse_s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur, bool pairs = true) {
     if constexpr (sizeof(T) == 8) {
       nx = nxcur;
       const int n = no;
@@ -959,18 +973,25 @@ struct Solver {
       v.Ft2 = (double*)Ft2.p;
       timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors(v, nx, st())); });
       timed_launch(kClsScatter, 3 * slice + 6.0 * n3 * sizeof(T), 0.0,
-                   [&] { CU(launch_sp_wbase(t1c, VB, imp, n, nx, pw1, pwab, pwr, st())); });
+                   [&] { CU(launch_sp_wbase(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0, st())); });
       // W'_mnij += 1/2 tau_ij^ef <mn||ef>        rows (i,j) | (m,n) by q_i + q_j, sum over e
-      sector_product(b->ssum, pta, n3, VB.oovv, 0, pw1, 0.5, 0, n2, n, 1, 0);
+      // (unordered: W^A_ijmn += sum_{e<f} tau_ij^ef <mn||ef> for i < j, m < n)
+      if (pairs) sector_product(b->ssum_u, pta, n3, VB.oovv, 0, pw1, 1.0, 0, n2, n, 1, 0);
+      else sector_product(b->ssum, pta, n3, VB.oovv, 0, pw1, 0.5, 0, n2, n, 1, 0);
       // W_mbej -= X_jn^fb <mn||ef>                rows (j,b) | (m,e) by q_j - q_b, sum over n
       sector_product(b->sdiff, pxp, n3, static_cast<const double*>(Vp.p), 0, pwr, -1.0, 0, n2, n, 1, 0);
       timed_launch(kClsScatter, 5 * slice, 0.0, [&] {
         CU(launch_sp_rinit(t1c, t2c, (double*)Ft.p, (double*)Ft2.p, VB, imp, n, nx, pR, st()));
       });
-      // hole ladder 1/8 W'_ijmn tau_mn^ab          rows (i,j) | (a,b) by q_i + q_j, sum over m
-      sector_product(b->ssum, pw1, n3, ptp, n3, pR, 0.125, 0, n2, n, 1, 0);
-      // particle ladder 1/8 tau_ij^ef W'_abef      rows (i,j) | (a,b), sum over e
-      sector_product(b->ssum, pta, n3, pwab, n3, pR, 0.125, 0, n2, n, 1, 0);
+      if (pairs) {
+        // L/4 in the four orientations of R: rows i < j | a < b, sums over m < n and e < f
+        sector_product(b->ssum_u, pw1, n3, ptp, n3, pR, 0.25, 0, 0, 0, 0, 0, pta, pwab, 1);
+      } else {
+        // hole ladder 1/8 W'_ijmn tau_mn^ab          rows (i,j) | (a,b) by q_i + q_j, sum over m
+        sector_product(b->ssum, pw1, n3, ptp, n3, pR, 0.125, 0, n2, n, 1, 0);
+        // particle ladder 1/8 tau_ij^ef W'_abef      rows (i,j) | (a,b), sum over e
+        sector_product(b->ssum, pta, n3, pwab, n3, pR, 0.125, 0, n2, n, 1, 0);
+      }
       // ring s_im^ae W_mbej                        rows (i,a) | (j,b) by q_i - q_a, sum over m
       sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
       timed_launch(kClsScatter, 6 * slice, 0.0,
@@ -1015,7 +1036,7 @@ struct Solver {
   // pass gives Abar += alpha Cbar B and Bbar += alpha Cbar^T A.
   void sparse_vjp(const T* t1c, const T* t2c, const T* u1, const T* u2, T* t1bar, T* t2bar, int nxcur) {
     if constexpr (sizeof(T) == 8) {
-      sparse_s_kernel(t1c, t2c, t1bar, t2bar, nxcur);
+      sparse_s_kernel(t1c, t2c, t1bar, t2bar, nxcur, false);
       const int n = no;
       const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
       const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
@@ -1396,7 +1417,8 @@ Batch::~Batch() {
   }
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
-               &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work};
+               &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
+               &ssum_u.sec, &ssum_u.work};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1438,12 +1460,12 @@ void build_implied(Batch& B, const ftcc_ctx* c) {
 // sectors of ordered pairs (p, q) by q_p + q_q (diff = false) or q_p - q_q;
 // the summed index of a sector runs over the first (sum) or second (diff)
 // letters of its pairs
-void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T) {
+void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unordered = false) {
   const int n = B.N, tile = sector_tile();
   std::unordered_map<uint64_t, int> sid;
   std::vector<std::vector<int2>> rows;
   for (int p = 0; p < n; ++p)
-    for (int q = 0; q < n; ++q) {
+    for (int q = unordered ? p + 1 : 0; q < n; ++q) {
       std::array<int, 4> ch;
       for (int k = 0; k < 4; ++k) ch[k] = c->charge[p][k] + (diff ? -c->charge[q][k] : c->charge[q][k]);
       const uint64_t key = charge_key(canon_charge(ch, c->charge_mod));
@@ -2027,6 +2049,7 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
     build_implied(*B, home);
     build_sectors(*B, home, false, B->ssum);
     build_sectors(*B, home, true, B->sdiff);
+    build_sectors(*B, home, false, B->ssum_u, true);
   }
   ensure(home, B->idxO, B->O.size() * sizeof(int));
   ensure(home, B->idxV, B->V.size() * sizeof(int));

@@ -208,7 +208,7 @@ namespace {
 struct SpW {
   const double *t1, *Voooo, *Vooov, *Vvvvv, *Vovvv, *Vovvo, *Voovo;
   const int16_t* imp;
-  int n;
+  int n, anti;
   double *w1, *wab, *wr;
 };
 
@@ -225,10 +225,19 @@ __global__ void sp_wbase_kernel(SpW a) {
     const long long o = x * n3 + e;
     {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
       const int q = impl(a.imp, n, p0, p1, p2);
-      a.w1[o] = q >= 0 ? a.Voooo[pos3(n, p2, q, p0)] - 2.0 * s1[p0] * a.Vooov[pos3(n, p2, q, p1)] : 0.0;
+      double v = 0.0;
+      if (q >= 0) {
+        v = a.Voooo[pos3(n, p2, q, p0)];
+        // antisymmetrised in (i, j): (W'_ijmn - W'_jimn) / 2 (<mn||ij> is antisymmetric already)
+        if (a.anti) v += -s1[p0] * a.Vooov[pos3(n, p2, q, p1)] + s1[p1] * a.Vooov[pos3(n, p2, q, p0)];
+        else v -= 2.0 * s1[p0] * a.Vooov[pos3(n, p2, q, p1)];
+      }
+      a.w1[o] = v;
     }
-    // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide
-    a.wab[o] = a.Vvvvv[e] - 2.0 * s1[p0] * a.Vovvv[e];
+    // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide; antisymmetrised
+    // in (a, b): <ab||ef> - s1[a] <ab||ef>_ovvv + s1[b] <ba||ef>_ovvv
+    a.wab[o] = a.anti ? a.Vvvvv[e] - s1[p0] * a.Vovvv[e] + s1[p1] * a.Vovvv[pos3(n, p1, p0, p2)]
+                      : a.Vvvvv[e] - 2.0 * s1[p0] * a.Vovvv[e];
     {   // (j, b, m) = (p0, p1, p2), e = q_b + q_m - q_j
       const int ee = impl(a.imp, n, p1, p2, p0);
       double v = 0.0;
@@ -318,14 +327,15 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g)
   const int4 w = g.work[blockIdx.x];
   const int4 sec = g.sec[w.x];   // entry offset, rows, K offset, K count
   const long long x = blockIdx.y;
-  const double* A = g.A + x * g.ax;
-  const double* B = g.B + x * g.bx;
   const int n = g.n;
   const int nr = min(kSecT, sec.y - w.y), nc = min(kSecT, sec.y - w.z);
   const int nout = nr * nc;
   double acc[kSecO];
 #pragma unroll
   for (int j = 0; j < kSecO; ++j) acc[j] = 0.0;
+  for (int prod = 0; prod < (g.A2 ? 2 : 1); ++prod) {
+  const double* A = (prod ? g.A2 : g.A) + x * g.ax;
+  const double* B = (prod ? g.B2 : g.B) + x * g.bx;
   for (int k0 = 0; k0 < sec.w; k0 += kSecKc) {
     const int kc = min(kSecKc, sec.w - k0);
     // stage A rows [nr][kc] and B rows [nc][kc] (consecutive threads walk a row's K list)
@@ -353,15 +363,27 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g)
     }
     __syncthreads();
   }
+  }
 #pragma unroll
   for (int j = 0; j < kSecO; ++j) {
     const int o = threadIdx.x + j * kSecThreads;
     if (o < nout) {
       const int r = o / nc, c = o - r * nc;
       const int2 pr = g.ent[sec.x + w.y + r], pc = g.ent[sec.x + w.z + c];
-      const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
-                          static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
-      g.C[q] += g.alpha * acc[j];
+      const double v = g.alpha * acc[j];
+      if (g.anti4) {
+        // (i, j) = pr, (a, b) = pc: the four orientations of the antisymmetric result
+        double* C = g.C + x * g.cx;
+        const long long ni = pr.x, nj = pr.y;
+        C[(ni * n + nj) * n + pc.x] += v;
+        C[(nj * n + ni) * n + pc.x] -= v;
+        C[(ni * n + nj) * n + pc.y] -= v;
+        C[(nj * n + ni) * n + pc.y] += v;
+      } else {
+        const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
+                            static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
+        g.C[q] += v;
+      }
     }
   }
 }
@@ -925,9 +947,9 @@ cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st) {
 }
 
 cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
-                            double* wab, double* wr, cudaStream_t st) {
+                            double* wab, double* wr, int anti, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  SpW a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, w1, wab, wr};
+  SpW a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, anti, w1, wab, wr};
   sp_wbase_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
