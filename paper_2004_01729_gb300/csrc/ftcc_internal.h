@@ -199,6 +199,12 @@ struct PropArgs {
   // block-sparse storage (null: dense): doubles are [i][j][a] with b =
   // imp[i][j][a] (no = nv = N, holes skipped), singles the diagonal [i]
   const int16_t* imp;
+  // with imp, propagation of the doubles only: the canonical elements
+  // (i < j, a < b) of the antisymmetric s2; each is propagated once and
+  // written to its four orientations with their signs (the energy and the
+  // maxima count it for all four)
+  const int* canon;
+  long long ncanon;
   int arith64;                   // FP32 storage: 0 = FP32 recurrence and energy sums, 1 = FP32
                                  // recurrence with FP64 energy sums, 2 = FP64 for both
 };

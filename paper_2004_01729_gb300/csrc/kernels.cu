@@ -741,7 +741,11 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
   const bool damped = a.damping != 1.0;
   const EA cE = static_cast<EA>(a.cE);
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long mu = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; mu < size; mu += stride) {
+  const bool canon = sparse && NS == 4 && a.canon != nullptr;
+  const long long nloop = canon ? a.ncanon : size;
+  for (long long cidx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; cidx < nloop;
+       cidx += stride) {
+    const long long mu = canon ? a.canon[cidx] : cidx;
     int i, j = 0, aa, b = 0;
     if (sparse) {
       // [i][j][a] with b implied (a hole of the storage is skipped), or the
@@ -816,6 +820,14 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
     // singles of this tau point; with diagonal singles only a = i (then b = j)
     // carries the s_i^a s_j^b energy term
     const T* s1y = (t1E && (!sparse || aa == i)) ? t1E + y0 * n1 : nullptr;
+    // offsets of the (ji)(ab), (ij)(ba) and (ji)(ba) orientations from mu
+    long long mirror[3] = {0, 0, 0};
+    if (canon) {
+      const long long N = a.N;
+      mirror[0] = (static_cast<long long>(j) * N + i) * N + aa - mu;
+      mirror[1] = (static_cast<long long>(i) * N + j) * N + b - mu;
+      mirror[2] = (static_cast<long long>(j) * N + i) * N + b - mu;
+    }
     const int oi = sparse ? i : i * a.nv + aa, oj = sparse ? j : j * a.nv + b;
     EA* ea = eacc + y0 * kPropThreads + threadIdx.x;
     for (int y = y0; y < y1; ++y) {
@@ -851,13 +863,20 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
       if (damped) next = (A(1) - damp) * old + damp * next;
       const T stored = static_cast<T>(next);
       *tq = stored;
+      if (canon) {   // the other three orientations of the antisymmetric element
+        tq[mirror[0]] = -stored;
+        tq[mirror[1]] = -stored;
+        tq[mirror[2]] = stored;
+      }
       // convergence maxima in the storage type, on what the next iteration reads
       dmax = max_abs(dmax, stored - tp_old);
       smax = max_abs(smax, stored);
       if (wE) {
-        EA e = cE * static_cast<EA>(stored);
+        // canonical: the four orientations give 4 w s; the s1 s1 term reaches
+        // two of them (a = i and its (ji)(ba) image)
+        EA e = (canon ? EA(4) : EA(1)) * cE * static_cast<EA>(stored);
         if (NS == 4 && s1y) {
-          e += EA(0.5) * static_cast<EA>(s1y[oi]) * static_cast<EA>(s1y[oj]);
+          e += (canon ? EA(1) : EA(0.5)) * static_cast<EA>(s1y[oi]) * static_cast<EA>(s1y[oj]);
           s1y += n1;
         }
         *ea += w * e;

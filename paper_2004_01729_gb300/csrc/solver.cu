@@ -193,6 +193,8 @@ struct Batch {
   // imp[a][b][c] (int16, N^3) and the pair-charge sectors
   bool sparse = false;
   Buf imp;
+  Buf canon;                     // canonical doubles positions (i < j, a < b) of the N^3 storage
+  long long ncanon = 0;
   SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
   ~Batch();
 };
@@ -1418,7 +1420,7 @@ Batch::~Batch() {
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
                &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
-               &ssum_u.sec, &ssum_u.work};
+               &ssum_u.sec, &ssum_u.work, &canon};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1454,6 +1456,18 @@ void build_implied(Batch& B, const ftcc_ctx* c) {
       }
   ensure(B.home, B.imp, n3 * sizeof(int16_t));
   CU(cudaMemcpyAsync(B.imp.p, t.data(), n3 * sizeof(int16_t), cudaMemcpyHostToDevice, B.home->st));
+  // canonical positions of the antisymmetric doubles: i < j, a < b
+  std::vector<int> cp;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      for (int a = 0; a < n; ++a) {
+        const long long e = (static_cast<long long>(i) * n + j) * n + a;
+        if (t[e] > a) cp.push_back(static_cast<int>(e));
+      }
+  B.ncanon = static_cast<long long>(cp.size());
+  ensure(B.home, B.canon, std::max<size_t>(1, cp.size()) * sizeof(int));
+  if (!cp.empty())
+    CU(cudaMemcpyAsync(B.canon.p, cp.data(), cp.size() * sizeof(int), cudaMemcpyHostToDevice, B.home->st));
   CU(cudaStreamSynchronize(B.home->st));
 }
 
@@ -1647,7 +1661,7 @@ Solver<T>& make_solver(Batch& B, int kind) {
         CU(cudaMemsetAsync(s.t2.p, 0, g * n2 * sizeof(T), h->st));
         s.sparse_alloc();
         s.nb1 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((n1 + 127) / 128)));
-        s.nb2 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((n2 + 127) / 128)));
+        s.nb2 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((B.ncanon + 127) / 128)));
         ensure(h, s.part1, static_cast<size_t>(s.nb1) * (s.ng + 2) * sizeof(double));
         ensure(h, s.part2, static_cast<size_t>(s.nb2) * (s.ng + 2) * sizeof(double));
         return s;
@@ -1699,6 +1713,10 @@ PropArgs prop_args(Batch& B, int nslot) {
   if (B.sparse) {
     a.size = nslot == 2 ? B.N : static_cast<long long>(B.N) * B.N * B.N;
     a.imp = static_cast<const int16_t*>(B.imp.p);
+    if (nslot == 4) {
+      a.canon = static_cast<const int*>(B.canon.p);
+      a.ncanon = B.ncanon;
+    }
   }
   a.y0 = 0;
   a.y1 = B.ng;
