@@ -46,6 +46,17 @@ __device__ __forceinline__ int impl(const int16_t* __restrict__ imp, int n, int 
   return imp[(static_cast<long long>(a) * n + b) * n + c];
 }
 
+// (p0, p1, p2) of the N^3 position e in 32-bit arithmetic (N^3 < 2^31): a
+// 64-bit division or remainder is a long instruction sequence, and three of
+// them per element dominated the element-wise kernels
+__device__ __forceinline__ void dec3(uint32_t e, uint32_t n, int& p0, int& p1, int& p2) {
+  const uint32_t q = e / n;
+  p2 = static_cast<int>(e - q * n);
+  const uint32_t r = q / n;
+  p1 = static_cast<int>(q - r * n);
+  p0 = static_cast<int>(r);
+}
+
 __device__ __forceinline__ long long pos3(int n, int a, int b, int c) {
   return (static_cast<long long>(a) * n + b) * n + c;
 }
@@ -66,9 +77,8 @@ __global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __res
   const double* s2 = t2 + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int p2 = static_cast<int>(e % n);
-    const int p1 = static_cast<int>((e / n) % n);
-    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p0, p1, p2;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
     {   // ta: (i, j, a) = (p0, p1, p2), b implied
       const int b = impl(imp, n, p0, p1, p2);
@@ -165,8 +175,8 @@ __global__ void sp_vec_kernel(SpVec a) {
     cs1 += s2[pos3(n, p, m, p)] * Fme[m] - s1[m] * a.Vovov[pos3(n, m, p, p)];
   }
   const long long nn = static_cast<long long>(n) * n;
-  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
-    const int m = static_cast<int>(r / n), q = static_cast<int>(r % n);
+  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
+    const int m = static_cast<int>(r / static_cast<uint32_t>(n)), q = static_cast<int>(r - static_cast<uint32_t>(m) * n);
     const long long o1 = pos3(n, m, q, p);   // (m, q, p)
     const long long o2 = pos3(n, p, m, q);   // (p, m, q)
     const double t_mqp = s2[o1];
@@ -219,9 +229,8 @@ __global__ void sp_wbase_kernel(SpW a) {
   const double* s1 = a.t1 + x * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int p2 = static_cast<int>(e % n);
-    const int p1 = static_cast<int>((e / n) % n);
-    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p0, p1, p2;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
     {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
       const int q = impl(a.imp, n, p0, p1, p2);
@@ -272,9 +281,8 @@ __global__ void sp_rinit_kernel(SpR a) {
   const double* Ft2 = a.Ft2 + x * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int aa = static_cast<int>(e % n);
-    const int j = static_cast<int>((e / n) % n);
-    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int i, j, aa;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
     double v = 0.0;
     if (b >= 0) {
@@ -294,9 +302,8 @@ __global__ void sp_s2_kernel(const double* __restrict__ R, const double* __restr
   const double* r = R + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int aa = static_cast<int>(e % n);
-    const int j = static_cast<int>((e / n) % n);
-    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int i, j, aa;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(imp, n, i, j, aa);
     double v = 0.0;
     if (b >= 0)
@@ -397,9 +404,8 @@ __global__ void sp_thermal_eri_kernel(const double* __restrict__ eri, const int1
   const long long n3 = static_cast<long long>(n) * n * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int r = static_cast<int>(e % n);
-    const int q = static_cast<int>((e / n) % n);
-    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p, q, r;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p, q, r);
     const int s = imp[e];
     out[e] = s >= 0 ? eri[e * n + s] * f0[p] * f1[q] * f2[r] * f3[s] : 0.0;
   }
@@ -410,9 +416,8 @@ __global__ void sp_swap12_kernel(const double* __restrict__ in, int n, double* _
   const long long n3 = static_cast<long long>(n) * n * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int p2 = static_cast<int>(e % n);
-    const int p1 = static_cast<int>((e / n) % n);
-    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p0, p1, p2;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     out[e] = in[pos3(n, p0, p2, p1)];
   }
 }
@@ -476,9 +481,8 @@ __global__ void sp_s2_t_kernel(const double* __restrict__ S2b, const int16_t* __
   const double* g = S2b + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int aa = static_cast<int>(e % n);
-    const int j = static_cast<int>((e / n) % n);
-    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int i, j, aa;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(imp, n, i, j, aa);
     Rb[x * n3 + e] = b >= 0 ? g[e] - g[pos3(n, j, i, aa)] - g[pos3(n, i, j, b)] + g[pos3(n, j, i, b)] : 0.0;
   }
@@ -514,9 +518,8 @@ __global__ void sp_t2bar_kernel(SpT2 a) {
   const double* xpb = a.xpb + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int aa = static_cast<int>(e % n);
-    const int j = static_cast<int>((e / n) % n);
-    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int i, j, aa;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
     double v = 0.0;
     if (b >= 0) {
@@ -555,8 +558,8 @@ __global__ void sp_vec_t1_kernel(SpVecT a) {
   const double* S1b = a.S1b + static_cast<long long>(x) * n;
   double ftb = 0.0, ft2b = 0.0, fme = 0.0;
   const long long nn = static_cast<long long>(n) * n;
-  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
-    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
+    const int u = static_cast<int>(r / static_cast<uint32_t>(n)), w = static_cast<int>(r - static_cast<uint32_t>(u) * n);
     const int aa = impl(a.imp, n, u, w, p);                    // (i, j, a) = (u, w, aa), b = p
     if (aa >= 0) ftb += Rb[pos3(n, u, w, aa)] * s2[pos3(n, u, w, aa)];
     ft2b += Rb[pos3(n, p, u, w)] * s2[pos3(n, u, p, w)];     // (i, j, a) = (p, u, w)
@@ -601,8 +604,8 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
   const double* Fmeb = a.Fmeb + static_cast<long long>(x) * n;
   double acc = 0.0;
   const long long nn = static_cast<long long>(n) * n;
-  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
-    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
+    const int u = static_cast<int>(r / static_cast<uint32_t>(n)), w = static_cast<int>(r - static_cast<uint32_t>(u) * n);
     {   // R: p as i, (j, a) = (u, w), b = imp(p, u, w)
       const int b = impl(a.imp, n, p, u, w);
       if (b >= 0) {
@@ -740,9 +743,8 @@ __global__ void sp_fixed_bar_kernel(SpFixT a) {
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int sl = a.imp[e];
     if (sl < 0) continue;
-    const int r = static_cast<int>(e % n);
-    const int q = static_cast<int>((e / n) % n);
-    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p, q, r;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p, q, r);
     double v = 0.0;
     for (int x = 0; x < a.nx; ++x) {
       const double* s1 = a.t1 + static_cast<long long>(x) * n;
@@ -830,9 +832,8 @@ __global__ void sp_swap12_add_kernel(const double* __restrict__ in, int n, doubl
   const long long n3 = static_cast<long long>(n) * n * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int p2 = static_cast<int>(e % n);
-    const int p1 = static_cast<int>((e / n) % n);
-    const int p0 = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p0, p1, p2;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     out[e] += in[pos3(n, p0, p2, p1)];
   }
 }
@@ -856,9 +857,8 @@ __global__ void sp_energy_bar_kernel(const double* __restrict__ t1, const double
       fovb[e] += f;
     }
     if (imp[e] < 0) continue;
-    const int aa = static_cast<int>(e % n);
-    const int j = static_cast<int>((e / n) % n);
-    const int i = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int i, j, aa;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     double v = 0.0;
     for (int x = 0; x < ng; ++x) {
       v += cz[x] * 0.25 * t2[x * n3 + e];
@@ -878,8 +878,8 @@ __global__ void sp_slot_sums_kernel(const double* __restrict__ I, const double* 
   const int q = blockIdx.x;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const long long nn = static_cast<long long>(n) * n;
-  for (long long r = threadIdx.x; r < nn; r += blockDim.x) {
-    const int u = static_cast<int>(r / n), w = static_cast<int>(r % n);
+  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
+    const int u = static_cast<int>(r / static_cast<uint32_t>(n)), w = static_cast<int>(r - static_cast<uint32_t>(u) * n);
     long long e = pos3(n, q, u, w);
     acc[0] += I[e] * Ib[e];
     e = pos3(n, u, q, w);
@@ -920,9 +920,8 @@ __global__ void sp_eri_adjoint_kernel(const double* __restrict__ bar, const int1
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int s = imp[e];
     if (s < 0) continue;
-    const int r = static_cast<int>(e % n);
-    const int q = static_cast<int>((e / n) % n);
-    const int p = static_cast<int>(e / (static_cast<long long>(n) * n));
+    int p, q, r;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p, q, r);
     gamma[e * n + s] += bar[e] * f0[p] * f1[q] * f2[r] * f3[s];
   }
 }
