@@ -612,6 +612,44 @@ def run_gpu(args, rank, world):
     s_per_iter = t_steps / args.steps
     roof = roofline_sparse(kstats, prof_steps, pk)
 
+    # the mixed pipeline on the same storage: FP32 sweep (SIMT sector
+    # products, FP64 propagator factors and energy sums), then FP64 residual
+    # corrections (refine_max_iter = 2, the default)
+    mixed = None
+    if not args.no_mixed:
+        mopts = dict(precision="bf16x3", block_sparse=1, max_iter=100)
+        cm = ftcc.Context(dev)
+        cm.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
+        cm.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **mopts)   # sizing and captures
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rm = cm.solve(C3["beta"], mu, C3["ngrid"], allow_unconverged=True, **mopts)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        cm.prepare(C3["beta"], mu, C3["ngrid"], **mopts)
+        cm.iterate(max(1, args.warmup))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cm.stream)
+        cm.iterate(args.steps)
+        e1.record(cm.stream)
+        torch.cuda.synchronize()
+        cm.profile(True)
+        cm.iterate(3)
+        km = cm.profile_read()
+        cm.profile(False)
+        cm.close()
+        mixed = {"s_per_iteration": e0.elapsed_time(e1) / 1e3 / args.steps, "steps": args.steps,
+                 "time_to_1e-6": {"s_total": tm, "iterations": rm["iterations"],
+                                  "fp64_corrections": rm["refine_iterations"], "converged": bool(rm["converged"]),
+                                  "omega": rm["omega"],
+                                  "abs_dOmega_vs_oracle": abs(rm["omega"] - gold["omega"]) if gold else None},
+                 "kernels": class_table(km, 3),
+                 "how": "FP32 block-sparse sweep (storage and SIMT sector products; propagator factors and energy "
+                        "sums in FP64) to |dOmega_CC| < tol_mixed, then up to 2 FP64 residual corrections; "
+                        "iterations of the FP32 sweep timed with CUDA events"}
+        mixed["fp64_over_mixed_time_to_solution"] = t_sol / tm if tm > 0 else None
+
     # e2e through the public API with host buffers: the gas's Hamiltonian and
     # its orbital charges from pinned host memory (build_integrals GENERIC
     # with charges), the block-sparse FP64 solve to convergence (the state
@@ -677,7 +715,7 @@ def run_gpu(args, rank, world):
                 "flops_note": "2 sum_s rows_s^3 over the charge sectors of the five products of two four-index "
                               "factors, every tau point; the dense schedule's 7.0e14 flops per iteration are in "
                               "extra.dense_mixed",
-                "time_to_1e-6": solve, "adjoint": adjoint,
+                "time_to_1e-6": solve, "adjoint": adjoint, "mixed_block_sparse": mixed,
                 "fp64_block_sparse_vs_dense_mixed_time_to_solution": (dts / t_sol if dts else None),
                 "peaks": pk, "roofline": roof, "kernels": class_table(kstats, prof_steps),
                 "e2e": e2e, "gpu_launches": k_iter * args.steps, "clocks": clk.summary()}
@@ -968,6 +1006,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the lambda sweep of the headline workload")
     ap.add_argument("--quick", action="store_true", help="headline only, no extra workloads")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense mixed-precision sweep")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32 block-sparse sweep")
     ap.add_argument("--c3-iterations", action="store_true",
                     help="prepare the headline workload and run W + K iterations (profiler launch lists)")
     ap.add_argument("--gemm", default=None, help="B,M,N,K: time the tensor-core GEMM alone on that shape")

@@ -269,24 +269,28 @@ cudaError_t launch_prop_response(const T* S, const T* m, const double* epsz, con
 // Four-index tensors are N^3 arrays [p0][p1][p2] with q_p0 + q_p1 = q_p2 + q_p3
 // and p3 implied; imp[a][b][c] (int16, N^3) = the orbital of charge
 // q_a + q_b - q_c or -1.  Two-index tensors are their diagonals [p].
-struct SpBlocks {   // thermal integral blocks <pq||rs> of each hole / particle class, N^3 each
-  const double *oovv, *ovvv, *ooov, *oooo, *vvvv, *ovvo, *oovo, *ovov, *vvoo, *vvvo, *ovoo;
+template <class T>
+struct SpBlocksT {   // thermal integral blocks <pq||rs> of each hole / particle class, N^3 each
+  const T *oovv, *ovvv, *ooov, *oooo, *vvvv, *ovvo, *oovo, *ovov, *vvoo, *vvvo, *ovoo;
 };
-struct SpVecArgs {
-  const double *t1, *t2;
-  const double *fov, *foo, *fvv, *fvo;   // diagonals of the thermal Fock blocks
-  const double *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
+using SpBlocks = SpBlocksT<double>;
+template <class T>
+struct SpVecArgsT {
+  const T *t1, *t2;
+  const T *fov, *foo, *fvv, *fvo;   // diagonals of the thermal Fock blocks
+  const T *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
   const int16_t* imp;
   int n;
-  double *Fme, *Fae, *Fmi, *S1, *Ft, *Ft2;   // [nx][n] each
+  T *Fme, *Fae, *Fmi, *S1, *Ft, *Ft2;   // [nx][n] each
 };
 // Products of the blocks of one pair-charge sector (see sparse.cu).
-struct SecGemmArgs {
-  const double* A;
+template <class T>
+struct SecGemmArgsT {
+  const T* A;
   long long ax;          // slice stride of A
-  const double* B;
+  const T* B;
   long long bx;          // slice stride of B (0: fixed)
-  double* C;
+  T* C;
   long long cx;
   double alpha;
   int n;
@@ -297,13 +301,14 @@ struct SecGemmArgs {
   const int4* sec;       // (entry offset, rows, K offset, K count)
   const int4* work;      // (sector, row tile start, column tile start, 0)
   // optional second product over the same rows and K list: C += alpha (A B^T + A2 B2^T)
-  const double* A2;
-  const double* B2;
+  const T* A2;
+  const T* B2;
   // anti4: rows (i, j), columns (a, b); the value is added to C[i][j][a],
   // C[j][i][a] (-), C[i][j][b] (-), C[j][i][b] (N^3 storage, the fourth index
   // implied), i.e. to all four orientations of an antisymmetric result
   int anti4;
 };
+using SecGemmArgs = SecGemmArgsT<double>;
 // Transposed sector products (see sparse.cu): D[orow(e_o)][k] += alpha
 // sum_{e_s} G[gpos(e_o, e_s)] A[srow(e_s)][k]; dx = 0: D fixed, the kernel
 // sums the nx slices of G and A.
@@ -354,23 +359,28 @@ cudaError_t launch_sp_slot_sums(const double* I, const double* Ib, const int16_t
 // out[x][m] = fov[m] + sum_n s1[x][n] <mn||mn>  (F_me, and dE/ds1 of Eq. E)
 cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voovv, int n, int nx, double* out,
                           cudaStream_t st);
-cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
-                          double* tp, double* tr, double* xp, cudaStream_t st);
-cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st);
+template <class T>
+cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
+                          cudaStream_t st);
+template <class T> cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st);
 // anti != 0: W'_mnij and W'_abef antisymmetrised in (i, j) / (a, b) (the
 // unordered-pair ladders)
-cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
-                            double* wab, double* wr, int anti, cudaStream_t st);
-cudaError_t launch_sp_rinit(const double* t1, const double* t2, const double* Ft, const double* Ft2, const SpBlocks& V,
-                            const int16_t* imp, int n, int nx, double* R, cudaStream_t st);
-cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* imp, int n, int nx, double* S2,
-                         cudaStream_t st);
-cudaError_t launch_sector_gemm(const SecGemmArgs& g, int nwork, int nx, cudaStream_t st);
+template <class T>
+cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* imp, int n, int nx, T* w1, T* wab,
+                            T* wr, int anti, cudaStream_t st);
+template <class T>
+cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
+                            const int16_t* imp, int n, int nx, T* R, cudaStream_t st);
+template <class T>
+cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, int n, int nx, T* S2, cudaStream_t st);
+template <class T> cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
 int sector_tile();
+template <class T>
 cudaError_t launch_sp_thermal_eri(const double* eri, const int16_t* imp, int n, const double* f0, const double* f1,
-                                  const double* f2, const double* f3, double* out, cudaStream_t st);
-cudaError_t launch_sp_swap12(const double* in, int n, double* out, cudaStream_t st);   // out[a][b][c] = in[a][c][b]
-cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, double* out,
+                                  const double* f2, const double* f3, T* out, cudaStream_t st);
+template <class T> cudaError_t launch_sp_swap12(const T* in, int n, T* out, cudaStream_t st);   // out[a][b][c] = in[a][c][b]
+template <class T>
+cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, T* out,
                                    cudaStream_t st);
 cudaError_t launch_sp_compress(const double* d1, const double* d2, const int16_t* imp, int n, int nx, double* s1,
                                double* s2, cudaStream_t st);

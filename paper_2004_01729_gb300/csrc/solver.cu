@@ -881,25 +881,20 @@ struct Solver {
     for (Buf* q : {&bR, &bta, &btt, &bY, &bX, &bWmnij, &bWabef, &bWmbej}) ensure(h_, *q, x * n3 * sizeof(T));
     for (Buf* q : {&bFme, &bFae, &bFmi, &bFt, &bFt2}) ensure(h_, *q, x * n * sizeof(T));
     ensure(h_, bP, n3 * sizeof(T));
-    if constexpr (sizeof(T) == 8)
-      CU(launch_sp_swap12(V("zmnef"), no, static_cast<double*>(Vp.p), st()));
+    CU(launch_sp_swap12<T>(V("zmnef"), no, static_cast<T*>(Vp.p), st()));
   }
 
-  SpBlocks sp_blocks() {
-    if constexpr (sizeof(T) == 8) {
-      return SpBlocks{V("zmnef"), V("zmbef"), V("zmnie"), V("zmnij"), V("zabef"), V("zmbej"),
-                      V("zmnej"), V("zmaie"), V("zabij"), V("zabej"), V("zmbij")};
-    } else {
-      throw Fail{FTCC_ERR_STATE, "block-sparse storage is FP64"};
-    }
+  SpBlocksT<T> sp_blocks() {
+    return SpBlocksT<T>{V("zmnef"), V("zmbef"), V("zmnie"), V("zmnij"), V("zabef"), V("zmbej"),
+                        V("zmnej"), V("zmaie"), V("zabij"), V("zabej"), V("zmbij")};
   }
 
   void sector_product(const SecTab& tab, const T* A, long long ax, const T* Bm, long long bx, T* C, double alpha,
                       int swapB, long long s0, long long s1, long long s2, long long s3, const T* A2 = nullptr,
                       const T* B2 = nullptr, int anti4 = 0) {
-    if constexpr (sizeof(T) == 8) {
+    {
       const long long n3 = static_cast<long long>(no) * no * no;
-      SecGemmArgs g{};
+      SecGemmArgsT<T> g{};
       g.A = A;
       g.ax = ax;
       g.B = Bm;
@@ -923,7 +918,7 @@ struct Solver {
       const double fl = tab.flops * nx * (A2 ? 2 : 1);
       if (counting) gemm_flops += static_cast<long long>(fl);
       timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl,
-                   [&] { CU(launch_sector_gemm(g, tab.nwork, nx, st())); });
+                   [&] { CU(launch_sector_gemm<T>(g, tab.nwork, nx, st())); });
     }
   }
 
@@ -942,18 +937,18 @@ struct Solver {
   // orientations (R enters S2 through P(ij)P(ab)); each product is an eighth
   // of its ordered form.  The transpose recomputes the ordered form.
   void sparse_s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur, bool pairs = true) {
-    if constexpr (sizeof(T) == 8) {
+    {
       nx = nxcur;
       const int n = no;
       const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
       const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
-      double *pta = (double*)ta.p, *ptp = (double*)tt.p, *ptr = (double*)Y.p, *pxp = (double*)X.p,
-             *pw1 = (double*)Wmnij.p, *pwab = (double*)Wabef.p, *pwr = (double*)Wmbej.p, *pR = (double*)R.p;
-      const SpBlocks VB = sp_blocks();
+      T *pta = (T*)ta.p, *ptp = (T*)tt.p, *ptr = (T*)Y.p, *pxp = (T*)X.p, *pw1 = (T*)Wmnij.p, *pwab = (T*)Wabef.p,
+        *pwr = (T*)Wmbej.p, *pR = (T*)R.p;
+      const SpBlocksT<T> VB = sp_blocks();
       const double slice = static_cast<double>(nx) * n3 * sizeof(T);
       timed_launch(kClsOther, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_amp(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, st())); });
-      SpVecArgs v{};
+                   [&] { CU(launch_sp_amp<T>(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, st())); });
+      SpVecArgsT<T> v{};
       v.t1 = t1c;
       v.t2 = t2c;
       v.fov = F("zme");
@@ -967,23 +962,23 @@ struct Solver {
       v.Voovo = VB.oovo;
       v.imp = imp;
       v.n = n;
-      v.Fme = (double*)Fme.p;
-      v.Fae = (double*)Fae.p;
-      v.Fmi = (double*)Fmi.p;
+      v.Fme = (T*)Fme.p;
+      v.Fae = (T*)Fae.p;
+      v.Fmi = (T*)Fmi.p;
       v.S1 = S1c;
-      v.Ft = (double*)Ft.p;
-      v.Ft2 = (double*)Ft2.p;
-      timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors(v, nx, st())); });
+      v.Ft = (T*)Ft.p;
+      v.Ft2 = (T*)Ft2.p;
+      timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors<T>(v, nx, st())); });
       timed_launch(kClsScatter, 3 * slice + 6.0 * n3 * sizeof(T), 0.0,
-                   [&] { CU(launch_sp_wbase(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0, st())); });
+                   [&] { CU(launch_sp_wbase<T>(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0, st())); });
       // W'_mnij += 1/2 tau_ij^ef <mn||ef>        rows (i,j) | (m,n) by q_i + q_j, sum over e
       // (unordered: W^A_ijmn += sum_{e<f} tau_ij^ef <mn||ef> for i < j, m < n)
       if (pairs) sector_product(b->ssum_u, pta, n3, VB.oovv, 0, pw1, 1.0, 0, n2, n, 1, 0);
       else sector_product(b->ssum, pta, n3, VB.oovv, 0, pw1, 0.5, 0, n2, n, 1, 0);
       // W_mbej -= X_jn^fb <mn||ef>                rows (j,b) | (m,e) by q_j - q_b, sum over n
-      sector_product(b->sdiff, pxp, n3, static_cast<const double*>(Vp.p), 0, pwr, -1.0, 0, n2, n, 1, 0);
+      sector_product(b->sdiff, pxp, n3, static_cast<const T*>(Vp.p), 0, pwr, -1.0, 0, n2, n, 1, 0);
       timed_launch(kClsScatter, 5 * slice, 0.0, [&] {
-        CU(launch_sp_rinit(t1c, t2c, (double*)Ft.p, (double*)Ft2.p, VB, imp, n, nx, pR, st()));
+        CU(launch_sp_rinit<T>(t1c, t2c, (T*)Ft.p, (T*)Ft2.p, VB, imp, n, nx, pR, st()));
       });
       if (pairs) {
         // L/4 in the four orientations of R: rows i < j | a < b, sums over m < n and e < f
@@ -997,7 +992,7 @@ struct Solver {
       // ring s_im^ae W_mbej                        rows (i,a) | (j,b) by q_i - q_a, sum over m
       sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
       timed_launch(kClsScatter, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_s2(pR, VB.vvoo, imp, n, nx, S2c, st())); });
+                   [&] { CU(launch_sp_s2<T>(pR, VB.vvoo, imp, n, nx, S2c, st())); });
     }
   }
 
@@ -1611,7 +1606,8 @@ void build_blocks(Batch& B, Solver<T>& s) {
 // The thermal integral and Fock blocks in block-sparse storage: each ERI
 // class as an N^3 array (fourth index implied), each Fock class as its
 // diagonal.  No truncation, so the hole and particle lists are every orbital.
-void build_blocks_sparse(Batch& B, Solver<double>& s) {
+template <class T>
+void build_blocks_sparse(Batch& B, Solver<T>& s) {
   ftcc_ctx* h = B.home;
   const int n = B.N;
   const long long n3 = static_cast<long long>(n) * n * n;
@@ -1621,16 +1617,16 @@ void build_blocks_sparse(Batch& B, Solver<double>& s) {
   const char* eri_pat[] = {"oovv", "ovvv", "ooov", "oooo", "vvvv", "vovv", "ovvo", "oovo", "ovov", "vvoo", "vvvo", "ovoo"};
   for (const char* pat : eri_pat) {
     Buf& buf = s.Vb[pat];
-    ensure(h, buf, n3 * sizeof(double));
-    CU(launch_sp_thermal_eri(static_cast<const double*>(I.ctx->eri.p), imp, n, fac(pat[0]), fac(pat[1]), fac(pat[2]),
-                             fac(pat[3]), static_cast<double*>(buf.p), h->st));
+    ensure(h, buf, n3 * sizeof(T));
+    CU(launch_sp_thermal_eri<T>(static_cast<const double*>(I.ctx->eri.p), imp, n, fac(pat[0]), fac(pat[1]),
+                                fac(pat[2]), fac(pat[3]), static_cast<T*>(buf.p), h->st));
   }
   const char* f_pat[] = {"ov", "vv", "oo", "vo"};
   for (const char* pat : f_pat) {
     Buf& buf = s.Fb[pat];
-    ensure(h, buf, n * sizeof(double));
-    CU(launch_sp_thermal_fock(static_cast<const double*>(I.fbar.p), n, fac(pat[0]), fac(pat[1]),
-                              static_cast<double*>(buf.p), h->st));
+    ensure(h, buf, n * sizeof(T));
+    CU(launch_sp_thermal_fock<T>(static_cast<const double*>(I.fbar.p), n, fac(pat[0]), fac(pat[1]),
+                                 static_cast<T*>(buf.p), h->st));
   }
 }
 
@@ -1647,7 +1643,7 @@ Solver<T>& make_solver(Batch& B, int kind) {
     s.no = B.no;
     s.nv = B.nv;
     s.ng = B.ng;
-    if constexpr (sizeof(T) == 8) {
+    {
       if (B.sparse) {
         s.sp = true;
         s.nxc = B.opt.tau_chunk > 0 ? std::min(B.opt.tau_chunk, B.ng) : B.ng;
@@ -1924,8 +1920,8 @@ void fill_result(Batch& B, int z, const std::vector<double>& st, ftcc_result* ou
 void promote_to_fp64(Batch& B) {
   Solver<double>& d = make_solver<double>(B, GEMM_F64);
   Solver<float>& s = *B.s32;
-  const long long n1 = static_cast<long long>(s.nz) * s.ng * s.no * s.nv;
-  const long long n2 = static_cast<long long>(s.nz) * s.ng * s.no * s.no * s.nv * s.nv;
+  const long long n1 = static_cast<long long>(s.nz) * s.ng * s.n1();
+  const long long n2 = static_cast<long long>(s.nz) * s.ng * s.n2();
   CU(launch_convert<float, double>(static_cast<const float*>(s.t1.p), static_cast<double*>(d.t1.p), n1, B.home->st));
   CU(launch_convert<float, double>(static_cast<const float*>(s.t2.p), static_cast<double*>(d.t2.p), n2, B.home->st));
   B.active = 0;
@@ -2058,7 +2054,6 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
   B->nv = static_cast<int>(B->V.size());
   if (o.block_sparse) {
     if (n != 1) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: one instance per solve"};
-    if (o.precision != FTCC_PREC_FP64) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: precision must be FP64"};
     if (static_cast<int>(home->charge.size()) != N)
       throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: the system has no conserved orbital charges (UEG or k-space Hubbard)"};
     if (B->no != N || B->nv != N) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: truncation must keep every orbital"};
@@ -2134,6 +2129,11 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
   if (B->prec == FTCC_PREC_FP64) {
     make_solver<double>(*B, GEMM_F64);
     B->active = 0;
+  } else if (B->sparse) {
+    // FP32 storage and arithmetic on the SIMT pipes (the sector products are
+    // small dense blocks); no tensor-core phases, so no polishing phase
+    make_solver<float>(*B, GEMM_BF16X3);
+    B->active = 1;
   } else {
     if (!tma_available()) throw Fail{FTCC_ERR_UNSUPPORTED, "tensor-map encoder unavailable in the driver"};
     make_solver<float>(*B, B->prec == FTCC_PREC_TF32 ? GEMM_TF32 : GEMM_BF16X3);
@@ -3229,7 +3229,7 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
     std::vector<std::vector<double>>& rdms = B.resp_rdm;
     if (B.resp_done) {
       // another member of a batch whose response is already known
-    } else if (B.active == 1 && B.opt.mixed_adjoint) {
+    } else if (B.active == 1 && B.opt.mixed_adjoint && !B.sparse) {
       // the lambda sweep and the response on the FP32 solver: FP32
       // multipliers, BF16X3 contractions in the VJP, FP64 propagator
       // factors, weights and sums

@@ -68,13 +68,14 @@ __device__ __forceinline__ long long pos3(int n, int a, int b, int c) {
 //   tr[i][a][m]  = s_im^ae                                      (e implied)
 //   xp[j][b][n]  = X_jn^fb = 1/2 s_jn^fb + s_j^f s_n^b          (f implied)
 // with s1 diagonal (s_i^a = delta_ia s1[i]).
-__global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __restrict__ t2,
-                              const int16_t* __restrict__ imp, int n, double* __restrict__ ta,
-                              double* __restrict__ tp, double* __restrict__ tr, double* __restrict__ xp) {
+template <class T>
+__global__ void sp_amp_kernel(const T* __restrict__ t1, const T* __restrict__ t2,
+                              const int16_t* __restrict__ imp, int n, T* __restrict__ ta,
+                              T* __restrict__ tp, T* __restrict__ tr, T* __restrict__ xp) {
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
-  const double* s1 = t1 + x * n;
-  const double* s2 = t2 + x * n3;
+  const T* s1 = t1 + x * n;
+  const T* s2 = t2 + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     int p0, p1, p2;
@@ -82,10 +83,10 @@ __global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __res
     const long long o = x * n3 + e;
     {   // ta: (i, j, a) = (p0, p1, p2), b implied
       const int b = impl(imp, n, p0, p1, p2);
-      double v = 0.0;
+      T v = T(0.0);
       if (b >= 0) {
         v = s2[e];
-        const double pr = s1[p0] * s1[p1];
+        const T pr = s1[p0] * s1[p1];
         if (p2 == p0) v += pr;
         if (p2 == p1) v -= pr;
       }
@@ -93,10 +94,10 @@ __global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __res
     }
     {   // tp: (a, b, m) = (p0, p1, p2), n = q_a + q_b - q_m
       const int nn = impl(imp, n, p0, p1, p2);
-      double v = 0.0;
+      T v = T(0.0);
       if (nn >= 0) {
         v = s2[pos3(n, p2, nn, p0)];   // s_{m nn}^{a b}
-        const double pr = s1[p2] * s1[nn];
+        const T pr = s1[p2] * s1[nn];
         if (p0 == p2) v += pr;
         if (p0 == nn) v -= pr;
       }
@@ -104,13 +105,13 @@ __global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __res
     }
     {   // tr: (i, a, m) = (p0, p1, p2), e = q_i + q_m - q_a
       const int ee = impl(imp, n, p0, p2, p1);
-      tr[o] = ee >= 0 ? s2[pos3(n, p0, p2, p1)] : 0.0;   // s_{i m}^{a e}
+      tr[o] = ee >= 0 ? s2[pos3(n, p0, p2, p1)] : T(0.0);   // s_{i m}^{a e}
     }
     {   // xp: (j, b, n) = (p0, p1, p2), f = q_j + q_n - q_b
       const int f = impl(imp, n, p0, p2, p1);
-      double v = 0.0;
+      T v = T(0.0);
       if (f >= 0) {
-        v = 0.5 * s2[pos3(n, p0, p2, f)];   // 1/2 s_{j n}^{f b}
+        v = T(0.5) * s2[pos3(n, p0, p2, f)];   // 1/2 s_{j n}^{f b}
         if (f == p0) v += s1[p0] * s1[p2];
       }
       xp[o] = v;
@@ -119,25 +120,27 @@ __global__ void sp_amp_kernel(const double* __restrict__ t1, const double* __res
 }
 
 // ---- F_me = f_me + sum_n s1[n] <mn||mn>   (diagonal, e = m, f = n)
-__global__ void sp_fme_kernel(const double* __restrict__ t1, const double* __restrict__ fov,
-                              const double* __restrict__ Voovv, int n, int nx, double* __restrict__ Fme) {
+template <class T>
+__global__ void sp_fme_kernel(const T* __restrict__ t1, const T* __restrict__ fov,
+                              const T* __restrict__ Voovv, int n, int nx, T* __restrict__ Fme) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n * nx) return;
   const int x = warp / n, m = warp % n;
-  const double* s1 = t1 + static_cast<long long>(x) * n;
-  double acc = 0.0;
+  const T* s1 = t1 + static_cast<long long>(x) * n;
+  T acc = T(0.0);
   for (int q = lane; q < n; q += 32) acc += s1[q] * Voovv[pos3(n, m, q, m)];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) Fme[static_cast<long long>(x) * n + m] = fov[m] + acc;
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0.0);
   if (threadIdx.x == 0)
     for (int k = 0; k < (blockDim.x >> 5); ++k) s += red[k];
   return s;   // valid in thread 0
@@ -151,24 +154,26 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 //   Ft[p] = F_ae[p] - 1/2 s1[p] F_me[p],  Ft2[p] = F_mi[p] + 1/2 s1[p] F_me[p]
 // (the diagonal forms of Eq. ccS1's terms and of the F intermediates; each
 // integral block in its own thermal scaling).
+template <class T>
 struct SpVec {
-  const double *t1, *t2, *Fme;
-  const double *foo, *fvv, *fvo;
-  const double *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
+  const T *t1, *t2, *Fme;
+  const T *foo, *fvv, *fvo;
+  const T *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
   const int16_t* imp;
   int n;
-  double *Fae, *Fmi, *S1, *Ft, *Ft2;
+  T *Fae, *Fmi, *S1, *Ft, *Ft2;
 };
 
-__global__ void sp_vec_kernel(SpVec a) {
-  __shared__ double red[32];
+template <class T>
+__global__ void sp_vec_kernel(SpVec<T> a) {
+  __shared__ T red[32];
   const int n = a.n;
   const long long n3 = static_cast<long long>(n) * n * n;
   const int p = blockIdx.x, x = blockIdx.y;
-  const double* s1 = a.t1 + static_cast<long long>(x) * n;
-  const double* s2 = a.t2 + x * n3;
-  const double* Fme = a.Fme + static_cast<long long>(x) * n;
-  double cae = 0.0, cmi = 0.0, cs1 = 0.0;
+  const T* s1 = a.t1 + static_cast<long long>(x) * n;
+  const T* s2 = a.t2 + x * n3;
+  const T* Fme = a.Fme + static_cast<long long>(x) * n;
+  T cae = T(0.0), cmi = T(0.0), cs1 = T(0.0);
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
     cae += s1[m] * a.Vovvv[pos3(n, m, p, m)];
     cmi += s1[m] * a.Vooov[pos3(n, p, m, p)];
@@ -179,13 +184,13 @@ __global__ void sp_vec_kernel(SpVec a) {
     const int m = static_cast<int>(r / static_cast<uint32_t>(n)), q = static_cast<int>(r - static_cast<uint32_t>(m) * n);
     const long long o1 = pos3(n, m, q, p);   // (m, q, p)
     const long long o2 = pos3(n, p, m, q);   // (p, m, q)
-    const double t_mqp = s2[o1];
-    cae -= 0.5 * t_mqp * a.Voovv[o1];
-    cmi += 0.5 * s2[o2] * a.Voovv[o2];
-    cs1 -= 0.5 * s2[o2] * a.Vovvv[pos3(n, m, p, q)];
-    if (t_mqp != 0.0) {
+    const T t_mqp = s2[o1];
+    cae -= T(0.5) * t_mqp * a.Voovv[o1];
+    cmi += T(0.5) * s2[o2] * a.Voovv[o2];
+    cs1 -= T(0.5) * s2[o2] * a.Vovvv[pos3(n, m, p, q)];
+    if (t_mqp != T(0.0)) {
       const int e = impl(a.imp, n, m, q, p);   // q_e = q_m + q_q - q_p
-      if (e >= 0) cs1 -= 0.5 * t_mqp * a.Voovo[pos3(n, q, m, e)];
+      if (e >= 0) cs1 -= T(0.5) * t_mqp * a.Voovo[pos3(n, q, m, e)];
     }
   }
   cae = block_sum(cae, red);
@@ -193,14 +198,14 @@ __global__ void sp_vec_kernel(SpVec a) {
   cs1 = block_sum(cs1, red);
   if (threadIdx.x == 0) {
     const long long o = static_cast<long long>(x) * n + p;
-    const double s = s1[p], fm = Fme[p];
-    const double fae = a.fvv[p] - 0.5 * s * fm + cae;
-    const double fmi = a.foo[p] + 0.5 * s * fm + cmi;
+    const T s = s1[p], fm = Fme[p];
+    const T fae = a.fvv[p] - T(0.5) * s * fm + cae;
+    const T fmi = a.foo[p] + T(0.5) * s * fm + cmi;
     a.Fae[o] = fae;
     a.Fmi[o] = fmi;
     a.S1[o] = a.fvo[p] + s * (fae - fmi) + cs1;
-    a.Ft[o] = fae - 0.5 * s * fm;
-    a.Ft2[o] = fmi + 0.5 * s * fm;
+    a.Ft[o] = fae - T(0.5) * s * fm;
+    a.Ft2[o] = fmi + T(0.5) * s * fm;
   }
 }
 
@@ -215,18 +220,20 @@ namespace {
 //               = <mb||ej> + s1[j] <mb||ej>_ovvv - s1[b] <mb||ej>_oovo          (e implied)
 // (s1 diagonal turns every s1 contraction of these intermediates into a
 // scaling; the integral blocks differ only by their thermal factors).
+template <class T>
 struct SpW {
-  const double *t1, *Voooo, *Vooov, *Vvvvv, *Vovvv, *Vovvo, *Voovo;
+  const T *t1, *Voooo, *Vooov, *Vvvvv, *Vovvv, *Vovvo, *Voovo;
   const int16_t* imp;
   int n, anti;
-  double *w1, *wab, *wr;
+  T *w1, *wab, *wr;
 };
 
-__global__ void sp_wbase_kernel(SpW a) {
+template <class T>
+__global__ void sp_wbase_kernel(SpW<T> a) {
   const int n = a.n;
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
-  const double* s1 = a.t1 + x * n;
+  const T* s1 = a.t1 + x * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     int p0, p1, p2;
@@ -234,22 +241,22 @@ __global__ void sp_wbase_kernel(SpW a) {
     const long long o = x * n3 + e;
     {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
       const int q = impl(a.imp, n, p0, p1, p2);
-      double v = 0.0;
+      T v = T(0.0);
       if (q >= 0) {
         v = a.Voooo[pos3(n, p2, q, p0)];
         // antisymmetrised in (i, j): (W'_ijmn - W'_jimn) / 2 (<mn||ij> is antisymmetric already)
         if (a.anti) v += -s1[p0] * a.Vooov[pos3(n, p2, q, p1)] + s1[p1] * a.Vooov[pos3(n, p2, q, p0)];
-        else v -= 2.0 * s1[p0] * a.Vooov[pos3(n, p2, q, p1)];
+        else v -= T(2.0) * s1[p0] * a.Vooov[pos3(n, p2, q, p1)];
       }
       a.w1[o] = v;
     }
     // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide; antisymmetrised
     // in (a, b): <ab||ef> - s1[a] <ab||ef>_ovvv + s1[b] <ba||ef>_ovvv
     a.wab[o] = a.anti ? a.Vvvvv[e] - s1[p0] * a.Vovvv[e] + s1[p1] * a.Vovvv[pos3(n, p1, p0, p2)]
-                      : a.Vvvvv[e] - 2.0 * s1[p0] * a.Vovvv[e];
+                      : a.Vvvvv[e] - T(2.0) * s1[p0] * a.Vovvv[e];
     {   // (j, b, m) = (p0, p1, p2), e = q_b + q_m - q_j
       const int ee = impl(a.imp, n, p1, p2, p0);
-      double v = 0.0;
+      T v = T(0.0);
       if (ee >= 0) {
         const long long c = pos3(n, p2, p1, ee);   // (m, b, e), j implied
         v = a.Vovvo[c] + s1[p0] * a.Vovvv[c] - s1[p1] * a.Voovo[c];
@@ -264,48 +271,51 @@ __global__ void sp_wbase_kernel(SpW a) {
 //   R = 1/2 s_ij^ab Ft[b] + 1/2 Ft2[i] s_ji^ab + 1/2 s1[i] <ab||ij>_vvvo
 //     - 1/2 s1[a] <ab||ij>_ovoo + s1[i] s1[b] <ba||ij>_ovvo
 // (the last is the s_i^e <mb||ej> s_m^b term of Eq. ccS2).
+template <class T>
 struct SpR {
-  const double *t1, *t2, *Ft, *Ft2, *Vvvvo, *Vovoo, *Vovvo;
+  const T *t1, *t2, *Ft, *Ft2, *Vvvvo, *Vovoo, *Vovvo;
   const int16_t* imp;
   int n;
-  double* R;
+  T* R;
 };
 
-__global__ void sp_rinit_kernel(SpR a) {
+template <class T>
+__global__ void sp_rinit_kernel(SpR<T> a) {
   const int n = a.n;
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
-  const double* s1 = a.t1 + x * n;
-  const double* s2 = a.t2 + x * n3;
-  const double* Ft = a.Ft + x * n;
-  const double* Ft2 = a.Ft2 + x * n;
+  const T* s1 = a.t1 + x * n;
+  const T* s2 = a.t2 + x * n3;
+  const T* Ft = a.Ft + x * n;
+  const T* Ft2 = a.Ft2 + x * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
-    double v = 0.0;
+    T v = T(0.0);
     if (b >= 0) {
       const long long c = pos3(n, aa, b, i);   // (a, b, i), j implied
-      v = 0.5 * s2[e] * Ft[b] + 0.5 * Ft2[i] * s2[pos3(n, j, i, aa)] + 0.5 * s1[i] * a.Vvvvo[c] -
-          0.5 * s1[aa] * a.Vovoo[c] + s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)];
+      v = T(0.5) * s2[e] * Ft[b] + T(0.5) * Ft2[i] * s2[pos3(n, j, i, aa)] + T(0.5) * s1[i] * a.Vvvvo[c] -
+          T(0.5) * s1[aa] * a.Vovoo[c] + s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)];
     }
     a.R[x * n3 + e] = v;
   }
 }
 
 // ---- S2 = P(ij)P(ab) R + <ab||ij>_vvoo
-__global__ void sp_s2_kernel(const double* __restrict__ R, const double* __restrict__ Vvvoo,
-                             const int16_t* __restrict__ imp, int n, double* __restrict__ S2) {
+template <class T>
+__global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Vvvoo,
+                             const int16_t* __restrict__ imp, int n, T* __restrict__ S2) {
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
-  const double* r = R + x * n3;
+  const T* r = R + x * n3;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(imp, n, i, j, aa);
-    double v = 0.0;
+    T v = T(0.0);
     if (b >= 0)
       v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
     S2[x * n3 + e] = v;
@@ -329,20 +339,21 @@ constexpr int kSecKc = 32;                     // K chunk staged in shared memor
 constexpr int kSecThreads = 256;
 constexpr int kSecO = (kSecT * kSecT + kSecThreads - 1) / kSecThreads;   // outputs per thread
 
-__global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g) {
-  __shared__ double As[kSecKc][kSecT + 1], Bs[kSecKc][kSecT + 1];
+template <class T>
+__global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgsT<T> g) {
+  __shared__ T As[kSecKc][kSecT + 1], Bs[kSecKc][kSecT + 1];
   const int4 w = g.work[blockIdx.x];
   const int4 sec = g.sec[w.x];   // entry offset, rows, K offset, K count
   const long long x = blockIdx.y;
   const int n = g.n;
   const int nr = min(kSecT, sec.y - w.y), nc = min(kSecT, sec.y - w.z);
   const int nout = nr * nc;
-  double acc[kSecO];
+  T acc[kSecO];
 #pragma unroll
-  for (int j = 0; j < kSecO; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kSecO; ++j) acc[j] = T(0.0);
   for (int prod = 0; prod < (g.A2 ? 2 : 1); ++prod) {
-  const double* A = (prod ? g.A2 : g.A) + x * g.ax;
-  const double* B = (prod ? g.B2 : g.B) + x * g.bx;
+  const T* A = (prod ? g.A2 : g.A) + x * g.ax;
+  const T* B = (prod ? g.B2 : g.B) + x * g.bx;
   for (int k0 = 0; k0 < sec.w; k0 += kSecKc) {
     const int kc = min(kSecKc, sec.w - k0);
     // stage A rows [nr][kc] and B rows [nc][kc] (consecutive threads walk a row's K list)
@@ -363,8 +374,8 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g)
       const int o = threadIdx.x + j * kSecThreads;
       if (o < nout) {
         const int r = o / nc, c = o - r * nc;
-        double a = acc[j];
-        for (int k = 0; k < kc; ++k) a = fma(As[k][r], Bs[k][c], a);
+        T a = acc[j];
+        for (int k = 0; k < kc; ++k) a = As[k][r] * Bs[k][c] + a;
         acc[j] = a;
       }
     }
@@ -377,10 +388,10 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g)
     if (o < nout) {
       const int r = o / nc, c = o - r * nc;
       const int2 pr = g.ent[sec.x + w.y + r], pc = g.ent[sec.x + w.z + c];
-      const double v = g.alpha * acc[j];
+      const T v = g.alpha * acc[j];
       if (g.anti4) {
         // (i, j) = pr, (a, b) = pc: the four orientations of the antisymmetric result
-        double* C = g.C + x * g.cx;
+        T* C = g.C + x * g.cx;
         const long long ni = pr.x, nj = pr.y;
         C[(ni * n + nj) * n + pc.x] += v;
         C[(nj * n + ni) * n + pc.x] -= v;
@@ -398,21 +409,23 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgs g)
 // ---- storage conversions
 // Thermal integral block of class (c0 c1 c2 c3) in N^3 storage:
 // out[p][q][r] = <pq||rs> f0[p] f1[q] f2[r] f3[s], s implied (0 where none).
+template <class T>
 __global__ void sp_thermal_eri_kernel(const double* __restrict__ eri, const int16_t* __restrict__ imp, int n,
                                       const double* f0, const double* f1, const double* f2, const double* f3,
-                                      double* __restrict__ out) {
+                                      T* __restrict__ out) {
   const long long n3 = static_cast<long long>(n) * n * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     int p, q, r;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p, q, r);
     const int s = imp[e];
-    out[e] = s >= 0 ? eri[e * n + s] * f0[p] * f1[q] * f2[r] * f3[s] : 0.0;
+    out[e] = static_cast<T>(s >= 0 ? eri[e * n + s] * f0[p] * f1[q] * f2[r] * f3[s] : 0.0);
   }
 }
 
 // out[p0][p1][p2] = in[p0][p2][p1] (a hole of one is a hole of the other)
-__global__ void sp_swap12_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
+template <class T>
+__global__ void sp_swap12_kernel(const T* __restrict__ in, int n, T* __restrict__ out) {
   const long long n3 = static_cast<long long>(n) * n * n;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -423,10 +436,11 @@ __global__ void sp_swap12_kernel(const double* __restrict__ in, int n, double* _
 }
 
 // diagonal of a thermal Fock block: out[p] = fbar[p][p] f0[p] f1[p]
+template <class T>
 __global__ void sp_thermal_fock_kernel(const double* __restrict__ fbar, int n, const double* f0, const double* f1,
-                                       double* __restrict__ out) {
+                                       T* __restrict__ out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) out[p] = fbar[static_cast<long long>(p) * n + p] * f0[p] * f1[p];
+  if (p < n) out[p] = static_cast<T>(fbar[static_cast<long long>(p) * n + p] * f0[p] * f1[p]);
 }
 
 // dense [x][i][j][a][b] / [x][i][a] <-> N^3 [x][i][j][a] / vector [x][i]
@@ -929,71 +943,96 @@ __global__ void sp_eri_adjoint_kernel(const double* __restrict__ bar, const int1
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_sp_amp(const double* t1, const double* t2, const int16_t* imp, int n, int nx, double* ta,
-                          double* tp, double* tr, double* xp, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
+                          cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_amp_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp);
+  sp_amp_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_vectors(const SpVecArgs& v, int nx, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st) {
   const int warps = v.n * nx;
-  sp_fme_kernel<<<(warps * 32 + 127) / 128, 128, 0, st>>>(v.t1, v.fov, v.Voovv, v.n, nx, v.Fme);
-  SpVec a{v.t1, v.t2, v.Fme, v.foo, v.fvv, v.fvo, v.Voovv, v.Vovvv, v.Vooov, v.Vovov, v.Voovo, v.imp, v.n,
-          v.Fae, v.Fmi, v.S1, v.Ft, v.Ft2};
-  sp_vec_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
+  sp_fme_kernel<T><<<(warps * 32 + 127) / 128, 128, 0, st>>>(v.t1, v.fov, v.Voovv, v.n, nx, v.Fme);
+  SpVec<T> a{v.t1, v.t2, v.Fme, v.foo, v.fvv, v.fvo, v.Voovv, v.Vovvv, v.Vooov, v.Vovov, v.Voovo, v.imp, v.n,
+             v.Fae, v.Fmi, v.S1, v.Ft, v.Ft2};
+  sp_vec_kernel<T><<<dim3(v.n, nx), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_wbase(const double* t1, const SpBlocks& V, const int16_t* imp, int n, int nx, double* w1,
-                            double* wab, double* wr, int anti, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* imp, int n, int nx, T* w1, T* wab,
+                            T* wr, int anti, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  SpW a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, anti, w1, wab, wr};
-  sp_wbase_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  SpW<T> a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, anti, w1, wab, wr};
+  sp_wbase_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_rinit(const double* t1, const double* t2, const double* Ft, const double* Ft2, const SpBlocks& V,
-                            const int16_t* imp, int n, int nx, double* R, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
+                            const int16_t* imp, int n, int nx, T* R, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  SpR a{t1, t2, Ft, Ft2, V.vvvo, V.ovoo, V.ovvo, imp, n, R};
-  sp_rinit_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  SpR<T> a{t1, t2, Ft, Ft2, V.vvvo, V.ovoo, V.ovvo, imp, n, R};
+  sp_rinit_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_s2(const double* R, const double* Vvvoo, const int16_t* imp, int n, int nx, double* S2,
-                         cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, int n, int nx, T* S2, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_s2_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, n, S2);
+  sp_s2_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, n, S2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sector_gemm(const SecGemmArgs& g, int nwork, int nx, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st) {
   if (nwork <= 0 || nx <= 0) return cudaSuccess;
   if (nx > 65535) return cudaErrorInvalidValue;
-  sector_gemm_kernel<<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
+  sector_gemm_kernel<T><<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 int sector_tile() { return kSecT; }
 
+template <class T>
 cudaError_t launch_sp_thermal_eri(const double* eri, const int16_t* imp, int n, const double* f0, const double* f1,
-                                  const double* f2, const double* f3, double* out, cudaStream_t st) {
+                                  const double* f2, const double* f3, T* out, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_thermal_eri_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(eri, imp, n, f0, f1, f2, f3, out);
+  sp_thermal_eri_kernel<T><<<sp_grid(n3), kSpThreads, 0, st>>>(eri, imp, n, f0, f1, f2, f3, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_swap12(const double* in, int n, double* out, cudaStream_t st) {
+template <class T>
+cudaError_t launch_sp_swap12(const T* in, int n, T* out, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_swap12_kernel<<<sp_grid(n3), kSpThreads, 0, st>>>(in, n, out);
+  sp_swap12_kernel<T><<<sp_grid(n3), kSpThreads, 0, st>>>(in, n, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, double* out,
+template <class T>
+cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, const double* f1, T* out,
                                    cudaStream_t st) {
-  sp_thermal_fock_kernel<<<(n + 127) / 128, 128, 0, st>>>(fbar, n, f0, f1, out);
+  sp_thermal_fock_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(fbar, n, f0, f1, out);
   return cudaGetLastError();
 }
+
+#define FTCC_SPARSE_INSTANTIATE(T)                                                                                  \
+  template cudaError_t launch_sp_amp<T>(const T*, const T*, const int16_t*, int, int, T*, T*, T*, T*, cudaStream_t); \
+  template cudaError_t launch_sp_vectors<T>(const SpVecArgsT<T>&, int, cudaStream_t);                              \
+  template cudaError_t launch_sp_wbase<T>(const T*, const SpBlocksT<T>&, const int16_t*, int, int, T*, T*, T*, int, \
+                                          cudaStream_t);                                                          \
+  template cudaError_t launch_sp_rinit<T>(const T*, const T*, const T*, const T*, const SpBlocksT<T>&,             \
+                                          const int16_t*, int, int, T*, cudaStream_t);                             \
+  template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, int, int, T*, cudaStream_t);            \
+  template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
+  template cudaError_t launch_sp_thermal_eri<T>(const double*, const int16_t*, int, const double*, const double*,  \
+                                                const double*, const double*, T*, cudaStream_t);                  \
+  template cudaError_t launch_sp_swap12<T>(const T*, int, T*, cudaStream_t);                                       \
+  template cudaError_t launch_sp_thermal_fock<T>(const double*, int, const double*, const double*, T*, cudaStream_t);
+FTCC_SPARSE_INSTANTIATE(float)
+FTCC_SPARSE_INSTANTIATE(double)
+#undef FTCC_SPARSE_INSTANTIATE
 
 cudaError_t launch_sp_compress(const double* d1, const double* d2, const int16_t* imp, int n, int nx, double* s1,
                                double* s2, cudaStream_t st) {

@@ -118,11 +118,32 @@ def test_sparse_converged_gases_match_goldens(ctx, name, tau_chunk):
     assert abs(r["omega"] - gold["omega"]) < 1e-9, (r["omega"], gold["omega"])
 
 
+@pytest.mark.parametrize("name", ["oracle_ueg57.json", "oracle_ueg81.json"])
+def test_sparse_mixed_precision_gases(ctx, name):
+    """The mixed pipeline on the block-sparse storage: FP32 sweep (storage
+    and SIMT sector products, FP64 propagator factors and energy sums)
+    alone, then followed by FP64 residual corrections, against the
+    block-sparse oracle's converged Omega; the FP32 phase within 1e-6 Ha,
+    the corrected solve within 1e-8 Ha."""
+    gold = json.load(open(os.path.join(GOLD, name)))
+    c = gold["config"]
+    ctx.build_ueg(c["n_elec"], c["rs"], c["n_pw"])
+    kw = dict(precision="bf16x3", block_sparse=1, trunc_thr=c["thr"], max_iter=80)
+    r = ctx.solve(c["beta"], gold["mu"], c["ngrid"], refine_max_iter=0, **kw)
+    assert r["converged"] and r["refine_iterations"] == 0
+    assert abs(r["omega"] - gold["omega"]) < 1e-6, (r["omega"], gold["omega"])
+    r = ctx.solve(c["beta"], gold["mu"], c["ngrid"], refine_max_iter=3, tol_omega=1e-10, tol_amp=1e-8, **kw)
+    assert r["converged"] and 1 <= r["refine_iterations"] <= 3
+    assert abs(r["omega"] - gold["omega"]) < 1e-8, (r["omega"], gold["omega"])
+
+
 def test_sparse_argument_checks(ctx):
     from paper_2004_01729_gb300 import ftcc
     ctx.build_ueg(6, 1.0, 7)
-    with pytest.raises(ftcc.FTCCError) as e:          # FP64 only
-        ctx.prepare(1.0, 0.5, 4, precision="tf32", block_sparse=1)
+    ctx.prepare(1.0, 0.5, 4, precision="tf32", block_sparse=1)
+    with pytest.raises(ftcc.FTCCError) as e:          # the dense-layout S evaluation is FP64 only
+        ctx.eval_s(torch.zeros((1, 14, 14), dtype=torch.float64), torch.zeros((1, 14, 14, 14, 14), dtype=torch.float64),
+                   precision="tf32")
     assert e.value.status == ftcc.ERR_INVALID_ARG
     with pytest.raises(ftcc.FTCCError) as e:          # Simpson integral form only
         ctx.solve(1.0, 0.5, 5, quad=ftcc.QUAD_RK4, precision="fp64", block_sparse=1)
