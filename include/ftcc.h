@@ -186,14 +186,19 @@ typedef struct {
  *                       one-index-pair factors become their diagonals, four-index
  *                       factors N^3 arrays with the fourth index implied, and
  *                       the contractions run over charge sectors only.  The same
- *                       equations and fixed point in FP64, with the work and
- *                       memory of one iteration cut by about the number of
- *                       k-points.  Needs precision FP64, a single instance of
- *                       such a system (FTCC_ERR_INVALID_ARG otherwise), no
- *                       truncation (trunc_thr removes nothing) and the Simpson
- *                       integral form; stream_tau is ignored.
- *                       ft_ccsd_adjoint (the lambda sweep through the transpose
- *                       of the block-sparse S kernel), ftcc_rdm2 and
+ *                       equations and fixed point, with the work and memory of
+ *                       one iteration cut by about the number of k-points.
+ *                       precision FP64: FP64 throughout; TF32 or BF16X3: an FP32
+ *                       sweep (FP32 storage and SIMT sector products, FP64
+ *                       propagator factors and energy sums) handing over at
+ *                       tol_mixed to at most refine_max_iter FP64 residual
+ *                       corrections (no polishing phase).  Needs a single
+ *                       instance of such a system (FTCC_ERR_INVALID_ARG
+ *                       otherwise), no truncation (trunc_thr removes nothing)
+ *                       and the Simpson integral form; stream_tau is ignored.
+ *                       ft_ccsd_adjoint (the FP64 lambda sweep through the
+ *                       transpose of the block-sparse S kernel; mixed_adjoint is
+ *                       ignored), ftcc_rdm2 and
  *                       ftcc_mu_for_n work on it; ftcc_get_amplitudes,
  *                       ftcc_eval_s and ftcc_eval_s_vjp convert between the
  *                       dense layouts and the compressed one (inputs projected
