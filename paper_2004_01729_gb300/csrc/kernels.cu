@@ -1588,18 +1588,20 @@ __global__ void pair_pack_kernel(const T* __restrict__ src, T* __restrict__ dst,
                                  const int2* __restrict__ pairs1, long long np1, const int2* __restrict__ pairs2,
                                  long long np2, long long s0, long long s1, long long s2, long long s3, int anti,
                                  T coef) {
-  const long long total = nb * np1 * np2;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long q = e % np2;
-    const long long r = e / np2;
-    const long long p = r % np1;
-    const long long b = r / np1;
-    const int2 a = pairs1[p], c = pairs2[q];
-    const T* x = src + b * sb + c.x * s2 + c.y * s3;
-    T v = x[a.x * s0 + a.y * s1];
-    if (anti) v = T(0.5) * (v - x[a.y * s0 + a.x * s1]);
-    dst[e] = coef * v;
+  // one batch entry per blockIdx.y; 32-bit indices within it (a 64-bit
+  // division per element costs a long instruction sequence)
+  const uint32_t per = static_cast<uint32_t>(np1 * np2), n2 = static_cast<uint32_t>(np2);
+  for (long long b = blockIdx.y; b < nb; b += gridDim.y) {
+    const T* xb = src + b * sb;
+    T* db = dst + b * static_cast<long long>(per);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x) {
+      const uint32_t p = e / n2, q = e - p * n2;
+      const int2 a = pairs1[p], c = pairs2[q];
+      const T* x = xb + c.x * s2 + c.y * s3;
+      T v = x[a.x * s0 + a.y * s1];
+      if (anti) v = T(0.5) * (v - x[a.y * s0 + a.x * s1]);
+      db[e] = coef * v;
+    }
   }
 }
 
@@ -1610,24 +1612,26 @@ template <class T>
 __global__ void pair_unpack_add_kernel(T* __restrict__ R, const T* __restrict__ L, long long nb, int no, int nv,
                                        T coef) {
   const long long npo = static_cast<long long>(no) * (no - 1) / 2, npv = static_cast<long long>(nv) * (nv - 1) / 2;
-  const long long per = static_cast<long long>(no) * no * nv * nv;
-  const long long total = nb * per;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    long long r = e;
-    const int c = static_cast<int>(r % nv);
-    r /= nv;
-    const int a = static_cast<int>(r % nv);
-    r /= nv;
-    const int j = static_cast<int>(r % no);
-    r /= no;
-    const int i = static_cast<int>(r % no);
-    const long long b = r / no;
-    if (i == j || a == c) continue;
-    const long long P = i < j ? pair_index(i, j, no) : pair_index(j, i, no);
-    const long long Q = a < c ? pair_index(a, c, nv) : pair_index(c, a, nv);
-    const T v = L[(b * npo + P) * npv + Q];
-    R[e] += ((i < j) == (a < c)) ? coef * v : -coef * v;
+  const uint32_t per = static_cast<uint32_t>(no) * no * nv * nv, uo = no, uv = nv;
+  for (long long b = blockIdx.y; b < nb; b += gridDim.y) {
+    T* Rb = R + b * static_cast<long long>(per);
+    const T* Lb = L + b * npo * npv;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x) {
+      uint32_t r = e, q = r / uv;
+      const int c = static_cast<int>(r - q * uv);
+      r = q;
+      q = r / uv;
+      const int a = static_cast<int>(r - q * uv);
+      r = q;
+      q = r / uo;
+      const int j = static_cast<int>(r - q * uo);
+      const int i = static_cast<int>(q);
+      if (i == j || a == c) continue;
+      const long long P = i < j ? pair_index(i, j, no) : pair_index(j, i, no);
+      const long long Q = a < c ? pair_index(a, c, nv) : pair_index(c, a, nv);
+      const T v = Lb[P * npv + Q];
+      Rb[e] += ((i < j) == (a < c)) ? coef * v : -coef * v;
+    }
   }
 }
 
@@ -1635,20 +1639,24 @@ template <class T>
 cudaError_t launch_pair_pack(const T* src, T* dst, long long nb, long long sb, const int2* pairs1, long long np1,
                              const int2* pairs2, long long np2, long long s0, long long s1, long long s2, long long s3,
                              int anti, double coef, cudaStream_t st) {
-  const long long total = nb * np1 * np2;
-  if (total <= 0) return cudaSuccess;
-  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 16));
-  pair_pack_kernel<T><<<blocks, 256, 0, st>>>(src, dst, nb, sb, pairs1, np1, pairs2, np2, s0, s1, s2, s3, anti,
+  const long long per = np1 * np2;
+  if (nb <= 0 || per <= 0) return cudaSuccess;
+  if (per >= (1LL << 31)) return cudaErrorInvalidValue;
+  const int by = static_cast<int>(std::min<long long>(nb, 65535));
+  const int blocks = static_cast<int>(std::max<long long>(1, std::min<long long>((per + 255) / 256, 152LL * 16 / by + 1)));
+  pair_pack_kernel<T><<<dim3(blocks, by), 256, 0, st>>>(src, dst, nb, sb, pairs1, np1, pairs2, np2, s0, s1, s2, s3, anti,
                                               static_cast<T>(coef));
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_pair_unpack_add(T* R, const T* L, long long nb, int no, int nv, double coef, cudaStream_t st) {
-  const long long total = nb * static_cast<long long>(no) * no * nv * nv;
-  if (total <= 0 || no < 2 || nv < 2) return cudaSuccess;
-  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 16));
-  pair_unpack_add_kernel<T><<<blocks, 256, 0, st>>>(R, L, nb, no, nv, static_cast<T>(coef));
+  const long long per = static_cast<long long>(no) * no * nv * nv;
+  if (nb <= 0 || per <= 0 || no < 2 || nv < 2) return cudaSuccess;
+  if (per >= (1LL << 31)) return cudaErrorInvalidValue;
+  const int by = static_cast<int>(std::min<long long>(nb, 65535));
+  const int blocks = static_cast<int>(std::max<long long>(1, std::min<long long>((per + 255) / 256, 152LL * 16 / by + 1)));
+  pair_unpack_add_kernel<T><<<dim3(blocks, by), 256, 0, st>>>(R, L, nb, no, nv, static_cast<T>(coef));
   return cudaGetLastError();
 }
 template cudaError_t launch_pair_pack<float>(const float*, float*, long long, long long, const int2*, long long,
