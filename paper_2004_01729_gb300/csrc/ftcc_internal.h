@@ -280,6 +280,9 @@ struct SpVecArgsT {
   const T *fov, *foo, *fvv, *fvo;   // diagonals of the thermal Fock blocks
   const T *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
   const int16_t* imp;
+  // per orbital p, the (m, q) = m n + q with a valid position (m, q, p) (l1)
+  // and (p, m, q) (l2); offsets [n + 1]
+  const int *l1, *off1, *l2, *off2;
   int n;
   T *Fme, *Fae, *Fmi, *S1, *Ft, *Ft2;   // [nx][n] each
 };
@@ -359,20 +362,27 @@ cudaError_t launch_sp_slot_sums(const double* I, const double* Ib, const int16_t
 // out[x][m] = fov[m] + sum_n s1[x][n] <mn||mn>  (F_me, and dE/ds1 of Eq. E)
 cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voovv, int n, int nx, double* out,
                           cudaStream_t st);
+// skip_tau: leave ta, tp to launch_sp_canon (the unordered-pair products read only their canonical elements)
 template <class T>
 cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
-                          cudaStream_t st);
+                          int skip_tau, cudaStream_t st);
+// ta, tp and the antisymmetrised W'_mnij, W'_abef at the canonical positions (p0 < p1, p2 < p3) only
+template <class T>
+cudaError_t launch_sp_canon(const T* t1, const T* t2, const SpBlocksT<T>& V, const int16_t* imp, const int* canon,
+                            int ncanon, int n, int nx, T* ta, T* tp, T* w1, T* wab, cudaStream_t st);
 template <class T> cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st);
-// anti != 0: W'_mnij and W'_abef antisymmetrised in (i, j) / (a, b) (the
-// unordered-pair ladders)
+// anti != 0: only W_mbej (the antisymmetrised W'_mnij, W'_abef of the
+// unordered-pair ladders come from launch_sp_canon)
 template <class T>
 cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* imp, int n, int nx, T* w1, T* wab,
                             T* wr, int anti, cudaStream_t st);
 template <class T>
 cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
                             const int16_t* imp, int n, int nx, T* R, cudaStream_t st);
+// S2 from its canonical elements, written to their four orientations
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, int n, int nx, T* S2, cudaStream_t st);
+cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,
+                         T* S2, cudaStream_t st);
 template <class T> cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
 int sector_tile();
 template <class T>

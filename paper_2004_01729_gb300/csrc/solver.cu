@@ -195,6 +195,7 @@ struct Batch {
   Buf imp;
   Buf canon;                     // canonical doubles positions (i < j, a < b) of the N^3 storage
   long long ncanon = 0;
+  Buf vl1, voff1, vl2, voff2;    // per orbital p: valid (m, q) of (m, q, p) and of (p, m, q)
   SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
   ~Batch();
 };
@@ -947,7 +948,7 @@ struct Solver {
       const SpBlocksT<T> VB = sp_blocks();
       const double slice = static_cast<double>(nx) * n3 * sizeof(T);
       timed_launch(kClsOther, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_amp<T>(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, st())); });
+                   [&] { CU(launch_sp_amp<T>(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, pairs ? 1 : 0, st())); });
       SpVecArgsT<T> v{};
       v.t1 = t1c;
       v.t2 = t2c;
@@ -961,6 +962,10 @@ struct Solver {
       v.Vovov = VB.ovov;
       v.Voovo = VB.oovo;
       v.imp = imp;
+      v.l1 = static_cast<const int*>(b->vl1.p);
+      v.off1 = static_cast<const int*>(b->voff1.p);
+      v.l2 = static_cast<const int*>(b->vl2.p);
+      v.off2 = static_cast<const int*>(b->voff2.p);
       v.n = n;
       v.Fme = (T*)Fme.p;
       v.Fae = (T*)Fae.p;
@@ -971,6 +976,12 @@ struct Solver {
       timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors<T>(v, nx, st())); });
       timed_launch(kClsScatter, 3 * slice + 6.0 * n3 * sizeof(T), 0.0,
                    [&] { CU(launch_sp_wbase<T>(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0, st())); });
+      const int* canon = static_cast<const int*>(b->canon.p);
+      const int ncanon = static_cast<int>(b->ncanon);
+      if (pairs)
+        timed_launch(kClsScatter, 4.0 * nx * ncanon * 4 * sizeof(T), 0.0, [&] {
+          CU(launch_sp_canon<T>(t1c, t2c, VB, imp, canon, ncanon, n, nx, pta, ptp, pw1, pwab, st()));
+        });
       // W'_mnij += 1/2 tau_ij^ef <mn||ef>        rows (i,j) | (m,n) by q_i + q_j, sum over e
       // (unordered: W^A_ijmn += sum_{e<f} tau_ij^ef <mn||ef> for i < j, m < n)
       if (pairs) sector_product(b->ssum_u, pta, n3, VB.oovv, 0, pw1, 1.0, 0, n2, n, 1, 0);
@@ -992,7 +1003,7 @@ struct Solver {
       // ring s_im^ae W_mbej                        rows (i,a) | (j,b) by q_i - q_a, sum over m
       sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
       timed_launch(kClsScatter, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_s2<T>(pR, VB.vvoo, imp, n, nx, S2c, st())); });
+                   [&] { CU(launch_sp_s2<T>(pR, VB.vvoo, imp, canon, ncanon, n, nx, S2c, st())); });
     }
   }
 
@@ -1415,7 +1426,7 @@ Batch::~Batch() {
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
                &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
-               &ssum_u.sec, &ssum_u.work, &canon};
+               &ssum_u.sec, &ssum_u.work, &canon, &vl1, &voff1, &vl2, &voff2};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1459,6 +1470,27 @@ void build_implied(Batch& B, const ftcc_ctx* c) {
         const long long e = (static_cast<long long>(i) * n + j) * n + a;
         if (t[e] > a) cp.push_back(static_cast<int>(e));
       }
+  // per orbital p, the valid positions (m, q, p) and (p, m, q) as m n + q
+  std::vector<int> l1, o1(n + 1, 0), l2, o2(n + 1, 0);
+  for (int p = 0; p < n; ++p) {
+    o1[p] = static_cast<int>(l1.size());
+    o2[p] = static_cast<int>(l2.size());
+    for (int m = 0; m < n; ++m)
+      for (int q = 0; q < n; ++q) {
+        if (t[(static_cast<long long>(m) * n + q) * n + p] >= 0) l1.push_back(m * n + q);
+        if (t[(static_cast<long long>(p) * n + m) * n + q] >= 0) l2.push_back(m * n + q);
+      }
+  }
+  o1[n] = static_cast<int>(l1.size());
+  o2[n] = static_cast<int>(l2.size());
+  auto upload = [&](Buf& b, const std::vector<int>& v) {
+    ensure(B.home, b, std::max<size_t>(1, v.size()) * sizeof(int));
+    if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, B.home->st));
+  };
+  upload(B.vl1, l1);
+  upload(B.voff1, o1);
+  upload(B.vl2, l2);
+  upload(B.voff2, o2);
   B.ncanon = static_cast<long long>(cp.size());
   ensure(B.home, B.canon, std::max<size_t>(1, cp.size()) * sizeof(int));
   if (!cp.empty())
@@ -1655,6 +1687,9 @@ Solver<T>& make_solver(Batch& B, int kind) {
         ensure(h, s.S2, g * n2 * sizeof(T));
         CU(cudaMemsetAsync(s.t1.p, 0, g * n1 * sizeof(T), h->st));
         CU(cudaMemsetAsync(s.t2.p, 0, g * n2 * sizeof(T), h->st));
+        // S2 is written through its canonical elements only: the elements with
+        // i = j or a = b stay zero
+        CU(cudaMemsetAsync(s.S2.p, 0, g * n2 * sizeof(T), h->st));
         s.sparse_alloc();
         s.nb1 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((n1 + 127) / 128)));
         s.nb2 = std::max(1, std::min(prop_blocks() + 1, static_cast<int>((B.ncanon + 127) / 128)));
@@ -3377,6 +3412,7 @@ ftcc_status ftcc_eval_s(ftcc_ctx* c, int nx, int precision, const double* t1_dev
       Buf a = c->get(nx * N * 8), b = c->get(nx * n3 * 8), d = c->get(nx * N * 8), e = c->get(nx * n3 * 8);
       if (!a.p || !b.p || !d.p || !e.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
       const int16_t* imp = static_cast<const int16_t*>(B.imp.p);
+      CU(cudaMemsetAsync(e.p, 0, nx * n3 * 8, c->st));   // the i = j / a = b elements of S2 are never written
       CU(launch_sp_compress(t1_dev, t2_dev, imp, B.N, nx, static_cast<double*>(a.p), static_cast<double*>(b.p), c->st));
       s.s_kernel(static_cast<double*>(a.p), static_cast<double*>(b.p), static_cast<double*>(d.p),
                  static_cast<double*>(e.p), nx);

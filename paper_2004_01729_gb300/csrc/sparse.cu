@@ -71,7 +71,7 @@ __device__ __forceinline__ long long pos3(int n, int a, int b, int c) {
 template <class T>
 __global__ void sp_amp_kernel(const T* __restrict__ t1, const T* __restrict__ t2,
                               const int16_t* __restrict__ imp, int n, T* __restrict__ ta,
-                              T* __restrict__ tp, T* __restrict__ tr, T* __restrict__ xp) {
+                              T* __restrict__ tp, T* __restrict__ tr, T* __restrict__ xp, int skip_tau) {
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
   const T* s1 = t1 + x * n;
@@ -81,7 +81,7 @@ __global__ void sp_amp_kernel(const T* __restrict__ t1, const T* __restrict__ t2
     int p0, p1, p2;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
-    {   // ta: (i, j, a) = (p0, p1, p2), b implied
+    if (!skip_tau) {   // ta: (i, j, a) = (p0, p1, p2), b implied
       const int b = impl(imp, n, p0, p1, p2);
       T v = T(0.0);
       if (b >= 0) {
@@ -92,7 +92,7 @@ __global__ void sp_amp_kernel(const T* __restrict__ t1, const T* __restrict__ t2
       }
       ta[o] = v;
     }
-    {   // tp: (a, b, m) = (p0, p1, p2), n = q_a + q_b - q_m
+    if (!skip_tau) {   // tp: (a, b, m) = (p0, p1, p2), n = q_a + q_b - q_m
       const int nn = impl(imp, n, p0, p1, p2);
       T v = T(0.0);
       if (nn >= 0) {
@@ -160,6 +160,7 @@ struct SpVec {
   const T *foo, *fvv, *fvo;
   const T *Voovv, *Vovvv, *Vooov, *Vovov, *Voovo;
   const int16_t* imp;
+  const int *l1, *off1, *l2, *off2;   // valid (m, q) = m n + q of (m, q, p) / (p, m, q) per p
   int n;
   T *Fae, *Fmi, *S1, *Ft, *Ft2;
 };
@@ -179,19 +180,24 @@ __global__ void sp_vec_kernel(SpVec<T> a) {
     cmi += s1[m] * a.Vooov[pos3(n, p, m, p)];
     cs1 += s2[pos3(n, p, m, p)] * Fme[m] - s1[m] * a.Vovov[pos3(n, m, p, p)];
   }
-  const long long nn = static_cast<long long>(n) * n;
-  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
-    const int m = static_cast<int>(r / static_cast<uint32_t>(n)), q = static_cast<int>(r - static_cast<uint32_t>(m) * n);
-    const long long o1 = pos3(n, m, q, p);   // (m, q, p)
-    const long long o2 = pos3(n, p, m, q);   // (p, m, q)
+  // only the positions whose implied index exists (the others hold zeros):
+  // (m, q, p) from the list l1 of p, (p, m, q) from l2
+  for (int k = a.off1[p] + threadIdx.x; k < a.off1[p + 1]; k += blockDim.x) {
+    const int mq = a.l1[k];
+    const int m = mq / n, q = mq - m * n;
+    const long long o1 = pos3(n, m, q, p);
     const T t_mqp = s2[o1];
     cae -= T(0.5) * t_mqp * a.Voovv[o1];
-    cmi += T(0.5) * s2[o2] * a.Voovv[o2];
-    cs1 -= T(0.5) * s2[o2] * a.Vovvv[pos3(n, m, p, q)];
-    if (t_mqp != T(0.0)) {
-      const int e = impl(a.imp, n, m, q, p);   // q_e = q_m + q_q - q_p
-      if (e >= 0) cs1 -= T(0.5) * t_mqp * a.Voovo[pos3(n, q, m, e)];
-    }
+    const int e = impl(a.imp, n, m, q, p);   // q_e = q_m + q_q - q_p
+    cs1 -= T(0.5) * t_mqp * a.Voovo[pos3(n, q, m, e)];
+  }
+  for (int k = a.off2[p] + threadIdx.x; k < a.off2[p + 1]; k += blockDim.x) {
+    const int mq = a.l2[k];
+    const int m = mq / n, q = mq - m * n;
+    const long long o2 = pos3(n, p, m, q);
+    const T t = s2[o2];
+    cmi += T(0.5) * t * a.Voovv[o2];
+    cs1 -= T(0.5) * t * a.Vovvv[pos3(n, m, p, q)];
   }
   cae = block_sum(cae, red);
   cmi = block_sum(cmi, red);
@@ -239,21 +245,14 @@ __global__ void sp_wbase_kernel(SpW<T> a) {
     int p0, p1, p2;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
-    {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
-      const int q = impl(a.imp, n, p0, p1, p2);
-      T v = T(0.0);
-      if (q >= 0) {
-        v = a.Voooo[pos3(n, p2, q, p0)];
-        // antisymmetrised in (i, j): (W'_ijmn - W'_jimn) / 2 (<mn||ij> is antisymmetric already)
-        if (a.anti) v += -s1[p0] * a.Vooov[pos3(n, p2, q, p1)] + s1[p1] * a.Vooov[pos3(n, p2, q, p0)];
-        else v -= T(2.0) * s1[p0] * a.Vooov[pos3(n, p2, q, p1)];
+    if (!a.anti) {   // (the antisymmetrised forms come from sp_canon_kernel)
+      {   // (i, j, m) = (p0, p1, p2), n = q_i + q_j - q_m
+        const int q = impl(a.imp, n, p0, p1, p2);
+        a.w1[o] = q >= 0 ? a.Voooo[pos3(n, p2, q, p0)] - T(2.0) * s1[p0] * a.Vooov[pos3(n, p2, q, p1)] : T(0.0);
       }
-      a.w1[o] = v;
+      // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide
+      a.wab[o] = a.Vvvvv[e] - T(2.0) * s1[p0] * a.Vovvv[e];
     }
-    // (a, b, e) = (p0, p1, p2): the positions of the blocks coincide; antisymmetrised
-    // in (a, b): <ab||ef> - s1[a] <ab||ef>_ovvv + s1[b] <ba||ef>_ovvv
-    a.wab[o] = a.anti ? a.Vvvvv[e] - s1[p0] * a.Vovvv[e] + s1[p1] * a.Vovvv[pos3(n, p1, p0, p2)]
-                      : a.Vvvvv[e] - T(2.0) * s1[p0] * a.Vovvv[e];
     {   // (j, b, m) = (p0, p1, p2), e = q_b + q_m - q_j
       const int ee = impl(a.imp, n, p1, p2, p0);
       T v = T(0.0);
@@ -306,19 +305,71 @@ __global__ void sp_rinit_kernel(SpR<T> a) {
 // ---- S2 = P(ij)P(ab) R + <ab||ij>_vvoo
 template <class T>
 __global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Vvvoo,
-                             const int16_t* __restrict__ imp, int n, T* __restrict__ S2) {
+                             const int16_t* __restrict__ imp, const int* __restrict__ canon, int ncanon, int n,
+                             T* __restrict__ S2) {
+  // one canonical element (i < j, a < b) per thread, written to its four
+  // orientations: S2 is exactly antisymmetric (holes of S2 are never read)
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
   const T* r = R + x * n3;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  T* s = S2 + x * n3;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncanon; c += gridDim.x * blockDim.x) {
+    const int e = canon[c];
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
-    const int b = impl(imp, n, i, j, aa);
-    T v = T(0.0);
-    if (b >= 0)
-      v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
-    S2[x * n3 + e] = v;
+    const int b = imp[e];
+    const T v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
+    s[e] = v;
+    s[pos3(n, j, i, aa)] = -v;
+    s[pos3(n, i, j, b)] = -v;
+    s[pos3(n, j, i, b)] = v;
+  }
+}
+
+// The operands the unordered-pair products read, at the canonical positions
+// (p0 < p1, p2 < p3 with p3 = imp[p0][p1][p2]) only:
+//   ta(i,j,a)  = tau_ij^ab,  tp(a,b,m) = tau_mn^ab,
+//   w1(i,j,m)  = (W'_ijmn - W'_jimn)/2 = <mn||ij> - s1[i] <mn||je>_(e=i) + s1[j] <mn||ie>_(e=j),
+//   wab(a,b,e) = (W'_abef - W'_baef)/2 = <ab||ef> - s1[a] <ab||ef>_ovvv + s1[b] <ba||ef>_ovvv
+template <class T>
+struct SpCanon {
+  const T *t1, *t2, *Voooo, *Vooov, *Vvvvv, *Vovvv;
+  const int16_t* imp;
+  const int* canon;
+  int ncanon, n;
+  T *ta, *tp, *w1, *wab;
+};
+
+template <class T>
+__global__ void sp_canon_kernel(SpCanon<T> a) {
+  const int n = a.n;
+  const long long n3 = static_cast<long long>(n) * n * n;
+  const long long x = blockIdx.y;
+  const T* s1 = a.t1 + x * n;
+  const T* s2 = a.t2 + x * n3;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.ncanon; c += gridDim.x * blockDim.x) {
+    const int e = a.canon[c];
+    int p0, p1, p2;
+    dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
+    const int q = a.imp[e];
+    const long long o = x * n3 + e;
+    {
+      T v = s2[e];
+      const T pr = s1[p0] * s1[p1];
+      if (p2 == p0) v += pr;
+      if (p2 == p1) v -= pr;
+      a.ta[o] = v;
+    }
+    {
+      T v = s2[pos3(n, p2, q, p0)];
+      const T pr = s1[p2] * s1[q];
+      if (p0 == p2) v += pr;
+      if (p0 == q) v -= pr;
+      a.tp[o] = v;
+    }
+    a.w1[o] = a.Voooo[pos3(n, p2, q, p0)] - s1[p0] * a.Vooov[pos3(n, p2, q, p1)] +
+              s1[p1] * a.Vooov[pos3(n, p2, q, p0)];
+    a.wab[o] = a.Vvvvv[e] - s1[p0] * a.Vovvv[e] + s1[p1] * a.Vovvv[pos3(n, p1, p0, p2)];
   }
 }
 
@@ -945,9 +996,17 @@ __global__ void sp_eri_adjoint_kernel(const double* __restrict__ bar, const int1
 // ------------------------------------------------------------------ launchers
 template <class T>
 cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
-                          cudaStream_t st) {
+                          int skip_tau, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_amp_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp);
+  sp_amp_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp, skip_tau);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sp_canon(const T* t1, const T* t2, const SpBlocksT<T>& V, const int16_t* imp, const int* canon,
+                            int ncanon, int n, int nx, T* ta, T* tp, T* w1, T* wab, cudaStream_t st) {
+  SpCanon<T> a{t1, t2, V.oooo, V.ooov, V.vvvv, V.ovvv, imp, canon, ncanon, n, ta, tp, w1, wab};
+  sp_canon_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -955,8 +1014,8 @@ template <class T>
 cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st) {
   const int warps = v.n * nx;
   sp_fme_kernel<T><<<(warps * 32 + 127) / 128, 128, 0, st>>>(v.t1, v.fov, v.Voovv, v.n, nx, v.Fme);
-  SpVec<T> a{v.t1, v.t2, v.Fme, v.foo, v.fvv, v.fvo, v.Voovv, v.Vovvv, v.Vooov, v.Vovov, v.Voovo, v.imp, v.n,
-             v.Fae, v.Fmi, v.S1, v.Ft, v.Ft2};
+  SpVec<T> a{v.t1, v.t2, v.Fme, v.foo, v.fvv, v.fvo, v.Voovv, v.Vovvv, v.Vooov, v.Vovov, v.Voovo, v.imp,
+             v.l1, v.off1, v.l2, v.off2, v.n, v.Fae, v.Fmi, v.S1, v.Ft, v.Ft2};
   sp_vec_kernel<T><<<dim3(v.n, nx), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -980,9 +1039,9 @@ cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2,
 }
 
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, int n, int nx, T* S2, cudaStream_t st) {
-  const long long n3 = static_cast<long long>(n) * n * n;
-  sp_s2_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, n, S2);
+cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,
+                         T* S2, cudaStream_t st) {
+  sp_s2_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, canon, ncanon, n, S2);
   return cudaGetLastError();
 }
 
@@ -1018,13 +1077,17 @@ cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, 
 }
 
 #define FTCC_SPARSE_INSTANTIATE(T)                                                                                  \
-  template cudaError_t launch_sp_amp<T>(const T*, const T*, const int16_t*, int, int, T*, T*, T*, T*, cudaStream_t); \
+  template cudaError_t launch_sp_amp<T>(const T*, const T*, const int16_t*, int, int, T*, T*, T*, T*, int,         \
+                                        cudaStream_t);                                                            \
+  template cudaError_t launch_sp_canon<T>(const T*, const T*, const SpBlocksT<T>&, const int16_t*, const int*, int, \
+                                          int, int, T*, T*, T*, T*, cudaStream_t);                                \
   template cudaError_t launch_sp_vectors<T>(const SpVecArgsT<T>&, int, cudaStream_t);                              \
   template cudaError_t launch_sp_wbase<T>(const T*, const SpBlocksT<T>&, const int16_t*, int, int, T*, T*, T*, int, \
                                           cudaStream_t);                                                          \
   template cudaError_t launch_sp_rinit<T>(const T*, const T*, const T*, const T*, const SpBlocksT<T>&,             \
                                           const int16_t*, int, int, T*, cudaStream_t);                             \
-  template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, int, int, T*, cudaStream_t);            \
+  template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, const int*, int, int, int, T*,          \
+                                       cudaStream_t);                                                             \
   template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
   template cudaError_t launch_sp_thermal_eri<T>(const double*, const int16_t*, int, const double*, const double*,  \
                                                 const double*, const double*, T*, cudaStream_t);                  \
