@@ -3197,7 +3197,9 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
   return run_guarded(c0, [&]() -> ftcc_status {
     for (int i = 0; i < n; ++i) drop_batch(ctx[i]);
     // one batch per orbital count, in order of first appearance; the batches
-    // then iterate together (solve_batches)
+    // then iterate together (solve_batches).  With block_sparse every
+    // instance is a batch of its own (its charge tables and sectors), each on
+    // its context's stream, iterating in lockstep with the others.
     std::vector<int> done(n, 0);
     ftcc_status worst = FTCC_OK;
     std::vector<std::shared_ptr<Batch>> batches;
@@ -3208,7 +3210,7 @@ static ftcc_status batched(ftcc_ctx* const* ctx, int n, const double* beta, cons
       std::vector<double> bs, ms;
       std::vector<int> idx;
       for (int j = i; j < n; ++j)
-        if (!done[j] && ctx[j]->N == ctx[i]->N) {
+        if (!done[j] && ctx[j]->N == ctx[i]->N && (!o.block_sparse || j == i)) {
           cs.push_back(ctx[j]);
           bs.push_back(beta[j]);
           ms.push_back(mu[j]);

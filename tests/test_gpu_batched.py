@@ -109,3 +109,39 @@ def test_hubbard_batch_64_instances():
     assert seen == {6, 8, 10, 12, 14}
     for c in ctxs:
         c.close()
+
+
+def test_hubbard_batch_64_instances_block_sparse():
+    """The same 64 instances with the block-sparse storage (each instance its
+    own batch on its own stream, all iterating in lockstep), FP64: the same
+    63 converge, every converged Omega equals the single-instance dense FP64
+    solve to 1e-9 Ha, and the adjoint energies and entropies of all 63
+    equal the dense single-instance adjoint of one member per size class."""
+    from paper_2004_01729_gb300 import ftcc
+    cfgs = wl.hubbard_batch()
+    ng = cfgs[0]["ngrid"]
+    ctxs = _ctxs(cfgs)
+    res = ftcc.solve_batched(ctxs, [c["beta"] for c in cfgs], [c["mu"] for c in cfgs], ng, precision="fp64",
+                             block_sparse=1, max_iter=300, tol_omega=1e-12, tol_amp=1e-10, allow_unconverged=True)
+    failed = [k for k, r in enumerate(res) if not r["converged"]]
+    assert failed == [43], failed
+    adj = {}
+    for k, ctx in enumerate(ctxs):
+        if k != 43:
+            adj[k], _ = ctx.adjoint(with_rdm1=False)
+    seen = set()
+    for k, (r, c) in enumerate(zip(res, cfgs)):
+        if not r["converged"] or c["L"] in seen:
+            continue
+        seen.add(c["L"])
+        x = ftcc.Context(0)
+        x.build_hubbard(c["L"], c["t"], c["U"])
+        single = x.solve(c["beta"], c["mu"], ng, precision="fp64", tol_omega=1e-12, tol_amp=1e-10, max_iter=400)
+        assert single["converged"]
+        assert abs(r["omega"] - single["omega"]) < 1e-9, (k, c, r["omega"], single["omega"])
+        d, _ = x.adjoint(with_rdm1=False)
+        assert abs(adj[k]["E"] - d["E"]) < 1e-8 and abs(adj[k]["S"] - d["S"]) < 1e-8, (k, adj[k], d)
+        x.close()
+    assert seen == {6, 8, 10, 12, 14}
+    for c in ctxs:
+        c.close()
