@@ -363,9 +363,10 @@ cudaError_t launch_sp_slot_sums(const double* I, const double* Ib, const int16_t
 cudaError_t launch_sp_fme(const double* t1, const double* fov, const double* Voovv, int n, int nx, double* out,
                           cudaStream_t st);
 // skip_tau: leave ta, tp to launch_sp_canon (the unordered-pair products read only their canonical elements)
+// list (may be null): with skip_tau, the positions whose (p0, p2, p1) is valid (tr, xp only)
 template <class T>
 cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
-                          int skip_tau, cudaStream_t st);
+                          int skip_tau, const int* list, int nlist, cudaStream_t st);
 // ta, tp and the antisymmetrised W'_mnij, W'_abef at the canonical positions (p0 < p1, p2 < p3) only
 template <class T>
 cudaError_t launch_sp_canon(const T* t1, const T* t2, const SpBlocksT<T>& V, const int16_t* imp, const int* canon,
@@ -373,12 +374,14 @@ cudaError_t launch_sp_canon(const T* t1, const T* t2, const SpBlocksT<T>& V, con
 template <class T> cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st);
 // anti != 0: only W_mbej (the antisymmetrised W'_mnij, W'_abef of the
 // unordered-pair ladders come from launch_sp_canon)
+// list (may be null): with anti, the positions (p0, p1, p2) whose (p1, p2, p0) is valid (W_mbej only)
 template <class T>
 cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* imp, int n, int nx, T* w1, T* wab,
-                            T* wr, int anti, cudaStream_t st);
+                            T* wr, int anti, const int* list, int nlist, cudaStream_t st);
+// R over the valid positions (list) only
 template <class T>
 cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
-                            const int16_t* imp, int n, int nx, T* R, cudaStream_t st);
+                            const int16_t* imp, const int* list, int nlist, int n, int nx, T* R, cudaStream_t st);
 // S2 from its canonical elements, written to their four orientations
 template <class T>
 cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,

@@ -196,6 +196,10 @@ struct Batch {
   Buf canon;                     // canonical doubles positions (i < j, a < b) of the N^3 storage
   long long ncanon = 0;
   Buf vl1, voff1, vl2, voff2;    // per orbital p: valid (m, q) of (m, q, p) and of (p, m, q)
+  // positions (p0, p1, p2) of the N^3 storage whose (p0, p1, p2), (p0, p2, p1)
+  // or (p1, p2, p0) has an implied index (the element-wise kernels' lists)
+  Buf vall, vswap, vrot;
+  int nvall = 0, nvswap = 0, nvrot = 0;
   SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
   ~Batch();
 };
@@ -948,7 +952,10 @@ struct Solver {
       const SpBlocksT<T> VB = sp_blocks();
       const double slice = static_cast<double>(nx) * n3 * sizeof(T);
       timed_launch(kClsOther, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_amp<T>(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, pairs ? 1 : 0, st())); });
+                   [&] {
+                     CU(launch_sp_amp<T>(t1c, t2c, imp, n, nx, pta, ptp, ptr, pxp, pairs ? 1 : 0,
+                                         pairs ? static_cast<const int*>(b->vswap.p) : nullptr, b->nvswap, st()));
+                   });
       SpVecArgsT<T> v{};
       v.t1 = t1c;
       v.t2 = t2c;
@@ -975,7 +982,10 @@ struct Solver {
       v.Ft2 = (T*)Ft2.p;
       timed_launch(kClsOther, 6 * slice, 0.0, [&] { CU(launch_sp_vectors<T>(v, nx, st())); });
       timed_launch(kClsScatter, 3 * slice + 6.0 * n3 * sizeof(T), 0.0,
-                   [&] { CU(launch_sp_wbase<T>(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0, st())); });
+                   [&] {
+                     CU(launch_sp_wbase<T>(t1c, VB, imp, n, nx, pw1, pwab, pwr, pairs ? 1 : 0,
+                                           pairs ? static_cast<const int*>(b->vrot.p) : nullptr, b->nvrot, st()));
+                   });
       const int* canon = static_cast<const int*>(b->canon.p);
       const int ncanon = static_cast<int>(b->ncanon);
       if (pairs)
@@ -989,7 +999,8 @@ struct Solver {
       // W_mbej -= X_jn^fb <mn||ef>                rows (j,b) | (m,e) by q_j - q_b, sum over n
       sector_product(b->sdiff, pxp, n3, static_cast<const T*>(Vp.p), 0, pwr, -1.0, 0, n2, n, 1, 0);
       timed_launch(kClsScatter, 5 * slice, 0.0, [&] {
-        CU(launch_sp_rinit<T>(t1c, t2c, (T*)Ft.p, (T*)Ft2.p, VB, imp, n, nx, pR, st()));
+        CU(launch_sp_rinit<T>(t1c, t2c, (T*)Ft.p, (T*)Ft2.p, VB, imp, static_cast<const int*>(b->vall.p), b->nvall, n,
+                              nx, pR, st()));
       });
       if (pairs) {
         // L/4 in the four orientations of R: rows i < j | a < b, sums over m < n and e < f
@@ -1426,7 +1437,7 @@ Batch::~Batch() {
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
                &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
-               &ssum_u.sec, &ssum_u.work, &canon, &vl1, &voff1, &vl2, &voff2};
+               &ssum_u.sec, &ssum_u.work, &canon, &vl1, &voff1, &vl2, &voff2, &vall, &vswap, &vrot};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1491,6 +1502,21 @@ void build_implied(Batch& B, const ftcc_ctx* c) {
   upload(B.voff1, o1);
   upload(B.vl2, l2);
   upload(B.voff2, o2);
+  std::vector<int> va, vs, vr;
+  for (int p0 = 0; p0 < n; ++p0)
+    for (int p1 = 0; p1 < n; ++p1)
+      for (int p2 = 0; p2 < n; ++p2) {
+        const int e = static_cast<int>((static_cast<long long>(p0) * n + p1) * n + p2);
+        if (t[e] >= 0) va.push_back(e);
+        if (t[(static_cast<long long>(p0) * n + p2) * n + p1] >= 0) vs.push_back(e);
+        if (t[(static_cast<long long>(p1) * n + p2) * n + p0] >= 0) vr.push_back(e);
+      }
+  upload(B.vall, va);
+  upload(B.vswap, vs);
+  upload(B.vrot, vr);
+  B.nvall = static_cast<int>(va.size());
+  B.nvswap = static_cast<int>(vs.size());
+  B.nvrot = static_cast<int>(vr.size());
   B.ncanon = static_cast<long long>(cp.size());
   ensure(B.home, B.canon, std::max<size_t>(1, cp.size()) * sizeof(int));
   if (!cp.empty())
@@ -2092,7 +2118,8 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
     if (static_cast<int>(home->charge.size()) != N)
       throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: the system has no conserved orbital charges (UEG or k-space Hubbard)"};
     if (B->no != N || B->nv != N) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: truncation must keep every orbital"};
-    if (N > 32767) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: at most 32767 spin orbitals"};
+    if (static_cast<long long>(N) * N * N >= (1LL << 31))
+      throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: N^3 positions must fit 32-bit indices (N <= 1290)"};
     B->sparse = true;
     build_implied(*B, home);
     build_sectors(*B, home, false, B->ssum);

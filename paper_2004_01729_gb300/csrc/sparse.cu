@@ -71,13 +71,18 @@ __device__ __forceinline__ long long pos3(int n, int a, int b, int c) {
 template <class T>
 __global__ void sp_amp_kernel(const T* __restrict__ t1, const T* __restrict__ t2,
                               const int16_t* __restrict__ imp, int n, T* __restrict__ ta,
-                              T* __restrict__ tp, T* __restrict__ tr, T* __restrict__ xp, int skip_tau) {
+                              T* __restrict__ tp, T* __restrict__ tr, T* __restrict__ xp, int skip_tau,
+                              const int* __restrict__ list, int nlist) {
+  // skip_tau with a list: only tr and xp, at the positions (p0, p1, p2) whose
+  // (p0, p2, p1) is valid (the only ones the ordered products read)
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
   const T* s1 = t1 + x * n;
   const T* s2 = t2 + x * n3;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  const long long nloop = list ? nlist : n3;
+  for (long long cc = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; cc < nloop;
+       cc += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long e = list ? list[cc] : cc;
     int p0, p1, p2;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
@@ -230,6 +235,8 @@ template <class T>
 struct SpW {
   const T *t1, *Voooo, *Vooov, *Vvvvv, *Vovvv, *Vovvo, *Voovo;
   const int16_t* imp;
+  const int* list;   // anti: the positions (j, b, m) of W_mbej whose e exists
+  int nlist;
   int n, anti;
   T *w1, *wab, *wr;
 };
@@ -240,8 +247,10 @@ __global__ void sp_wbase_kernel(SpW<T> a) {
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
   const T* s1 = a.t1 + x * n;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  const long long nloop = a.list ? a.nlist : n3;
+  for (long long cc = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; cc < nloop;
+       cc += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long e = a.list ? a.list[cc] : cc;
     int p0, p1, p2;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p0, p1, p2);
     const long long o = x * n3 + e;
@@ -274,6 +283,8 @@ template <class T>
 struct SpR {
   const T *t1, *t2, *Ft, *Ft2, *Vvvvo, *Vovoo, *Vovvo;
   const int16_t* imp;
+  const int* list;   // the valid positions (imp >= 0): every warp lane does useful FP64 work
+  int nlist;
   int n;
   T* R;
 };
@@ -287,13 +298,16 @@ __global__ void sp_rinit_kernel(SpR<T> a) {
   const T* s2 = a.t2 + x * n3;
   const T* Ft = a.Ft + x * n;
   const T* Ft2 = a.Ft2 + x * n;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  // positions whose implied index is missing are never read: only the valid
+  // list is written (a warp's FP64 instructions cost the pipe for all of its
+  // lanes, so a dense loop that skips holes costs as much as one that does not)
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nlist; c += gridDim.x * blockDim.x) {
+    const long long e = a.list[c];
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
     T v = T(0.0);
-    if (b >= 0) {
+    {
       const long long c = pos3(n, aa, b, i);   // (a, b, i), j implied
       v = T(0.5) * s2[e] * Ft[b] + T(0.5) * Ft2[i] * s2[pos3(n, j, i, aa)] + T(0.5) * s1[i] * a.Vvvvo[c] -
           T(0.5) * s1[aa] * a.Vovoo[c] + s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)];
@@ -996,9 +1010,10 @@ __global__ void sp_eri_adjoint_kernel(const double* __restrict__ bar, const int1
 // ------------------------------------------------------------------ launchers
 template <class T>
 cudaError_t launch_sp_amp(const T* t1, const T* t2, const int16_t* imp, int n, int nx, T* ta, T* tp, T* tr, T* xp,
-                          int skip_tau, cudaStream_t st) {
+                          int skip_tau, const int* list, int nlist, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  sp_amp_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp, skip_tau);
+  sp_amp_kernel<T><<<dim3(sp_grid(list ? nlist : n3), nx), kSpThreads, 0, st>>>(t1, t2, imp, n, ta, tp, tr, xp,
+                                                                                skip_tau, list, nlist);
   return cudaGetLastError();
 }
 
@@ -1022,19 +1037,18 @@ cudaError_t launch_sp_vectors(const SpVecArgsT<T>& v, int nx, cudaStream_t st) {
 
 template <class T>
 cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* imp, int n, int nx, T* w1, T* wab,
-                            T* wr, int anti, cudaStream_t st) {
+                            T* wr, int anti, const int* list, int nlist, cudaStream_t st) {
   const long long n3 = static_cast<long long>(n) * n * n;
-  SpW<T> a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, n, anti, w1, wab, wr};
-  sp_wbase_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+  SpW<T> a{t1, V.oooo, V.ooov, V.vvvv, V.ovvv, V.ovvo, V.oovo, imp, list, nlist, n, anti, w1, wab, wr};
+  sp_wbase_kernel<T><<<dim3(sp_grid(list ? nlist : n3), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
-                            const int16_t* imp, int n, int nx, T* R, cudaStream_t st) {
-  const long long n3 = static_cast<long long>(n) * n * n;
-  SpR<T> a{t1, t2, Ft, Ft2, V.vvvo, V.ovoo, V.ovvo, imp, n, R};
-  sp_rinit_kernel<T><<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+                            const int16_t* imp, const int* list, int nlist, int n, int nx, T* R, cudaStream_t st) {
+  SpR<T> a{t1, t2, Ft, Ft2, V.vvvo, V.ovoo, V.ovvo, imp, list, nlist, n, R};
+  sp_rinit_kernel<T><<<dim3(sp_grid(nlist), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1078,14 +1092,14 @@ cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, 
 
 #define FTCC_SPARSE_INSTANTIATE(T)                                                                                  \
   template cudaError_t launch_sp_amp<T>(const T*, const T*, const int16_t*, int, int, T*, T*, T*, T*, int,         \
-                                        cudaStream_t);                                                            \
+                                        const int*, int, cudaStream_t);                                           \
   template cudaError_t launch_sp_canon<T>(const T*, const T*, const SpBlocksT<T>&, const int16_t*, const int*, int, \
                                           int, int, T*, T*, T*, T*, cudaStream_t);                                \
   template cudaError_t launch_sp_vectors<T>(const SpVecArgsT<T>&, int, cudaStream_t);                              \
   template cudaError_t launch_sp_wbase<T>(const T*, const SpBlocksT<T>&, const int16_t*, int, int, T*, T*, T*, int, \
-                                          cudaStream_t);                                                          \
+                                          const int*, int, cudaStream_t);                                         \
   template cudaError_t launch_sp_rinit<T>(const T*, const T*, const T*, const T*, const SpBlocksT<T>&,             \
-                                          const int16_t*, int, int, T*, cudaStream_t);                             \
+                                          const int16_t*, const int*, int, int, int, T*, cudaStream_t);            \
   template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, const int*, int, int, int, T*,          \
                                        cudaStream_t);                                                             \
   template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
