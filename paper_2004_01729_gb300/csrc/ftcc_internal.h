@@ -387,6 +387,9 @@ template <class T>
 cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,
                          T* S2, cudaStream_t st);
 template <class T> cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
+// the same products for work items of sectors of at most 16 pairs (16 x 16 tiles, 64 threads)
+template <class T>
+cudaError_t launch_sector_gemm_small(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
 int sector_tile();
 template <class T>
 cudaError_t launch_sp_thermal_eri(const double* eri, const int16_t* imp, int n, const double* f0, const double* f1,

@@ -153,8 +153,8 @@ struct Inst {
 // (sum) or q_p - q_q (difference), with the summed-index list of each sector
 // and the tiles of its products (see sector_gemm_kernel).
 struct SecTab {
-  Buf ent, kl, sec, work;
-  int nwork = 0;
+  Buf ent, kl, sec, work, work_small;
+  int nwork = 0, nwork_small = 0;   // work_small: one item per sector of at most 16 pairs
   double flops = 0;   // 2 sum_s rows_s^2 K_s per slice
 };
 
@@ -922,8 +922,12 @@ struct Solver {
       g.anti4 = anti4;
       const double fl = tab.flops * nx * (A2 ? 2 : 1);
       if (counting) gemm_flops += static_cast<long long>(fl);
-      timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl,
-                   [&] { CU(launch_sector_gemm<T>(g, tab.nwork, nx, st())); });
+      timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl, [&] {
+        CU(launch_sector_gemm<T>(g, tab.nwork, nx, st()));
+        SecGemmArgsT<T> gs = g;
+        gs.work = static_cast<const int4*>(tab.work_small.p);
+        CU(launch_sector_gemm_small<T>(gs, tab.nwork_small, nx, st()));
+      });
     }
   }
 
@@ -1043,8 +1047,12 @@ struct Solver {
     g.kl = static_cast<const int*>(tab.kl.p);
     g.sec = static_cast<const int4*>(tab.sec.p);
     g.work = static_cast<const int4*>(tab.work.p);
-    timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(double), tab.flops * nx,
-                 [&] { CU(launch_sector_tn(g, tab.nwork, st())); });
+    timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(double), tab.flops * nx, [&] {
+      CU(launch_sector_tn(g, tab.nwork, st()));
+      SecTnArgs gs = g;
+      gs.work = static_cast<const int4*>(tab.work_small.p);
+      CU(launch_sector_tn(gs, tab.nwork_small, st()));
+    });
   }
 
   // Transpose of sparse_s_kernel: (u1, u2) = cotangents of (S1, S2) ->
@@ -1437,7 +1445,7 @@ Batch::~Batch() {
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
                &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
                &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
-               &ssum_u.sec, &ssum_u.work, &canon, &vl1, &voff1, &vl2, &voff2, &vall, &vswap, &vrot};
+               &ssum_u.sec, &ssum_u.work, &ssum.work_small, &sdiff.work_small, &ssum_u.work_small, &canon, &vl1, &voff1, &vl2, &voff2, &vall, &vswap, &vrot};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1545,7 +1553,7 @@ void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unord
     }
   std::vector<int2> ent;
   std::vector<int> kl;
-  std::vector<int4> sec, work;
+  std::vector<int4> sec, work, work_small;
   T.flops = 0;
   for (size_t s = 0; s < rows.size(); ++s) {
     const int off = static_cast<int>(ent.size()), cnt = static_cast<int>(rows[s].size());
@@ -1554,21 +1562,31 @@ void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unord
       kl.push_back(diff ? e.y : e.x);
     }
     sec.push_back(make_int4(off, cnt, off, cnt));
-    for (int r0 = 0; r0 < cnt; r0 += tile)
-      for (int c0 = 0; c0 < cnt; c0 += tile) work.push_back(make_int4(static_cast<int>(s), r0, c0, 0));
+    if (cnt <= 16) {
+      work_small.push_back(make_int4(static_cast<int>(s), 0, 0, 0));
+    } else {
+      for (int r0 = 0; r0 < cnt; r0 += tile)
+        for (int c0 = 0; c0 < cnt; c0 += tile) work.push_back(make_int4(static_cast<int>(s), r0, c0, 0));
+    }
     T.flops += 2.0 * cnt * static_cast<double>(cnt) * cnt;
   }
   ftcc_ctx* h = B.home;
   ensure(h, T.ent, ent.size() * sizeof(int2));
   ensure(h, T.kl, kl.size() * sizeof(int));
   ensure(h, T.sec, sec.size() * sizeof(int4));
-  ensure(h, T.work, work.size() * sizeof(int4));
+  ensure(h, T.work, std::max<size_t>(1, work.size()) * sizeof(int4));
+  ensure(h, T.work_small, std::max<size_t>(1, work_small.size()) * sizeof(int4));
+  if (!work_small.empty())
+    CU(cudaMemcpyAsync(T.work_small.p, work_small.data(), work_small.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                       h->st));
   CU(cudaMemcpyAsync(T.ent.p, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
   CU(cudaMemcpyAsync(T.kl.p, kl.data(), kl.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CU(cudaMemcpyAsync(T.sec.p, sec.data(), sec.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
-  CU(cudaMemcpyAsync(T.work.p, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+  if (!work.empty())
+    CU(cudaMemcpyAsync(T.work.p, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
   CU(cudaStreamSynchronize(h->st));
   T.nwork = static_cast<int>(work.size());
+  T.nwork_small = static_cast<int>(work_small.size());
 }
 
 }  // namespace ftcc

@@ -404,30 +404,34 @@ constexpr int kSecKc = 32;                     // K chunk staged in shared memor
 constexpr int kSecThreads = 256;
 constexpr int kSecO = (kSecT * kSecT + kSecThreads - 1) / kSecThreads;   // outputs per thread
 
-template <class T>
-__global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgsT<T> g) {
-  __shared__ T As[kSecKc][kSecT + 1], Bs[kSecKc][kSecT + 1];
+// TILE x TILE outputs per CTA of THREADS threads: 48 / 256 for the sectors
+// of more than 16 pairs, 16 / 64 for the small ones (less staging and
+// synchronisation per CTA, more CTAs per SM)
+template <class T, int TILE, int THREADS>
+__global__ void __launch_bounds__(THREADS) sector_gemm_kernel(SecGemmArgsT<T> g) {
+  constexpr int NO = (TILE * TILE + THREADS - 1) / THREADS;
+  __shared__ T As[kSecKc][TILE + 1], Bs[kSecKc][TILE + 1];
   const int4 w = g.work[blockIdx.x];
   const int4 sec = g.sec[w.x];   // entry offset, rows, K offset, K count
   const long long x = blockIdx.y;
   const int n = g.n;
-  const int nr = min(kSecT, sec.y - w.y), nc = min(kSecT, sec.y - w.z);
+  const int nr = min(TILE, sec.y - w.y), nc = min(TILE, sec.y - w.z);
   const int nout = nr * nc;
-  T acc[kSecO];
+  T acc[NO];
 #pragma unroll
-  for (int j = 0; j < kSecO; ++j) acc[j] = T(0.0);
+  for (int j = 0; j < NO; ++j) acc[j] = T(0.0);
   for (int prod = 0; prod < (g.A2 ? 2 : 1); ++prod) {
   const T* A = (prod ? g.A2 : g.A) + x * g.ax;
   const T* B = (prod ? g.B2 : g.B) + x * g.bx;
   for (int k0 = 0; k0 < sec.w; k0 += kSecKc) {
     const int kc = min(kSecKc, sec.w - k0);
     // stage A rows [nr][kc] and B rows [nc][kc] (consecutive threads walk a row's K list)
-    for (int idx = threadIdx.x; idx < nr * kc; idx += kSecThreads) {
+    for (int idx = threadIdx.x; idx < nr * kc; idx += THREADS) {
       const int r = idx / kc, k = idx - r * kc;
       const int2 pr = g.ent[sec.x + w.y + r];
       As[k][r] = A[(static_cast<long long>(pr.x) * n + pr.y) * n + g.kl[sec.z + k0 + k]];
     }
-    for (int idx = threadIdx.x; idx < nc * kc; idx += kSecThreads) {
+    for (int idx = threadIdx.x; idx < nc * kc; idx += THREADS) {
       const int c = idx / kc, k = idx - c * kc;
       const int2 pr = g.ent[sec.x + w.z + c];
       const long long row = g.swapB ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
@@ -435,8 +439,8 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgsT<T
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSecO; ++j) {
-      const int o = threadIdx.x + j * kSecThreads;
+    for (int j = 0; j < NO; ++j) {
+      const int o = threadIdx.x + j * THREADS;
       if (o < nout) {
         const int r = o / nc, c = o - r * nc;
         T a = acc[j];
@@ -448,8 +452,8 @@ __global__ void __launch_bounds__(kSecThreads) sector_gemm_kernel(SecGemmArgsT<T
   }
   }
 #pragma unroll
-  for (int j = 0; j < kSecO; ++j) {
-    const int o = threadIdx.x + j * kSecThreads;
+  for (int j = 0; j < NO; ++j) {
+    const int o = threadIdx.x + j * THREADS;
     if (o < nout) {
       const int r = o / nc, c = o - r * nc;
       const int2 pr = g.ent[sec.x + w.y + r], pc = g.ent[sec.x + w.z + c];
@@ -1063,7 +1067,15 @@ template <class T>
 cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st) {
   if (nwork <= 0 || nx <= 0) return cudaSuccess;
   if (nx > 65535) return cudaErrorInvalidValue;
-  sector_gemm_kernel<T><<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
+  sector_gemm_kernel<T, kSecT, kSecThreads><<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_sector_gemm_small(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st) {
+  if (nwork <= 0 || nx <= 0) return cudaSuccess;
+  if (nx > 65535) return cudaErrorInvalidValue;
+  sector_gemm_kernel<T, 16, 64><<<dim3(nwork, nx), 64, 0, st>>>(g);
   return cudaGetLastError();
 }
 int sector_tile() { return kSecT; }
@@ -1103,6 +1115,7 @@ cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, 
   template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, const int*, int, int, int, T*,          \
                                        cudaStream_t);                                                             \
   template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
+  template cudaError_t launch_sector_gemm_small<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                \
   template cudaError_t launch_sp_thermal_eri<T>(const double*, const int16_t*, int, const double*, const double*,  \
                                                 const double*, const double*, T*, cudaStream_t);                  \
   template cudaError_t launch_sp_swap12<T>(const T*, int, T*, cudaStream_t);                                       \
