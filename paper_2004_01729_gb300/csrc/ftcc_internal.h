@@ -339,11 +339,14 @@ struct SpVjpArgs {
   const double *Rb, *w1b, *wabb, *wrb, *tab, *tpb, *trb, *xpb;
   SpBlocks V;
   const int16_t* imp;
+  const int* list;                                   // the valid N^3 positions
+  int nlist;
   int n;
   double *Ftb, *Ft2b, *Faeb, *Fmib, *Fmeb;           // vector cotangents (written)
-  double *t1b, *t2b;                                 // outputs
+  double *t1b, *t2b;                                 // outputs (the holes of t2b must be zero: not written)
 };
-cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, int n, int nx, double* Rb, cudaStream_t st);
+cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, const int* list, int nlist, int n, int nx,
+                           double* Rb, cudaStream_t st);
 cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st);
 cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st);
 cudaError_t launch_sp_t2bar(const SpVjpArgs& v, int nx, cudaStream_t st);

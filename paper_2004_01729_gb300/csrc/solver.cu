@@ -1074,7 +1074,9 @@ struct Solver {
         CU(cudaMemsetAsync(q, 0, nx * n3 * sizeof(double), st()));
       const double *ta_ = (double*)ta.p, *tp_ = (double*)tt.p, *tr_ = (double*)Y.p, *xp_ = (double*)X.p,
                    *w1_ = (double*)Wmnij.p, *wab_ = (double*)Wabef.p, *wr_ = (double*)Wmbej.p;
-      timed_launch(kClsScatter, 2.0 * nx * n3 * 8, 0.0, [&] { CU(launch_sp_s2_t(u2, imp, n, nx, Rb, st())); });
+      const int* vall = static_cast<const int*>(b->vall.p);
+      timed_launch(kClsScatter, 2.0 * nx * n3 * 8, 0.0,
+                   [&] { CU(launch_sp_s2_t(u2, imp, vall, b->nvall, n, nx, Rb, st())); });
       // ring: R += tr wr (rows (i,a) | (j,b) swapped, output (n2, 1, 0, n))
       sector_tn(b->sdiff, trb, n3, Rb, wr_, n3, 1.0, 0, 1, n2, 1, 0, n);
       sector_tn(b->sdiff, wrb, n3, Rb, tr_, n3, 1.0, 1, 0, 0, n, n2, 1);
@@ -1120,6 +1122,8 @@ struct Solver {
       va.xpb = xpb;
       va.V = VB;
       va.imp = imp;
+      va.list = vall;
+      va.nlist = b->nvall;
       va.n = n;
       va.Ftb = (double*)bFt.p;
       va.Ft2b = (double*)bFt2.p;
@@ -2576,6 +2580,8 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   ensure(h, B.u2, n2 * es);
   ensure(h, B.tb1, n1 * es);
   ensure(h, B.tb2, n2 * es);
+  // (the block-sparse transpose writes only the valid positions: its holes stay zero)
+  CU(cudaMemsetAsync(B.tb2.p, 0, n2 * es, h->st));
   ensure(h, B.dE1, n1 * es);
   ensure(h, B.cz, nz * ng * 8);
   const int nblk = 152 * 4;

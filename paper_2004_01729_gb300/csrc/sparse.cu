@@ -557,17 +557,18 @@ __global__ void sp_expand_kernel(const double* __restrict__ s1, const double* __
 namespace {
 
 // Rb = P(ij)P(ab) S2b (the antisymmetriser is its own transpose)
-__global__ void sp_s2_t_kernel(const double* __restrict__ S2b, const int16_t* __restrict__ imp, int n,
-                               double* __restrict__ Rb) {
+// (over the valid positions only: the holes of Rb are never read)
+__global__ void sp_s2_t_kernel(const double* __restrict__ S2b, const int16_t* __restrict__ imp,
+                               const int* __restrict__ list, int nlist, int n, double* __restrict__ Rb) {
   const long long n3 = static_cast<long long>(n) * n * n;
   const long long x = blockIdx.y;
   const double* g = S2b + x * n3;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nlist; c += gridDim.x * blockDim.x) {
+    const long long e = list[c];
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(imp, n, i, j, aa);
-    Rb[x * n3 + e] = b >= 0 ? g[e] - g[pos3(n, j, i, aa)] - g[pos3(n, i, j, b)] + g[pos3(n, j, i, b)] : 0.0;
+    Rb[x * n3 + e] = g[e] - g[pos3(n, j, i, aa)] - g[pos3(n, i, j, b)] + g[pos3(n, j, i, b)];
   }
 }
 
@@ -580,6 +581,8 @@ struct SpT2 {
   const double *t1, *Rb, *Ft, *Ft2, *S1b, *Fme, *Fmib, *Faeb, *tab, *tpb, *trb, *xpb;
   const double *Vovvv, *Voovv, *Voovo;
   const int16_t* imp;
+  const int* list;   // valid positions (the holes of t2b are zero from the start and stay so)
+  int nlist;
   int n;
   double* t2b;
 };
@@ -599,8 +602,8 @@ __global__ void sp_t2bar_kernel(SpT2 a) {
   const double* tpb = a.tpb + x * n3;
   const double* trb = a.trb + x * n3;
   const double* xpb = a.xpb + x * n3;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nlist; c += gridDim.x * blockDim.x) {
+    const long long e = a.list[c];
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
@@ -812,6 +815,8 @@ namespace {
 struct SpFixT {
   const double *t1, *t2, *S2b, *Rb, *w1b, *wabb, *wrb, *S1b, *Faeb, *Fmib, *Fmeb, *cz;
   const int16_t* imp;
+  const int* list;   // valid positions of the blocks
+  int nlist;
   int n, nx;
   double* Vb[11];
 };
@@ -822,10 +827,9 @@ __global__ void sp_fixed_bar_kernel(SpFixT a) {
   const int blk = blockIdx.y;
   double* out = a.Vb[blk];
   if (!out) return;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n3;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nlist; c += gridDim.x * blockDim.x) {
+    const long long e = a.list[c];
     const int sl = a.imp[e];
-    if (sl < 0) continue;
     int p, q, r;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), p, q, r);
     double v = 0.0;
@@ -1138,9 +1142,9 @@ cudaError_t launch_sp_expand(const double* s1, const double* s2, const int16_t* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, int n, int nx, double* Rb, cudaStream_t st) {
-  const long long n3 = static_cast<long long>(n) * n * n;
-  sp_s2_t_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(S2b, imp, n, Rb);
+cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, const int* list, int nlist, int n, int nx,
+                           double* Rb, cudaStream_t st) {
+  sp_s2_t_kernel<<<dim3(sp_grid(nlist), nx), kSpThreads, 0, st>>>(S2b, imp, list, nlist, n, Rb);
   return cudaGetLastError();
 }
 
@@ -1163,8 +1167,9 @@ cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st) {
 cudaError_t launch_sp_t2bar(const SpVjpArgs& v, int nx, cudaStream_t st) {
   const long long n3 = static_cast<long long>(v.n) * v.n * v.n;
   SpT2 a{v.t1, v.Rb, v.Ft, v.Ft2, v.S1b, v.Fme, v.Fmib, v.Faeb, v.tab, v.tpb, v.trb, v.xpb, v.V.ovvv, v.V.oovv,
-         v.V.oovo, v.imp, v.n, v.t2b};
-  sp_t2bar_kernel<<<dim3(sp_grid(n3), nx), kSpThreads, 0, st>>>(a);
+         v.V.oovo, v.imp, v.list, v.nlist, v.n, v.t2b};
+  (void)n3;
+  sp_t2bar_kernel<<<dim3(sp_grid(v.nlist), nx), kSpThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1185,10 +1190,13 @@ cudaError_t launch_sp_fixed_bar(const SpVjpArgs& v, const double* S2b, const dou
   a.Fmeb = v.Fmeb;
   a.cz = cz;
   a.imp = v.imp;
+  a.list = v.list;
+  a.nlist = v.nlist;
   a.n = v.n;
   a.nx = nx;
   for (int k = 0; k < 11; ++k) a.Vb[k] = Vbar[k];
-  sp_fixed_bar_kernel<<<dim3(sp_grid(n3), 11), kSpThreads, 0, st>>>(a);
+  (void)n3;
+  sp_fixed_bar_kernel<<<dim3(sp_grid(v.nlist), 11), kSpThreads, 0, st>>>(a);
   sp_fock_bar_kernel<<<(v.n + 127) / 128, 128, 0, st>>>(v.t1, v.Fmeb, v.Faeb, v.Fmib, v.S1b, cz, v.n, nx, fbar[0],
                                                           fbar[1], fbar[2], fbar[3]);
   return cudaGetLastError();
