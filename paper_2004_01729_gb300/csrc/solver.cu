@@ -47,6 +47,7 @@ inline bool is_hole(char c) { return c >= 'i' && c <= 'n'; }
 
 template <class T> struct Solver;
 struct Batch;
+struct SpTables;
 
 }  // namespace ftcc
 
@@ -74,6 +75,10 @@ struct ftcc_ctx {
   // Hubbard ring: crystal momentum mod L and S_z); empty otherwise
   std::vector<std::array<int, 4>> charge;
   int charge_mod[4] = {0, 0, 0, 0};
+  // block-sparse tables of these charges (implied-index table, lists of valid
+  // positions, pair sectors), built by the first block-sparse prepare and
+  // kept until the system is rebuilt
+  std::shared_ptr<ftcc::SpTables> sptab;
 
   ftcc::Buf get(size_t bytes) {
     ftcc::Buf b;
@@ -158,7 +163,29 @@ struct SecTab {
   double flops = 0;   // 2 sum_s rows_s^2 K_s per slice
 };
 
-struct Batch {
+// Block-sparse tables of one set of orbital charges (option block_sparse): the
+// implied-index table imp[a][b][c] (int16, N^3), lists of valid positions and
+// the pair-charge sectors.  SpTables owns the device buffers (cached on the
+// context); a batch holds a copy of the view and a reference to the owner.
+struct SpTableView {
+  Buf imp;
+  Buf canon;                     // canonical doubles positions (i < j, a < b) of the N^3 storage
+  long long ncanon = 0;
+  Buf vl1, voff1, vl2, voff2;    // per orbital p: valid (m, q) of (m, q, p) and of (p, m, q)
+  // positions (p0, p1, p2) of the N^3 storage whose (p0, p1, p2), (p0, p2, p1)
+  // or (p1, p2, p0) has an implied index (the element-wise kernels' lists)
+  Buf vall, vswap, vrot;
+  int nvall = 0, nvswap = 0, nvrot = 0;
+  SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
+};
+
+struct SpTables : SpTableView {
+  ftcc_ctx* home = nullptr;
+  int n = 0;
+  ~SpTables();
+};
+
+struct Batch : SpTableView {
   ftcc_ctx* home = nullptr;      // allocator, stream and error flag of the batch
   std::vector<Inst> inst;
   int nz = 0, N = 0, no = 0, nv = 0, ng = 0, prec = 0;
@@ -189,18 +216,9 @@ struct Batch {
   bool solved = false;
   bool solved_live = false;   // every live member converged (diverged members are frozen)
   int quad = FTCC_QUAD_SIMPSON;   // integral form (Simpson fixed point) or an RK march of Eq. smud
-  // block-sparse storage (option block_sparse): the implied-index table
-  // imp[a][b][c] (int16, N^3) and the pair-charge sectors
+  // block-sparse storage (option block_sparse)
   bool sparse = false;
-  Buf imp;
-  Buf canon;                     // canonical doubles positions (i < j, a < b) of the N^3 storage
-  long long ncanon = 0;
-  Buf vl1, voff1, vl2, voff2;    // per orbital p: valid (m, q) of (m, q, p) and of (p, m, q)
-  // positions (p0, p1, p2) of the N^3 storage whose (p0, p1, p2), (p0, p2, p1)
-  // or (p1, p2, p0) has an implied index (the element-wise kernels' lists)
-  Buf vall, vswap, vrot;
-  int nvall = 0, nvswap = 0, nvrot = 0;
-  SecTab ssum, sdiff, ssum_u;   // ssum_u: unordered pairs p < q only
+  std::shared_ptr<SpTables> sp_owner;
   ~Batch();
 };
 
@@ -1447,9 +1465,14 @@ Batch::~Batch() {
     for (Buf* q : bs) home->put(*q);
   }
   Buf* bs[] = {&idxO, &idxV, &em, &ep, &hz, &V64, &F64, &state, &live, &m1, &m2, &mn1, &mn2, &u1, &u2, &tb1,
-               &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz, &imp, &ssum.ent, &ssum.kl, &ssum.sec,
-               &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work, &ssum_u.ent, &ssum_u.kl,
-               &ssum_u.sec, &ssum_u.work, &ssum.work_small, &sdiff.work_small, &ssum_u.work_small, &canon, &vl1, &voff1, &vl2, &voff2, &vall, &vswap, &vrot};
+               &tb2, &dE1, &cz, &lpart, &facOz, &facVz, &epsz};
+  for (Buf* q : bs) home->put(*q);
+}
+
+SpTables::~SpTables() {
+  Buf* bs[] = {&imp, &ssum.ent, &ssum.kl, &ssum.sec, &ssum.work, &sdiff.ent, &sdiff.kl, &sdiff.sec, &sdiff.work,
+               &ssum_u.ent, &ssum_u.kl, &ssum_u.sec, &ssum_u.work, &ssum.work_small, &sdiff.work_small,
+               &ssum_u.work_small, &canon, &vl1, &voff1, &vl2, &voff2, &vall, &vswap, &vrot};
   for (Buf* q : bs) home->put(*q);
 }
 
@@ -1467,82 +1490,15 @@ uint64_t charge_key(const std::array<int, 4>& q) {
 }
 }  // namespace
 
-// imp[a][b][c] = the orbital whose charge is q_a + q_b - q_c, or -1
-void build_implied(Batch& B, const ftcc_ctx* c) {
-  const int n = B.N;
-  std::unordered_map<uint64_t, int> orb;
-  for (int p = 0; p < n; ++p) orb[charge_key(canon_charge(c->charge[p], c->charge_mod))] = p;
-  if (static_cast<int>(orb.size()) != n) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: two orbitals share a charge"};
-  const long long n3 = static_cast<long long>(n) * n * n;
-  std::vector<int16_t> t(n3);
-  for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b)
-      for (int cc = 0; cc < n; ++cc) {
-        std::array<int, 4> q;
-        for (int k = 0; k < 4; ++k) q[k] = c->charge[a][k] + c->charge[b][k] - c->charge[cc][k];
-        auto it = orb.find(charge_key(canon_charge(q, c->charge_mod)));
-        t[(static_cast<long long>(a) * n + b) * n + cc] = static_cast<int16_t>(it == orb.end() ? -1 : it->second);
-      }
-  ensure(B.home, B.imp, n3 * sizeof(int16_t));
-  CU(cudaMemcpyAsync(B.imp.p, t.data(), n3 * sizeof(int16_t), cudaMemcpyHostToDevice, B.home->st));
-  // canonical positions of the antisymmetric doubles: i < j, a < b
-  std::vector<int> cp;
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j)
-      for (int a = 0; a < n; ++a) {
-        const long long e = (static_cast<long long>(i) * n + j) * n + a;
-        if (t[e] > a) cp.push_back(static_cast<int>(e));
-      }
-  // per orbital p, the valid positions (m, q, p) and (p, m, q) as m n + q
-  std::vector<int> l1, o1(n + 1, 0), l2, o2(n + 1, 0);
-  for (int p = 0; p < n; ++p) {
-    o1[p] = static_cast<int>(l1.size());
-    o2[p] = static_cast<int>(l2.size());
-    for (int m = 0; m < n; ++m)
-      for (int q = 0; q < n; ++q) {
-        if (t[(static_cast<long long>(m) * n + q) * n + p] >= 0) l1.push_back(m * n + q);
-        if (t[(static_cast<long long>(p) * n + m) * n + q] >= 0) l2.push_back(m * n + q);
-      }
-  }
-  o1[n] = static_cast<int>(l1.size());
-  o2[n] = static_cast<int>(l2.size());
-  auto upload = [&](Buf& b, const std::vector<int>& v) {
-    ensure(B.home, b, std::max<size_t>(1, v.size()) * sizeof(int));
-    if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, B.home->st));
-  };
-  upload(B.vl1, l1);
-  upload(B.voff1, o1);
-  upload(B.vl2, l2);
-  upload(B.voff2, o2);
-  std::vector<int> va, vs, vr;
-  for (int p0 = 0; p0 < n; ++p0)
-    for (int p1 = 0; p1 < n; ++p1)
-      for (int p2 = 0; p2 < n; ++p2) {
-        const int e = static_cast<int>((static_cast<long long>(p0) * n + p1) * n + p2);
-        if (t[e] >= 0) va.push_back(e);
-        if (t[(static_cast<long long>(p0) * n + p2) * n + p1] >= 0) vs.push_back(e);
-        if (t[(static_cast<long long>(p1) * n + p2) * n + p0] >= 0) vr.push_back(e);
-      }
-  upload(B.vall, va);
-  upload(B.vswap, vs);
-  upload(B.vrot, vr);
-  B.nvall = static_cast<int>(va.size());
-  B.nvswap = static_cast<int>(vs.size());
-  B.nvrot = static_cast<int>(vr.size());
-  B.ncanon = static_cast<long long>(cp.size());
-  ensure(B.home, B.canon, std::max<size_t>(1, cp.size()) * sizeof(int));
-  if (!cp.empty())
-    CU(cudaMemcpyAsync(B.canon.p, cp.data(), cp.size() * sizeof(int), cudaMemcpyHostToDevice, B.home->st));
-  CU(cudaStreamSynchronize(B.home->st));
-}
-
-// sectors of ordered pairs (p, q) by q_p + q_q (diff = false) or q_p - q_q;
-// the summed index of a sector runs over the first (sum) or second (diff)
-// letters of its pairs
-void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unordered = false) {
-  const int n = B.N, tile = sector_tile();
+// Pairs (p, q) of orbitals grouped by the charge q_p + q_q (diff = false) or
+// q_p - q_q, in order of first appearance over p-major (p, q); within a
+// sector the pairs are p-ascending and no two share p (nor q), since the
+// orbitals' charges are distinct.
+std::vector<std::vector<int2>> pair_sectors(const ftcc_ctx* c, int n, bool diff, bool unordered,
+                                            std::vector<int>* sector_of = nullptr) {
   std::unordered_map<uint64_t, int> sid;
   std::vector<std::vector<int2>> rows;
+  if (sector_of) sector_of->assign(static_cast<size_t>(n) * n, -1);
   for (int p = 0; p < n; ++p)
     for (int q = unordered ? p + 1 : 0; q < n; ++q) {
       std::array<int, 4> ch;
@@ -1554,7 +1510,105 @@ void build_sectors(Batch& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unord
         rows.emplace_back();
       }
       rows[it->second].push_back(make_int2(p, q));
+      if (sector_of) (*sector_of)[static_cast<size_t>(p) * n + q] = it->second;
     }
+  return rows;
+}
+
+// imp[a][b][c] = the orbital d with q_d = q_a + q_b - q_c, or -1: (c, d) is
+// then a pair of the sum sector of (a, b), so the table and every list of
+// valid positions are read off the sectors without visiting a hole.
+void build_implied(SpTables& B, const ftcc_ctx* c) {
+  const int n = B.n;
+  std::unordered_map<uint64_t, int> orb;
+  for (int p = 0; p < n; ++p) orb[charge_key(canon_charge(c->charge[p], c->charge_mod))] = p;
+  if (static_cast<int>(orb.size()) != n) throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: two orbitals share a charge"};
+  std::vector<int> ssec, dsec;
+  const std::vector<std::vector<int2>> srows = pair_sectors(c, n, false, false, &ssec);
+  const std::vector<std::vector<int2>> drows = pair_sectors(c, n, true, false, &dsec);
+  // second letters of every difference sector, ascending
+  std::vector<std::vector<int>> dsecond(drows.size());
+  for (size_t s = 0; s < drows.size(); ++s) {
+    for (const int2& e : drows[s]) dsecond[s].push_back(e.y);
+    std::sort(dsecond[s].begin(), dsecond[s].end());
+  }
+  const long long n3 = static_cast<long long>(n) * n * n;
+  std::vector<int16_t> t(n3, -1);
+  // valid positions (p0, p1, p2) ascending: p2 runs over the first letters of
+  // the sum sector of (p0, p1), which are ascending
+  std::vector<int> va, vs, vr, cp;
+  std::vector<int> o1(n + 1, 0), o2(n + 1, 0);
+  va.reserve(n3 / 4);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      const int base = (a * n + b) * n;
+      int16_t* row = t.data() + base;
+      const std::vector<int2>& sec = srows[ssec[static_cast<size_t>(a) * n + b]];
+      o2[a + 1] += static_cast<int>(sec.size());
+      for (const int2& e : sec) {
+        row[e.x] = static_cast<int16_t>(e.y);
+        va.push_back(base + e.x);
+        ++o1[e.x + 1];
+        // canonical positions of the antisymmetric doubles: a < b, p2 < implied
+        if (a < b && e.x < e.y) cp.push_back(base + e.x);
+      }
+    }
+  // (p0, p2, p1) valid: q_p0 - q_p1 = q_d - q_p2, p2 a second letter of the
+  // difference sector of (p0, p1); (p1, p2, p0) valid: p2 a second letter of
+  // the difference sector of (p1, p0)
+  vs.reserve(va.size());
+  vr.reserve(va.size());
+  for (int p0 = 0; p0 < n; ++p0)
+    for (int p1 = 0; p1 < n; ++p1) {
+      const int base = (p0 * n + p1) * n;
+      for (int p2 : dsecond[dsec[static_cast<size_t>(p0) * n + p1]]) vs.push_back(base + p2);
+      for (int p2 : dsecond[dsec[static_cast<size_t>(p1) * n + p0]]) vr.push_back(base + p2);
+    }
+  // per orbital p, the valid positions (m, q, p) and (p, m, q) as m n + q,
+  // ascending: (p, m, q) is a slice of the valid list, (m, q, p) a stable
+  // bucketing of it by its last letter
+  std::vector<int> l1(va.size()), l2(va.size());
+  for (int p = 0; p < n; ++p) {
+    o1[p + 1] += o1[p];
+    o2[p + 1] += o2[p];
+  }
+  {
+    std::vector<int> pos(o1.begin(), o1.end() - 1);
+    size_t k = 0;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b)
+        for (const int2& e : srows[ssec[static_cast<size_t>(a) * n + b]]) {
+          l1[pos[e.x]++] = a * n + b;
+          l2[k++] = b * n + e.x;
+        }
+  }
+  auto upload = [&](Buf& b, const std::vector<int>& v) {
+    ensure(B.home, b, std::max<size_t>(1, v.size()) * sizeof(int));
+    if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, B.home->st));
+  };
+  ensure(B.home, B.imp, n3 * sizeof(int16_t));
+  CU(cudaMemcpyAsync(B.imp.p, t.data(), n3 * sizeof(int16_t), cudaMemcpyHostToDevice, B.home->st));
+  upload(B.vl1, l1);
+  upload(B.voff1, o1);
+  upload(B.vl2, l2);
+  upload(B.voff2, o2);
+  upload(B.vall, va);
+  upload(B.vswap, vs);
+  upload(B.vrot, vr);
+  upload(B.canon, cp);
+  B.nvall = static_cast<int>(va.size());
+  B.nvswap = static_cast<int>(vs.size());
+  B.nvrot = static_cast<int>(vr.size());
+  B.ncanon = static_cast<long long>(cp.size());
+  CU(cudaStreamSynchronize(B.home->st));
+}
+
+// sectors of ordered pairs (p, q) by q_p + q_q (diff = false) or q_p - q_q;
+// the summed index of a sector runs over the first (sum) or second (diff)
+// letters of its pairs
+void build_sectors(SpTables& B, const ftcc_ctx* c, bool diff, SecTab& T, bool unordered = false) {
+  const int n = B.n, tile = sector_tile();
+  const std::vector<std::vector<int2>> rows = pair_sectors(c, n, diff, unordered);
   std::vector<int2> ent;
   std::vector<int> kl;
   std::vector<int4> sec, work, work_small;
@@ -2143,10 +2197,19 @@ std::shared_ptr<Batch> prepare_batch(ftcc_ctx* const* cs, int n, const double* b
     if (static_cast<long long>(N) * N * N >= (1LL << 31))
       throw Fail{FTCC_ERR_INVALID_ARG, "block_sparse: N^3 positions must fit 32-bit indices (N <= 1290)"};
     B->sparse = true;
-    build_implied(*B, home);
-    build_sectors(*B, home, false, B->ssum);
-    build_sectors(*B, home, true, B->sdiff);
-    build_sectors(*B, home, false, B->ssum_u, true);
+    if (!home->sptab || home->sptab->n != N) {
+      home->sptab.reset();
+      auto T = std::make_shared<SpTables>();
+      T->home = home;
+      T->n = N;
+      build_implied(*T, home);
+      build_sectors(*T, home, false, T->ssum);
+      build_sectors(*T, home, true, T->sdiff);
+      build_sectors(*T, home, false, T->ssum_u, true);
+      home->sptab = T;
+    }
+    B->sp_owner = home->sptab;
+    static_cast<SpTableView&>(*B) = *home->sptab;
   }
   ensure(home, B->idxO, B->O.size() * sizeof(int));
   ensure(home, B->idxV, B->V.size() * sizeof(int));
@@ -3005,6 +3068,7 @@ ftcc_status build_integrals(ftcc_ctx* c, const ftcc_system* s) {
     c->put(c->eri);
     c->put(c->eps);
     c->N = 0;
+    c->sptab.reset();
     ensure(c, c->h, static_cast<size_t>(N) * N * sizeof(double));
     ensure(c, c->eri, N4 * sizeof(double));
     ensure(c, c->eps, static_cast<size_t>(N) * sizeof(double));
