@@ -386,8 +386,10 @@ ftcc_status ftcc_get_amplitudes(ftcc_ctx* ctx, double* s1, double* s2);
 /* Evaluate the S kernel (Eqs. ccS1, ccS2) of the prepared problem for nx
  * caller amplitude slices.  t1_dev[nx*o*v], t2_dev[nx*o*o*v*v] are FP64
  * device inputs; s1_dev, s2_dev FP64 device outputs of the same shapes.
- * `precision` selects the arithmetic (FP64, TF32 or BF16X3).  Requires
- * ftcc_prepare.  Used to check the contraction schedule element by element. */
+ * `precision` selects the arithmetic (FP64, TF32 or BF16X3; with
+ * block_sparse, TF32 and BF16X3 both run the FP32 block-sparse kernels of the
+ * mixed sweep on the inputs rounded to FP32).  Requires ftcc_prepare.  Used to
+ * check the contraction schedule element by element. */
 ftcc_status ftcc_eval_s(ftcc_ctx* ctx, int nx, int precision, const double* t1_dev,
                         const double* t2_dev, double* s1_dev, double* s2_dev);
 

@@ -3522,17 +3522,35 @@ ftcc_status ftcc_eval_s(ftcc_ctx* c, int nx, int precision, const double* t1_dev
       // dense in and out: the inputs are projected onto the charge-conserving
       // elements (s1 diagonal, s2 with q_i + q_j = q_a + q_b), the outputs
       // expanded with zeros elsewhere
-      if (precision != FTCC_PREC_FP64) return fail(c, FTCC_ERR_INVALID_ARG, "block_sparse: FP64 only");
-      Solver<double>& s = make_solver<double>(B, GEMM_F64);
-      if (nx > s.nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
+      // (TF32 / BF16X3: the FP32 block-sparse kernels of the mixed sweep, on
+      // the rounded inputs, the outputs widened)
+      const int nxc = precision == FTCC_PREC_FP64 ? make_solver<double>(B, GEMM_F64).nxc
+                                                  : make_solver<float>(B, GEMM_BF16X3).nxc;
+      if (nx > nxc) return fail(c, FTCC_ERR_INVALID_ARG, "nx exceeds the tau chunk");
       const long long N = B.N, n3 = N * N * N;
       Buf a = c->get(nx * N * 8), b = c->get(nx * n3 * 8), d = c->get(nx * N * 8), e = c->get(nx * n3 * 8);
       if (!a.p || !b.p || !d.p || !e.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
       const int16_t* imp = static_cast<const int16_t*>(B.imp.p);
       CU(cudaMemsetAsync(e.p, 0, nx * n3 * 8, c->st));   // the i = j / a = b elements of S2 are never written
       CU(launch_sp_compress(t1_dev, t2_dev, imp, B.N, nx, static_cast<double*>(a.p), static_cast<double*>(b.p), c->st));
-      s.s_kernel(static_cast<double*>(a.p), static_cast<double*>(b.p), static_cast<double*>(d.p),
-                 static_cast<double*>(e.p), nx);
+      if (precision == FTCC_PREC_FP64) {
+        Solver<double>& s = make_solver<double>(B, GEMM_F64);
+        s.s_kernel(static_cast<double*>(a.p), static_cast<double*>(b.p), static_cast<double*>(d.p),
+                   static_cast<double*>(e.p), nx);
+      } else {
+        Solver<float>& s = make_solver<float>(B, GEMM_BF16X3);
+        Buf fa = c->get(nx * N * 4), fb = c->get(nx * n3 * 4), fd = c->get(nx * N * 4), fe = c->get(nx * n3 * 4);
+        if (!fa.p || !fb.p || !fd.p || !fe.p) throw Fail{FTCC_ERR_OOM, "allocation failed"};
+        CU(cudaMemsetAsync(fe.p, 0, nx * n3 * 4, c->st));
+        CU(launch_convert<double, float>(static_cast<double*>(a.p), static_cast<float*>(fa.p), nx * N, c->st));
+        CU(launch_convert<double, float>(static_cast<double*>(b.p), static_cast<float*>(fb.p), nx * n3, c->st));
+        s.s_kernel(static_cast<float*>(fa.p), static_cast<float*>(fb.p), static_cast<float*>(fd.p),
+                   static_cast<float*>(fe.p), nx);
+        CU(launch_convert<float, double>(static_cast<float*>(fd.p), static_cast<double*>(d.p), nx * N, c->st));
+        CU(launch_convert<float, double>(static_cast<float*>(fe.p), static_cast<double*>(e.p), nx * n3, c->st));
+        sync(c);
+        for (Buf* q : {&fa, &fb, &fd, &fe}) c->put(*q);
+      }
       CU(launch_sp_expand(static_cast<double*>(d.p), static_cast<double*>(e.p), imp, B.N, nx, s1_dev, s2_dev, c->st));
       sync(c);
       for (Buf* q : {&a, &b, &d, &e}) c->put(*q);

@@ -186,35 +186,42 @@ __global__ void sp_vec_kernel(SpVec<T> a) {
     cs1 += s2[pos3(n, p, m, p)] * Fme[m] - s1[m] * a.Vovov[pos3(n, m, p, p)];
   }
   // only the positions whose implied index exists (the others hold zeros):
-  // (m, q, p) from the list l1 of p, (p, m, q) from l2
+  // (m, q, p) from the list l1 of p, (p, m, q) from l2.  The doubles terms
+  // carry a factor 1/2, applied once to their sums (hae, hmi, hs1): FP64
+  // issues at a few operations per clock per SM on this part, and the scale
+  // per term was a third of these loops' FP64 instructions
+  T hae = T(0.0), hmi = T(0.0), hs1 = T(0.0);
   for (int k = a.off1[p] + threadIdx.x; k < a.off1[p + 1]; k += blockDim.x) {
     const int mq = a.l1[k];
     const int m = mq / n, q = mq - m * n;
     const long long o1 = pos3(n, m, q, p);
     const T t_mqp = s2[o1];
-    cae -= T(0.5) * t_mqp * a.Voovv[o1];
+    hae += t_mqp * a.Voovv[o1];
     const int e = impl(a.imp, n, m, q, p);   // q_e = q_m + q_q - q_p
-    cs1 -= T(0.5) * t_mqp * a.Voovo[pos3(n, q, m, e)];
+    hs1 += t_mqp * a.Voovo[pos3(n, q, m, e)];
   }
   for (int k = a.off2[p] + threadIdx.x; k < a.off2[p + 1]; k += blockDim.x) {
     const int mq = a.l2[k];
     const int m = mq / n, q = mq - m * n;
     const long long o2 = pos3(n, p, m, q);
     const T t = s2[o2];
-    cmi += T(0.5) * t * a.Voovv[o2];
-    cs1 -= T(0.5) * t * a.Vovvv[pos3(n, m, p, q)];
+    hmi += t * a.Voovv[o2];
+    hs1 += t * a.Vovvv[pos3(n, m, p, q)];
   }
   cae = block_sum(cae, red);
   cmi = block_sum(cmi, red);
   cs1 = block_sum(cs1, red);
+  hae = block_sum(hae, red);
+  hmi = block_sum(hmi, red);
+  hs1 = block_sum(hs1, red);
   if (threadIdx.x == 0) {
     const long long o = static_cast<long long>(x) * n + p;
     const T s = s1[p], fm = Fme[p];
-    const T fae = a.fvv[p] - T(0.5) * s * fm + cae;
-    const T fmi = a.foo[p] + T(0.5) * s * fm + cmi;
+    const T fae = a.fvv[p] - T(0.5) * s * fm + (cae - T(0.5) * hae);
+    const T fmi = a.foo[p] + T(0.5) * s * fm + (cmi + T(0.5) * hmi);
     a.Fae[o] = fae;
     a.Fmi[o] = fmi;
-    a.S1[o] = a.fvo[p] + s * (fae - fmi) + cs1;
+    a.S1[o] = a.fvo[p] + s * (fae - fmi) + (cs1 - T(0.5) * hs1);
     a.Ft[o] = fae - T(0.5) * s * fm;
     a.Ft2[o] = fmi + T(0.5) * s * fm;
   }
@@ -306,13 +313,12 @@ __global__ void sp_rinit_kernel(SpR<T> a) {
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = impl(a.imp, n, i, j, aa);
-    T v = T(0.0);
-    {
-      const long long c = pos3(n, aa, b, i);   // (a, b, i), j implied
-      v = T(0.5) * s2[e] * Ft[b] + T(0.5) * Ft2[i] * s2[pos3(n, j, i, aa)] + T(0.5) * s1[i] * a.Vvvvo[c] -
-          T(0.5) * s1[aa] * a.Vovoo[c] + s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)];
-    }
-    a.R[x * n3 + e] = v;
+    const long long cb = pos3(n, aa, b, i);  // (a, b, i), j implied
+    T h = s2[e] * Ft[b];                       // the four halved terms, scaled once
+    h = fma(Ft2[i], s2[pos3(n, j, i, aa)], h);
+    h = fma(s1[i], a.Vvvvo[cb], h);
+    h = fma(-s1[aa], a.Vovoo[cb], h);
+    a.R[x * n3 + e] = fma(T(0.5), h, s1[i] * s1[b] * a.Vovvo[pos3(n, b, aa, i)]);
   }
 }
 
@@ -369,16 +375,14 @@ __global__ void sp_canon_kernel(SpCanon<T> a) {
     const long long o = x * n3 + e;
     {
       T v = s2[e];
-      const T pr = s1[p0] * s1[p1];
-      if (p2 == p0) v += pr;
-      if (p2 == p1) v -= pr;
+      if (p2 == p0) v += s1[p0] * s1[p1];   // (the products only where they enter:
+      if (p2 == p1) v -= s1[p0] * s1[p1];   // every FP64 instruction counts here)
       a.ta[o] = v;
     }
     {
       T v = s2[pos3(n, p2, q, p0)];
-      const T pr = s1[p2] * s1[q];
-      if (p0 == p2) v += pr;
-      if (p0 == q) v -= pr;
+      if (p0 == p2) v += s1[p2] * s1[q];
+      if (p0 == q) v -= s1[p2] * s1[q];
       a.tp[o] = v;
     }
     a.w1[o] = a.Voooo[pos3(n, p2, q, p0)] - s1[p0] * a.Vooov[pos3(n, p2, q, p1)] +
@@ -461,6 +465,121 @@ __global__ void __launch_bounds__(THREADS) sector_gemm_kernel(SecGemmArgsT<T> g)
       if (g.anti4) {
         // (i, j) = pr, (a, b) = pc: the four orientations of the antisymmetric result
         T* C = g.C + x * g.cx;
+        const long long ni = pr.x, nj = pr.y;
+        C[(ni * n + nj) * n + pc.x] += v;
+        C[(nj * n + ni) * n + pc.x] -= v;
+        C[(ni * n + nj) * n + pc.y] -= v;
+        C[(nj * n + ni) * n + pc.y] += v;
+      } else {
+        const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
+                            static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
+        g.C[q] += v;
+      }
+    }
+  }
+}
+
+// FP32 form of the same products.  The FP32 pipe issues 64 times the FP64
+// rate, so the flattened kernel above is bound there by its staging (index
+// arithmetic per element, and global-load latency between two barriers).
+// This one
+//  * gives each thread a 4 x 4 block of the TILE x TILE tile (rows 4 ty ..
+//    4 ty + 3, columns 4 tx .. 4 tx + 3): one float4 of each operand per k
+//    feeds 16 FMAs;
+//  * keeps the row offsets of the tile in shared memory and gives every
+//    staging thread one fixed k of a chunk, so an element costs an address
+//    add and an asynchronous copy (cp.async, 4 bytes);
+//  * stages chunk c + 1 while chunk c is multiplied (two buffers).
+// A warp stages 8 consecutive k of 4 rows at a time: its four row segments
+// are contiguous stretches of a row's K list, and its shared stores fall in
+// 32 distinct banks (row pitch TILE + 4 words).  Outputs past the sector's
+// edge are computed from whatever the unstaged rows hold and never written.
+// Every output sums its k terms in the order of the flattened kernel (fma
+// into one accumulator, chunk after chunk, the second product after the
+// first).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int TILE>
+__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) sector_gemm_f32_kernel(SecGemmArgsT<float> g) {
+  constexpr int TD = TILE / 4, THREADS = TD * TD, LD = TILE + 4;
+  static_assert(THREADS >= 4 * 32 && kSecKc == 32, "four staging warps cover a 32-wide K chunk");
+  __shared__ __align__(16) float As[2][kSecKc][LD];
+  __shared__ __align__(16) float Bs[2][kSecKc][LD];
+  __shared__ int rowA[TILE], rowB[TILE];
+  const int4 w = g.work[blockIdx.x];
+  const int4 sec = g.sec[w.x];   // entry offset, rows, K offset, K count
+  const long long x = blockIdx.y;
+  const int n = g.n;
+  const int nr = min(TILE, sec.y - w.y), nc = min(TILE, sec.y - w.z);
+  for (int r = threadIdx.x; r < nr; r += THREADS) {
+    const int2 pr = g.ent[sec.x + w.y + r];
+    rowA[r] = (pr.x * n + pr.y) * n;
+  }
+  for (int c = threadIdx.x; c < nc; c += THREADS) {
+    const int2 pr = g.ent[sec.x + w.z + c];
+    rowB[c] = (g.swapB ? pr.y * n + pr.x : pr.x * n + pr.y) * n;
+  }
+  __syncthreads();
+  const int nch = (sec.w + kSecKc - 1) / kSecKc;
+  const int nchunk = nch * (g.A2 ? 2 : 1);
+  const int lane = threadIdx.x & 31;
+  const int sk = (lane >> 2) + 8 * (threadIdx.x >> 5), sr = lane & 3;   // staging: k of the chunk, first row
+  auto stage = [&](int ci, int buf) {
+    if (threadIdx.x >= 128) return;
+    const int prod = ci >= nch ? 1 : 0;
+    const int k0 = (ci - prod * nch) * kSecKc;
+    if (sk >= sec.w - k0) return;
+    const float* A = (prod ? g.A2 : g.A) + x * g.ax;
+    const float* B = (prod ? g.B2 : g.B) + x * g.bx;
+    const int col = g.kl[sec.z + k0 + sk];
+    for (int r = sr; r < nr; r += 4) cp_async4(&As[buf][sk][r], A + rowA[r] + col);
+    for (int c = sr; c < nc; c += 4) cp_async4(&Bs[buf][sk][c], B + rowB[c] + col);
+  };
+  const int tx = threadIdx.x % TD, ty = threadIdx.x / TD;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  stage(0, 0);
+  cp_async_commit();
+  for (int ci = 0; ci < nchunk; ++ci) {
+    if (ci + 1 < nchunk) stage(ci + 1, (ci + 1) & 1);
+    cp_async_commit();
+    cp_async_wait1();   // every group but the newest: chunk ci has landed
+    __syncthreads();
+    const int prod = ci >= nch ? 1 : 0;
+    const int kc = min(kSecKc, sec.w - (ci - prod * nch) * kSecKc);
+    const int buf = ci & 1;
+    for (int k = 0; k < kc; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[buf][k][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][k][4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();   // buffer ci & 1 is restaged for chunk ci + 2
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * ty + i;
+    if (r >= nr) continue;
+    const int2 pr = g.ent[sec.x + w.y + r];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * tx + j;
+      if (c >= nc) continue;
+      const int2 pc = g.ent[sec.x + w.z + c];
+      const float v = g.alpha * acc[i][j];
+      if (g.anti4) {
+        float* C = g.C + x * g.cx;
         const long long ni = pr.x, nj = pr.y;
         C[(ni * n + nj) * n + pc.x] += v;
         C[(nj * n + ni) * n + pc.x] -= v;
@@ -1071,7 +1190,10 @@ template <class T>
 cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st) {
   if (nwork <= 0 || nx <= 0) return cudaSuccess;
   if (nx > 65535) return cudaErrorInvalidValue;
-  sector_gemm_kernel<T, kSecT, kSecThreads><<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
+  if constexpr (sizeof(T) == 4)
+    sector_gemm_f32_kernel<kSecT><<<dim3(nwork, nx), (kSecT / 4) * (kSecT / 4), 0, st>>>(g);
+  else
+    sector_gemm_kernel<T, kSecT, kSecThreads><<<dim3(nwork, nx), kSecThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,40 @@ def test_sparse_s_kernel_matches_oracle_terms(ctx, n_elec, n_pw):
     assert e2 < 1e-12 * max(1.0, torch.max(torch.abs(r2)).item()), e2
 
 
+@pytest.mark.parametrize("n_elec,n_pw,against", [(6, 7, "oracle"), (14, 19, "oracle"), (14, 33, "fp64")])
+def test_sparse_s_kernel_fp32_elementwise(ctx, n_elec, n_pw, against):
+    """The FP32 block-sparse S kernel of the mixed sweep (register-tiled
+    sector products, FP32 reductions) element by element: against the
+    oracle's printed terms on the 7- and 19-plane-wave gases, and against
+    the FP64 block-sparse kernel on the 33-plane-wave gas, whose sectors of
+    up to 66 pairs span two 48-wide tiles and two K chunks with a ragged
+    tail.  Bound: 2e-6 of max |S| (FP32 rounding of sums over at most N^2
+    terms of the rounded inputs)."""
+    rs, beta, ng = 1.0, 1.5, 4
+    sysc = bs.ueg(n_elec, rs, n_pw)
+    t1c, t2c = bs.random_amplitudes(sysc["charges"], 17, 2, 0.05)
+    d1, d2 = bs.dense_amplitudes(sysc["charges"], t1c, t2c)
+    ctx.build_ueg(n_elec, rs, n_pw)
+    mu = ctx.reference_mu(beta, float(n_elec))
+    ctx.prepare(beta, mu, ng, precision="bf16x3", block_sparse=1)
+    s1, s2 = ctx.eval_s(d1, d2, precision="bf16x3")
+    if against == "oracle":
+        prob = fc.Problem(systems.ueg(n_elec, rs, n_pw), beta, mu, ng, 0.0)
+        r1, r2 = fc.S1(prob, d1, d2), fc.S2(prob, d1, d2)
+    else:
+        ctx.prepare(beta, mu, ng, precision="fp64", block_sparse=1)
+        r1, r2 = ctx.eval_s(d1, d2)
+        r1, r2 = r1.cpu(), r2.cpu()
+    m1, m2 = torch.max(torch.abs(r1)).item(), torch.max(torch.abs(r2)).item()
+    assert m2 > 1e-3
+    e1 = torch.max(torch.abs(s1.cpu() - r1)).item()
+    e2 = torch.max(torch.abs(s2.cpu() - r2)).item()
+    assert e1 < 2e-6 * max(m1, m2), (e1, m1)
+    assert e2 < 2e-6 * m2, (e2, m2)
+    # and not exact: the FP32 path really ran
+    assert e2 > 0.0
+
+
 def test_sparse_s_kernel_matches_dense_gpu(ctx):
     """The same S evaluation through the dense FP64 engine: identical up to
     rounding order."""
@@ -141,8 +175,8 @@ def test_sparse_argument_checks(ctx):
     from paper_2004_01729_gb300 import ftcc
     ctx.build_ueg(6, 1.0, 7)
     ctx.prepare(1.0, 0.5, 4, precision="tf32", block_sparse=1)
-    with pytest.raises(ftcc.FTCCError) as e:          # the dense-layout S evaluation is FP64 only
-        ctx.eval_s(torch.zeros((1, 14, 14), dtype=torch.float64), torch.zeros((1, 14, 14, 14, 14), dtype=torch.float64),
+    with pytest.raises(ftcc.FTCCError) as e:          # more slices than the grid holds
+        ctx.eval_s(torch.zeros((5, 14, 14), dtype=torch.float64), torch.zeros((5, 14, 14, 14, 14), dtype=torch.float64),
                    precision="tf32")
     assert e.value.status == ftcc.ERR_INVALID_ARG
     with pytest.raises(ftcc.FTCCError) as e:          # Simpson integral form only
