@@ -365,6 +365,16 @@ ftcc_status ftcc_prepare_batched(ftcc_ctx* const* ctx, int n, const double* beta
  * FTCC_ERR_NOT_CONVERGED when the lambda iteration does not converge. */
 ftcc_status ft_ccsd_adjoint(ftcc_ctx* ctx, ftcc_adjoint_result* out, double* rdm1);
 
+/* ft_ccsd_adjoint for n contexts at once (without the 1-RDM): the batches
+ * they belong to run their lambda sweeps and responses concurrently, each on
+ * its home context's stream from its own host thread (at most as many threads
+ * as host cores), the members of one batch one after another.  out[n] and
+ * status[n] are caller-owned host arrays; status[i] is what ft_ccsd_adjoint
+ * would return for ctx[i].  Returns FTCC_OK when every status is FTCC_OK,
+ * else the first failing status in context order; FTCC_ERR_INVALID_ARG for
+ * NULL arrays, a NULL context or n < 1 (nothing is run then). */
+ftcc_status ft_ccsd_adjoint_batched(ftcc_ctx* const* ctx, int n, ftcc_adjoint_result* out, ftcc_status* status);
+
 /* Unrelaxed normal-ordered two-particle density Gamma_N of the converged
  * solve (App. B), read as the derivative of the CC Lagrangian with respect
  * to the antisymmetrised integrals <pq||rs> that enter the CC equations and

@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded (about two seconds of clock64); on expiry the
 // thread records an error code in *err and leaves its loop, so the block
 // always reaches the TMEM release and exits.
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -473,17 +474,17 @@ __global__ void tc_splitk_reduce(const float* __restrict__ W, float* __restrict_
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 bool get_encode() {
-  if (g_encode) return true;
+  if (g_encode.load()) return true;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
           cudaSuccess ||
       q != cudaDriverEntryPointSuccess || fn == nullptr)
     return false;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));   // (idempotent under a race)
   return true;
 }
 
@@ -498,7 +499,7 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, long long K, long lon
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld * es), static_cast<cuuint64_t>(bs * es)};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / es), static_cast<cuuint32_t>(box_rows), 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
-  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+  CUresult r = g_encode.load()(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                         const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -517,7 +518,7 @@ bool make_cmap(CUtensorMap* m, void* C, int M, int N, long long ldc, long long s
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldc * 4), static_cast<cuuint64_t>(((bs * 4 + 15) / 16) * 16)};
   cuuint32_t box[3] = {32u, 32u, 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
-  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  return g_encode.load()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -536,18 +537,22 @@ cudaError_t launch_tc(const GemmArgs& g, int* dev_err, cudaStream_t st) {
     mB2 = mB;
   }
   constexpr int smem = TcCfg<KIND, BN>::kSmem;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // (set once per instantiation; host threads driving distinct contexts may
+  // race here, and both the attribute call and the SM count are idempotent)
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load()) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true);
   }
-  static int sms = 0;
+  static std::atomic<int> sms_cached{0};
+  int sms = sms_cached.load();
   if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 148;
+    sms_cached.store(sms);
   }
   const long long tiles = static_cast<long long>((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * g.batch;
   const int nk = (g.K + TcCfg<KIND, BN>::kKElems - 1) / TcCfg<KIND, BN>::kKElems;

@@ -1,6 +1,7 @@
 // Memory-bound kernels of the FT-CCSD sweep: operand packing, the
 // antisymmetrising scatter, tau builds, the model Hamiltonians, the
 // reference / Fermi scaling, and the propagator with the fused energy.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
@@ -1833,13 +1834,13 @@ cudaError_t launch_antisym4(T* dst, const Anti4Desc& d, cudaStream_t st) {
   if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
   const size_t smem = static_cast<size_t>(d.nsrc * 4 + 1) * dd.ta * (dd.ta + 1) * sizeof(T);
   const int kp = (dd.ta * dd.ta + 255) / 256;   // element slots per thread, 1..4
-  static bool attr[5] = {false, false, false, false, false};   // per instantiation (this T)
+  static std::atomic<bool> attr[5] = {{false}, {false}, {false}, {false}, {false}};   // per instantiation (this T)
   auto launch = [&](auto kern) -> cudaError_t {
-    if (smem > 48 * 1024 && !attr[kp]) {   // the largest tile set of this instantiation
+    if (smem > 48 * 1024 && !attr[kp].load()) {   // the largest tile set of this instantiation
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(9 * kAT * (kAT + 1) * sizeof(T)));
       if (e != cudaSuccess) return e;
-      attr[kp] = true;
+      attr[kp].store(true);
     }
     kern<<<static_cast<unsigned>(blocks), 256, smem, st>>>(dst, dd);
     return cudaGetLastError();

@@ -7,6 +7,9 @@
 // an instance index z in front, so one launch of each contraction serves the
 // whole batch and one CUDA graph replays an iteration of all instances.
 #include <algorithm>
+#include <system_error>
+#include <atomic>
+#include <thread>
 #include <array>
 #include <tuple>
 #include <cmath>
@@ -79,6 +82,10 @@ struct ftcc_ctx {
   // positions, pair sectors), built by the first block-sparse prepare and
   // kept until the system is rebuilt
   std::shared_ptr<ftcc::SpTables> sptab;
+  // pinned host copy of the per-instance convergence state of the batch
+  // this context is home to (written by each iteration's graph tail)
+  double* pin_state = nullptr;
+  size_t pin_state_n = 0;
 
   ftcc::Buf get(size_t bytes) {
     ftcc::Buf b;
@@ -2410,31 +2417,51 @@ struct SolveDriver {
   bool conv = false, finished = false, refining = false;
   int it = 0, r = 0;
   ftcc_status status = FTCC_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  double* pin = nullptr;   // the home context's pinned state copy (nullptr: read back after the wait)
 
-  explicit SolveDriver(Batch& b) : B(b), o(b.opt), h(b.home), best(b.nz, 1e300), stall(b.nz, 0) {
+  SolveDriver(Batch& b, bool pinned) : B(b), o(b.opt), h(b.home), best(b.nz, 1e300), stall(b.nz, 0) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
+    CU(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    const size_t need = static_cast<size_t>(B.nz) * kStateStride;
+    if (pinned) {
+      if (h->pin_state_n < need) {
+        if (h->pin_state) CU(cudaFreeHost(h->pin_state));
+        h->pin_state = nullptr;
+        h->pin_state_n = 0;
+        CU(cudaMallocHost(&h->pin_state, need * sizeof(double)));
+        h->pin_state_n = need;
+      }
+      pin = h->pin_state;
+    }
     if (o.max_iter <= 0) end();
   }
   ~SolveDriver() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
   }
-  // enqueue one iteration on the batch's stream (no host wait)
+  // enqueue one iteration on the batch's stream, and the copy of its state
+  // to pinned host memory behind it (no host wait)
   void launch() {
     CU(cudaEventRecord(e0, h->st));
     run_batch(B, 1);
     CU(cudaEventRecord(e1, h->st));
+    if (pin)
+      CU(cudaMemcpyAsync(pin, B.state.p, static_cast<size_t>(B.nz) * kStateStride * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->st));
+    CU(cudaEventRecord(e2, h->st));
   }
   // wait for it, then the convergence and phase logic
   void collect() {
-    CU(cudaEventSynchronize(e1));
+    CU(cudaEventSynchronize(e2));
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     B.ms_total += ms;
     B.ms_count += 1;
-    s = read_states(B);
+    if (pin) s.assign(pin, pin + static_cast<size_t>(B.nz) * kStateStride);
+    else s = read_states(B);
     step();
   }
   bool all_done(double tol_o, double tol_a) {
@@ -2569,7 +2596,7 @@ struct SolveDriver {
 
 ftcc_status solve_batch(Batch& B) {
   if (B.quad != FTCC_QUAD_SIMPSON) return rk_solve(B);
-  SolveDriver d(B);
+  SolveDriver d(B, true);
   while (!d.finished) {
     d.launch();
     d.collect();
@@ -2577,8 +2604,8 @@ ftcc_status solve_batch(Batch& B) {
   return d.status;
 }
 
-// The batches of one batched solve advanced together: each iteration is
-// launched on every unfinished batch's stream before any is waited for.
+// The batches of one batched solve advanced together, each with one
+// iteration in flight on its own stream.
 std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
   std::vector<ftcc_status> st(Bs.size(), FTCC_OK);
   std::vector<std::unique_ptr<SolveDriver>> ds;
@@ -2588,18 +2615,26 @@ std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
       ds.emplace_back(nullptr);
       continue;
     }
-    ds.emplace_back(new SolveDriver(*Bs[k]));
+    // the pinned state copy lives on the home context: two batches with one
+    // home (never made by the batching, but possible) read back unpinned
+    bool shared = false;
+    for (size_t q = 0; q < k; ++q) shared = shared || Bs[q]->home == Bs[k]->home;
+    ds.emplace_back(new SolveDriver(*Bs[k], !shared));
   }
+  // every batch keeps one iteration in flight on its own stream: as soon as
+  // its last iteration is collected (and the phase logic has run), its next
+  // one is enqueued, so no batch waits for the slowest one of a round
+  for (auto& d : ds)
+    if (d && !d->finished) d->launch();
   for (;;) {
     bool any = false;
     for (auto& d : ds)
       if (d && !d->finished) {
-        d->launch();
         any = true;
+        d->collect();
+        if (!d->finished) d->launch();
       }
     if (!any) break;
-    for (auto& d : ds)
-      if (d && !d->finished) d->collect();
   }
   for (size_t k = 0; k < ds.size(); ++k)
     if (ds[k]) st[k] = ds[k]->status;
@@ -3014,6 +3049,8 @@ void ftcc_destroy(ftcc_ctx* c) {
     c->batch.reset();
   }
   c->batch.reset();
+  c->sptab.reset();
+  if (c->pin_state) cudaFreeHost(c->pin_state);
   c->put(c->h);
   c->put(c->eri);
   c->put(c->eps);
@@ -3404,6 +3441,46 @@ ftcc_status ft_ccsd_adjoint(ftcc_ctx* c, ftcc_adjoint_result* out, double* rdm1)
     check_device_error(B.home);
     return FTCC_OK;
   });
+}
+
+ftcc_status ft_ccsd_adjoint_batched(ftcc_ctx* const* ctx, int n, ftcc_adjoint_result* out, ftcc_status* status) {
+  if (!ctx || n < 1 || !out || !status) return FTCC_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctx[i]) return FTCC_ERR_INVALID_ARG;
+  // members of one batch share its response: one group per batch (a context
+  // without a batch is a group of its own and fails with FTCC_ERR_STATE)
+  std::vector<std::vector<int>> groups;
+  std::map<const Batch*, size_t> gid;
+  for (int i = 0; i < n; ++i) {
+    const Batch* b = ctx[i]->batch.get();
+    if (b) {
+      auto it = gid.find(b);
+      if (it != gid.end()) {
+        groups[it->second].push_back(i);
+        continue;
+      }
+      gid.emplace(b, groups.size());
+    }
+    groups.push_back({i});
+  }
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (size_t g; (g = next.fetch_add(1)) < groups.size();)
+      for (int i : groups[g]) status[i] = ft_ccsd_adjoint(ctx[i], &out[i], nullptr);
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(groups.size(), hw);
+  std::vector<std::thread> pool;
+  try {
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+  } catch (const std::system_error&) {
+    // fewer threads than asked for: the ones that started (and this one) take the rest
+  }
+  work();
+  for (std::thread& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (status[i] != FTCC_OK) return status[i];
+  return FTCC_OK;
 }
 
 ftcc_status ftcc_rdm2(ftcc_ctx* c, double* gamma) {

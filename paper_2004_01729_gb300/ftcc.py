@@ -94,6 +94,8 @@ _SIGS = [
     ("ftcc_prepare_batched", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
                                        C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(Options)]),
     ("ft_ccsd_adjoint", C.c_int, [C.c_void_p, C.POINTER(AdjointResult), C.c_void_p]),
+    ("ft_ccsd_adjoint_batched", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AdjointResult),
+                                          C.POINTER(C.c_int)]),
     ("ftcc_get_amplitudes", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ftcc_rdm2", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ftcc_eval_s", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -439,6 +441,28 @@ def solve_batched(ctxs, betas, mus, ngrid, quad=QUAD_SIMPSON, allow_unconverged=
     res = [r.as_dict() for r in out]
     for r in res:
         r["status"] = s
+    return res
+
+
+def adjoint_batched(ctxs):
+    """ft_ccsd_adjoint_batched: the adjoints of several contexts, their batches
+    concurrently; one (result dict, status) pair per context, no exception
+    for a failing member."""
+    lib = load()
+    n = len(ctxs)
+    hs = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    out = (AdjointResult * n)()
+    st = (C.c_int * n)()
+    for c in ctxs:
+        c.stream.wait_stream(c._torch.cuda.current_stream(c.device))
+    s = lib.ft_ccsd_adjoint_batched(hs, n, out, st)
+    if s == ERR_INVALID_ARG and all(v == 0 for v in st):
+        raise FTCCError(s, "ft_ccsd_adjoint_batched: invalid arguments")
+    res = []
+    for r, v in zip(out, st):
+        d = {k: getattr(r, k) for k, _ in r._fields_}
+        d["status"] = v
+        res.append(d)
     return res
 
 

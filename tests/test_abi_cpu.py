@@ -66,4 +66,10 @@ def test_null_arguments_are_rejected():
     assert L.build_integrals(None, None) == ftcc.ERR_INVALID_ARG
     assert L.ft_ccsd_iterate(None, 1, None) == ftcc.ERR_INVALID_ARG
     assert L.ft_ccsd_adjoint(None, None, None) == ftcc.ERR_INVALID_ARG
+    st = (ctypes.c_int * 2)()
+    out = (ftcc.AdjointResult * 2)()
+    assert L.ft_ccsd_adjoint_batched(None, 2, out, st) == ftcc.ERR_INVALID_ARG
+    hs = (ctypes.c_void_p * 2)(None, None)   # a NULL context: nothing runs
+    assert L.ft_ccsd_adjoint_batched(hs, 2, out, st) == ftcc.ERR_INVALID_ARG
+    assert L.ft_ccsd_adjoint_batched(hs, 0, out, st) == ftcc.ERR_INVALID_ARG
     L.ftcc_destroy(None)

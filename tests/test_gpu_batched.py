@@ -115,8 +115,9 @@ def test_hubbard_batch_64_instances_block_sparse():
     """The same 64 instances with the block-sparse storage (each instance its
     own batch on its own stream, all iterating in lockstep), FP64: the same
     63 converge, every converged Omega equals the single-instance dense FP64
-    solve to 1e-9 Ha, and the adjoint energies and entropies of all 63
-    equal the dense single-instance adjoint of one member per size class."""
+    solve to 1e-9 Ha, and the adjoint energies and entropies of all 63 (run
+    concurrently through ft_ccsd_adjoint_batched) equal the dense
+    single-instance adjoint of one member per size class."""
     from paper_2004_01729_gb300 import ftcc
     cfgs = wl.hubbard_batch()
     ng = cfgs[0]["ngrid"]
@@ -125,10 +126,12 @@ def test_hubbard_batch_64_instances_block_sparse():
                              block_sparse=1, max_iter=300, tol_omega=1e-12, tol_amp=1e-10, allow_unconverged=True)
     failed = [k for k, r in enumerate(res) if not r["converged"]]
     assert failed == [43], failed
-    adj = {}
-    for k, ctx in enumerate(ctxs):
-        if k != 43:
-            adj[k], _ = ctx.adjoint(with_rdm1=False)
+    # the 63 adjoints concurrently (ft_ccsd_adjoint_batched); the diverged
+    # member has no converged solve
+    adjs = ftcc.adjoint_batched(ctxs)
+    assert [k for k, a in enumerate(adjs) if a["status"] != ftcc.OK] == [43]
+    assert adjs[43]["status"] == ftcc.ERR_STATE
+    adj = {k: a for k, a in enumerate(adjs) if k != 43}
     seen = set()
     for k, (r, c) in enumerate(zip(res, cfgs)):
         if not r["converged"] or c["L"] in seen:
