@@ -310,8 +310,10 @@ def run_c3_iteration(args):
     ctx = ftcc.Context(0)
     ctx.build_ueg(C3["n_elec"], C3["rs"], C3["n_pw"])
     mu = ctx.reference_mu(C3["beta"], float(C3["n_elec"]))
-    if args.no_dense:   # the headline path: block-sparse FP64
+    if args.no_dense and args.sparse_precision == "fp64":   # the headline path: block-sparse FP64
         ctx.prepare(C3["beta"], mu, C3["ngrid"], **sparse_opts())
+    elif args.no_dense:   # the FP32 sweep of the mixed block-sparse path
+        ctx.prepare(C3["beta"], mu, C3["ngrid"], precision="bf16x3", block_sparse=1)
     else:
         ctx.prepare(C3["beta"], mu, C3["ngrid"], precision=args.precision, tau_chunk=8)
     ctx.iterate(args.warmup + args.steps)
@@ -1027,6 +1029,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32 block-sparse sweep")
     ap.add_argument("--c3-iterations", action="store_true",
                     help="prepare the headline workload and run W + K iterations (profiler launch lists)")
+    ap.add_argument("--sparse-precision", default="fp64", choices=["fp64", "bf16x3"],
+                    help="with --c3-iterations --no-dense: the block-sparse FP64 iteration or its FP32 sweep")
     ap.add_argument("--gemm", default=None, help="B,M,N,K: time the tensor-core GEMM alone on that shape")
     args = ap.parse_args()
     rank, world = dist_init(args)

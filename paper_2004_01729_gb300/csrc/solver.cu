@@ -319,6 +319,13 @@ struct Solver {
   std::map<const void*, T*> bar;            // forward buffer -> its adjoint
   std::map<const void*, Buf> fixed_bar;     // integral / Fock block -> adjoint (when wanted)
   bool want_fixed_bar = false;
+  // block-sparse transpose: the forward intermediates of the amplitudes at
+  // vjp_fwd_key (nx = vjp_fwd_nx slices) are still in their buffers.  Only
+  // the lambda sweep and the response set vjp_fwd_reuse (the amplitudes are
+  // fixed there); every forward S evaluation clears the key.
+  bool vjp_fwd_reuse = false;
+  const void* vjp_fwd_key = nullptr;
+  int vjp_fwd_nx = 0;
   Buf btt, bta, bX, bWmnij, bWabef, bWmbej, bY, bFae, bFmi, bFme, bFt, bFt2, bR, bR2, bD, bP, bQ, ones, sx1, sx2;
 
   Solver(Batch* batch, int kind) : b(batch), h_(batch->home), gk(kind) {}
@@ -971,6 +978,7 @@ struct Solver {
   // orientations (R enters S2 through P(ij)P(ab)); each product is an eighth
   // of its ordered form.  The transpose recomputes the ordered form.
   void sparse_s_kernel(const T* t1c, const T* t2c, T* S1c, T* S2c, int nxcur, bool pairs = true) {
+    vjp_fwd_key = nullptr;
     {
       nx = nxcur;
       const int n = no;
@@ -1088,7 +1096,16 @@ struct Solver {
   // pass gives Abar += alpha Cbar B and Bbar += alpha Cbar^T A.
   void sparse_vjp(const T* t1c, const T* t2c, const T* u1, const T* u2, T* t1bar, T* t2bar, int nxcur) {
     if constexpr (sizeof(T) == 8) {
-      sparse_s_kernel(t1c, t2c, t1bar, t2bar, nxcur, false);
+      // the forward intermediates (ordered ladders), recomputed unless the
+      // lambda sweep's fixed amplitudes already left them in place
+      nx = nxcur;
+      if (!(vjp_fwd_reuse && vjp_fwd_key == t2c && vjp_fwd_nx == nxcur)) {
+        sparse_s_kernel(t1c, t2c, t1bar, t2bar, nxcur, false);
+        if (vjp_fwd_reuse) {
+          vjp_fwd_key = t2c;
+          vjp_fwd_nx = nxcur;
+        }
+      }
       const int n = no;
       const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
       const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
@@ -2663,8 +2680,19 @@ void ensure_fp64_solution(Batch& B) {
 // Stationarity of the discrete Lagrangian (Eqs. Lagrangian, lmu, ltilde):
 // m = -dEcc/ds - (dS/ds)^T u,  u_x = sum_y G[y,x] exp(-Delta(tau_y - tau_x)) m_y,
 // with m_y = g_y lambda_y / beta; fixed-point iteration from m = 0.
+// The amplitudes are fixed while this lives: the block-sparse transpose may
+// keep its forward intermediates from one application to the next.
+template <class T>
+struct FixedAmplitudes {
+  Solver<T>& s;
+  explicit FixedAmplitudes(Solver<T>& s_) : s(s_) { s.vjp_fwd_reuse = true; }
+  ~FixedAmplitudes() { s.vjp_fwd_reuse = false; }
+};
+
 template <class T>
 int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
+  s.vjp_fwd_key = nullptr;
+  FixedAmplitudes<T> fixed(s);
   ftcc_ctx* h = B.home;
   constexpr size_t es = sizeof(T);
   const long long ng = B.ng, nz = B.nz;
@@ -2776,6 +2804,7 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
 // rdm[q][p] pairs with X[p][q]).
 template <class T>
 void response(Batch& B, Solver<T>& s, std::vector<ftcc_adjoint_result>& out, std::vector<std::vector<double>>& rdm) {
+  FixedAmplitudes<T> fixed(s);
   ftcc_ctx* h = B.home;
   const int nz = B.nz, no = B.no, nv = B.nv, N = B.N, ng = B.ng;
   const long long n1 = static_cast<long long>(nz) * ng * no * nv;
