@@ -318,6 +318,10 @@ def run_c3_iteration(args):
         ctx.prepare(C3["beta"], mu, C3["ngrid"], precision=args.precision, tau_chunk=8)
     ctx.iterate(args.warmup + args.steps)
     torch.cuda.synchronize()
+    if args.c3_adjoint:   # the headline solve to convergence and its adjoint (lambda sweep + response)
+        ctx.solve(C3["beta"], mu, C3["ngrid"], **sparse_opts())
+        ctx.adjoint(with_rdm1=False)
+        torch.cuda.synchronize()
     ctx.close()
 
 
@@ -1029,6 +1033,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32 block-sparse sweep")
     ap.add_argument("--c3-iterations", action="store_true",
                     help="prepare the headline workload and run W + K iterations (profiler launch lists)")
+    ap.add_argument("--c3-adjoint", action="store_true",
+                    help="with --c3-iterations --no-dense: then solve and run the adjoint (profiler launch lists)")
     ap.add_argument("--sparse-precision", default="fp64", choices=["fp64", "bf16x3"],
                     help="with --c3-iterations --no-dense: the block-sparse FP64 iteration or its FP32 sweep")
     ap.add_argument("--gemm", default=None, help="B,M,N,K: time the tensor-core GEMM alone on that shape")

@@ -330,6 +330,10 @@ struct SecTnArgs {
   const int* kl;
   const int4* sec;
   const int4* work;
+  // unordered sectors (pairs p < q): antiA reads A antisymmetrised in its
+  // row pair, (A[p q] - A[q p]) / 2; anti4 writes each output (p_o q_o, k l)
+  // to its four orientations with signs +, -, -, + (l the partner of k)
+  int antiA, anti4;
 };
 // Forward values and cotangents of the block-sparse S-kernel transpose ([nx][N^3] / [nx][N]).
 struct SpVjpArgs {
@@ -348,6 +352,7 @@ struct SpVjpArgs {
 cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, const int* list, int nlist, int n, int nx,
                            double* Rb, cudaStream_t st);
 cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st);
+cudaError_t launch_sector_tn_small(const SecTnArgs& g, int nwork, cudaStream_t st);   // sectors of <= 16 pairs
 cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st);
 cudaError_t launch_sp_t2bar(const SpVjpArgs& v, int nx, cudaStream_t st);
 // Vbar[11] in SpBlocks order (null entries skipped), fbar[4] = ov, vv, oo, vo (null skipped); cz may be null

@@ -1058,7 +1058,8 @@ struct Solver {
   // One transposed sector product (see SecTnArgs): with fixed D (dx = 0)
   // the slices are summed inside the kernel.
   void sector_tn(const SecTab& tab, double* D, long long dx, const double* G, const double* A, long long ax,
-                 double alpha, int swapD, int swapA, long long g0, long long g1, long long g2, long long g3) {
+                 double alpha, int swapD, int swapA, long long g0, long long g1, long long g2, long long g3,
+                 int antiA = 0, int anti4 = 0) {
     const long long n3 = static_cast<long long>(no) * no * no;
     SecTnArgs g{};
     g.D = D;
@@ -1080,11 +1081,13 @@ struct Solver {
     g.kl = static_cast<const int*>(tab.kl.p);
     g.sec = static_cast<const int4*>(tab.sec.p);
     g.work = static_cast<const int4*>(tab.work.p);
+    g.antiA = antiA;
+    g.anti4 = anti4;
     timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(double), tab.flops * nx, [&] {
       CU(launch_sector_tn(g, tab.nwork, st()));
       SecTnArgs gs = g;
       gs.work = static_cast<const int4*>(tab.work_small.p);
-      CU(launch_sector_tn(gs, tab.nwork_small, st()));
+      CU(launch_sector_tn_small(gs, tab.nwork_small, st()));
     });
   }
 
@@ -1122,15 +1125,21 @@ struct Solver {
       // ring: R += tr wr (rows (i,a) | (j,b) swapped, output (n2, 1, 0, n))
       sector_tn(b->sdiff, trb, n3, Rb, wr_, n3, 1.0, 0, 1, n2, 1, 0, n);
       sector_tn(b->sdiff, wrb, n3, Rb, tr_, n3, 1.0, 1, 0, 0, n, n2, 1);
+      // The ladders' cotangents over unordered pairs.  R-bar = P(ij)P(ab)
+      // S2-bar is antisymmetric in ij and in ab, and so are the results
+      // (tau, <mn||ef> antisymmetric in both pairs; W'_abef and W'_mnij in
+      // their second pair): a sum over ordered (a, b) is twice the sum over
+      // a < b of R-bar times the operand antisymmetrised in (a, b), and each
+      // canonical output (i < j, e < f) is written to its four orientations.
       // particle ladder: R += 1/8 ta wab
-      sector_tn(b->ssum, tab_, n3, Rb, wab_, n3, 0.125, 0, 0, n2, n, 1, 0);
-      sector_tn(b->ssum, wabb, n3, Rb, ta_, n3, 0.125, 0, 0, 1, 0, n2, n);
+      sector_tn(b->ssum_u, tab_, n3, Rb, wab_, n3, 0.25, 0, 0, n2, n, 1, 0, 1, 1);
+      sector_tn(b->ssum_u, wabb, n3, Rb, ta_, n3, 0.25, 0, 0, 1, 0, n2, n, 0, 1);
       // hole ladder: R += 1/8 w1 tp
-      sector_tn(b->ssum, w1b, n3, Rb, tp_, n3, 0.125, 0, 0, n2, n, 1, 0);
-      sector_tn(b->ssum, tpb, n3, Rb, w1_, n3, 0.125, 0, 0, 1, 0, n2, n);
+      sector_tn(b->ssum_u, w1b, n3, Rb, tp_, n3, 0.25, 0, 0, n2, n, 1, 0, 0, 1);
+      sector_tn(b->ssum_u, tpb, n3, Rb, w1_, n3, 0.25, 0, 0, 1, 0, n2, n, 1, 1);
       // W_mbej: wr -= xp Vp;  W_mnij: w1 += 1/2 ta <mn||ef>
       sector_tn(b->sdiff, xpb, n3, wrb, static_cast<const double*>(Vp.p), 0, -1.0, 0, 0, n2, n, 1, 0);
-      sector_tn(b->ssum, tab_, n3, w1b, VB.oovv, 0, 0.5, 0, 0, n2, n, 1, 0);
+      sector_tn(b->ssum_u, tab_, n3, w1b, VB.oovv, 0, 1.0, 0, 0, n2, n, 1, 0, 0, 1);
       double* Vbar[11] = {nullptr};
       double* fbar[4] = {nullptr};
       if (want_fixed_bar) {
@@ -2711,7 +2720,7 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   ensure(h, B.dE1, n1 * es);
   ensure(h, B.cz, nz * ng * 8);
   const int nblk = 152 * 4;
-  ensure(h, B.lpart, 2 * nblk * 8);
+  ensure(h, B.lpart, 4 * nblk * 8);   // [singles | doubles][block][max change, max value]
   std::vector<double> c(nz * ng);
   for (long long z = 0; z < nz; ++z)
     for (long long x = 0; x < ng; ++x) c[z * ng + x] = simpson_weight_host(static_cast<int>(x), static_cast<int>(ng)) / (ng - 1);
@@ -2741,7 +2750,7 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   PropArgs a1 = prop_args(B, 2), a2 = prop_args(B, 4);
   a1.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a1.size + 127) / 128)));
   a2.nblocks = std::max(1, std::min(prop_blocks(), static_cast<int>((a2.size + 127) / 128)));
-  std::vector<double> parts(2 * nblk);
+  std::vector<double> parts(4 * nblk);
   int it = 0, stall = 0;
   double best_rel = 1e300;
   for (it = 1; it <= max_iter; ++it) {
@@ -2755,25 +2764,20 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
             static_cast<T*>(B.tb2.p) + f2, nx);
     }
     double dmax = 0, smax = 0;
-    for (int k = 0; k < 2; ++k) {
-      const bool one = k == 0;
-      if (one)
-        CU(launch_lambda_combine<T, T>(dE1, static_cast<const T*>(B.tb1.p), static_cast<T*>(B.mn1.p),
-                                       static_cast<const T*>(B.m1.p), e1, static_cast<int>(ng), static_cast<int>(nz),
-                                       static_cast<const double*>(B.cz.p), 0.0, static_cast<double*>(B.lpart.p), nblk,
-                                       h->st));
-      else
-        CU(launch_lambda_combine<T, double>(static_cast<const double*>(B.V64.p), static_cast<const T*>(B.tb2.p),
-                                            static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), e2,
-                                            static_cast<int>(ng), static_cast<int>(nz),
-                                            static_cast<const double*>(B.cz.p), 0.25, static_cast<double*>(B.lpart.p),
-                                            nblk, h->st));
-      CU(cudaMemcpyAsync(parts.data(), B.lpart.p, 2 * nblk * 8, cudaMemcpyDeviceToHost, h->st));
-      sync(h);
-      for (int b = 0; b < nblk; ++b) {
-        dmax = std::max(dmax, parts[2 * b]);
-        smax = std::max(smax, parts[2 * b + 1]);
-      }
+    double* lp = static_cast<double*>(B.lpart.p);
+    CU(launch_lambda_combine<T, T>(dE1, static_cast<const T*>(B.tb1.p), static_cast<T*>(B.mn1.p),
+                                   static_cast<const T*>(B.m1.p), e1, static_cast<int>(ng), static_cast<int>(nz),
+                                   static_cast<const double*>(B.cz.p), 0.0, lp, nblk, h->st));
+    CU(launch_lambda_combine<T, double>(static_cast<const double*>(B.V64.p), static_cast<const T*>(B.tb2.p),
+                                        static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), e2,
+                                        static_cast<int>(ng), static_cast<int>(nz),
+                                        static_cast<const double*>(B.cz.p), 0.25, lp + 2 * nblk, nblk, h->st));
+    // one read-back of both maxima per iteration
+    CU(cudaMemcpyAsync(parts.data(), lp, 4 * nblk * 8, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    for (int b = 0; b < 2 * nblk; ++b) {
+      dmax = std::max(dmax, parts[2 * b]);
+      smax = std::max(smax, parts[2 * b + 1]);
     }
     std::swap(B.m1, B.mn1);
     std::swap(B.m2, B.mn2);

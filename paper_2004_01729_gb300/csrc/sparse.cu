@@ -865,39 +865,49 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
 // are p n + q or (swapped) q n + p; gpos = p_o g0 + q_o g1 + p_s g2 + q_s g3.
 // With dx = 0 the output is fixed (an integral block) and the kernel sums
 // the nx slices of G and A itself.
-__global__ void __launch_bounds__(kSecThreads) sector_tn_kernel(SecTnArgs g) {
-  __shared__ double Gs[kSecKc][kSecT + 1], As[kSecKc][kSecT + 1];
+// TILE x TILE outputs per CTA of THREADS threads (48 / 256 for the sectors
+// of more than 16 pairs, 16 / 64 for the small ones, as in the forward)
+template <int TILE, int THREADS>
+__global__ void __launch_bounds__(THREADS) sector_tn_kernel(SecTnArgs g) {
+  constexpr int NO = (TILE * TILE + THREADS - 1) / THREADS;
+  __shared__ double Gs[kSecKc][TILE + 1], As[kSecKc][TILE + 1];
   const int4 w = g.work[blockIdx.x];
   const int4 sec = g.sec[w.x];
   const int n = g.n;
-  const int no_ = min(kSecT, sec.y - w.y), nk = min(kSecT, sec.w - w.z);   // output rows, k columns
+  const int no_ = min(TILE, sec.y - w.y), nk = min(TILE, sec.w - w.z);   // output rows, k columns
   const int nout = no_ * nk;
   const int xr0 = g.dx ? blockIdx.y : 0, xr1 = g.dx ? blockIdx.y + 1 : g.nx;
-  double acc[kSecO];
+  double acc[NO];
 #pragma unroll
-  for (int j = 0; j < kSecO; ++j) acc[j] = 0.0;
+  for (int j = 0; j < NO; ++j) acc[j] = 0.0;
   for (int x = xr0; x < xr1; ++x) {
     const double* G = g.G + x * g.gx;
     const double* A = g.A + x * g.ax;
     for (int s0 = 0; s0 < sec.y; s0 += kSecKc) {
       const int sc = min(kSecKc, sec.y - s0);
       // Gs[s][o] = G(output row o, summed row s), As[s][k] = A(summed row s, column k)
-      for (int idx = threadIdx.x; idx < no_ * sc; idx += kSecThreads) {
+      for (int idx = threadIdx.x; idx < no_ * sc; idx += THREADS) {
         const int o = idx / sc, ss = idx - o * sc;
         const int2 po = g.ent[sec.x + w.y + o], ps = g.ent[sec.x + s0 + ss];
         Gs[ss][o] = G[static_cast<long long>(po.x) * g.g0 + static_cast<long long>(po.y) * g.g1 +
                       static_cast<long long>(ps.x) * g.g2 + static_cast<long long>(ps.y) * g.g3];
       }
-      for (int idx = threadIdx.x; idx < nk * sc; idx += kSecThreads) {
+      for (int idx = threadIdx.x; idx < nk * sc; idx += THREADS) {
         const int ss = idx / nk, k = idx - ss * nk;
         const int2 ps = g.ent[sec.x + s0 + ss];
         const long long srow = g.swapA ? static_cast<long long>(ps.y) * n + ps.x : static_cast<long long>(ps.x) * n + ps.y;
-        As[ss][k] = A[srow * n + g.kl[sec.z + w.z + k]];
+        const int col = g.kl[sec.z + w.z + k];
+        double v = A[srow * n + col];
+        if (g.antiA) {
+          const long long srw = g.swapA ? static_cast<long long>(ps.x) * n + ps.y : static_cast<long long>(ps.y) * n + ps.x;
+          v = 0.5 * (v - A[srw * n + col]);
+        }
+        As[ss][k] = v;
       }
       __syncthreads();
 #pragma unroll
-      for (int j = 0; j < kSecO; ++j) {
-        const int o = threadIdx.x + j * kSecThreads;
+      for (int j = 0; j < NO; ++j) {
+        const int o = threadIdx.x + j * THREADS;
         if (o < nout) {
           const int r = o / nk, k = o - r * nk;
           double a = acc[j];
@@ -909,14 +919,24 @@ __global__ void __launch_bounds__(kSecThreads) sector_tn_kernel(SecTnArgs g) {
     }
   }
 #pragma unroll
-  for (int j = 0; j < kSecO; ++j) {
-    const int o = threadIdx.x + j * kSecThreads;
+  for (int j = 0; j < NO; ++j) {
+    const int o = threadIdx.x + j * THREADS;
     if (o < nout) {
       const int r = o / nk, k = o - r * nk;
       const int2 pr = g.ent[sec.x + w.y + r];
       const long long orow = g.swapD ? static_cast<long long>(pr.y) * n + pr.x : static_cast<long long>(pr.x) * n + pr.y;
-      const long long q = (g.dx ? static_cast<long long>(blockIdx.y) * g.dx : 0) + orow * n + g.kl[sec.z + w.z + k];
-      g.D[q] += g.alpha * acc[j];
+      const long long base = g.dx ? static_cast<long long>(blockIdx.y) * g.dx : 0;
+      const double v = g.alpha * acc[j];
+      if (g.anti4) {
+        const int2 pk = g.ent[sec.z + w.z + k];   // (k, l)
+        const long long r1 = static_cast<long long>(pr.x) * n + pr.y, r2 = static_cast<long long>(pr.y) * n + pr.x;
+        g.D[base + r1 * n + pk.x] += v;
+        g.D[base + r2 * n + pk.x] -= v;
+        g.D[base + r1 * n + pk.y] -= v;
+        g.D[base + r2 * n + pk.y] += v;
+      } else {
+        g.D[base + orow * n + g.kl[sec.z + w.z + k]] += v;
+      }
     }
   }
 }
@@ -1273,7 +1293,14 @@ cudaError_t launch_sp_s2_t(const double* S2b, const int16_t* imp, const int* lis
 cudaError_t launch_sector_tn(const SecTnArgs& g, int nwork, cudaStream_t st) {
   if (nwork <= 0 || g.nx <= 0) return cudaSuccess;
   if (g.nx > 65535) return cudaErrorInvalidValue;
-  sector_tn_kernel<<<dim3(nwork, g.dx ? g.nx : 1), kSecThreads, 0, st>>>(g);
+  sector_tn_kernel<kSecT, kSecThreads><<<dim3(nwork, g.dx ? g.nx : 1), kSecThreads, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_tn_small(const SecTnArgs& g, int nwork, cudaStream_t st) {
+  if (nwork <= 0 || g.nx <= 0) return cudaSuccess;
+  if (g.nx > 65535) return cudaErrorInvalidValue;
+  sector_tn_kernel<16, 64><<<dim3(nwork, g.dx ? g.nx : 1), 64, 0, st>>>(g);
   return cudaGetLastError();
 }
 
