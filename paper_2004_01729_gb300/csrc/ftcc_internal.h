@@ -345,6 +345,7 @@ struct SpVjpArgs {
   const int16_t* imp;
   const int* list;                                   // the valid N^3 positions
   int nlist;
+  const int *l1, *off1, *l2, *off2;                  // per orbital p: valid (m, q) of (m, q, p) / (p, m, q)
   int n;
   double *Ftb, *Ft2b, *Faeb, *Fmib, *Fmeb;           // vector cotangents (written)
   double *t1b, *t2b;                                 // outputs (the holes of t2b must be zero: not written)

@@ -1175,6 +1175,10 @@ struct Solver {
       va.imp = imp;
       va.list = vall;
       va.nlist = b->nvall;
+      va.l1 = static_cast<const int*>(b->vl1.p);
+      va.off1 = static_cast<const int*>(b->voff1.p);
+      va.l2 = static_cast<const int*>(b->vl2.p);
+      va.off2 = static_cast<const int*>(b->voff2.p);
       va.n = n;
       va.Ftb = (double*)bFt.p;
       va.Ft2b = (double*)bFt2.p;

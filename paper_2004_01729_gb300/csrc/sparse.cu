@@ -138,6 +138,28 @@ __global__ void sp_fme_kernel(const T* __restrict__ t1, const T* __restrict__ fo
   if (lane == 0) Fme[static_cast<long long>(x) * n + m] = fov[m] + acc;
 }
 
+// K sums of one block at once: each warp reduces its K values by shuffles,
+// one barrier, thread 0 adds the warps' partials in order (the same order per
+// value as K separate block_sum calls).  red: K * 32 slots; valid in thread 0.
+template <class T, int K>
+__device__ __forceinline__ void block_sums(T (&v)[K], T* red) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k * 32 + w] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T s = T(0.0);
+      for (int q = 0; q < (blockDim.x >> 5); ++q) s += red[k * 32 + q];
+      v[k] = s;
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -172,7 +194,7 @@ struct SpVec {
 
 template <class T>
 __global__ void sp_vec_kernel(SpVec<T> a) {
-  __shared__ T red[32];
+  __shared__ T red[6 * 32];
   const int n = a.n;
   const long long n3 = static_cast<long long>(n) * n * n;
   const int p = blockIdx.x, x = blockIdx.y;
@@ -208,12 +230,14 @@ __global__ void sp_vec_kernel(SpVec<T> a) {
     hmi += t * a.Voovv[o2];
     hs1 += t * a.Vovvv[pos3(n, m, p, q)];
   }
-  cae = block_sum(cae, red);
-  cmi = block_sum(cmi, red);
-  cs1 = block_sum(cs1, red);
-  hae = block_sum(hae, red);
-  hmi = block_sum(hmi, red);
-  hs1 = block_sum(hs1, red);
+  T sums[6] = {cae, cmi, cs1, hae, hmi, hs1};
+  block_sums(sums, red);
+  cae = sums[0];
+  cmi = sums[1];
+  cs1 = sums[2];
+  hae = sums[3];
+  hmi = sums[4];
+  hs1 = sums[5];
   if (threadIdx.x == 0) {
     const long long o = static_cast<long long>(x) * n + p;
     const T s = s1[p], fm = Fme[p];
@@ -749,12 +773,13 @@ struct SpVecT {
   const double *Vvvvo, *Vovvo, *Vovoo, *Vooov, *Vovvv, *Voovo, *Vovov, *Voovv;
   const double *w1b, *wabb, *wrb, *tab, *tpb, *xpb;
   const int16_t* imp;
+  const int *l1, *off1, *l2, *off2;   // valid (m, q) = m n + q of (m, q, p) / (p, m, q) per p
   int n;
   double *Ftb, *Ft2b, *Faeb, *Fmib, *Fmeb, *t1b;
 };
 
 __global__ void sp_vec_t1_kernel(SpVecT a) {
-  __shared__ double red[32];
+  __shared__ double red[3 * 32];
   const int n = a.n;
   const long long n3 = static_cast<long long>(n) * n * n;
   const int p = blockIdx.x, x = blockIdx.y;
@@ -762,17 +787,26 @@ __global__ void sp_vec_t1_kernel(SpVecT a) {
   const double* Rb = a.Rb + x * n3;
   const double* S1b = a.S1b + static_cast<long long>(x) * n;
   double ftb = 0.0, ft2b = 0.0, fme = 0.0;
-  const long long nn = static_cast<long long>(n) * n;
-  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
-    const int u = static_cast<int>(r / static_cast<uint32_t>(n)), w = static_cast<int>(r - static_cast<uint32_t>(u) * n);
+  // only the valid positions (the rest of Rb and s2 is zero): (u, w, a) with
+  // a = imp(u, w, p) from p's list l1, (p, u, w) from l2
+  for (int k = a.off1[p] + threadIdx.x; k < a.off1[p + 1]; k += blockDim.x) {
+    const int uw = a.l1[k];
+    const int u = uw / n, w = uw - u * n;
     const int aa = impl(a.imp, n, u, w, p);                    // (i, j, a) = (u, w, aa), b = p
-    if (aa >= 0) ftb += Rb[pos3(n, u, w, aa)] * s2[pos3(n, u, w, aa)];
+    const long long o = pos3(n, u, w, aa);
+    ftb += Rb[o] * s2[o];
+  }
+  for (int k = a.off2[p] + threadIdx.x; k < a.off2[p + 1]; k += blockDim.x) {
+    const int uw = a.l2[k];
+    const int u = uw / n, w = uw - u * n;
     ft2b += Rb[pos3(n, p, u, w)] * s2[pos3(n, u, p, w)];     // (i, j, a) = (p, u, w)
   }
   for (int q = threadIdx.x; q < n; q += blockDim.x) fme += S1b[q] * s2[pos3(n, q, p, q)];
-  ftb = block_sum(ftb, red);
-  ft2b = block_sum(ft2b, red);
-  fme = block_sum(fme, red);
+  double sums[3] = {ftb, ft2b, fme};
+  block_sums(sums, red);
+  ftb = sums[0];
+  ft2b = sums[1];
+  fme = sums[2];
   if (threadIdx.x == 0) {
     const long long o = static_cast<long long>(x) * n + p;
     const double s = a.t1[o];
@@ -808,38 +842,36 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
   const double* Fmib = a.Fmib + static_cast<long long>(x) * n;
   const double* Fmeb = a.Fmeb + static_cast<long long>(x) * n;
   double acc = 0.0;
-  const long long nn = static_cast<long long>(n) * n;
-  for (uint32_t r = threadIdx.x; r < static_cast<uint32_t>(nn); r += blockDim.x) {
-    const int u = static_cast<int>(r / static_cast<uint32_t>(n)), w = static_cast<int>(r - static_cast<uint32_t>(u) * n);
+  // every term below vanishes unless its implied index exists: the terms
+  // with a valid (p, u, w) run over p's list l2, those with a valid (u, w, p)
+  // over l1, the one with a valid (p, w, u) over l2 with the pair swapped
+  for (int k = a.off2[p] + threadIdx.x; k < a.off2[p + 1]; k += blockDim.x) {
+    const int uw = a.l2[k];
+    const int u = uw / n, w = uw - u * n;
+    const long long o = pos3(n, p, u, w);
     {   // R: p as i, (j, a) = (u, w), b = imp(p, u, w)
-      const int b = impl(a.imp, n, p, u, w);
-      if (b >= 0) {
-        const double g = Rb[pos3(n, p, u, w)];
-        acc += g * (0.5 * a.Vvvvo[pos3(n, w, b, p)] + s1[b] * a.Vovvo[pos3(n, b, w, p)]);
-      }
-    }
-    {   // R: p as a, (i, j) = (u, w), b = imp(u, w, p)
-      const int b = impl(a.imp, n, u, w, p);
-      if (b >= 0) acc -= 0.5 * Rb[pos3(n, u, w, p)] * a.Vovoo[pos3(n, p, b, u)];
-    }
-    {   // R: p as b, (i, j) = (u, w), a = imp(u, w, p)
-      const int aa = impl(a.imp, n, u, w, p);
-      if (aa >= 0) acc += Rb[pos3(n, u, w, aa)] * s1[u] * a.Vovvo[pos3(n, p, aa, u)];
-    }
-    {   // W'_mnij base: p as i, (j, m) = (u, w), n = imp(p, u, w)
-      const int q = impl(a.imp, n, p, u, w);
-      if (q >= 0) acc -= 2.0 * w1b[pos3(n, p, u, w)] * a.Vooov[pos3(n, w, q, u)];
+      const int b = a.imp[o];
+      acc += Rb[o] * (0.5 * a.Vvvvo[pos3(n, w, b, p)] + s1[b] * a.Vovvo[pos3(n, b, w, p)]);
+      // W'_mnij base: p as i, (j, m) = (u, w), n = imp(p, u, w)
+      acc -= 2.0 * w1b[o] * a.Vooov[pos3(n, w, b, u)];
     }
     // W'_abef base: p as a, (b, e) = (u, w)
-    acc -= 2.0 * wabb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, p, u, w)];
-    {   // W_mbej base, p as j: (b, m) = (u, w), e = imp(u, w, p)
-      const int ee = impl(a.imp, n, u, w, p);
-      if (ee >= 0) acc += wrb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, w, u, ee)];
+    acc -= 2.0 * wabb[o] * a.Vovvv[o];
+    {   // W_mbej base, p as b: (j, m) = (w, u) here, e = imp(p, u, w)
+      const int ee = a.imp[o];
+      acc -= wrb[pos3(n, w, p, u)] * a.Voovo[pos3(n, u, p, ee)];
     }
-    {   // W_mbej base, p as b: (j, m) = (u, w), e = imp(p, w, u)
-      const int ee = impl(a.imp, n, p, w, u);
-      if (ee >= 0) acc -= wrb[pos3(n, u, p, w)] * a.Voovo[pos3(n, w, p, ee)];
-    }
+  }
+  for (int k = a.off1[p] + threadIdx.x; k < a.off1[p + 1]; k += blockDim.x) {
+    const int uw = a.l1[k];
+    const int u = uw / n, w = uw - u * n;
+    const int c = impl(a.imp, n, u, w, p);   // b (p as a), a (p as b), e (p as j)
+    // R: p as a, (i, j) = (u, w), b = imp(u, w, p)
+    acc -= 0.5 * Rb[pos3(n, u, w, p)] * a.Vovoo[pos3(n, p, c, u)];
+    // R: p as b, (i, j) = (u, w), a = imp(u, w, p)
+    acc += Rb[pos3(n, u, w, c)] * s1[u] * a.Vovvo[pos3(n, p, c, u)];
+    // W_mbej base, p as j: (b, m) = (u, w), e = imp(u, w, p)
+    acc += wrb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, w, u, c)];
   }
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     // S1 and the F intermediates
@@ -1306,8 +1338,8 @@ cudaError_t launch_sector_tn_small(const SecTnArgs& g, int nwork, cudaStream_t s
 
 cudaError_t launch_sp_vjp_vectors(const SpVjpArgs& v, int nx, cudaStream_t st) {
   SpVecT a{v.t1, v.t2, v.Rb, v.S1b, v.Fme, v.Fae, v.Fmi, v.V.vvvo, v.V.ovvo, v.V.ovoo, v.V.ooov, v.V.ovvv,
-           v.V.oovo, v.V.ovov, v.V.oovv, v.w1b, v.wabb, v.wrb, v.tab, v.tpb, v.xpb, v.imp, v.n,
-           v.Ftb, v.Ft2b, v.Faeb, v.Fmib, v.Fmeb, v.t1b};
+           v.V.oovo, v.V.ovov, v.V.oovv, v.w1b, v.wabb, v.wrb, v.tab, v.tpb, v.xpb, v.imp,
+           v.l1, v.off1, v.l2, v.off2, v.n, v.Ftb, v.Ft2b, v.Faeb, v.Fmib, v.Fmeb, v.t1b};
   sp_vec_t1_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
   sp_vec_t2_kernel<<<dim3(v.n, nx), 256, 0, st>>>(a);
   return cudaGetLastError();
