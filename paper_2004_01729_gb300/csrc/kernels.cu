@@ -929,6 +929,13 @@ __global__ void __launch_bounds__(kPropThreads, sizeof(A) == 4 ? 8 : 4) propagat
 // Transposed propagation: u_x = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m_y,
 // the adjoint of the Simpson recurrences above, run from the last tau point
 // down with the even-chain adjoint E'_y = m_y + r^2 E'_{y+2} + r^3 m_{y+3}.
+// Block-sparse doubles with a canonical list: u = P^T (pi m), pi the
+// projection onto tensors antisymmetric in (i, j) and (a, b) (the mean of the
+// four signed orientations): each canonical element is propagated once and
+// written to its four orientations.  Every consumer of u contracts it with
+// antisymmetric tensors (S2, its derivatives, the antisymmetric integrals),
+// which see only pi u, and pi P^T m = P^T pi m; the elements with i = j or
+// a = b are left alone (zero).
 template <class T, int NS>
 __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __restrict__ m, T* __restrict__ u,
                                                                    PropArgs a) {
@@ -941,9 +948,13 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
   const double* ep = a.ep + static_cast<long long>(z) * a.N;
   const double h = a.hz[z];
   const bool sparse = a.imp != nullptr;
-  for (long long mu = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; mu < size;
-       mu += static_cast<long long>(gridDim.x) * blockDim.x) {
+  const bool canon = sparse && NS == 4 && a.canon != nullptr;
+  const long long nloop = canon ? a.ncanon : size;
+  for (long long cidx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; cidx < nloop;
+       cidx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long mu = canon ? a.canon[cidx] : cidx;
     int i, j = 0, aa, b = 0;
+    long long o1 = 0, o2 = 0, o3 = 0;   // canonical: (j, i, a), (i, j, b), (j, i, b)
     if (sparse) {
       // [i][j][a] with b implied (a hole of the storage is skipped), or the
       // diagonal singles [i] (a = i)
@@ -957,6 +968,12 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
         i = q;
         b = a.imp[mu];
         if (b < 0) continue;
+        if (canon) {
+          const long long nn = a.nv;
+          o1 = (static_cast<long long>(j) * nn + i) * nn + aa;
+          o2 = (static_cast<long long>(i) * nn + j) * nn + b;
+          o3 = (static_cast<long long>(j) * nn + i) * nn + b;
+        }
       } else {
         i = aa = static_cast<int>(r);
       }
@@ -986,11 +1003,17 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
       ri *= ep[pb] * em[pj];
     }
     const double r2 = rr * rr, r3 = r2 * rr;
-    const double m1 = static_cast<double>(m[size + mu]);
+    auto mval = [&](int x) -> double {
+      const T* mr = m + static_cast<long long>(x) * size;
+      if (!canon) return static_cast<double>(mr[mu]);
+      return 0.25 * ((static_cast<double>(mr[mu]) - static_cast<double>(mr[o1])) -
+                     (static_cast<double>(mr[o2]) - static_cast<double>(mr[o3])));
+    };
+    const double m1 = mval(1);
     double mp1 = 0.0, mp2 = 0.0, mp3 = 0.0;   // m_{x+1}, m_{x+2}, m_{x+3}
     double Ep1 = 0.0, Ep2 = 0.0;              // E'_{x+1}, E'_{x+2}
     for (int x = ng - 1; x >= 0; --x) {
-      const double mx = static_cast<double>(m[static_cast<long long>(x) * size + mu]);
+      const double mx = mval(x);
       double Ex = 0.0;
       if ((x & 1) == 0 && x >= 2) Ex = mx + r2 * Ep2 + r3 * mp3;
       double ux = 0.0;
@@ -1004,7 +1027,13 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
       if (x == 0) ux += 5.0 * h / 12.0 * rr * m1;
       if (x == 1) ux += 8.0 * h / 12.0 * m1;
       if (x == 2) ux -= h / 12.0 * ri * m1;
-      u[static_cast<long long>(x) * size + mu] = static_cast<T>(ux);
+      T* ur = u + static_cast<long long>(x) * size;
+      ur[mu] = static_cast<T>(ux);
+      if (canon) {
+        ur[o1] = static_cast<T>(-ux);
+        ur[o2] = static_cast<T>(-ux);
+        ur[o3] = static_cast<T>(ux);
+      }
       mp3 = mp2;
       mp2 = mp1;
       mp1 = mx;

@@ -2719,8 +2719,10 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   ensure(h, B.u2, n2 * es);
   ensure(h, B.tb1, n1 * es);
   ensure(h, B.tb2, n2 * es);
-  // (the block-sparse transpose writes only the valid positions: its holes stay zero)
+  // (the block-sparse transpose writes only the valid positions: its holes stay zero;
+  // the canonical transposed propagation leaves the i = j and a = b elements of u2 zero)
   CU(cudaMemsetAsync(B.tb2.p, 0, n2 * es, h->st));
+  CU(cudaMemsetAsync(B.u2.p, 0, n2 * es, h->st));
   ensure(h, B.dE1, n1 * es);
   ensure(h, B.cz, nz * ng * 8);
   const int nblk = 152 * 4;
