@@ -245,10 +245,12 @@ double simpson_weight_host(int y, int ng);
 // u[z][x][mu] = sum_y G[y,x] exp(-Delta (tau_y - tau_x)) m[z][y][mu] (transpose of the propagation)
 template <class T> cudaError_t launch_propagate_t(const T* m, T* u, const PropArgs& a, cudaStream_t st);
 // m_new = -c[z][x] * base' - tbar with base' = cbase * base[z][mu] (cbase != 0, tau-independent base)
-// or base[z][x][mu] (cbase == 0); partials [nblocks][2] = max|m_new - m_old|, max|m_new|
+// or base[z][x][mu] (cbase == 0); partials [nblocks][2] = max|m_new - m_old|, max|m_new|.  With a
+// list, only the positions mu of the list (block-sparse valid positions; the rest stays zero)
 template <class T, class BT>
 cudaError_t launch_lambda_combine(const BT* base, const T* tbar, T* mnew, const T* mold, long long size, int ng, int nz,
-                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st);
+                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st,
+                                  const int* list = nullptr, int nlist = 0);
 
 // ---- response (App. B) ----
 // Do[z][q] / Dv[z][q] += sum A*I over elements with a hole-like / particle-like

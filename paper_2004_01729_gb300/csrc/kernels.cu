@@ -1049,10 +1049,32 @@ __global__ void __launch_bounds__(kPropThreads) propagate_t_kernel(const T* __re
 template <class T, class BT>
 __global__ void lambda_combine_kernel(const BT* __restrict__ base, const T* __restrict__ tbar,
                                       T* __restrict__ mnew, const T* __restrict__ mold, long long size, int ng,
-                                      int nz, const double* __restrict__ cz, double cbase, double* partials) {
+                                      int nz, const double* __restrict__ cz, double cbase, double* partials,
+                                      const int* __restrict__ list, int nlist) {
   __shared__ double dm[256], sm[256];
   double dmax = 0.0, smax = 0.0;
-  const long long total = static_cast<long long>(nz) * ng * size;
+  if (list) {
+    // block-sparse doubles: only the valid positions (the holes of base, tbar
+    // and m are zero and stay so); slices outer, no index division
+    const int stride = gridDim.x * blockDim.x;
+    for (int zx = 0; zx < nz * ng; ++zx) {
+      const double c = cz[zx];
+      const int z = zx / ng;
+      const BT* bz = base + static_cast<long long>(z) * size * (cbase != 0.0 ? 1 : ng) +
+                     (cbase != 0.0 ? 0 : static_cast<long long>(zx - z * ng) * size);
+      for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlist; k += stride) {
+        const long long mu = list[k];
+        const long long e = static_cast<long long>(zx) * size + mu;
+        const double bval = static_cast<double>(bz[mu]);
+        const double v = -c * (cbase != 0.0 ? cbase * bval : bval) - static_cast<double>(tbar[e]);
+        const T vs = static_cast<T>(v);
+        dmax = fmax(dmax, fabs(static_cast<double>(vs) - static_cast<double>(mold[e])));
+        smax = fmax(smax, fabs(static_cast<double>(vs)));
+        mnew[e] = vs;
+      }
+    }
+  }
+  const long long total = list ? 0 : static_cast<long long>(nz) * ng * size;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long zx = e / size;
@@ -2058,8 +2080,11 @@ cudaError_t launch_propagate_t(const T* m, T* u, const PropArgs& a_in, cudaStrea
 
 template <class T, class BT>
 cudaError_t launch_lambda_combine(const BT* base, const T* tbar, T* mnew, const T* mold, long long size, int ng, int nz,
-                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st) {
-  lambda_combine_kernel<T, BT><<<nblocks, 256, 0, st>>>(base, tbar, mnew, mold, size, ng, nz, cz, cbase, partials);
+                                  const double* cz, double cbase, double* partials, int nblocks, cudaStream_t st,
+                                  const int* list, int nlist) {
+  if (list && static_cast<long long>(nz) * ng * size >= (1LL << 31)) return cudaErrorInvalidValue;
+  lambda_combine_kernel<T, BT><<<nblocks, 256, 0, st>>>(base, tbar, mnew, mold, size, ng, nz, cz, cbase, partials,
+                                                        list, nlist);
   return cudaGetLastError();
 }
 
@@ -2109,11 +2134,12 @@ cudaError_t launch_prop_response(const T* S, const T* m, const double* epsz, con
   template cudaError_t launch_prop_response<T>(const T*, const T*, const double*, const PropArgs&, double*, double*, \
                                                cudaStream_t);                                                       \
   template cudaError_t launch_lambda_combine<T, T>(const T*, const T*, T*, const T*, long long, int, int,           \
-                                                   const double*, double, double*, int, cudaStream_t);
+                                                   const double*, double, double*, int, cudaStream_t, const int*, int);
 FTCC_ADJOINT_INSTANTIATE(float)
 FTCC_ADJOINT_INSTANTIATE(double)
 #undef FTCC_ADJOINT_INSTANTIATE
 template cudaError_t launch_lambda_combine<float, double>(const double*, const float*, float*, const float*, long long,
-                                                          int, int, const double*, double, double*, int, cudaStream_t);
+                                                          int, int, const double*, double, double*, int, cudaStream_t,
+                                                          const int*, int);
 
 }  // namespace ftcc

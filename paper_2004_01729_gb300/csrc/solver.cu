@@ -2733,6 +2733,7 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
   CU(cudaMemcpyAsync(B.cz.p, c.data(), c.size() * 8, cudaMemcpyHostToDevice, h->st));
   CU(cudaMemsetAsync(B.m1.p, 0, n1 * es, h->st));
   CU(cudaMemsetAsync(B.m2.p, 0, n2 * es, h->st));
+  CU(cudaMemsetAsync(B.mn2.p, 0, n2 * es, h->st));   // (block-sparse: only valid positions are rewritten)
   // a member frozen after diverging takes no part: its amplitudes are set to
   // zero so that its (unused) multipliers stay finite
   for (long long z = 0; z < nz; ++z)
@@ -2777,7 +2778,8 @@ int lambda_solve(Batch& B, Solver<T>& s, double tol, int max_iter) {
     CU(launch_lambda_combine<T, double>(static_cast<const double*>(B.V64.p), static_cast<const T*>(B.tb2.p),
                                         static_cast<T*>(B.mn2.p), static_cast<const T*>(B.m2.p), e2,
                                         static_cast<int>(ng), static_cast<int>(nz),
-                                        static_cast<const double*>(B.cz.p), 0.25, lp + 2 * nblk, nblk, h->st));
+                                        static_cast<const double*>(B.cz.p), 0.25, lp + 2 * nblk, nblk, h->st,
+                                        s.sp ? static_cast<const int*>(B.vall.p) : nullptr, s.sp ? B.nvall : 0));
     // one read-back of both maxima per iteration
     CU(cudaMemcpyAsync(parts.data(), lp, 4 * nblk * 8, cudaMemcpyDeviceToHost, h->st));
     sync(h);

@@ -752,11 +752,16 @@ __global__ void sp_t2bar_kernel(SpT2 a) {
     const int b = impl(a.imp, n, i, j, aa);
     double v = 0.0;
     if (b >= 0) {
-      v = 0.5 * Rb[e] * Ft[b] + 0.5 * Ft2[j] * Rb[pos3(n, j, i, aa)];
+      // the halved terms summed first and scaled once (FP64 instructions
+      // are the cost here)
+      double hsum = Rb[e] * Ft[b];
+      hsum = fma(Ft2[j], Rb[pos3(n, j, i, aa)], hsum);
+      hsum = fma(-S1b[i], a.Vovvv[pos3(n, j, i, aa)], hsum);
+      hsum = fma(Fmib[i] - Faeb[aa], a.Voovv[e], hsum);
+      hsum = fma(-S1b[aa], a.Voovo[pos3(n, j, i, b)], hsum);
+      hsum += xpb[pos3(n, i, b, j)];
+      v = fma(0.5, hsum, tab[e] + tpb[pos3(n, aa, b, i)] + trb[pos3(n, i, aa, j)]);
       if (aa == i) v += S1b[i] * Fme[j];
-      v += -0.5 * S1b[i] * a.Vovvv[pos3(n, j, i, aa)] + 0.5 * Fmib[i] * a.Voovv[e] -
-           0.5 * S1b[aa] * a.Voovo[pos3(n, j, i, b)] - 0.5 * Faeb[aa] * a.Voovv[e];
-      v += tab[e] + tpb[pos3(n, aa, b, i)] + trb[pos3(n, i, aa, j)] + 0.5 * xpb[pos3(n, i, b, j)];
     }
     a.t2b[x * n3 + e] = v;
   }
@@ -841,7 +846,7 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
   const double* Faeb = a.Faeb + static_cast<long long>(x) * n;
   const double* Fmib = a.Fmib + static_cast<long long>(x) * n;
   const double* Fmeb = a.Fmeb + static_cast<long long>(x) * n;
-  double acc = 0.0;
+  double acc = 0.0, acch = 0.0, acc2 = 0.0;   // terms of weight 1, 1/2 and -2, scaled once at the end
   // every term below vanishes unless its implied index exists: the terms
   // with a valid (p, u, w) run over p's list l2, those with a valid (u, w, p)
   // over l1, the one with a valid (p, w, u) over l2 with the pair swapped
@@ -849,30 +854,30 @@ __global__ void sp_vec_t2_kernel(SpVecT a) {
     const int uw = a.l2[k];
     const int u = uw / n, w = uw - u * n;
     const long long o = pos3(n, p, u, w);
-    {   // R: p as i, (j, a) = (u, w), b = imp(p, u, w)
-      const int b = a.imp[o];
-      acc += Rb[o] * (0.5 * a.Vvvvo[pos3(n, w, b, p)] + s1[b] * a.Vovvo[pos3(n, b, w, p)]);
-      // W'_mnij base: p as i, (j, m) = (u, w), n = imp(p, u, w)
-      acc -= 2.0 * w1b[o] * a.Vooov[pos3(n, w, b, u)];
-    }
+    const int b = a.imp[o];   // b (R, p as i), n (W'_mnij, p as i), e (W_mbej, p as b)
+    const double g = Rb[o];
+    // R: p as i, (j, a) = (u, w), b = imp(p, u, w)
+    acch = fma(g, a.Vvvvo[pos3(n, w, b, p)], acch);
+    acc = fma(g * s1[b], a.Vovvo[pos3(n, b, w, p)], acc);
+    // W'_mnij base: p as i, (j, m) = (u, w), n = imp(p, u, w)
+    acc2 = fma(w1b[o], a.Vooov[pos3(n, w, b, u)], acc2);
     // W'_abef base: p as a, (b, e) = (u, w)
-    acc -= 2.0 * wabb[o] * a.Vovvv[o];
-    {   // W_mbej base, p as b: (j, m) = (w, u) here, e = imp(p, u, w)
-      const int ee = a.imp[o];
-      acc -= wrb[pos3(n, w, p, u)] * a.Voovo[pos3(n, u, p, ee)];
-    }
+    acc2 = fma(wabb[o], a.Vovvv[o], acc2);
+    // W_mbej base, p as b: (j, m) = (w, u) here, e = imp(p, u, w)
+    acc = fma(-wrb[pos3(n, w, p, u)], a.Voovo[pos3(n, u, p, b)], acc);
   }
   for (int k = a.off1[p] + threadIdx.x; k < a.off1[p + 1]; k += blockDim.x) {
     const int uw = a.l1[k];
     const int u = uw / n, w = uw - u * n;
     const int c = impl(a.imp, n, u, w, p);   // b (p as a), a (p as b), e (p as j)
     // R: p as a, (i, j) = (u, w), b = imp(u, w, p)
-    acc -= 0.5 * Rb[pos3(n, u, w, p)] * a.Vovoo[pos3(n, p, c, u)];
+    acch = fma(-Rb[pos3(n, u, w, p)], a.Vovoo[pos3(n, p, c, u)], acch);
     // R: p as b, (i, j) = (u, w), a = imp(u, w, p)
-    acc += Rb[pos3(n, u, w, c)] * s1[u] * a.Vovvo[pos3(n, p, c, u)];
+    acc = fma(Rb[pos3(n, u, w, c)] * s1[u], a.Vovvo[pos3(n, p, c, u)], acc);
     // W_mbej base, p as j: (b, m) = (u, w), e = imp(u, w, p)
-    acc += wrb[pos3(n, p, u, w)] * a.Vovvv[pos3(n, w, u, c)];
+    acc = fma(wrb[pos3(n, p, u, w)], a.Vovvv[pos3(n, w, u, c)], acc);
   }
+  acc = fma(0.5, acch, fma(-2.0, acc2, acc));
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     // S1 and the F intermediates
     acc += -S1b[q] * a.Vovov[pos3(n, p, q, q)] + Faeb[q] * a.Vovvv[pos3(n, p, q, p)] +
