@@ -86,6 +86,10 @@ struct ftcc_ctx {
   // this context is home to (written by each iteration's graph tail)
   double* pin_state = nullptr;
   size_t pin_state_n = 0;
+  // a second stream for work that may overlap the main stream's (created on
+  // first use; joined back through ev_join before the main stream goes on)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   ftcc::Buf get(size_t bytes) {
     ftcc::Buf b;
@@ -377,6 +381,22 @@ struct Solver {
     }
   }
   cudaStream_t st() const { return h_->st; }
+  // fork: the side stream waits for everything enqueued on st() so far
+  cudaStream_t side_begin() {
+    if (!h_->st2) {
+      CU(cudaStreamCreateWithFlags(&h_->st2, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&h_->ev_fork, cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&h_->ev_join, cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(h_->ev_fork, st()));
+    CU(cudaStreamWaitEvent(h_->st2, h_->ev_fork, 0));
+    return h_->st2;
+  }
+  // join: st() waits for the side stream's work
+  void side_end() {
+    CU(cudaEventRecord(h_->ev_join, h_->st2));
+    CU(cudaStreamWaitEvent(st(), h_->ev_join, 0));
+  }
 
   long long dimof(char ch) const {
     if (ch == 'z') return nz;
@@ -955,6 +975,9 @@ struct Solver {
       const double fl = tab.flops * nx * (A2 ? 2 : 1);
       if (counting) gemm_flops += static_cast<long long>(fl);
       timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl, [&] {
+        // (one stream: running the small sectors beside the large ones on a
+        // side stream measured 3.81 -> 3.86 ms per FP64 iteration of the
+        // 114-orbital gas, no gain in FP32; it pays in the transpose, below)
         CU(launch_sector_gemm<T>(g, tab.nwork, nx, st()));
         SecGemmArgsT<T> gs = g;
         gs.work = static_cast<const int4*>(tab.work_small.p);
@@ -1084,10 +1107,17 @@ struct Solver {
     g.antiA = antiA;
     g.anti4 = anti4;
     timed_launch(kClsSector, static_cast<double>(nx) * n3 * 3 * sizeof(double), tab.flops * nx, [&] {
-      CU(launch_sector_tn(g, tab.nwork, st()));
+      // the sectors of at most 16 pairs (latency-bound, short K loops) run on
+      // the side stream beside the large ones: the two write disjoint outputs
+      // (kept on one stream for dx = 0, where the output is one fixed block);
+      // the adjoint of the 114-orbital gas 0.114 -> 0.108 s
       SecTnArgs gs = g;
       gs.work = static_cast<const int4*>(tab.work_small.p);
-      CU(launch_sector_tn_small(gs, tab.nwork_small, st()));
+      const bool fork = dx != 0 && tab.nwork > 0 && tab.nwork_small > 0;
+      if (fork) CU(launch_sector_tn_small(gs, tab.nwork_small, side_begin()));
+      CU(launch_sector_tn(g, tab.nwork, st()));
+      if (fork) side_end();
+      else CU(launch_sector_tn_small(gs, tab.nwork_small, st()));
     });
   }
 
@@ -3092,6 +3122,9 @@ void ftcc_destroy(ftcc_ctx* c) {
   c->batch.reset();
   c->sptab.reset();
   if (c->pin_state) cudaFreeHost(c->pin_state);
+  if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   c->put(c->h);
   c->put(c->eri);
   c->put(c->eps);
