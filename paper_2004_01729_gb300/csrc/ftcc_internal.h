@@ -312,6 +312,9 @@ struct SecGemmArgsT {
   // C[j][i][a] (-), C[i][j][b] (-), C[j][i][b] (N^3 storage, the fourth index
   // implied), i.e. to all four orientations of an antisymmetric result
   int anti4;
+  // store (without anti4): C[q] = value, for an output that no other term
+  // touches (every position written exactly once), instead of C[q] += value
+  int store;
 };
 using SecGemmArgs = SecGemmArgsT<double>;
 // Transposed sector products (see sparse.cu): D[orow(e_o)][k] += alpha
@@ -393,10 +396,11 @@ cudaError_t launch_sp_wbase(const T* t1, const SpBlocksT<T>& V, const int16_t* i
 template <class T>
 cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
                             const int16_t* imp, const int* list, int nlist, int n, int nx, T* R, cudaStream_t st);
-// S2 from its canonical elements, written to their four orientations
+// S2 from its canonical elements, written to their four orientations; R is
+// [i][j][a] (b implied), Xr the ring term [i][a][b] (j implied) or null
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,
-                         T* S2, cudaStream_t st);
+cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon,
+                         int n, int nx, T* S2, cudaStream_t st);
 template <class T> cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
 // the same products for work items of sectors of at most 16 pairs (16 x 16 tiles, 64 threads)
 template <class T>

@@ -931,7 +931,7 @@ struct Solver {
   // <mn||ef> block in the W_mbej operand order.
   void sparse_alloc() {
     const long long n = no, n3 = n * n * n, x = nxc;
-    for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R}) ensure(h_, *q, x * n3 * sizeof(T));
+    for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R, &R2}) ensure(h_, *q, x * n3 * sizeof(T));   // R2: the ring term
     for (Buf* q : {&Fme, &Fae, &Fmi, &Ft, &Ft2}) ensure(h_, *q, x * n * sizeof(T));
     ensure(h_, Vp, n3 * sizeof(T));
     // cotangents of the transpose (sparse_vjp)
@@ -948,7 +948,7 @@ struct Solver {
 
   void sector_product(const SecTab& tab, const T* A, long long ax, const T* Bm, long long bx, T* C, double alpha,
                       int swapB, long long s0, long long s1, long long s2, long long s3, const T* A2 = nullptr,
-                      const T* B2 = nullptr, int anti4 = 0) {
+                      const T* B2 = nullptr, int anti4 = 0, int store = 0) {
     {
       const long long n3 = static_cast<long long>(no) * no * no;
       SecGemmArgsT<T> g{};
@@ -972,6 +972,7 @@ struct Solver {
       g.A2 = A2;
       g.B2 = B2;
       g.anti4 = anti4;
+      g.store = store;
       const double fl = tab.flops * nx * (A2 ? 2 : 1);
       if (counting) gemm_flops += static_cast<long long>(fl);
       timed_launch(kClsSector, static_cast<double>(nx) * n3 * (A2 ? 5 : 3) * sizeof(T), fl, [&] {
@@ -1008,7 +1009,7 @@ struct Solver {
       const long long n2 = static_cast<long long>(n) * n, n3 = n2 * n;
       const int16_t* imp = static_cast<const int16_t*>(b->imp.p);
       T *pta = (T*)ta.p, *ptp = (T*)tt.p, *ptr = (T*)Y.p, *pxp = (T*)X.p, *pw1 = (T*)Wmnij.p, *pwab = (T*)Wabef.p,
-        *pwr = (T*)Wmbej.p, *pR = (T*)R.p;
+        *pwr = (T*)Wmbej.p, *pR = (T*)R.p, *pXr = (T*)R2.p;
       const SpBlocksT<T> VB = sp_blocks();
       const double slice = static_cast<double>(nx) * n3 * sizeof(T);
       timed_launch(kClsOther, 6 * slice, 0.0,
@@ -1072,9 +1073,13 @@ struct Solver {
         sector_product(b->ssum, pta, n3, pwab, n3, pR, 0.125, 0, n2, n, 1, 0);
       }
       // ring s_im^ae W_mbej                        rows (i,a) | (j,b) by q_i - q_a, sum over m
-      sector_product(b->sdiff, ptr, n3, pwr, n3, pR, 1.0, 1, n2, 1, 0, n);
+      // ring: rows (i, a), columns (b, j) (wr rows swapped); stored apart as
+      // Xr[i][a][b] (each position written once, nearly contiguous along a
+      // CTA's columns), added into S2 by its gather; into R[i][j][a] it would
+      // be a read-modify-write of one 32-byte sector per output
+      sector_product(b->sdiff, ptr, n3, pwr, n3, pXr, 1.0, 1, n2, n, 1, 0, nullptr, nullptr, 0, 1);
       timed_launch(kClsScatter, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_s2<T>(pR, VB.vvoo, imp, canon, ncanon, n, nx, S2c, st())); });
+                   [&] { CU(launch_sp_s2<T>(pR, pXr, VB.vvoo, imp, canon, ncanon, n, nx, S2c, st())); });
     }
   }
 

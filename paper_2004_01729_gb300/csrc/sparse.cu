@@ -346,9 +346,10 @@ __global__ void sp_rinit_kernel(SpR<T> a) {
   }
 }
 
-// ---- S2 = P(ij)P(ab) R + <ab||ij>_vvoo
+// ---- S2 = P(ij)P(ab) (R + ring) + <ab||ij>_vvoo, the ring term held apart as
+// Xr[i][a][b] (j implied) when Xr is given
 template <class T>
-__global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Vvvoo,
+__global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Xr, const T* __restrict__ Vvvoo,
                              const int16_t* __restrict__ imp, const int* __restrict__ canon, int ncanon, int n,
                              T* __restrict__ S2) {
   // one canonical element (i < j, a < b) per thread, written to its four
@@ -362,7 +363,11 @@ __global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Vvvo
     int i, j, aa;
     dec3(static_cast<uint32_t>(e), static_cast<uint32_t>(n), i, j, aa);
     const int b = imp[e];
-    const T v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
+    T v = r[e] - r[pos3(n, j, i, aa)] - r[pos3(n, i, j, b)] + r[pos3(n, j, i, b)] + Vvvoo[pos3(n, aa, b, i)];
+    if (Xr) {
+      const T* xr = Xr + x * n3;
+      v += (xr[pos3(n, i, aa, b)] - xr[pos3(n, j, aa, b)]) - (xr[pos3(n, i, b, aa)] - xr[pos3(n, j, b, aa)]);
+    }
     s[e] = v;
     s[pos3(n, j, i, aa)] = -v;
     s[pos3(n, i, j, b)] = -v;
@@ -497,7 +502,8 @@ __global__ void __launch_bounds__(THREADS) sector_gemm_kernel(SecGemmArgsT<T> g)
       } else {
         const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
                             static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
-        g.C[q] += v;
+        if (g.store) g.C[q] = v;
+        else g.C[q] += v;
       }
     }
   }
@@ -612,7 +618,8 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) sector_gemm_f32_kerne
       } else {
         const long long q = x * g.cx + static_cast<long long>(pr.x) * g.s0 + static_cast<long long>(pr.y) * g.s1 +
                             static_cast<long long>(pc.x) * g.s2 + static_cast<long long>(pc.y) * g.s3;
-        g.C[q] += v;
+        if (g.store) g.C[q] = v;
+        else g.C[q] += v;
       }
     }
   }
@@ -1237,9 +1244,9 @@ cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2,
 }
 
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon, int n, int nx,
-                         T* S2, cudaStream_t st) {
-  sp_s2_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(R, Vvvoo, imp, canon, ncanon, n, S2);
+cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon,
+                         int n, int nx, T* S2, cudaStream_t st) {
+  sp_s2_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(R, Xr, Vvvoo, imp, canon, ncanon, n, S2);
   return cudaGetLastError();
 }
 
@@ -1295,7 +1302,7 @@ cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, 
                                           const int*, int, cudaStream_t);                                         \
   template cudaError_t launch_sp_rinit<T>(const T*, const T*, const T*, const T*, const SpBlocksT<T>&,             \
                                           const int16_t*, const int*, int, int, int, T*, cudaStream_t);            \
-  template cudaError_t launch_sp_s2<T>(const T*, const T*, const int16_t*, const int*, int, int, int, T*,          \
+  template cudaError_t launch_sp_s2<T>(const T*, const T*, const T*, const int16_t*, const int*, int, int, int, T*, \
                                        cudaStream_t);                                                             \
   template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
   template cudaError_t launch_sector_gemm_small<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                \
