@@ -397,10 +397,11 @@ template <class T>
 cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2, const SpBlocksT<T>& V,
                             const int16_t* imp, const int* list, int nlist, int n, int nx, T* R, cudaStream_t st);
 // S2 from its canonical elements, written to their four orientations; R is
-// [i][j][a] (b implied), Xr the ring term [i][a][b] (j implied) or null
+// [i][j][a] (b implied), Xr the ring term [i][a][b] (j implied) or null, Lc
+// a term given at the canonical elements only (added once) or null
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon,
-                         int n, int nx, T* S2, cudaStream_t st);
+cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Lc, const T* Vvvoo, const int16_t* imp, const int* canon,
+                         int ncanon, int n, int nx, T* S2, cudaStream_t st);
 template <class T> cudaError_t launch_sector_gemm(const SecGemmArgsT<T>& g, int nwork, int nx, cudaStream_t st);
 // the same products for work items of sectors of at most 16 pairs (16 x 16 tiles, 64 threads)
 template <class T>

@@ -931,7 +931,8 @@ struct Solver {
   // <mn||ef> block in the W_mbej operand order.
   void sparse_alloc() {
     const long long n = no, n3 = n * n * n, x = nxc;
-    for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R, &R2}) ensure(h_, *q, x * n3 * sizeof(T));   // R2: the ring term
+    // R2: the ring term [i][a][b]; Lp: the ladders at the canonical elements [i][j][a]
+    for (Buf* q : {&ta, &tt, &Y, &X, &Wmnij, &Wabef, &Wmbej, &R, &R2, &Lp}) ensure(h_, *q, x * n3 * sizeof(T));
     for (Buf* q : {&Fme, &Fae, &Fmi, &Ft, &Ft2}) ensure(h_, *q, x * n * sizeof(T));
     ensure(h_, Vp, n3 * sizeof(T));
     // cotangents of the transpose (sparse_vjp)
@@ -1063,9 +1064,13 @@ struct Solver {
         CU(launch_sp_rinit<T>(t1c, t2c, (T*)Ft.p, (T*)Ft2.p, VB, imp, static_cast<const int*>(b->vall.p), b->nvall, n,
                               nx, pR, st()));
       });
+      T* pLc = pairs ? (T*)Lp.p : nullptr;
       if (pairs) {
-        // L/4 in the four orientations of R: rows i < j | a < b, sums over m < n and e < f
-        sector_product(b->ssum_u, pw1, n3, ptp, n3, pR, 0.25, 0, 0, 0, 0, 0, pta, pwab, 1);
+        // both ladders L at the canonical elements only, rows i < j | a < b,
+        // sums over m < n and e < f: stored at Lc[i][j][a] (written once) and
+        // added by the S2 kernel, which works on the canonical elements (as
+        // L/4 in the four orientations of R it was four read-modify-writes)
+        sector_product(b->ssum_u, pw1, n3, ptp, n3, pLc, 1.0, 0, n2, n, 1, 0, pta, pwab, 0, 1);
       } else {
         // hole ladder 1/8 W'_ijmn tau_mn^ab          rows (i,j) | (a,b) by q_i + q_j, sum over m
         sector_product(b->ssum, pw1, n3, ptp, n3, pR, 0.125, 0, n2, n, 1, 0);
@@ -1079,7 +1084,7 @@ struct Solver {
       // be a read-modify-write of one 32-byte sector per output
       sector_product(b->sdiff, ptr, n3, pwr, n3, pXr, 1.0, 1, n2, n, 1, 0, nullptr, nullptr, 0, 1);
       timed_launch(kClsScatter, 6 * slice, 0.0,
-                   [&] { CU(launch_sp_s2<T>(pR, pXr, VB.vvoo, imp, canon, ncanon, n, nx, S2c, st())); });
+                   [&] { CU(launch_sp_s2<T>(pR, pXr, pLc, VB.vvoo, imp, canon, ncanon, n, nx, S2c, st())); });
     }
   }
 

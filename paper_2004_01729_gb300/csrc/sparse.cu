@@ -346,10 +346,12 @@ __global__ void sp_rinit_kernel(SpR<T> a) {
   }
 }
 
-// ---- S2 = P(ij)P(ab) (R + ring) + <ab||ij>_vvoo, the ring term held apart as
-// Xr[i][a][b] (j implied) when Xr is given
+// ---- S2 = P(ij)P(ab) (R + ring) + L + <ab||ij>_vvoo, the ring term held apart
+// as Xr[i][a][b] (j implied) when Xr is given, L (antisymmetric, the ladders)
+// at the canonical elements when Lc is given
 template <class T>
-__global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Xr, const T* __restrict__ Vvvoo,
+__global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Xr, const T* __restrict__ Lc,
+                             const T* __restrict__ Vvvoo,
                              const int16_t* __restrict__ imp, const int* __restrict__ canon, int ncanon, int n,
                              T* __restrict__ S2) {
   // one canonical element (i < j, a < b) per thread, written to its four
@@ -368,6 +370,7 @@ __global__ void sp_s2_kernel(const T* __restrict__ R, const T* __restrict__ Xr, 
       const T* xr = Xr + x * n3;
       v += (xr[pos3(n, i, aa, b)] - xr[pos3(n, j, aa, b)]) - (xr[pos3(n, i, b, aa)] - xr[pos3(n, j, b, aa)]);
     }
+    if (Lc) v += Lc[x * n3 + e];
     s[e] = v;
     s[pos3(n, j, i, aa)] = -v;
     s[pos3(n, i, j, b)] = -v;
@@ -1244,9 +1247,9 @@ cudaError_t launch_sp_rinit(const T* t1, const T* t2, const T* Ft, const T* Ft2,
 }
 
 template <class T>
-cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Vvvoo, const int16_t* imp, const int* canon, int ncanon,
-                         int n, int nx, T* S2, cudaStream_t st) {
-  sp_s2_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(R, Xr, Vvvoo, imp, canon, ncanon, n, S2);
+cudaError_t launch_sp_s2(const T* R, const T* Xr, const T* Lc, const T* Vvvoo, const int16_t* imp, const int* canon,
+                         int ncanon, int n, int nx, T* S2, cudaStream_t st) {
+  sp_s2_kernel<T><<<dim3(sp_grid(ncanon), nx), kSpThreads, 0, st>>>(R, Xr, Lc, Vvvoo, imp, canon, ncanon, n, S2);
   return cudaGetLastError();
 }
 
@@ -1302,8 +1305,8 @@ cudaError_t launch_sp_thermal_fock(const double* fbar, int n, const double* f0, 
                                           const int*, int, cudaStream_t);                                         \
   template cudaError_t launch_sp_rinit<T>(const T*, const T*, const T*, const T*, const SpBlocksT<T>&,             \
                                           const int16_t*, const int*, int, int, int, T*, cudaStream_t);            \
-  template cudaError_t launch_sp_s2<T>(const T*, const T*, const T*, const int16_t*, const int*, int, int, int, T*, \
-                                       cudaStream_t);                                                             \
+  template cudaError_t launch_sp_s2<T>(const T*, const T*, const T*, const T*, const int16_t*, const int*, int, int, \
+                                       int, T*, cudaStream_t);                                                    \
   template cudaError_t launch_sector_gemm<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                      \
   template cudaError_t launch_sector_gemm_small<T>(const SecGemmArgsT<T>&, int, int, cudaStream_t);                \
   template cudaError_t launch_sp_thermal_eri<T>(const double*, const int16_t*, int, const double*, const double*,  \
