@@ -2693,7 +2693,7 @@ std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
   }
   // every batch keeps one iteration in flight on its own stream: as soon as
   // its last iteration is collected (and the phase logic has run), its next
-  // one is enqueued, so no batch waits for the slowest one of a round
+  // one is enqueued, so no batch waits for the slowest of the others
   for (auto& d : ds)
     if (d && !d->finished) d->launch();
   for (;;) {
