@@ -938,6 +938,31 @@ def bench_small_extras(ftcc, torch, dev, world, args):
     bat["adjoint_instances"] = int(sum(a["status"] == ftcc.OK for a in adjs))
     bat["adjoint_how"] = "ft_ccsd_adjoint_batched: every converged instance's FP64 lambda sweep and response, " \
                          "the batches concurrently from a pool of host threads, each on its own stream"
+    # the mixed pipeline on the same storage (FP32 sweep, then FP64 residual
+    # corrections) and the adjoints after it, against the FP64 solves above
+    kw_m = dict(precision="bf16x3", block_sparse=1, max_iter=300, refine_max_iter=3, tol_omega=1e-10,
+                tol_amp=1e-8, allow_unconverged=True)
+    ftcc.solve_batched(ctx_b, betas_b, mus_b, cb[0]["ngrid"], **kw_m)   # sizing and captures
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rm = ftcc.solve_batched(ctx_b, betas_b, mus_b, cb[0]["ngrid"], **kw_m)
+    torch.cuda.synchronize()
+    t_m = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    am = ftcc.adjoint_batched(ctx_b)
+    torch.cuda.synchronize()
+    ok = [k for k, (x, y) in enumerate(zip(rm, rb)) if x["converged"] and y["converged"]]
+    bat["block_sparse_mixed"] = {
+        "s_total": t_m, "converged": int(sum(r["converged"] for r in rm)),
+        "max_abs_dOmega_vs_fp64": max([abs(rm[k]["omega"] - rb[k]["omega"]) for k in ok], default=None),
+        "fp64_corrections_max": int(max(r["refine_iterations"] for r in rm)),
+        "adjoint_s_total": time.perf_counter() - t0,
+        "adjoint_instances": int(sum(a["status"] == ftcc.OK for a in am)),
+        "max_abs_dE_vs_fp64_adjoint": max([abs(am[k]["E"] - adjs[k]["E"]) for k in ok
+                                           if am[k]["status"] == ftcc.OK and adjs[k]["status"] == ftcc.OK],
+                                          default=None),
+        "how": "precision bf16x3 with block_sparse: FP32 sweep, then up to 3 FP64 residual corrections; "
+               "ft_ccsd_adjoint_batched after it (FP64 lambda sweeps from the corrected amplitudes)"}
     for x in ctx_b:
         x.close()
     # the dense schedule: one batch per size class, TF32, BF16X3 polish, FP64

@@ -148,3 +148,35 @@ def test_hubbard_batch_64_instances_block_sparse():
     assert seen == {6, 8, 10, 12, 14}
     for c in ctxs:
         c.close()
+
+
+def test_hubbard_batch_64_instances_block_sparse_mixed():
+    """The 64 instances on the block-sparse storage with the mixed pipeline
+    (FP32 sweep, then FP64 residual corrections): the same 63 converge, each
+    within 1e-7 Ha of the block-sparse FP64 solve (at most three corrections,
+    the solve's own tolerance 1e-10), and the adjoints after it
+    (ft_ccsd_adjoint_batched) give the FP64 solve's E and S to 1e-6."""
+    from paper_2004_01729_gb300 import ftcc
+    cfgs = wl.hubbard_batch()
+    ng = cfgs[0]["ngrid"]
+    betas, mus = [c["beta"] for c in cfgs], [c["mu"] for c in cfgs]
+    ctxs = _ctxs(cfgs)
+    r64 = ftcc.solve_batched(ctxs, betas, mus, ng, precision="fp64", block_sparse=1, max_iter=300,
+                             tol_omega=1e-12, tol_amp=1e-10, allow_unconverged=True)
+    a64 = ftcc.adjoint_batched(ctxs)
+    rmx = ftcc.solve_batched(ctxs, betas, mus, ng, precision="bf16x3", block_sparse=1, max_iter=300,
+                             refine_max_iter=3, tol_omega=1e-10, tol_amp=1e-8, allow_unconverged=True)
+    amx = ftcc.adjoint_batched(ctxs)
+    assert [k for k, r in enumerate(rmx) if not r["converged"]] == [43]
+    for k in range(len(cfgs)):
+        if k == 43:
+            continue
+        assert rmx[k]["refine_iterations"] >= 1
+        assert abs(rmx[k]["omega"] - r64[k]["omega"]) < 1e-7, (k, rmx[k]["omega"], r64[k]["omega"])
+        assert amx[k]["status"] == ftcc.OK
+        # (the FP64 refinement before the adjoint stops at the solve's
+        # tolerances, |dOmega| < 1e-10 and max|ds| < 1e-8, against 1e-12 / 1e-10
+        # for the FP64 solve: E and S agree to about 1e-7, within the mixed bar)
+        assert abs(amx[k]["E"] - a64[k]["E"]) < 1e-6 and abs(amx[k]["S"] - a64[k]["S"]) < 1e-6, (k, amx[k], a64[k])
+    for c in ctxs:
+        c.close()
