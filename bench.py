@@ -925,8 +925,8 @@ def bench_small_extras(ftcc, torch, dev, world, args):
     rb = ftcc.solve_batched(ctx_b, betas_b, mus_b, cb[0]["ngrid"], **kw_sp)
     torch.cuda.synchronize()
     bat = {"workload": "64 hubbard_1d instances, L in {6..14}, U in [1,8], T in [0.25,4], half filling, ngrid=24; "
-                       "block-sparse FP64, every instance its own batch on its own stream, each with one iteration "
-                       "in flight",
+                       "block-sparse FP64, every instance its own batch; once each has captured its iteration, a step "
+                       "of all unfinished instances is one graph launch (their iterations as child graphs)",
            "s_total": time.perf_counter() - t0, "instances": len(cb),
            "converged": int(sum(r["converged"] for r in rb)),
            "iterations_max": int(max(r["iterations"] for r in rb))}

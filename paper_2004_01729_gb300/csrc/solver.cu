@@ -263,6 +263,8 @@ struct Solver {
   Buf part1, part2;
   int nb1 = 0, nb2 = 0;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;   // the captured iteration gexec was made from (a batched step embeds it)
+  unsigned graph_gen = 0;        // bumped at every capture
   bool warm = false;       // one uncaptured iteration has sized every workspace
   int graph_nodes = 0;     // kernels in one captured iteration
   long long gemm_flops = 0;   // algorithmic GEMM flops counted while `counting`
@@ -353,11 +355,14 @@ struct Solver {
     amp_cache.clear();
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+    graph = nullptr;
     warm = false;
     graph_nodes = 0;
   }
   ~Solver() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
     for (auto& kv : Vb) h_->put(kv.second);
     for (auto& kv : Fb) h_->put(kv.second);
     for (auto& kv : packed) {
@@ -2040,7 +2045,9 @@ void run_iterations(Batch& B, Solver<T>& s, int n) {
       CU(cudaGraphGetNodes(g, nullptr, &nn));
       s.graph_nodes = static_cast<int>(nn);
       CU(cudaGraphInstantiate(&s.gexec, g, 0));
-      cudaGraphDestroy(g);
+      if (s.graph) cudaGraphDestroy(s.graph);
+      s.graph = g;   // kept: a batched step embeds it in one graph with the other batches'
+      ++s.graph_gen;
       CU(cudaGraphLaunch(s.gexec, h->st));
     } else {
       iterate_once<T>(B, s);
@@ -2523,6 +2530,14 @@ struct SolveDriver {
                          cudaMemcpyDeviceToHost, h->st));
     CU(cudaEventRecord(e2, h->st));
   }
+  // after a grouped step (its state already in pinned memory): the
+  // convergence and phase logic
+  void collect_grouped(float ms) {
+    B.ms_total += ms;
+    B.ms_count += 1;
+    s.assign(pin, pin + static_cast<size_t>(B.nz) * kStateStride);
+    step();
+  }
   // wait for it, then the convergence and phase logic
   void collect() {
     CU(cudaEventSynchronize(e2));
@@ -2674,8 +2689,77 @@ ftcc_status solve_batch(Batch& B) {
   return d.status;
 }
 
-// The batches of one batched solve advanced together, each with one
-// iteration in flight on its own stream.
+// The captured iteration of a batch's current solver, if a step of it can
+// run inside a graph of many batches (captured, not profiling).
+cudaGraph_t step_graph(Batch& B, unsigned* gen) {
+  if (!B.opt.use_graph) return nullptr;
+  if (B.active == 1) {
+    if (!B.s32 || !B.s32->gexec || B.s32->profiling) return nullptr;
+    *gen = B.s32->graph_gen;
+    return B.s32->graph;
+  }
+  if (!B.s64 || !B.s64->gexec || B.s64->profiling) return nullptr;
+  *gen = B.s64->graph_gen;
+  return B.s64->graph;
+}
+
+// One step of several batches as one graph launch: every member's captured
+// iteration as a child node, each followed by the copy of its convergence
+// state to the pinned host memory of its home context.  The graph is rebuilt
+// when the members or one of their iterations change (a batch finished, or
+// switched precision); between rebuilds a step is one cudaGraphLaunch and one
+// wait, where one launch, copy and wait per batch made the host the bound of
+// a step of many small instances.
+struct GroupStep {
+  std::vector<SolveDriver*> members;
+  std::vector<std::pair<cudaGraph_t, unsigned>> keys;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr, done = nullptr;
+  bool broken = false;   // building failed once: batches launch on their own
+  ~GroupStep() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (done) cudaEventDestroy(done);
+  }
+  bool ready(const std::vector<SolveDriver*>& ms, const std::vector<std::pair<cudaGraph_t, unsigned>>& ks) {
+    if (exec && ms == members && ks == keys) return true;
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    members.clear();
+    keys.clear();
+    if (!t0 && (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess ||
+                cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess))
+      return false;
+    cudaGraph_t P = nullptr;
+    if (cudaGraphCreate(&P, 0) != cudaSuccess) return false;
+    bool ok = true;
+    for (size_t k = 0; ok && k < ms.size(); ++k) {
+      cudaGraphNode_t c = nullptr, cp = nullptr;
+      ok = cudaGraphAddChildGraphNode(&c, P, nullptr, 0, ks[k].first) == cudaSuccess &&
+           cudaGraphAddMemcpyNode1D(&cp, P, &c, 1, ms[k]->pin, ms[k]->B.state.p,
+                                    static_cast<size_t>(ms[k]->B.nz) * kStateStride * sizeof(double),
+                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    ok = ok && cudaGraphInstantiate(&exec, P, 0) == cudaSuccess;
+    cudaGraphDestroy(P);
+    if (!ok) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      cudaGetLastError();   // (the failure is reported by falling back, not as a sticky error)
+      return false;
+    }
+    members = ms;
+    keys = ks;
+    return true;
+  }
+};
+
+// The batches of one batched solve advanced together.  Once every unfinished
+// batch has captured its iteration, a step of all of them is one graph
+// (GroupStep); before that, or for a batch that cannot join (no pinned state
+// copy, profiling, no graph), each batch runs on its own stream with one
+// iteration in flight.
 std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
   std::vector<ftcc_status> st(Bs.size(), FTCC_OK);
   std::vector<std::unique_ptr<SolveDriver>> ds;
@@ -2691,20 +2775,51 @@ std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
     for (size_t q = 0; q < k; ++q) shared = shared || Bs[q]->home == Bs[k]->home;
     ds.emplace_back(new SolveDriver(*Bs[k], !shared));
   }
-  // every batch keeps one iteration in flight on its own stream: as soon as
-  // its last iteration is collected (and the phase logic has run), its next
-  // one is enqueued, so no batch waits for the slowest of the others
-  for (auto& d : ds)
-    if (d && !d->finished) d->launch();
+  GroupStep grp;
   for (;;) {
-    bool any = false;
-    for (auto& d : ds)
-      if (d && !d->finished) {
-        any = true;
-        d->collect();
-        if (!d->finished) d->launch();
+    std::vector<SolveDriver*> solo, grouped;
+    std::vector<std::pair<cudaGraph_t, unsigned>> keys;
+    for (auto& d : ds) {
+      if (!d || d->finished) continue;
+      unsigned gen = 0;
+      cudaGraph_t g = d->pin && !grp.broken ? step_graph(d->B, &gen) : nullptr;
+      if (g) {
+        grouped.push_back(d.get());
+        keys.emplace_back(g, gen);
+      } else {
+        solo.push_back(d.get());
       }
-    if (!any) break;
+    }
+    if (solo.empty() && grouped.empty()) break;
+    if (grouped.size() < 2 || !grp.ready(grouped, keys)) {
+      if (grouped.size() >= 2) grp.broken = true;
+      solo.insert(solo.end(), grouped.begin(), grouped.end());
+      grouped.clear();
+    }
+    for (SolveDriver* d : solo) d->launch();
+    if (!grouped.empty()) {
+      cudaStream_t s0 = grouped[0]->h->st;
+      for (SolveDriver* d : grouped) {
+        if (d->h->st == s0) continue;
+        CU(cudaEventRecord(d->e1, d->h->st));   // the member's earlier work (host copies, phase changes)
+        CU(cudaStreamWaitEvent(s0, d->e1, 0));
+      }
+      CU(cudaEventRecord(grp.t0, s0));
+      CU(cudaGraphLaunch(grp.exec, s0));
+      CU(cudaEventRecord(grp.t1, s0));
+      CU(cudaEventRecord(grp.done, s0));
+      for (SolveDriver* d : grouped) {
+        d->B.iterations += 1;
+        if (d->h->st != s0) CU(cudaStreamWaitEvent(d->h->st, grp.done, 0));
+      }
+    }
+    for (SolveDriver* d : solo) d->collect();
+    if (!grouped.empty()) {
+      CU(cudaEventSynchronize(grp.done));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, grp.t0, grp.t1);
+      for (SolveDriver* d : grouped) d->collect_grouped(ms);
+    }
   }
   for (size_t k = 0; k < ds.size(); ++k)
     if (ds[k]) st[k] = ds[k]->status;
@@ -3870,6 +3985,8 @@ ftcc_status ftcc_profile(ftcc_ctx* c, int enable) {
       if (s->profiling != (enable != 0)) {
         if (s->gexec) cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->graph = nullptr;
         s->warm = false;   // the next iteration runs uncaptured, then a new graph with / without event nodes
       }
       s->profiling = enable != 0;
