@@ -2755,11 +2755,12 @@ struct GroupStep {
   }
 };
 
-// The batches of one batched solve advanced together.  Once every unfinished
-// batch has captured its iteration, a step of all of them is one graph
-// (GroupStep); before that, or for a batch that cannot join (no pinned state
-// copy, profiling, no graph), each batch runs on its own stream with one
-// iteration in flight.
+// The batches of one batched solve advanced together.  With at least
+// kGroupMinBatches batches, once every unfinished batch has captured its
+// iteration a step of all of them is one graph (GroupStep); before that, or
+// for a batch that cannot join (no pinned state copy, profiling, no graph),
+// a batch steps on its own stream.
+constexpr int kGroupMinBatches = 8;
 std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
   std::vector<ftcc_status> st(Bs.size(), FTCC_OK);
   std::vector<std::unique_ptr<SolveDriver>> ds;
@@ -2774,6 +2775,30 @@ std::vector<ftcc_status> solve_batches(const std::vector<Batch*>& Bs) {
     bool shared = false;
     for (size_t q = 0; q < k; ++q) shared = shared || Bs[q]->home == Bs[k]->home;
     ds.emplace_back(new SolveDriver(*Bs[k], !shared));
+  }
+  // many small batches (the block-sparse batching makes one per instance):
+  // grouped steps; a few batches (size classes of the dense batching):
+  // every batch keeps one iteration in flight on its own stream, so that no
+  // batch waits for the slowest of the others
+  int npinned = 0;
+  for (auto& d : ds)
+    if (d && d->pin) ++npinned;
+  if (npinned < kGroupMinBatches) {
+    for (auto& d : ds)
+      if (d && !d->finished) d->launch();
+    for (;;) {
+      bool any = false;
+      for (auto& d : ds)
+        if (d && !d->finished) {
+          any = true;
+          d->collect();
+          if (!d->finished) d->launch();
+        }
+      if (!any) break;
+    }
+    for (size_t k = 0; k < ds.size(); ++k)
+      if (ds[k]) st[k] = ds[k]->status;
+    return st;
   }
   GroupStep grp;
   for (;;) {
