@@ -335,8 +335,11 @@ ftcc_status ft_ccsd_solve(ftcc_ctx* ctx, double beta, double mu, int ngrid,
  * quadrature and options.  Instances with equal spin-orbital counts (and
  * equal truncation sets) form one batch: every contraction, propagation and
  * reduction of an iteration covers the whole batch in one launch, and one
- * CUDA graph replays the iteration; batches of different sizes run one after
- * another.  out[i] receives instance i.  Returns the first failure
+ * CUDA graph replays the iteration (with block_sparse every instance is a
+ * batch of its own).  The batches advance together: fewer than eight each
+ * keep one iteration in flight on their own home stream; eight or more,
+ * once each has captured its iteration, step as one graph launch holding
+ * every unfinished batch's iteration.  out[i] receives instance i.  Returns the first failure
  * (FTCC_ERR_DIVERGED before FTCC_ERR_NOT_CONVERGED); FTCC_ERR_INVALID_ARG for
  * a repeated context, mixed devices, or truncation sets that differ inside a
  * size class.  The batch's memory comes from the allocator of its first
